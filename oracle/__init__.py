@@ -1,0 +1,265 @@
+"""Plain FP64 CPU oracle of the DSPS photometry hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the package smoke check and
+by the CPU-baseline leg of ``bench.py``.  The product path never imports it.
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, loop by loop,
+each function citing the equation of Hearin et al. 2021, arXiv:2112.06830 it
+follows).  This module compiles it with gcc on first use and marshals numpy
+arrays through ctypes.  Parameters use the structure-of-arrays layout described
+in ``oracle.c``: ``params[12, G]`` (sfh0..4, mdf_mu, mdf_sigma, mdf_slope, Av,
+delta, logM, z) and gradients ``[11, G]`` (the same rows without z).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NPAR = 12
+NGRAD = 11
+AB0 = 1.13492e-13
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_build/liboracle.so (gcc, -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Grid(C.Structure):
+    _fields_ = [("n_age", C.c_int), ("n_z", C.c_int), ("n_lam", C.c_int),
+                ("log_age_yr", C.POINTER(C.c_double)), ("lgz", C.POINTER(C.c_double)),
+                ("lam", C.POINTER(C.c_double)), ("l_ssp", C.POINTER(C.c_double)),
+                ("t0", C.c_double), ("t1", C.c_double), ("n_t", C.c_int),
+                ("om0", C.c_double), ("w0", C.c_double), ("h", C.c_double),
+                ("sfh_model", C.c_int), ("mdf_kernel", C.c_int)]
+
+
+class _Filters(C.Structure):
+    _fields_ = [("n_filt", C.c_int), ("n_pts", C.POINTER(C.c_int)),
+                ("lam", C.POINTER(C.c_double)), ("trans", C.POINTER(C.c_double))]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            dp = C.POINTER(C.c_double)
+            for name in ("orc_triweight_pdf", "orc_triweight_cdf", "orc_gauss_cdf", "orc_gauss_pdf"):
+                getattr(lib, name).restype = C.c_double
+                getattr(lib, name).argtypes = [C.c_double]
+            for name in ("orc_age_gyr", "orc_lum_dist_mpc", "orc_dist_mod"):
+                getattr(lib, name).restype = C.c_double
+                getattr(lib, name).argtypes = [C.c_double] * 4
+            lib.orc_sfr.restype = C.c_double
+            lib.orc_sfr.argtypes = [C.c_int, dp, C.c_double, dp]
+            lib.orc_cum_mass.restype = C.c_double
+            lib.orc_cum_mass.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double, dp]
+            lib.orc_age_edges_gyr.argtypes = [C.POINTER(_Grid), dp]
+            lib.orc_age_fracs_from_sfr.argtypes = [C.POINTER(_Grid), dp, C.c_double, dp]
+            lib.orc_mdf.argtypes = [C.POINTER(_Grid), C.c_double, C.c_double, dp, dp, dp]
+            lib.orc_dust_trans.restype = C.c_double
+            lib.orc_dust_trans.argtypes = [C.c_double] * 3
+            lib.orc_filter_trans.restype = C.c_double
+            lib.orc_filter_trans.argtypes = [dp, dp, C.c_int, C.c_double]
+            lib.orc_filter_norm.restype = C.c_double
+            lib.orc_filter_norm.argtypes = [dp, dp, C.c_int]
+            lib.orc_mags_from_weights.argtypes = [C.POINTER(_Grid), C.POINTER(_Filters), dp,
+                                                  C.c_double, C.c_double, C.c_double, C.c_double,
+                                                  C.c_double, dp]
+            lib.orc_weights.argtypes = [C.POINTER(_Grid), C.c_long, dp, dp, C.c_int]
+            lib.orc_mags.argtypes = [C.POINTER(_Grid), C.POINTER(_Filters), C.c_long, dp, dp, C.c_int]
+            lib.orc_mags_vjp.argtypes = [C.POINTER(_Grid), C.POINTER(_Filters), C.c_long, dp, dp,
+                                         dp, dp, C.c_int]
+            _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Grid:
+    """SSP grid + SFR time grid + cosmology + model switches, held as float64."""
+
+    def __init__(self, log_age_yr, lgz, lam, l_ssp, t0=0.05, t1=13.8, n_t=200,
+                 om0=0.3, w0=-1.0, h=0.7, sfh_model=0, mdf_kernel=0):
+        self.log_age_yr = _f64(log_age_yr)
+        self.lgz = _f64(lgz)
+        self.lam = _f64(lam)
+        self.l_ssp = _f64(l_ssp).reshape(len(self.log_age_yr), len(self.lgz), len(self.lam))
+        self.t0, self.t1, self.n_t = float(t0), float(t1), int(n_t)
+        self.om0, self.w0, self.h = float(om0), float(w0), float(h)
+        self.sfh_model, self.mdf_kernel = int(sfh_model), int(mdf_kernel)
+        self._c = _Grid(len(self.log_age_yr), len(self.lgz), len(self.lam), _dp(self.log_age_yr),
+                        _dp(self.lgz), _dp(self.lam), _dp(self.l_ssp), self.t0, self.t1, self.n_t,
+                        self.om0, self.w0, self.h, self.sfh_model, self.mdf_kernel)
+
+    @property
+    def n_age(self):
+        return len(self.log_age_yr)
+
+    @property
+    def n_z(self):
+        return len(self.lgz)
+
+    @property
+    def n_lam(self):
+        return len(self.lam)
+
+
+class Filters:
+    """A list of (lambda [A], transmission) tables."""
+
+    def __init__(self, tables):
+        self.tables = [(_f64(l), _f64(t)) for l, t in tables]
+        self.n_pts = np.array([len(l) for l, _ in self.tables], dtype=np.int32)
+        self.lam = _f64(np.concatenate([l for l, _ in self.tables]))
+        self.trans = _f64(np.concatenate([t for _, t in self.tables]))
+        self._c = _Filters(len(self.tables), self.n_pts.ctypes.data_as(C.POINTER(C.c_int)),
+                           _dp(self.lam), _dp(self.trans))
+
+    @property
+    def n_filt(self):
+        return len(self.tables)
+
+
+def _nthreads(n):
+    if n is not None:
+        return int(n)
+    return os.cpu_count() or 1
+
+
+# ---- scalar functions -------------------------------------------------------
+
+def triweight_pdf(z):
+    return _load().orc_triweight_pdf(float(z))
+
+
+def triweight_cdf(z):
+    return _load().orc_triweight_cdf(float(z))
+
+
+def gauss_cdf(z):
+    return _load().orc_gauss_cdf(float(z))
+
+
+def age_gyr(z, om0=0.3, w0=-1.0, h=0.7):
+    return _load().orc_age_gyr(om0, w0, h, float(z))
+
+
+def lum_dist_mpc(z, om0=0.3, w0=-1.0, h=0.7):
+    return _load().orc_lum_dist_mpc(om0, w0, h, float(z))
+
+
+def dist_mod(z, om0=0.3, w0=-1.0, h=0.7):
+    return _load().orc_dist_mod(om0, w0, h, float(z))
+
+
+def sfr(model, p, t):
+    p = _f64(np.resize(np.asarray(p, dtype=np.float64), 5))
+    g = np.zeros(5)
+    v = _load().orc_sfr(int(model), _dp(p), float(t), _dp(g))
+    return v, g
+
+
+def cum_mass(sfr_nodes, t0, t1, tau):
+    s = _f64(sfr_nodes)
+    coef = np.zeros(len(s))
+    v = _load().orc_cum_mass(_dp(s), len(s), float(t0), float(t1), float(tau), _dp(coef))
+    return v, coef
+
+
+def age_edges_gyr(grid: Grid):
+    e = np.zeros(grid.n_age + 1)
+    _load().orc_age_edges_gyr(C.byref(grid._c), _dp(e))
+    return e
+
+
+def age_fracs_from_sfr(grid: Grid, sfr_nodes, t_obs):
+    s = _f64(sfr_nodes)
+    assert len(s) == grid.n_t
+    out = np.zeros(grid.n_age)
+    _load().orc_age_fracs_from_sfr(C.byref(grid._c), _dp(s), float(t_obs), _dp(out))
+    return out
+
+
+def mdf(grid: Grid, mu_i, sigma):
+    P, dmu, dsig = np.zeros(grid.n_z), np.zeros(grid.n_z), np.zeros(grid.n_z)
+    _load().orc_mdf(C.byref(grid._c), float(mu_i), float(sigma), _dp(P), _dp(dmu), _dp(dsig))
+    return P, dmu, dsig
+
+
+def dust_trans(lam, Av, delta):
+    return _load().orc_dust_trans(float(lam), float(Av), float(delta))
+
+
+def filter_trans(lam_tab, tr_tab, x):
+    l, t = _f64(lam_tab), _f64(tr_tab)
+    return _load().orc_filter_trans(_dp(l), _dp(t), len(l), float(x))
+
+
+def filter_norm(lam_tab, tr_tab):
+    l, t = _f64(lam_tab), _f64(tr_tab)
+    return _load().orc_filter_norm(_dp(l), _dp(t), len(l))
+
+
+def mags_from_weights(grid: Grid, filters: Filters, omega, Av, delta, logM, z, dmod):
+    w = _f64(omega).reshape(-1)
+    out = np.zeros(filters.n_filt)
+    _load().orc_mags_from_weights(C.byref(grid._c), C.byref(filters._c), _dp(w), float(Av),
+                                  float(delta), float(logM), float(z), float(dmod), _dp(out))
+    return out
+
+
+# ---- batched entry points ---------------------------------------------------
+
+def weights(grid: Grid, params, nthreads=None):
+    """SSP weights in Msun, shape [G, n_age, n_z]."""
+    p = _f64(params)
+    G = p.shape[1]
+    out = np.zeros((G, grid.n_age, grid.n_z))
+    _load().orc_weights(C.byref(grid._c), G, _dp(p), _dp(out), _nthreads(nthreads))
+    return out
+
+
+def mags(grid: Grid, filters: Filters, params, nthreads=None):
+    """Observer-frame AB magnitudes, shape [G, Q]."""
+    p = _f64(params)
+    G = p.shape[1]
+    out = np.zeros((G, filters.n_filt))
+    _load().orc_mags(C.byref(grid._c), C.byref(filters._c), G, _dp(p), _dp(out), _nthreads(nthreads))
+    return out
+
+
+def mags_vjp(grid: Grid, filters: Filters, params, mag_bar, nthreads=None):
+    """Returns (mags [G, Q], param_bar [11, G]) with param_bar = J^T mag_bar."""
+    p = _f64(params)
+    G = p.shape[1]
+    mb = _f64(mag_bar).reshape(G, filters.n_filt)
+    m = np.zeros((G, filters.n_filt))
+    pb = np.zeros((NGRAD, G))
+    _load().orc_mags_vjp(C.byref(grid._c), C.byref(filters._c), G, _dp(p), _dp(mb), _dp(m), _dp(pb),
+                         _nthreads(nthreads))
+    return m, pb

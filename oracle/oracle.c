@@ -1,0 +1,584 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle of the DSPS photometry hot path
+ * (Hearin et al., "DSPS: Differentiable Stellar Population Synthesis").
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the package smoke check and the
+ * benchmark's CPU-baseline leg load this file. The product path (the CUDA
+ * library) never includes, links or calls it, and this file includes nothing
+ * from the product path.
+ *
+ * Every function is a direct, loop-by-loop statement of the paper's equations
+ * in double precision, with no blocking, fusion or reordering beyond what the
+ * equation itself states.  Where the paper is silent or garbled the reading
+ * taken is stated beside the code.
+ *
+ * Parameter layout (per galaxy, structure of arrays, row r at params + r*G):
+ *   rows 0..4  SFH parameters
+ *              model 0 (delayed tau):  p0 = tau [Gyr]
+ *              model 1 (double power law with quench):
+ *                      p0 = t_peak [Gyr], p1 = alpha_rise, p2 = alpha_fall,
+ *                      p3 = t_q [Gyr], p4 = q_drop [dex]
+ *   row 5      mdf_mu     (log10 Z/Zsun at the 1 Gyr pivot)
+ *   row 6      mdf_sigma  [dex]
+ *   row 7      mdf_slope  d mu / d log10(age/yr)
+ *   row 8      Av
+ *   row 9      dust delta
+ *   row 10     logM       log10 of the stellar mass formed by t_obs [Msun]
+ *   row 11     z          redshift
+ * Gradient layout (11 rows): rows 0..10 of the above (z gets no gradient).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_NPAR 12
+#define ORC_NGRAD 11
+#define ORC_AB0 1.13492e-13          /* Sec. 2.2, Eq. (restmag): AB zero point at 10 pc, Lsun/Hz */
+#define ORC_LAMV 5500.0              /* Sec. 3.4, Eq. (salim): lambda_V in Angstrom */
+#define ORC_SIGQ 0.3                 /* width of the quench transition [Gyr] (reading) */
+#define ORC_C_KMS 299792.458
+#define ORC_GYR_PER_INV_H0 977.792221 /* 1/(1 km/s/Mpc) in Gyr */
+
+typedef struct {
+    int n_age, n_z, n_lam;
+    const double *log_age_yr;  /* [n_age] log10(age/yr), increasing        */
+    const double *lgz;         /* [n_z]   log10(Z/Zsun), increasing        */
+    const double *lam;         /* [n_lam] rest wavelength, Angstrom        */
+    const double *l_ssp;       /* [n_age][n_z][n_lam] Lsun/Hz/Msun         */
+    double t0, t1;             /* cosmic-time grid for SFR, Gyr            */
+    int n_t;
+    double om0, w0, h;         /* flat wCDM                                 */
+    int sfh_model;             /* 0 delayed tau, 1 double power law+quench */
+    int mdf_kernel;            /* 0 triweight, 1 Gaussian                  */
+} orc_grid;
+
+typedef struct {
+    int n_filt;
+    const int *n_pts;          /* [n_filt]                                  */
+    const double *lam;         /* concatenated tables, Angstrom, increasing */
+    const double *trans;       /* concatenated transmissions                */
+} orc_filters;
+
+/* ------------------------------------------------------------------ */
+/* Appendix B: triweight kernel and its cumulative integral            */
+/* ------------------------------------------------------------------ */
+
+/* Eq. (triweight), as a density in z = (x - mu)/sigma. */
+double orc_triweight_pdf(double z)
+{
+    if (z < -3.0 || z > 3.0) return 0.0;
+    double t = 1.0 - (z / 3.0) * (z / 3.0);
+    return 35.0 / 96.0 * t * t * t;
+}
+
+/* Eq. (terf).  Reading: 0 below z = -3 and 1 above z = +3 (the printed
+ * "0 otherwise" contradicts p(3) = 1). */
+double orc_triweight_cdf(double z)
+{
+    if (z <= -3.0) return 0.0;
+    if (z >= 3.0) return 1.0;
+    double z2 = z * z, z3 = z2 * z, z5 = z3 * z2, z7 = z5 * z2;
+    return 0.5 + 35.0 / 96.0 * z - 35.0 / 864.0 * z3 + 7.0 / 2592.0 * z5 - 5.0 / 69984.0 * z7;
+}
+
+double orc_gauss_cdf(double z) { return 0.5 * erfc(-z / sqrt(2.0)); }
+double orc_gauss_pdf(double z) { return exp(-0.5 * z * z) / sqrt(2.0 * M_PI); }
+
+static double mdf_cdf(int kernel, double z) { return kernel == 0 ? orc_triweight_cdf(z) : orc_gauss_cdf(z); }
+static double mdf_pdf(int kernel, double z) { return kernel == 0 ? orc_triweight_pdf(z) : orc_gauss_pdf(z); }
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.2: flat wCDM time of observation and distance modulus        */
+/* ------------------------------------------------------------------ */
+
+static double cosmo_E(double om0, double w0, double z)
+{
+    double a1 = 1.0 + z;
+    return sqrt(om0 * a1 * a1 * a1 + (1.0 - om0) * pow(a1, 3.0 * (1.0 + w0)));
+}
+
+typedef struct { double om0, w0; int which; } cosmo_args;
+
+/* which = 0: 1/E(z) (comoving distance integrand in z).
+ * which = 1: age integrand after a = s^2:  2 / (s E(z(s))), z = 1/s^2 - 1. */
+static double cosmo_integrand(const cosmo_args *c, double x)
+{
+    if (c->which == 0) return 1.0 / cosmo_E(c->om0, c->w0, x);
+    if (x <= 0.0) return 0.0;
+    double z = 1.0 / (x * x) - 1.0;
+    return 2.0 / (x * cosmo_E(c->om0, c->w0, z));
+}
+
+static double simpson_rec(const cosmo_args *c, double a, double b, double fa, double fm, double fb,
+                          double whole, double tol, int depth)
+{
+    double m = 0.5 * (a + b);
+    double lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+    double flm = cosmo_integrand(c, lm), frm = cosmo_integrand(c, rm);
+    double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
+    double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+    double diff = left + right - whole;
+    if (depth <= 0 || fabs(diff) <= 15.0 * tol) return left + right + diff / 15.0;
+    return simpson_rec(c, a, m, fa, flm, fm, left, 0.5 * tol, depth - 1) +
+           simpson_rec(c, m, b, fm, frm, fb, right, 0.5 * tol, depth - 1);
+}
+
+static double adaptive_simpson(const cosmo_args *c, double a, double b, double tol)
+{
+    if (b <= a) return 0.0;
+    double fa = cosmo_integrand(c, a), fb = cosmo_integrand(c, b), fm = cosmo_integrand(c, 0.5 * (a + b));
+    double whole = (b - a) / 6.0 * (fa + 4.0 * fm + fb);
+    return simpson_rec(c, a, b, fa, fm, fb, whole, tol, 48);
+}
+
+/* Age of the universe at z [Gyr]:  t = (1/H0) * int_0^{a} da / (a E(a)),
+ * evaluated with a = s^2 so the integrand is smooth at s = 0. */
+double orc_age_gyr(double om0, double w0, double h, double z)
+{
+    cosmo_args c = {om0, w0, 1};
+    double smax = sqrt(1.0 / (1.0 + z));
+    double I = adaptive_simpson(&c, 0.0, smax, 1e-14);
+    return ORC_GYR_PER_INV_H0 / (100.0 * h) * I;
+}
+
+/* Luminosity distance [Mpc]: d_L = (1+z) (c/H0) int_0^z dz'/E(z'). */
+double orc_lum_dist_mpc(double om0, double w0, double h, double z)
+{
+    cosmo_args c = {om0, w0, 0};
+    double I = adaptive_simpson(&c, 0.0, z, 1e-14);
+    return (1.0 + z) * ORC_C_KMS / (100.0 * h) * I;
+}
+
+/* Distance modulus 5 log10(d_L / 10 pc). */
+double orc_dist_mod(double om0, double w0, double h, double z)
+{
+    return 5.0 * log10(orc_lum_dist_mpc(om0, w0, h, z) * 1e5);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.1: star formation history on the cosmic-time grid            */
+/* ------------------------------------------------------------------ */
+
+/* SFR(t) for the two parametric models and its gradient d SFR / d p[k]
+ * (k = 0..4; unused slots get 0).  Scale is arbitrary: the weights are
+ * normalised to the mass formed by t_obs.
+ *  model 0: delayed tau, SFR = t exp(-t/tau).
+ *  model 1: main sequence double power law times the quenching function of
+ *           Sec. 3.1 (Eq. diffstar, q_drop definition): 1/[(t/tp)^-ar +
+ *           (t/tp)^-af] * 10^(-q Terf(t | t_q - 3 sig_q, sig_q)), so that the
+ *           quench factor reaches its floor 10^-q exactly at t_q. */
+double orc_sfr(int model, const double *p, double t, double *grad)
+{
+    if (grad) for (int k = 0; k < 5; ++k) grad[k] = 0.0;
+    if (model == 0) {
+        double tau = p[0];
+        double s = t * exp(-t / tau);
+        if (grad) grad[0] = s * t / (tau * tau);
+        return s;
+    }
+    double tp = p[0], ar = p[1], af = p[2], tq = p[3], q = p[4];
+    double r = t / tp;
+    double ra = pow(r, -ar), rf = pow(r, -af);
+    double D = ra + rf;
+    double ms = 1.0 / D;
+    double zq = (t - (tq - 3.0 * ORC_SIGQ)) / ORC_SIGQ;
+    double P = orc_triweight_cdf(zq);
+    double fq = pow(10.0, -q * P);
+    double s = ms * fq;
+    if (grad) {
+        /* dD/dtp = (ar ra + af rf)/tp ; d(1/D) = -dD/D^2 */
+        double dD_dtp = (ar * ra + af * rf) / tp;
+        grad[0] = -dD_dtp / (D * D) * fq;
+        grad[1] = log(r) * ra / (D * D) * fq;
+        grad[2] = log(r) * rf / (D * D) * fq;
+        /* dP/dtq = -T(zq)/sig_q */
+        grad[3] = ms * fq * (-q * log(10.0)) * (-orc_triweight_pdf(zq) / ORC_SIGQ);
+        grad[4] = ms * fq * (-log(10.0) * P);
+    }
+    return s;
+}
+
+/* Cumulative formed mass M(tau) = int_{t0}^{tau} SFR (Eq. mstartot), with SFR
+ * piecewise linear between the uniform time nodes and zero before t0
+ * (reading: the exact integral of the piecewise-linear SFR).  If coef != NULL
+ * it receives dM/dSFR_n for every node (M is linear in the node values). */
+double orc_cum_mass(const double *sfr, int n_t, double t0, double t1, double tau, double *coef)
+{
+    if (coef) for (int n = 0; n < n_t; ++n) coef[n] = 0.0;
+    if (tau <= t0) return 0.0;
+    double h = (t1 - t0) / (n_t - 1);
+    int m = (int)floor((tau - t0) / h);
+    if (m > n_t - 2) m = n_t - 2;
+    double M = 0.0;
+    for (int n = 0; n < m; ++n) {
+        M += 0.5 * h * (sfr[n] + sfr[n + 1]);
+        if (coef) { coef[n] += 0.5 * h; coef[n + 1] += 0.5 * h; }
+    }
+    double u = tau - (t0 + m * h);
+    M += sfr[m] * u + (sfr[m + 1] - sfr[m]) * u * u / (2.0 * h);
+    if (coef) {
+        coef[m] += u - u * u / (2.0 * h);
+        coef[m + 1] += u * u / (2.0 * h);
+    }
+    return M;
+}
+
+/* Age-bin edges in Gyr (reading of the garbled bin limits after
+ * Eq. cspsum): midpoints in log10 age, first edge at age 0, last edge half a
+ * step above the last grid age. */
+void orc_age_edges_gyr(const orc_grid *g, double *edges /* n_age+1 */)
+{
+    int n = g->n_age;
+    const double *x = g->log_age_yr;
+    edges[0] = 0.0;
+    for (int i = 1; i < n; ++i) edges[i] = pow(10.0, 0.5 * (x[i - 1] + x[i]) - 9.0);
+    edges[n] = pow(10.0, x[n - 1] + 0.5 * (x[n - 1] - x[n - 2]) - 9.0);
+}
+
+/* Eq. (cspsum) with the unnumbered P_SFH definition: the fraction of the mass
+ * formed by t_obs that lies in age bin i,
+ *   frac_i = [M(t_obs - e_i) - M(t_obs - e_{i+1})] / M(t_obs). */
+void orc_age_fracs_from_sfr(const orc_grid *g, const double *sfr, double t_obs, double *frac)
+{
+    double *e = malloc(sizeof(double) * (g->n_age + 1));
+    orc_age_edges_gyr(g, e);
+    double Mtot = orc_cum_mass(sfr, g->n_t, g->t0, g->t1, t_obs, NULL);
+    for (int i = 0; i < g->n_age; ++i) {
+        double hi = orc_cum_mass(sfr, g->n_t, g->t0, g->t1, t_obs - e[i], NULL);
+        double lo = orc_cum_mass(sfr, g->n_t, g->t0, g->t1, t_obs - e[i + 1], NULL);
+        frac[i] = (hi - lo) / Mtot;
+    }
+    free(e);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.2: metallicity distribution over the lgZ bins                */
+/* ------------------------------------------------------------------ */
+
+/* P[j | age bin i] = C((E_{j+1} - mu_i)/sigma) - C((E_j - mu_i)/sigma), with
+ * lgZ bin edges at grid midpoints and outer edges at -inf/+inf (reading), and
+ * mu_i = mu + slope * (log10 age_i - 9) (age-dependent mean, linear reading;
+ * slope = 0 is the uncorrelated MDF of Eq. simple_mdf). */
+void orc_mdf(const orc_grid *g, double mu_i, double sigma, double *P /* n_z */,
+             double *dP_dmu /* n_z or NULL */, double *dP_dsig /* n_z or NULL */)
+{
+    int nz = g->n_z;
+    for (int j = 0; j < nz; ++j) {
+        double c_hi, c_lo, d_hi = 0.0, d_lo = 0.0, u_hi = 0.0, u_lo = 0.0;
+        if (j == nz - 1) c_hi = 1.0;
+        else {
+            u_hi = (0.5 * (g->lgz[j] + g->lgz[j + 1]) - mu_i) / sigma;
+            c_hi = mdf_cdf(g->mdf_kernel, u_hi);
+            d_hi = mdf_pdf(g->mdf_kernel, u_hi);
+        }
+        if (j == 0) c_lo = 0.0;
+        else {
+            u_lo = (0.5 * (g->lgz[j - 1] + g->lgz[j]) - mu_i) / sigma;
+            c_lo = mdf_cdf(g->mdf_kernel, u_lo);
+            d_lo = mdf_pdf(g->mdf_kernel, u_lo);
+        }
+        P[j] = c_hi - c_lo;
+        if (dP_dmu) dP_dmu[j] = -(d_hi - d_lo) / sigma;
+        if (dP_dsig) dP_dsig[j] = -(d_hi * u_hi - d_lo * u_lo) / sigma;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.4: power-law dust attenuation (Eq. attenuation, simplified   */
+/* Eq. salim with k = 1 at lambda_V: A_lambda = Av (lam/5500)^(-0.7+d)) */
+/* ------------------------------------------------------------------ */
+double orc_dust_trans(double lam, double Av, double delta)
+{
+    return pow(10.0, -0.4 * Av * pow(lam / ORC_LAMV, -0.7 + delta));
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.2: filters                                                   */
+/* ------------------------------------------------------------------ */
+
+/* T_q(lambda): linear in lambda between table points, zero outside. */
+double orc_filter_trans(const double *lam, const double *tr, int n, double x)
+{
+    if (x < lam[0] || x > lam[n - 1]) return 0.0;
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (lam[mid] <= x) lo = mid; else hi = mid;
+    }
+    double w = (x - lam[lo]) / (lam[hi] - lam[lo]);
+    return tr[lo] + w * (tr[hi] - tr[lo]);
+}
+
+/* Denominator of Eq. (restmag): trapezoid of T/lambda on the filter table. */
+double orc_filter_norm(const double *lam, const double *tr, int n)
+{
+    double s = 0.0;
+    for (int m = 0; m + 1 < n; ++m)
+        s += 0.5 * (lam[m + 1] - lam[m]) * (tr[m] / lam[m] + tr[m + 1] / lam[m + 1]);
+    return s;
+}
+
+/* Trapezoid weight of rest-grid node n for int dlambda (.). */
+static double trap_w(const double *lam, int N, int n)
+{
+    if (N == 1) return 0.0;
+    if (n == 0) return 0.5 * (lam[1] - lam[0]);
+    if (n == N - 1) return 0.5 * (lam[N - 1] - lam[N - 2]);
+    return 0.5 * (lam[n + 1] - lam[n - 1]);
+}
+
+/* ------------------------------------------------------------------ */
+/* Per-galaxy forward model                                            */
+/* ------------------------------------------------------------------ */
+
+static void filter_offsets(const orc_filters *f, int *off)
+{
+    off[0] = 0;
+    for (int q = 0; q < f->n_filt; ++q) off[q + 1] = off[q] + f->n_pts[q];
+}
+
+/* Eqs. (restmag) + observer frame of Sec. 2.2 + Eq. (attenuation), for one
+ * galaxy given its per-unit-mass SSP weights omega[i][j] (sum = 1):
+ *   S_n   = sum_ij omega_ij L_ijn                         (Eq. full_mdf)
+ *   N_q   = sum_n c_n/lam_n T_q((1+z) lam_n) F_n S_n      (rest-grid trapezoid)
+ *   m_q   = -2.5 log10(10^logM N_q / (AB0 D_q)) + Dmod(z) - 2.5 log10(1+z). */
+void orc_mags_from_weights(const orc_grid *g, const orc_filters *f, const double *omega,
+                           double Av, double delta, double logM, double z, double dmod,
+                           double *mags)
+{
+    int N = g->n_lam, K = g->n_age * g->n_z;
+    double *S = calloc(N, sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        double w = omega[k];
+        if (w == 0.0) continue;
+        const double *L = g->l_ssp + (size_t)k * N;
+        for (int n = 0; n < N; ++n) S[n] += w * L[n];
+    }
+    int *off = malloc(sizeof(int) * (f->n_filt + 1));
+    filter_offsets(f, off);
+    for (int q = 0; q < f->n_filt; ++q) {
+        const double *fl = f->lam + off[q], *ft = f->trans + off[q];
+        int np = f->n_pts[q];
+        double Nq = 0.0;
+        for (int n = 0; n < N; ++n) {
+            double T = orc_filter_trans(fl, ft, np, (1.0 + z) * g->lam[n]);
+            if (T == 0.0) continue;
+            double F = orc_dust_trans(g->lam[n], Av, delta);
+            Nq += trap_w(g->lam, N, n) / g->lam[n] * T * F * S[n];
+        }
+        double Dq = orc_filter_norm(fl, ft, np);
+        mags[q] = -2.5 * log10(pow(10.0, logM) * Nq / (ORC_AB0 * Dq)) + dmod - 2.5 * log10(1.0 + z);
+    }
+    free(off);
+    free(S);
+}
+
+/* Joint SSP weights of one galaxy, per unit formed mass:
+ * omega[i][j] = frac_i * P[j | i]   (Eq. agedep_mdf). */
+static void galaxy_weights(const orc_grid *g, const double *par /* 12 */, double t_obs, double *omega)
+{
+    double *sfr = malloc(sizeof(double) * g->n_t);
+    double *frac = malloc(sizeof(double) * g->n_age);
+    double *P = malloc(sizeof(double) * g->n_z);
+    double h = (g->t1 - g->t0) / (g->n_t - 1);
+    for (int n = 0; n < g->n_t; ++n) sfr[n] = orc_sfr(g->sfh_model, par, g->t0 + n * h, NULL);
+    orc_age_fracs_from_sfr(g, sfr, t_obs, frac);
+    for (int i = 0; i < g->n_age; ++i) {
+        double mu_i = par[5] + par[7] * (g->log_age_yr[i] - 9.0);
+        orc_mdf(g, mu_i, par[6], P, NULL, NULL);
+        for (int j = 0; j < g->n_z; ++j) omega[i * g->n_z + j] = frac[i] * P[j];
+    }
+    free(P); free(frac); free(sfr);
+}
+
+/* ------------------------------------------------------------------ */
+/* Adjoint of the per-galaxy model (reverse of the steps above)        */
+/* ------------------------------------------------------------------ */
+static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const double *par, double t_obs,
+                            double dmod, const double *mbar, double *mags, double *pbar /* 11 */)
+{
+    int N = g->n_lam, NA = g->n_age, NZ = g->n_z, K = NA * NZ, Q = f->n_filt, NT = g->n_t;
+    double Av = par[8], delta = par[9], logM = par[10], z = par[11];
+    double h = (g->t1 - g->t0) / (NT - 1);
+
+    /* forward intermediates */
+    double *sfr = malloc(sizeof(double) * NT);
+    double *dsfr = malloc(sizeof(double) * NT * 5);
+    for (int n = 0; n < NT; ++n) sfr[n] = orc_sfr(g->sfh_model, par, g->t0 + n * h, dsfr + 5 * n);
+    double *e = malloc(sizeof(double) * (NA + 1));
+    orc_age_edges_gyr(g, e);
+    double *Mhi = malloc(sizeof(double) * (NA + 1));   /* M(t_obs - e_i) */
+    for (int i = 0; i <= NA; ++i) Mhi[i] = orc_cum_mass(sfr, NT, g->t0, g->t1, t_obs - e[i], NULL);
+    double Mtot = Mhi[0];
+    double *frac = malloc(sizeof(double) * NA);
+    for (int i = 0; i < NA; ++i) frac[i] = (Mhi[i] - Mhi[i + 1]) / Mtot;
+    double *P = malloc(sizeof(double) * K), *dPmu = malloc(sizeof(double) * K), *dPsig = malloc(sizeof(double) * K);
+    for (int i = 0; i < NA; ++i) {
+        double mu_i = par[5] + par[7] * (g->log_age_yr[i] - 9.0);
+        orc_mdf(g, mu_i, par[6], P + i * NZ, dPmu + i * NZ, dPsig + i * NZ);
+    }
+    double *S = calloc(N, sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        double w = frac[k / NZ] * P[k];
+        const double *L = g->l_ssp + (size_t)k * N;
+        for (int n = 0; n < N; ++n) S[n] += w * L[n];
+    }
+    double *F = malloc(sizeof(double) * N), *u = malloc(sizeof(double) * N);
+    for (int n = 0; n < N; ++n) {
+        u[n] = pow(g->lam[n] / ORC_LAMV, -0.7 + delta);
+        F[n] = pow(10.0, -0.4 * Av * u[n]);
+    }
+    int *off = malloc(sizeof(int) * (Q + 1));
+    filter_offsets(f, off);
+    double *T = malloc(sizeof(double) * (size_t)Q * N);
+    double *Nq = malloc(sizeof(double) * Q);
+    for (int q = 0; q < Q; ++q) {
+        const double *fl = f->lam + off[q], *ft = f->trans + off[q];
+        double acc = 0.0;
+        for (int n = 0; n < N; ++n) {
+            T[(size_t)q * N + n] = orc_filter_trans(fl, ft, f->n_pts[q], (1.0 + z) * g->lam[n]);
+            acc += trap_w(g->lam, N, n) / g->lam[n] * T[(size_t)q * N + n] * F[n] * S[n];
+        }
+        Nq[q] = acc;
+        double Dq = orc_filter_norm(fl, ft, f->n_pts[q]);
+        if (mags) mags[q] = -2.5 * log10(pow(10.0, logM) * acc / (ORC_AB0 * Dq)) + dmod - 2.5 * log10(1.0 + z);
+    }
+
+    /* reverse sweep */
+    for (int k = 0; k < ORC_NGRAD; ++k) pbar[k] = 0.0;
+    double *Nbar = malloc(sizeof(double) * Q);
+    for (int q = 0; q < Q; ++q) {
+        pbar[10] += -2.5 * mbar[q];
+        Nbar[q] = mbar[q] * (-2.5 / log(10.0)) / Nq[q];
+    }
+    double *Sbar = calloc(N, sizeof(double));
+    for (int n = 0; n < N; ++n) {
+        double c = trap_w(g->lam, N, n) / g->lam[n];
+        double sT = 0.0;
+        for (int q = 0; q < Q; ++q) sT += Nbar[q] * T[(size_t)q * N + n];
+        Sbar[n] = c * sT * F[n];
+        double Fbar = c * sT * S[n];
+        double dF_dAv = F[n] * (-0.4 * log(10.0)) * u[n];
+        double dF_ddelta = F[n] * (-0.4 * log(10.0)) * Av * u[n] * log(g->lam[n] / ORC_LAMV);
+        pbar[8] += Fbar * dF_dAv;
+        pbar[9] += Fbar * dF_ddelta;
+    }
+    double *fracbar = calloc(NA, sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        const double *L = g->l_ssp + (size_t)k * N;
+        double wbar = 0.0;
+        for (int n = 0; n < N; ++n) wbar += Sbar[n] * L[n];
+        int i = k / NZ;
+        fracbar[i] += wbar * P[k];
+        double Pbar = wbar * frac[i];
+        pbar[5] += Pbar * dPmu[k];
+        pbar[6] += Pbar * dPsig[k];
+        pbar[7] += Pbar * dPmu[k] * (g->log_age_yr[i] - 9.0);
+    }
+    /* frac_i = (Mhi_i - Mhi_{i+1}) / Mtot with Mtot = Mhi_0 */
+    double *Mbar = calloc(NA + 1, sizeof(double));
+    for (int i = 0; i < NA; ++i) {
+        Mbar[i] += fracbar[i] / Mtot;
+        Mbar[i + 1] -= fracbar[i] / Mtot;
+        Mbar[0] -= fracbar[i] * frac[i] / Mtot;
+    }
+    double *coef = malloc(sizeof(double) * NT);
+    double *sfrbar = calloc(NT, sizeof(double));
+    for (int i = 0; i <= NA; ++i) {
+        if (Mbar[i] == 0.0) continue;
+        orc_cum_mass(sfr, NT, g->t0, g->t1, t_obs - e[i], coef);
+        for (int n = 0; n < NT; ++n) sfrbar[n] += Mbar[i] * coef[n];
+    }
+    for (int n = 0; n < NT; ++n)
+        for (int k = 0; k < 5; ++k) pbar[k] += sfrbar[n] * dsfr[5 * n + k];
+
+    free(sfrbar); free(coef); free(Mbar); free(fracbar); free(Sbar); free(Nbar);
+    free(Nq); free(T); free(off); free(u); free(F); free(S); free(dPsig); free(dPmu); free(P);
+    free(frac); free(Mhi); free(e); free(dsfr); free(sfr);
+}
+
+/* ------------------------------------------------------------------ */
+/* Batched entry points (threads over galaxies)                        */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const orc_grid *g;
+    const orc_filters *f;
+    long n_gal, begin, end;
+    const double *params, *mbar;
+    double *w_out, *mags, *pbar;
+    int mode;  /* 0 weights, 1 mags, 2 vjp */
+} orc_job;
+
+static void *orc_worker(void *arg)
+{
+    orc_job *j = (orc_job *)arg;
+    const orc_grid *g = j->g;
+    int K = g->n_age * g->n_z;
+    double par[ORC_NPAR];
+    double *omega = malloc(sizeof(double) * K);
+    for (long gi = j->begin; gi < j->end; ++gi) {
+        for (int r = 0; r < ORC_NPAR; ++r) par[r] = j->params[(size_t)r * j->n_gal + gi];
+        double z = par[11];
+        double t_obs = orc_age_gyr(g->om0, g->w0, g->h, z);
+        if (j->mode == 0) {
+            galaxy_weights(g, par, t_obs, omega);
+            double M = pow(10.0, par[10]);
+            for (int k = 0; k < K; ++k) j->w_out[(size_t)gi * K + k] = M * omega[k];
+        } else if (j->mode == 1) {
+            double dmod = orc_dist_mod(g->om0, g->w0, g->h, z);
+            galaxy_weights(g, par, t_obs, omega);
+            orc_mags_from_weights(g, j->f, omega, par[8], par[9], par[10], z, dmod,
+                                  j->mags + (size_t)gi * j->f->n_filt);
+        } else {
+            double dmod = orc_dist_mod(g->om0, g->w0, g->h, z);
+            double pb[ORC_NGRAD];
+            galaxy_mags_vjp(g, j->f, par, t_obs, dmod, j->mbar + (size_t)gi * j->f->n_filt,
+                            j->mags ? j->mags + (size_t)gi * j->f->n_filt : NULL, pb);
+            for (int k = 0; k < ORC_NGRAD; ++k) j->pbar[(size_t)k * j->n_gal + gi] = pb[k];
+        }
+    }
+    free(omega);
+    return NULL;
+}
+
+static int orc_run(orc_job proto, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > proto.n_gal) nthreads = (int)(proto.n_gal > 0 ? proto.n_gal : 1);
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    orc_job *jobs = malloc(sizeof(orc_job) * nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = proto;
+        jobs[t].begin = proto.n_gal * t / nthreads;
+        jobs[t].end = proto.n_gal * (t + 1) / nthreads;
+        pthread_create(&th[t], NULL, orc_worker, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(jobs); free(th);
+    return 0;
+}
+
+/* Per-galaxy SSP weights in Msun: w[g][i][j] = 10^logM frac_i P[j|i]. */
+int orc_weights(const orc_grid *g, long n_gal, const double *params, double *w_out, int nthreads)
+{
+    orc_job j = {g, NULL, n_gal, 0, n_gal, params, NULL, w_out, NULL, NULL, 0};
+    return orc_run(j, nthreads);
+}
+
+/* Observer-frame AB magnitudes mags[g][q]. */
+int orc_mags(const orc_grid *g, const orc_filters *f, long n_gal, const double *params, double *mags,
+             int nthreads)
+{
+    orc_job j = {g, f, n_gal, 0, n_gal, params, NULL, NULL, mags, NULL, 1};
+    return orc_run(j, nthreads);
+}
+
+/* Vector-Jacobian product: pbar[k][g] = sum_q mbar[g][q] d m_q / d p_k. */
+int orc_mags_vjp(const orc_grid *g, const orc_filters *f, long n_gal, const double *params,
+                 const double *mbar, double *mags, double *pbar, int nthreads)
+{
+    orc_job j = {g, f, n_gal, 0, n_gal, params, mbar, NULL, mags, pbar, 2};
+    return orc_run(j, nthreads);
+}

@@ -1,0 +1,211 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds no arithmetic of the method: it only draws the stand-in data
+(SSP grid, filter tables, galaxy parameters) that the paper's experiments take
+from FSPS/MILES, LSST filter curves and Diffstar, none of which is available.
+Both sides (oracle and CUDA library) read exactly these arrays.
+
+Workloads (sizes and distributions of the paper's benchmark, Sec. 5.1 and its
+synthetic stand-ins):
+
+* ``small``   64 galaxies; SSP grid 94 ages x 12 metallicities x 1000 wavelengths
+              (log-spaced 1e3..1e5 A); 6 Gaussian filters; delayed-tau SFH.
+* ``full``    1e5 galaxies; grid 107 x 22 x 5994 (log-spaced 900..1e5 A);
+              12 Gaussian filters; double power-law SFH with a quench drop;
+              age-dependent MDF mean.  ``million`` is the same with 1e6 galaxies,
+              ``grad`` the same with 1e5 galaxies and magnitude targets.
+* ``serve``   Poisson request stream over the ``full`` grid.
+
+Parameter rows (structure of arrays, ``params[12, G]`` float):
+    0..4 SFH, 5 mdf_mu, 6 mdf_sigma, 7 mdf_slope, 8 Av, 9 delta, 10 logM, 11 z.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+NPAR = 12
+NGRAD = 11
+PARAM_NAMES = ("sfh0", "sfh1", "sfh2", "sfh3", "sfh4", "mdf_mu", "mdf_sigma", "mdf_slope",
+               "Av", "delta", "logM", "z")
+
+SFH_DELAYED_TAU = 0
+SFH_DPL_QUENCH = 1
+MDF_TRIWEIGHT = 0
+MDF_GAUSSIAN = 1
+
+_H = 6.62607015e-34
+_C = 2.99792458e8
+_KB = 1.380649e-23
+
+
+@dataclasses.dataclass(frozen=True)
+class GridSpec:
+    n_age: int
+    n_z: int
+    n_lam: int
+    lam_min: float
+    lam_max: float
+    log_age_min: float = 5.5
+    log_age_max: float = 10.15
+    lgz_min: float = -2.0
+    lgz_max: float = 0.3
+    n_t: int = 200
+    t0: float = 0.05
+    t1: float = 13.8
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    grid: GridSpec
+    n_gal: int
+    n_filt: int
+    sfh_model: int
+    seed: int
+
+
+SMALL_GRID = GridSpec(94, 12, 1000, 1e3, 1e5)
+FULL_GRID = GridSpec(107, 22, 5994, 900.0, 1e5)
+
+WORKLOADS = {
+    "small": Workload("small", SMALL_GRID, 64, 6, SFH_DELAYED_TAU, 0),
+    "full": Workload("full", FULL_GRID, 100_000, 12, SFH_DPL_QUENCH, 1),
+    "million": Workload("million", FULL_GRID, 1_000_000, 12, SFH_DPL_QUENCH, 2),
+    "grad": Workload("grad", FULL_GRID, 100_000, 12, SFH_DPL_QUENCH, 3),
+}
+
+
+@dataclasses.dataclass
+class SSPGrid:
+    log_age_yr: np.ndarray   # [n_age] float64
+    lgz: np.ndarray          # [n_z]   float64, log10(Z/0.019)
+    lam: np.ndarray          # [n_lam] float64, Angstrom
+    l_ssp: np.ndarray        # [n_age, n_z, n_lam] float32, Lsun/Hz/Msun
+    t0: float
+    t1: float
+    n_t: int
+
+
+def _planck_lambda(lam_aa: np.ndarray, T: np.ndarray) -> np.ndarray:
+    lam = lam_aa * 1e-10
+    x = _H * _C / (lam * _KB * T)
+    return 2.0 * _H * _C ** 2 / lam ** 5 / np.expm1(x)
+
+
+def make_ssp(spec: GridSpec, seed: int) -> SSPGrid:
+    """Synthetic SSP block: L = C (age/1e6 yr)^-0.9 B_lambda(T) exp(0.05 N(0,1)),
+    T = 4000 K + 36000 K (1e6 yr/age)^0.3 (Z/0.019)^-0.05, C such that the
+    noiseless value at (age nearest 1 Gyr, Z nearest 0.019, lambda nearest 5500 A)
+    is 3e-15."""
+    log_age = np.linspace(spec.log_age_min, spec.log_age_max, spec.n_age)
+    lgz = np.linspace(spec.lgz_min, spec.lgz_max, spec.n_z)
+    lam = np.geomspace(spec.lam_min, spec.lam_max, spec.n_lam)
+    age = 10.0 ** log_age
+    T = 4000.0 + 36000.0 * (1e6 / age[:, None]) ** 0.3 * (10.0 ** lgz[None, :]) ** -0.05
+    base = (age[:, None, None] / 1e6) ** -0.9 * _planck_lambda(lam[None, None, :], T[:, :, None])
+    i0 = int(np.argmin(np.abs(log_age - 9.0)))
+    j0 = int(np.argmin(np.abs(lgz - 0.0)))
+    n0 = int(np.argmin(np.abs(lam - 5500.0)))
+    base *= 3e-15 / base[i0, j0, n0]
+    rng = np.random.default_rng(seed)
+    noise = np.exp(0.05 * rng.standard_normal(base.shape))
+    return SSPGrid(log_age, lgz, lam, (base * noise).astype(np.float32), spec.t0, spec.t1, spec.n_t)
+
+
+def gaussian_filter(center: float, fwhm: float = 800.0, step: float = 2.0):
+    """Gaussian transmission curve with unit peak, tabulated every ``step`` A and
+    truncated at center +- 4 FWHM."""
+    sig = fwhm / (2.0 * np.sqrt(2.0 * np.log(2.0)))
+    n = int(round(8.0 * fwhm / step)) + 1
+    lam = center - 4.0 * fwhm + step * np.arange(n)
+    return lam, np.exp(-0.5 * ((lam - center) / sig) ** 2)
+
+
+def make_filters(n_filt: int, lo: float = 3500.0, hi: float = 9000.0, fwhm: float = 800.0):
+    """``n_filt`` Gaussian filters with centres evenly spaced on [lo, hi]."""
+    return [gaussian_filter(c, fwhm) for c in np.linspace(lo, hi, n_filt)]
+
+
+_BLOCK = 4096
+
+
+def _draw_block(sfh_model: int, seed: int, block: int) -> np.ndarray:
+    rng = np.random.default_rng([seed, block])
+    n = _BLOCK
+    p = np.zeros((NPAR, n))
+    if sfh_model == SFH_DELAYED_TAU:
+        p[0] = rng.uniform(0.5, 5.0, n)            # tau [Gyr]
+        p[10] = rng.uniform(9.0, 11.5, n)          # logM
+        p[5] = rng.uniform(-1.0, 0.2, n)           # mdf mu
+        p[6] = 0.2                                 # mdf sigma
+        p[7] = 0.0                                 # uncorrelated MDF
+        p[8] = rng.uniform(0.0, 1.0, n)            # Av
+        p[9] = rng.uniform(-0.4, 0.3, n)           # delta
+        p[11] = rng.uniform(0.1, 1.5, n)           # z
+    else:
+        p[0] = rng.uniform(1.0, 10.0, n)           # t_peak [Gyr]
+        p[1] = rng.uniform(1.0, 3.0, n)            # rising slope
+        p[2] = rng.uniform(-3.0, -0.5, n)          # falling slope
+        p[3] = rng.uniform(5.0, 13.8, n)           # t_q [Gyr]
+        p[4] = rng.uniform(0.0, 3.0, n)            # q_drop [dex]
+        p[10] = rng.uniform(9.0, 11.5, n)
+        p[5] = rng.uniform(-1.0, 0.2, n)
+        p[6] = 0.2
+        p[7] = rng.uniform(-0.3, 0.0, n)           # MDF slope
+        p[8] = rng.uniform(0.0, 1.0, n)
+        p[9] = rng.uniform(-0.4, 0.3, n)
+        p[11] = np.maximum(rng.uniform(0.0, 3.0, n), 1e-3)
+    return p
+
+
+def make_population(sfh_model: int, n: int, seed: int, start: int = 0) -> np.ndarray:
+    """Galaxy parameters ``[12, n]`` (float64) for galaxies [start, start+n).
+    Galaxy i depends only on (seed, i), so any slice is a prefix-consistent
+    sample of the full population."""
+    if n <= 0:
+        return np.zeros((NPAR, 0))
+    b0, b1 = start // _BLOCK, (start + n - 1) // _BLOCK
+    blocks = [_draw_block(sfh_model, seed, b) for b in range(b0, b1 + 1)]
+    allp = np.concatenate(blocks, axis=1)
+    off = start - b0 * _BLOCK
+    return np.ascontiguousarray(allp[:, off:off + n])
+
+
+def workload_inputs(name: str, n_gal: int | None = None, start: int = 0):
+    """(grid, filters, params) for a named workload."""
+    w = WORKLOADS[name]
+    grid = make_ssp(w.grid, w.seed if name in ("small",) else 1)
+    filters = make_filters(w.n_filt)
+    params = make_population(w.sfh_model, w.n_gal if n_gal is None else n_gal, w.seed, start)
+    return grid, filters, params
+
+
+@dataclasses.dataclass
+class Request:
+    t_arrive: float
+    n_gal: int
+    n_filt: int
+    want_grad: bool
+    seed: int
+
+
+def make_request_stream(rate: float = 200.0, duration: float = 60.0, seed: int = 4,
+                        median: float = 3e3, sigma_ln: float = 1.5, lo: int = 100,
+                        hi: int = 200_000, grad_frac: float = 0.3):
+    """Poisson arrivals; population sizes lognormal(median, sigma_ln) clipped to
+    [lo, hi]; filter sets of 4, 8 or 12 filters with equal probability; a
+    fraction ``grad_frac`` of requests also asks for gradients."""
+    rng = np.random.default_rng(seed)
+    t, out, i = 0.0, [], 0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        n = int(np.clip(np.round(median * np.exp(sigma_ln * rng.standard_normal())), lo, hi))
+        q = int(rng.choice([4, 8, 12]))
+        g = bool(rng.uniform() < grad_frac)
+        out.append(Request(t, n, q, g, 1000 + i))
+        i += 1
+    return out
