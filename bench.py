@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark of the DSPS photometry hot path (Hearin et al. 2021) on GB300.
+
+One step = the whole hot path over one batch: per-galaxy SSP weights (SFH
+prefix mass, age-bin differencing, MDF) and the fused photometry kernel
+(contraction with the SSP block, dust, redshifted filter integral, AB mags),
+for the 1e5-galaxy workload on the 107 x 22 x 5994 SSP grid with 12 filters.
+
+Prints one JSON line (rank 0).  ``value`` is galaxy-magnitudes per second of
+the split-bf16 tensor-core form with inputs already in HBM; ``e2e`` is the
+same metric with the host->device copy of the parameters and the
+device->host copy of the magnitudes inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (the only other implementation
+of the method available) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "full"
+N_GAL = 100_000
+N_FILT = 12
+METRIC = "galaxy-mags/sec"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-gal", type=int, default=N_GAL)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    return ap.parse_args()
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        rows = list(csv.reader(io.StringIO(open(self.path).read())))
+        os.unlink(self.path)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_baseline(sample: int):
+    """The FP64 oracle as it stands, on all host cores, over a bounded sample of
+    the same workload."""
+    import oracle
+    from paper_2112_06830_gb300 import synth
+    ssp = synth.make_ssp(synth.FULL_GRID, 1)
+    grid = oracle.Grid(ssp.log_age_yr, ssp.lgz, ssp.lam, ssp.l_ssp, sfh_model=synth.SFH_DPL_QUENCH)
+    F = oracle.Filters(synth.make_filters(N_FILT))
+    p = synth.make_population(synth.SFH_DPL_QUENCH, sample, 1).astype(np.float32).astype(np.float64)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.mags(grid, F, p, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample * N_FILT / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} galaxies of the 1e5-galaxy workload (107x22x5994 grid, 12 filters), "
+                      f"FP64, {cores} threads, {dt:.2f} s wall"}
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2112_06830_gb300 import synth
+    oracle.build()
+    ssp = synth.make_ssp(synth.FULL_GRID, 1)
+    grid = oracle.Grid(ssp.log_age_yr, ssp.lgz, ssp.lam, ssp.l_ssp, sfh_model=synth.SFH_DPL_QUENCH)
+    F = oracle.Filters(synth.make_filters(N_FILT))
+    sample = 256
+    cores = os.cpu_count() or 1
+    times = []
+    for i in range(a.warmup + a.steps):
+        p = synth.make_population(synth.SFH_DPL_QUENCH, sample, 1, start=i * sample)
+        p = p.astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.mags(grid, F, p, nthreads=cores)
+        if i >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    v = sample * N_FILT / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: {sample}-galaxy sample per step of the 1e5-galaxy population, "
+                               "SSP grid 107x22x5994, 12 Gaussian filters", "n_gal_per_step": sample},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} galaxies per step, FP64 C oracle, {cores} threads"},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(a):
+    import torch
+
+    from paper_2112_06830_gb300 import dsps, synth
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    G = a.n_gal
+    ssp = synth.make_ssp(synth.FULL_GRID, 1)
+    ctx = dsps.Context(ssp, sfh_model=synth.SFH_DPL_QUENCH, device=local)
+    sid = ctx.add_filters(synth.make_filters(N_FILT))
+    params_h = synth.make_population(synth.SFH_DPL_QUENCH, G, 1, start=rank * G).astype(np.float32)
+    d_params = torch.from_numpy(params_h).cuda()
+    d_mags = torch.empty((G, N_FILT), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        ctx.photometry(d_params, sid, precision=prec, out=d_mags, stream=stream)
+
+    def timed(prec, sampler=None):
+        for _ in range(a.warmup):
+            step(prec)
+        barrier()
+        dsps.dsps_profile_read(ctx.handle)
+        dsps.dsps_profile_enable(ctx.handle, True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(a.steps)]
+        if sampler:
+            sampler.start()
+        for e0, e1 in evs:
+            flush.fill_(1)
+            e0.record(stream)
+            step(prec)
+            e1.record(stream)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        dsps.dsps_profile_enable(ctx.handle, False)
+        prof = dsps.dsps_profile_read(ctx.handle)
+        ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof, clocks
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms_tc, prof_tc, clocks = timed(dsps.DSPS_PREC_BF16X3, sampler)
+    ms_fp32, prof_fp32, _ = timed(dsps.DSPS_PREC_FP32)
+
+    # End to end: pinned host params -> device, photometry, magnitudes -> host.
+    h_params = torch.from_numpy(params_h).pin_memory()
+    h_mags = torch.empty((G, N_FILT), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        d_params.copy_(h_params, non_blocking=True)
+        step(dsps.DSPS_PREC_BF16X3)
+        h_mags.copy_(d_mags, non_blocking=True)
+
+    for _ in range(a.warmup):
+        e2e_step()
+    barrier()
+    e_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    for e0, e1 in e_evs:
+        flush.fill_(1)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+    barrier()
+    ms_e2e = float(np.mean([e0.elapsed_time(e1) for e0, e1 in e_evs]))
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    assert np.isfinite(h_mags.numpy()).all()
+    assert ctx.device_error() == 0
+
+    if rank != 0:
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = _peaks()
+    K = ssp.l_ssp.shape[0] * ssp.l_ssp.shape[1]
+    N = ssp.l_ssp.shape[2]
+    launches, kms = prof_tc[2]
+    per_launch_ms = kms / max(launches, 1)
+    gal_per_launch = G / max(launches // a.steps, 1)
+    flops_per_launch = 3 * 2.0 * K * N * gal_per_launch   # bf16x3: three bf16 products per multiply-add
+    achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+    peak = float(peaks["bf16_tflops"])
+    total_launches = sum(v[0] for v in prof_tc.values())
+    value = ws * G * N_FILT / (ms_tc * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms_tc, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: {G} galaxies per GPU, SSP grid 107 ages x 22 Z x 5994 lambda "
+                               "(900-1e5 A), 12 Gaussian filters, double power-law + quench SFH, "
+                               "age-dependent triweight MDF, power-law dust, z in [0.001, 3]",
+                   "global_batch": ws * G, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single"},
+        "fp32": {"value": ws * G * N_FILT / (ms_fp32 * 1e-3), "ms_per_step": ms_fp32,
+                 "kernel_ms_per_launch": prof_fp32[1][1] / max(prof_fp32[1][0], 1)},
+        "kernels": {"weights_ms_per_launch": prof_tc[0][1] / max(prof_tc[0][0], 1),
+                    "phot_tc_ms_per_launch": per_launch_ms},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "phot_tc_kernel (split-bf16 tcgen05 contraction + fused epilogue)",
+                     "peak_source": f"{peak_src} bf16 burst"},
+        "e2e": {"value": ws * G * N_FILT / (ms_e2e * 1e-3), "unit": METRIC,
+                "h2d_bytes_per_step": int(params_h.nbytes), "d2h_bytes_per_step": int(G * N_FILT * 4)},
+        "gpu_launches": int(total_launches),
+        "clocks": clocks,
+    }
+    if not a.no_cpu_baseline:
+        out["cpu_baseline"] = _cpu_baseline(a.cpu_sample)
+    print(json.dumps(out))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * dsps.h -- C ABI of libdsps, the GB300 (sm_103a) photometry hot path of
+ * Hearin et al. 2021, "DSPS: Differentiable Stellar Population Synthesis"
+ * (arXiv:2112.06830).
+ *
+ * For each galaxy the library turns its star-formation history into
+ * stellar-mass weights over an SSP age grid (Sec. 3.1, Eqs. cspsum and
+ * mstartot) and its (age-dependent) metallicity distribution into weights over
+ * a metallicity grid (Sec. 3.2, Eqs. simple_mdf and agedep_mdf, Appendix B),
+ * contracts the joint weights with a resident SSP spectral grid
+ * (Sec. 2.1, Eq. cspdeftheta; Sec. 3.2, Eq. full_mdf), applies power-law dust
+ * attenuation (Sec. 3.4, Eq. attenuation), redshifts the spectrum and
+ * integrates it through filter curves to AB magnitudes (Sec. 2.2, Eq. restmag
+ * and the observer-frame relation that follows it).  The gradient entry point
+ * returns the vector-Jacobian product of the magnitudes with respect to the
+ * per-galaxy parameters (the derivatives the paper obtains by autodiff,
+ * Sec. 2.1 and Sec. 3).
+ *
+ * Conventions
+ * -----------
+ * - Every function returns DSPS_OK (0) or a negative error code; no C++
+ *   exception crosses this boundary.  DSPS_PENDING (1) is returned only by
+ *   dsps_poll.
+ * - Pointers documented as "device" must be CUDA device (or managed) memory of
+ *   the context's device; "host" pointers are ordinary host memory.  The
+ *   caller owns every buffer it passes; the context owns the resident SSP
+ *   copies, filter tables, cosmology table, work space and streams.
+ * - Compute calls are asynchronous on the given stream (0 = legacy default
+ *   stream) and are ordered with other work on that stream.  Two calls on the
+ *   same context must not run concurrently on different streams because they
+ *   share the context's work space; dsps_submit/dsps_poll are thread-safe.
+ * - Values that can only be checked on the device (z outside (0, z_max],
+ *   sigma <= 0, non-finite parameters) make the affected magnitudes NaN and
+ *   set a sticky device error word, read (with a stream sync) by
+ *   dsps_device_error().
+ *
+ * Per-galaxy parameter layout (float32, structure of arrays, row r of G
+ * galaxies at params + r*G):
+ *    0..4  SFH parameters.
+ *          DSPS_SFH_DELAYED_TAU : p0 = tau [Gyr], SFR ~ t exp(-t/tau).
+ *          DSPS_SFH_DPL_QUENCH  : p0 = t_peak [Gyr], p1 = rising slope,
+ *                                 p2 = falling slope, p3 = t_q [Gyr],
+ *                                 p4 = q_drop [dex];
+ *                                 SFR ~ 1/[(t/tp)^-p1 + (t/tp)^-p2]
+ *                                       * 10^(-q Terf(t | t_q - 0.9, 0.3))
+ *                                 (quench floor reached at t_q, Sec. 3.1).
+ *    5     mdf_mu     mean log10(Z/Zsun) at age 1 Gyr
+ *    6     mdf_sigma  MDF width [dex], > 0
+ *    7     mdf_slope  d mean / d log10(age/yr)  (0 = uncorrelated MDF)
+ *    8     Av         V-band attenuation [mag]
+ *    9     delta      dust slope: A(lam) = Av (lam/5500 A)^(-0.7 + delta)
+ *    10    logM       log10 of the stellar mass formed by t_obs [Msun]
+ *    11    z          redshift, 0 < z <= z_max
+ * Gradient rows (param_bar, float32 [11][G]) are rows 0..10 above.
+ */
+#ifndef DSPS_H
+#define DSPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dsps_ctx dsps_ctx;
+typedef struct CUstream_st *dsps_stream_t;   /* == cudaStream_t */
+
+enum {
+    DSPS_OK = 0,
+    DSPS_PENDING = 1,
+    DSPS_ERR_INVALID_ARG = -1,
+    DSPS_ERR_OUT_OF_BUDGET = -2,
+    DSPS_ERR_CUDA = -3,
+    DSPS_ERR_TIMEOUT = -4,
+    DSPS_ERR_DEVICE_FAULT = -5,
+    DSPS_ERR_UNSUPPORTED = -6,
+    DSPS_ERR_NOT_FOUND = -7
+};
+
+enum { DSPS_SFH_DELAYED_TAU = 0, DSPS_SFH_DPL_QUENCH = 1 };
+enum { DSPS_MDF_TRIWEIGHT = 0, DSPS_MDF_GAUSSIAN = 1 };
+
+/* Arithmetic of the contraction (Eq. full_mdf):
+ *   DSPS_PREC_FP32   FP32 weights x FP32 SSP grid, FP32 FMA on the SIMT cores.
+ *   DSPS_PREC_BF16X3 SSP rows scaled by powers of two and split into
+ *                    bf16 hi + lo, weights likewise; hi*hi + hi*lo + lo*hi
+ *                    products on the tcgen05 tensor cores, FP32 accumulate.
+ * Both use the same weights kernel (FP64 cumulative SFH mass and age-bin
+ * differencing) and the same FP32 epilogue. */
+enum { DSPS_PREC_FP32 = 0, DSPS_PREC_BF16X3 = 1 };
+
+#define DSPS_NPAR 12
+#define DSPS_NGRAD 11
+#define DSPS_MAX_FILTERS 16
+
+/* SSP block and grids (host memory, copied at dsps_create).
+ * Sec. 2.1 (Eq. cspdef: the SSP block is precomputed and held fixed) and
+ * Sec. 3.1 (age grid), Sec. 3.2 (metallicity grid). */
+typedef struct {
+    int32_t n_age;             /* >= 2                                          */
+    int32_t n_z;               /* >= 1                                          */
+    int32_t n_lam;             /* >= 2                                          */
+    const double *log_age_yr;  /* [n_age] log10(age/yr), strictly increasing    */
+    const double *lgz;         /* [n_z] log10(Z/Zsun), strictly increasing       */
+    const double *lam;         /* [n_lam] rest wavelength [A], uniform in ln
+                                  lambda to 1e-9 relative (DSPS_ERR_UNSUPPORTED
+                                  otherwise)                                    */
+    const float *l_ssp;        /* [n_age][n_z][n_lam] L_nu [Lsun/Hz/Msun], >= 0  */
+    double t0_gyr, t1_gyr;     /* uniform cosmic-time grid of the SFR           */
+    int32_t n_t;               /* nodes, 2..1024                                */
+} dsps_grid;
+
+typedef struct {
+    double om0, w0, h;         /* flat wCDM (Sec. 2.2); defaults 0.3, -1, 0.7   */
+    int32_t sfh_model;         /* DSPS_SFH_*                                    */
+    int32_t mdf_kernel;        /* DSPS_MDF_*                                    */
+    int32_t device;            /* CUDA device ordinal                            */
+    int64_t max_chunk;         /* galaxies per internal launch (work space size) */
+    int64_t hbm_budget_bytes;  /* admission budget of the request loop          */
+    int32_t n_streams;         /* streams of the request loop                    */
+    double z_max;              /* largest accepted redshift (cosmology table)    */
+} dsps_opts;
+
+/* Fills *o with the defaults above (device 0, max_chunk 262144,
+ * hbm_budget 8 GiB, 4 streams, z_max 10). */
+void dsps_default_opts(dsps_opts *o);
+
+/* Creates a context on o->device: uploads the SSP block (FP32 copy, and the
+ * bf16 hi/lo row-scaled copies for DSPS_PREC_BF16X3), builds the cosmology
+ * table t_obs(z), Dmod(z) (Sec. 2.2) and allocates the work space.
+ * Errors: INVALID_ARG for bad sizes/orderings, UNSUPPORTED for a wavelength
+ * grid that is not uniform in ln lambda, CUDA on allocation/copy failure. */
+int dsps_create(dsps_ctx **out, const dsps_grid *grid, const dsps_opts *opts);
+int dsps_destroy(dsps_ctx *ctx);
+
+/* Registers a filter set (Sec. 2.2, Eq. restmag: T_Q(lambda) is a photon
+ * transmission probability).  Host tables, lam strictly increasing [A],
+ * trans >= 0, each with >= 2 points; T is linear in lambda between points and
+ * zero outside.  n_filt in 1..DSPS_MAX_FILTERS.  The tables are resampled onto
+ * the SSP grid's ln-lambda spacing and kept on the device; the normalisation
+ * int dlambda/lambda T (trapezoid on the caller's table) is kept per filter.
+ * *set_id receives a small non-negative id. */
+int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts,
+                     const double *const *lam, const double *const *trans, int32_t *set_id);
+int dsps_filters_count(dsps_ctx *ctx, int32_t set_id, int32_t *n_filt);
+
+/* SSP weights in Msun, w_out[g][i][j] = 10^logM * P_SFH(age_i) * P_met(Z_j | age_i)
+ * (Sec. 3.1 Eq. cspsum with P_SFH, Sec. 3.2 Eq. agedep_mdf).
+ * params: device float32 [12][n_gal]; w_out: device float32 [n_gal][n_age][n_z]. */
+int dsps_weights(dsps_ctx *ctx, int64_t n_gal, const float *params, float *w_out,
+                 dsps_stream_t stream);
+
+/* Observer-frame AB magnitudes (Sec. 2.2): mags[g][q], device float32
+ * [n_gal][n_filt of set_id].  params: device float32 [12][n_gal].
+ * precision: DSPS_PREC_FP32 or DSPS_PREC_BF16X3. */
+int dsps_photometry(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
+                    int32_t precision, float *mags, dsps_stream_t stream);
+
+/* Vector-Jacobian product of the magnitudes (Sec. 2.1: gradients of the SED
+ * follow from dP(x_i)/dtheta; Sec. 3 per ingredient):
+ *   param_bar[k][g] = sum_q mag_bar[g][q] d mags[g][q] / d params[k][g],  k = 0..10.
+ * mag_bar: device float32 [n_gal][n_filt]; mags: device float32
+ * [n_gal][n_filt] or NULL (forward magnitudes written as a by-product);
+ * param_bar: device float32 [11][n_gal]. */
+int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
+                        int32_t precision, const float *mag_bar, float *mags,
+                        float *param_bar, dsps_stream_t stream);
+
+/* Request loop (continuous batching).  A request carries a population of
+ * galaxies in HOST memory (params float32 [12][n_gal], outputs float32) and is
+ * admitted when its device footprint fits the HBM budget; requests admitted
+ * together are packed into shared launches, their copies and kernels
+ * overlapping on the loop's streams.  Results are identical to a lone
+ * dsps_photometry(_vjp) call on the same inputs. */
+typedef struct {
+    int64_t n_gal;
+    const float *params;       /* host [12][n_gal]                              */
+    int32_t set_id;
+    int32_t precision;
+    int32_t want_grad;         /* 0: mags only; 1: also param_bar                */
+    const float *mag_bar;      /* host [n_gal][n_filt], if want_grad             */
+    float *mags;               /* host [n_gal][n_filt]                           */
+    float *param_bar;          /* host [11][n_gal], if want_grad                 */
+} dsps_request;
+
+/* Queues a request; *ticket identifies it.  The host buffers must stay valid
+ * until dsps_poll reports completion.  OUT_OF_BUDGET if the request alone can
+ * never fit the budget. */
+int dsps_submit(dsps_ctx *ctx, const dsps_request *req, uint64_t *ticket);
+
+/* Waits up to timeout_us microseconds (0 = just test) for a request.
+ * Returns DSPS_OK once its outputs are in the host buffers (the ticket is then
+ * retired), DSPS_PENDING if still running, DSPS_ERR_TIMEOUT never (a timed
+ * out wait returns DSPS_PENDING), DSPS_ERR_NOT_FOUND for an unknown ticket, or
+ * the request's own error.  *latency_us (optional) receives submit->done time. */
+int dsps_poll(dsps_ctx *ctx, uint64_t ticket, int64_t timeout_us, double *latency_us);
+
+/* Synchronises the context's streams and the given stream, then returns and
+ * clears the sticky device error word: DSPS_OK, or DSPS_ERR_INVALID_ARG if
+ * some galaxy had out-of-range parameters, or DSPS_ERR_DEVICE_FAULT if a
+ * kernel gave up on a bounded wait. */
+int dsps_device_error(dsps_ctx *ctx, dsps_stream_t stream);
+
+/* Kernel timing (tracing).  When enabled, every compute call records CUDA
+ * events on the caller's stream around each kernel it launches; read() waits
+ * for them and returns, per kernel kind, the number of launches and the summed
+ * device time since the last read (then resets).  Kinds: 0 weights,
+ * 1 FP32 photometry, 2 tensor-core photometry, 3 adjoint kernels. */
+#define DSPS_PROF_KINDS 4
+typedef struct {
+    int64_t launches[DSPS_PROF_KINDS];
+    double ms[DSPS_PROF_KINDS];
+} dsps_profile_t;
+int dsps_profile_enable(dsps_ctx *ctx, int32_t enable);
+int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out);
+
+const char *dsps_strerror(int code);
+
+/* Human-readable detail of the last error returned on the calling thread. */
+const char *dsps_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSPS_H */

@@ -1,0 +1,457 @@
+// api.cu -- the C ABI of libdsps (include/dsps.h): context set-up, filter
+// registration, and the per-call dispatch of the weights and photometry
+// kernels over chunks of galaxies.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dsps_internal.cuh"
+
+using namespace dsps;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, const char *detail = "") {
+    char buf[512];
+    std::snprintf(buf, sizeof buf, fmt, detail);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+    g_last_error = buf;
+    return DSPS_ERR_CUDA;
+}
+
+#define DSPS_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on the
+// three-term recurrence of the Legendre polynomials).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            pp = n * (z * p1 - p2) / (z * z - 1.0);
+            double z1 = z;
+            z = z1 - p1 / pp;
+            if (std::fabs(z - z1) < 1e-15) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+struct GL {
+    std::vector<double> x, w;
+    explicit GL(int n) { gauss_legendre(n, x, w); }
+    template <class F>
+    double integrate(F f, double a, double b) const {
+        double c = 0.5 * (a + b), h = 0.5 * (b - a), s = 0.0;
+        for (size_t i = 0; i < x.size(); ++i) s += w[i] * f(c + h * x[i]);
+        return s * h;
+    }
+};
+
+// Sec. 2.2: t_obs(z) [Gyr] and Dmod(z) - 5 log10 z for flat wCDM on a uniform
+// z table, FP64.
+void build_cosmology(double om0, double w0, double h, double zmax, double dz, std::vector<double> &tl,
+                     std::vector<double> &gl) {
+    const int n = (int)std::ceil(zmax / dz) + 2;
+    tl.assign(n, 0.0);
+    gl.assign(n, 0.0);
+    const double inv_h0_gyr = 977.792221 / (100.0 * h);
+    const double c_h0_mpc = 299792.458 / (100.0 * h);
+    auto E = [&](double z) {
+        double a1 = 1.0 + z;
+        return std::sqrt(om0 * a1 * a1 * a1 + (1.0 - om0) * std::pow(a1, 3.0 * (1.0 + w0)));
+    };
+    GL g8(8);
+    // comoving distance, cumulative upward
+    double dc = 0.0;
+    gl[0] = 5.0 * std::log10(c_h0_mpc * 1e5);
+    for (int i = 1; i < n; ++i) {
+        double za = (i - 1) * dz, zb = i * dz;
+        dc += g8.integrate([&](double z) { return 1.0 / E(z); }, za, zb);
+        gl[i] = 5.0 * std::log10((1.0 + zb) * c_h0_mpc * dc / zb * 1e5);
+    }
+    // age at the top of the table: int_0^{sqrt(a)} 2 ds / (s E(1/s^2 - 1))
+    const double ztop = (n - 1) * dz;
+    const double smax = std::sqrt(1.0 / (1.0 + ztop));
+    auto f = [&](double s) { return s <= 0.0 ? 0.0 : 2.0 / (s * E(1.0 / (s * s) - 1.0)); };
+    double t = 0.0;
+    const int panels = 256;
+    for (int p = 0; p < panels; ++p) t += g8.integrate(f, smax * p / panels, smax * (p + 1) / panels);
+    tl[n - 1] = inv_h0_gyr * t;
+    for (int i = n - 2; i >= 0; --i) {
+        double za = i * dz, zb = (i + 1) * dz;
+        tl[i] = tl[i + 1] + inv_h0_gyr * g8.integrate([&](double z) { return 1.0 / ((1.0 + z) * E(z)); }, za, zb);
+    }
+}
+
+double filter_interp(const double *l, const double *t, int n, double x) {
+    if (x < l[0] || x > l[n - 1]) return 0.0;
+    const double *it = std::upper_bound(l, l + n, x);
+    int hi = (int)(it - l);
+    if (hi >= n) hi = n - 1;
+    int lo = hi - 1;
+    if (lo < 0) return t[0];
+    double w = (x - l[lo]) / (l[hi] - l[lo]);
+    return t[lo] + w * (t[hi] - t[lo]);
+}
+
+template <class T>
+int dmalloc(T **p, size_t count) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    return DSPS_OK;
+}
+
+void free_ctx(Ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    for (auto &fs : c->sets) {
+        cudaFree(fs.d_tab);
+        cudaFree(fs.d_offq);
+    }
+    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_edges, c->d_zedge,
+                    c->d_tlut, c->d_glut, c->d_w32, c->d_whi, c->d_wlo, c->d_aux, c->d_magoff, c->d_err};
+    for (void *p : ptrs) cudaFree(p);
+    for (auto &r : c->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+}  // namespace
+
+namespace dsps {
+int serve_start(Ctx *c);
+void serve_stop(Ctx *c);
+int serve_submit(Ctx *c, const dsps_request *r, uint64_t *ticket);
+int serve_poll(Ctx *c, uint64_t ticket, int64_t timeout_us, double *latency_us);
+int run_photometry(Ctx *c, int64_t n_gal, const float *params, int32_t set_id, int32_t precision, float *mags,
+                   cudaStream_t s);
+int run_photometry_vjp(Ctx *c, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
+                       const float *mag_bar, float *mags, float *param_bar, cudaStream_t s);
+const char *last_error_message() { return g_last_error.c_str(); }
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace dsps
+
+extern "C" {
+
+void dsps_default_opts(dsps_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->om0 = 0.3;
+    o->w0 = -1.0;
+    o->h = 0.7;
+    o->sfh_model = DSPS_SFH_DELAYED_TAU;
+    o->mdf_kernel = DSPS_MDF_TRIWEIGHT;
+    o->device = 0;
+    o->max_chunk = 262144;
+    o->hbm_budget_bytes = (int64_t)8 << 30;
+    o->n_streams = 4;
+    o->z_max = 10.0;
+}
+
+const char *dsps_last_error_message(void) { return g_last_error.c_str(); }
+
+int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
+    if (!out || !g) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: null argument%s");
+    *out = nullptr;
+    dsps_opts opts;
+    if (o) opts = *o; else dsps_default_opts(&opts);
+    if (g->n_age < 2 || g->n_age > MAX_NAGE || g->n_z < 1 || g->n_lam < 2 || g->n_t < 2 || g->n_t > MAX_NT)
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_create: grid sizes out of range%s");
+    if (!g->log_age_yr || !g->lgz || !g->lam || !g->l_ssp)
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_create: null grid array%s");
+    if (!(g->t1_gyr > g->t0_gyr) || !(g->t0_gyr >= 0))
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_create: bad SFR time grid%s");
+    for (int i = 1; i < g->n_age; ++i)
+        if (!(g->log_age_yr[i] > g->log_age_yr[i - 1])) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: ages not increasing%s");
+    for (int j = 1; j < g->n_z; ++j)
+        if (!(g->lgz[j] > g->lgz[j - 1])) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: lgZ not increasing%s");
+    if (!(g->lam[0] > 0)) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: wavelengths must be positive%s");
+    const double dl = std::log(g->lam[g->n_lam - 1] / g->lam[0]) / (g->n_lam - 1);
+    if (!(dl > 0)) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: wavelengths not increasing%s");
+    for (int n = 0; n < g->n_lam; ++n) {
+        double expect = g->lam[0] * std::exp(n * dl);
+        if (std::fabs(g->lam[n] / expect - 1.0) > 1e-9)
+            return fail(DSPS_ERR_UNSUPPORTED, "dsps_create: wavelength grid is not uniform in ln(lambda)%s");
+    }
+    if (opts.sfh_model < 0 || opts.sfh_model > 1 || opts.mdf_kernel < 0 || opts.mdf_kernel > 1)
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_create: unknown model switch%s");
+    if (!(opts.z_max > 0) || opts.z_max > 50 || !(opts.om0 > 0) || !(opts.h > 0))
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_create: bad cosmology options%s");
+    if (opts.max_chunk < 128) opts.max_chunk = 128;
+    if (opts.n_streams < 1) opts.n_streams = 1;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(DSPS_ERR_CUDA, "dsps_create: no CUDA device%s");
+    if (opts.device < 0 || opts.device >= ndev) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: bad device%s");
+    DSPS_CUDA(cudaSetDevice(opts.device));
+    cudaDeviceProp prop;
+    DSPS_CUDA(cudaGetDeviceProperties(&prop, opts.device));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(DSPS_ERR_UNSUPPORTED, "dsps_create: libdsps is built for sm_103a (GB300) only%s");
+
+    Ctx *c = new Ctx();
+    c->device = opts.device;
+    c->opts = opts;
+    c->num_sms = prop.multiProcessorCount;
+    c->n_age = g->n_age;
+    c->n_z = g->n_z;
+    c->n_lam = g->n_lam;
+    c->K = g->n_age * g->n_z;
+    c->K_pad = (c->K + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
+    c->N_pad = (c->n_lam + 1 + N_ALIGN - 1) / N_ALIGN * N_ALIGN;   // >= n_lam + 1: room for the closing term
+    c->n_t = g->n_t;
+    c->t0 = g->t0_gyr;
+    c->t1 = g->t1_gyr;
+    c->lnlam0 = std::log(g->lam[0]);
+    c->dlnlam = dl;
+    c->chunk = (opts.max_chunk + 127) / 128 * 128;
+
+    int rc = DSPS_OK;
+    auto chk = [&](int r) { if (rc == DSPS_OK) rc = r; };
+    chk(dmalloc(&c->d_L32, (size_t)c->K_pad * c->N_pad));
+    chk(dmalloc(&c->d_Lt_hi, (size_t)c->K_pad * c->N_pad));
+    chk(dmalloc(&c->d_Lt_lo, (size_t)c->K_pad * c->N_pad));
+    chk(dmalloc(&c->d_wmul, (size_t)c->K_pad));
+    chk(dmalloc(&c->d_logage, (size_t)c->n_age));
+    chk(dmalloc(&c->d_edges, (size_t)c->n_age + 1));
+    chk(dmalloc(&c->d_zedge, (size_t)c->n_z + 1));
+    chk(dmalloc(&c->d_w32, (size_t)c->chunk * c->K_pad));
+    chk(dmalloc(&c->d_whi, (size_t)c->chunk * c->K_pad));
+    chk(dmalloc(&c->d_wlo, (size_t)c->chunk * c->K_pad));
+    chk(dmalloc(&c->d_aux, (size_t)c->chunk * AUX_STRIDE));
+    chk(dmalloc(&c->d_magoff, (size_t)c->chunk));
+    chk(dmalloc(&c->d_err, 1));
+    if (rc != DSPS_OK) { free_ctx(c); return rc; }
+
+    // Age-bin edges [Gyr]: log-midpoints, first edge at age 0, last half a step
+    // above the last grid age (Sec. 3.1).
+    std::vector<double> edges(c->n_age + 1);
+    edges[0] = 0.0;
+    for (int i = 1; i < c->n_age; ++i) edges[i] = std::pow(10.0, 0.5 * (g->log_age_yr[i - 1] + g->log_age_yr[i]) - 9.0);
+    edges[c->n_age] = std::pow(10.0, g->log_age_yr[c->n_age - 1] +
+                                        0.5 * (g->log_age_yr[c->n_age - 1] - g->log_age_yr[c->n_age - 2]) - 9.0);
+    std::vector<float> logage(c->n_age);
+    for (int i = 0; i < c->n_age; ++i) logage[i] = (float)g->log_age_yr[i];
+    // lgZ bin edges: midpoints, outer edges at -/+ infinity (Sec. 3.2).
+    std::vector<float> zedge(c->n_z + 1);
+    zedge[0] = -1e30f;
+    zedge[c->n_z] = 1e30f;
+    for (int j = 1; j < c->n_z; ++j) zedge[j] = (float)(0.5 * (g->lgz[j - 1] + g->lgz[j]));
+    std::vector<double> tl, gl;
+    c->dz_lut = 1e-3;
+    build_cosmology(opts.om0, opts.w0, opts.h, opts.z_max, c->dz_lut, tl, gl);
+    c->n_lut = (int)tl.size();
+    if (dmalloc(&c->d_tlut, tl.size()) != DSPS_OK || dmalloc(&c->d_glut, gl.size()) != DSPS_OK) {
+        free_ctx(c);
+        return DSPS_ERR_CUDA;
+    }
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void *d, const void *h, size_t b) { if (e == cudaSuccess) e = cudaMemcpy(d, h, b, cudaMemcpyHostToDevice); };
+    up(c->d_edges, edges.data(), edges.size() * sizeof(double));
+    up(c->d_logage, logage.data(), logage.size() * sizeof(float));
+    up(c->d_zedge, zedge.data(), zedge.size() * sizeof(float));
+    up(c->d_tlut, tl.data(), tl.size() * sizeof(double));
+    up(c->d_glut, gl.data(), gl.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = prepare_ssp_device(*c, g->l_ssp);
+    if (e != cudaSuccess) {
+        int r = cuda_fail(e, "dsps_create upload");
+        free_ctx(c);
+        return r;
+    }
+    *out = reinterpret_cast<dsps_ctx *>(c);
+    return DSPS_OK;
+}
+
+int dsps_destroy(dsps_ctx *ctx) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return DSPS_OK;
+    serve_stop(c);
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_ctx(c);
+    return DSPS_OK;
+}
+
+int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const double *const *lam,
+                     const double *const *trans, int32_t *set_id) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !n_pts || !lam || !trans || !set_id) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: null argument%s");
+    if (n_filt < 1 || n_filt > DSPS_MAX_FILTERS) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: 1..16 filters%s");
+    double lmax = 0.0;
+    std::vector<double> offq(n_filt);
+    for (int q = 0; q < n_filt; ++q) {
+        if (n_pts[q] < 2 || !lam[q] || !trans[q]) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: bad table%s");
+        double D = 0.0;
+        for (int m = 0; m < n_pts[q]; ++m) {
+            if (!(trans[q][m] >= 0) || !(lam[q][m] > 0)) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: bad values%s");
+            if (m > 0) {
+                if (!(lam[q][m] > lam[q][m - 1])) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: lambda not increasing%s");
+                D += 0.5 * (lam[q][m] - lam[q][m - 1]) * (trans[q][m] / lam[q][m] + trans[q][m - 1] / lam[q][m - 1]);
+            }
+        }
+        if (!(D > 0)) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: filter with zero transmission%s");
+        offq[q] = 2.5 * std::log10(AB0 * D);   // Eq. (restmag) denominator
+        lmax = std::max(lmax, lam[q][n_pts[q] - 1]);
+    }
+    FilterSet fs;
+    fs.Q = n_filt;
+    fs.Q4 = (n_filt + 3) / 4;
+    const double l0 = std::exp(c->lnlam0);
+    int M = lmax > l0 ? (int)std::ceil(std::log(lmax / l0) / c->dlnlam) + 2 : 1;
+    fs.m_rows = M + 2;
+    std::vector<float> tab((size_t)fs.m_rows * 4 * fs.Q4, 0.f);
+    for (int m = 0; m < M; ++m) {
+        double x = l0 * std::exp(m * c->dlnlam);
+        for (int q = 0; q < n_filt; ++q)
+            tab[(size_t)m * 4 * fs.Q4 + q] = (float)filter_interp(lam[q], trans[q], n_pts[q], x);
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    if (dmalloc(&fs.d_tab, tab.size()) != DSPS_OK) return DSPS_ERR_CUDA;
+    if (dmalloc(&fs.d_offq, (size_t)n_filt) != DSPS_OK) { cudaFree(fs.d_tab); return DSPS_ERR_CUDA; }
+    cudaError_t e = cudaMemcpy(fs.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fs.d_offq, offq.data(), offq.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(fs.d_tab); cudaFree(fs.d_offq); return cuda_fail(e, "dsps_filters_add upload"); }
+    c->sets.push_back(fs);
+    *set_id = (int32_t)c->sets.size() - 1;
+    return DSPS_OK;
+}
+
+int dsps_filters_count(dsps_ctx *ctx, int32_t set_id, int32_t *n_filt) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !n_filt) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_count: null argument%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (set_id < 0 || set_id >= (int)c->sets.size()) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_count: unknown set%s");
+    *n_filt = c->sets[set_id].Q;
+    return DSPS_OK;
+}
+
+int dsps_weights(dsps_ctx *ctx, int64_t n_gal, const float *params, float *w_out, dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || n_gal < 0 || (n_gal > 0 && (!params || !w_out))) return fail(DSPS_ERR_INVALID_ARG, "dsps_weights: bad argument%s");
+    if (n_gal == 0) return DSPS_OK;
+    DSPS_CUDA(cudaSetDevice(c->device));
+    DSPS_CUDA(launch_weights(*c, W_MSUN, params, n_gal, 0, n_gal, w_out, reinterpret_cast<cudaStream_t>(stream)));
+    return DSPS_OK;
+}
+
+int dsps_photometry(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
+                    float *mags, dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry: null context%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    return run_photometry(c, n_gal, params, set_id, precision, mags, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
+                        const float *mag_bar, float *mags, float *param_bar, dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry_vjp: null context%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    return run_photometry_vjp(c, n_gal, params, set_id, precision, mag_bar, mags, param_bar,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
+int dsps_submit(dsps_ctx *ctx, const dsps_request *req, uint64_t *ticket) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !req || !ticket) return fail(DSPS_ERR_INVALID_ARG, "dsps_submit: null argument%s");
+    return serve_submit(c, req, ticket);
+}
+
+int dsps_poll(dsps_ctx *ctx, uint64_t ticket, int64_t timeout_us, double *latency_us) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_poll: null context%s");
+    return serve_poll(c, ticket, timeout_us, latency_us);
+}
+
+int dsps_device_error(dsps_ctx *ctx, dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_device_error: null context%s");
+    DSPS_CUDA(cudaSetDevice(c->device));
+    DSPS_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    DSPS_CUDA(cudaDeviceSynchronize());
+    unsigned v = 0;
+    DSPS_CUDA(cudaMemcpy(&v, c->d_err, sizeof v, cudaMemcpyDeviceToHost));
+    DSPS_CUDA(cudaMemset(c->d_err, 0, sizeof v));
+    if (v & DERR_TIMEOUT) return fail(DSPS_ERR_DEVICE_FAULT, "a kernel gave up on a bounded wait%s");
+    if (v & DERR_PARAM) return fail(DSPS_ERR_INVALID_ARG, "some galaxies had out-of-range parameters%s");
+    return DSPS_OK;
+}
+
+int dsps_profile_enable(dsps_ctx *ctx, int32_t enable) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_profile_enable: null context%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->prof = enable != 0;
+    return DSPS_OK;
+}
+
+int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !out) return fail(DSPS_ERR_INVALID_ARG, "dsps_profile_read: null argument%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    std::memset(out, 0, sizeof *out);
+    DSPS_CUDA(cudaSetDevice(c->device));
+    int rc = DSPS_OK;
+    for (auto &r : c->prof_recs) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess && rc == DSPS_OK) rc = cuda_fail(e, "dsps_profile_read");
+        if (r.kind >= 0 && r.kind < DSPS_PROF_KINDS) {
+            out->launches[r.kind] += 1;
+            out->ms[r.kind] += ms;
+        }
+        c->ev_pool.push_back(r.a);
+        c->ev_pool.push_back(r.b);
+    }
+    c->prof_recs.clear();
+    return rc;
+}
+
+const char *dsps_strerror(int code) {
+    switch (code) {
+    case DSPS_OK: return "ok";
+    case DSPS_PENDING: return "pending";
+    case DSPS_ERR_INVALID_ARG: return "invalid argument";
+    case DSPS_ERR_OUT_OF_BUDGET: return "request does not fit the HBM budget";
+    case DSPS_ERR_CUDA: return "CUDA error";
+    case DSPS_ERR_TIMEOUT: return "timeout";
+    case DSPS_ERR_DEVICE_FAULT: return "device fault (bounded wait expired)";
+    case DSPS_ERR_UNSUPPORTED: return "unsupported";
+    case DSPS_ERR_NOT_FOUND: return "unknown ticket";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// dsps_internal.cuh -- context layout and device helpers shared by the CUDA
+// translation units of libdsps (sm_103a only).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/dsps.h"
+
+namespace dsps {
+
+constexpr int NPAR = DSPS_NPAR;
+constexpr int NGRAD = DSPS_NGRAD;
+constexpr int K_ALIGN = 64;      // K (= n_age * n_z) padding: multiple of the 32-wide TMA box
+constexpr int N_ALIGN = 256;     // wavelength padding: multiple of the 256-wide MMA tile
+constexpr int MAX_NT = 1024;     // SFR time nodes
+constexpr int MAX_NAGE = 512;
+constexpr int AUX_STRIDE = 8;    // floats of per-galaxy epilogue constants
+
+// Device error word bits.
+constexpr unsigned DERR_PARAM = 1u;    // out-of-range galaxy parameters
+constexpr unsigned DERR_TIMEOUT = 2u;  // a kernel gave up on a bounded wait
+
+constexpr double AB0 = 1.13492e-13;     // Sec. 2.2, Eq. (restmag)
+constexpr double LAM_V = 5500.0;        // Sec. 3.4, Eq. (salim)
+constexpr double SIG_Q = 0.3;           // quench transition width [Gyr]
+
+// Per-galaxy epilogue constants (aux[g*AUX_STRIDE + .]):
+//   0 alpha = -0.4 log2(10) Av      (F = 2^(alpha u))
+//   1 beta  = delta - 0.7           (u = 2^(beta log2(lam/5500)))
+//   2 s     = ln(1+z) / dlnlam      (observer-frame shift in grid steps)
+//   3 valid (1 or 0)
+//   4 Av, 5 delta  (gradient path)
+// magoff[g] (double) = -2.5 logM + Dmod(z) - 2.5 log10(1+z)
+
+struct FilterSet {
+    int Q = 0, Q4 = 0;         // filters; float4 groups per table row
+    int m_rows = 0;            // table rows; row m_rows-1 is all zero
+    float *d_tab = nullptr;    // [m_rows][4*Q4] T_q(lam0 exp(m dlnlam))
+    double *d_offq = nullptr;  // [Q] 2.5 log10(AB0 D_q)
+};
+
+struct Serve;  // request loop (serve.cu)
+
+struct Ctx {
+    int device = 0;
+    dsps_opts opts{};
+    int n_age = 0, n_z = 0, n_lam = 0, K = 0, K_pad = 0, N_pad = 0, n_t = 0;
+    double t0 = 0, t1 = 0;
+    double lnlam0 = 0, dlnlam = 0;
+    int num_sms = 0;
+
+    // Resident SSP copies.
+    float *d_L32 = nullptr;                 // [K_pad][N_pad] fp32 (SIMT path)
+    __nv_bfloat16 *d_Lt_hi = nullptr;       // [N_pad][K_pad] row-scaled hi (tensor path)
+    __nv_bfloat16 *d_Lt_lo = nullptr;       // [N_pad][K_pad] row-scaled lo
+    float *d_wmul = nullptr;                // [K_pad] 2^E_k: weight multiplier of the scaled rows
+
+    // Grids and tables.
+    float *d_logage = nullptr;              // [n_age] log10(age/yr)
+    double *d_edges = nullptr;              // [n_age+1] age-bin edges [Gyr]
+    float *d_zedge = nullptr;               // [n_z+1] lgZ bin edges (+-1e30 outer)
+    double *d_tlut = nullptr;               // [n_lut] t_obs(z) [Gyr]
+    double *d_glut = nullptr;               // [n_lut] Dmod(z) - 5 log10 z
+    int n_lut = 0;
+    double dz_lut = 0;
+
+    // Work space (one chunk of galaxies).
+    int64_t chunk = 0;                      // galaxies per chunk (multiple of 128)
+    float *d_w32 = nullptr;                 // [chunk][K_pad] fp32 weights
+    __nv_bfloat16 *d_whi = nullptr;         // [chunk][K_pad]
+    __nv_bfloat16 *d_wlo = nullptr;         // [chunk][K_pad]
+    float *d_aux = nullptr;                 // [chunk][AUX_STRIDE]
+    double *d_magoff = nullptr;             // [chunk]
+    unsigned *d_err = nullptr;              // sticky error word
+
+    std::vector<FilterSet> sets;
+    std::mutex mu;
+    Serve *serve = nullptr;
+
+    // Kernel timing (dsps_profile_*): event pairs recorded around launches.
+    struct ProfRec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    bool prof = false;
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+// Records an event pair around the launches made during its lifetime when the
+// context's profiling is on (caller holds ctx.mu).
+struct ProfScope {
+    Ctx &c;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEvent_t take() {
+        cudaEvent_t e = nullptr;
+        if (!c.ev_pool.empty()) {
+            e = c.ev_pool.back();
+            c.ev_pool.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+        }
+        return e;
+    }
+    ProfScope(Ctx &c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
+        if (!c.prof) return;
+        a = take();
+        b = take();
+        if (a && b) cudaEventRecord(a, s);
+    }
+    ~ProfScope() {
+        if (a && b) {
+            cudaEventRecord(b, s);
+            c.prof_recs.push_back({kind, a, b});
+        }
+    }
+};
+
+// ----------------------------------------------------------------------------
+// Kernel launch wrappers (defined in the .cu files)
+// ----------------------------------------------------------------------------
+enum WeightsMode { W_MSUN = 0, W_OMEGA_F32 = 1, W_OMEGA_BF16X2 = 2 };
+
+cudaError_t launch_weights(const Ctx &c, int mode, const float *params, int64_t G_stride,
+                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s);
+
+cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags,
+                             cudaStream_t s);
+
+cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, float *mags,
+                           cudaStream_t s);
+
+cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp);
+
+// ----------------------------------------------------------------------------
+// Device helpers
+// ----------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+// Appendix B, Eq. (terf): triweight CDF in the standardised variable, saturated
+// to 0 / 1 outside [-3, 3].
+__device__ __forceinline__ float terf_f(float z) {
+    if (z <= -3.f) return 0.f;
+    if (z >= 3.f) return 1.f;
+    float z2 = z * z;
+    float p = fmaf(z2, -5.f / 69984.f, 7.f / 2592.f);
+    p = fmaf(z2, p, -35.f / 864.f);
+    p = fmaf(z2, p, 35.f / 96.f);
+    return fmaf(z, p, 0.5f);
+}
+
+// Appendix B, Eq. (triweight): density in the standardised variable.
+__device__ __forceinline__ float triweight_f(float z) {
+    if (z <= -3.f || z >= 3.f) return 0.f;
+    float t = fmaf(-z / 3.f, z / 3.f, 1.f);
+    return (35.f / 96.f) * t * t * t;
+}
+
+__device__ __forceinline__ float gauss_cdf_f(float z) { return 0.5f * erfcf(-z * 0.70710678118654752f); }
+__device__ __forceinline__ float gauss_pdf_f(float z) { return 0.39894228040143268f * expf(-0.5f * z * z); }
+
+#endif  // __CUDACC__
+
+}  // namespace dsps

@@ -1,0 +1,181 @@
+// phot_simt.cu -- FP32 SIMT form of the fused photometry kernel.
+//
+// S = omega . L (Eq. full_mdf) as a register-tiled FP32 GEMM: each CTA owns 128
+// galaxies and walks every 128-wide wavelength tile; after the K loop of a tile
+// the 128x128 block of S goes through shared memory to the epilogue, where two
+// threads per galaxy row apply dust, the redshifted filter lookup and the
+// wavelength reduction (epilogue.cuh).  Per-(galaxy, filter) sums stay in
+// registers across tiles; no spectrum is written to global memory.
+#include "dsps_internal.cuh"
+#include "epilogue.cuh"
+
+namespace dsps {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 16, THREADS = 256;
+constexpr int AS_LD = BM + 4;
+constexpr int CS_LD = BN + 1;
+
+struct SArgs {
+    const float *W;        // [n][K_pad]
+    const float *L;        // [K_pad][N_pad]
+    int K_pad, N_pad, Q, m_last;
+    int64_t n;
+    const float *aux;
+    const double *magoff;
+    const float4 *tab;
+    const double *offq;
+    ColConst cc;
+    float *mags;           // [n][Q]
+};
+
+template <int Q4>
+__global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
+    __shared__ __align__(16) float As[2][BK][AS_LD];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+    extern __shared__ float Cs[];  // [BM][CS_LD]
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int er = tid >> 1, eh = tid & 1;
+    const RowConst rc = load_row_const(a.aux, m0 + er, a.n);
+
+    float acc[4 * Q4];
+#pragma unroll
+    for (int q = 0; q < 4 * Q4; ++q) acc[q] = 0.f;
+
+    const int KT = a.K_pad / BK;
+    for (int n0 = 0; n0 < a.N_pad; n0 += BN) {
+        float c[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) c[i][j] = 0.f;
+
+        float4 ra[2], rb[2];
+        auto gload = [&](int k0) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                int idx = tid + t * THREADS;
+                int row = idx >> 2, kq = (idx & 3) * 4;
+                int64_t gr = m0 + row;
+                ra[t] = gr < a.n ? *reinterpret_cast<const float4 *>(a.W + gr * a.K_pad + k0 + kq)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                int k = idx >> 5, nq = (idx & 31) * 4;
+                rb[t] = *reinterpret_cast<const float4 *>(a.L + (int64_t)(k0 + k) * a.N_pad + n0 + nq);
+            }
+        };
+        auto sstore = [&](int buf) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                int idx = tid + t * THREADS;
+                int row = idx >> 2, kq = (idx & 3) * 4;
+                As[buf][kq + 0][row] = ra[t].x;
+                As[buf][kq + 1][row] = ra[t].y;
+                As[buf][kq + 2][row] = ra[t].z;
+                As[buf][kq + 3][row] = ra[t].w;
+                int k = idx >> 5, nq = (idx & 31) * 4;
+                *reinterpret_cast<float4 *>(&Bs[buf][k][nq]) = rb[t];
+            }
+        };
+
+        gload(0);
+        sstore(0);
+        __syncthreads();
+        for (int kt = 0; kt < KT; ++kt) {
+            const int buf = kt & 1;
+            if (kt + 1 < KT) gload((kt + 1) * BK);
+#pragma unroll
+            for (int k = 0; k < BK; ++k) {
+                float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
+                float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][64 + ty * 4]);
+                float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
+                float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][64 + tx * 4]);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) c[i][j] = fmaf(av[i], bv[j], c[i][j]);
+            }
+            if (kt + 1 < KT) sstore(buf ^ 1);
+            __syncthreads();
+        }
+
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int r = (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                int col = (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+                Cs[r * CS_LD + col] = c[i][j];
+            }
+        }
+        __syncthreads();
+
+        if (rc.valid) {
+            float vprev = 0.f;
+            const int nb = n0 + eh * 64;
+            for (int jj = 0; jj < 64; ++jj)
+                epi_node<Q4>(acc, vprev, Cs[er * CS_LD + eh * 64 + jj], nb + jj, rc, a.cc, a.tab, a.m_last);
+            epi_close<Q4>(acc, vprev, nb + 64, rc, a.tab, a.m_last);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int q = 0; q < 4 * Q4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 1);
+    const int64_t row = m0 + er;
+    if (eh == 0 && row < a.n)
+        write_mags<Q4>(acc, a.Q, a.magoff[row], a.offq, a.mags + row * a.Q);
+}
+
+template <int Q4>
+cudaError_t launch_q4(const SArgs &a, int64_t n, cudaStream_t s) {
+    size_t smem = (size_t)BM * CS_LD * sizeof(float);
+    cudaFuncSetAttribute(phot_simt_kernel<Q4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((unsigned)((n + BM - 1) / BM));
+    phot_simt_kernel<Q4><<<grid, THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+ColConst make_col_const(const Ctx &c) {
+    ColConst cc;
+    cc.ell0 = (float)((c.lnlam0 - std::log(LAM_V)) / std::log(2.0));
+    cc.dell = (float)(c.dlnlam / std::log(2.0));
+    cc.kap0 = (float)(0.5 * std::expm1(c.dlnlam));
+    cc.kapmid = (float)std::sinh(c.dlnlam);
+    cc.kapN = (float)(-0.5 * std::expm1(-c.dlnlam));
+    cc.N = c.n_lam;
+    return cc;
+}
+
+cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    SArgs a{};
+    a.W = c.d_w32;
+    a.L = c.d_L32;
+    a.K_pad = c.K_pad;
+    a.N_pad = c.N_pad;
+    a.Q = fs.Q;
+    a.m_last = fs.m_rows - 1;
+    a.n = n;
+    a.aux = c.d_aux;
+    a.magoff = c.d_magoff;
+    a.tab = reinterpret_cast<const float4 *>(fs.d_tab);
+    a.offq = fs.d_offq;
+    a.cc = make_col_const(c);
+    a.mags = mags;
+    switch (fs.Q4) {
+    case 1: return launch_q4<1>(a, n, s);
+    case 2: return launch_q4<2>(a, n, s);
+    case 3: return launch_q4<3>(a, n, s);
+    default: return launch_q4<4>(a, n, s);
+    }
+}
+
+}  // namespace dsps

@@ -1,0 +1,428 @@
+// phot_tc.cu -- tcgen05 (5th-generation tensor core) form of the fused
+// photometry kernel for sm_103a.
+//
+// Contraction S[g, n] = sum_k omega[g, k] L[k, n] (Eq. full_mdf), M = galaxies,
+// N = wavelength nodes, K = n_age * n_z, in the split-bf16 form
+//   S = W_hi L_hi + W_hi L_lo + W_lo L_hi     (bf16 operands, FP32 accumulate)
+// where W = omega * 2^E_k and L = L_ssp * 2^-E_k are split into bf16 hi + lo.
+//
+// Persistent CTAs (one per SM) walk 128-galaxy tiles; each tile sweeps all
+// 256-wide wavelength tiles.  Warp roles:
+//   warp 0      TMA producer: 4-stage ring of {W_hi, W_lo, L_hi, L_lo} K-slices
+//               (32 bf16 = 64 B rows, 64-byte swizzle), one mbarrier per stage.
+//   warp 1      TMEM allocator and single-thread MMA issuer: per K-slice six
+//               128x256x16 tcgen05.mma kind::f16 into one of two TMEM
+//               accumulators (2 x 256 columns), tcgen05.commit to free the
+//               stage and, per tile, to hand the accumulator to the epilogue.
+//   warps 2..9  epilogue: tcgen05.ld 32x32b (one galaxy row per thread), dust,
+//               redshifted filter lookup and wavelength reduction in registers
+//               (epilogue.cuh); two warps per TMEM lane quadrant split the 256
+//               columns.  No spectrum leaves the SM.
+// Every wait on an mbarrier is bounded; on expiry the kernel records
+// DERR_TIMEOUT, lets its in-flight copies and MMAs land, frees TMEM and returns.
+#include <cudaTypedefs.h>
+
+#include "dsps_internal.cuh"
+#include "epilogue.cuh"
+
+namespace dsps {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 32;
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int NUM_EPI_WARPS = 8;
+constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
+constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr long long WAIT_LIMIT = 2000000000LL;   // SM clock cycles, about one second
+constexpr int QMAX = 16;
+constexpr size_t BAR_BYTES = 1024;
+constexpr size_t COMB_BYTES = (size_t)BM * QMAX * 4;
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + COMB_BYTES;
+
+// kind::f16 instruction descriptor: FP32 accumulate (bits 4-5 = 1), A and B
+// bf16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct TArgs {
+    const float *aux;
+    const double *magoff;
+    const float4 *tab;
+    const double *offq;
+    ColConst cc;
+    int Q, m_last, n_mtiles, n_ntiles, kblocks;
+    int64_t n;
+    float *mags;
+    unsigned *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true once the phase of the given parity has completed; false
+// if another role aborted or the limit expired (which aborts the CTA).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_LIMIT) {
+            *abort_flag = 1;
+            atomicOr(err, DERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand with the 64-byte swizzle:
+// start address >> 4 (bits 0-13), leading offset unused (1), stride between
+// 8-row groups 8 x 64 B = 512 B (bits 32-45, >> 4), descriptor version 1
+// (bit 46), layout type 4 = SWIZZLE_64B (bits 61-63).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)4u << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+template <int Q4>
+__global__ void __launch_bounds__(THREADS, 1)
+phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+               const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+               const TArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + (size_t)STAGES * STAGE_BYTES);
+    const uint32_t full0 = smem_u32(bars);
+    const uint32_t empty0 = smem_u32(bars + STAGES);
+    const uint32_t accf0 = smem_u32(bars + 2 * STAGES);
+    const uint32_t acce0 = smem_u32(bars + 2 * STAGES + 2);
+    const uint32_t ebar = smem_u32(bars + 2 * STAGES + 4);
+    const uint32_t drain = smem_u32(bars + 2 * STAGES + 5);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 6);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *comb = reinterpret_cast<float *>(sm + (size_t)STAGES * STAGE_BYTES + BAR_BYTES);
+    const uint32_t sbase = smem_u32(sm);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(accf0 + 8 * i, 1);
+            mbar_init(acce0 + 8 * i, NUM_EPI_WARPS);
+        }
+        mbar_init(ebar, NUM_EPI_WARPS);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int armed[STAGES];
+            for (int s = 0; s < STAGES; ++s) armed[s] = -1;
+            bool ok = true;
+            for (int mt = blockIdx.x; ok && mt < a.n_mtiles; mt += gridDim.x)
+                for (int nt = 0; ok && nt < a.n_ntiles; ++nt)
+                    for (int kb = 0; kb < a.kblocks; ++kb) {
+                        if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, a.err)) { ok = false; break; }
+                        const uint32_t fb = full0 + 8 * stage;
+                        const uint32_t st = sbase + stage * STAGE_BYTES;
+                        mbar_expect_tx(fb, STAGE_BYTES);
+                        tma_load_2d(st, &tmA_hi, fb, kb * BK, mt * BM);
+                        tma_load_2d(st + A_BYTES, &tmA_lo, fb, kb * BK, mt * BM);
+                        tma_load_2d(st + 2 * A_BYTES, &tmB_hi, fb, kb * BK, nt * BN);
+                        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmB_lo, fb, kb * BK, nt * BN);
+                        armed[stage] = (int)phase;
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+            // Let every armed copy land before the CTA can exit.
+            for (int s = 0; s < STAGES; ++s)
+                if (armed[s] >= 0) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(full0 + 8 * s, (uint32_t)armed[s]) && clock64() - t0 < WAIT_LIMIT) {
+                    }
+                }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int stage = 0, as = 0;
+            uint32_t phase = 0, aphase = 0;
+            bool ok = true;
+            for (int mt = blockIdx.x; ok && mt < a.n_mtiles; mt += gridDim.x)
+                for (int nt = 0; ok && nt < a.n_ntiles; ++nt) {
+                    if (!mbar_wait(acce0 + 8 * as, aphase ^ 1u, abort_flag, a.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + (uint32_t)(as * BN);
+                    for (int kb = 0; kb < a.kblocks; ++kb) {
+                        if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, a.err)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t st = sbase + stage * STAGE_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint64_t ah = sdesc_sw64(st + kk * 32);
+                            const uint64_t al = sdesc_sw64(st + A_BYTES + kk * 32);
+                            const uint64_t bh = sdesc_sw64(st + 2 * A_BYTES + kk * 32);
+                            const uint64_t bl = sdesc_sw64(st + 2 * A_BYTES + B_BYTES + kk * 32);
+                            mma_bf16(d, ah, bh, (kb | kk) != 0 ? 1u : 0u);
+                            mma_bf16(d, ah, bl, 1u);
+                            mma_bf16(d, al, bh, 1u);
+                        }
+                        mma_commit(empty0 + 8 * stage);
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    mma_commit(accf0 + 8 * as);
+                    if (++as == 2) { as = 0; aphase ^= 1u; }
+                }
+            // Every MMA issued so far completes before this commit arrives.
+            mma_commit(drain);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int ew = warp - 2;
+        const int qd = warp & 3;
+        const int half = ew >> 2;
+        const int row = qd * 32 + lane;
+        int as = 0;
+        uint32_t aphase = 0, ephase = 0;
+        bool ok = true;
+        for (int mt = blockIdx.x; ok && mt < a.n_mtiles; mt += gridDim.x) {
+            const int64_t rowg = (int64_t)mt * BM + row;
+            const RowConst rc = load_row_const(a.aux, rowg, a.n);
+            float acc[4 * Q4];
+#pragma unroll
+            for (int q = 0; q < 4 * Q4; ++q) acc[q] = 0.f;
+            for (int nt = 0; nt < a.n_ntiles; ++nt) {
+                int got = 1;
+                if (lane == 0) got = mbar_wait(accf0 + 8 * as, aphase, abort_flag, a.err) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t tb = tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(as * BN + half * 128);
+                const int nb = nt * BN + half * 128;
+                float vprev = 0.f;
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t r[32];
+                    tmem_ld32(tb + c * 32, r);
+                    if (c == 3) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acce0 + 8 * as);
+                    }
+                    if (rc.valid) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            epi_node<Q4>(acc, vprev, __uint_as_float(r[j]), nb + c * 32 + j, rc, a.cc, a.tab,
+                                         a.m_last);
+                    }
+                }
+                if (rc.valid) epi_close<Q4>(acc, vprev, nb + 128, rc, a.tab, a.m_last);
+                if (++as == 2) { as = 0; aphase ^= 1u; }
+            }
+            if (!ok) break;
+            // Combine the two column halves of each row (bounded barrier).
+            if (half == 1)
+#pragma unroll
+                for (int q = 0; q < 4 * Q4; ++q) comb[row * QMAX + q] = acc[q];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ebar);
+            int got = 1;
+            if (lane == 0) got = mbar_wait(ebar, ephase, abort_flag, a.err) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            ephase ^= 1u;
+            if (!got) break;
+            if (half == 0 && rowg < a.n) {
+#pragma unroll
+                for (int q = 0; q < 4 * Q4; ++q) acc[q] += comb[row * QMAX + q];
+                write_mags<Q4>(acc, a.Q, a.magoff[rowg], a.offq, a.mags + rowg * a.Q);
+            }
+            // Second bounded barrier: half 0 has read comb before half 1 rewrites it.
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ebar);
+            got = 1;
+            if (lane == 0) got = mbar_wait(ebar, ephase, abort_flag, a.err) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            ephase ^= 1u;
+            if (!got) break;
+        }
+    }
+
+    __syncwarp();   // lanes 1..31 of the producer / MMA warps wait for their lane 0
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D bf16 tensor [outer][inner] with row pitch `inner` elements, box
+// {BK, box_outer}, 64-byte swizzle; rows past `outer` read as zero.
+bool make_tmap(CUtensorMap *tm, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_outer) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int Q4>
+cudaError_t launch_q4(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
+                      const TArgs &a, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(phot_tc_kernel<Q4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    phot_tc_kernel<Q4><<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, float *mags, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (fs.Q > QMAX) return cudaErrorInvalidValue;
+    CUtensorMap ah, al, bh, bl;
+    if (!make_tmap(&ah, c.d_whi, (uint64_t)c.K_pad, (uint64_t)n, BM) ||
+        !make_tmap(&al, c.d_wlo, (uint64_t)c.K_pad, (uint64_t)n, BM) ||
+        !make_tmap(&bh, c.d_Lt_hi, (uint64_t)c.K_pad, (uint64_t)c.N_pad, BN) ||
+        !make_tmap(&bl, c.d_Lt_lo, (uint64_t)c.K_pad, (uint64_t)c.N_pad, BN))
+        return cudaErrorInvalidValue;
+    TArgs a{};
+    a.aux = c.d_aux;
+    a.magoff = c.d_magoff;
+    a.tab = reinterpret_cast<const float4 *>(fs.d_tab);
+    a.offq = fs.d_offq;
+    a.cc = make_col_const(c);
+    a.Q = fs.Q;
+    a.m_last = fs.m_rows - 1;
+    a.n_mtiles = (int)((n + BM - 1) / BM);
+    a.n_ntiles = c.N_pad / BN;
+    a.kblocks = c.K_pad / BK;
+    a.n = n;
+    a.mags = mags;
+    a.err = c.d_err;
+    int grid = a.n_mtiles < c.num_sms ? a.n_mtiles : c.num_sms;
+    switch (fs.Q4) {
+    case 1: return launch_q4<1>(ah, al, bh, bl, a, grid, s);
+    case 2: return launch_q4<2>(ah, al, bh, bl, a, grid, s);
+    case 3: return launch_q4<3>(ah, al, bh, bl, a, grid, s);
+    default: return launch_q4<4>(ah, al, bh, bl, a, grid, s);
+    }
+}
+
+}  // namespace dsps

@@ -1,0 +1,90 @@
+// prep.cu -- one-time preparation of the resident SSP block (Sec. 2.1: the SSP
+// spectra are computed in advance, loaded once as a contiguous block and held
+// fixed).  Builds, from the caller's FP32 L[k][n] (k = i * n_z + j):
+//   d_L32   [K_pad][N_pad] FP32, zero padded                (SIMT form)
+//   d_Lt_*  [N_pad][K_pad] bf16 hi / lo of L[k][n] 2^-E_k    (tensor form, K-major rows)
+//   d_wmul  [K_pad] 2^E_k, the factor folded into the weights, so that
+//           sum_k (omega_k 2^E_k)(L_kn 2^-E_k) = sum_k omega_k L_kn exactly.
+// E_k is the binary exponent of max_n L[k][n]: every scaled row peaks in
+// [1, 2), far from the bf16 underflow threshold.
+#include "dsps_internal.cuh"
+
+namespace dsps {
+
+namespace {
+
+__global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, float *wmul, float *rscale) {
+    const int k = blockIdx.x;
+    if (k >= K_pad) return;
+    float m = 0.f;
+    if (k < K)
+        for (int n = threadIdx.x; n < N; n += blockDim.x) m = fmaxf(m, L[(size_t)k * N + n]);
+    __shared__ float red[32];
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mm = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, red[w]);
+        int E = 0;
+        if (mm > 0.f) E = ilogbf(mm);
+        E = max(-120, min(120, E));
+        wmul[k] = k < K ? ldexpf(1.f, E) : 0.f;
+        rscale[k] = k < K ? ldexpf(1.f, -E) : 0.f;
+    }
+}
+
+__global__ void build_l32_kernel(const float *L, int K, int N, int K_pad, int N_pad, float *L32) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)K_pad * N_pad;
+    if (idx >= total) return;
+    const int k = (int)(idx / N_pad), n = (int)(idx % N_pad);
+    L32[idx] = (k < K && n < N) ? L[(size_t)k * N + n] : 0.f;
+}
+
+// Transposing split: tile of 32 (k) x 32 (n) through shared memory.
+__global__ void build_lt_kernel(const float *L, const float *rscale, int K, int N, int K_pad, int N_pad,
+                                __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+    __shared__ float t[32][33];
+    const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        int k = k0 + r, n = n0 + tx;
+        t[r][tx] = (k < K && n < N) ? L[(size_t)k * N + n] * rscale[k] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        int n = n0 + r, k = k0 + tx;
+        if (n < N_pad && k < K_pad) {
+            float v = t[tx][r];
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            hi[(size_t)n * K_pad + k] = h;
+            lo[(size_t)n * K_pad + k] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
+    const size_t KN = (size_t)c.K * c.n_lam;
+    float *d_raw = nullptr, *d_rscale = nullptr;
+    cudaError_t e = cudaMalloc(&d_raw, KN * sizeof(float));
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&d_rscale, (size_t)c.K_pad * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(d_raw, h_lssp, KN * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        row_exponent_kernel<<<c.K_pad, 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.d_wmul, d_rscale);
+        const size_t tot = (size_t)c.K_pad * c.N_pad;
+        build_l32_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.N_pad, c.d_L32);
+        dim3 g(c.N_pad / 32, c.K_pad / 32), b(32, 8);
+        build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.K, c.n_lam, c.K_pad, c.N_pad, c.d_Lt_hi, c.d_Lt_lo);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    cudaFree(d_rscale);
+    cudaFree(d_raw);
+    return e;
+}
+
+}  // namespace dsps

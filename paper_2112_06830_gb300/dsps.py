@@ -1,0 +1,301 @@
+"""Thin ctypes binding of libdsps (include/dsps.h).
+
+The functions ``dsps_*`` below have the names and arguments of the C ABI and
+only marshal arguments; every step of the photometry path runs in the CUDA
+library.  ``Context`` is a small convenience layer over them that takes torch
+tensors (torch is used for device memory and streams only).
+
+Loading fails loudly (``RuntimeError``) when libdsps.so cannot be built or
+loaded: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+DSPS_OK = 0
+DSPS_PENDING = 1
+DSPS_ERR_INVALID_ARG = -1
+DSPS_ERR_OUT_OF_BUDGET = -2
+DSPS_ERR_CUDA = -3
+DSPS_ERR_TIMEOUT = -4
+DSPS_ERR_DEVICE_FAULT = -5
+DSPS_ERR_UNSUPPORTED = -6
+DSPS_ERR_NOT_FOUND = -7
+
+DSPS_SFH_DELAYED_TAU = 0
+DSPS_SFH_DPL_QUENCH = 1
+DSPS_MDF_TRIWEIGHT = 0
+DSPS_MDF_GAUSSIAN = 1
+DSPS_PREC_FP32 = 0
+DSPS_PREC_BF16X3 = 1
+DSPS_NPAR = 12
+DSPS_NGRAD = 11
+DSPS_MAX_FILTERS = 16
+
+
+class dsps_grid(C.Structure):
+    _fields_ = [("n_age", C.c_int32), ("n_z", C.c_int32), ("n_lam", C.c_int32),
+                ("log_age_yr", C.POINTER(C.c_double)), ("lgz", C.POINTER(C.c_double)),
+                ("lam", C.POINTER(C.c_double)), ("l_ssp", C.POINTER(C.c_float)),
+                ("t0_gyr", C.c_double), ("t1_gyr", C.c_double), ("n_t", C.c_int32)]
+
+
+class dsps_opts(C.Structure):
+    _fields_ = [("om0", C.c_double), ("w0", C.c_double), ("h", C.c_double),
+                ("sfh_model", C.c_int32), ("mdf_kernel", C.c_int32), ("device", C.c_int32),
+                ("max_chunk", C.c_int64), ("hbm_budget_bytes", C.c_int64), ("n_streams", C.c_int32),
+                ("z_max", C.c_double)]
+
+
+DSPS_PROF_KINDS = 4
+
+
+class dsps_profile_t(C.Structure):
+    _fields_ = [("launches", C.c_int64 * DSPS_PROF_KINDS), ("ms", C.c_double * DSPS_PROF_KINDS)]
+
+
+class dsps_request(C.Structure):
+    _fields_ = [("n_gal", C.c_int64), ("params", C.c_void_p), ("set_id", C.c_int32),
+                ("precision", C.c_int32), ("want_grad", C.c_int32), ("mag_bar", C.c_void_p),
+                ("mags", C.c_void_p), ("param_bar", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("dsps_default_opts", None, [C.POINTER(dsps_opts)]),
+    ("dsps_create", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(dsps_grid), C.POINTER(dsps_opts)]),
+    ("dsps_destroy", C.c_int, [C.c_void_p]),
+    ("dsps_filters_add", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
+                                   C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.POINTER(C.c_double)),
+                                   C.POINTER(C.c_int32)]),
+    ("dsps_filters_count", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    ("dsps_weights", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("dsps_photometry", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                  C.c_void_p]),
+    ("dsps_photometry_vjp", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("dsps_submit", C.c_int, [C.c_void_p, C.POINTER(dsps_request), C.POINTER(C.c_uint64)]),
+    ("dsps_poll", C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(C.c_double)]),
+    ("dsps_device_error", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("dsps_profile_enable", C.c_int, [C.c_void_p, C.c_int32]),
+    ("dsps_profile_read", C.c_int, [C.c_void_p, C.POINTER(dsps_profile_t)]),
+    ("dsps_strerror", C.c_char_p, [C.c_int]),
+    ("dsps_last_error_message", C.c_char_p, []),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Builds (if needed) and loads libdsps.so; raises RuntimeError on failure."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            try:
+                path = _build.build()
+                lib = C.CDLL(path)
+            except Exception as e:  # noqa: BLE001
+                raise RuntimeError(f"libdsps.so could not be built or loaded: {e}") from e
+            for name, res, args in _SIGS:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class DSPSError(RuntimeError):
+    def __init__(self, code, where):
+        lib = load()
+        msg = lib.dsps_last_error_message().decode(errors="replace")
+        super().__init__(f"{where}: {lib.dsps_strerror(code).decode()} ({code}): {msg}")
+        self.code = code
+
+
+def _check(code, where):
+    if code < 0:
+        raise DSPSError(code, where)
+    return code
+
+
+# ---- C ABI, one function per entry point -------------------------------------
+
+def dsps_default_opts():
+    o = dsps_opts()
+    load().dsps_default_opts(C.byref(o))
+    return o
+
+
+def dsps_create(grid: dsps_grid, opts: dsps_opts):
+    h = C.c_void_p()
+    _check(load().dsps_create(C.byref(h), C.byref(grid), C.byref(opts)), "dsps_create")
+    return h
+
+
+def dsps_destroy(ctx):
+    return _check(load().dsps_destroy(ctx), "dsps_destroy")
+
+
+def dsps_filters_add(ctx, tables):
+    n = len(tables)
+    lam = [np.ascontiguousarray(l, dtype=np.float64) for l, _ in tables]
+    tr = [np.ascontiguousarray(t, dtype=np.float64) for _, t in tables]
+    n_pts = (C.c_int32 * n)(*[len(x) for x in lam])
+    lp = (C.POINTER(C.c_double) * n)(*[x.ctypes.data_as(C.POINTER(C.c_double)) for x in lam])
+    tp = (C.POINTER(C.c_double) * n)(*[x.ctypes.data_as(C.POINTER(C.c_double)) for x in tr])
+    sid = C.c_int32()
+    _check(load().dsps_filters_add(ctx, n, n_pts, lp, tp, C.byref(sid)), "dsps_filters_add")
+    return sid.value
+
+
+def dsps_filters_count(ctx, set_id):
+    q = C.c_int32()
+    _check(load().dsps_filters_count(ctx, set_id, C.byref(q)), "dsps_filters_count")
+    return q.value
+
+
+def dsps_weights(ctx, n_gal, params_ptr, w_out_ptr, stream=0):
+    return _check(load().dsps_weights(ctx, n_gal, params_ptr, w_out_ptr, stream), "dsps_weights")
+
+
+def dsps_photometry(ctx, n_gal, params_ptr, set_id, precision, mags_ptr, stream=0):
+    return _check(load().dsps_photometry(ctx, n_gal, params_ptr, set_id, precision, mags_ptr, stream),
+                  "dsps_photometry")
+
+
+def dsps_photometry_vjp(ctx, n_gal, params_ptr, set_id, precision, mag_bar_ptr, mags_ptr, param_bar_ptr,
+                        stream=0):
+    return _check(load().dsps_photometry_vjp(ctx, n_gal, params_ptr, set_id, precision, mag_bar_ptr,
+                                             mags_ptr, param_bar_ptr, stream), "dsps_photometry_vjp")
+
+
+def dsps_submit(ctx, req: dsps_request):
+    t = C.c_uint64()
+    _check(load().dsps_submit(ctx, C.byref(req), C.byref(t)), "dsps_submit")
+    return t.value
+
+
+def dsps_poll(ctx, ticket, timeout_us=0):
+    lat = C.c_double(0.0)
+    rc = _check(load().dsps_poll(ctx, ticket, timeout_us, C.byref(lat)), "dsps_poll")
+    return rc, lat.value
+
+
+def dsps_device_error(ctx, stream=0):
+    return load().dsps_device_error(ctx, stream)
+
+
+def dsps_profile_enable(ctx, enable=True):
+    return _check(load().dsps_profile_enable(ctx, 1 if enable else 0), "dsps_profile_enable")
+
+
+def dsps_profile_read(ctx):
+    """{kind: (launches, ms)} for kinds 0 weights, 1 fp32, 2 tensor, 3 adjoint."""
+    p = dsps_profile_t()
+    _check(load().dsps_profile_read(ctx, C.byref(p)), "dsps_profile_read")
+    return {k: (int(p.launches[k]), float(p.ms[k])) for k in range(DSPS_PROF_KINDS)}
+
+
+def dsps_strerror(code):
+    return load().dsps_strerror(code).decode()
+
+
+# ---- convenience layer over torch tensors ------------------------------------
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Context:
+    """Owns a dsps context (resident SSP block, cosmology table, work space)."""
+
+    def __init__(self, ssp, sfh_model=DSPS_SFH_DELAYED_TAU, mdf_kernel=DSPS_MDF_TRIWEIGHT, device=0,
+                 max_chunk=None, hbm_budget_bytes=None, n_streams=None, om0=0.3, w0=-1.0, h=0.7, z_max=10.0):
+        self._keep = [np.ascontiguousarray(ssp.log_age_yr, dtype=np.float64),
+                      np.ascontiguousarray(ssp.lgz, dtype=np.float64),
+                      np.ascontiguousarray(ssp.lam, dtype=np.float64),
+                      np.ascontiguousarray(ssp.l_ssp, dtype=np.float32)]
+        la, lz, lm, ls = self._keep
+        g = dsps_grid(len(la), len(lz), len(lm), la.ctypes.data_as(C.POINTER(C.c_double)),
+                      lz.ctypes.data_as(C.POINTER(C.c_double)), lm.ctypes.data_as(C.POINTER(C.c_double)),
+                      ls.ctypes.data_as(C.POINTER(C.c_float)), float(ssp.t0), float(ssp.t1), int(ssp.n_t))
+        o = dsps_default_opts()
+        o.om0, o.w0, o.h, o.z_max = om0, w0, h, z_max
+        o.sfh_model, o.mdf_kernel, o.device = sfh_model, mdf_kernel, device
+        if max_chunk is not None:
+            o.max_chunk = max_chunk
+        if hbm_budget_bytes is not None:
+            o.hbm_budget_bytes = hbm_budget_bytes
+        if n_streams is not None:
+            o.n_streams = n_streams
+        self.device = device
+        self.n_age, self.n_z = len(la), len(lz)
+        self.handle = dsps_create(g, o)
+        self.n_filt = {}
+
+    def close(self):
+        if self.handle:
+            dsps_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def add_filters(self, tables) -> int:
+        sid = dsps_filters_add(self.handle, tables)
+        self.n_filt[sid] = len(tables)
+        return sid
+
+    def weights(self, params, stream=None):
+        import torch
+        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == DSPS_NPAR
+        params = params.contiguous()
+        G = params.shape[1]
+        out = torch.empty((G, self.n_age, self.n_z), dtype=torch.float32, device=params.device)
+        dsps_weights(self.handle, G, params.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def photometry(self, params, set_id, precision=DSPS_PREC_BF16X3, out=None, stream=None):
+        import torch
+        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == DSPS_NPAR
+        params = params.contiguous()
+        G = params.shape[1]
+        Q = self.n_filt[set_id]
+        if out is None:
+            out = torch.empty((G, Q), dtype=torch.float32, device=params.device)
+        dsps_photometry(self.handle, G, params.data_ptr(), set_id, precision, out.data_ptr(),
+                        _stream_handle(stream))
+        return out
+
+    def photometry_vjp(self, params, set_id, mag_bar, precision=DSPS_PREC_BF16X3, want_mags=True, stream=None):
+        import torch
+        params = params.contiguous()
+        mag_bar = mag_bar.contiguous().to(torch.float32)
+        G = params.shape[1]
+        Q = self.n_filt[set_id]
+        mags = torch.empty((G, Q), dtype=torch.float32, device=params.device) if want_mags else None
+        pbar = torch.empty((DSPS_NGRAD, G), dtype=torch.float32, device=params.device)
+        dsps_photometry_vjp(self.handle, G, params.data_ptr(), set_id, precision, mag_bar.data_ptr(),
+                            mags.data_ptr() if mags is not None else None, pbar.data_ptr(),
+                            _stream_handle(stream))
+        return mags, pbar
+
+    def device_error(self, stream=None):
+        return dsps_device_error(self.handle, _stream_handle(stream))

@@ -1,0 +1,164 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs.  Tolerances: 1e-4 mag for the FP32 contraction, 1e-3 mag for
+the split-bf16 tensor-core contraction; weights to 2e-5 relative."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_06830_gb300 import synth
+
+import _util
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PREC = {"fp32": (0, _util.TOL_FP32), "bf16x3": (1, _util.TOL_BF16X3)}
+
+
+def _ctx(kind, sfh_model, mdf_kernel=0, **kw):
+    from paper_2112_06830_gb300 import dsps
+    return dsps.Context(_util.ssp(kind), sfh_model=sfh_model, mdf_kernel=mdf_kernel, **kw)
+
+
+@pytest.fixture(scope="module")
+def small():
+    c = _ctx("small", synth.SFH_DELAYED_TAU)
+    f = synth.make_filters(6)
+    return c, c.add_filters(f), oracle.Filters(f)
+
+
+@pytest.fixture(scope="module")
+def full():
+    c = _ctx("full", synth.SFH_DPL_QUENCH)
+    f = synth.make_filters(12)
+    return c, c.add_filters(f), oracle.Filters(f)
+
+
+def _run(ctx, sid, p32, prec):
+    out = ctx.photometry(torch.from_numpy(p32).cuda(), sid, precision=prec)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def test_weights_match_oracle_small(small):
+    ctx, _, _ = small
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DELAYED_TAU, 64, 0))
+    w = ctx.weights(torch.from_numpy(p32).cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle.weights(_util.oracle_grid("small", 0), p64)
+    mass = 10.0 ** p64[10]
+    err = np.abs(w - ref)
+    assert (err <= 2e-5 * np.abs(ref) + 1e-6 * mass[:, None, None]).all(), err.max()
+    np.testing.assert_allclose(w.sum(axis=(1, 2)), mass, rtol=1e-5)
+
+
+@pytest.mark.parametrize("model,kernel", [(1, 0), (1, 1)])
+def test_weights_match_oracle_full(full, model, kernel):
+    ctx = _ctx("full", model, kernel) if kernel else full[0]
+    p32, p64 = _util.params_f32(synth.make_population(model, 37, 9))
+    w = ctx.weights(torch.from_numpy(p32).cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle.weights(_util.oracle_grid("full", model, kernel), p64)
+    mass = 10.0 ** p64[10]
+    err = np.abs(w - ref)
+    assert (err <= 2e-5 * np.abs(ref) + 1e-6 * mass[:, None, None]).all(), err.max()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_photometry_small_matches_oracle(small, prec):
+    ctx, sid, F = small
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DELAYED_TAU, 64, 0))
+    m = _run(ctx, sid, p32, PREC[prec][0])
+    ref = oracle.mags(_util.oracle_grid("small", 0), F, p64)
+    err = np.abs(m - ref)
+    print(f"small {prec}: max |dm| = {err.max():.3e}, p99 = {np.quantile(err, 0.99):.3e}")
+    assert err.max() <= PREC[prec][1]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("n", [1, 129, 300])
+def test_photometry_full_grid_ragged(full, prec, n):
+    ctx, sid, F = full
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, n, 1, start=1000))
+    m = _run(ctx, sid, p32, PREC[prec][0])
+    ref = oracle.mags(_util.oracle_grid("full", 1), F, p64)
+    err = np.abs(m - ref)
+    print(f"full n={n} {prec}: max |dm| = {err.max():.3e}, p99 = {np.quantile(err, 0.99):.3e}")
+    assert err.max() <= PREC[prec][1]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_photometry_full_size_sampled(full, prec):
+    """The 1e5-galaxy workload in the bench's launch configuration; the oracle
+    checks a sample of 48 galaxies spread over the batch (first and last
+    included)."""
+    ctx, sid, F = full
+    G = 100_000
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, G, 1))
+    m = _run(ctx, sid, p32, PREC[prec][0])
+    idx = np.unique(np.concatenate([[0, G - 1], np.random.default_rng(5).integers(0, G, 46)]))
+    ref = oracle.mags(_util.oracle_grid("full", 1), F, p64[:, idx])
+    err = np.abs(m[idx] - ref)
+    print(f"full 1e5 {prec}: sampled max |dm| = {err.max():.3e}")
+    assert err.max() <= PREC[prec][1]
+    assert np.isfinite(m).all()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_results_do_not_depend_on_the_batch(full, prec):
+    ctx, sid, _ = full
+    p32, _ = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, 700, 1, start=5000))
+    whole = _run(ctx, sid, p32, prec)
+    part = _run(ctx, sid, np.ascontiguousarray(p32[:, 300:333]), prec)
+    np.testing.assert_array_equal(whole[300:333], part)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_chunked_launches_equal_one_launch(prec):
+    ctx = _ctx("small", synth.SFH_DELAYED_TAU, max_chunk=128)
+    f = synth.make_filters(6)
+    sid = ctx.add_filters(f)
+    p32, _ = _util.params_f32(synth.make_population(synth.SFH_DELAYED_TAU, 333, 3))
+    a = _run(ctx, sid, p32, prec)
+    ctx1 = _ctx("small", synth.SFH_DELAYED_TAU)
+    sid1 = ctx1.add_filters(f)
+    b = _run(ctx1, sid1, p32, prec)
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_edge_redshifts_and_filter_counts(full, prec):
+    """z near 0 and at the top of the range (filters partly off the rest grid),
+    Av = 0, one-filter and sixteen-filter sets."""
+    ctx, _, _ = full
+    p = synth.make_population(synth.SFH_DPL_QUENCH, 6, 8)
+    p[11] = [1e-3, 0.02, 1.0, 2.9, 3.0, 6.0]
+    p[8, 0] = 0.0
+    p32, p64 = _util.params_f32(p)
+    for tables in (synth.make_filters(1), synth.make_filters(16, 3000.0, 11000.0)):
+        sid = ctx.add_filters(tables)
+        m = _run(ctx, sid, p32, PREC[prec][0])
+        ref = oracle.mags(_util.oracle_grid("full", 1), oracle.Filters(tables), p64)
+        fin = np.isfinite(ref)
+        assert (np.isfinite(m) == fin).all()
+        err = np.abs(m[fin] - ref[fin])
+        assert err.max() <= PREC[prec][1], err.max()
+
+
+def test_invalid_parameters_give_nan_and_error(small):
+    from paper_2112_06830_gb300 import dsps
+    ctx, sid, _ = small
+    assert ctx.device_error() == 0
+    p = synth.make_population(synth.SFH_DELAYED_TAU, 5, 4)
+    p[11, 1] = -0.5      # negative redshift
+    p[6, 3] = 0.0        # zero MDF width
+    p32, _ = _util.params_f32(p)
+    m = _run(ctx, sid, p32, 0)
+    assert np.isnan(m[1]).all() and np.isnan(m[3]).all()
+    assert np.isfinite(m[[0, 2, 4]]).all()
+    assert ctx.device_error() == dsps.DSPS_ERR_INVALID_ARG
+    assert ctx.device_error() == 0
+
+
+def test_empty_batch(small):
+    ctx, sid, _ = small
+    out = ctx.photometry(torch.zeros((12, 0), dtype=torch.float32, device="cuda"), sid)
+    assert out.shape == (0, 6)
