@@ -45,15 +45,19 @@ __device__ __forceinline__ float sfr_f(int model, const float *p, float t) {
     return ms * exp10f(-p[4] * terf_f(zq));
 }
 
-__device__ __forceinline__ float mdf_cdf(int kernel, float u) {
-    return kernel == DSPS_MDF_TRIWEIGHT ? terf_f(u) : gauss_cdf_f(u);
+// Triweight / Gaussian CDF in the form S(u) = C(u) for u <= 0 and C(u) - 1 for
+// u > 0, so that differences of neighbouring edges keep their relative
+// precision in both tails; P = S(u_hi) - S(u_lo) + [u_lo <= 0 < u_hi].
+__device__ __forceinline__ float mdf_s(int kernel, float u) {
+    const float a = -fabsf(u);
+    const float c = kernel == DSPS_MDF_TRIWEIGHT ? terf_f(a) : gauss_cdf_f(a);
+    return u > 0.f ? -c : c;
 }
 
-// P over [lo, hi] in standardised units; mirrored in the upper tail so that
-// small bin probabilities keep their relative precision.
 __device__ __forceinline__ float mdf_bin(int kernel, float u_lo, float u_hi) {
-    if (u_lo > 0.f) return mdf_cdf(kernel, -u_lo) - mdf_cdf(kernel, -u_hi);
-    return mdf_cdf(kernel, u_hi) - mdf_cdf(kernel, u_lo);
+    float p = mdf_s(kernel, u_hi) - mdf_s(kernel, u_lo);
+    if (u_lo <= 0.f && u_hi > 0.f) p += 1.f;
+    return p;
 }
 
 template <int MODE>
@@ -78,84 +82,101 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
     for (int r = 0; r < NPAR; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
 
     const float z = p[11], sig = p[6];
-    bool valid = isfinite(mine) || lane >= NPAR;
-    valid = __all_sync(0xffffffffu, valid);
+    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NPAR);
     valid = valid && z > 0.f && (double)z <= a.zmax && sig > 0.f && p[0] > 0.f;
 
-    // 1. cosmology (lane 0, FP64) -------------------------------------------
-    double t_obs = 0.0, magoff = 0.0;
-    if (lane == 0 && valid) {
-        double zd = z, x = zd / a.dz;
-        int i = min((int)x, a.n_lut - 2);
+    // 1. cosmology: FP64 table lookup of t_obs; Dmod in FP32 pieces summed in FP64
+    double t_obs = 0.0;
+    {
+        double x = (double)z / a.dz;
+        int i = valid ? min((int)x, a.n_lut - 2) : 0;
         double fr = x - i;
         t_obs = a.tlut[i] + fr * (a.tlut[i + 1] - a.tlut[i]);
-        double dmod = a.glut[i] + fr * (a.glut[i + 1] - a.glut[i]) + 5.0 * log10(zd);
-        magoff = -2.5 * (double)p[10] + dmod - 2.5 * log10(1.0 + zd);
     }
-    t_obs = __shfl_sync(0xffffffffu, t_obs, 0);
 
-    // 2. SFR at the time nodes ---------------------------------------------
+    // 2. SFR at the time nodes (FP32 evaluation, stored as FP64)
     for (int n = lane; n < a.n_t; n += 32)
         sfr[n] = valid ? (double)sfr_f(a.sfh_model, p, (float)(a.t0 + n * a.h)) : 0.0;
     __syncwarp();
 
-    // 3. FP64 prefix of the trapezoid sums ----------------------------------
+    // 3. FP64 prefix of the trapezoid sums (Eq. mstartot)
+    const double hh = 0.5 * a.h;
     const int cnt = (a.n_t + 31) / 32;
     const int b = min(lane * cnt, a.n_t), e = min(b + cnt, a.n_t);
     double tot = 0.0;
-    for (int j = b; j < e && j < a.n_t - 1; ++j) tot += 0.5 * a.h * (sfr[j] + sfr[j + 1]);
+    for (int j = b; j < e && j < a.n_t - 1; ++j) tot += sfr[j] + sfr[j + 1];
     double incl = tot;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         double o = __shfl_up_sync(0xffffffffu, incl, off);
         if (lane >= off) incl += o;
     }
-    double run = incl - tot;
+    double run = incl - tot;   // in units of h/2
     for (int j = b; j < e; ++j) {
-        cum[j] = run;
-        if (j < a.n_t - 1) run += 0.5 * a.h * (sfr[j] + sfr[j + 1]);
+        cum[j] = run * hh;
+        if (j < a.n_t - 1) run += sfr[j] + sfr[j + 1];
     }
     __syncwarp();
 
-    // 4. mass at the age-bin edges, FP64 ------------------------------------
+    // 4. mass formed before t_obs - e for every age-bin edge, FP64
+    const double hinv2 = 0.5 * a.inv_h;
     for (int ei = lane; ei <= a.n_age; ei += 32) {
-        double tau = t_obs - a.edges[ei];
+        const double tau = t_obs - a.edges[ei];
         double M = 0.0;
         if (tau > a.t0) {
-            int m = (int)((tau - a.t0) * a.inv_h);
-            m = min(m, a.n_t - 2);
-            double u = tau - (a.t0 + m * a.h);
-            M = cum[m] + sfr[m] * u + (sfr[m + 1] - sfr[m]) * u * u * (0.5 * a.inv_h);
+            const double x = (tau - a.t0) * a.inv_h;
+            const int m = min((int)x, a.n_t - 2);
+            const double u = (x - m) * a.h;
+            M = cum[m] + u * (sfr[m] + (sfr[m + 1] - sfr[m]) * u * hinv2);
         }
         phi[ei] = M;
     }
     __syncwarp();
     const double Mtot = phi[0];
     valid = valid && Mtot > 0.0 && isfinite(Mtot);
-    for (int i = lane; i < a.n_age; i += 32) frac[i] = valid ? (float)((phi[i] - phi[i + 1]) / Mtot) : 0.f;
+    const float inv_mtot = valid ? 1.f / (float)Mtot : 0.f;
+    // bin masses: FP64 differences of the prefix, then FP32
+    for (int i = lane; i < a.n_age; i += 32) frac[i] = (float)(phi[i] - phi[i + 1]) * inv_mtot;
     __syncwarp();
 
-    // 5-6. metallicity weights and output ------------------------------------
+    // 5-6. metallicity weights and output, two consecutive k per lane
+    const float inv_sig = 1.f / sig;
     const float mass = exp10f(p[10]);
-    for (int k = lane; k < (MODE == W_MSUN ? a.K : a.K_pad); k += 32) {
-        float om = 0.f;
-        if (k < a.K && valid) {
-            int i = k / a.n_z, j = k - i * a.n_z;
-            float mu_i = fmaf(p[7], a.logage[i] - 9.f, p[5]);
-            float u_lo = (a.zedge[j] - mu_i) / sig, u_hi = (a.zedge[j + 1] - mu_i) / sig;
-            om = frac[i] * mdf_bin(a.mdf_kernel, u_lo, u_hi);
+    const int kend = MODE == W_MSUN ? a.K : a.K_pad;
+    const int nz = a.n_z;
+    const int di = 64 / nz, dj = 64 % nz;
+    int k = 2 * lane;
+    int i0 = k / nz, j0 = k - i0 * nz;
+    for (; k < kend; k += 64) {
+        float om[2];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            int i = i0, j = j0 + h2;
+            if (j >= nz) { j -= nz; ++i; }
+            om[h2] = 0.f;
+            if (k + h2 < a.K && valid) {
+                const float mu_i = fmaf(p[7], __ldg(a.logage + i) - 9.f, p[5]);
+                const float u_lo = (__ldg(a.zedge + j) - mu_i) * inv_sig;
+                const float u_hi = (__ldg(a.zedge + j + 1) - mu_i) * inv_sig;
+                om[h2] = frac[i] * mdf_bin(a.mdf_kernel, u_lo, u_hi);
+            }
         }
         if (MODE == W_MSUN) {
-            a.w_msun[gi * a.K + k] = mass * om;
+            if (k < a.K) a.w_msun[gi * a.K + k] = mass * om[0];
+            if (k + 1 < a.K) a.w_msun[gi * a.K + k + 1] = mass * om[1];
         } else if (MODE == W_OMEGA_F32) {
-            a.w32[gi * a.K_pad + k] = om;
+            *reinterpret_cast<float2 *>(a.w32 + gi * a.K_pad + k) = make_float2(om[0], om[1]);
         } else {
-            float ws = om * a.wmul[k];
-            __nv_bfloat16 hi = __float2bfloat16_rn(ws);
-            __nv_bfloat16 lo = __float2bfloat16_rn(ws - __bfloat162float(hi));
-            a.whi[gi * a.K_pad + k] = hi;
-            a.wlo[gi * a.K_pad + k] = lo;
+            const float2 wm = __ldg(reinterpret_cast<const float2 *>(a.wmul + k));
+            const float w0 = om[0] * wm.x, w1 = om[1] * wm.y;
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(w0, w1);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(w0 - __low2float(hi), w1 - __high2float(hi));
+            *reinterpret_cast<__nv_bfloat162 *>(a.whi + gi * a.K_pad + k) = hi;
+            *reinterpret_cast<__nv_bfloat162 *>(a.wlo + gi * a.K_pad + k) = lo;
         }
+        i0 += di;
+        j0 += dj;
+        if (j0 >= nz) { j0 -= nz; ++i0; }
     }
 
     if (lane == 0) {
@@ -164,13 +185,21 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
             float *ax = a.aux + gi * AUX_STRIDE;
             ax[0] = -0.4f * 3.32192809488736235f * p[8];
             ax[1] = p[9] - 0.7f;
-            ax[2] = valid ? (float)(log1p((double)z) / a.dlnlam) : 0.f;
+            ax[2] = valid ? (float)(log1pf(z) / (float)a.dlnlam) : 0.f;
             ax[3] = valid ? 1.f : 0.f;
             ax[4] = p[8];
             ax[5] = p[9];
             ax[6] = 0.f;
             ax[7] = 0.f;
-            a.magoff[gi] = valid ? magoff : __longlong_as_double(0x7ff8000000000000LL);
+            double magoff = __longlong_as_double(0x7ff8000000000000LL);
+            if (valid) {
+                double x = (double)z / a.dz;
+                int i = min((int)x, a.n_lut - 2);
+                double fr = x - i;
+                double gz = a.glut[i] + fr * (a.glut[i + 1] - a.glut[i]);
+                magoff = -2.5 * (double)p[10] + gz + (double)(5.f * log10f(z)) - (double)(2.5f * log10f(1.f + z));
+            }
+            a.magoff[gi] = magoff;
         }
     }
 }
