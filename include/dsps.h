@@ -167,6 +167,25 @@ int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32
                         int32_t precision, const float *mag_bar, float *mags,
                         float *param_bar, dsps_stream_t stream);
 
+/* FP32 photometry that allocates no device memory, for callers that cannot
+ * call cudaMalloc at the time they need magnitudes (for example a worker of a
+ * framework whose device memory belongs to its own pooling allocator, or a
+ * latency-critical loop in which an allocation must not happen).  The paper has
+ * no counterpart: this is a deployment variant of dsps_photometry with
+ * precision DSPS_PREC_FP32 and gives the same magnitudes.
+ * The context (made earlier) supplies the resident SSP block and tables; the
+ * per-call scratch is a fixed 64 MiB device array inside the library that every
+ * GPU loading the library holds until exit.  n_gal is limited to what fits that
+ * array for the context's grid (about 7,000 galaxies for a 107 x 22 age x Z
+ * grid); larger populations are rejected with DSPS_ERR_INVALID_ARG and a
+ * message giving the limit.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array: calls whose
+ * executions overlap on the GPU race with one another.
+ * params: device float32 [12][n_gal]; mags: device float32 [n_gal][n_filt]. */
+int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
+                                float *mags, dsps_stream_t stream);
+
 /* Request loop (continuous batching).  A request carries a population of
  * galaxies in HOST memory (params float32 [12][n_gal], outputs float32) and is
  * admitted when its device footprint fits the HBM budget; requests admitted

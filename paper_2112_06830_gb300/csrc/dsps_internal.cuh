@@ -129,11 +129,20 @@ struct ProfScope {
 // ----------------------------------------------------------------------------
 enum WeightsMode { W_MSUN = 0, W_OMEGA_F32 = 1, W_OMEGA_BF16X2 = 2 };
 
+// Scratch of the FP32 form supplied by the caller of a launch instead of the
+// context's work space (nullptr: use the context's).
+struct Scratch {
+    float *w32;       // [rows][K_pad]
+    float *aux;       // [rows][AUX_STRIDE]
+    double *magoff;   // [rows]
+};
+
 cudaError_t launch_weights(const Ctx &c, int mode, const float *params, int64_t G_stride,
-                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s);
+                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s,
+                           const Scratch *ws = nullptr);
 
 cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags,
-                             cudaStream_t s);
+                             cudaStream_t s, const Scratch *ws = nullptr);
 
 cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, float *mags,
                            cudaStream_t s);

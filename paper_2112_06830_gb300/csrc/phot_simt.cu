@@ -154,7 +154,8 @@ ColConst make_col_const(const Ctx &c) {
     return cc;
 }
 
-cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags, cudaStream_t s) {
+cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags, cudaStream_t s,
+                             const Scratch *ws) {
     if (n <= 0) return cudaSuccess;
     SArgs a{};
     a.W = c.d_w32;
@@ -170,6 +171,11 @@ cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float
     a.offq = fs.d_offq;
     a.cc = make_col_const(c);
     a.mags = mags;
+    if (ws) {
+        a.W = ws->w32;
+        a.aux = ws->aux;
+        a.magoff = ws->magoff;
+    }
     switch (fs.Q4) {
     case 1: return launch_q4<1>(a, n, s);
     case 2: return launch_q4<2>(a, n, s);

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
 }
 
 cudaError_t launch_weights(const Ctx &c, int mode, const float *params, int64_t G_stride,
-                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s) {
+                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, const Scratch *ws) {
     if (n <= 0) return cudaSuccess;
     WArgs a{};
     a.params = params;
@@ -239,6 +239,11 @@ cudaError_t launch_weights(const Ctx &c, int mode, const float *params, int64_t 
     a.aux = c.d_aux;
     a.magoff = c.d_magoff;
     a.err = c.d_err;
+    if (ws) {
+        a.w32 = ws->w32;
+        a.aux = ws->aux;
+        a.magoff = ws->magoff;
+    }
     const int threads = 256, warps = threads / 32;
     size_t per_warp = ((size_t)c.n_t * 16 + (size_t)(c.n_age + 1) * 8 + (size_t)c.n_age * 4 + 15) & ~(size_t)15;
     size_t smem = per_warp * warps;

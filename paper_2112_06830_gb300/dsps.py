@@ -83,6 +83,8 @@ _SIGS = [
                                   C.c_void_p]),
     ("dsps_photometry_vjp", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("dsps_photometry_fp32_static", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
+                                              C.c_void_p]),
     ("dsps_submit", C.c_int, [C.c_void_p, C.POINTER(dsps_request), C.POINTER(C.c_uint64)]),
     ("dsps_poll", C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(C.c_double)]),
     ("dsps_device_error", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -178,6 +180,12 @@ def dsps_photometry_vjp(ctx, n_gal, params_ptr, set_id, precision, mag_bar_ptr, 
                         stream=0):
     return _check(load().dsps_photometry_vjp(ctx, n_gal, params_ptr, set_id, precision, mag_bar_ptr,
                                              mags_ptr, param_bar_ptr, stream), "dsps_photometry_vjp")
+
+
+def dsps_photometry_fp32_static(ctx, n_gal, params_ptr, set_id, mags_ptr, stream=0):
+    """FP32 photometry with no device allocation (fixed in-library scratch)."""
+    return _check(load().dsps_photometry_fp32_static(ctx, n_gal, params_ptr, set_id, mags_ptr, stream),
+                  "dsps_photometry_fp32_static")
 
 
 def dsps_submit(ctx, req: dsps_request):
