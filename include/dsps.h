@@ -120,10 +120,14 @@ typedef struct {
     int64_t hbm_budget_bytes;  /* admission budget of the request loop          */
     int32_t n_streams;         /* streams of the request loop                    */
     double z_max;              /* largest accepted redshift (cosmology table)    */
+    int32_t band_skip;         /* 1: the tensor-core path skips wavelength tiles
+                                  outside every redshifted filter of a tile's
+                                  galaxies (exact: their transmission is zero);
+                                  0: dense contraction over all wavelengths     */
 } dsps_opts;
 
 /* Fills *o with the defaults above (device 0, max_chunk 262144,
- * hbm_budget 8 GiB, 4 streams, z_max 10). */
+ * hbm_budget 8 GiB, 4 streams, z_max 10, band_skip 1). */
 void dsps_default_opts(dsps_opts *o);
 
 /* Creates a context on o->device: uploads the SSP block (FP32 copy, and the
@@ -224,12 +228,14 @@ int dsps_device_error(dsps_ctx *ctx, dsps_stream_t stream);
 /* Kernel timing (tracing).  When enabled, every compute call records CUDA
  * events on the caller's stream around each kernel it launches; read() waits
  * for them and returns, per kernel kind, the number of launches and the summed
- * device time since the last read (then resets).  Kinds: 0 weights,
- * 1 FP32 photometry, 2 tensor-core photometry, 3 adjoint kernels. */
+ * device time since the last read (then resets).  Kinds: 0 weights, redshift
+ * sort and partial-sum combination, 1 FP32 photometry, 2 tensor-core
+ * photometry, 3 adjoint kernels. */
 #define DSPS_PROF_KINDS 4
 typedef struct {
     int64_t launches[DSPS_PROF_KINDS];
     double ms[DSPS_PROF_KINDS];
+    int64_t tc_tiles;          /* 128 x 256 x K_pad tensor-core tiles executed */
 } dsps_profile_t;
 int dsps_profile_enable(dsps_ctx *ctx, int32_t enable);
 int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out);

@@ -133,8 +133,9 @@ void free_ctx(Ctx *c) {
         cudaFree(fs.d_tab);
         cudaFree(fs.d_offq);
     }
-    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_edges, c->d_zedge,
-                    c->d_tlut, c->d_glut, c->d_w32, c->d_whi, c->d_wlo, c->d_aux, c->d_magoff, c->d_err};
+    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_edges, c->d_einh, c->d_bwidth, c->d_zedge,
+                    c->d_tlut, c->d_glut, c->d_w32, c->d_whi, c->d_wlo, c->d_aux, c->d_magoff, c->d_err,
+                    c->d_perm, c->d_gidx, c->d_hist, c->d_partial, c->d_stats};
     for (void *p : ptrs) cudaFree(p);
     for (auto &r : c->prof_recs) {
         cudaEventDestroy(r.a);
@@ -174,6 +175,7 @@ void dsps_default_opts(dsps_opts *o) {
     o->hbm_budget_bytes = (int64_t)8 << 30;
     o->n_streams = 4;
     o->z_max = 10.0;
+    o->band_skip = 1;
 }
 
 const char *dsps_last_error_message(void) { return g_last_error.c_str(); }
@@ -243,6 +245,8 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_wmul, (size_t)c->K_pad));
     chk(dmalloc(&c->d_logage, (size_t)c->n_age));
     chk(dmalloc(&c->d_edges, (size_t)c->n_age + 1));
+    chk(dmalloc(&c->d_einh, (size_t)c->n_age + 1));
+    chk(dmalloc(&c->d_bwidth, (size_t)c->n_age));
     chk(dmalloc(&c->d_zedge, (size_t)c->n_z + 1));
     chk(dmalloc(&c->d_w32, (size_t)c->chunk * c->K_pad));
     chk(dmalloc(&c->d_whi, (size_t)c->chunk * c->K_pad));
@@ -250,6 +254,11 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_aux, (size_t)c->chunk * AUX_STRIDE));
     chk(dmalloc(&c->d_magoff, (size_t)c->chunk));
     chk(dmalloc(&c->d_err, 1));
+    chk(dmalloc(&c->d_perm, (size_t)c->chunk));
+    chk(dmalloc(&c->d_gidx, (size_t)c->chunk));
+    chk(dmalloc(&c->d_hist, (size_t)ZSORT_BUCKETS));
+    chk(dmalloc(&c->d_partial, (size_t)TC_PARTS * c->chunk * QSTRIDE_MAX));
+    chk(dmalloc(&c->d_stats, 1));
     if (rc != DSPS_OK) { free_ctx(c); return rc; }
 
     // Age-bin edges [Gyr]: log-midpoints, first edge at age 0, last half a step
@@ -259,6 +268,10 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     for (int i = 1; i < c->n_age; ++i) edges[i] = std::pow(10.0, 0.5 * (g->log_age_yr[i - 1] + g->log_age_yr[i]) - 9.0);
     edges[c->n_age] = std::pow(10.0, g->log_age_yr[c->n_age - 1] +
                                         0.5 * (g->log_age_yr[c->n_age - 1] - g->log_age_yr[c->n_age - 2]) - 9.0);
+    const double hstep = (c->t1 - c->t0) / (c->n_t - 1);
+    std::vector<float> einh(c->n_age + 1), bwidth(c->n_age);
+    for (int i = 0; i <= c->n_age; ++i) einh[i] = (float)(edges[i] / hstep);
+    for (int i = 0; i < c->n_age; ++i) bwidth[i] = (float)(edges[i + 1] - edges[i]);
     std::vector<float> logage(c->n_age);
     for (int i = 0; i < c->n_age; ++i) logage[i] = (float)g->log_age_yr[i];
     // lgZ bin edges: midpoints, outer edges at -/+ infinity (Sec. 3.2).
@@ -277,11 +290,14 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     cudaError_t e = cudaSuccess;
     auto up = [&](void *d, const void *h, size_t b) { if (e == cudaSuccess) e = cudaMemcpy(d, h, b, cudaMemcpyHostToDevice); };
     up(c->d_edges, edges.data(), edges.size() * sizeof(double));
+    up(c->d_einh, einh.data(), einh.size() * sizeof(float));
+    up(c->d_bwidth, bwidth.data(), bwidth.size() * sizeof(float));
     up(c->d_logage, logage.data(), logage.size() * sizeof(float));
     up(c->d_zedge, zedge.data(), zedge.size() * sizeof(float));
     up(c->d_tlut, tl.data(), tl.size() * sizeof(double));
     up(c->d_glut, gl.data(), gl.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = prepare_ssp_device(*c, g->l_ssp);
     if (e != cudaSuccess) {
         int r = cuda_fail(e, "dsps_create upload");
@@ -330,10 +346,18 @@ int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const 
     int M = lmax > l0 ? (int)std::ceil(std::log(lmax / l0) / c->dlnlam) + 2 : 1;
     fs.m_rows = M + 2;
     std::vector<float> tab((size_t)fs.m_rows * 4 * fs.Q4, 0.f);
+    fs.m_nz_lo = fs.m_rows;
+    fs.m_nz_hi = -1;
     for (int m = 0; m < M; ++m) {
         double x = l0 * std::exp(m * c->dlnlam);
-        for (int q = 0; q < n_filt; ++q)
-            tab[(size_t)m * 4 * fs.Q4 + q] = (float)filter_interp(lam[q], trans[q], n_pts[q], x);
+        for (int q = 0; q < n_filt; ++q) {
+            float v = (float)filter_interp(lam[q], trans[q], n_pts[q], x);
+            tab[(size_t)m * 4 * fs.Q4 + q] = v;
+            if (v != 0.f) {
+                fs.m_nz_lo = std::min(fs.m_nz_lo, m);
+                fs.m_nz_hi = std::max(fs.m_nz_hi, m);
+            }
+        }
     }
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
@@ -436,6 +460,11 @@ int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out) {
         c->ev_pool.push_back(r.b);
     }
     c->prof_recs.clear();
+    unsigned long long tiles = 0;
+    if (cudaMemcpy(&tiles, c->d_stats, sizeof tiles, cudaMemcpyDeviceToHost) == cudaSuccess) {
+        out->tc_tiles = (int64_t)tiles;
+        cudaMemset(c->d_stats, 0, sizeof tiles);
+    }
     return rc;
 }
 

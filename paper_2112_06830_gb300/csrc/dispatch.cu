@@ -28,16 +28,32 @@ int run_photometry(Ctx *c, int64_t n_gal, const float *params, int32_t set_id, i
     const FilterSet &fs = c->sets[set_id];
     for (int64_t g0 = 0; g0 < n_gal; g0 += c->chunk) {
         const int64_t n = n_gal - g0 < c->chunk ? n_gal - g0 : c->chunk;
-        cudaError_t e;
-        {
-            ProfScope ps(*c, 0, s);
-            e = launch_weights(*c, precision == DSPS_PREC_FP32 ? W_OMEGA_F32 : W_OMEGA_BF16X2, params, n_gal, g0,
-                               n, nullptr, s);
-        }
-        if (e == cudaSuccess) {
-            ProfScope ps(*c, precision == DSPS_PREC_FP32 ? 1 : 2, s);
-            e = precision == DSPS_PREC_FP32 ? launch_phot_simt(*c, fs, n, mags + g0 * fs.Q, s)
-                                            : launch_phot_tc(*c, fs, n, mags + g0 * fs.Q, s);
+        cudaError_t e = cudaSuccess;
+        if (precision == DSPS_PREC_FP32) {
+            {
+                ProfScope ps(*c, 0, s);
+                e = launch_weights(*c, W_OMEGA_F32, params, n_gal, g0, n, nullptr, s);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 1, s);
+                e = launch_phot_simt(*c, fs, n, mags + g0 * fs.Q, s);
+            }
+        } else {
+            int parts = 0;
+            {
+                ProfScope ps(*c, 0, s);
+                e = launch_zsort(*c, params + (int64_t)11 * n_gal + g0, n, s);
+                if (e == cudaSuccess) e = launch_weights(*c, W_OMEGA_BF16X2, params, n_gal, g0, n, nullptr, s,
+                                                         nullptr, true);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 2, s);
+                e = launch_phot_tc(*c, fs, n, &parts, s);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 0, s);
+                e = launch_combine(*c, fs, n, parts, mags + g0 * fs.Q, s);
+            }
         }
         if (e != cudaSuccess) {
             set_last_error(cudaGetErrorString(e));

@@ -21,6 +21,9 @@ constexpr int N_ALIGN = 256;     // wavelength padding: multiple of the 256-wide
 constexpr int MAX_NT = 1024;     // SFR time nodes
 constexpr int MAX_NAGE = 512;
 constexpr int AUX_STRIDE = 8;    // floats of per-galaxy epilogue constants
+constexpr int ZSORT_BUCKETS = 4096;  // redshift-sort buckets (multiple of 1024)
+constexpr int TC_PARTS = 4;      // work units per 128-galaxy tile in the tensor-core kernel
+constexpr int QSTRIDE_MAX = 16;  // floats per row of the partial filter sums
 
 // Device error word bits.
 constexpr unsigned DERR_PARAM = 1u;    // out-of-range galaxy parameters
@@ -41,6 +44,7 @@ constexpr double SIG_Q = 0.3;           // quench transition width [Gyr]
 struct FilterSet {
     int Q = 0, Q4 = 0;         // filters; float4 groups per table row
     int m_rows = 0;            // table rows; row m_rows-1 is all zero
+    int m_nz_lo = 0, m_nz_hi = -1;  // first / last table row where some filter is non-zero
     float *d_tab = nullptr;    // [m_rows][4*Q4] T_q(lam0 exp(m dlnlam))
     double *d_offq = nullptr;  // [Q] 2.5 log10(AB0 D_q)
 };
@@ -64,6 +68,8 @@ struct Ctx {
     // Grids and tables.
     float *d_logage = nullptr;              // [n_age] log10(age/yr)
     double *d_edges = nullptr;              // [n_age+1] age-bin edges [Gyr]
+    float *d_einh = nullptr;                // [n_age+1] edge / time step
+    float *d_bwidth = nullptr;              // [n_age] bin widths [Gyr]
     float *d_zedge = nullptr;               // [n_z+1] lgZ bin edges (+-1e30 outer)
     double *d_tlut = nullptr;               // [n_lut] t_obs(z) [Gyr]
     double *d_glut = nullptr;               // [n_lut] Dmod(z) - 5 log10 z
@@ -77,6 +83,11 @@ struct Ctx {
     __nv_bfloat16 *d_wlo = nullptr;         // [chunk][K_pad]
     float *d_aux = nullptr;                 // [chunk][AUX_STRIDE]
     double *d_magoff = nullptr;             // [chunk]
+    int *d_perm = nullptr;                  // [chunk] sorted row -> galaxy (chunk-local)
+    int *d_gidx = nullptr;                  // [chunk] sorted row -> galaxy, written by the weights kernel
+    int *d_hist = nullptr;                  // [ZSORT_BUCKETS]
+    float *d_partial = nullptr;             // [TC_PARTS][chunk][QSTRIDE_MAX] partial filter sums
+    unsigned long long *d_stats = nullptr;  // [1] tensor-core tiles executed (profiling)
     unsigned *d_err = nullptr;              // sticky error word
 
     std::vector<FilterSet> sets;
@@ -139,13 +150,20 @@ struct Scratch {
 
 cudaError_t launch_weights(const Ctx &c, int mode, const float *params, int64_t G_stride,
                            int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s,
-                           const Scratch *ws = nullptr);
+                           const Scratch *ws = nullptr, bool sorted = false);
+
+// Counting sort of the chunk's galaxies by redshift shift into ctx.d_perm.
+cudaError_t launch_zsort(const Ctx &c, const float *z, int64_t n, cudaStream_t s);
+float zsort_key_scale(const Ctx &c);
+// Sums the tensor-core kernel's per-part filter sums and writes magnitudes.
+cudaError_t launch_combine(const Ctx &c, const FilterSet &fs, int64_t n, int parts, float *mags, cudaStream_t s);
 
 cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags,
                              cudaStream_t s, const Scratch *ws = nullptr);
 
-cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, float *mags,
-                           cudaStream_t s);
+// Writes per-part filter sums to ctx.d_partial (sorted rows); returns the
+// number of parts through *parts.
+cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *parts, cudaStream_t s);
 
 cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp);
 
@@ -154,16 +172,21 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp);
 // ----------------------------------------------------------------------------
 #ifdef __CUDACC__
 
-// Appendix B, Eq. (terf): triweight CDF in the standardised variable, saturated
-// to 0 / 1 outside [-3, 3].
+// Appendix B, Eq. (terf) for z <= 0, written in x = z + 3: the same polynomial
+// equals (35/69984) x^4 (54 - 21.6 x + 3 x^2 - x^3/7), which keeps its relative
+// precision in FP32 down to the far lower tail (the printed monomial form
+// cancels there).  Zero below z = -3.
+__device__ __forceinline__ float terf_lower_f(float z) {
+    const float x = z + 3.f;
+    if (x <= 0.f) return 0.f;
+    const float x2 = x * x;
+    const float poly = fmaf(x, fmaf(x, fmaf(x, -1.f / 7.f, 3.f), -21.6f), 54.f);
+    return (35.f / 69984.f) * x2 * x2 * poly;
+}
+
+// Triweight CDF, saturated to 0 / 1 outside [-3, 3]; upper half by symmetry.
 __device__ __forceinline__ float terf_f(float z) {
-    if (z <= -3.f) return 0.f;
-    if (z >= 3.f) return 1.f;
-    float z2 = z * z;
-    float p = fmaf(z2, -5.f / 69984.f, 7.f / 2592.f);
-    p = fmaf(z2, p, -35.f / 864.f);
-    p = fmaf(z2, p, 35.f / 96.f);
-    return fmaf(z, p, 0.5f);
+    return z <= 0.f ? terf_lower_f(z) : 1.f - terf_lower_f(-z);
 }
 
 // Appendix B, Eq. (triweight): density in the standardised variable.

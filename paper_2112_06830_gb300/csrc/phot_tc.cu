@@ -22,6 +22,8 @@
 // DERR_TIMEOUT, lets its in-flight copies and MMAs land, frees TMEM and returns.
 #include <cudaTypedefs.h>
 
+#include <cmath>
+
 #include "dsps_internal.cuh"
 #include "epilogue.cuh"
 
@@ -50,13 +52,13 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >
 
 struct TArgs {
     const float *aux;
-    const double *magoff;
     const float4 *tab;
-    const double *offq;
     ColConst cc;
-    int Q, m_last, n_mtiles, n_ntiles, kblocks;
+    int m_last, n_mtiles, n_ntiles, kblocks, parts, n_units;
+    int band_skip, m_nz_lo, m_nz_hi, i0_margin;
     int64_t n;
-    float *mags;
+    float *partial;                 // [parts][n][4*Q4]
+    unsigned long long *tiles;      // tiles executed (profiling)
     unsigned *err;
 };
 
@@ -157,6 +159,34 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "memory");
 }
 
+// Wavelength tiles [nt0, nt1) that galaxy tile mt needs: rows are sorted by
+// the redshift shift s, so the tile's shifts lie in [s(first row), s(last row)]
+// up to one sort bucket; a wavelength tile whose filter-table rows n + i0 and
+// n + i0 + 1 all fall outside the band [m_nz_lo, m_nz_hi] of non-zero
+// transmission contributes exactly zero and is skipped.
+__device__ __forceinline__ void tile_nrange(const TArgs &a, int mt, int &nt0, int &nt1) {
+    nt0 = 0;
+    nt1 = a.n_ntiles;
+    if (!a.band_skip) return;
+    const int64_t r0 = (int64_t)mt * BM;
+    const int64_t r1 = min(r0 + BM, a.n) - 1;
+    const int i0_lo = max((int)floorf(a.aux[r0 * AUX_STRIDE + 2]) - a.i0_margin, 0);
+    const int i0_hi = (int)floorf(a.aux[r1 * AUX_STRIDE + 2]) + a.i0_margin;
+    const int n_lo = a.m_nz_lo - i0_hi - 1;
+    const int n_hi = a.m_nz_hi - i0_lo;
+    if (n_hi < 0 || a.m_nz_hi < a.m_nz_lo) { nt1 = nt0; return; }
+    nt0 = n_lo <= 0 ? 0 : n_lo / BN;
+    nt1 = min(a.n_ntiles, n_hi / BN + 1);
+    if (nt1 < nt0) nt1 = nt0;
+}
+
+// Wavelength tile nt belongs to part nt mod parts, whatever the tile's range:
+// every galaxy's partial sums then add the same non-zero terms in the same
+// order in any batch (skipped tiles would only have added exact zeros).
+__device__ __forceinline__ int first_tile(int nt0, int part, int parts) {
+    return nt0 + ((part - nt0 % parts) % parts + parts) % parts;
+}
+
 template <int Q4>
 __global__ void __launch_bounds__(THREADS, 1)
 phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
@@ -212,8 +242,11 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
             int armed[STAGES];
             for (int s = 0; s < STAGES; ++s) armed[s] = -1;
             bool ok = true;
-            for (int mt = blockIdx.x; ok && mt < a.n_mtiles; mt += gridDim.x)
-                for (int nt = 0; ok && nt < a.n_ntiles; ++nt)
+            for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+                const int mt = u / a.parts, part = u - mt * a.parts;
+                int nt0, nt1;
+                tile_nrange(a, mt, nt0, nt1);
+                for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts)
                     for (int kb = 0; kb < a.kblocks; ++kb) {
                         if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                         const uint32_t fb = full0 + 8 * stage;
@@ -226,6 +259,7 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                         armed[stage] = (int)phase;
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
+            }
             // Let every armed copy land before the CTA can exit.
             for (int s = 0; s < STAGES; ++s)
                 if (armed[s] >= 0) {
@@ -239,9 +273,13 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
         if (lane == 0) {
             int stage = 0, as = 0;
             uint32_t phase = 0, aphase = 0;
+            unsigned long long ntiles = 0;
             bool ok = true;
-            for (int mt = blockIdx.x; ok && mt < a.n_mtiles; mt += gridDim.x)
-                for (int nt = 0; ok && nt < a.n_ntiles; ++nt) {
+            for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+                const int mt = u / a.parts, part = u - mt * a.parts;
+                int nt0, nt1;
+                tile_nrange(a, mt, nt0, nt1);
+                for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
                     if (!mbar_wait(acce0 + 8 * as, aphase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d = tmem_base + (uint32_t)(as * BN);
@@ -264,13 +302,16 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                     }
                     if (!ok) break;
                     mma_commit(accf0 + 8 * as);
+                    ++ntiles;
                     if (++as == 2) { as = 0; aphase ^= 1u; }
                 }
+            }
             // Every MMA issued so far completes before this commit arrives.
             mma_commit(drain);
             const long long t0 = clock64();
             while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
             }
+            if (a.tiles) atomicAdd(a.tiles, ntiles);
         }
     } else {
         // ---------------------------------------------------------------- epilogue
@@ -281,13 +322,16 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
         int as = 0;
         uint32_t aphase = 0, ephase = 0;
         bool ok = true;
-        for (int mt = blockIdx.x; ok && mt < a.n_mtiles; mt += gridDim.x) {
+        for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+            const int mt = u / a.parts, part = u - mt * a.parts;
+            int nt0, nt1;
+            tile_nrange(a, mt, nt0, nt1);
             const int64_t rowg = (int64_t)mt * BM + row;
             const RowConst rc = load_row_const(a.aux, rowg, a.n);
             float acc[4 * Q4];
 #pragma unroll
             for (int q = 0; q < 4 * Q4; ++q) acc[q] = 0.f;
-            for (int nt = 0; nt < a.n_ntiles; ++nt) {
+            for (int nt = first_tile(nt0, part, a.parts); nt < nt1; nt += a.parts) {
                 int got = 1;
                 if (lane == 0) got = mbar_wait(accf0 + 8 * as, aphase, abort_flag, a.err) ? 1 : 0;
                 got = __shfl_sync(0xffffffffu, got, 0);
@@ -328,9 +372,13 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
             ephase ^= 1u;
             if (!got) break;
             if (half == 0 && rowg < a.n) {
+                float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)part * a.n + rowg) * (4 * Q4));
 #pragma unroll
-                for (int q = 0; q < 4 * Q4; ++q) acc[q] += comb[row * QMAX + q];
-                write_mags<Q4>(acc, a.Q, a.magoff[rowg], a.offq, a.mags + rowg * a.Q);
+                for (int qq = 0; qq < Q4; ++qq)
+                    dst[qq] = make_float4(acc[4 * qq + 0] + comb[row * QMAX + 4 * qq + 0],
+                                          acc[4 * qq + 1] + comb[row * QMAX + 4 * qq + 1],
+                                          acc[4 * qq + 2] + comb[row * QMAX + 4 * qq + 2],
+                                          acc[4 * qq + 3] + comb[row * QMAX + 4 * qq + 3]);
             }
             // Second bounded barrier: half 0 has read comb before half 1 rewrites it.
             __syncwarp();
@@ -393,7 +441,8 @@ cudaError_t launch_q4(const CUtensorMap &ah, const CUtensorMap &al, const CUtens
 
 }  // namespace
 
-cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, float *mags, cudaStream_t s) {
+cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *parts, cudaStream_t s) {
+    *parts = TC_PARTS;
     if (n <= 0) return cudaSuccess;
     if (fs.Q > QMAX) return cudaErrorInvalidValue;
     CUtensorMap ah, al, bh, bl;
@@ -404,19 +453,23 @@ cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, float *
         return cudaErrorInvalidValue;
     TArgs a{};
     a.aux = c.d_aux;
-    a.magoff = c.d_magoff;
     a.tab = reinterpret_cast<const float4 *>(fs.d_tab);
-    a.offq = fs.d_offq;
     a.cc = make_col_const(c);
-    a.Q = fs.Q;
     a.m_last = fs.m_rows - 1;
     a.n_mtiles = (int)((n + BM - 1) / BM);
     a.n_ntiles = c.N_pad / BN;
     a.kblocks = c.K_pad / BK;
+    a.parts = TC_PARTS;
+    a.n_units = a.n_mtiles * TC_PARTS;
+    a.band_skip = c.opts.band_skip ? 1 : 0;
+    a.m_nz_lo = fs.m_nz_lo;
+    a.m_nz_hi = fs.m_nz_hi;
+    a.i0_margin = (int)std::ceil(1.0 / zsort_key_scale(c)) + 1;
     a.n = n;
-    a.mags = mags;
+    a.partial = c.d_partial;
+    a.tiles = c.prof ? c.d_stats : nullptr;
     a.err = c.d_err;
-    int grid = a.n_mtiles < c.num_sms ? a.n_mtiles : c.num_sms;
+    int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;
     switch (fs.Q4) {
     case 1: return launch_q4<1>(ah, al, bh, bl, a, grid, s);
     case 2: return launch_q4<2>(ah, al, bh, bl, a, grid, s);

@@ -50,14 +50,15 @@ class dsps_opts(C.Structure):
     _fields_ = [("om0", C.c_double), ("w0", C.c_double), ("h", C.c_double),
                 ("sfh_model", C.c_int32), ("mdf_kernel", C.c_int32), ("device", C.c_int32),
                 ("max_chunk", C.c_int64), ("hbm_budget_bytes", C.c_int64), ("n_streams", C.c_int32),
-                ("z_max", C.c_double)]
+                ("z_max", C.c_double), ("band_skip", C.c_int32)]
 
 
 DSPS_PROF_KINDS = 4
 
 
 class dsps_profile_t(C.Structure):
-    _fields_ = [("launches", C.c_int64 * DSPS_PROF_KINDS), ("ms", C.c_double * DSPS_PROF_KINDS)]
+    _fields_ = [("launches", C.c_int64 * DSPS_PROF_KINDS), ("ms", C.c_double * DSPS_PROF_KINDS),
+                ("tc_tiles", C.c_int64)]
 
 
 class dsps_request(C.Structure):
@@ -209,10 +210,13 @@ def dsps_profile_enable(ctx, enable=True):
 
 
 def dsps_profile_read(ctx):
-    """{kind: (launches, ms)} for kinds 0 weights, 1 fp32, 2 tensor, 3 adjoint."""
+    """{kind: (launches, ms)} for kinds 0 weights/sort/combine, 1 fp32, 2 tensor, 3 adjoint, plus
+    "tc_tiles": tensor-core tiles executed."""
     p = dsps_profile_t()
     _check(load().dsps_profile_read(ctx, C.byref(p)), "dsps_profile_read")
-    return {k: (int(p.launches[k]), float(p.ms[k])) for k in range(DSPS_PROF_KINDS)}
+    out = {k: (int(p.launches[k]), float(p.ms[k])) for k in range(DSPS_PROF_KINDS)}
+    out["tc_tiles"] = int(p.tc_tiles)
+    return out
 
 
 def dsps_strerror(code):
@@ -232,7 +236,8 @@ class Context:
     """Owns a dsps context (resident SSP block, cosmology table, work space)."""
 
     def __init__(self, ssp, sfh_model=DSPS_SFH_DELAYED_TAU, mdf_kernel=DSPS_MDF_TRIWEIGHT, device=0,
-                 max_chunk=None, hbm_budget_bytes=None, n_streams=None, om0=0.3, w0=-1.0, h=0.7, z_max=10.0):
+                 max_chunk=None, hbm_budget_bytes=None, n_streams=None, om0=0.3, w0=-1.0, h=0.7, z_max=10.0,
+                 band_skip=True):
         self._keep = [np.ascontiguousarray(ssp.log_age_yr, dtype=np.float64),
                       np.ascontiguousarray(ssp.lgz, dtype=np.float64),
                       np.ascontiguousarray(ssp.lam, dtype=np.float64),
@@ -244,6 +249,7 @@ class Context:
         o = dsps_default_opts()
         o.om0, o.w0, o.h, o.z_max = om0, w0, h, z_max
         o.sfh_model, o.mdf_kernel, o.device = sfh_model, mdf_kernel, device
+        o.band_skip = 1 if band_skip else 0
         if max_chunk is not None:
             o.max_chunk = max_chunk
         if hbm_budget_bytes is not None:

@@ -170,3 +170,36 @@ def test_empty_batch(small):
     ctx, sid, _ = small
     out = ctx.photometry(torch.zeros((12, 0), dtype=torch.float32, device="cuda"), sid)
     assert out.shape == (0, 6)
+
+
+def test_band_skipping_is_exact(full):
+    """Skipping wavelength tiles outside every redshifted filter changes no bit."""
+    ctx, sid, _ = full
+    dense = _ctx("full", synth.SFH_DPL_QUENCH, band_skip=False)
+    sid_d = dense.add_filters(synth.make_filters(12))
+    p32, _ = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, 1500, 1, start=20_000))
+    np.testing.assert_array_equal(_run(ctx, sid, p32, 1), _run(dense, sid_d, p32, 1))
+
+
+def test_young_bins_keep_relative_precision(full):
+    """Quenched galaxies observed after t_q: the youngest age bins hold ~1e-8 of
+    the formed mass; the GPU must still get them to 1e-4 relative."""
+    ctx = full[0]
+    p = synth.make_population(synth.SFH_DPL_QUENCH, 24, 17)
+    p[3] = 5.0          # quench early
+    p[4] = 3.0          # by 3 dex
+    p[11] = np.linspace(0.01, 0.4, 24)
+    p32, p64 = _util.params_f32(p)
+    w = ctx.weights(torch.from_numpy(p32).cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle.weights(_util.oracle_grid("full", 1), p64)
+    mass = (10.0 ** p64[10])[:, None, None]
+    # age-bin masses (summed over metallicity): the SFH part alone
+    wa, ra = w.sum(axis=2), ref.sum(axis=2)
+    big = ra > 1e-12 * mass[:, :, 0]
+    rel = np.abs(wa - ra)[big] / ra[big]
+    assert rel.max() <= 1e-4, rel.max()
+    assert (ra[:, 0] / mass[:, 0, 0] < 1e-5).all()   # the youngest bin is tiny indeed
+    # joint weights, including the triweight tails of the MDF
+    big = ref > 1e-8 * mass
+    rel = np.abs(w - ref)[big] / ref[big]
+    assert rel.max() <= 3e-4, rel.max()
