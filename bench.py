@@ -232,6 +232,37 @@ def run_ours(a):
     ms_dense, prof_dense, _ = timed(dsps.DSPS_PREC_BF16X3, c=ctx_dense, sid_=sid_dense)
     ctx_dense.close()
 
+    # Forward + gradient: magnitudes and dLoss/dparams for a given dLoss/dmags.
+    d_mbar = torch.from_numpy(np.random.default_rng(rank).standard_normal((G, N_FILT)).astype(np.float32)).cuda()
+    d_pbar = torch.empty((dsps.DSPS_NGRAD, G), dtype=torch.float32, device="cuda")
+
+    def grad_step(prec):
+        dsps.dsps_photometry_vjp(ctx.handle, G, d_params.data_ptr(), sid, prec, d_mbar.data_ptr(), d_mags.data_ptr(),
+                                 d_pbar.data_ptr(), stream.cuda_stream)
+
+    def timed_grad(prec):
+        for _ in range(a.warmup):
+            grad_step(prec)
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(a.steps)]
+        for e0, e1 in evs:
+            flush.fill_(1)
+            e0.record(stream)
+            grad_step(prec)
+            e1.record(stream)
+        barrier()
+        ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    ms_grad_tc = timed_grad(dsps.DSPS_PREC_BF16X3)
+    ms_grad_fp32 = timed_grad(dsps.DSPS_PREC_FP32)
+    assert torch.isfinite(d_pbar).all()
+
     # End to end: pinned host params -> device, photometry, magnitudes -> host.
     h_params = torch.from_numpy(params_h).pin_memory()
     h_mags = torch.empty((G, N_FILT), dtype=torch.float32).pin_memory()
@@ -303,6 +334,9 @@ def run_ours(a):
         "kernels": {"weights_sort_combine_ms_per_step": prof_tc[0][1] / a.steps,
                     "phot_tc_ms_per_launch": roof["ms_per_launch"]},
         "roofline": roof,
+        "fwd_grad": {"value": ws * G * N_FILT / (ms_grad_tc * 1e-3), "ms_per_step": ms_grad_tc,
+                     "fp32": {"value": ws * G * N_FILT / (ms_grad_fp32 * 1e-3), "ms_per_step": ms_grad_fp32},
+                     "note": "magnitudes and d(loss)/d(11 parameters) per galaxy, split-bf16 form"},
         "dense": {"value": ws * G * N_FILT / (ms_dense * 1e-3), "ms_per_step": ms_dense,
                   "note": "band skipping off: every wavelength tile contracted", "roofline": roof_dense},
         "e2e": {"value": ws * G * N_FILT / (ms_e2e * 1e-3), "unit": METRIC,

@@ -135,7 +135,8 @@ void free_ctx(Ctx *c) {
     }
     void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_edges, c->d_einh, c->d_bwidth, c->d_zedge,
                     c->d_tlut, c->d_glut, c->d_w32, c->d_whi, c->d_wlo, c->d_aux, c->d_magoff, c->d_err,
-                    c->d_perm, c->d_gidx, c->d_hist, c->d_partial, c->d_stats};
+                    c->d_perm, c->d_gidx, c->d_hist, c->d_partial, c->d_stats, c->d_cq, c->d_shat,
+                    c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d};
     for (void *p : ptrs) cudaFree(p);
     for (auto &r : c->prof_recs) {
         cudaEventDestroy(r.a);
@@ -257,8 +258,13 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_perm, (size_t)c->chunk));
     chk(dmalloc(&c->d_gidx, (size_t)c->chunk));
     chk(dmalloc(&c->d_hist, (size_t)ZSORT_BUCKETS));
-    chk(dmalloc(&c->d_partial, (size_t)TC_PARTS * c->chunk * QSTRIDE_MAX));
+    chk(dmalloc(&c->d_partial, (size_t)TC_PARTS * c->chunk * 3 * QSTRIDE_MAX));
     chk(dmalloc(&c->d_stats, 1));
+    chk(dmalloc(&c->d_cq, (size_t)c->chunk * QSTRIDE_MAX));
+    chk(dmalloc(&c->d_L_hi, (size_t)c->K_pad * c->N_pad));
+    chk(dmalloc(&c->d_Ld32, (size_t)c->K_pad * c->N_pad));
+    chk(dmalloc(&c->d_wmul_d, (size_t)c->K_pad));
+    chk(dmalloc(&c->d_L_lo, (size_t)c->K_pad * c->N_pad));
     if (rc != DSPS_OK) { free_ctx(c); return rc; }
 
     // Age-bin edges [Gyr]: log-midpoints, first edge at age 0, last half a step
@@ -343,16 +349,19 @@ int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const 
     fs.Q = n_filt;
     fs.Q4 = (n_filt + 3) / 4;
     const double l0 = std::exp(c->lnlam0);
+    // Grid samples m = -1 .. M-1 at l0 exp(m dlnlam) in table rows t = m + 1,
+    // then three zero rows (the 4-point interpolation reads up to m + 2).
     int M = lmax > l0 ? (int)std::ceil(std::log(lmax / l0) / c->dlnlam) + 2 : 1;
-    fs.m_rows = M + 2;
+    fs.m_rows = M + 4;
     std::vector<float> tab((size_t)fs.m_rows * 4 * fs.Q4, 0.f);
     fs.m_nz_lo = fs.m_rows;
     fs.m_nz_hi = -1;
-    for (int m = 0; m < M; ++m) {
+    for (int t = 0; t <= M; ++t) {
+        const int m = t - 1;
         double x = l0 * std::exp(m * c->dlnlam);
         for (int q = 0; q < n_filt; ++q) {
             float v = (float)filter_interp(lam[q], trans[q], n_pts[q], x);
-            tab[(size_t)m * 4 * fs.Q4 + q] = v;
+            tab[(size_t)t * 4 * fs.Q4 + q] = v;
             if (v != 0.f) {
                 fs.m_nz_lo = std::min(fs.m_nz_lo, m);
                 fs.m_nz_hi = std::max(fs.m_nz_hi, m);

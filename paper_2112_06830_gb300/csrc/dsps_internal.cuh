@@ -88,6 +88,12 @@ struct Ctx {
     int *d_hist = nullptr;                  // [ZSORT_BUCKETS]
     float *d_partial = nullptr;             // [TC_PARTS][chunk][QSTRIDE_MAX] partial filter sums
     unsigned long long *d_stats = nullptr;  // [1] tensor-core tiles executed (profiling)
+    float *d_cq = nullptr;                  // [chunk][QSTRIDE_MAX] Nbar_q of the adjoint
+    void *d_shat = nullptr;                 // adjoint Shat: FP32 [chunk][N_pad] or bf16 hi, lo (lazy)
+    float *d_Ld32 = nullptr;                // [K_pad][N_pad] metallicity-differenced block (FP32 adjoint)
+    float *d_wmul_d = nullptr;              // [K_pad] 2^E'_k of the differenced rows
+    __nv_bfloat16 *d_L_hi = nullptr;        // [K_pad][N_pad] differenced block, row-scaled hi (tensor adjoint)
+    __nv_bfloat16 *d_L_lo = nullptr;        // [K_pad][N_pad] row-scaled lo
     unsigned *d_err = nullptr;              // sticky error word
 
     std::vector<FilterSet> sets;
@@ -158,14 +164,27 @@ float zsort_key_scale(const Ctx &c);
 // Sums the tensor-core kernel's per-part filter sums and writes magnitudes.
 cudaError_t launch_combine(const Ctx &c, const FilterSet &fs, int64_t n, int parts, float *mags, cudaStream_t s);
 
+// grad: instead of magnitudes, writes the sums N, A, D per filter (see
+// epilogue.cuh) to ctx.d_partial as a single part.
 cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags,
-                             cudaStream_t s, const Scratch *ws = nullptr);
+                             cudaStream_t s, const Scratch *ws = nullptr, bool grad = false);
 
 // Writes per-part filter sums to ctx.d_partial (sorted rows); returns the
 // number of parts through *parts.
-cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *parts, cudaStream_t s);
+cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *parts, cudaStream_t s,
+                           bool grad = false);
 
 cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp);
+
+// Adjoint (vjp.cu, vjp_tc.cu, weights.cu).
+cudaError_t launch_combine_grad(const Ctx &c, const FilterSet &fs, int64_t n, int parts, bool sorted,
+                                const float *mag_bar, float *mags, float *param_bar, int64_t G_stride,
+                                int64_t g_begin, cudaStream_t s);
+cudaError_t launch_shat(const Ctx &c, const FilterSet &fs, int64_t n, bool bf16, bool band, cudaStream_t s);
+cudaError_t launch_vjp_simt(const Ctx &c, int64_t n, cudaStream_t s);
+cudaError_t launch_vjp_tc(const Ctx &c, const FilterSet &fs, int64_t n, cudaStream_t s);
+cudaError_t launch_weights_vjp(const Ctx &c, const float *params, int64_t G_stride, int64_t g_begin, int64_t n,
+                               bool sorted, bool scaled, float *param_bar, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // Device helpers

@@ -8,12 +8,15 @@
 //   v_n  = S_gn F c_n / lam_n                          rest-grid trapezoid of dlam/lam
 //   N_q += v_n T_q((1+z) lam_n)                        Eq. (restmag) in the observer frame
 // The filters are tabulated on the SSP grid's ln-lambda spacing, so the
-// observer-frame position of node n is table index n + s, s = ln(1+z)/dlnlam,
-// and T_q there is (1-f) T[n+i0] + f T[n+i0+1] with i0 = floor(s), f = s - i0.
-// Regrouping the sum by table row m gives
-//   N_q = sum_m T_q[m] y_m,  y_m = (1-f) v_{m-i0} + f v_{m-i0-1},
-// which the kernels evaluate over a contiguous run of nodes [a, b) as a
-// sliding pair (v_prev) plus one closing term f v_{b-1} T[b+i0].
+// observer-frame position of node n is grid index n + s, s = ln(1+z)/dlnlam,
+// i0 = floor(s), f = s - i0, and T_q there is the 4-point Lagrange
+// interpolation  sum_{d=-1..2} w_d(f) T[n + i0 + d]  (error O(dlnlam^4)).
+// Regrouping the sum by grid index m gives
+//   N_q = sum_m T_q[m] y_m,  y_m = sum_d w_d v_{m - i0 - d},
+// which the kernels evaluate over a contiguous run of nodes [a, b) with the
+// last three v kept in registers; at node n the row m = n + i0 - 1 is complete,
+// and three closing rows b + i0 - 1, b + i0, b + i0 + 1 end the run.
+// Table row t holds grid index m = t - 1 (one leading row for m = -1).
 #pragma once
 #include <cmath>
 
@@ -22,26 +25,35 @@
 namespace dsps {
 
 struct RowConst {
-    float alpha, beta, f, omf;
+    float alpha, beta;
+    float w[4];   // Lagrange weights of grid indices i0-1, i0, i0+1, i0+2
     int i0;
     bool valid;
 };
 
 __device__ __forceinline__ RowConst load_row_const(const float *aux, int64_t row, int64_t n_rows) {
-    RowConst rc{0.f, 0.f, 0.f, 1.f, 0, false};
+    RowConst rc{0.f, 0.f, {0.f, 1.f, 0.f, 0.f}, 0, false};
     if (row < n_rows) {
         const float *ax = aux + row * AUX_STRIDE;
         rc.alpha = ax[0];
         rc.beta = ax[1];
-        float s = ax[2];
-        float fl = floorf(s);
+        const float s = ax[2];
+        const float fl = floorf(s);
         rc.i0 = (int)fl;
-        rc.f = s - fl;
-        rc.omf = 1.f - rc.f;
+        const float f = s - fl;
+        rc.w[0] = -f * (f - 1.f) * (f - 2.f) * (1.f / 6.f);
+        rc.w[1] = (f + 1.f) * (f - 1.f) * (f - 2.f) * 0.5f;
+        rc.w[2] = -(f + 1.f) * f * (f - 2.f) * 0.5f;
+        rc.w[3] = (f + 1.f) * f * (f - 1.f) * (1.f / 6.f);
         rc.valid = ax[3] != 0.f;
     }
     return rc;
 }
+
+// Sliding state of a run: the last three v (v_{n-1}, v_{n-2}, v_{n-3}).
+struct Slide {
+    float v1 = 0.f, v2 = 0.f, v3 = 0.f;
+};
 
 struct ColConst {
     float ell0, dell;          // log2(lam_n / 5500) = ell0 + n dell
@@ -69,26 +81,118 @@ __device__ __forceinline__ void acc_row(float (&acc)[4 * Q4], const float4 *__re
     }
 }
 
-// One node of the sliding sum.
+// One node of the sliding sum: completes grid row m = n + i0 - 1 (table row n + i0).
 template <int Q4>
-__device__ __forceinline__ void epi_node(float (&acc)[4 * Q4], float &vprev, float S, int n,
-                                         const RowConst &rc, const ColConst &cc,
-                                         const float4 *__restrict__ tab, int m_last) {
-    float ell = fmaf((float)n, cc.dell, cc.ell0);
-    float u = exp2f(rc.beta * ell);
-    float F = exp2f(rc.alpha * u);
-    float v = S * F * col_kappa(cc, n);
-    float y = fmaf(rc.omf, v, rc.f * vprev);
-    vprev = v;
+__device__ __forceinline__ void epi_node(float (&acc)[4 * Q4], Slide &sl, float S, int n, const RowConst &rc,
+                                         const ColConst &cc, const float4 *__restrict__ tab, int m_last) {
+    const float ell = fmaf((float)n, cc.dell, cc.ell0);
+    const float u = exp2f(rc.beta * ell);
+    const float F = exp2f(rc.alpha * u);
+    const float v = S * F * col_kappa(cc, n);
+    const float y = fmaf(rc.w[0], v, fmaf(rc.w[1], sl.v1, fmaf(rc.w[2], sl.v2, rc.w[3] * sl.v3)));
+    sl.v3 = sl.v2;
+    sl.v2 = sl.v1;
+    sl.v1 = v;
     acc_row<Q4>(acc, tab, min(n + rc.i0, m_last), y);
 }
 
-// Closing term of a run that ended at node b-1.
+// Closing rows of a run that ended at node b-1 (grid rows b+i0-1 .. b+i0+1).
 template <int Q4>
-__device__ __forceinline__ void epi_close(float (&acc)[4 * Q4], float vprev, int b, const RowConst &rc,
+__device__ __forceinline__ void epi_close(float (&acc)[4 * Q4], const Slide &sl, int b, const RowConst &rc,
                                           const float4 *__restrict__ tab, int m_last) {
-    acc_row<Q4>(acc, tab, min(b + rc.i0, m_last), rc.f * vprev);
+    acc_row<Q4>(acc, tab, min(b + rc.i0, m_last), fmaf(rc.w[1], sl.v1, fmaf(rc.w[2], sl.v2, rc.w[3] * sl.v3)));
+    acc_row<Q4>(acc, tab, min(b + rc.i0 + 1, m_last), fmaf(rc.w[2], sl.v1, rc.w[3] * sl.v2));
+    acc_row<Q4>(acc, tab, min(b + rc.i0 + 2, m_last), rc.w[3] * sl.v1);
 }
+
+// Gradient mode: besides N_q (acc[0]) the same sliding sums accumulate
+//   A_q = sum_n v_n u_n T_q        (acc[1]),  d N_q / d Av    = -0.4 ln10 A_q
+//   D_q = sum_n v_n u_n l_n T_q    (acc[2]),  d N_q / d delta = -0.4 ln10 Av D_q
+// with l_n = ln(lam_n / 5500 A), since dF/dAv = -0.4 ln10 u F and
+// du/ddelta = u l_n (Sec. 3.4, Eq. attenuation).
+template <int Q4>
+__device__ __forceinline__ void acc_row3(float (&acc)[3][4 * Q4], const float4 *__restrict__ tab, int m,
+                                         float y0, float y1, float y2) {
+    const float4 *tp = tab + (size_t)m * Q4;
+#pragma unroll
+    for (int qq = 0; qq < Q4; ++qq) {
+        const float4 t = __ldg(tp + qq);
+        const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc[0][4 * qq + c] = fmaf(y0, tv[c], acc[0][4 * qq + c]);
+            acc[1][4 * qq + c] = fmaf(y1, tv[c], acc[1][4 * qq + c]);
+            acc[2][4 * qq + c] = fmaf(y2, tv[c], acc[2][4 * qq + c]);
+        }
+    }
+}
+
+template <int Q4>
+__device__ __forceinline__ void epi_node_grad(float (&acc)[3][4 * Q4], Slide (&sl)[3], float S, int n,
+                                              const RowConst &rc, const ColConst &cc,
+                                              const float4 *__restrict__ tab, int m_last) {
+    const float ell = fmaf((float)n, cc.dell, cc.ell0);
+    const float u = exp2f(rc.beta * ell);
+    const float F = exp2f(rc.alpha * u);
+    const float v = S * F * col_kappa(cc, n);
+    const float vv[3] = {v, v * u, v * u * (ell * 0.69314718055994531f)};
+    float y[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        y[r] = fmaf(rc.w[0], vv[r], fmaf(rc.w[1], sl[r].v1, fmaf(rc.w[2], sl[r].v2, rc.w[3] * sl[r].v3)));
+        sl[r].v3 = sl[r].v2;
+        sl[r].v2 = sl[r].v1;
+        sl[r].v1 = vv[r];
+    }
+    acc_row3<Q4>(acc, tab, min(n + rc.i0, m_last), y[0], y[1], y[2]);
+}
+
+template <int Q4>
+__device__ __forceinline__ void epi_close_grad(float (&acc)[3][4 * Q4], const Slide (&sl)[3], int b,
+                                               const RowConst &rc, const float4 *__restrict__ tab, int m_last) {
+    float y[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) y[r] = fmaf(rc.w[1], sl[r].v1, fmaf(rc.w[2], sl[r].v2, rc.w[3] * sl[r].v3));
+    acc_row3<Q4>(acc, tab, min(b + rc.i0, m_last), y[0], y[1], y[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) y[r] = fmaf(rc.w[2], sl[r].v1, rc.w[3] * sl[r].v2);
+    acc_row3<Q4>(acc, tab, min(b + rc.i0 + 1, m_last), y[0], y[1], y[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) y[r] = rc.w[3] * sl[r].v1;
+    acc_row3<Q4>(acc, tab, min(b + rc.i0 + 2, m_last), y[0], y[1], y[2]);
+}
+
+// Columns (in 32-wide blocks [kb0, kb1)) of the adjoint Shat[g, n] that can be
+// non-zero for the 128-row galaxy tile mt (rows sorted by redshift shift):
+// Shat_n uses grid indices n + i0 - 1 .. n + i0 + 2, so it vanishes unless
+// n + i0 lies in [m_nz_lo - 2, m_nz_hi + 1].  At least one block is kept.
+struct VjpBand {
+    int on, m_nz_lo, m_nz_hi, i0_margin, Q;
+};
+
+__device__ __forceinline__ void vjp_band(const VjpBand &b, const float *aux, int64_t n, int mt, int N_pad, int &kb0,
+                                         int &kb1) {
+    kb0 = 0;
+    kb1 = N_pad / 32;
+    if (!b.on) return;
+    const int64_t r0 = (int64_t)mt * 128;
+    const int64_t r1 = min(r0 + 128, n) - 1;
+    const int i0_lo = max((int)floorf(aux[r0 * AUX_STRIDE + 2]) - b.i0_margin, 0);
+    const int i0_hi = (int)floorf(aux[r1 * AUX_STRIDE + 2]) + b.i0_margin;
+    int n_lo = b.m_nz_lo - i0_hi - 2;
+    int n_hi = b.m_nz_hi - i0_lo + 1;
+    n_lo = max(n_lo, 0);
+    n_hi = min(n_hi, N_pad - 1);
+    if (b.m_nz_hi < b.m_nz_lo || n_hi < n_lo) {
+        kb0 = 0;
+        kb1 = 1;
+        return;
+    }
+    kb0 = n_lo / 32;
+    kb1 = n_hi / 32 + 1;
+}
+
+VjpBand make_vjp_band(const Ctx &c, const FilterSet &fs, bool band);
 
 // m_q = -2.5 log10(N_q) + 2.5 log10(AB0 D_q) - 2.5 logM + Dmod - 2.5 log10(1+z)
 template <int Q4>

@@ -28,9 +28,10 @@ struct SArgs {
     const double *offq;
     ColConst cc;
     float *mags;           // [n][Q]
+    float *partial;        // gradient mode: [n][3 * 4 * Q4] sums N, A, D per filter
 };
 
-template <int Q4>
+template <int Q4, bool GRAD>
 __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
     __shared__ __align__(16) float As[2][BK][AS_LD];
     __shared__ __align__(16) float Bs[2][BK][BN];
@@ -42,9 +43,12 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
     const int er = tid >> 1, eh = tid & 1;
     const RowConst rc = load_row_const(a.aux, m0 + er, a.n);
 
-    float acc[4 * Q4];
+    constexpr int NR = GRAD ? 3 : 1;
+    float acc[NR][4 * Q4];
 #pragma unroll
-    for (int q = 0; q < 4 * Q4; ++q) acc[q] = 0.f;
+    for (int r3 = 0; r3 < NR; ++r3)
+#pragma unroll
+        for (int q = 0; q < 4 * Q4; ++q) acc[r3][q] = 0.f;
 
     const int KT = a.K_pad / BK;
     for (int n0 = 0; n0 < a.N_pad; n0 += BN) {
@@ -116,28 +120,46 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
         __syncthreads();
 
         if (rc.valid) {
-            float vprev = 0.f;
+            Slide sl[3];
             const int nb = n0 + eh * 64;
-            for (int jj = 0; jj < 64; ++jj)
-                epi_node<Q4>(acc, vprev, Cs[er * CS_LD + eh * 64 + jj], nb + jj, rc, a.cc, a.tab, a.m_last);
-            epi_close<Q4>(acc, vprev, nb + 64, rc, a.tab, a.m_last);
+            for (int jj = 0; jj < 64; ++jj) {
+                if constexpr (GRAD)
+                    epi_node_grad<Q4>(acc, sl, Cs[er * CS_LD + eh * 64 + jj], nb + jj, rc, a.cc, a.tab, a.m_last);
+                else
+                    epi_node<Q4>(acc[0], sl[0], Cs[er * CS_LD + eh * 64 + jj], nb + jj, rc, a.cc, a.tab, a.m_last);
+            }
+            if constexpr (GRAD)
+                epi_close_grad<Q4>(acc, sl, nb + 64, rc, a.tab, a.m_last);
+            else
+                epi_close<Q4>(acc[0], sl[0], nb + 64, rc, a.tab, a.m_last);
         }
         __syncthreads();
     }
 
 #pragma unroll
-    for (int q = 0; q < 4 * Q4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 1);
+    for (int r3 = 0; r3 < NR; ++r3)
+#pragma unroll
+        for (int q = 0; q < 4 * Q4; ++q) acc[r3][q] += __shfl_xor_sync(0xffffffffu, acc[r3][q], 1);
     const int64_t row = m0 + er;
-    if (eh == 0 && row < a.n)
-        write_mags<Q4>(acc, a.Q, a.magoff[row], a.offq, a.mags + row * a.Q);
+    if (eh == 0 && row < a.n) {
+        if constexpr (GRAD) {
+            float *dst = a.partial + row * (NR * 4 * Q4);
+#pragma unroll
+            for (int r3 = 0; r3 < NR; ++r3)
+#pragma unroll
+                for (int q = 0; q < 4 * Q4; ++q) dst[r3 * 4 * Q4 + q] = acc[r3][q];
+        } else {
+            write_mags<Q4>(acc[0], a.Q, a.magoff[row], a.offq, a.mags + row * a.Q);
+        }
+    }
 }
 
-template <int Q4>
+template <int Q4, bool GRAD>
 cudaError_t launch_q4(const SArgs &a, int64_t n, cudaStream_t s) {
     size_t smem = (size_t)BM * CS_LD * sizeof(float);
-    cudaFuncSetAttribute(phot_simt_kernel<Q4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(phot_simt_kernel<Q4, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((unsigned)((n + BM - 1) / BM));
-    phot_simt_kernel<Q4><<<grid, THREADS, smem, s>>>(a);
+    phot_simt_kernel<Q4, GRAD><<<grid, THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -155,7 +177,7 @@ ColConst make_col_const(const Ctx &c) {
 }
 
 cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags, cudaStream_t s,
-                             const Scratch *ws) {
+                             const Scratch *ws, bool grad) {
     if (n <= 0) return cudaSuccess;
     SArgs a{};
     a.W = c.d_w32;
@@ -176,11 +198,20 @@ cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float
         a.aux = ws->aux;
         a.magoff = ws->magoff;
     }
+    a.partial = c.d_partial;
+    if (grad) {
+        switch (fs.Q4) {
+        case 1: return launch_q4<1, true>(a, n, s);
+        case 2: return launch_q4<2, true>(a, n, s);
+        case 3: return launch_q4<3, true>(a, n, s);
+        default: return launch_q4<4, true>(a, n, s);
+        }
+    }
     switch (fs.Q4) {
-    case 1: return launch_q4<1>(a, n, s);
-    case 2: return launch_q4<2>(a, n, s);
-    case 3: return launch_q4<3>(a, n, s);
-    default: return launch_q4<4>(a, n, s);
+    case 1: return launch_q4<1, false>(a, n, s);
+    case 2: return launch_q4<2, false>(a, n, s);
+    case 3: return launch_q4<3, false>(a, n, s);
+    default: return launch_q4<4, false>(a, n, s);
     }
 }
 

@@ -26,10 +26,13 @@
 
 #include "dsps_internal.cuh"
 #include "epilogue.cuh"
+#include "tc_common.cuh"
 
 namespace dsps {
 
 namespace {
+
+using namespace tc;
 
 constexpr int BM = 128, BN = 256, BK = 32;
 constexpr int STAGES = 4;
@@ -39,16 +42,10 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
 constexpr uint32_t TMEM_COLS = 2 * BN;
-constexpr long long WAIT_LIMIT = 2000000000LL;   // SM clock cycles, about one second
 constexpr int QMAX = 16;
 constexpr size_t BAR_BYTES = 1024;
-constexpr size_t COMB_BYTES = (size_t)BM * QMAX * 4;
+constexpr size_t COMB_BYTES = (size_t)BM * 3 * QMAX * 4;   // up to 3 sums per filter (gradient mode)
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + COMB_BYTES;
-
-// kind::f16 instruction descriptor: FP32 accumulate (bits 4-5 = 1), A and B
-// bf16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
 
 struct TArgs {
     const float *aux;
@@ -62,108 +59,11 @@ struct TArgs {
     unsigned *err;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: true once the phase of the given parity has completed; false
-// if another role aborted or the limit expired (which aborts the CTA).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          unsigned *err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
-            *abort_flag = 1;
-            atomicOr(err, DERR_TIMEOUT);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, uint32_t bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(x), "r"(y)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor, K-major operand with the 64-byte swizzle:
-// start address >> 4 (bits 0-13), leading offset unused (1), stride between
-// 8-row groups 8 x 64 B = 512 B (bits 32-45, >> 4), descriptor version 1
-// (bit 46), layout type 4 = SWIZZLE_64B (bits 61-63).
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1u << 16;
-    d |= (uint64_t)(512u >> 4) << 32;
-    d |= (uint64_t)1u << 46;
-    d |= (uint64_t)4u << 61;
-    return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-}
-
 // Wavelength tiles [nt0, nt1) that galaxy tile mt needs: rows are sorted by
 // the redshift shift s, so the tile's shifts lie in [s(first row), s(last row)]
-// up to one sort bucket; a wavelength tile whose filter-table rows n + i0 and
-// n + i0 + 1 all fall outside the band [m_nz_lo, m_nz_hi] of non-zero
-// transmission contributes exactly zero and is skipped.
+// up to one sort bucket; a wavelength tile whose interpolation rows (grid
+// indices n + i0 - 1 .. n + i0 + 2) all fall outside the band [m_nz_lo, m_nz_hi]
+// of non-zero transmission contributes exactly zero and is skipped.
 __device__ __forceinline__ void tile_nrange(const TArgs &a, int mt, int &nt0, int &nt1) {
     nt0 = 0;
     nt1 = a.n_ntiles;
@@ -172,8 +72,8 @@ __device__ __forceinline__ void tile_nrange(const TArgs &a, int mt, int &nt0, in
     const int64_t r1 = min(r0 + BM, a.n) - 1;
     const int i0_lo = max((int)floorf(a.aux[r0 * AUX_STRIDE + 2]) - a.i0_margin, 0);
     const int i0_hi = (int)floorf(a.aux[r1 * AUX_STRIDE + 2]) + a.i0_margin;
-    const int n_lo = a.m_nz_lo - i0_hi - 1;
-    const int n_hi = a.m_nz_hi - i0_lo;
+    const int n_lo = a.m_nz_lo - i0_hi - 2;
+    const int n_hi = a.m_nz_hi - i0_lo + 1;
     if (n_hi < 0 || a.m_nz_hi < a.m_nz_lo) { nt1 = nt0; return; }
     nt0 = n_lo <= 0 ? 0 : n_lo / BN;
     nt1 = min(a.n_ntiles, n_hi / BN + 1);
@@ -187,7 +87,7 @@ __device__ __forceinline__ int first_tile(int nt0, int part, int parts) {
     return nt0 + ((part - nt0 % parts) % parts + parts) % parts;
 }
 
-template <int Q4>
+template <int Q4, bool GRAD>
 __global__ void __launch_bounds__(THREADS, 1)
 phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -328,9 +228,12 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
             tile_nrange(a, mt, nt0, nt1);
             const int64_t rowg = (int64_t)mt * BM + row;
             const RowConst rc = load_row_const(a.aux, rowg, a.n);
-            float acc[4 * Q4];
+            constexpr int NR = GRAD ? 3 : 1;   // sums per filter: N (and A, D for the gradient)
+            float acc[NR][4 * Q4];
 #pragma unroll
-            for (int q = 0; q < 4 * Q4; ++q) acc[q] = 0.f;
+            for (int r3 = 0; r3 < NR; ++r3)
+#pragma unroll
+                for (int q = 0; q < 4 * Q4; ++q) acc[r3][q] = 0.f;
             for (int nt = first_tile(nt0, part, a.parts); nt < nt1; nt += a.parts) {
                 int got = 1;
                 if (lane == 0) got = mbar_wait(accf0 + 8 * as, aphase, abort_flag, a.err) ? 1 : 0;
@@ -339,7 +242,7 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                 tc_fence_after();
                 const uint32_t tb = tmem_base + ((uint32_t)(qd * 32) << 16) + (uint32_t)(as * BN + half * 128);
                 const int nb = nt * BN + half * 128;
-                float vprev = 0.f;
+                Slide sl[3];
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
                     uint32_t r[32];
@@ -351,19 +254,32 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                     }
                     if (rc.valid) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            epi_node<Q4>(acc, vprev, __uint_as_float(r[j]), nb + c * 32 + j, rc, a.cc, a.tab,
-                                         a.m_last);
+                        for (int j = 0; j < 32; ++j) {
+                            if constexpr (GRAD)
+                                epi_node_grad<Q4>(acc, sl, __uint_as_float(r[j]), nb + c * 32 + j, rc, a.cc, a.tab,
+                                                  a.m_last);
+                            else
+                                epi_node<Q4>(acc[0], sl[0], __uint_as_float(r[j]), nb + c * 32 + j, rc, a.cc,
+                                             a.tab, a.m_last);
+                        }
                     }
                 }
-                if (rc.valid) epi_close<Q4>(acc, vprev, nb + 128, rc, a.tab, a.m_last);
+                if (rc.valid) {
+                    if constexpr (GRAD)
+                        epi_close_grad<Q4>(acc, sl, nb + 128, rc, a.tab, a.m_last);
+                    else
+                        epi_close<Q4>(acc[0], sl[0], nb + 128, rc, a.tab, a.m_last);
+                }
                 if (++as == 2) { as = 0; aphase ^= 1u; }
             }
             if (!ok) break;
             // Combine the two column halves of each row (bounded barrier).
+            float *cr = comb + row * (3 * QMAX);
             if (half == 1)
 #pragma unroll
-                for (int q = 0; q < 4 * Q4; ++q) comb[row * QMAX + q] = acc[q];
+                for (int r3 = 0; r3 < NR; ++r3)
+#pragma unroll
+                    for (int q = 0; q < 4 * Q4; ++q) cr[r3 * 4 * Q4 + q] = acc[r3][q];
             __syncwarp();
             if (lane == 0) mbar_arrive(ebar);
             int got = 1;
@@ -372,13 +288,15 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
             ephase ^= 1u;
             if (!got) break;
             if (half == 0 && rowg < a.n) {
-                float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)part * a.n + rowg) * (4 * Q4));
+                float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)part * a.n + rowg) * (NR * 4 * Q4));
 #pragma unroll
-                for (int qq = 0; qq < Q4; ++qq)
-                    dst[qq] = make_float4(acc[4 * qq + 0] + comb[row * QMAX + 4 * qq + 0],
-                                          acc[4 * qq + 1] + comb[row * QMAX + 4 * qq + 1],
-                                          acc[4 * qq + 2] + comb[row * QMAX + 4 * qq + 2],
-                                          acc[4 * qq + 3] + comb[row * QMAX + 4 * qq + 3]);
+                for (int r3 = 0; r3 < NR; ++r3)
+#pragma unroll
+                    for (int qq = 0; qq < Q4; ++qq) {
+                        const float *cq = cr + r3 * 4 * Q4 + 4 * qq;
+                        dst[r3 * Q4 + qq] = make_float4(acc[r3][4 * qq + 0] + cq[0], acc[r3][4 * qq + 1] + cq[1],
+                                                        acc[r3][4 * qq + 2] + cq[2], acc[r3][4 * qq + 3] + cq[3]);
+                    }
             }
             // Second bounded barrier: half 0 has read comb before half 1 rewrites it.
             __syncwarp();
@@ -400,48 +318,19 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-// 2-D bf16 tensor [outer][inner] with row pitch `inner` elements, box
-// {BK, box_outer}, 64-byte swizzle; rows past `outer` read as zero.
-bool make_tmap(CUtensorMap *tm, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_outer) {
-    auto fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {inner * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, box_outer};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-template <int Q4>
+template <int Q4, bool GRAD>
 cudaError_t launch_q4(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
                       const TArgs &a, int grid, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(phot_tc_kernel<Q4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(phot_tc_kernel<Q4, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    phot_tc_kernel<Q4><<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
+    phot_tc_kernel<Q4, GRAD><<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *parts, cudaStream_t s) {
+cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *parts, cudaStream_t s, bool grad) {
     *parts = TC_PARTS;
     if (n <= 0) return cudaSuccess;
     if (fs.Q > QMAX) return cudaErrorInvalidValue;
@@ -470,11 +359,19 @@ cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *pa
     a.tiles = c.prof ? c.d_stats : nullptr;
     a.err = c.d_err;
     int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;
+    if (grad) {
+        switch (fs.Q4) {
+        case 1: return launch_q4<1, true>(ah, al, bh, bl, a, grid, s);
+        case 2: return launch_q4<2, true>(ah, al, bh, bl, a, grid, s);
+        case 3: return launch_q4<3, true>(ah, al, bh, bl, a, grid, s);
+        default: return launch_q4<4, true>(ah, al, bh, bl, a, grid, s);
+        }
+    }
     switch (fs.Q4) {
-    case 1: return launch_q4<1>(ah, al, bh, bl, a, grid, s);
-    case 2: return launch_q4<2>(ah, al, bh, bl, a, grid, s);
-    case 3: return launch_q4<3>(ah, al, bh, bl, a, grid, s);
-    default: return launch_q4<4>(ah, al, bh, bl, a, grid, s);
+    case 1: return launch_q4<1, false>(ah, al, bh, bl, a, grid, s);
+    case 2: return launch_q4<2, false>(ah, al, bh, bl, a, grid, s);
+    case 3: return launch_q4<3, false>(ah, al, bh, bl, a, grid, s);
+    default: return launch_q4<4, false>(ah, al, bh, bl, a, grid, s);
     }
 }
 

@@ -3,6 +3,13 @@
 // fixed).  Builds, from the caller's FP32 L[k][n] (k = i * n_z + j):
 //   d_L32   [K_pad][N_pad] FP32, zero padded                (SIMT form)
 //   d_Lt_*  [N_pad][K_pad] bf16 hi / lo of L[k][n] 2^-E_k    (tensor form, K-major rows)
+//   d_Ld32  [K_pad][N_pad] FP32 metallicity-differenced block: row (i, 0) is
+//           L[i, 0], row (i, j >= 1) is L[i, j] - L[i, j-1]   (FP32 adjoint)
+//   d_L_*   [K_pad][N_pad] bf16 hi / lo of the differenced block scaled by
+//           2^-E'_k, with d_wmul_d = 2^E'_k               (tensor adjoint)
+// The adjoint contracts with the differenced block so that the differences of
+// dLoss/domega between neighbouring metallicity bins -- all the metallicity
+// gradients need (summation by parts) -- come out at full relative precision.
 //   d_wmul  [K_pad] 2^E_k, the factor folded into the weights, so that
 //           sum_k (omega_k 2^E_k)(L_kn 2^-E_k) = sum_k omega_k L_kn exactly.
 // E_k is the binary exponent of max_n L[k][n]: every scaled row peaks in
@@ -64,6 +71,50 @@ __global__ void build_lt_kernel(const float *L, const float *rscale, int K, int 
     }
 }
 
+// Metallicity-differenced block, FP32 [K_pad][N_pad] (padding zero).
+__global__ void build_ldiff_kernel(const float *L, int K, int N, int n_z, int K_pad, int N_pad, float *Ld) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)K_pad * N_pad) return;
+    const int k = (int)(idx / N_pad), n = (int)(idx % N_pad);
+    float v = 0.f;
+    if (k < K && n < N) {
+        v = L[(size_t)k * N + n];
+        if (k % n_z != 0) v -= L[(size_t)(k - 1) * N + n];
+    }
+    Ld[idx] = v;
+}
+
+// Binary exponent of max_n |row k| of a [K_pad][N_pad] block.
+__global__ void row_exponent_abs_kernel(const float *A, int K, int N_pad, float *wmul, float *rscale) {
+    const int k = blockIdx.x;
+    float m = 0.f;
+    if (k < K)
+        for (int n = threadIdx.x; n < N_pad; n += blockDim.x) m = fmaxf(m, fabsf(A[(size_t)k * N_pad + n]));
+    __shared__ float red[32];
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mm = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, red[w]);
+        int E = mm > 0.f ? ilogbf(mm) : 0;
+        E = max(-120, min(120, E));
+        wmul[k] = k < K ? ldexpf(1.f, E) : 0.f;
+        rscale[k] = k < K ? ldexpf(1.f, -E) : 0.f;
+    }
+}
+
+// Row-scaled bf16 split of a [K_pad][N_pad] FP32 block.
+__global__ void build_split_kernel(const float *A, const float *rscale, int K_pad, int N_pad, __nv_bfloat16 *hi,
+                                   __nv_bfloat16 *lo) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)K_pad * N_pad) return;
+    const float v = A[idx] * rscale[idx / N_pad];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[idx] = h;
+    lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 }  // namespace
 
 cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
@@ -79,6 +130,10 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
         build_l32_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.N_pad, c.d_L32);
         dim3 g(c.N_pad / 32, c.K_pad / 32), b(32, 8);
         build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.K, c.n_lam, c.K_pad, c.N_pad, c.d_Lt_hi, c.d_Lt_lo);
+        const unsigned blk = (unsigned)((tot + 255) / 256);
+        build_ldiff_kernel<<<blk, 256>>>(d_raw, c.K, c.n_lam, c.n_z, c.K_pad, c.N_pad, c.d_Ld32);
+        row_exponent_abs_kernel<<<c.K_pad, 256>>>(c.d_Ld32, c.K, c.N_pad, c.d_wmul_d, d_rscale);
+        build_split_kernel<<<blk, 256>>>(c.d_Ld32, d_rscale, c.K_pad, c.N_pad, c.d_L_hi, c.d_L_lo);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }

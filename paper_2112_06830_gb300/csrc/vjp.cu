@@ -1,0 +1,240 @@
+// vjp.cu -- adjoint of the photometry (Sec. 2.1: the gradient of the SED with
+// respect to the parameters follows from the gradients of the SSP weights;
+// Sec. 3.4 for dust).  Given mag_bar = dLoss/dm[g][q]:
+//
+//   Nbar_q  = mag_bar_q * (-2.5 / ln 10) / N_q                (Sec. 2.2 magnitudes)
+//   Av_bar  = sum_q Nbar_q (-0.4 ln 10) A_q,   delta_bar = sum_q Nbar_q (-0.4 ln 10 Av) D_q
+//   logM_bar = -2.5 sum_q mag_bar_q
+//   Shat[g, n] = kappa_n F_gn sum_q Nbar_q T_q((1+z_g) lam_n)  (= dLoss/dS[g, n])
+//   What[g, k] = sum_n Shat[g, n] Ld[k, n]
+// with Ld the metallicity-differenced SSP block (prep.cu), so What holds
+// dLoss/domega[g, (i, 0)] and the differences dLoss/domega[g, (i, j)] -
+// dLoss/domega[g, (i, j-1)]; the weights adjoint (weights.cu) follows.  A_q, D_q come from the
+// forward kernels' gradient mode, so no spectrum is ever stored.
+#include <cmath>
+
+#include "dsps_internal.cuh"
+#include "epilogue.cuh"
+
+namespace dsps {
+
+namespace {
+
+__global__ void combine_grad_kernel(const float *partial, int parts, int64_t n, int qs, int Q, const double *magoff,
+                                    const double *offq, const int *gidx, const float *aux, const float *mag_bar,
+                                    float *mags, float *param_bar, int64_t G_stride, int64_t g_begin, float *cq) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t g = gidx ? (int64_t)gidx[r] : r;
+    const bool valid = aux[r * AUX_STRIDE + 3] != 0.f;
+    const float Av = aux[r * AUX_STRIDE + 4];
+    const double mo = magoff[r];
+    const float k10 = -2.5f / 2.302585092994046f;
+    const float kd = -0.4f * 2.302585092994046f;
+    float av_bar = 0.f, d_bar = 0.f, lm_bar = 0.f;
+    for (int q = 0; q < Q; ++q) {
+        float N = 0.f, A = 0.f, D = 0.f;
+        for (int p = 0; p < parts; ++p) {
+            const float *src = partial + ((int64_t)p * n + r) * (3 * qs);
+            N += src[q];
+            A += src[qs + q];
+            D += src[2 * qs + q];
+        }
+        const float mb = mag_bar[g * Q + q];
+        const float nb = valid ? mb * k10 / N : 0.f;
+        av_bar = fmaf(nb * kd, A, av_bar);
+        d_bar = fmaf(nb * kd * Av, D, d_bar);
+        lm_bar = fmaf(-2.5f, mb, lm_bar);
+        cq[r * QSTRIDE_MAX + q] = nb;
+        if (mags) mags[g * Q + q] = (float)(-2.5 * log10((double)N) + mo + offq[q]);
+    }
+    const float nan = __int_as_float(0x7fc00000);
+    param_bar[8 * G_stride + g_begin + g] = valid ? av_bar : nan;
+    param_bar[9 * G_stride + g_begin + g] = valid ? d_bar : nan;
+    param_bar[10 * G_stride + g_begin + g] = valid ? lm_bar : nan;
+}
+
+// One warp per (sorted) row: Shat over the row's band columns [32 kb0, 32 kb1).
+template <int Q4, bool BF16>
+__global__ void __launch_bounds__(256) shat_kernel(const float *aux, const float *cq, const float4 *tab, int m_last,
+                                                   ColConst cc, int64_t n, int N_pad, VjpBand band, float *out32,
+                                                   __nv_bfloat16 *out_hi, __nv_bfloat16 *out_lo) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    int kb0, kb1;
+    vjp_band(band, aux, n, (int)(r / 128), N_pad, kb0, kb1);
+    const RowConst rc = load_row_const(aux, r, n);
+    float nb[4 * Q4];
+#pragma unroll
+    for (int q = 0; q < 4 * Q4; ++q) nb[q] = q < band.Q ? cq[r * QSTRIDE_MAX + q] : 0.f;
+    for (int col = kb0 * 32 + lane; col < kb1 * 32; col += 32) {
+        float sh = 0.f;
+        if (rc.valid) {
+            // grid indices col + i0 - 1 .. col + i0 + 2 are table rows col + i0 .. col + i0 + 3
+            float cm[4];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                const float4 *tr = tab + (size_t)min(col + rc.i0 + d, m_last) * Q4;
+                float acc = 0.f;
+#pragma unroll
+                for (int qq = 0; qq < Q4; ++qq) {
+                    const float4 t = __ldg(tr + qq);
+                    acc = fmaf(nb[4 * qq + 0], t.x, fmaf(nb[4 * qq + 1], t.y, fmaf(nb[4 * qq + 2], t.z, fmaf(nb[4 * qq + 3], t.w, acc))));
+                }
+                cm[d] = acc;
+            }
+            const float ell = fmaf((float)col, cc.dell, cc.ell0);
+            const float F = exp2f(rc.alpha * exp2f(rc.beta * ell));
+            sh = col_kappa(cc, col) * F *
+                 fmaf(rc.w[0], cm[0], fmaf(rc.w[1], cm[1], fmaf(rc.w[2], cm[2], rc.w[3] * cm[3])));
+        }
+        if (BF16) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(sh);
+            out_hi[r * N_pad + col] = h;
+            out_lo[r * N_pad + col] = __float2bfloat16_rn(sh - __bfloat162float(h));
+        } else {
+            out32[r * N_pad + col] = sh;
+        }
+    }
+}
+
+// What[r][k] = sum_n A[r][n] B[k][n]: both operands K-contiguous (A = Shat,
+// B = the FP32 differenced SSP block), register-tiled like the forward SIMT kernel.
+constexpr int BM = 128, BN = 128, BK = 16, THREADS = 256, AS_LD = BM + 4;
+
+__global__ void __launch_bounds__(THREADS, 2) vjp_simt_kernel(const float *A, const float *B, int64_t n, int K_pad,
+                                                              int N_pad, float *C) {
+    __shared__ __align__(16) float As[2][BK][AS_LD];
+    __shared__ __align__(16) float Bs[2][BK][AS_LD];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int k0c = blockIdx.y * BN;   // output column block (SSP index k)
+    float c[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) c[i][j] = 0.f;
+    float4 ra[2], rb[2];
+    auto gload = [&](int kk) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int idx = tid + t * THREADS;
+            const int row = idx >> 2, q = (idx & 3) * 4;
+            const int64_t gr = m0 + row;
+            ra[t] = gr < n ? *reinterpret_cast<const float4 *>(A + gr * N_pad + kk + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int kr = k0c + row;
+            rb[t] = kr < K_pad ? *reinterpret_cast<const float4 *>(B + (int64_t)kr * N_pad + kk + q)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int idx = tid + t * THREADS;
+            const int row = idx >> 2, q = (idx & 3) * 4;
+            As[buf][q + 0][row] = ra[t].x;
+            As[buf][q + 1][row] = ra[t].y;
+            As[buf][q + 2][row] = ra[t].z;
+            As[buf][q + 3][row] = ra[t].w;
+            Bs[buf][q + 0][row] = rb[t].x;
+            Bs[buf][q + 1][row] = rb[t].y;
+            Bs[buf][q + 2][row] = rb[t].z;
+            Bs[buf][q + 3][row] = rb[t].w;
+        }
+    };
+    const int KT = N_pad / BK;
+    gload(0);
+    sstore(0);
+    __syncthreads();
+    for (int kt = 0; kt < KT; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < KT) gload((kt + 1) * BK);
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) c[i][j] = fmaf(av[i], bv[j], c[i][j]);
+        }
+        if (kt + 1 < KT) sstore(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        if (r >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 8; j += 4) {
+            const int col = k0c + (j < 4 ? tx * 4 : 64 + tx * 4);
+            if (col < K_pad)
+                *reinterpret_cast<float4 *>(C + r * K_pad + col) =
+                    make_float4(c[i][j], c[i][j + 1], c[i][j + 2], c[i][j + 3]);
+        }
+    }
+}
+
+}  // namespace
+
+VjpBand make_vjp_band(const Ctx &c, const FilterSet &fs, bool band) {
+    VjpBand b;
+    b.on = band ? 1 : 0;
+    b.m_nz_lo = fs.m_nz_lo;
+    b.m_nz_hi = fs.m_nz_hi;
+    b.i0_margin = (int)std::ceil(1.0 / zsort_key_scale(c)) + 1;
+    b.Q = fs.Q;
+    return b;
+}
+
+cudaError_t launch_combine_grad(const Ctx &c, const FilterSet &fs, int64_t n, int parts, bool sorted,
+                                const float *mag_bar, float *mags, float *param_bar, int64_t G_stride,
+                                int64_t g_begin, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    combine_grad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        c.d_partial, parts, n, 4 * fs.Q4, fs.Q, c.d_magoff, fs.d_offq, sorted ? c.d_gidx : nullptr, c.d_aux, mag_bar,
+        mags, param_bar, G_stride, g_begin, c.d_cq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shat(const Ctx &c, const FilterSet &fs, int64_t n, bool bf16, bool band, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const VjpBand b = make_vjp_band(c, fs, band);
+    const ColConst cc = make_col_const(c);
+    const auto *tab = reinterpret_cast<const float4 *>(fs.d_tab);
+    const int m_last = fs.m_rows - 1;
+    float *o32 = reinterpret_cast<float *>(c.d_shat);
+    auto *ohi = reinterpret_cast<__nv_bfloat16 *>(c.d_shat);
+    __nv_bfloat16 *olo = ohi + (size_t)c.chunk * c.N_pad;
+    const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
+#define DSPS_SHAT(Q4)                                                                                      \
+    if (bf16)                                                                                              \
+        shat_kernel<Q4, true><<<blocks, 256, 0, s>>>(c.d_aux, c.d_cq, tab, m_last, cc, n, c.N_pad, b, o32, \
+                                                     ohi, olo);                                            \
+    else                                                                                                   \
+        shat_kernel<Q4, false><<<blocks, 256, 0, s>>>(c.d_aux, c.d_cq, tab, m_last, cc, n, c.N_pad, b, o32, \
+                                                      ohi, olo);
+    switch (fs.Q4) {
+    case 1: DSPS_SHAT(1) break;
+    case 2: DSPS_SHAT(2) break;
+    case 3: DSPS_SHAT(3) break;
+    default: DSPS_SHAT(4) break;
+    }
+#undef DSPS_SHAT
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vjp_simt(const Ctx &c, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((n + BM - 1) / BM), (unsigned)((c.K_pad + BN - 1) / BN));
+    vjp_simt_kernel<<<grid, THREADS, 0, s>>>(reinterpret_cast<const float *>(c.d_shat), c.d_Ld32, n, c.K_pad,
+                                             c.N_pad, c.d_w32);
+    return cudaGetLastError();
+}
+
+}  // namespace dsps

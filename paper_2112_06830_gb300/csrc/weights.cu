@@ -73,35 +73,33 @@ __host__ __device__ inline size_t weights_smem_per_warp(int n_t, int n_age) {
     return (((size_t)n_t * 3 + (size_t)(n_age + 1) * 2 + (size_t)n_age * 2) * 4 + 15) & ~(size_t)15;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    const size_t per_warp = weights_smem_per_warp(a.n_t, a.n_age);
-    unsigned char *base = smem_raw + per_warp * warp;
-    float *sfr = reinterpret_cast<float *>(base);       // [n_t]
-    float *itg = sfr + a.n_t;                            // [n_t]
-    float *cum = itg + a.n_t;                            // [n_t]
-    int *em = reinterpret_cast<int *>(cum + a.n_t);     // [n_age + 1]
-    float *er = reinterpret_cast<float *>(em + a.n_age + 1);
-    float *bmass = er + a.n_age + 1;                     // [n_age]
-    float *frac = bmass + a.n_age;                       // [n_age]
+struct SfhSmem {
+    float *sfr, *itg, *cum;   // [n_t] SFR at nodes, interval integrals, FP32 node prefix
+    int *em;                  // [n_age + 1] interval index of each age-bin edge
+    float *er;                // [n_age + 1] position of the edge inside its interval
+    float *bmass, *frac;      // [n_age] bin masses, fractions of the total
+};
 
-    const int64_t gi = (int64_t)blockIdx.x * nwarps + warp;
-    if (gi >= a.n) return;
-    const int64_t gl = a.perm ? (int64_t)a.perm[gi] : gi;
-    const int64_t g = a.g_begin + gl;
+__device__ __forceinline__ SfhSmem sfh_smem(unsigned char *base, int n_t, int n_age) {
+    SfhSmem m;
+    m.sfr = reinterpret_cast<float *>(base);
+    m.itg = m.sfr + n_t;
+    m.cum = m.itg + n_t;
+    m.em = reinterpret_cast<int *>(m.cum + n_t);
+    m.er = reinterpret_cast<float *>(m.em + n_age + 1);
+    m.bmass = m.er + n_age + 1;
+    m.frac = m.bmass + n_age;
+    return m;
+}
 
-    float mine = lane < NPAR ? a.params[(int64_t)lane * a.G_stride + g] : 0.f;
-    float p[NPAR];
-#pragma unroll
-    for (int r = 0; r < NPAR; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
-
-    const float z = p[11], sig = p[6];
-    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NPAR);
-    valid = valid && z > 0.f && (double)z <= a.zmax && sig > 0.f && p[0] > 0.f;
-
+// Stages 1-4 for one galaxy (whole warp): SFR at the nodes, the age-bin
+// masses and their fractions of the total; returns the galaxy's validity and
+// the total formed mass (FP64) through msum_out.
+__device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool valid, int lane, const SfhSmem &sm,
+                                       double &msum_out) {
+    float *sfr = sm.sfr, *itg = sm.itg, *cum = sm.cum, *er = sm.er, *bmass = sm.bmass, *frac = sm.frac;
+    int *em = sm.em;
+    const float z = p[11];
     // 1. cosmology: FP64 table lookup of t_obs, and t_obs's position on the
     //    time grid, a = (t_obs - t0)/h = m_obs + f_obs (FP64, split once)
     int m_obs = 0;
@@ -200,6 +198,36 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
     __syncwarp();
     for (int i = lane; i < a.n_age; i += 32) frac[i] = bmass[i] * inv_mtot;
     __syncwarp();
+    msum_out = msum;
+    return valid;
+
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const size_t per_warp = weights_smem_per_warp(a.n_t, a.n_age);
+    const SfhSmem sm = sfh_smem(smem_raw + per_warp * warp, a.n_t, a.n_age);
+
+    const int64_t gi = (int64_t)blockIdx.x * nwarps + warp;
+    if (gi >= a.n) return;
+    const int64_t gl = a.perm ? (int64_t)a.perm[gi] : gi;
+    const int64_t g = a.g_begin + gl;
+
+    float mine = lane < NPAR ? a.params[(int64_t)lane * a.G_stride + g] : 0.f;
+    float p[NPAR];
+#pragma unroll
+    for (int r = 0; r < NPAR; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
+
+    const float z = p[11], sig = p[6];
+    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NPAR);
+    valid = valid && z > 0.f && (double)z <= a.zmax && sig > 0.f && p[0] > 0.f;
+
+    double msum = 0.0;
+    valid = sfh_stage(a, p, valid, lane, sm, msum);
+    float *frac = sm.frac;
 
     // 5-6. metallicity weights and output, four consecutive k per lane.  The
     //      CDF at the upper edge of bin j is the lower edge of bin j+1, and the
@@ -289,6 +317,211 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
             a.magoff[gi] = magoff;
         }
     }
+}
+
+
+// ---------------------------------------------------------------------------
+// Adjoint of the weights (reverse of stages 6 .. 2).  Input: What[r][k], the
+// adjoint contraction against the metallicity-differenced SSP block (scaled
+// by 2^-E'_k in the tensor form: multiplied back by wmul_d here).  Output:
+// param_bar rows 0..7 (SFH, mdf_mu, mdf_sigma, slope).
+// ---------------------------------------------------------------------------
+
+// Sec. 3.1: dSFR/dp_k at time t (same parametrisation as sfr_f), k = 0..4.
+__device__ __forceinline__ void sfr_grad_f(int model, const float *p, float t, float (&gr)[5]) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) gr[k] = 0.f;
+    if (model == DSPS_SFH_DELAYED_TAU) {
+        const float sv = t * expf(-t / p[0]);
+        gr[0] = sv * t / (p[0] * p[0]);
+        return;
+    }
+    const float lr = logf(t / p[0]);
+    const float ra = expf(-p[1] * lr), rf = expf(-p[2] * lr);
+    const float D = ra + rf, invD2 = 1.f / (D * D);
+    const float ms = 1.f / D;
+    const float zq = (t - (p[3] - 0.9f)) * (1.f / 0.3f);
+    const float P = terf_f(zq);
+    const float fq = exp10f(-p[4] * P);
+    gr[0] = -(p[1] * ra + p[2] * rf) / p[0] * invD2 * fq;
+    gr[1] = lr * ra * invD2 * fq;
+    gr[2] = lr * rf * invD2 * fq;
+    gr[3] = ms * fq * p[4] * 2.302585093f * triweight_f(zq) * (1.f / 0.3f);
+    gr[4] = -ms * fq * 2.302585093f * P;
+}
+
+__device__ __forceinline__ float mdf_pdf(int kernel, float u) {
+    return kernel == DSPS_MDF_TRIWEIGHT ? triweight_f(u) : gauss_pdf_f(u);
+}
+
+__host__ __device__ inline size_t weights_vjp_smem_per_warp(int n_t, int n_age) {
+    return weights_smem_per_warp(n_t, n_age) + ((((size_t)n_t + (size_t)n_age) * 4 + 15) & ~(size_t)15);
+}
+
+__global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *what, int scaled, float *pbar) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    unsigned char *base = smem_raw + weights_vjp_smem_per_warp(a.n_t, a.n_age) * warp;
+    const SfhSmem sm = sfh_smem(base, a.n_t, a.n_age);
+    float *fracbar = reinterpret_cast<float *>(base + weights_smem_per_warp(a.n_t, a.n_age));   // [n_age]
+    float *sbar = fracbar + a.n_age;                                                            // [n_t]
+
+    const int64_t gi = (int64_t)blockIdx.x * nwarps + warp;
+    if (gi >= a.n) return;
+    const int64_t gl = a.perm ? (int64_t)a.perm[gi] : gi;
+    const int64_t g = a.g_begin + gl;
+    float mine = lane < NPAR ? a.params[(int64_t)lane * a.G_stride + g] : 0.f;
+    float p[NPAR];
+#pragma unroll
+    for (int r = 0; r < NPAR; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
+    const float z = p[11], sig = p[6];
+    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NPAR);
+    valid = valid && z > 0.f && (double)z <= a.zmax && sig > 0.f && p[0] > 0.f;
+    double msum = 0.0;
+    valid = sfh_stage(a, p, valid, lane, sm, msum);
+    const float *frac = sm.frac;
+    for (int i = lane; i < a.n_age; i += 32) fracbar[i] = 0.f;
+    for (int n = lane; n < a.n_t; n += 32) sbar[n] = 0.f;
+    __syncwarp();
+
+    // reverse of stages 5-6, by parts: with dw_(i,e) = dLoss/domega_(i,e) -
+    // dLoss/domega_(i,e-1) (dw_(i,0) = dLoss/domega_(i,0)) from the adjoint
+    // contraction against the differenced block,
+    //   dLoss/dfrac_i = sum_e dw_(i,e) P(Z >= edge e | i)
+    //   dLoss/dmu_i   = frac_i / sigma sum_{e>=1} dw_(i,e) pdf(u_e)
+    //   dLoss/dsigma  = sum_i frac_i / sigma sum_{e>=1} dw_(i,e) pdf(u_e) u_e
+    // (the MDF bin probabilities are CDF differences, Sec. 3.2 / Appendix B).
+    const float inv_sig = 1.f / sig;
+    const int nz = a.n_z;
+    float mu_bar = 0.f, sig_bar = 0.f, slope_bar = 0.f;
+    for (int k = lane; k < a.K && valid; k += 32) {
+        const int i = k / nz, e = k - i * nz;
+        float wd = what[gi * a.K_pad + k];
+        if (scaled) wd *= __ldg(a.wmul + k);
+        const float xl = __ldg(a.logage + i) - 9.f;
+        if (e == 0) {
+            atomicAdd(fracbar + i, wd);
+            continue;
+        }
+        const float u = (__ldg(a.zedge + e) - fmaf(p[7], xl, p[5])) * inv_sig;
+        const float sv = mdf_s(a.mdf_kernel, u);
+        const float tail = u > 0.f ? -sv : 1.f - sv;
+        atomicAdd(fracbar + i, wd * tail);
+        const float t = frac[i] * wd * mdf_pdf(a.mdf_kernel, u) * inv_sig;
+        mu_bar += t;
+        sig_bar = fmaf(t, u, sig_bar);
+        slope_bar = fmaf(t, xl, slope_bar);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mu_bar += __shfl_xor_sync(0xffffffffu, mu_bar, off);
+        sig_bar += __shfl_xor_sync(0xffffffffu, sig_bar, off);
+        slope_bar += __shfl_xor_sync(0xffffffffu, slope_bar, off);
+    }
+    __syncwarp();
+
+    // reverse of the normalisation frac_i = B_i / sum_i B_i
+    float dot = 0.f;
+    for (int i = lane; i < a.n_age; i += 32) dot = fmaf(fracbar[i], frac[i], dot);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+    const float inv_m = valid ? 1.f / (float)msum : 0.f;
+
+    // reverse of stages 3-4: each bin integral is linear in the node SFRs
+    const float h = (float)a.h;
+    for (int i = lane; i < a.n_age && valid; i += 32) {
+        const float bb = (fracbar[i] - dot) * inv_m;
+        const int mi = sm.em[i], mo = sm.em[i + 1];
+        const float ri = sm.er[i], ro = sm.er[i + 1];
+        if (mi < 0 || bb == 0.f) continue;
+        auto add = [&](int m, float len, float rbar) {
+            atomicAdd(sbar + m, bb * len * (1.f - rbar));
+            atomicAdd(sbar + m + 1, bb * len * rbar);
+        };
+        if (mo < 0) {
+            for (int m = 0; m < mi; ++m) add(m, h, 0.5f);
+            add(mi, ri * h, 0.5f * ri);
+        } else if (mi == mo) {
+            add(mi, __ldg(a.bwidth + i), 0.5f * (ri + ro));
+        } else {
+            add(mo, mi == mo + 1 ? __ldg(a.bwidth + i) - ri * h : (1.f - ro) * h, 0.5f * (ro + 1.f));
+            for (int m = mo + 1; m < mi; ++m) add(m, h, 0.5f);
+            add(mi, ri * h, 0.5f * ri);
+        }
+    }
+    __syncwarp();
+
+    // reverse of stage 2: the SFR parameters
+    float tb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int n = lane; n < a.n_t && valid; n += 32) {
+        float gr[5];
+        sfr_grad_f(a.sfh_model, p, fmaf((float)n, h, (float)a.t0), gr);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) tb[q] = fmaf(sbar[n], gr[q], tb[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) tb[q] += __shfl_xor_sync(0xffffffffu, tb[q], off);
+
+    if (lane == 0) {
+        const float nan = __int_as_float(0x7fc00000);
+        const float out[8] = {tb[0], tb[1], tb[2], tb[3], tb[4], mu_bar, sig_bar, slope_bar};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) pbar[(int64_t)q * a.G_stride + g] = valid ? out[q] : nan;
+    }
+}
+
+WArgs make_wargs(const Ctx &c, const float *params, int64_t G_stride, int64_t g_begin, int64_t n) {
+    WArgs a{};
+    a.params = params;
+    a.G_stride = G_stride;
+    a.g_begin = g_begin;
+    a.n = n;
+    a.n_age = c.n_age;
+    a.n_z = c.n_z;
+    a.K = c.K;
+    a.K_pad = c.K_pad;
+    a.n_t = c.n_t;
+    a.sfh_model = c.opts.sfh_model;
+    a.mdf_kernel = c.opts.mdf_kernel;
+    a.n_lut = c.n_lut;
+    a.t0 = c.t0;
+    a.h = (c.t1 - c.t0) / (c.n_t - 1);
+    a.inv_h = 1.0 / a.h;
+    a.dz = c.dz_lut;
+    a.inv_dz = 1.0 / c.dz_lut;
+    a.zmax = c.opts.z_max;
+    a.dlnlam = c.dlnlam;
+    a.logage = c.d_logage;
+    a.einh = c.d_einh;
+    a.bwidth = c.d_bwidth;
+    a.zedge = c.d_zedge;
+    a.tlut = c.d_tlut;
+    a.glut = c.d_glut;
+    a.wmul = c.d_wmul;
+    a.w32 = c.d_w32;
+    a.whi = c.d_whi;
+    a.wlo = c.d_wlo;
+    a.aux = c.d_aux;
+    a.magoff = c.d_magoff;
+    a.err = c.d_err;
+    return a;
+}
+
+cudaError_t launch_weights_vjp(const Ctx &c, const float *params, int64_t G_stride, int64_t g_begin, int64_t n,
+                               bool sorted, bool scaled, float *param_bar, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    WArgs a = make_wargs(c, params, G_stride, g_begin, n);
+    a.perm = sorted ? c.d_perm : nullptr;
+    a.wmul = c.d_wmul_d;
+    const int threads = 256, warps = threads / 32;
+    const size_t smem = weights_vjp_smem_per_warp(c.n_t, c.n_age) * warps;
+    cudaFuncSetAttribute(weights_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    weights_vjp_kernel<<<(unsigned)((n + warps - 1) / warps), threads, smem, s>>>(a, c.d_w32, scaled ? 1 : 0,
+                                                                                 param_bar);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_weights(const Ctx &c, int mode, const float *params, int64_t G_stride,

@@ -1,0 +1,133 @@
+"""Gradient parity: dsps_photometry_vjp (through the C ABI) against the FP64
+oracle's analytic adjoint, itself pinned by central differences in
+test_oracle_pins.py.  Tolerance per galaxy and parameter:
+|g - g_oracle| <= 1e-3 * max(|g_oracle|, f * max_k |g_oracle[k]|), a 1e-3
+relative bound with an absolute floor for components near zero: f = 1e-3 for
+the FP32 form and f = 1e-2 for the split-bf16 form, whose products carry a
+relative error of about 2^-16 = 1.5e-5 (so its floor, 1e-5 of the largest
+component, is one unit roundoff of that arithmetic)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_06830_gb300 import synth
+
+import _util
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(kind, sfh_model, **kw):
+    from paper_2112_06830_gb300 import dsps
+    return dsps.Context(_util.ssp(kind), sfh_model=sfh_model, **kw)
+
+
+FLOOR = {0: 1e-3, 1: 1e-2}
+
+
+def _check(pb, ref, prec):
+    scale = np.maximum(np.abs(ref), FLOOR[prec] * np.abs(ref).max(axis=0, keepdims=True))
+    rel = np.abs(pb - ref) / scale
+    return rel.max(), np.unravel_index(np.argmax(rel), rel.shape)
+
+
+@pytest.fixture(scope="module")
+def small():
+    c = _ctx("small", synth.SFH_DELAYED_TAU)
+    f = synth.make_filters(6)
+    return c, c.add_filters(f), oracle.Filters(f)
+
+
+@pytest.fixture(scope="module")
+def full():
+    c = _ctx("full", synth.SFH_DPL_QUENCH)
+    f = synth.make_filters(12)
+    return c, c.add_filters(f), oracle.Filters(f)
+
+
+def _vjp(ctx, sid, p32, mbar, prec):
+    mags, pb = ctx.photometry_vjp(torch.from_numpy(p32).cuda(), sid, torch.from_numpy(mbar.astype(np.float32)).cuda(),
+                                  precision=prec)
+    torch.cuda.synchronize()
+    return mags.cpu().numpy().astype(np.float64), pb.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vjp_small_matches_oracle(small, prec):
+    ctx, sid, F = small
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DELAYED_TAU, 64, 0))
+    mbar = np.random.default_rng(1).standard_normal((64, 6))
+    m, pb = _vjp(ctx, sid, p32, mbar, prec)
+    m_ref, pb_ref = oracle.mags_vjp(_util.oracle_grid("small", 0), F, p64, mbar)
+    err, where = _check(pb, pb_ref, prec)
+    print(f"small prec={prec}: max scaled gradient error {err:.2e} at {where}")
+    assert err <= 1e-3
+    assert np.abs(m - m_ref).max() <= (1e-4 if prec == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [1, 300])
+def test_vjp_full_grid_matches_oracle(full, prec, n):
+    ctx, sid, F = full
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, n, 1, start=3000))
+    mbar = np.random.default_rng(2).standard_normal((n, 12))
+    m, pb = _vjp(ctx, sid, p32, mbar, prec)
+    m_ref, pb_ref = oracle.mags_vjp(_util.oracle_grid("full", 1), F, p64, mbar)
+    err, where = _check(pb, pb_ref, prec)
+    print(f"full n={n} prec={prec}: max scaled gradient error {err:.2e} at {where}")
+    assert err <= 1e-3
+    assert np.abs(m - m_ref).max() <= (1e-4 if prec == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vjp_full_size_sampled(full, prec):
+    """1e5 galaxies; the oracle checks 24 of them."""
+    ctx, sid, F = full
+    G = 100_000
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, G, 3))
+    mbar = np.random.default_rng(3).standard_normal((G, 12))
+    m, pb = _vjp(ctx, sid, p32, mbar, prec)
+    assert np.isfinite(pb).all() and np.isfinite(m).all()
+    idx = np.unique(np.concatenate([[0, G - 1], np.random.default_rng(4).integers(0, G, 22)]))
+    _, pb_ref = oracle.mags_vjp(_util.oracle_grid("full", 1), F, p64[:, idx], mbar[idx])
+    err, where = _check(pb[:, idx], pb_ref, prec)
+    print(f"full 1e5 prec={prec}: sampled max scaled gradient error {err:.2e} at {where}")
+    assert err <= 1e-3
+
+
+def test_vjp_mags_equal_forward(full):
+    ctx, sid, _ = full
+    p32, _ = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, 500, 1, start=7000))
+    for prec in (0, 1):
+        m, _ = _vjp(ctx, sid, p32, np.ones((500, 12)), prec)
+        fwd = ctx.photometry(torch.from_numpy(p32).cuda(), sid, precision=prec).cpu().numpy()
+        np.testing.assert_allclose(m, fwd, atol=2e-6, rtol=0)
+
+
+def test_gradient_signs(full):
+    """More dust dims every band; a unit shift of logM moves every band by -2.5."""
+    ctx, sid, _ = full
+    p32, _ = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, 200, 1, start=9000))
+    for q in range(12):
+        mb = np.zeros((200, 12))
+        mb[:, q] = 1.0
+        _, pb = _vjp(ctx, sid, p32, mb, 1)
+        assert (pb[8] > 0).all()
+        np.testing.assert_allclose(pb[10], -2.5, rtol=1e-6)
+
+
+def test_autograd_function(full):
+    from paper_2112_06830_gb300 import autograd
+    ctx, sid, _ = full
+    p32, _ = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, 256, 1, start=11000))
+    params = torch.from_numpy(p32).cuda().requires_grad_(True)
+    target = autograd.photometry(ctx, params, sid).detach() + 0.05
+    loss = ((autograd.photometry(ctx, params, sid) - target) ** 2).sum()
+    loss.backward()
+    g = params.grad.detach()
+    mb = (2 * (ctx.photometry(params.detach(), sid) - target)).contiguous()
+    _, pb = ctx.photometry_vjp(params.detach(), sid, mb)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(g[:11], pb, rtol=0, atol=0)
+    assert (g[11] == 0).all()
