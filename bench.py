@@ -47,6 +47,8 @@ def _args():
     ap.add_argument("--n-gal", type=int, default=N_GAL)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4096)
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the Poisson request stream (the serving workload is 60 s)")
     return ap.parse_args()
 
 
@@ -131,6 +133,68 @@ def _cpu_baseline(sample: int):
     return {"value": sample * N_FILT / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
             "sample": f"first {sample} galaxies of the 1e5-galaxy workload (107x22x5994 grid, 12 filters), "
                       f"FP64, {cores} threads, {dt:.2f} s wall"}
+
+
+def _serve_bench(ctx, sids, seconds, rate=200.0):
+    """Poisson stream of populations through dsps_submit/dsps_poll (host buffers):
+    sizes lognormal(median 3e3, sigma_ln 1.5) clipped to [1e2, 2e5], 4/8/12
+    filters, 30% with gradients.  Latency is submit -> outputs in host memory."""
+    import threading
+
+    from paper_2112_06830_gb300 import dsps, synth
+    reqs = synth.make_request_stream(rate=rate, duration=seconds, seed=4)
+    pool = synth.make_population(synth.SFH_DPL_QUENCH, 400_000, 1, start=1_000_000).astype(np.float32)
+    mbar_pool = np.random.default_rng(9).standard_normal((400_000, 12)).astype(np.float32)
+    rng = np.random.default_rng(5)
+    starts = [int(rng.integers(0, pool.shape[1] - r.n_gal + 1)) for r in reqs]
+    done = []
+    lock = threading.Lock()
+    queue = []
+    finished_submitting = threading.Event()
+
+    def poller():
+        while True:
+            with lock:
+                item = queue.pop(0) if queue else None
+            if item is None:
+                if finished_submitting.is_set():
+                    with lock:
+                        if not queue:
+                            return
+                    continue
+                time.sleep(1e-4)
+                continue
+            r, t = item
+            rc = ctx.poll(t, timeout_us=120_000_000)
+            if rc != dsps.DSPS_OK:
+                raise RuntimeError(f"request failed: {rc}")
+            done.append((r, t.latency_us, time.perf_counter()))
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for r, s0 in zip(reqs, starts):
+        now = time.perf_counter() - t0
+        if r.t_arrive > now:
+            time.sleep(r.t_arrive - now)
+        p = pool[:, s0:s0 + r.n_gal]
+        mb = np.ascontiguousarray(mbar_pool[s0:s0 + r.n_gal, :r.n_filt]) if r.want_grad else None
+        t = ctx.submit(p, sids[r.n_filt], precision=dsps.DSPS_PREC_BF16X3, mag_bar=mb)
+        with lock:
+            queue.append((r, t))
+    finished_submitting.set()
+    th.join()
+    t_end = max(d[2] for d in done)
+    wall = t_end - t0
+    lat = np.array([d[1] for d in done]) * 1e-3
+    gal = sum(r.n_gal for r in reqs)
+    gmags = sum(r.n_gal * r.n_filt for r in reqs)
+    return {"requests": len(reqs), "seconds": round(seconds, 3), "rate_per_s": rate,
+            "galaxies": int(gal), "galaxies_per_s": gal / wall, "galaxy_mags_per_s": gmags / wall,
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "latency_ms_max": float(lat.max()),
+            "grad_fraction": float(np.mean([r.want_grad for r in reqs])),
+            "note": "offered load is the Poisson stream; throughput = work / (last completion - first arrival)"}
 
 
 def run_reference(a):
@@ -290,6 +354,13 @@ def run_ours(a):
     assert np.isfinite(h_mags.numpy()).all()
     assert ctx.device_error() == 0
 
+    serve = None
+    if a.serve_seconds > 0 and rank == 0:
+        sids = {N_FILT: sid}
+        for q in (4, 8):
+            sids[q] = ctx.add_filters(synth.make_filters(q))
+        serve = _serve_bench(ctx, sids, a.serve_seconds)
+
     if rank != 0:
         ctx.close()
         if dist is not None:
@@ -342,6 +413,7 @@ def run_ours(a):
         "e2e": {"value": ws * G * N_FILT / (ms_e2e * 1e-3), "unit": METRIC,
                 "h2d_bytes_per_step": int(params_h.nbytes), "d2h_bytes_per_step": int(G * N_FILT * 4)},
         "gpu_launches": int(total_launches),
+        "serve": serve,
         "clocks": clocks,
     }
     if not a.no_cpu_baseline:

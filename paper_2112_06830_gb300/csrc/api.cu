@@ -133,9 +133,8 @@ void free_ctx(Ctx *c) {
         cudaFree(fs.d_tab);
         cudaFree(fs.d_offq);
     }
-    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_edges, c->d_einh, c->d_bwidth, c->d_zedge,
-                    c->d_tlut, c->d_glut, c->d_w32, c->d_whi, c->d_wlo, c->d_aux, c->d_magoff, c->d_err,
-                    c->d_perm, c->d_gidx, c->d_hist, c->d_partial, c->d_stats, c->d_cq, c->d_shat,
+    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_edges, c->d_einh, c->d_bwidth,
+                    c->d_zedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->d_err, c->d_stats,
                     c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d};
     for (void *p : ptrs) cudaFree(p);
     for (auto &r : c->prof_recs) {
@@ -249,23 +248,15 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_einh, (size_t)c->n_age + 1));
     chk(dmalloc(&c->d_bwidth, (size_t)c->n_age));
     chk(dmalloc(&c->d_zedge, (size_t)c->n_z + 1));
-    chk(dmalloc(&c->d_w32, (size_t)c->chunk * c->K_pad));
-    chk(dmalloc(&c->d_whi, (size_t)c->chunk * c->K_pad));
-    chk(dmalloc(&c->d_wlo, (size_t)c->chunk * c->K_pad));
-    chk(dmalloc(&c->d_aux, (size_t)c->chunk * AUX_STRIDE));
-    chk(dmalloc(&c->d_magoff, (size_t)c->chunk));
+    chk(dmalloc(&c->d_ws_block, workspace_bytes(*c, c->chunk, false)));
     chk(dmalloc(&c->d_err, 1));
-    chk(dmalloc(&c->d_perm, (size_t)c->chunk));
-    chk(dmalloc(&c->d_gidx, (size_t)c->chunk));
-    chk(dmalloc(&c->d_hist, (size_t)ZSORT_BUCKETS));
-    chk(dmalloc(&c->d_partial, (size_t)TC_PARTS * c->chunk * 3 * QSTRIDE_MAX));
     chk(dmalloc(&c->d_stats, 1));
-    chk(dmalloc(&c->d_cq, (size_t)c->chunk * QSTRIDE_MAX));
     chk(dmalloc(&c->d_L_hi, (size_t)c->K_pad * c->N_pad));
     chk(dmalloc(&c->d_Ld32, (size_t)c->K_pad * c->N_pad));
     chk(dmalloc(&c->d_wmul_d, (size_t)c->K_pad));
     chk(dmalloc(&c->d_L_lo, (size_t)c->K_pad * c->N_pad));
     if (rc != DSPS_OK) { free_ctx(c); return rc; }
+    c->ws = workspace_carve(*c, c->d_ws_block, c->chunk, false);
 
     // Age-bin edges [Gyr]: log-midpoints, first edge at age 0, last half a step
     // above the last grid age (Sec. 3.1).
@@ -394,7 +385,7 @@ int dsps_weights(dsps_ctx *ctx, int64_t n_gal, const float *params, float *w_out
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !w_out))) return fail(DSPS_ERR_INVALID_ARG, "dsps_weights: bad argument%s");
     if (n_gal == 0) return DSPS_OK;
     DSPS_CUDA(cudaSetDevice(c->device));
-    DSPS_CUDA(launch_weights(*c, W_MSUN, params, n_gal, 0, n_gal, w_out, reinterpret_cast<cudaStream_t>(stream)));
+    DSPS_CUDA(launch_weights(*c, c->ws, W_MSUN, params, n_gal, 0, n_gal, w_out, reinterpret_cast<cudaStream_t>(stream)));
     return DSPS_OK;
 }
 

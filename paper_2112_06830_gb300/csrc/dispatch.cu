@@ -1,13 +1,129 @@
 // dispatch.cu -- per-call driver of the fused path: for each chunk of at most
-// ctx.chunk galaxies, the weights kernel writes the chunk's SSP weights (in the
+// w.cap galaxies, the weights kernel writes the chunk's SSP weights (in the
 // operand form of the chosen contraction) and per-galaxy epilogue constants,
 // then the photometry kernel contracts, attenuates, redshifts and integrates
-// them into magnitudes.  Both launches go to the caller's stream.
+// them into magnitudes (and, for the adjoint, the chain of vjp.cu).  All
+// launches go to the given stream.
 #include "dsps_internal.cuh"
 
 namespace dsps {
 
 void set_last_error(const char *msg);
+
+namespace {
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+size_t workspace_bytes(const Ctx &c, int64_t rows, bool adjoint) {
+    const size_t R = (size_t)rows;
+    size_t b = al256(R * c.K_pad * 4) + 2 * al256(R * c.K_pad * 2) + al256(R * AUX_STRIDE * 4) + al256(R * 8) +
+               2 * al256(R * 4) + al256((size_t)ZSORT_BUCKETS * 4) + al256((size_t)TC_PARTS * R * 3 * QSTRIDE_MAX * 4) +
+               al256(R * QSTRIDE_MAX * 4);
+    if (adjoint) b += al256(R * c.N_pad * 4);
+    return b;
+}
+
+Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint) {
+    const size_t R = (size_t)rows;
+    unsigned char *p = static_cast<unsigned char *>(base);
+    auto take = [&](size_t bytes) {
+        void *q = p;
+        p += al256(bytes);
+        return q;
+    };
+    Workspace w;
+    w.cap = rows;
+    w.w32 = static_cast<float *>(take(R * c.K_pad * 4));
+    w.whi = static_cast<__nv_bfloat16 *>(take(R * c.K_pad * 2));
+    w.wlo = static_cast<__nv_bfloat16 *>(take(R * c.K_pad * 2));
+    w.aux = static_cast<float *>(take(R * AUX_STRIDE * 4));
+    w.magoff = static_cast<double *>(take(R * 8));
+    w.perm = static_cast<int *>(take(R * 4));
+    w.gidx = static_cast<int *>(take(R * 4));
+    w.hist = static_cast<int *>(take((size_t)ZSORT_BUCKETS * 4));
+    w.partial = static_cast<float *>(take((size_t)TC_PARTS * R * 3 * QSTRIDE_MAX * 4));
+    w.cq = static_cast<float *>(take(R * QSTRIDE_MAX * 4));
+    w.shat = adjoint ? take(R * c.N_pad * 4) : nullptr;
+    return w;
+}
+
+int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *params, const FilterSet &fs,
+                      int32_t precision, float *mags, cudaStream_t s, bool profile) {
+    Workspace w = w0;
+    w.stats = (profile && c->prof) ? c->d_stats : nullptr;
+    const bool prof = profile && c->prof;
+    for (int64_t g0 = 0; g0 < n_gal; g0 += w.cap) {
+        const int64_t n = n_gal - g0 < w.cap ? n_gal - g0 : w.cap;
+        cudaError_t e = cudaSuccess;
+        if (precision == DSPS_PREC_FP32) {
+            {
+                ProfScope ps(*c, 0, s, prof);
+                e = launch_weights(*c, w, W_OMEGA_F32, params, n_gal, g0, n, nullptr, s);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 1, s, prof);
+                e = launch_phot_simt(*c, w, fs, n, mags + g0 * fs.Q, s);
+            }
+        } else {
+            int parts = 0;
+            {
+                ProfScope ps(*c, 0, s, prof);
+                e = launch_zsort(*c, w, params + (int64_t)11 * n_gal + g0, n, s);
+                if (e == cudaSuccess) e = launch_weights(*c, w, W_OMEGA_BF16X2, params, n_gal, g0, n, nullptr, s, true);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 2, s, prof);
+                e = launch_phot_tc(*c, w, fs, n, &parts, s);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 0, s, prof);
+                e = launch_combine(*c, w, fs, n, parts, mags + g0 * fs.Q, s);
+            }
+        }
+        if (e != cudaSuccess) {
+            set_last_error(cudaGetErrorString(e));
+            return DSPS_ERR_CUDA;
+        }
+    }
+    return DSPS_OK;
+}
+
+int run_photometry_vjp_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *params, const FilterSet &fs,
+                          int32_t precision, const float *mag_bar, float *mags, float *param_bar, cudaStream_t s,
+                          bool profile) {
+    Workspace w = w0;
+    w.stats = (profile && c->prof) ? c->d_stats : nullptr;
+    const bool prof = profile && c->prof;
+    const bool tc = precision == DSPS_PREC_BF16X3;
+    for (int64_t g0 = 0; g0 < n_gal; g0 += w.cap) {
+        const int64_t n = n_gal - g0 < w.cap ? n_gal - g0 : w.cap;
+        cudaError_t e = cudaSuccess;
+        int parts = 1;
+        {
+            ProfScope ps(*c, 0, s, prof);
+            if (tc) e = launch_zsort(*c, w, params + (int64_t)11 * n_gal + g0, n, s);
+            if (e == cudaSuccess)
+                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, tc);
+        }
+        if (e == cudaSuccess) {
+            ProfScope ps(*c, tc ? 2 : 1, s, prof);
+            e = tc ? launch_phot_tc(*c, w, fs, n, &parts, s, true) : launch_phot_simt(*c, w, fs, n, nullptr, s, true);
+        }
+        if (e == cudaSuccess) {
+            ProfScope ps(*c, 3, s, prof);
+            e = launch_combine_grad(*c, w, fs, n, parts, tc, mag_bar + g0 * fs.Q, mags ? mags + g0 * fs.Q : nullptr,
+                                    param_bar, n_gal, g0, s);
+            if (e == cudaSuccess) e = launch_shat(*c, w, fs, n, tc, tc && c->opts.band_skip, s);
+            if (e == cudaSuccess) e = tc ? launch_vjp_tc(*c, w, fs, n, s) : launch_vjp_simt(*c, w, n, s);
+            if (e == cudaSuccess) e = launch_weights_vjp(*c, w, params, n_gal, g0, n, tc, tc, param_bar, s);
+        }
+        if (e != cudaSuccess) {
+            set_last_error(cudaGetErrorString(e));
+            return DSPS_ERR_CUDA;
+        }
+    }
+    return DSPS_OK;
+}
 
 int run_photometry(Ctx *c, int64_t n_gal, const float *params, int32_t set_id, int32_t precision, float *mags,
                    cudaStream_t s) {
@@ -25,42 +141,7 @@ int run_photometry(Ctx *c, int64_t n_gal, const float *params, int32_t set_id, i
     }
     if (n_gal == 0) return DSPS_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return DSPS_ERR_CUDA;
-    const FilterSet &fs = c->sets[set_id];
-    for (int64_t g0 = 0; g0 < n_gal; g0 += c->chunk) {
-        const int64_t n = n_gal - g0 < c->chunk ? n_gal - g0 : c->chunk;
-        cudaError_t e = cudaSuccess;
-        if (precision == DSPS_PREC_FP32) {
-            {
-                ProfScope ps(*c, 0, s);
-                e = launch_weights(*c, W_OMEGA_F32, params, n_gal, g0, n, nullptr, s);
-            }
-            if (e == cudaSuccess) {
-                ProfScope ps(*c, 1, s);
-                e = launch_phot_simt(*c, fs, n, mags + g0 * fs.Q, s);
-            }
-        } else {
-            int parts = 0;
-            {
-                ProfScope ps(*c, 0, s);
-                e = launch_zsort(*c, params + (int64_t)11 * n_gal + g0, n, s);
-                if (e == cudaSuccess) e = launch_weights(*c, W_OMEGA_BF16X2, params, n_gal, g0, n, nullptr, s,
-                                                         nullptr, true);
-            }
-            if (e == cudaSuccess) {
-                ProfScope ps(*c, 2, s);
-                e = launch_phot_tc(*c, fs, n, &parts, s);
-            }
-            if (e == cudaSuccess) {
-                ProfScope ps(*c, 0, s);
-                e = launch_combine(*c, fs, n, parts, mags + g0 * fs.Q, s);
-            }
-        }
-        if (e != cudaSuccess) {
-            set_last_error(cudaGetErrorString(e));
-            return DSPS_ERR_CUDA;
-        }
-    }
-    return DSPS_OK;
+    return run_photometry_ws(c, c->ws, n_gal, params, c->sets[set_id], precision, mags, s, true);
 }
 
 int run_photometry_vjp(Ctx *c, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
@@ -79,46 +160,18 @@ int run_photometry_vjp(Ctx *c, int64_t n_gal, const float *params, int32_t set_i
     }
     if (n_gal == 0) return DSPS_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return DSPS_ERR_CUDA;
-    if (!c->d_shat) {
+    if (!c->ws.shat) {
         // Adjoint work space, made on the first gradient call (FP32, or bf16 hi + lo).
-        cudaError_t e = cudaMalloc(&c->d_shat, (size_t)c->chunk * c->N_pad * 4);
-        if (e != cudaSuccess) {
-            c->d_shat = nullptr;
-            set_last_error(cudaGetErrorString(e));
-            return DSPS_ERR_CUDA;
-        }
-    }
-    const FilterSet &fs = c->sets[set_id];
-    const bool tc = precision == DSPS_PREC_BF16X3;
-    for (int64_t g0 = 0; g0 < n_gal; g0 += c->chunk) {
-        const int64_t n = n_gal - g0 < c->chunk ? n_gal - g0 : c->chunk;
-        cudaError_t e = cudaSuccess;
-        int parts = 1;
-        {
-            ProfScope ps(*c, 0, s);
-            if (tc) e = launch_zsort(*c, params + (int64_t)11 * n_gal + g0, n, s);
-            if (e == cudaSuccess)
-                e = launch_weights(*c, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, nullptr,
-                                   tc);
-        }
-        if (e == cudaSuccess) {
-            ProfScope ps(*c, tc ? 2 : 1, s);
-            e = tc ? launch_phot_tc(*c, fs, n, &parts, s, true) : launch_phot_simt(*c, fs, n, nullptr, s, nullptr, true);
-        }
-        if (e == cudaSuccess) {
-            ProfScope ps(*c, 3, s);
-            e = launch_combine_grad(*c, fs, n, parts, tc, mag_bar + g0 * fs.Q, mags ? mags + g0 * fs.Q : nullptr,
-                                    param_bar, n_gal, g0, s);
-            if (e == cudaSuccess) e = launch_shat(*c, fs, n, tc, tc && c->opts.band_skip, s);
-            if (e == cudaSuccess) e = tc ? launch_vjp_tc(*c, fs, n, s) : launch_vjp_simt(*c, n, s);
-            if (e == cudaSuccess) e = launch_weights_vjp(*c, params, n_gal, g0, n, tc, tc, param_bar, s);
-        }
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)c->chunk * c->N_pad * 4);
         if (e != cudaSuccess) {
             set_last_error(cudaGetErrorString(e));
             return DSPS_ERR_CUDA;
         }
+        c->ws.shat = p;
     }
-    return DSPS_OK;
+    return run_photometry_vjp_ws(c, c->ws, n_gal, params, c->sets[set_id], precision, mag_bar, mags, param_bar, s,
+                                 true);
 }
 
 }  // namespace dsps

@@ -51,6 +51,24 @@ struct FilterSet {
 
 struct Serve;  // request loop (serve.cu)
 
+// Per-launch work space of the photometry path (rows = galaxies of one chunk
+// or batch).  The context owns one (Ctx::ws); the request loop carves one per
+// in-flight batch out of its device arena; the allocation-free entry point
+// points one at its static array.
+struct Workspace {
+    int64_t cap = 0;                            // rows
+    float *w32 = nullptr;                       // [cap][K_pad] FP32 weights / adjoint output
+    __nv_bfloat16 *whi = nullptr, *wlo = nullptr;  // [cap][K_pad] split weights
+    float *aux = nullptr;                       // [cap][AUX_STRIDE]
+    double *magoff = nullptr;                   // [cap]
+    int *perm = nullptr, *gidx = nullptr;       // [cap]
+    int *hist = nullptr;                        // [ZSORT_BUCKETS]
+    float *partial = nullptr;                   // [TC_PARTS][cap][3 * QSTRIDE_MAX]
+    float *cq = nullptr;                        // [cap][QSTRIDE_MAX]
+    void *shat = nullptr;                       // [cap][N_pad] x 4 bytes (adjoint only)
+    unsigned long long *stats = nullptr;        // tensor-core tile counter, or nullptr
+};
+
 struct Ctx {
     int device = 0;
     dsps_opts opts{};
@@ -76,20 +94,11 @@ struct Ctx {
     int n_lut = 0;
     double dz_lut = 0;
 
-    // Work space (one chunk of galaxies).
+    // Work space of the direct calls (one chunk of galaxies; Shat made lazily).
     int64_t chunk = 0;                      // galaxies per chunk (multiple of 128)
-    float *d_w32 = nullptr;                 // [chunk][K_pad] fp32 weights
-    __nv_bfloat16 *d_whi = nullptr;         // [chunk][K_pad]
-    __nv_bfloat16 *d_wlo = nullptr;         // [chunk][K_pad]
-    float *d_aux = nullptr;                 // [chunk][AUX_STRIDE]
-    double *d_magoff = nullptr;             // [chunk]
-    int *d_perm = nullptr;                  // [chunk] sorted row -> galaxy (chunk-local)
-    int *d_gidx = nullptr;                  // [chunk] sorted row -> galaxy, written by the weights kernel
-    int *d_hist = nullptr;                  // [ZSORT_BUCKETS]
-    float *d_partial = nullptr;             // [TC_PARTS][chunk][QSTRIDE_MAX] partial filter sums
+    unsigned char *d_ws_block = nullptr;    // device block holding ws (without Shat)
+    Workspace ws;
     unsigned long long *d_stats = nullptr;  // [1] tensor-core tiles executed (profiling)
-    float *d_cq = nullptr;                  // [chunk][QSTRIDE_MAX] Nbar_q of the adjoint
-    void *d_shat = nullptr;                 // adjoint Shat: FP32 [chunk][N_pad] or bf16 hi, lo (lazy)
     float *d_Ld32 = nullptr;                // [K_pad][N_pad] metallicity-differenced block (FP32 adjoint)
     float *d_wmul_d = nullptr;              // [K_pad] 2^E'_k of the differenced rows
     __nv_bfloat16 *d_L_hi = nullptr;        // [K_pad][N_pad] differenced block, row-scaled hi (tensor adjoint)
@@ -127,8 +136,8 @@ struct ProfScope {
         }
         return e;
     }
-    ProfScope(Ctx &c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
-        if (!c.prof) return;
+    ProfScope(Ctx &c_, int kind_, cudaStream_t s_, bool on = true) : c(c_), kind(kind_), s(s_) {
+        if (!on || !c.prof) return;
         a = take();
         b = take();
         if (a && b) cudaEventRecord(a, s);
@@ -146,45 +155,52 @@ struct ProfScope {
 // ----------------------------------------------------------------------------
 enum WeightsMode { W_MSUN = 0, W_OMEGA_F32 = 1, W_OMEGA_BF16X2 = 2 };
 
-// Scratch of the FP32 form supplied by the caller of a launch instead of the
-// context's work space (nullptr: use the context's).
-struct Scratch {
-    float *w32;       // [rows][K_pad]
-    float *aux;       // [rows][AUX_STRIDE]
-    double *magoff;   // [rows]
-};
+// Bytes of a work space for `rows` galaxies (what = 1: forward only, 2: with adjoint).
+size_t workspace_bytes(const Ctx &c, int64_t rows, bool adjoint);
+// Carves a work space for `rows` galaxies out of [base, base + workspace_bytes).
+Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint);
 
-cudaError_t launch_weights(const Ctx &c, int mode, const float *params, int64_t G_stride,
-                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s,
-                           const Scratch *ws = nullptr, bool sorted = false);
+cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const float *params, int64_t G_stride,
+                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted = false);
 
-// Counting sort of the chunk's galaxies by redshift shift into ctx.d_perm.
-cudaError_t launch_zsort(const Ctx &c, const float *z, int64_t n, cudaStream_t s);
+// Counting sort of the chunk's galaxies by redshift shift into w.perm.
+cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *z, int64_t n, cudaStream_t s);
 float zsort_key_scale(const Ctx &c);
 // Sums the tensor-core kernel's per-part filter sums and writes magnitudes.
-cudaError_t launch_combine(const Ctx &c, const FilterSet &fs, int64_t n, int parts, float *mags, cudaStream_t s);
+cudaError_t launch_combine(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts, float *mags,
+                           cudaStream_t s);
 
 // grad: instead of magnitudes, writes the sums N, A, D per filter (see
 // epilogue.cuh) to ctx.d_partial as a single part.
-cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags,
-                             cudaStream_t s, const Scratch *ws = nullptr, bool grad = false);
+cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, float *mags,
+                             cudaStream_t s, bool grad = false);
 
 // Writes per-part filter sums to ctx.d_partial (sorted rows); returns the
 // number of parts through *parts.
-cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *parts, cudaStream_t s,
-                           bool grad = false);
+cudaError_t launch_phot_tc(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int *parts,
+                           cudaStream_t s, bool grad = false);
 
 cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp);
 
 // Adjoint (vjp.cu, vjp_tc.cu, weights.cu).
-cudaError_t launch_combine_grad(const Ctx &c, const FilterSet &fs, int64_t n, int parts, bool sorted,
-                                const float *mag_bar, float *mags, float *param_bar, int64_t G_stride,
+cudaError_t launch_combine_grad(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts,
+                                bool sorted, const float *mag_bar, float *mags, float *param_bar, int64_t G_stride,
                                 int64_t g_begin, cudaStream_t s);
-cudaError_t launch_shat(const Ctx &c, const FilterSet &fs, int64_t n, bool bf16, bool band, cudaStream_t s);
-cudaError_t launch_vjp_simt(const Ctx &c, int64_t n, cudaStream_t s);
-cudaError_t launch_vjp_tc(const Ctx &c, const FilterSet &fs, int64_t n, cudaStream_t s);
-cudaError_t launch_weights_vjp(const Ctx &c, const float *params, int64_t G_stride, int64_t g_begin, int64_t n,
-                               bool sorted, bool scaled, float *param_bar, cudaStream_t s);
+cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, bool bf16, bool band,
+                        cudaStream_t s);
+cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s);
+cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, cudaStream_t s);
+cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride,
+                               int64_t g_begin, int64_t n, bool sorted, bool scaled, float *param_bar,
+                               cudaStream_t s);
+
+// Whole photometry / adjoint of a population on one stream with one work space
+// (dispatch.cu); mags/param_bar are the caller's device pointers.
+int run_photometry_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
+                      int32_t precision, float *mags, cudaStream_t s, bool profile);
+int run_photometry_vjp_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
+                          int32_t precision, const float *mag_bar, float *mags, float *param_bar, cudaStream_t s,
+                          bool profile);
 
 // ----------------------------------------------------------------------------
 // Device helpers

@@ -176,29 +176,24 @@ ColConst make_col_const(const Ctx &c) {
     return cc;
 }
 
-cudaError_t launch_phot_simt(const Ctx &c, const FilterSet &fs, int64_t n, float *mags, cudaStream_t s,
-                             const Scratch *ws, bool grad) {
+cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, float *mags,
+                             cudaStream_t s, bool grad) {
     if (n <= 0) return cudaSuccess;
     SArgs a{};
-    a.W = c.d_w32;
+    a.W = w.w32;
     a.L = c.d_L32;
     a.K_pad = c.K_pad;
     a.N_pad = c.N_pad;
     a.Q = fs.Q;
     a.m_last = fs.m_rows - 1;
     a.n = n;
-    a.aux = c.d_aux;
-    a.magoff = c.d_magoff;
+    a.aux = w.aux;
+    a.magoff = w.magoff;
     a.tab = reinterpret_cast<const float4 *>(fs.d_tab);
     a.offq = fs.d_offq;
     a.cc = make_col_const(c);
     a.mags = mags;
-    if (ws) {
-        a.W = ws->w32;
-        a.aux = ws->aux;
-        a.magoff = ws->magoff;
-    }
-    a.partial = c.d_partial;
+    a.partial = w.partial;
     if (grad) {
         switch (fs.Q4) {
         case 1: return launch_q4<1, true>(a, n, s);

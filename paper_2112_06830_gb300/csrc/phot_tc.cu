@@ -330,18 +330,19 @@ cudaError_t launch_q4(const CUtensorMap &ah, const CUtensorMap &al, const CUtens
 
 }  // namespace
 
-cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *parts, cudaStream_t s, bool grad) {
+cudaError_t launch_phot_tc(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int *parts,
+                           cudaStream_t s, bool grad) {
     *parts = TC_PARTS;
     if (n <= 0) return cudaSuccess;
     if (fs.Q > QMAX) return cudaErrorInvalidValue;
     CUtensorMap ah, al, bh, bl;
-    if (!make_tmap(&ah, c.d_whi, (uint64_t)c.K_pad, (uint64_t)n, BM) ||
-        !make_tmap(&al, c.d_wlo, (uint64_t)c.K_pad, (uint64_t)n, BM) ||
+    if (!make_tmap(&ah, w.whi, (uint64_t)c.K_pad, (uint64_t)n, BM) ||
+        !make_tmap(&al, w.wlo, (uint64_t)c.K_pad, (uint64_t)n, BM) ||
         !make_tmap(&bh, c.d_Lt_hi, (uint64_t)c.K_pad, (uint64_t)c.N_pad, BN) ||
         !make_tmap(&bl, c.d_Lt_lo, (uint64_t)c.K_pad, (uint64_t)c.N_pad, BN))
         return cudaErrorInvalidValue;
     TArgs a{};
-    a.aux = c.d_aux;
+    a.aux = w.aux;
     a.tab = reinterpret_cast<const float4 *>(fs.d_tab);
     a.cc = make_col_const(c);
     a.m_last = fs.m_rows - 1;
@@ -355,8 +356,8 @@ cudaError_t launch_phot_tc(const Ctx &c, const FilterSet &fs, int64_t n, int *pa
     a.m_nz_hi = fs.m_nz_hi;
     a.i0_margin = (int)std::ceil(1.0 / zsort_key_scale(c)) + 1;
     a.n = n;
-    a.partial = c.d_partial;
-    a.tiles = c.prof ? c.d_stats : nullptr;
+    a.partial = w.partial;
+    a.tiles = w.stats;
     a.err = c.d_err;
     int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;
     if (grad) {

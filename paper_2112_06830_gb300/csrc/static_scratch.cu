@@ -98,15 +98,16 @@ extern "C" int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const f
         set_last_error(cudaGetErrorString(e));
         return DSPS_ERR_CUDA;
     }
-    Scratch ws;
+    Workspace ws;
+    ws.cap = cap;
     ws.w32 = reinterpret_cast<float *>(base);
     const size_t off_aux = align256((size_t)cap * c->K_pad * 4);
     ws.aux = reinterpret_cast<float *>(base + off_aux);
     ws.magoff = reinterpret_cast<double *>(base + off_aux + align256((size_t)cap * AUX_STRIDE * 4));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const FilterSet &fs = c->sets[set_id];
-    e = launch_weights(*c, W_OMEGA_F32, params, n_gal, 0, n_gal, nullptr, s, &ws);
-    if (e == cudaSuccess) e = launch_phot_simt(*c, fs, n_gal, mags, s, &ws);
+    e = launch_weights(*c, ws, W_OMEGA_F32, params, n_gal, 0, n_gal, nullptr, s);
+    if (e == cudaSuccess) e = launch_phot_simt(*c, ws, fs, n_gal, mags, s);
     if (e != cudaSuccess) {
         set_last_error(cudaGetErrorString(e));
         return DSPS_ERR_CUDA;

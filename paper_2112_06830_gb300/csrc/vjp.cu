@@ -192,32 +192,34 @@ VjpBand make_vjp_band(const Ctx &c, const FilterSet &fs, bool band) {
     return b;
 }
 
-cudaError_t launch_combine_grad(const Ctx &c, const FilterSet &fs, int64_t n, int parts, bool sorted,
-                                const float *mag_bar, float *mags, float *param_bar, int64_t G_stride,
+cudaError_t launch_combine_grad(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts,
+                                bool sorted, const float *mag_bar, float *mags, float *param_bar, int64_t G_stride,
                                 int64_t g_begin, cudaStream_t s) {
+    (void)c;
     if (n <= 0) return cudaSuccess;
     combine_grad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        c.d_partial, parts, n, 4 * fs.Q4, fs.Q, c.d_magoff, fs.d_offq, sorted ? c.d_gidx : nullptr, c.d_aux, mag_bar,
-        mags, param_bar, G_stride, g_begin, c.d_cq);
+        w.partial, parts, n, 4 * fs.Q4, fs.Q, w.magoff, fs.d_offq, sorted ? w.gidx : nullptr, w.aux, mag_bar,
+        mags, param_bar, G_stride, g_begin, w.cq);
     return cudaGetLastError();
 }
 
-cudaError_t launch_shat(const Ctx &c, const FilterSet &fs, int64_t n, bool bf16, bool band, cudaStream_t s) {
+cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, bool bf16, bool band,
+                        cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const VjpBand b = make_vjp_band(c, fs, band);
     const ColConst cc = make_col_const(c);
     const auto *tab = reinterpret_cast<const float4 *>(fs.d_tab);
     const int m_last = fs.m_rows - 1;
-    float *o32 = reinterpret_cast<float *>(c.d_shat);
-    auto *ohi = reinterpret_cast<__nv_bfloat16 *>(c.d_shat);
-    __nv_bfloat16 *olo = ohi + (size_t)c.chunk * c.N_pad;
+    float *o32 = reinterpret_cast<float *>(w.shat);
+    auto *ohi = reinterpret_cast<__nv_bfloat16 *>(w.shat);
+    __nv_bfloat16 *olo = ohi + (size_t)w.cap * c.N_pad;
     const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
 #define DSPS_SHAT(Q4)                                                                                      \
     if (bf16)                                                                                              \
-        shat_kernel<Q4, true><<<blocks, 256, 0, s>>>(c.d_aux, c.d_cq, tab, m_last, cc, n, c.N_pad, b, o32, \
+        shat_kernel<Q4, true><<<blocks, 256, 0, s>>>(w.aux, w.cq, tab, m_last, cc, n, c.N_pad, b, o32, \
                                                      ohi, olo);                                            \
     else                                                                                                   \
-        shat_kernel<Q4, false><<<blocks, 256, 0, s>>>(c.d_aux, c.d_cq, tab, m_last, cc, n, c.N_pad, b, o32, \
+        shat_kernel<Q4, false><<<blocks, 256, 0, s>>>(w.aux, w.cq, tab, m_last, cc, n, c.N_pad, b, o32, \
                                                       ohi, olo);
     switch (fs.Q4) {
     case 1: DSPS_SHAT(1) break;
@@ -229,11 +231,11 @@ cudaError_t launch_shat(const Ctx &c, const FilterSet &fs, int64_t n, bool bf16,
     return cudaGetLastError();
 }
 
-cudaError_t launch_vjp_simt(const Ctx &c, int64_t n, cudaStream_t s) {
+cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     dim3 grid((unsigned)((n + BM - 1) / BM), (unsigned)((c.K_pad + BN - 1) / BN));
-    vjp_simt_kernel<<<grid, THREADS, 0, s>>>(reinterpret_cast<const float *>(c.d_shat), c.d_Ld32, n, c.K_pad,
-                                             c.N_pad, c.d_w32);
+    vjp_simt_kernel<<<grid, THREADS, 0, s>>>(reinterpret_cast<const float *>(w.shat), c.d_Ld32, n, c.K_pad,
+                                             c.N_pad, w.w32);
     return cudaGetLastError();
 }
 

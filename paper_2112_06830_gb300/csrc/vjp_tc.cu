@@ -201,10 +201,10 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
 
 }  // namespace
 
-cudaError_t launch_vjp_tc(const Ctx &c, const FilterSet &fs, int64_t n, cudaStream_t s) {
+cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const auto *hi = reinterpret_cast<const __nv_bfloat16 *>(c.d_shat);
-    const __nv_bfloat16 *lo = hi + (size_t)c.chunk * c.N_pad;
+    const auto *hi = reinterpret_cast<const __nv_bfloat16 *>(w.shat);
+    const __nv_bfloat16 *lo = hi + (size_t)w.cap * c.N_pad;
     CUtensorMap ah, al, bh, bl;
     if (!make_tmap(&ah, hi, (uint64_t)c.N_pad, (uint64_t)n, BM) ||
         !make_tmap(&al, lo, (uint64_t)c.N_pad, (uint64_t)n, BM) ||
@@ -212,7 +212,7 @@ cudaError_t launch_vjp_tc(const Ctx &c, const FilterSet &fs, int64_t n, cudaStre
         !make_tmap(&bl, c.d_L_lo, (uint64_t)c.N_pad, (uint64_t)c.K_pad, BN))
         return cudaErrorInvalidValue;
     VArgs a{};
-    a.aux = c.d_aux;
+    a.aux = w.aux;
     a.band = make_vjp_band(c, fs, c.opts.band_skip != 0);
     a.n_mtiles = (int)((n + BM - 1) / BM);
     a.n_ktiles = (c.K_pad + BN - 1) / BN;
@@ -220,7 +220,7 @@ cudaError_t launch_vjp_tc(const Ctx &c, const FilterSet &fs, int64_t n, cudaStre
     a.N_pad = c.N_pad;
     a.K_pad = c.K_pad;
     a.n = n;
-    a.out = c.d_w32;
+    a.out = w.w32;
     a.err = c.d_err;
     const int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;
     cudaError_t e = cudaFuncSetAttribute(vjp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);

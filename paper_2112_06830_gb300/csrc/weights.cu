@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     }
 }
 
-WArgs make_wargs(const Ctx &c, const float *params, int64_t G_stride, int64_t g_begin, int64_t n) {
+WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride, int64_t g_begin, int64_t n) {
     WArgs a{};
     a.params = params;
     a.G_stride = G_stride;
@@ -501,77 +501,39 @@ WArgs make_wargs(const Ctx &c, const float *params, int64_t G_stride, int64_t g_
     a.tlut = c.d_tlut;
     a.glut = c.d_glut;
     a.wmul = c.d_wmul;
-    a.w32 = c.d_w32;
-    a.whi = c.d_whi;
-    a.wlo = c.d_wlo;
-    a.aux = c.d_aux;
-    a.magoff = c.d_magoff;
+    a.w32 = w.w32;
+    a.whi = w.whi;
+    a.wlo = w.wlo;
+    a.aux = w.aux;
+    a.magoff = w.magoff;
     a.err = c.d_err;
     return a;
 }
 
-cudaError_t launch_weights_vjp(const Ctx &c, const float *params, int64_t G_stride, int64_t g_begin, int64_t n,
-                               bool sorted, bool scaled, float *param_bar, cudaStream_t s) {
+cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride,
+                               int64_t g_begin, int64_t n, bool sorted, bool scaled, float *param_bar,
+                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    WArgs a = make_wargs(c, params, G_stride, g_begin, n);
-    a.perm = sorted ? c.d_perm : nullptr;
+    WArgs a = make_wargs(c, w, params, G_stride, g_begin, n);
+    a.perm = sorted ? w.perm : nullptr;
     a.wmul = c.d_wmul_d;
     const int threads = 256, warps = threads / 32;
     const size_t smem = weights_vjp_smem_per_warp(c.n_t, c.n_age) * warps;
     cudaFuncSetAttribute(weights_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    weights_vjp_kernel<<<(unsigned)((n + warps - 1) / warps), threads, smem, s>>>(a, c.d_w32, scaled ? 1 : 0,
+    weights_vjp_kernel<<<(unsigned)((n + warps - 1) / warps), threads, smem, s>>>(a, w.w32, scaled ? 1 : 0,
                                                                                  param_bar);
     return cudaGetLastError();
 }
 
-cudaError_t launch_weights(const Ctx &c, int mode, const float *params, int64_t G_stride,
-                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, const Scratch *ws,
-                           bool sorted) {
+cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const float *params, int64_t G_stride,
+                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted) {
     if (n <= 0) return cudaSuccess;
-    WArgs a{};
-    a.params = params;
-    a.G_stride = G_stride;
-    a.g_begin = g_begin;
-    a.n = n;
-    a.n_age = c.n_age;
-    a.n_z = c.n_z;
-    a.K = c.K;
-    a.K_pad = c.K_pad;
-    a.n_t = c.n_t;
-    a.sfh_model = c.opts.sfh_model;
-    a.mdf_kernel = c.opts.mdf_kernel;
-    a.n_lut = c.n_lut;
-    a.t0 = c.t0;
-    a.h = (c.t1 - c.t0) / (c.n_t - 1);
-    a.inv_h = 1.0 / a.h;
-    a.dz = c.dz_lut;
-    a.inv_dz = 1.0 / c.dz_lut;
-    a.zmax = c.opts.z_max;
-    a.dlnlam = c.dlnlam;
-    a.logage = c.d_logage;
-    a.einh = c.d_einh;
-    a.bwidth = c.d_bwidth;
-    a.zedge = c.d_zedge;
-    a.tlut = c.d_tlut;
-    a.glut = c.d_glut;
-    a.wmul = c.d_wmul;
+    WArgs a = make_wargs(c, w, params, G_stride, g_begin, n);
     a.w_msun = w_msun;
-    a.w32 = c.d_w32;
-    a.whi = c.d_whi;
-    a.wlo = c.d_wlo;
-    a.aux = c.d_aux;
-    a.magoff = c.d_magoff;
-    a.err = c.d_err;
-    if (ws) {
-        a.w32 = ws->w32;
-        a.aux = ws->aux;
-        a.magoff = ws->magoff;
-    }
-    a.perm = sorted ? c.d_perm : nullptr;
-    a.gidx = sorted ? c.d_gidx : nullptr;
+    a.perm = sorted ? w.perm : nullptr;
+    a.gidx = sorted ? w.gidx : nullptr;
     const int threads = 256, warps = threads / 32;
-    size_t per_warp = ((size_t)c.n_t * 16 + (size_t)(c.n_age + 1) * 8 + (size_t)c.n_age * 4 + 15) & ~(size_t)15;
-    size_t smem = per_warp * warps;
+    const size_t smem = weights_smem_per_warp(c.n_t, c.n_age) * warps;
     dim3 grid((unsigned)((n + warps - 1) / warps));
     switch (mode) {
     case W_MSUN:

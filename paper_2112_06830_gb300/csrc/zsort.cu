@@ -82,22 +82,24 @@ float zsort_key_scale(const Ctx &c) {
     return (float)(ZSORT_BUCKETS / (smax + 1.0));
 }
 
-cudaError_t launch_zsort(const Ctx &c, const float *z, int64_t n, cudaStream_t s) {
+cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *z, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const float inv_d = (float)(1.0 / c.dlnlam), ks = zsort_key_scale(c);
-    cudaError_t e = cudaMemsetAsync(c.d_hist, 0, ZSORT_BUCKETS * sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(w.hist, 0, ZSORT_BUCKETS * sizeof(int), s);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    zsort_hist_kernel<<<blocks, 256, 0, s>>>(z, n, inv_d, ks, c.d_hist);
-    zsort_scan_kernel<<<1, 1024, 0, s>>>(c.d_hist);
-    zsort_scatter_kernel<<<blocks, 256, 0, s>>>(z, n, inv_d, ks, c.d_hist, c.d_perm);
+    zsort_hist_kernel<<<blocks, 256, 0, s>>>(z, n, inv_d, ks, w.hist);
+    zsort_scan_kernel<<<1, 1024, 0, s>>>(w.hist);
+    zsort_scatter_kernel<<<blocks, 256, 0, s>>>(z, n, inv_d, ks, w.hist, w.perm);
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const Ctx &c, const FilterSet &fs, int64_t n, int parts, float *mags, cudaStream_t s) {
+cudaError_t launch_combine(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts, float *mags,
+                           cudaStream_t s) {
+    (void)c;
     if (n <= 0) return cudaSuccess;
-    combine_mags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_partial, parts, n, 4 * fs.Q4, fs.Q,
-                                                                      c.d_magoff, fs.d_offq, c.d_gidx, mags);
+    combine_mags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.partial, parts, n, 4 * fs.Q4, fs.Q,
+                                                                      w.magoff, fs.d_offq, w.gidx, mags);
     return cudaGetLastError();
 }
 

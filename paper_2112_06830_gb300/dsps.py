@@ -313,3 +313,38 @@ class Context:
 
     def device_error(self, stream=None):
         return dsps_device_error(self.handle, _stream_handle(stream))
+
+    # ---- request loop (host buffers) ----
+    def submit(self, params, set_id, precision=DSPS_PREC_BF16X3, mag_bar=None):
+        """Queues a population held in host memory (numpy float32 [12, G]); the
+        returned Ticket keeps the host buffers alive until it is polled."""
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        G = params.shape[1]
+        Q = self.n_filt[set_id]
+        t = Ticket(params, np.empty((G, Q), dtype=np.float32))
+        req = dsps_request(G, params.ctypes.data, set_id, precision, 0, None, t.mags.ctypes.data, None)
+        if mag_bar is not None:
+            t.mag_bar = np.ascontiguousarray(mag_bar, dtype=np.float32).reshape(G, Q)
+            t.param_bar = np.empty((DSPS_NGRAD, G), dtype=np.float32)
+            req.want_grad = 1
+            req.mag_bar = t.mag_bar.ctypes.data
+            req.param_bar = t.param_bar.ctypes.data
+        t.id = dsps_submit(self.handle, req)
+        return t
+
+    def poll(self, ticket, timeout_us=0):
+        """DSPS_OK (outputs ready in ticket.mags / ticket.param_bar) or DSPS_PENDING."""
+        rc, lat = dsps_poll(self.handle, ticket.id, timeout_us)
+        if rc == DSPS_OK:
+            ticket.latency_us = lat
+        return rc
+
+
+class Ticket:
+    def __init__(self, params, mags):
+        self.params = params
+        self.mags = mags
+        self.mag_bar = None
+        self.param_bar = None
+        self.id = None
+        self.latency_us = None
