@@ -117,6 +117,21 @@ def _dist():
     return ws, rank, local
 
 
+def shard_start(rank: int, n_per_rank: int) -> int:
+    """Weak scaling: rank r owns galaxies [r n, (r + 1) n) of the population."""
+    return rank * n_per_rank
+
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time (the job's time); identity without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _cpu_baseline(sample: int):
     """The FP64 oracle as it stands, on all host cores, over a bounded sample of
     the same workload."""
@@ -252,7 +267,7 @@ def run_ours(a):
     ssp = synth.make_ssp(synth.FULL_GRID, 1)
     ctx = dsps.Context(ssp, sfh_model=synth.SFH_DPL_QUENCH, device=local)
     sid = ctx.add_filters(synth.make_filters(N_FILT))
-    params_h = synth.make_population(synth.SFH_DPL_QUENCH, G, 1, start=rank * G).astype(np.float32)
+    params_h = synth.make_population(synth.SFH_DPL_QUENCH, G, 1, start=shard_start(rank, G)).astype(np.float32)
     d_params = torch.from_numpy(params_h).cuda()
     d_mags = torch.empty((G, N_FILT), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
@@ -283,11 +298,7 @@ def run_ours(a):
         clocks = sampler.stop() if sampler else None
         dsps.dsps_profile_enable(c.handle, False)
         prof = dsps.dsps_profile_read(c.handle)
-        ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs])), dist, "cuda")
         return ms, prof, clocks
 
     sampler = ClockSampler(local) if rank == 0 else None
@@ -316,12 +327,7 @@ def run_ours(a):
             grad_step(prec)
             e1.record(stream)
         barrier()
-        ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs])), dist, "cuda")
 
     ms_grad_tc = timed_grad(dsps.DSPS_PREC_BF16X3)
     ms_grad_fp32 = timed_grad(dsps.DSPS_PREC_FP32)
@@ -346,11 +352,7 @@ def run_ours(a):
         e2e_step()
         e1.record(stream)
     barrier()
-    ms_e2e = float(np.mean([e0.elapsed_time(e1) for e0, e1 in e_evs]))
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(float(np.mean([e0.elapsed_time(e1) for e0, e1 in e_evs])), dist, "cuda")
     assert np.isfinite(h_mags.numpy()).all()
     assert ctx.device_error() == 0
 

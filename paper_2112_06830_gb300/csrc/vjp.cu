@@ -68,22 +68,36 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const float
     float nb[4 * Q4];
 #pragma unroll
     for (int q = 0; q < 4 * Q4; ++q) nb[q] = q < band.Q ? cq[r * QSTRIDE_MAX + q] : 0.f;
-    for (int col = kb0 * 32 + lane; col < kb1 * 32; col += 32) {
+    // Grid indices col + i0 - 1 .. col + i0 + 2 are table rows col + i0 .. col +
+    // i0 + 3.  For the 32 columns of one pass the warp needs 35 consecutive
+    // rows: each lane reduces its own row (and lanes 0..2 the last three), the
+    // neighbours' come by shuffles.
+    for (int col0 = kb0 * 32; col0 < kb1 * 32; col0 += 32) {
+        const int col = col0 + lane;
+        float own = 0.f, extra = 0.f;
+        if (rc.valid) {
+            const float4 *tr = tab + (size_t)min(col + rc.i0, m_last) * Q4;
+            const float4 *te = tab + (size_t)min(col + rc.i0 + 32, m_last) * Q4;
+#pragma unroll
+            for (int qq = 0; qq < Q4; ++qq) {
+                const float4 t = __ldg(tr + qq);
+                own = fmaf(nb[4 * qq + 0], t.x, fmaf(nb[4 * qq + 1], t.y, fmaf(nb[4 * qq + 2], t.z, fmaf(nb[4 * qq + 3], t.w, own))));
+                if (lane < 3) {
+                    const float4 x = __ldg(te + qq);
+                    extra = fmaf(nb[4 * qq + 0], x.x, fmaf(nb[4 * qq + 1], x.y, fmaf(nb[4 * qq + 2], x.z, fmaf(nb[4 * qq + 3], x.w, extra))));
+                }
+            }
+        }
+        float cm[4];
+        cm[0] = own;
+#pragma unroll
+        for (int d = 1; d < 4; ++d) {
+            const float a1 = __shfl_sync(0xffffffffu, own, (lane + d) & 31);
+            const float a2 = __shfl_sync(0xffffffffu, extra, (lane + d - 32) & 31);
+            cm[d] = lane + d < 32 ? a1 : a2;
+        }
         float sh = 0.f;
         if (rc.valid) {
-            // grid indices col + i0 - 1 .. col + i0 + 2 are table rows col + i0 .. col + i0 + 3
-            float cm[4];
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                const float4 *tr = tab + (size_t)min(col + rc.i0 + d, m_last) * Q4;
-                float acc = 0.f;
-#pragma unroll
-                for (int qq = 0; qq < Q4; ++qq) {
-                    const float4 t = __ldg(tr + qq);
-                    acc = fmaf(nb[4 * qq + 0], t.x, fmaf(nb[4 * qq + 1], t.y, fmaf(nb[4 * qq + 2], t.z, fmaf(nb[4 * qq + 3], t.w, acc))));
-                }
-                cm[d] = acc;
-            }
             const float ell = fmaf((float)col, cc.dell, cc.ell0);
             const float F = exp2f(rc.alpha * exp2f(rc.beta * ell));
             sh = col_kappa(cc, col) * F *

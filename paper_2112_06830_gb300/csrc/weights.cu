@@ -395,23 +395,54 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     const float inv_sig = 1.f / sig;
     const int nz = a.n_z;
     float mu_bar = 0.f, sig_bar = 0.f, slope_bar = 0.f;
-    for (int k = lane; k < a.K && valid; k += 32) {
-        const int i = k / nz, e = k - i * nz;
-        float wd = what[gi * a.K_pad + k];
-        if (scaled) wd *= __ldg(a.wmul + k);
-        const float xl = __ldg(a.logage + i) - 9.f;
-        if (e == 0) {
-            atomicAdd(fracbar + i, wd);
-            continue;
+    // Each lane takes runs of 8 consecutive bins (coalesced float4 loads); the
+    // row sum dLoss/dfrac_i is flushed with one shared atomic per row change.
+    for (int k0 = 8 * lane; k0 < a.K && valid; k0 += 256) {
+        int i = k0 / nz, e = k0 - i * nz;
+        const float4 *wp = reinterpret_cast<const float4 *>(what + gi * a.K_pad + k0);
+        float4 wa = wp[0], wb4 = wp[1];
+        float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb4.x, wb4.y, wb4.z, wb4.w};
+        if (scaled) {
+            const float4 *mp = reinterpret_cast<const float4 *>(a.wmul + k0);
+            const float4 ma = __ldg(mp), mb = __ldg(mp + 1);
+            const float mv[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) wv[c] *= mv[c];
         }
-        const float u = (__ldg(a.zedge + e) - fmaf(p[7], xl, p[5])) * inv_sig;
-        const float sv = mdf_s(a.mdf_kernel, u);
-        const float tail = u > 0.f ? -sv : 1.f - sv;
-        atomicAdd(fracbar + i, wd * tail);
-        const float t = frac[i] * wd * mdf_pdf(a.mdf_kernel, u) * inv_sig;
-        mu_bar += t;
-        sig_bar = fmaf(t, u, sig_bar);
-        slope_bar = fmaf(t, xl, slope_bar);
+        float xl = __ldg(a.logage + i) - 9.f;
+        float mu_i = fmaf(p[7], xl, p[5]);
+        float fr = frac[i];
+        float fb = 0.f;
+        bool open = false;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (k0 + c >= a.K) break;
+            const float wd = wv[c];
+            if (e == 0) {
+                fb += wd;
+            } else {
+                const float u = (__ldg(a.zedge + e) - mu_i) * inv_sig;
+                const float sv = mdf_s(a.mdf_kernel, u);
+                fb = fmaf(wd, u > 0.f ? -sv : 1.f - sv, fb);
+                const float t = fr * wd * mdf_pdf(a.mdf_kernel, u) * inv_sig;
+                mu_bar += t;
+                sig_bar = fmaf(t, u, sig_bar);
+                slope_bar = fmaf(t, xl, slope_bar);
+            }
+            open = true;
+            if (++e == nz) {
+                atomicAdd(fracbar + i, fb);
+                fb = 0.f;
+                open = false;
+                e = 0;
+                if (++i < a.n_age) {
+                    xl = __ldg(a.logage + i) - 9.f;
+                    mu_i = fmaf(p[7], xl, p[5]);
+                    fr = frac[i];
+                }
+            }
+        }
+        if (open) atomicAdd(fracbar + i, fb);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
