@@ -52,6 +52,24 @@ def _args():
     return ap.parse_args()
 
 
+def _traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    if the kernel's sources changed since that capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    h = hashlib.sha256()
+    for f in d["source_files"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != d["source_sha256"]:
+        return None
+    return d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -390,6 +408,8 @@ def run_ours(a):
                 "dense_equivalent_tflops": dense_flops / (per_launch_ms * 1e-3) / 1e12}
 
     roof = tc_roofline(prof_tc)
+    roof["traffic"] = _traffic("phot_tc_kernel")
+    roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof_dense = tc_roofline(prof_dense)
     total_launches = sum(v[0] for k, v in prof_tc.items() if k != "tc_tiles")
     value = ws * G * N_FILT / (ms_tc * 1e-3)
