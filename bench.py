@@ -395,23 +395,24 @@ def run_ours(a):
     def tc_roofline(prof):
         launches, kms = prof[2]
         per_launch_ms = kms / max(launches, 1)
-        tiles = prof["tc_tiles"] / max(launches, 1)
-        # bf16x3: three bf16 products per multiply-add of the contraction; each
-        # 128 x 256 tile runs the whole (unpadded) K = n_age * n_z
-        exec_flops = tiles * 128 * 256 * K * 2.0 * 3
+        kblocks = prof["tc_kblocks"] / max(launches, 1)
+        # bf16x3: three bf16 products per multiply-add of the contraction, each
+        # executed 128 x 256 x 32 block (only the K blocks a tile's non-zero
+        # weights fill, only the wavelength tiles inside its filter band)
+        exec_flops = kblocks * 128 * 256 * 32 * 2.0 * 3
         dense_flops = 3 * 2.0 * K * N * G
         return {"bound": "tensor", "achieved": exec_flops / (per_launch_ms * 1e-3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "frac": exec_flops / (per_launch_ms * 1e-3) / 1e12 / peak, "traffic": None,
                 "kernel": "phot_tc_kernel (split-bf16 tcgen05 contraction + fused epilogue)",
                 "peak_source": f"{peak_src} bf16 burst",
-                "ms_per_launch": per_launch_ms, "tiles_per_launch": tiles,
+                "ms_per_launch": per_launch_ms, "kblocks_per_launch": kblocks,
                 "dense_equivalent_tflops": dense_flops / (per_launch_ms * 1e-3) / 1e12}
 
     roof = tc_roofline(prof_tc)
     roof["traffic"] = _traffic("phot_tc_kernel")
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof_dense = tc_roofline(prof_dense)
-    total_launches = sum(v[0] for k, v in prof_tc.items() if k != "tc_tiles")
+    total_launches = sum(v[0] for k, v in prof_tc.items() if k != "tc_kblocks")
     value = ws * G * N_FILT / (ms_tc * 1e-3)
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,

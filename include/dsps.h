@@ -235,7 +235,7 @@ int dsps_device_error(dsps_ctx *ctx, dsps_stream_t stream);
 typedef struct {
     int64_t launches[DSPS_PROF_KINDS];
     double ms[DSPS_PROF_KINDS];
-    int64_t tc_tiles;          /* 128 x 256 x K_pad tensor-core tiles executed */
+    int64_t tc_kblocks;        /* 128 x 256 x 32 split-bf16 tensor-core block products executed */
 } dsps_profile_t;
 int dsps_profile_enable(dsps_ctx *ctx, int32_t enable);
 int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out);

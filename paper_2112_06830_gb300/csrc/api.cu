@@ -236,6 +236,9 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     c->lnlam0 = std::log(g->lam[0]);
     c->dlnlam = dl;
     c->chunk = (opts.max_chunk + 127) / 128 * 128;
+    c->sort_xmid = (float)(0.5 * (g->log_age_yr[0] + g->log_age_yr[g->n_age - 1]) - 9.0);
+    c->sort_mu_lo = (float)g->lgz[0];
+    c->sort_mu_scale = g->n_z > 1 ? (float)(ZSORT_MUBINS / (g->lgz[g->n_z - 1] - g->lgz[0])) : 0.f;
 
     int rc = DSPS_OK;
     auto chk = [&](int r) { if (rc == DSPS_OK) rc = r; };
@@ -460,10 +463,10 @@ int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out) {
         c->ev_pool.push_back(r.b);
     }
     c->prof_recs.clear();
-    unsigned long long tiles = 0;
-    if (cudaMemcpy(&tiles, c->d_stats, sizeof tiles, cudaMemcpyDeviceToHost) == cudaSuccess) {
-        out->tc_tiles = (int64_t)tiles;
-        cudaMemset(c->d_stats, 0, sizeof tiles);
+    unsigned long long kblocks = 0;
+    if (cudaMemcpy(&kblocks, c->d_stats, sizeof kblocks, cudaMemcpyDeviceToHost) == cudaSuccess) {
+        out->tc_kblocks = (int64_t)kblocks;
+        cudaMemset(c->d_stats, 0, sizeof kblocks);
     }
     return rc;
 }

@@ -18,7 +18,7 @@ size_t workspace_bytes(const Ctx &c, int64_t rows, bool adjoint) {
     const size_t R = (size_t)rows;
     size_t b = al256(R * c.K_pad * 4) + 2 * al256(R * c.K_pad * 2) + al256(R * AUX_STRIDE * 4) + al256(R * 8) +
                2 * al256(R * 4) + al256((size_t)ZSORT_BUCKETS * 4) + al256((size_t)TC_PARTS * R * 3 * QSTRIDE_MAX * 4) +
-               al256(R * QSTRIDE_MAX * 4);
+               al256(R * QSTRIDE_MAX * 4) + al256((R / 128 + 1) * sizeof(int4)) + al256(sizeof(int));
     if (adjoint) b += al256(R * c.N_pad * 4);
     return b;
 }
@@ -43,6 +43,8 @@ Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint) 
     w.hist = static_cast<int *>(take((size_t)ZSORT_BUCKETS * 4));
     w.partial = static_cast<float *>(take((size_t)TC_PARTS * R * 3 * QSTRIDE_MAX * 4));
     w.cq = static_cast<float *>(take(R * QSTRIDE_MAX * 4));
+    w.trange = static_cast<int4 *>(take((R / 128 + 1) * sizeof(int4)));
+    w.sched = static_cast<int *>(take(sizeof(int)));
     w.shat = adjoint ? take(R * c.N_pad * 4) : nullptr;
     return w;
 }
@@ -68,7 +70,7 @@ int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *p
             int parts = 0;
             {
                 ProfScope ps(*c, 0, s, prof);
-                e = launch_zsort(*c, w, params + (int64_t)11 * n_gal + g0, n, s);
+                e = launch_zsort(*c, w, params, n_gal, g0, n, s);
                 if (e == cudaSuccess) e = launch_weights(*c, w, W_OMEGA_BF16X2, params, n_gal, g0, n, nullptr, s, true);
             }
             if (e == cudaSuccess) {
@@ -101,7 +103,7 @@ int run_photometry_vjp_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const floa
         int parts = 1;
         {
             ProfScope ps(*c, 0, s, prof);
-            if (tc) e = launch_zsort(*c, w, params + (int64_t)11 * n_gal + g0, n, s);
+            if (tc) e = launch_zsort(*c, w, params, n_gal, g0, n, s);
             if (e == cudaSuccess)
                 e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, tc);
         }

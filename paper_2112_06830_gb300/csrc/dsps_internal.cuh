@@ -21,7 +21,9 @@ constexpr int N_ALIGN = 256;     // wavelength padding: multiple of the 256-wide
 constexpr int MAX_NT = 1024;     // SFR time nodes
 constexpr int MAX_NAGE = 512;
 constexpr int AUX_STRIDE = 8;    // floats of per-galaxy epilogue constants
-constexpr int ZSORT_BUCKETS = 4096;  // redshift-sort buckets (multiple of 1024)
+constexpr int ZSORT_BUCKETS = 4096;  // sort buckets (multiple of 1024) = ZSORT_ZBINS x ZSORT_MUBINS
+constexpr int ZSORT_ZBINS = 16;      // coarse redshift-shift bins of the sort key
+constexpr int ZSORT_MUBINS = ZSORT_BUCKETS / ZSORT_ZBINS;  // mean-metallicity bins inside each
 constexpr int TC_PARTS = 4;      // work units per 128-galaxy tile in the tensor-core kernel
 constexpr int QSTRIDE_MAX = 16;  // floats per row of the partial filter sums
 
@@ -32,6 +34,29 @@ constexpr unsigned DERR_TIMEOUT = 2u;  // a kernel gave up on a bounded wait
 constexpr double AB0 = 1.13492e-13;     // Sec. 2.2, Eq. (restmag)
 constexpr double LAM_V = 5500.0;        // Sec. 3.4, Eq. (salim)
 constexpr double SIG_Q = 0.3;           // quench transition width [Gyr]
+
+// Order of the K = n_age * n_z axis.  The SSP block, dsps_weights and the FP32
+// and adjoint paths use the age-major k = i * n_z + j.  The tensor-core forward
+// operands (split weights and d_Lt_*) use the metallicity-major kz = j * n_age
+// + i: the metallicity kernel moves a galaxy's non-zero weights into one
+// contiguous run of kz (the triweight has compact support), so a tile of
+// galaxies with similar metallicity needs only the K blocks of that run.
+__host__ __device__ inline int kz_to_k(int kz, int n_age, int n_z) {
+    const int j = kz / n_age;
+    return (kz - j * n_age) * n_z + j;
+}
+__host__ __device__ inline int k_to_kz(int k, int n_age, int n_z) {
+    const int i = k / n_z;
+    return (k - i * n_z) * n_age + i;
+}
+
+// Per 128-row tile of sorted galaxies (Workspace::trange), reduced with
+// atomics by the weights kernel over the tile's valid rows:
+//   x, y  smallest / largest floor(s) (s = aux[.+2], the redshift shift)
+//   z, w  smallest / largest kz at which some row's split weights are non-zero
+// Empty tiles keep the initial {INT_MAX, INT_MIN, INT_MAX, INT_MIN}.
+constexpr int TRANGE_EMPTY_LO = 0x7fffffff;
+constexpr int TRANGE_EMPTY_HI = (int)0x80000000;
 
 // Per-galaxy epilogue constants (aux[g*AUX_STRIDE + .]):
 //   0 alpha = -0.4 log2(10) Av      (F = 2^(alpha u))
@@ -64,6 +89,8 @@ struct Workspace {
     int *perm = nullptr, *gidx = nullptr;       // [cap]
     int *hist = nullptr;                        // [ZSORT_BUCKETS]
     float *partial = nullptr;                   // [TC_PARTS][cap][3 * QSTRIDE_MAX]
+    int4 *trange = nullptr;                     // [cap/128 + 1] per sorted 128-row tile (ranges below)
+    int *sched = nullptr;                       // [1] work-unit counter of the tensor-core kernels
     float *cq = nullptr;                        // [cap][QSTRIDE_MAX]
     void *shat = nullptr;                       // [cap][N_pad] x 4 bytes (adjoint only)
     unsigned long long *stats = nullptr;        // tensor-core tile counter, or nullptr
@@ -76,12 +103,15 @@ struct Ctx {
     double t0 = 0, t1 = 0;
     double lnlam0 = 0, dlnlam = 0;
     int num_sms = 0;
+    // Sort key of the tensor-core path: mean metallicity at the middle log age,
+    // mu + slope * sort_xmid, binned from sort_mu_lo at sort_mu_scale bins per dex.
+    float sort_mu_lo = 0.f, sort_mu_scale = 0.f, sort_xmid = 0.f;
 
     // Resident SSP copies.
     float *d_L32 = nullptr;                 // [K_pad][N_pad] fp32 (SIMT path)
-    __nv_bfloat16 *d_Lt_hi = nullptr;       // [N_pad][K_pad] row-scaled hi (tensor path)
+    __nv_bfloat16 *d_Lt_hi = nullptr;       // [N_pad][K_pad] row-scaled hi, metallicity-major K (tensor path)
     __nv_bfloat16 *d_Lt_lo = nullptr;       // [N_pad][K_pad] row-scaled lo
-    float *d_wmul = nullptr;                // [K_pad] 2^E_k: weight multiplier of the scaled rows
+    float *d_wmul = nullptr;                // [K_pad] 2^E_k of the scaled rows, metallicity-major K
 
     // Grids and tables.
     float *d_logage = nullptr;              // [n_age] log10(age/yr)
@@ -163,9 +193,10 @@ Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint);
 cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const float *params, int64_t G_stride,
                            int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted = false);
 
-// Counting sort of the chunk's galaxies by redshift shift into w.perm.
-cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *z, int64_t n, cudaStream_t s);
-float zsort_key_scale(const Ctx &c);
+// Counting sort of the chunk's galaxies into w.perm by (coarse redshift shift,
+// mean metallicity); also resets w.trange.
+cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride, int64_t g_begin,
+                         int64_t n, cudaStream_t s);
 // Sums the tensor-core kernel's per-part filter sums and writes magnitudes.
 cudaError_t launch_combine(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts, float *mags,
                            cudaStream_t s);

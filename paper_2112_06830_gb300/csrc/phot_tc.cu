@@ -6,8 +6,12 @@
 //   S = W_hi L_hi + W_hi L_lo + W_lo L_hi     (bf16 operands, FP32 accumulate)
 // where W = omega * 2^E_k and L = L_ssp * 2^-E_k are split into bf16 hi + lo.
 //
-// Persistent CTAs (one per SM) walk 128-galaxy tiles; each tile sweeps all
-// 256-wide wavelength tiles.  Warp roles:
+// Persistent CTAs (one per SM) take work units -- a 128-galaxy tile and one of
+// TC_PARTS interleaved subsets of its wavelength tiles -- from a global counter
+// (tc::UnitRing), so that units of unequal cost balance across SMs; each tile sweeps the
+// 256-wide wavelength tiles inside its redshifted filter band, and contracts
+// only the K blocks (metallicity-major K) where some row's weights are non-zero
+// (tile_ranges).  Warp roles:
 //   warp 0      TMA producer: 4-stage ring of {W_hi, W_lo, L_hi, L_lo} K-slices
 //               (32 bf16 = 64 B rows, 64-byte swizzle), one mbarrier per stage.
 //   warp 1      TMEM allocator and single-thread MMA issuer: per K-slice six
@@ -49,32 +53,38 @@ constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + 
 
 struct TArgs {
     const float *aux;
+    const int4 *trange;             // per-tile ranges from the weights kernel
     const float4 *tab;
     ColConst cc;
     int m_last, n_mtiles, n_ntiles, kblocks, parts, n_units;
-    int band_skip, m_nz_lo, m_nz_hi, i0_margin;
+    int band_skip, m_nz_lo, m_nz_hi;
     int64_t n;
+    int *sched;                     // unit counter, zero at launch
     float *partial;                 // [parts][n][4*Q4]
-    unsigned long long *tiles;      // tiles executed (profiling)
+    unsigned long long *kblk;       // 128 x 256 x 32 block products executed (profiling)
     unsigned *err;
 };
 
-// Wavelength tiles [nt0, nt1) that galaxy tile mt needs: rows are sorted by
-// the redshift shift s, so the tile's shifts lie in [s(first row), s(last row)]
-// up to one sort bucket; a wavelength tile whose interpolation rows (grid
-// indices n + i0 - 1 .. n + i0 + 2) all fall outside the band [m_nz_lo, m_nz_hi]
-// of non-zero transmission contributes exactly zero and is skipped.
-__device__ __forceinline__ void tile_nrange(const TArgs &a, int mt, int &nt0, int &nt1) {
+// Wavelength tiles [nt0, nt1) and K blocks [kb0, kb1) that galaxy tile mt
+// needs, from the tile's exact ranges over its valid rows (trange: smallest and
+// largest floor(s), first and last non-zero kz).  A wavelength tile whose
+// interpolation rows (grid indices n + i0 - 1 .. n + i0 + 2) fall outside the
+// band [m_nz_lo, m_nz_hi] of non-zero transmission for every i0 of the tile,
+// and a K block where every row's weights are zero, contribute exact zeros and
+// are skipped.  A tile with no non-zero weight does no work.
+__device__ __forceinline__ void tile_ranges(const TArgs &a, int mt, int &nt0, int &nt1, int &kb0, int &kb1) {
     nt0 = 0;
     nt1 = a.n_ntiles;
+    kb0 = 0;
+    kb1 = a.kblocks;
     if (!a.band_skip) return;
-    const int64_t r0 = (int64_t)mt * BM;
-    const int64_t r1 = min(r0 + BM, a.n) - 1;
-    const int i0_lo = max((int)floorf(a.aux[r0 * AUX_STRIDE + 2]) - a.i0_margin, 0);
-    const int i0_hi = (int)floorf(a.aux[r1 * AUX_STRIDE + 2]) + a.i0_margin;
-    const int n_lo = a.m_nz_lo - i0_hi - 2;
-    const int n_hi = a.m_nz_hi - i0_lo + 1;
-    if (n_hi < 0 || a.m_nz_hi < a.m_nz_lo) { nt1 = nt0; return; }
+    const int4 r = a.trange[mt];
+    if (r.w < r.z || a.m_nz_hi < a.m_nz_lo) { nt1 = nt0; return; }
+    kb0 = r.z / BK;
+    kb1 = r.w / BK + 1;
+    const int n_lo = a.m_nz_lo - r.y - 2;
+    const int n_hi = a.m_nz_hi - r.x + 1;
+    if (n_hi < 0) { nt1 = nt0; return; }
     nt0 = n_lo <= 0 ? 0 : n_lo / BN;
     nt1 = min(a.n_ntiles, n_hi / BN + 1);
     if (nt1 < nt0) nt1 = nt0;
@@ -104,6 +114,10 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
     const uint32_t drain = smem_u32(bars + 2 * STAGES + 5);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 6);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    UnitRing ring;
+    ring.full0 = smem_u32(bars + 2 * STAGES + 8);
+    ring.empty0 = smem_u32(bars + 2 * STAGES + 8 + UNIT_RING);
+    ring.slot = reinterpret_cast<volatile int *>(bars + 2 * STAGES + 8 + 2 * UNIT_RING);
     float *comb = reinterpret_cast<float *>(sm + (size_t)STAGES * STAGE_BYTES + BAR_BYTES);
     const uint32_t sbase = smem_u32(sm);
 
@@ -120,6 +134,10 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
         }
         mbar_init(ebar, NUM_EPI_WARPS);
         mbar_init(drain, 1);
+        for (int i = 0; i < UNIT_RING; ++i) {
+            mbar_init(ring.full0 + 8 * i, 1);
+            mbar_init(ring.empty0 + 8 * i, 1 + NUM_EPI_WARPS);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -142,12 +160,15 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
             int armed[STAGES];
             for (int s = 0; s < STAGES; ++s) armed[s] = -1;
             bool ok = true;
-            for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+            while (ok) {
+                int u;
+                if (!ring_claim(ring, a.sched, a.n_units, u, abort_flag, a.err)) break;
+                if (u < 0) break;
                 const int mt = u / a.parts, part = u - mt * a.parts;
-                int nt0, nt1;
-                tile_nrange(a, mt, nt0, nt1);
+                int nt0, nt1, kb0, kb1;
+                tile_ranges(a, mt, nt0, nt1, kb0, kb1);
                 for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts)
-                    for (int kb = 0; kb < a.kblocks; ++kb) {
+                    for (int kb = kb0; kb < kb1; ++kb) {
                         if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                         const uint32_t fb = full0 + 8 * stage;
                         const uint32_t st = sbase + stage * STAGE_BYTES;
@@ -173,17 +194,19 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
         if (lane == 0) {
             int stage = 0, as = 0;
             uint32_t phase = 0, aphase = 0;
-            unsigned long long ntiles = 0;
+            unsigned long long nblk = 0;
             bool ok = true;
-            for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+            while (ok) {
+                int u;
+                if (!ring_next(ring, u, abort_flag, a.err) || u < 0) break;
                 const int mt = u / a.parts, part = u - mt * a.parts;
-                int nt0, nt1;
-                tile_nrange(a, mt, nt0, nt1);
+                int nt0, nt1, kb0, kb1;
+                tile_ranges(a, mt, nt0, nt1, kb0, kb1);
                 for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
                     if (!mbar_wait(acce0 + 8 * as, aphase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d = tmem_base + (uint32_t)(as * BN);
-                    for (int kb = 0; kb < a.kblocks; ++kb) {
+                    for (int kb = kb0; kb < kb1; ++kb) {
                         if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, a.err)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t st = sbase + stage * STAGE_BYTES;
@@ -193,7 +216,7 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                             const uint64_t al = sdesc_sw64(st + A_BYTES + kk * 32);
                             const uint64_t bh = sdesc_sw64(st + 2 * A_BYTES + kk * 32);
                             const uint64_t bl = sdesc_sw64(st + 2 * A_BYTES + B_BYTES + kk * 32);
-                            mma_bf16(d, ah, bh, (kb | kk) != 0 ? 1u : 0u);
+                            mma_bf16(d, ah, bh, (kb != kb0 || kk != 0) ? 1u : 0u);
                             mma_bf16(d, ah, bl, 1u);
                             mma_bf16(d, al, bh, 1u);
                         }
@@ -202,7 +225,7 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                     }
                     if (!ok) break;
                     mma_commit(accf0 + 8 * as);
-                    ++ntiles;
+                    nblk += (unsigned long long)(kb1 - kb0);
                     if (++as == 2) { as = 0; aphase ^= 1u; }
                 }
             }
@@ -211,7 +234,7 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
             const long long t0 = clock64();
             while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
             }
-            if (a.tiles) atomicAdd(a.tiles, ntiles);
+            if (a.kblk) atomicAdd(a.kblk, nblk);
         }
     } else {
         // ---------------------------------------------------------------- epilogue
@@ -222,10 +245,15 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
         int as = 0;
         uint32_t aphase = 0, ephase = 0;
         bool ok = true;
-        for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+        while (ok) {
+            int u = -1, have = 1;
+            if (lane == 0) have = ring_next(ring, u, abort_flag, a.err) ? 1 : 0;
+            have = __shfl_sync(0xffffffffu, have, 0);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (!have || u < 0) break;
             const int mt = u / a.parts, part = u - mt * a.parts;
-            int nt0, nt1;
-            tile_nrange(a, mt, nt0, nt1);
+            int nt0, nt1, kb0, kb1;
+            tile_ranges(a, mt, nt0, nt1, kb0, kb1);
             const int64_t rowg = (int64_t)mt * BM + row;
             const RowConst rc = load_row_const(a.aux, rowg, a.n);
             constexpr int NR = GRAD ? 3 : 1;   // sums per filter: N (and A, D for the gradient)
@@ -343,6 +371,7 @@ cudaError_t launch_phot_tc(const Ctx &c, const Workspace &w, const FilterSet &fs
         return cudaErrorInvalidValue;
     TArgs a{};
     a.aux = w.aux;
+    a.trange = w.trange;
     a.tab = reinterpret_cast<const float4 *>(fs.d_tab);
     a.cc = make_col_const(c);
     a.m_last = fs.m_rows - 1;
@@ -354,12 +383,14 @@ cudaError_t launch_phot_tc(const Ctx &c, const Workspace &w, const FilterSet &fs
     a.band_skip = c.opts.band_skip ? 1 : 0;
     a.m_nz_lo = fs.m_nz_lo;
     a.m_nz_hi = fs.m_nz_hi;
-    a.i0_margin = (int)std::ceil(1.0 / zsort_key_scale(c)) + 1;
     a.n = n;
+    a.sched = w.sched;
     a.partial = w.partial;
-    a.tiles = w.stats;
+    a.kblk = w.stats;
     a.err = c.d_err;
     int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;
+    cudaError_t e = cudaMemsetAsync(w.sched, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
     if (grad) {
         switch (fs.Q4) {
         case 1: return launch_q4<1, true>(ah, al, bh, bl, a, grid, s);

@@ -2,7 +2,8 @@
 // spectra are computed in advance, loaded once as a contiguous block and held
 // fixed).  Builds, from the caller's FP32 L[k][n] (k = i * n_z + j):
 //   d_L32   [K_pad][N_pad] FP32, zero padded                (SIMT form)
-//   d_Lt_*  [N_pad][K_pad] bf16 hi / lo of L[k][n] 2^-E_k    (tensor form, K-major rows)
+//   d_Lt_*  [N_pad][K_pad] bf16 hi / lo of L[k][n] 2^-E_k    (tensor form, K-contiguous
+//           rows, columns in the metallicity-major order kz = j * n_age + i)
 //   d_Ld32  [K_pad][N_pad] FP32 metallicity-differenced block: row (i, 0) is
 //           L[i, 0], row (i, j >= 1) is L[i, j] - L[i, j-1]   (FP32 adjoint)
 //   d_L_*   [K_pad][N_pad] bf16 hi / lo of the differenced block scaled by
@@ -11,7 +12,8 @@
 // dLoss/domega between neighbouring metallicity bins -- all the metallicity
 // gradients need (summation by parts) -- come out at full relative precision.
 //   d_wmul  [K_pad] 2^E_k, the factor folded into the weights, so that
-//           sum_k (omega_k 2^E_k)(L_kn 2^-E_k) = sum_k omega_k L_kn exactly.
+//           sum_k (omega_k 2^E_k)(L_kn 2^-E_k) = sum_k omega_k L_kn exactly
+//           (indexed by kz, like d_Lt_*).
 // E_k is the binary exponent of max_n L[k][n]: every scaled row peaks in
 // [1, 2), far from the bf16 underflow threshold.
 #include "dsps_internal.cuh"
@@ -20,7 +22,9 @@ namespace dsps {
 
 namespace {
 
-__global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, float *wmul, float *rscale) {
+// wmul is written at the metallicity-major position of row k, rscale at k.
+__global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, int n_age, int n_z, float *wmul,
+                                    float *rscale) {
     const int k = blockIdx.x;
     if (k >= K_pad) return;
     float m = 0.f;
@@ -36,7 +40,7 @@ __global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, flo
         int E = 0;
         if (mm > 0.f) E = ilogbf(mm);
         E = max(-120, min(120, E));
-        wmul[k] = k < K ? ldexpf(1.f, E) : 0.f;
+        wmul[k < K ? k_to_kz(k, n_age, n_z) : k] = k < K ? ldexpf(1.f, E) : 0.f;
         rscale[k] = k < K ? ldexpf(1.f, -E) : 0.f;
     }
 }
@@ -49,15 +53,17 @@ __global__ void build_l32_kernel(const float *L, int K, int N, int K_pad, int N_
     L32[idx] = (k < K && n < N) ? L[(size_t)k * N + n] : 0.f;
 }
 
-// Transposing split: tile of 32 (k) x 32 (n) through shared memory.
-__global__ void build_lt_kernel(const float *L, const float *rscale, int K, int N, int K_pad, int N_pad,
-                                __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+// Transposing split: tile of 32 (kz) x 32 (n) through shared memory; column
+// kz of the output takes SSP row k = kz_to_k(kz).
+__global__ void build_lt_kernel(const float *L, const float *rscale, int K, int N, int K_pad, int N_pad, int n_age,
+                                int n_z, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
     __shared__ float t[32][33];
     const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     for (int r = ty; r < 32; r += 8) {
-        int k = k0 + r, n = n0 + tx;
-        t[r][tx] = (k < K && n < N) ? L[(size_t)k * N + n] * rscale[k] : 0.f;
+        const int kz = k0 + r, n = n0 + tx;
+        const int k = kz < K ? kz_to_k(kz, n_age, n_z) : kz;
+        t[r][tx] = (kz < K && n < N) ? L[(size_t)k * N + n] * rscale[k] : 0.f;
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
@@ -125,11 +131,12 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
     e = cudaMalloc(&d_rscale, (size_t)c.K_pad * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(d_raw, h_lssp, KN * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        row_exponent_kernel<<<c.K_pad, 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.d_wmul, d_rscale);
+        row_exponent_kernel<<<c.K_pad, 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.n_age, c.n_z, c.d_wmul, d_rscale);
         const size_t tot = (size_t)c.K_pad * c.N_pad;
         build_l32_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.N_pad, c.d_L32);
         dim3 g(c.N_pad / 32, c.K_pad / 32), b(32, 8);
-        build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.K, c.n_lam, c.K_pad, c.N_pad, c.d_Lt_hi, c.d_Lt_lo);
+        build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.K, c.n_lam, c.K_pad, c.N_pad, c.n_age, c.n_z, c.d_Lt_hi,
+                                  c.d_Lt_lo);
         const unsigned blk = (unsigned)((tot + 255) / 256);
         build_ldiff_kernel<<<blk, 256>>>(d_raw, c.K, c.n_lam, c.n_z, c.K_pad, c.N_pad, c.d_Ld32);
         row_exponent_abs_kernel<<<c.K_pad, 256>>>(c.d_Ld32, c.K, c.N_pad, c.d_wmul_d, d_rscale);

@@ -65,6 +65,50 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Dynamic distribution of work units inside a persistent CTA.  The producer
+// thread claims units from a global counter (so CTAs that drew cheap units
+// take more of them) and publishes each, in claim order, in a ring of
+// UNIT_RING shared-memory slots; every consumer (the MMA thread and each
+// epilogue warp's lane 0) reads every slot once.  full[i] completes when slot i
+// is written (count 1), empty[i] when all consumers have read it.  A claim past
+// the last unit publishes -1, which ends every role's loop.
+constexpr int UNIT_RING = 4;
+
+struct UnitRing {
+    uint32_t full0, empty0;   // mbarrier arrays (8-byte stride)
+    volatile int *slot;       // [UNIT_RING]
+    int pos = 0;
+    uint32_t phase = 0;
+};
+
+// Producer: waits for a free slot, claims the next unit and publishes it (or
+// -1).  False if the wait gave up.
+__device__ __forceinline__ bool ring_claim(UnitRing &r, int *counter, int n_units, int &u, volatile int *abort_flag,
+                                           unsigned *err) {
+    if (!mbar_wait(r.empty0 + 8 * r.pos, r.phase ^ 1u, abort_flag, err)) return false;
+    const int c = atomicAdd(counter, 1);
+    u = c < n_units ? c : -1;
+    r.slot[r.pos] = u;
+    mbar_arrive(r.full0 + 8 * r.pos);
+    if (++r.pos == UNIT_RING) {
+        r.pos = 0;
+        r.phase ^= 1u;
+    }
+    return true;
+}
+
+// Consumer: waits for the next published unit, reads it and frees its slot.
+__device__ __forceinline__ bool ring_next(UnitRing &r, int &u, volatile int *abort_flag, unsigned *err) {
+    if (!mbar_wait(r.full0 + 8 * r.pos, r.phase, abort_flag, err)) return false;
+    u = r.slot[r.pos];
+    mbar_arrive(r.empty0 + 8 * r.pos);
+    if (++r.pos == UNIT_RING) {
+        r.pos = 0;
+        r.phase ^= 1u;
+    }
+    return true;
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, uint32_t bar, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"

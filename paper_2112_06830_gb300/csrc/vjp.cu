@@ -56,14 +56,15 @@ __global__ void combine_grad_kernel(const float *partial, int parts, int64_t n, 
 
 // One warp per (sorted) row: Shat over the row's band columns [32 kb0, 32 kb1).
 template <int Q4, bool BF16>
-__global__ void __launch_bounds__(256) shat_kernel(const float *aux, const float *cq, const float4 *tab, int m_last,
-                                                   ColConst cc, int64_t n, int N_pad, VjpBand band, float *out32,
+__global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int4 *trange, const float *cq,
+                                                   const float4 *tab, int m_last, ColConst cc, int64_t n, int N_pad,
+                                                   VjpBand band, float *out32,
                                                    __nv_bfloat16 *out_hi, __nv_bfloat16 *out_lo) {
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
     int kb0, kb1;
-    vjp_band(band, aux, n, (int)(r / 128), N_pad, kb0, kb1);
+    vjp_band(band, trange, (int)(r / 128), N_pad, kb0, kb1);
     const RowConst rc = load_row_const(aux, r, n);
     float nb[4 * Q4];
 #pragma unroll
@@ -201,7 +202,6 @@ VjpBand make_vjp_band(const Ctx &c, const FilterSet &fs, bool band) {
     b.on = band ? 1 : 0;
     b.m_nz_lo = fs.m_nz_lo;
     b.m_nz_hi = fs.m_nz_hi;
-    b.i0_margin = (int)std::ceil(1.0 / zsort_key_scale(c)) + 1;
     b.Q = fs.Q;
     return b;
 }
@@ -228,12 +228,12 @@ cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, i
     auto *ohi = reinterpret_cast<__nv_bfloat16 *>(w.shat);
     __nv_bfloat16 *olo = ohi + (size_t)w.cap * c.N_pad;
     const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
-#define DSPS_SHAT(Q4)                                                                                      \
-    if (bf16)                                                                                              \
-        shat_kernel<Q4, true><<<blocks, 256, 0, s>>>(w.aux, w.cq, tab, m_last, cc, n, c.N_pad, b, o32, \
-                                                     ohi, olo);                                            \
-    else                                                                                                   \
-        shat_kernel<Q4, false><<<blocks, 256, 0, s>>>(w.aux, w.cq, tab, m_last, cc, n, c.N_pad, b, o32, \
+#define DSPS_SHAT(Q4)                                                                                              \
+    if (bf16)                                                                                                      \
+        shat_kernel<Q4, true><<<blocks, 256, 0, s>>>(w.aux, w.trange, w.cq, tab, m_last, cc, n, c.N_pad, b, o32,   \
+                                                     ohi, olo);                                                    \
+    else                                                                                                           \
+        shat_kernel<Q4, false><<<blocks, 256, 0, s>>>(w.aux, w.trange, w.cq, tab, m_last, cc, n, c.N_pad, b, o32,  \
                                                       ohi, olo);
     switch (fs.Q4) {
     case 1: DSPS_SHAT(1) break;

@@ -3,9 +3,10 @@
 // with Shat and the row-scaled SSP block both split into bf16 hi + lo
 // (hi*hi + hi*lo + lo*hi, FP32 accumulate in TMEM), written as FP32.
 //
-// Work unit = (128-galaxy tile, 256-wide block of SSP indices k); the
-// reduction runs only over the wavelength blocks where the tile's Shat can be
-// non-zero (the redshifted filter band, epilogue.cuh: vjp_band).  Warp roles
+// Work unit = (128-galaxy tile, 256-wide block of SSP indices k), claimed from
+// a global counter (tc::UnitRing); the reduction runs only over the wavelength
+// blocks where the tile's Shat can be non-zero (the redshifted filter band,
+// epilogue.cuh: vjp_band).  Warp roles
 // as in phot_tc.cu: TMA producer, single-thread MMA issuer with a double
 // TMEM accumulator, eight epilogue warps that read rows with tcgen05.ld and
 // store them.  Every mbarrier wait is bounded.
@@ -31,10 +32,11 @@ constexpr size_t BAR_BYTES = 1024;
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES;
 
 struct VArgs {
-    const float *aux;
+    const int4 *trange;
     VjpBand band;
     int n_mtiles, n_ktiles, n_units, N_pad, K_pad;
     int64_t n;
+    int *sched;       // unit counter, zero at launch
     float *out;       // [n][K_pad]
     unsigned *err;
 };
@@ -53,6 +55,10 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
     const uint32_t drain = smem_u32(bars + 2 * STAGES + 4);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    UnitRing ring;
+    ring.full0 = smem_u32(bars + 2 * STAGES + 8);
+    ring.empty0 = smem_u32(bars + 2 * STAGES + 8 + UNIT_RING);
+    ring.slot = reinterpret_cast<volatile int *>(bars + 2 * STAGES + 8 + 2 * UNIT_RING);
     const uint32_t sbase = smem_u32(sm);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -66,6 +72,10 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
             mbar_init(acce0 + 8 * i, NUM_EPI_WARPS);
         }
         mbar_init(drain, 1);
+        for (int i = 0; i < UNIT_RING; ++i) {
+            mbar_init(ring.full0 + 8 * i, 1);
+            mbar_init(ring.empty0 + 8 * i, 1 + NUM_EPI_WARPS);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -88,10 +98,12 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
             int armed[STAGES];
             for (int s = 0; s < STAGES; ++s) armed[s] = -1;
             bool ok = true;
-            for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+            while (ok) {
+                int u;
+                if (!ring_claim(ring, a.sched, a.n_units, u, abort_flag, a.err) || u < 0) break;
                 const int mt = u / a.n_ktiles, kt = u - mt * a.n_ktiles;
                 int kb0, kb1;
-                vjp_band(a.band, a.aux, a.n, mt, a.N_pad, kb0, kb1);
+                vjp_band(a.band, a.trange, mt, a.N_pad, kb0, kb1);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                     const uint32_t fb = full0 + 8 * stage;
@@ -118,10 +130,12 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
             int stage = 0, as = 0;
             uint32_t phase = 0, aphase = 0;
             bool ok = true;
-            for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+            while (ok) {
+                int u;
+                if (!ring_next(ring, u, abort_flag, a.err) || u < 0) break;
                 const int mt = u / a.n_ktiles;
                 int kb0, kb1;
-                vjp_band(a.band, a.aux, a.n, mt, a.N_pad, kb0, kb1);
+                vjp_band(a.band, a.trange, mt, a.N_pad, kb0, kb1);
                 if (!mbar_wait(acce0 + 8 * as, aphase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(as * BN);
@@ -159,7 +173,12 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
         const int row = qd * 32 + lane;
         int as = 0;
         uint32_t aphase = 0;
-        for (int u = blockIdx.x; u < a.n_units; u += gridDim.x) {
+        while (true) {
+            int u = -1, have = 1;
+            if (lane == 0) have = ring_next(ring, u, abort_flag, a.err) ? 1 : 0;
+            have = __shfl_sync(0xffffffffu, have, 0);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (!have || u < 0) break;
             const int mt = u / a.n_ktiles, kt = u - mt * a.n_ktiles;
             const int64_t rowg = (int64_t)mt * BM + row;
             int got = 1;
@@ -212,7 +231,7 @@ cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs,
         !make_tmap(&bl, c.d_L_lo, (uint64_t)c.N_pad, (uint64_t)c.K_pad, BN))
         return cudaErrorInvalidValue;
     VArgs a{};
-    a.aux = w.aux;
+    a.trange = w.trange;
     a.band = make_vjp_band(c, fs, c.opts.band_skip != 0);
     a.n_mtiles = (int)((n + BM - 1) / BM);
     a.n_ktiles = (c.K_pad + BN - 1) / BN;
@@ -220,10 +239,12 @@ cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs,
     a.N_pad = c.N_pad;
     a.K_pad = c.K_pad;
     a.n = n;
+    a.sched = w.sched;
     a.out = w.w32;
     a.err = c.d_err;
     const int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;
     cudaError_t e = cudaFuncSetAttribute(vjp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.sched, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     vjp_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
     return cudaGetLastError();

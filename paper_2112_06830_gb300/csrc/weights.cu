@@ -16,7 +16,10 @@
 //      moving linearly in log age (Sec. 3.2, Eq. agedep_mdf), FP32.
 //   6. Joint weights omega_ij = P_SFH(i) P_met(j | i) (Eq. full_mdf), written as
 //      Msun (dsps_weights), FP32 per unit mass (SIMT photometry) or scaled by
-//      the SSP row multiplier and split into bf16 hi + lo (tensor photometry).
+//      the SSP row multiplier and split into bf16 hi + lo (tensor photometry,
+//      metallicity-major K, with the per-tile ranges of Workspace::trange).
+#include <climits>
+
 #include "dsps_internal.cuh"
 
 namespace dsps {
@@ -38,6 +41,7 @@ struct WArgs {
     double *magoff;
     const int *perm;   // sorted row -> chunk-local galaxy, or nullptr
     int *gidx;         // out: sorted row -> chunk-local galaxy, or nullptr
+    int4 *trange;      // out: per-tile ranges (atomics), or nullptr
     unsigned *err;
 };
 
@@ -59,8 +63,13 @@ __device__ __forceinline__ float mdf_s(int kernel, float u) {
     return u > 0.f ? -c : c;
 }
 
-__device__ __forceinline__ float mdf_bin(int kernel, float u_lo, float u_hi) {
-    float p = mdf_s(kernel, u_hi) - mdf_s(kernel, u_lo);
+// P_met of the bin between standardised edges u_lo < u_hi (first / last bin:
+// open below / above).  The triweight vanishes outside [-3, 3], and a bin
+// entirely beyond either end is exactly 0 without evaluating the CDF (the
+// general expression gives the same 0).
+__device__ __forceinline__ float mdf_bin(int kernel, float u_lo, float u_hi, bool first, bool last) {
+    if (kernel == DSPS_MDF_TRIWEIGHT && (u_hi <= -3.f || u_lo >= 3.f)) return 0.f;
+    float p = (last ? 0.f : mdf_s(kernel, u_hi)) - (first ? 0.f : mdf_s(kernel, u_lo));
     if (u_lo <= 0.f && u_hi > 0.f) p += 1.f;
     return p;
 }
@@ -229,53 +238,41 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
     valid = sfh_stage(a, p, valid, lane, sm, msum);
     float *frac = sm.frac;
 
-    // 5-6. metallicity weights and output, four consecutive k per lane.  The
-    //      CDF at the upper edge of bin j is the lower edge of bin j+1, and the
-    //      outer edges (-inf, +inf) need no evaluation, so each k costs about
-    //      one CDF evaluation.
+    // 5-6. metallicity weights and output.
     const float inv_sig = 1.f / sig;
     const float mass = exp10f(p[10]);
-    const int kend = MODE == W_MSUN ? a.K : a.K_pad;
+    const float s_shift = valid ? log1pf(z) / (float)a.dlnlam : 0.f;   // redshift shift in grid steps
     const int nz = a.n_z;
-    const int di = 128 / nz, dj = 128 % nz;
-    int k = 4 * lane;
-    int i0 = k / nz, j0 = k - i0 * nz;
-    for (; k < kend; k += 128) {
-        float om[4];
-        int i = i0, j = j0;
-        float mu_i = fmaf(p[7], __ldg(a.logage + min(i, a.n_age - 1)) - 9.f, p[5]);
-        float u_lo = (__ldg(a.zedge + j) - mu_i) * inv_sig;
-        float s_lo = j == 0 ? 0.f : mdf_s(a.mdf_kernel, u_lo);
+    if constexpr (MODE == W_OMEGA_BF16X2) {
+        // Metallicity-major kz = j * n_age + i, four consecutive kz per lane
+        // (each weight from its own two CDF values: consecutive kz are
+        // neighbouring ages).  The lane also keeps the first and last kz it
+        // wrote non-zero, for the tile's K range.
+        const int na = a.n_age;
+        int kz_min = INT_MAX, kz_max = -1;
+        for (int kz = 4 * lane; kz < a.K_pad; kz += 128) {
+            float om[4];
+            int j = kz / na, i = kz - j * na;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            om[c] = 0.f;
-            if (k + c < a.K && valid) {
-                const bool last = j == nz - 1;
-                const float u_hi = last ? 1e30f : (__ldg(a.zedge + j + 1) - mu_i) * inv_sig;
-                const float s_hi = last ? 0.f : mdf_s(a.mdf_kernel, u_hi);
-                float pj = s_hi - s_lo;
-                if (u_lo <= 0.f && u_hi > 0.f) pj += 1.f;
-                om[c] = frac[i] * pj;
-                s_lo = s_hi;
-                u_lo = u_hi;
+            for (int c = 0; c < 4; ++c) {
+                om[c] = 0.f;
+                if (kz + c < a.K && valid) {
+                    const float mu_i = fmaf(p[7], __ldg(a.logage + i) - 9.f, p[5]);
+                    const bool first = j == 0, last = j == nz - 1;
+                    const float u_lo = first ? -1e30f : (__ldg(a.zedge + j) - mu_i) * inv_sig;
+                    const float u_hi = last ? 1e30f : (__ldg(a.zedge + j + 1) - mu_i) * inv_sig;
+                    om[c] = frac[i] * mdf_bin(a.mdf_kernel, u_lo, u_hi, first, last);
+                    if (om[c] != 0.f) {
+                        kz_min = min(kz_min, kz + c);
+                        kz_max = kz + c;
+                    }
+                }
+                if (++i == na) {
+                    i = 0;
+                    ++j;
+                }
             }
-            if (++j == nz) {   // next age row: its lower edge is -inf
-                j = 0;
-                ++i;
-                mu_i = fmaf(p[7], __ldg(a.logage + min(i, a.n_age - 1)) - 9.f, p[5]);
-                u_lo = -1e30f;
-                s_lo = 0.f;
-            }
-        }
-        if (MODE == W_MSUN) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (k + c < a.K) a.w_msun[gi * a.K + k + c] = mass * om[c];
-        } else if (MODE == W_OMEGA_F32) {
-            if (k < a.K_pad)
-                *reinterpret_cast<float4 *>(a.w32 + gi * a.K_pad + k) = make_float4(om[0], om[1], om[2], om[3]);
-        } else if (k < a.K_pad) {
-            const float4 wm = __ldg(reinterpret_cast<const float4 *>(a.wmul + k));
+            const float4 wm = __ldg(reinterpret_cast<const float4 *>(a.wmul + kz));
             const float w0 = om[0] * wm.x, w1 = om[1] * wm.y, w2 = om[2] * wm.z, w3 = om[3] * wm.w;
             const __nv_bfloat162 h01 = __floats2bfloat162_rn(w0, w1), h23 = __floats2bfloat162_rn(w2, w3);
             const __nv_bfloat162 l01 = __floats2bfloat162_rn(w0 - __low2float(h01), w1 - __high2float(h01));
@@ -285,12 +282,67 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
             hv.y = *reinterpret_cast<const unsigned *>(&h23);
             lv.x = *reinterpret_cast<const unsigned *>(&l01);
             lv.y = *reinterpret_cast<const unsigned *>(&l23);
-            *reinterpret_cast<uint2 *>(a.whi + gi * a.K_pad + k) = hv;
-            *reinterpret_cast<uint2 *>(a.wlo + gi * a.K_pad + k) = lv;
+            *reinterpret_cast<uint2 *>(a.whi + gi * a.K_pad + kz) = hv;
+            *reinterpret_cast<uint2 *>(a.wlo + gi * a.K_pad + kz) = lv;
         }
-        i0 += di;
-        j0 += dj;
-        if (j0 >= nz) { j0 -= nz; ++i0; }
+        kz_min = __reduce_min_sync(0xffffffffu, kz_min);
+        kz_max = __reduce_max_sync(0xffffffffu, kz_max);
+        if (lane == 0 && a.trange && valid) {
+            int4 *t = a.trange + (gi >> 7);
+            const int i0 = (int)floorf(s_shift);
+            atomicMin(&t->x, i0);
+            atomicMax(&t->y, i0);
+            if (kz_max >= 0) {
+                atomicMin(&t->z, kz_min);
+                atomicMax(&t->w, kz_max);
+            }
+        }
+    } else {
+        // Age-major k, four consecutive k per lane.  The CDF at the upper edge
+        // of bin j is the lower edge of bin j+1, and the outer edges (-inf,
+        // +inf) need no evaluation, so each k costs about one CDF evaluation.
+        const int kend = MODE == W_MSUN ? a.K : a.K_pad;
+        const int di = 128 / nz, dj = 128 % nz;
+        int k = 4 * lane;
+        int i0 = k / nz, j0 = k - i0 * nz;
+        for (; k < kend; k += 128) {
+            float om[4];
+            int i = i0, j = j0;
+            float mu_i = fmaf(p[7], __ldg(a.logage + min(i, a.n_age - 1)) - 9.f, p[5]);
+            float u_lo = (__ldg(a.zedge + j) - mu_i) * inv_sig;
+            float s_lo = j == 0 ? 0.f : mdf_s(a.mdf_kernel, u_lo);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                om[c] = 0.f;
+                if (k + c < a.K && valid) {
+                    const bool last = j == nz - 1;
+                    const float u_hi = last ? 1e30f : (__ldg(a.zedge + j + 1) - mu_i) * inv_sig;
+                    const float s_hi = last ? 0.f : mdf_s(a.mdf_kernel, u_hi);
+                    float pj = s_hi - s_lo;
+                    if (u_lo <= 0.f && u_hi > 0.f) pj += 1.f;
+                    om[c] = frac[i] * pj;
+                    s_lo = s_hi;
+                    u_lo = u_hi;
+                }
+                if (++j == nz) {   // next age row: its lower edge is -inf
+                    j = 0;
+                    ++i;
+                    mu_i = fmaf(p[7], __ldg(a.logage + min(i, a.n_age - 1)) - 9.f, p[5]);
+                    u_lo = -1e30f;
+                    s_lo = 0.f;
+                }
+            }
+            if (MODE == W_MSUN) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (k + c < a.K) a.w_msun[gi * a.K + k + c] = mass * om[c];
+            } else if (k < a.K_pad) {
+                *reinterpret_cast<float4 *>(a.w32 + gi * a.K_pad + k) = make_float4(om[0], om[1], om[2], om[3]);
+            }
+            i0 += di;
+            j0 += dj;
+            if (j0 >= nz) { j0 -= nz; ++i0; }
+        }
     }
 
     if (lane == 0) {
@@ -300,7 +352,7 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
             float *ax = a.aux + gi * AUX_STRIDE;
             ax[0] = -0.4f * 3.32192809488736235f * p[8];
             ax[1] = p[9] - 0.7f;
-            ax[2] = valid ? (float)(log1pf(z) / (float)a.dlnlam) : 0.f;
+            ax[2] = s_shift;
             ax[3] = valid ? 1.f : 0.f;
             ax[4] = p[8];
             ax[5] = p[9];
@@ -563,6 +615,7 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
     a.w_msun = w_msun;
     a.perm = sorted ? w.perm : nullptr;
     a.gidx = sorted ? w.gidx : nullptr;
+    a.trange = sorted && mode == W_OMEGA_BF16X2 ? w.trange : nullptr;
     const int threads = 256, warps = threads / 32;
     const size_t smem = weights_smem_per_warp(c.n_t, c.n_age) * warps;
     dim3 grid((unsigned)((n + warps - 1) / warps));

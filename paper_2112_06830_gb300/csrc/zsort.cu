@@ -1,13 +1,17 @@
-// zsort.cu -- orders a chunk of galaxies by redshift shift s = ln(1+z)/dlnlam
-// (counting sort on floor(s * key_scale)) and combines the per-part partial
-// filter sums of the tensor-core kernel into magnitudes.
+// zsort.cu -- orders a chunk of galaxies for the tensor-core kernel (counting
+// sort on a two-level key) and combines that kernel's per-part partial filter
+// sums into magnitudes.
 //
-// Sorting is a scheduling device only: every galaxy's magnitudes are computed
-// from its own row and do not depend on which rows share its tile, so the
-// order within a bucket (set by atomics) does not change any result.  With the
-// rows of a 128-galaxy tile close in redshift, the tile needs the filter table
-// only near one shift (near-broadcast reads) and only the wavelength tiles
-// that fall inside the redshifted filter band.
+// Key: ZSORT_ZBINS coarse bins of the redshift shift s = ln(1+z)/dlnlam, and
+// inside each ZSORT_MUBINS bins of the galaxy's mean metallicity at the middle
+// log age.  Rows of one 128-galaxy tile then share a narrow redshift range (the
+// tile needs only the wavelength tiles inside the redshifted filter band, and
+// reads the filter table near one shift) and a narrow metallicity range (the
+// tile's non-zero weights fill only the K blocks of a few metallicity bins).
+// Sorting is a scheduling device only: every galaxy's magnitudes come from its
+// own row, and skipped tiles and blocks hold exact zeros for every row, so the
+// order within a bucket (set by atomics) changes no result.
+#include <climits>
 #include <cmath>
 
 #include "dsps_internal.cuh"
@@ -16,15 +20,27 @@ namespace dsps {
 
 namespace {
 
-__device__ __forceinline__ int zkey(float z, float inv_dlnlam, float key_scale) {
-    if (!(z > 0.f) || !isfinite(z)) return 0;
-    int k = (int)(log1pf(z) * inv_dlnlam * key_scale);
-    return min(max(k, 0), ZSORT_BUCKETS - 1);
+struct SortKey {
+    const float *z, *mu, *slope;   // parameter rows 11, 5, 7 of the chunk
+    float inv_dlnlam, zscale;      // s = log1p(z) * inv_dlnlam; z bin = floor(s * zscale)
+    float mu_lo, mu_scale, xmid;   // mu bin = floor((mu + slope * xmid - mu_lo) * mu_scale)
+};
+
+__device__ __forceinline__ int sort_key(const SortKey &k, int64_t i) {
+    const float z = k.z[i];
+    int zb = 0;
+    if (z > 0.f && isfinite(z)) zb = min(max((int)(log1pf(z) * k.inv_dlnlam * k.zscale), 0), ZSORT_ZBINS - 1);
+    const float m = fmaf(k.slope[i], k.xmid, k.mu[i]);
+    int mb = 0;
+    if (isfinite(m)) mb = (int)fminf(fmaxf((m - k.mu_lo) * k.mu_scale, 0.f), (float)(ZSORT_MUBINS - 1));
+    return zb * ZSORT_MUBINS + mb;
 }
 
-__global__ void zsort_hist_kernel(const float *z, int64_t n, float inv_dlnlam, float key_scale, int *hist) {
+// Histogram of the keys; the first threads also reset the per-tile ranges.
+__global__ void zsort_hist_kernel(SortKey k, int64_t n, int *hist, int4 *trange, int n_tiles) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(hist + zkey(z[i], inv_dlnlam, key_scale), 1);
+    if (i < n_tiles) trange[i] = make_int4(TRANGE_EMPTY_LO, TRANGE_EMPTY_HI, TRANGE_EMPTY_LO, TRANGE_EMPTY_HI);
+    if (i < n) atomicAdd(hist + sort_key(k, i), 1);
 }
 
 // Exclusive scan of ZSORT_BUCKETS counts in one block of 1024 threads.
@@ -54,10 +70,9 @@ __global__ void zsort_scan_kernel(int *hist) {
     }
 }
 
-__global__ void zsort_scatter_kernel(const float *z, int64_t n, float inv_dlnlam, float key_scale, int *offsets,
-                                     int *perm) {
+__global__ void zsort_scatter_kernel(SortKey k, int64_t n, int *offsets, int *perm) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) perm[atomicAdd(offsets + zkey(z[i], inv_dlnlam, key_scale), 1)] = (int)i;
+    if (i < n) perm[atomicAdd(offsets + sort_key(k, i), 1)] = (int)i;
 }
 
 // Sum of the parts in fixed order, then Sec. 2.2's magnitude; written to the
@@ -77,20 +92,25 @@ __global__ void combine_mags_kernel(const float *partial, int parts, int64_t n, 
 
 }  // namespace
 
-float zsort_key_scale(const Ctx &c) {
-    const double smax = std::log1p(c.opts.z_max) / c.dlnlam;
-    return (float)(ZSORT_BUCKETS / (smax + 1.0));
-}
-
-cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *z, int64_t n, cudaStream_t s) {
+cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride, int64_t g_begin,
+                         int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const float inv_d = (float)(1.0 / c.dlnlam), ks = zsort_key_scale(c);
+    SortKey k;
+    k.z = params + 11 * G_stride + g_begin;
+    k.mu = params + 5 * G_stride + g_begin;
+    k.slope = params + 7 * G_stride + g_begin;
+    k.inv_dlnlam = (float)(1.0 / c.dlnlam);
+    k.zscale = (float)(ZSORT_ZBINS / (std::log1p(c.opts.z_max) / c.dlnlam + 1.0));
+    k.mu_lo = c.sort_mu_lo;
+    k.mu_scale = c.sort_mu_scale;
+    k.xmid = c.sort_xmid;
+    const int n_tiles = (int)((n + 127) / 128);
     cudaError_t e = cudaMemsetAsync(w.hist, 0, ZSORT_BUCKETS * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((n + 255) / 256);
-    zsort_hist_kernel<<<blocks, 256, 0, s>>>(z, n, inv_d, ks, w.hist);
+    const unsigned blocks = (unsigned)((n + 255) / 256);   // n >= n_tiles
+    zsort_hist_kernel<<<blocks, 256, 0, s>>>(k, n, w.hist, w.trange, n_tiles);
     zsort_scan_kernel<<<1, 1024, 0, s>>>(w.hist);
-    zsort_scatter_kernel<<<blocks, 256, 0, s>>>(z, n, inv_d, ks, w.hist, w.perm);
+    zsort_scatter_kernel<<<blocks, 256, 0, s>>>(k, n, w.hist, w.perm);
     return cudaGetLastError();
 }
 

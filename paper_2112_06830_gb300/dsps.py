@@ -58,7 +58,7 @@ DSPS_PROF_KINDS = 4
 
 class dsps_profile_t(C.Structure):
     _fields_ = [("launches", C.c_int64 * DSPS_PROF_KINDS), ("ms", C.c_double * DSPS_PROF_KINDS),
-                ("tc_tiles", C.c_int64)]
+                ("tc_kblocks", C.c_int64)]
 
 
 class dsps_request(C.Structure):
@@ -211,11 +211,11 @@ def dsps_profile_enable(ctx, enable=True):
 
 def dsps_profile_read(ctx):
     """{kind: (launches, ms)} for kinds 0 weights/sort/combine, 1 fp32, 2 tensor, 3 adjoint, plus
-    "tc_tiles": tensor-core tiles executed."""
+    "tc_kblocks": 128 x 256 x 32 split-bf16 tensor-core block products executed."""
     p = dsps_profile_t()
     _check(load().dsps_profile_read(ctx, C.byref(p)), "dsps_profile_read")
     out = {k: (int(p.launches[k]), float(p.ms[k])) for k in range(DSPS_PROF_KINDS)}
-    out["tc_tiles"] = int(p.tc_tiles)
+    out["tc_kblocks"] = int(p.tc_kblocks)
     return out
 
 
