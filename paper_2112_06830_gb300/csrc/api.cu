@@ -229,6 +229,9 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     c->n_lam = g->n_lam;
     c->K = g->n_age * g->n_z;
     c->K_pad = (c->K + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
+    c->A_pad = (c->n_age + 3) / 4 * 4;
+    c->KZ_pad = (c->n_z * c->A_pad + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
+    c->kmask_words = (c->KZ_pad / KBLOCK + 31) / 32;
     c->N_pad = (c->n_lam + 1 + N_ALIGN - 1) / N_ALIGN * N_ALIGN;   // >= n_lam + 1: room for the closing term
     c->n_t = g->n_t;
     c->t0 = g->t0_gyr;
@@ -243,9 +246,9 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     int rc = DSPS_OK;
     auto chk = [&](int r) { if (rc == DSPS_OK) rc = r; };
     chk(dmalloc(&c->d_L32, (size_t)c->K_pad * c->N_pad));
-    chk(dmalloc(&c->d_Lt_hi, (size_t)c->K_pad * c->N_pad));
-    chk(dmalloc(&c->d_Lt_lo, (size_t)c->K_pad * c->N_pad));
-    chk(dmalloc(&c->d_wmul, (size_t)c->K_pad));
+    chk(dmalloc(&c->d_Lt_hi, (size_t)c->KZ_pad * c->N_pad));
+    chk(dmalloc(&c->d_Lt_lo, (size_t)c->KZ_pad * c->N_pad));
+    chk(dmalloc(&c->d_wmul, (size_t)c->KZ_pad));
     chk(dmalloc(&c->d_logage, (size_t)c->n_age));
     chk(dmalloc(&c->d_edges, (size_t)c->n_age + 1));
     chk(dmalloc(&c->d_einh, (size_t)c->n_age + 1));
@@ -388,7 +391,12 @@ int dsps_weights(dsps_ctx *ctx, int64_t n_gal, const float *params, float *w_out
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !w_out))) return fail(DSPS_ERR_INVALID_ARG, "dsps_weights: bad argument%s");
     if (n_gal == 0) return DSPS_OK;
     DSPS_CUDA(cudaSetDevice(c->device));
-    DSPS_CUDA(launch_weights(*c, c->ws, W_MSUN, params, n_gal, 0, n_gal, w_out, reinterpret_cast<cudaStream_t>(stream)));
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (int64_t g0 = 0; g0 < n_gal; g0 += c->ws.cap) {
+        const int64_t n = n_gal - g0 < c->ws.cap ? n_gal - g0 : c->ws.cap;
+        DSPS_CUDA(launch_weights(*c, c->ws, W_MSUN, params, n_gal, g0, n, w_out + g0 * c->K,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+    }
     return DSPS_OK;
 }
 

@@ -22,7 +22,7 @@ constexpr int MAX_NT = 1024;     // SFR time nodes
 constexpr int MAX_NAGE = 512;
 constexpr int AUX_STRIDE = 8;    // floats of per-galaxy epilogue constants
 constexpr int ZSORT_BUCKETS = 4096;  // sort buckets (multiple of 1024) = ZSORT_ZBINS x ZSORT_MUBINS
-constexpr int ZSORT_ZBINS = 16;      // coarse redshift-shift bins of the sort key
+constexpr int ZSORT_ZBINS = 32;      // coarse redshift-shift bins of the sort key
 constexpr int ZSORT_MUBINS = ZSORT_BUCKETS / ZSORT_ZBINS;  // mean-metallicity bins inside each
 constexpr int TC_PARTS = 4;      // work units per 128-galaxy tile in the tensor-core kernel
 constexpr int QSTRIDE_MAX = 16;  // floats per row of the partial filter sums
@@ -37,26 +37,31 @@ constexpr double SIG_Q = 0.3;           // quench transition width [Gyr]
 
 // Order of the K = n_age * n_z axis.  The SSP block, dsps_weights and the FP32
 // and adjoint paths use the age-major k = i * n_z + j.  The tensor-core forward
-// operands (split weights and d_Lt_*) use the metallicity-major kz = j * n_age
-// + i: the metallicity kernel moves a galaxy's non-zero weights into one
-// contiguous run of kz (the triweight has compact support), so a tile of
-// galaxies with similar metallicity needs only the K blocks of that run.
-__host__ __device__ inline int kz_to_k(int kz, int n_age, int n_z) {
-    const int j = kz / n_age;
-    return (kz - j * n_age) * n_z + j;
+// operands (split weights and d_Lt_*) use the metallicity-major kz = j * A_pad
+// + i, A_pad = n_age rounded up to 4 (so that every metallicity row starts on a
+// 16-byte boundary; ages n_age .. A_pad-1 are zero columns), in rows of KZ_pad
+// = n_z * A_pad rounded up to K_ALIGN.  The triweight metallicity kernel has
+// compact support, so a galaxy's non-zero weights fill one contiguous run of
+// kz, and a tile of galaxies with similar metallicity needs only the K blocks
+// of that run.
+__host__ __device__ inline int kz_to_k(int kz, int a_pad, int n_age, int n_z) {   // -1: padding
+    const int j = kz / a_pad, i = kz - j * a_pad;
+    return (j < n_z && i < n_age) ? i * n_z + j : -1;
 }
-__host__ __device__ inline int k_to_kz(int k, int n_age, int n_z) {
+__host__ __device__ inline int k_to_kz(int k, int a_pad, int n_z) {
     const int i = k / n_z;
-    return (k - i * n_z) * n_age + i;
+    return (k - i * n_z) * a_pad + i;
 }
 
-// Per 128-row tile of sorted galaxies (Workspace::trange), reduced with
-// atomics by the weights kernel over the tile's valid rows:
-//   x, y  smallest / largest floor(s) (s = aux[.+2], the redshift shift)
-//   z, w  smallest / largest kz at which some row's split weights are non-zero
-// Empty tiles keep the initial {INT_MAX, INT_MIN, INT_MAX, INT_MIN}.
+// Per 128-row tile of sorted galaxies, reduced with atomics by the weights
+// kernel over the tile's valid rows:
+//   Workspace::trange  {smallest, largest} floor(s) (s = aux[.+2], the
+//                      redshift shift); an empty tile keeps {INT_MAX, INT_MIN}
+//   Workspace::kmask   Ctx::kmask_words words: bit b set if some row's split
+//                      weights are non-zero in kz block [32 b, 32 b + 32)
 constexpr int TRANGE_EMPTY_LO = 0x7fffffff;
 constexpr int TRANGE_EMPTY_HI = (int)0x80000000;
+constexpr int KBLOCK = 32;   // kz block of the tensor-core contraction (one TMA box)
 
 // Per-galaxy epilogue constants (aux[g*AUX_STRIDE + .]):
 //   0 alpha = -0.4 log2(10) Av      (F = 2^(alpha u))
@@ -76,6 +81,13 @@ struct FilterSet {
 
 struct Serve;  // request loop (serve.cu)
 
+// Per-galaxy scalars of the cosmology (weights.cu: galaxy_prep_kernel).
+struct GalPrep {
+    int m_obs;       // interval of the SFR time grid holding t_obs(z); -1 if z is out of range
+    float f_obs;     // position of t_obs inside that interval, [0, 1)
+    double magoff;   // -2.5 logM + Dmod(z) - 2.5 log10(1+z) (NaN if z is out of range)
+};
+
 // Per-launch work space of the photometry path (rows = galaxies of one chunk
 // or batch).  The context owns one (Ctx::ws); the request loop carves one per
 // in-flight batch out of its device arena; the allocation-free entry point
@@ -83,13 +95,15 @@ struct Serve;  // request loop (serve.cu)
 struct Workspace {
     int64_t cap = 0;                            // rows
     float *w32 = nullptr;                       // [cap][K_pad] FP32 weights / adjoint output
-    __nv_bfloat16 *whi = nullptr, *wlo = nullptr;  // [cap][K_pad] split weights
+    __nv_bfloat16 *whi = nullptr, *wlo = nullptr;  // [cap][KZ_pad] split weights (metallicity-major)
     float *aux = nullptr;                       // [cap][AUX_STRIDE]
     double *magoff = nullptr;                   // [cap]
+    GalPrep *prep = nullptr;                    // [cap] (chunk order)
     int *perm = nullptr, *gidx = nullptr;       // [cap]
     int *hist = nullptr;                        // [ZSORT_BUCKETS]
     float *partial = nullptr;                   // [TC_PARTS][cap][3 * QSTRIDE_MAX]
-    int4 *trange = nullptr;                     // [cap/128 + 1] per sorted 128-row tile (ranges below)
+    int2 *trange = nullptr;                     // [cap/128 + 1] per sorted 128-row tile (see above)
+    unsigned *kmask = nullptr;                  // [cap/128 + 1][kmask_words]
     int *sched = nullptr;                       // [1] work-unit counter of the tensor-core kernels
     float *cq = nullptr;                        // [cap][QSTRIDE_MAX]
     void *shat = nullptr;                       // [cap][N_pad] x 4 bytes (adjoint only)
@@ -100,6 +114,8 @@ struct Ctx {
     int device = 0;
     dsps_opts opts{};
     int n_age = 0, n_z = 0, n_lam = 0, K = 0, K_pad = 0, N_pad = 0, n_t = 0;
+    int A_pad = 0, KZ_pad = 0;              // metallicity-major K: n_age padded to 4, row length
+    int kmask_words = 0;                    // ceil(KZ_pad / KBLOCK / 32)
     double t0 = 0, t1 = 0;
     double lnlam0 = 0, dlnlam = 0;
     int num_sms = 0;
@@ -109,9 +125,9 @@ struct Ctx {
 
     // Resident SSP copies.
     float *d_L32 = nullptr;                 // [K_pad][N_pad] fp32 (SIMT path)
-    __nv_bfloat16 *d_Lt_hi = nullptr;       // [N_pad][K_pad] row-scaled hi, metallicity-major K (tensor path)
-    __nv_bfloat16 *d_Lt_lo = nullptr;       // [N_pad][K_pad] row-scaled lo
-    float *d_wmul = nullptr;                // [K_pad] 2^E_k of the scaled rows, metallicity-major K
+    __nv_bfloat16 *d_Lt_hi = nullptr;       // [N_pad][KZ_pad] row-scaled hi, metallicity-major K (tensor path)
+    __nv_bfloat16 *d_Lt_lo = nullptr;       // [N_pad][KZ_pad] row-scaled lo
+    float *d_wmul = nullptr;                // [KZ_pad] 2^E_k of the scaled rows, metallicity-major K
 
     // Grids and tables.
     float *d_logage = nullptr;              // [n_age] log10(age/yr)
@@ -194,7 +210,7 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
                            int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted = false);
 
 // Counting sort of the chunk's galaxies into w.perm by (coarse redshift shift,
-// mean metallicity); also resets w.trange.
+// mean metallicity); also resets w.trange and w.kmask.
 cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride, int64_t g_begin,
                          int64_t n, cudaStream_t s);
 // Sums the tensor-core kernel's per-part filter sums and writes magnitudes.

@@ -165,18 +165,18 @@ __device__ __forceinline__ void epi_close_grad(float (&acc)[3][4 * Q4], const Sl
 // Columns (in 32-wide blocks [kb0, kb1)) of the adjoint Shat[g, n] that can be
 // non-zero for the 128-row galaxy tile mt: Shat_n uses grid indices n + i0 - 1
 // .. n + i0 + 2, so it vanishes unless n + i0 lies in [m_nz_lo - 2, m_nz_hi + 1]
-// for some i0 of the tile (trange.x .. trange.y, over its valid rows).  At
+// for some i0 of the tile (trange x .. y, over its valid rows).  At
 // least one block is kept.
 struct VjpBand {
     int on, m_nz_lo, m_nz_hi, Q;
 };
 
-__device__ __forceinline__ void vjp_band(const VjpBand &b, const int4 *trange, int mt, int N_pad, int &kb0,
+__device__ __forceinline__ void vjp_band(const VjpBand &b, const int2 *trange, int mt, int N_pad, int &kb0,
                                          int &kb1) {
     kb0 = 0;
     kb1 = N_pad / 32;
     if (!b.on) return;
-    const int4 r = trange[mt];
+    const int2 r = trange[mt];
     const int n_lo = r.y < r.x ? 0 : max(b.m_nz_lo - r.y - 2, 0);
     const int n_hi = r.y < r.x ? -1 : min(b.m_nz_hi - r.x + 1, N_pad - 1);
     if (b.m_nz_hi < b.m_nz_lo || n_hi < n_lo) {

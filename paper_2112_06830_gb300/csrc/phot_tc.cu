@@ -11,7 +11,7 @@
 // (tc::UnitRing), so that units of unequal cost balance across SMs; each tile sweeps the
 // 256-wide wavelength tiles inside its redshifted filter band, and contracts
 // only the K blocks (metallicity-major K) where some row's weights are non-zero
-// (tile_ranges).  Warp roles:
+// (tile_ranges, next_kb).  Warp roles:
 //   warp 0      TMA producer: 4-stage ring of {W_hi, W_lo, L_hi, L_lo} K-slices
 //               (32 bf16 = 64 B rows, 64-byte swizzle), one mbarrier per stage.
 //   warp 1      TMEM allocator and single-thread MMA issuer: per K-slice six
@@ -53,7 +53,9 @@ constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + 
 
 struct TArgs {
     const float *aux;
-    const int4 *trange;             // per-tile ranges from the weights kernel
+    const int2 *trange;             // per-tile redshift-shift ranges from the weights kernel
+    const unsigned *kmask;          // per-tile kz-block masks from the weights kernel, or nullptr
+    int kmw;                        // mask words per tile
     const float4 *tab;
     ColConst cc;
     int m_last, n_mtiles, n_ntiles, kblocks, parts, n_units;
@@ -65,29 +67,42 @@ struct TArgs {
     unsigned *err;
 };
 
-// Wavelength tiles [nt0, nt1) and K blocks [kb0, kb1) that galaxy tile mt
-// needs, from the tile's exact ranges over its valid rows (trange: smallest and
-// largest floor(s), first and last non-zero kz).  A wavelength tile whose
+// Wavelength tiles [nt0, nt1) that galaxy tile mt needs and its K-block mask
+// (up to 128 blocks, held in registers; all ones without skipping), from the
+// tile's exact ranges over its valid rows.  A wavelength tile whose
 // interpolation rows (grid indices n + i0 - 1 .. n + i0 + 2) fall outside the
 // band [m_nz_lo, m_nz_hi] of non-zero transmission for every i0 of the tile,
 // and a K block where every row's weights are zero, contribute exact zeros and
 // are skipped.  A tile with no non-zero weight does no work.
-__device__ __forceinline__ void tile_ranges(const TArgs &a, int mt, int &nt0, int &nt1, int &kb0, int &kb1) {
+__device__ __forceinline__ void tile_ranges(const TArgs &a, int mt, int &nt0, int &nt1, uint4 &km) {
     nt0 = 0;
     nt1 = a.n_ntiles;
-    kb0 = 0;
-    kb1 = a.kblocks;
+    km = make_uint4(~0u, ~0u, ~0u, ~0u);
     if (!a.band_skip) return;
-    const int4 r = a.trange[mt];
-    if (r.w < r.z || a.m_nz_hi < a.m_nz_lo) { nt1 = nt0; return; }
-    kb0 = r.z / BK;
-    kb1 = r.w / BK + 1;
+    const int2 r = a.trange[mt];
+    if (a.kmask) {
+        const unsigned *m = a.kmask + (size_t)mt * a.kmw;
+        km = make_uint4(__ldg(m), a.kmw > 1 ? __ldg(m + 1) : 0u, a.kmw > 2 ? __ldg(m + 2) : 0u,
+                        a.kmw > 3 ? __ldg(m + 3) : 0u);
+    }
+    if (r.y < r.x || a.m_nz_hi < a.m_nz_lo || (km.x | km.y | km.z | km.w) == 0u) { nt1 = nt0; return; }
     const int n_lo = a.m_nz_lo - r.y - 2;
     const int n_hi = a.m_nz_hi - r.x + 1;
     if (n_hi < 0) { nt1 = nt0; return; }
     nt0 = n_lo <= 0 ? 0 : n_lo / BN;
     nt1 = min(a.n_ntiles, n_hi / BN + 1);
     if (nt1 < nt0) nt1 = nt0;
+}
+
+// First K block >= kb set in the tile's mask (a.kblocks if none).
+__device__ __forceinline__ int next_kb(const TArgs &a, const uint4 &km, int kb) {
+    while (kb < a.kblocks) {
+        const int wi = kb >> 5;
+        const unsigned w = (wi == 0 ? km.x : wi == 1 ? km.y : wi == 2 ? km.z : km.w) >> (kb & 31);
+        if (w) return min(kb + __ffs(w) - 1, a.kblocks);
+        kb = (kb | 31) + 1;
+    }
+    return a.kblocks;
 }
 
 // Wavelength tile nt belongs to part nt mod parts, whatever the tile's range:
@@ -165,10 +180,11 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                 if (!ring_claim(ring, a.sched, a.n_units, u, abort_flag, a.err)) break;
                 if (u < 0) break;
                 const int mt = u / a.parts, part = u - mt * a.parts;
-                int nt0, nt1, kb0, kb1;
-                tile_ranges(a, mt, nt0, nt1, kb0, kb1);
+                int nt0, nt1;
+                uint4 km;
+                tile_ranges(a, mt, nt0, nt1, km);
                 for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts)
-                    for (int kb = kb0; kb < kb1; ++kb) {
+                    for (int kb = next_kb(a, km, 0); kb < a.kblocks; kb = next_kb(a, km, kb + 1)) {
                         if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                         const uint32_t fb = full0 + 8 * stage;
                         const uint32_t st = sbase + stage * STAGE_BYTES;
@@ -200,13 +216,15 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                 int u;
                 if (!ring_next(ring, u, abort_flag, a.err) || u < 0) break;
                 const int mt = u / a.parts, part = u - mt * a.parts;
-                int nt0, nt1, kb0, kb1;
-                tile_ranges(a, mt, nt0, nt1, kb0, kb1);
+                int nt0, nt1;
+                uint4 km;
+                tile_ranges(a, mt, nt0, nt1, km);
+                const int kb_first = next_kb(a, km, 0);
                 for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
                     if (!mbar_wait(acce0 + 8 * as, aphase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d = tmem_base + (uint32_t)(as * BN);
-                    for (int kb = kb0; kb < kb1; ++kb) {
+                    for (int kb = kb_first; kb < a.kblocks; kb = next_kb(a, km, kb + 1)) {
                         if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, a.err)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t st = sbase + stage * STAGE_BYTES;
@@ -216,16 +234,16 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                             const uint64_t al = sdesc_sw64(st + A_BYTES + kk * 32);
                             const uint64_t bh = sdesc_sw64(st + 2 * A_BYTES + kk * 32);
                             const uint64_t bl = sdesc_sw64(st + 2 * A_BYTES + B_BYTES + kk * 32);
-                            mma_bf16(d, ah, bh, (kb != kb0 || kk != 0) ? 1u : 0u);
+                            mma_bf16(d, ah, bh, (kb != kb_first || kk != 0) ? 1u : 0u);
                             mma_bf16(d, ah, bl, 1u);
                             mma_bf16(d, al, bh, 1u);
                         }
                         mma_commit(empty0 + 8 * stage);
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                        ++nblk;
                     }
                     if (!ok) break;
                     mma_commit(accf0 + 8 * as);
-                    nblk += (unsigned long long)(kb1 - kb0);
                     if (++as == 2) { as = 0; aphase ^= 1u; }
                 }
             }
@@ -252,8 +270,9 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
             u = __shfl_sync(0xffffffffu, u, 0);
             if (!have || u < 0) break;
             const int mt = u / a.parts, part = u - mt * a.parts;
-            int nt0, nt1, kb0, kb1;
-            tile_ranges(a, mt, nt0, nt1, kb0, kb1);
+            int nt0, nt1;
+            uint4 km;
+            tile_ranges(a, mt, nt0, nt1, km);
             const int64_t rowg = (int64_t)mt * BM + row;
             const RowConst rc = load_row_const(a.aux, rowg, a.n);
             constexpr int NR = GRAD ? 3 : 1;   // sums per filter: N (and A, D for the gradient)
@@ -364,20 +383,22 @@ cudaError_t launch_phot_tc(const Ctx &c, const Workspace &w, const FilterSet &fs
     if (n <= 0) return cudaSuccess;
     if (fs.Q > QMAX) return cudaErrorInvalidValue;
     CUtensorMap ah, al, bh, bl;
-    if (!make_tmap(&ah, w.whi, (uint64_t)c.K_pad, (uint64_t)n, BM) ||
-        !make_tmap(&al, w.wlo, (uint64_t)c.K_pad, (uint64_t)n, BM) ||
-        !make_tmap(&bh, c.d_Lt_hi, (uint64_t)c.K_pad, (uint64_t)c.N_pad, BN) ||
-        !make_tmap(&bl, c.d_Lt_lo, (uint64_t)c.K_pad, (uint64_t)c.N_pad, BN))
+    if (!make_tmap(&ah, w.whi, (uint64_t)c.KZ_pad, (uint64_t)n, BM) ||
+        !make_tmap(&al, w.wlo, (uint64_t)c.KZ_pad, (uint64_t)n, BM) ||
+        !make_tmap(&bh, c.d_Lt_hi, (uint64_t)c.KZ_pad, (uint64_t)c.N_pad, BN) ||
+        !make_tmap(&bl, c.d_Lt_lo, (uint64_t)c.KZ_pad, (uint64_t)c.N_pad, BN))
         return cudaErrorInvalidValue;
     TArgs a{};
     a.aux = w.aux;
     a.trange = w.trange;
+    a.kmask = c.kmask_words <= 4 ? w.kmask : nullptr;   // larger grids contract every K block
+    a.kmw = c.kmask_words;
     a.tab = reinterpret_cast<const float4 *>(fs.d_tab);
     a.cc = make_col_const(c);
     a.m_last = fs.m_rows - 1;
     a.n_mtiles = (int)((n + BM - 1) / BM);
     a.n_ntiles = c.N_pad / BN;
-    a.kblocks = c.K_pad / BK;
+    a.kblocks = c.KZ_pad / BK;
     a.parts = TC_PARTS;
     a.n_units = a.n_mtiles * TC_PARTS;
     a.band_skip = c.opts.band_skip ? 1 : 0;

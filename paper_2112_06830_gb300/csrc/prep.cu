@@ -2,8 +2,8 @@
 // spectra are computed in advance, loaded once as a contiguous block and held
 // fixed).  Builds, from the caller's FP32 L[k][n] (k = i * n_z + j):
 //   d_L32   [K_pad][N_pad] FP32, zero padded                (SIMT form)
-//   d_Lt_*  [N_pad][K_pad] bf16 hi / lo of L[k][n] 2^-E_k    (tensor form, K-contiguous
-//           rows, columns in the metallicity-major order kz = j * n_age + i)
+//   d_Lt_*  [N_pad][KZ_pad] bf16 hi / lo of L[k][n] 2^-E_k   (tensor form, K-contiguous
+//           rows, columns in the metallicity-major order kz = j * A_pad + i)
 //   d_Ld32  [K_pad][N_pad] FP32 metallicity-differenced block: row (i, 0) is
 //           L[i, 0], row (i, j >= 1) is L[i, j] - L[i, j-1]   (FP32 adjoint)
 //   d_L_*   [K_pad][N_pad] bf16 hi / lo of the differenced block scaled by
@@ -11,7 +11,7 @@
 // The adjoint contracts with the differenced block so that the differences of
 // dLoss/domega between neighbouring metallicity bins -- all the metallicity
 // gradients need (summation by parts) -- come out at full relative precision.
-//   d_wmul  [K_pad] 2^E_k, the factor folded into the weights, so that
+//   d_wmul  [KZ_pad] 2^E_k, the factor folded into the weights, so that
 //           sum_k (omega_k 2^E_k)(L_kn 2^-E_k) = sum_k omega_k L_kn exactly
 //           (indexed by kz, like d_Lt_*).
 // E_k is the binary exponent of max_n L[k][n]: every scaled row peaks in
@@ -23,7 +23,7 @@ namespace dsps {
 namespace {
 
 // wmul is written at the metallicity-major position of row k, rscale at k.
-__global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, int n_age, int n_z, float *wmul,
+__global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, int a_pad, int n_z, float *wmul,
                                     float *rscale) {
     const int k = blockIdx.x;
     if (k >= K_pad) return;
@@ -40,7 +40,7 @@ __global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, int
         int E = 0;
         if (mm > 0.f) E = ilogbf(mm);
         E = max(-120, min(120, E));
-        wmul[k < K ? k_to_kz(k, n_age, n_z) : k] = k < K ? ldexpf(1.f, E) : 0.f;
+        if (k < K) wmul[k_to_kz(k, a_pad, n_z)] = ldexpf(1.f, E);
         rscale[k] = k < K ? ldexpf(1.f, -E) : 0.f;
     }
 }
@@ -54,25 +54,26 @@ __global__ void build_l32_kernel(const float *L, int K, int N, int K_pad, int N_
 }
 
 // Transposing split: tile of 32 (kz) x 32 (n) through shared memory; column
-// kz of the output takes SSP row k = kz_to_k(kz).
-__global__ void build_lt_kernel(const float *L, const float *rscale, int K, int N, int K_pad, int N_pad, int n_age,
-                                int n_z, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+// kz of the output [N_pad][KZ_pad] takes SSP row k = kz_to_k(kz) (zero for
+// padding columns).
+__global__ void build_lt_kernel(const float *L, const float *rscale, int N, int KZ_pad, int N_pad, int a_pad,
+                                int n_age, int n_z, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
     __shared__ float t[32][33];
     const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     for (int r = ty; r < 32; r += 8) {
         const int kz = k0 + r, n = n0 + tx;
-        const int k = kz < K ? kz_to_k(kz, n_age, n_z) : kz;
-        t[r][tx] = (kz < K && n < N) ? L[(size_t)k * N + n] * rscale[k] : 0.f;
+        const int k = kz_to_k(kz, a_pad, n_age, n_z);
+        t[r][tx] = (k >= 0 && n < N) ? L[(size_t)k * N + n] * rscale[k] : 0.f;
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         int n = n0 + r, k = k0 + tx;
-        if (n < N_pad && k < K_pad) {
+        if (n < N_pad && k < KZ_pad) {
             float v = t[tx][r];
             __nv_bfloat16 h = __float2bfloat16_rn(v);
-            hi[(size_t)n * K_pad + k] = h;
-            lo[(size_t)n * K_pad + k] = __float2bfloat16_rn(v - __bfloat162float(h));
+            hi[(size_t)n * KZ_pad + k] = h;
+            lo[(size_t)n * KZ_pad + k] = __float2bfloat16_rn(v - __bfloat162float(h));
         }
     }
 }
@@ -130,12 +131,13 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
     if (e != cudaSuccess) return e;
     e = cudaMalloc(&d_rscale, (size_t)c.K_pad * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(d_raw, h_lssp, KN * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c.d_wmul, 0, (size_t)c.KZ_pad * sizeof(float));
     if (e == cudaSuccess) {
-        row_exponent_kernel<<<c.K_pad, 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.n_age, c.n_z, c.d_wmul, d_rscale);
+        row_exponent_kernel<<<c.K_pad, 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.A_pad, c.n_z, c.d_wmul, d_rscale);
         const size_t tot = (size_t)c.K_pad * c.N_pad;
         build_l32_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.N_pad, c.d_L32);
-        dim3 g(c.N_pad / 32, c.K_pad / 32), b(32, 8);
-        build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.K, c.n_lam, c.K_pad, c.N_pad, c.n_age, c.n_z, c.d_Lt_hi,
+        dim3 g(c.N_pad / 32, c.KZ_pad / 32), b(32, 8);
+        build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.n_lam, c.KZ_pad, c.N_pad, c.A_pad, c.n_age, c.n_z, c.d_Lt_hi,
                                   c.d_Lt_lo);
         const unsigned blk = (unsigned)((tot + 255) / 256);
         build_ldiff_kernel<<<blk, 256>>>(d_raw, c.K, c.n_lam, c.n_z, c.K_pad, c.N_pad, c.d_Ld32);

@@ -55,12 +55,12 @@ cudaError_t scratch_address(int dev, unsigned char **out) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Largest population that fits: [rows][K_pad] FP32 weights, then
-// [rows][AUX_STRIDE] FP32 constants, then [rows] FP64 offsets.
+// [rows][AUX_STRIDE] FP32 constants, [rows] FP64 offsets and [rows] GalPrep.
 int64_t max_rows(int K_pad) {
-    const size_t per = (size_t)K_pad * 4 + AUX_STRIDE * 4 + 8;
-    int64_t r = (int64_t)((STATIC_SCRATCH_BYTES - 3 * 256) / per);
+    const size_t per = (size_t)K_pad * 4 + AUX_STRIDE * 4 + 8 + sizeof(GalPrep);
+    int64_t r = (int64_t)((STATIC_SCRATCH_BYTES - 4 * 256) / per);
     while (r > 0 && align256((size_t)r * K_pad * 4) + align256((size_t)r * AUX_STRIDE * 4) +
-                            align256((size_t)r * 8) > STATIC_SCRATCH_BYTES)
+                            align256((size_t)r * 8) + align256((size_t)r * sizeof(GalPrep)) > STATIC_SCRATCH_BYTES)
         --r;
     return r;
 }
@@ -103,7 +103,9 @@ extern "C" int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const f
     ws.w32 = reinterpret_cast<float *>(base);
     const size_t off_aux = align256((size_t)cap * c->K_pad * 4);
     ws.aux = reinterpret_cast<float *>(base + off_aux);
-    ws.magoff = reinterpret_cast<double *>(base + off_aux + align256((size_t)cap * AUX_STRIDE * 4));
+    const size_t off_mo = off_aux + align256((size_t)cap * AUX_STRIDE * 4);
+    ws.magoff = reinterpret_cast<double *>(base + off_mo);
+    ws.prep = reinterpret_cast<GalPrep *>(base + off_mo + align256((size_t)cap * 8));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const FilterSet &fs = c->sets[set_id];
     e = launch_weights(*c, ws, W_OMEGA_F32, params, n_gal, 0, n_gal, nullptr, s);

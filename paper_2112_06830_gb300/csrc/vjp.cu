@@ -56,7 +56,7 @@ __global__ void combine_grad_kernel(const float *partial, int parts, int64_t n, 
 
 // One warp per (sorted) row: Shat over the row's band columns [32 kb0, 32 kb1).
 template <int Q4, bool BF16>
-__global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int4 *trange, const float *cq,
+__global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 *trange, const float *cq,
                                                    const float4 *tab, int m_last, ColConst cc, int64_t n, int N_pad,
                                                    VjpBand band, float *out32,
                                                    __nv_bfloat16 *out_hi, __nv_bfloat16 *out_lo) {

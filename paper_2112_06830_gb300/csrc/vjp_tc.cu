@@ -32,7 +32,7 @@ constexpr size_t BAR_BYTES = 1024;
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES;
 
 struct VArgs {
-    const int4 *trange;
+    const int2 *trange;
     VjpBand band;
     int n_mtiles, n_ktiles, n_units, N_pad, K_pad;
     int64_t n;

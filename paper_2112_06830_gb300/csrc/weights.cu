@@ -17,8 +17,9 @@
 //   6. Joint weights omega_ij = P_SFH(i) P_met(j | i) (Eq. full_mdf), written as
 //      Msun (dsps_weights), FP32 per unit mass (SIMT photometry) or scaled by
 //      the SSP row multiplier and split into bf16 hi + lo (tensor photometry,
-//      metallicity-major K, with the per-tile ranges of Workspace::trange).
+//      metallicity-major K, with the per-tile ranges and kz-block masks).
 #include <climits>
+#include <cmath>
 
 #include "dsps_internal.cuh"
 
@@ -27,8 +28,9 @@ namespace dsps {
 struct WArgs {
     const float *params;
     int64_t G_stride, g_begin, n;
-    int n_age, n_z, K, K_pad, n_t, sfh_model, mdf_kernel, n_lut;
+    int n_age, n_z, K, K_pad, A_pad, KZ_pad, n_t, sfh_model, mdf_kernel, n_lut;
     double t0, h, inv_h, dz, inv_dz, zmax, dlnlam;
+    float zmax_f;          // largest float <= zmax (z <= zmax_f iff (double)z <= zmax)
     const float *logage;
     const float *einh;     // [n_age+1] age-bin edge / h
     const float *bwidth;   // [n_age] e_{i+1} - e_i [Gyr]
@@ -41,13 +43,23 @@ struct WArgs {
     double *magoff;
     const int *perm;   // sorted row -> chunk-local galaxy, or nullptr
     int *gidx;         // out: sorted row -> chunk-local galaxy, or nullptr
-    int4 *trange;      // out: per-tile ranges (atomics), or nullptr
+    int2 *trange;      // out: per-tile redshift-shift ranges (atomics), or nullptr
+    unsigned *kmask;   // out: per-tile kz-block masks (atomics), with trange
+    int kmw;           // mask words per tile
+    GalPrep *prep;     // per-galaxy scalars, chunk order (galaxy_prep_kernel)
     unsigned *err;
 };
 
-// Sec. 3.1: SFR at cosmic time t [Gyr] (arbitrary normalisation).
-__device__ __forceinline__ float sfr_f(int model, const float *p, float t) {
-    if (model == DSPS_SFH_DELAYED_TAU) return t * expf(-t / p[0]);
+// Sec. 3.1: SFR at cosmic time t [Gyr] (arbitrary normalisation).  The power
+// laws take ln(t / tau) of the correctly rounded ratio, which keeps the
+// exponent's absolute error near 1e-7 (the metallicity gradients, sums with
+// strong cancellation, see that error through the age-bin fractions).
+// The SFH model and the metallicity kernel are template parameters of the
+// kernels (SFH = DSPS_SFH_*, MDF = DSPS_MDF_*), so that no evaluation pays
+// for the other model's branch.
+template <int SFH>
+__device__ __forceinline__ float sfr_f(const float *p, float t) {
+    if constexpr (SFH == DSPS_SFH_DELAYED_TAU) return t * expf(-t / p[0]);
     float lr = logf(t / p[0]);
     float ms = 1.f / (expf(-p[1] * lr) + expf(-p[2] * lr));
     float zq = (t - (p[3] - 0.9f)) * (1.f / 0.3f);
@@ -57,33 +69,22 @@ __device__ __forceinline__ float sfr_f(int model, const float *p, float t) {
 // Triweight / Gaussian CDF in the form S(u) = C(u) for u <= 0 and C(u) - 1 for
 // u > 0, so that differences of neighbouring edges keep their relative
 // precision in both tails; P = S(u_hi) - S(u_lo) + [u_lo <= 0 < u_hi].
-__device__ __forceinline__ float mdf_s(int kernel, float u) {
+template <int MDF>
+__device__ __forceinline__ float mdf_s(float u) {
     const float a = -fabsf(u);
-    const float c = kernel == DSPS_MDF_TRIWEIGHT ? terf_lower_f(a) : gauss_cdf_f(a);
+    float c;
+    if constexpr (MDF == DSPS_MDF_TRIWEIGHT) c = terf_lower_f(a);
+    else c = gauss_cdf_f(a);
     return u > 0.f ? -c : c;
 }
 
-// P_met of the bin between standardised edges u_lo < u_hi (first / last bin:
-// open below / above).  The triweight vanishes outside [-3, 3], and a bin
-// entirely beyond either end is exactly 0 without evaluating the CDF (the
-// general expression gives the same 0).
-__device__ __forceinline__ float mdf_bin(int kernel, float u_lo, float u_hi, bool first, bool last) {
-    if (kernel == DSPS_MDF_TRIWEIGHT && (u_hi <= -3.f || u_lo >= 3.f)) return 0.f;
-    float p = (last ? 0.f : mdf_s(kernel, u_hi)) - (first ? 0.f : mdf_s(kernel, u_lo));
-    if (u_lo <= 0.f && u_hi > 0.f) p += 1.f;
-    return p;
-}
-
-// Bins spanning more time intervals than this use the FP32 node prefix (their
-// mass is a large share of the prefix, so the difference does not cancel).
-constexpr int PREFIX_SPAN = 64;
-
 __host__ __device__ inline size_t weights_smem_per_warp(int n_t, int n_age) {
-    return (((size_t)n_t * 3 + (size_t)(n_age + 1) * 2 + (size_t)n_age * 2) * 4 + 15) & ~(size_t)15;
+    return (((size_t)n_t * 4 + (size_t)(n_age + 1) * 2 + (size_t)n_age * 2) * 4 + 15) & ~(size_t)15;
 }
 
 struct SfhSmem {
-    float *sfr, *itg, *cum;   // [n_t] SFR at nodes, interval integrals, FP32 node prefix
+    float *sfr, *itg;         // [n_t] SFR at nodes, interval integrals
+    float *cum_hi, *cum_lo;   // [n_t] node prefix of the interval integrals, unevaluated sum hi + lo
     int *em;                  // [n_age + 1] interval index of each age-bin edge
     float *er;                // [n_age + 1] position of the edge inside its interval
     float *bmass, *frac;      // [n_age] bin masses, fractions of the total
@@ -93,67 +94,75 @@ __device__ __forceinline__ SfhSmem sfh_smem(unsigned char *base, int n_t, int n_
     SfhSmem m;
     m.sfr = reinterpret_cast<float *>(base);
     m.itg = m.sfr + n_t;
-    m.cum = m.itg + n_t;
-    m.em = reinterpret_cast<int *>(m.cum + n_t);
+    m.cum_hi = m.itg + n_t;
+    m.cum_lo = m.cum_hi + n_t;
+    m.em = reinterpret_cast<int *>(m.cum_lo + n_t);
     m.er = reinterpret_cast<float *>(m.em + n_age + 1);
     m.bmass = m.er + n_age + 1;
     m.frac = m.bmass + n_age;
     return m;
 }
 
-// Stages 1-4 for one galaxy (whole warp): SFR at the nodes, the age-bin
+// Error-free sum: s + e = a + b exactly (Knuth's TwoSum, six FP32 additions).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Stages 2-4 for one galaxy (whole warp), given t_obs's position on the time
+// grid (m_obs + f_obs, from galaxy_prep_kernel): SFR at the nodes, the age-bin
 // masses and their fractions of the total; returns the galaxy's validity and
-// the total formed mass (FP64) through msum_out.
-__device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool valid, int lane, const SfhSmem &sm,
-                                       double &msum_out) {
-    float *sfr = sm.sfr, *itg = sm.itg, *cum = sm.cum, *er = sm.er, *bmass = sm.bmass, *frac = sm.frac;
+// the total formed mass through msum_out.
+template <int SFH>
+__device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool valid, int m_obs, float f_obs, int lane,
+                                       const SfhSmem &sm, float &msum_out) {
+    float *sfr = sm.sfr, *itg = sm.itg, *er = sm.er, *bmass = sm.bmass, *frac = sm.frac;
+    float *ch = sm.cum_hi, *cl = sm.cum_lo;
     int *em = sm.em;
-    const float z = p[11];
-    // 1. cosmology: FP64 table lookup of t_obs, and t_obs's position on the
-    //    time grid, a = (t_obs - t0)/h = m_obs + f_obs (FP64, split once)
-    int m_obs = 0;
-    float f_obs = 0.f;
-    if (lane == 0 && valid) {
-        double x = (double)z * a.inv_dz;
-        int i = min((int)x, a.n_lut - 2);
-        double fr = x - i;
-        const double t_obs = a.tlut[i] + fr * (a.tlut[i + 1] - a.tlut[i]);
-        const double apos = (t_obs - a.t0) * a.inv_h;
-        if (apos > 0.0) {
-            m_obs = min((int)apos, a.n_t - 2);
-            f_obs = (float)(apos - m_obs);
-        } else {
-            m_obs = -1;
-        }
-    }
-    m_obs = __shfl_sync(0xffffffffu, m_obs, 0);
-    f_obs = __shfl_sync(0xffffffffu, f_obs, 0);
     valid = valid && m_obs >= 0;
 
     // 2. SFR at the time nodes (FP32) and the interval integrals I_j
     const float h = (float)a.h;
     for (int n = lane; n < a.n_t; n += 32)
-        sfr[n] = valid ? sfr_f(a.sfh_model, p, fmaf((float)n, h, (float)a.t0)) : 0.f;
+        sfr[n] = valid ? sfr_f<SFH>(p, fmaf((float)n, h, (float)a.t0)) : 0.f;
     __syncwarp();
     for (int j = lane; j < a.n_t - 1; j += 32) itg[j] = 0.5f * h * (sfr[j] + sfr[j + 1]);
     __syncwarp();
 
-    // 3. FP32 prefix of the interval integrals at the nodes, C[j] = sum_{j'<j} I_j'
-    //    (used only for bins wider than PREFIX_SPAN intervals, where it does not cancel)
+    // 3. node prefix C[j] = sum_{j'<j} I_j' as an unevaluated FP32 pair
+    //    (TwoSum at every addition): a bin's mass C[mi] - C[mo+1] then keeps
+    //    FP32 relative precision however small it is next to C.  Each lane
+    //    sums a run of cnt intervals; an inclusive warp scan of the run sums
+    //    gives every run's offset.
     const int cnt = (a.n_t + 31) / 32;
     const int b = min(lane * cnt, a.n_t), e = min(b + cnt, a.n_t);
-    float tot = 0.f;
-    for (int j = b; j < e && j < a.n_t - 1; ++j) tot += itg[j];
-    float incl = tot;
+    float th = 0.f, tl = 0.f;
+    for (int j = b; j < e && j < a.n_t - 1; ++j) {
+        float err;
+        two_sum(th, itg[j], th, err);
+        tl += err;
+    }
+    float ih = th, il = tl;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        float o = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += o;
+        const float oh = __shfl_up_sync(0xffffffffu, ih, off), ol = __shfl_up_sync(0xffffffffu, il, off);
+        if (lane >= off) {
+            float err;
+            two_sum(ih, oh, ih, err);
+            il = il + ol + err;
+        }
     }
-    float run = incl - tot;
+    float rh = __shfl_up_sync(0xffffffffu, ih, 1), rl = __shfl_up_sync(0xffffffffu, il, 1);
+    if (lane == 0) rh = rl = 0.f;
     for (int j = b; j < e; ++j) {
-        cum[j] = run;
-        if (j < a.n_t - 1) run += itg[j];
+        ch[j] = rh;
+        cl[j] = rl;
+        if (j < a.n_t - 1) {
+            float err;
+            two_sum(rh, itg[j], rh, err);
+            rl += err;
+        }
     }
     // position of every age-bin edge on the time grid: y = f_obs - e/h
     for (int ei = lane; ei <= a.n_age; ei += 32) {
@@ -165,7 +174,9 @@ __device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool vali
     __syncwarp();
 
     // 4. age-bin masses (Eq. cspsum's P_SFH numerator) integrated directly from
-    //    the piecewise-linear SFR; the total (Eq. mstartot at t_obs) in FP64.
+    //    the piecewise-linear SFR: partial intervals at both edges plus the
+    //    whole intervals between them (a difference of the prefix pair); the
+    //    total (Eq. mstartot at t_obs) as a warp tree sum.
     float lsum = 0.f;
     for (int i = lane; i < a.n_age; i += 32) {
         const int mi = em[i], mo = em[i + 1];
@@ -175,7 +186,7 @@ __device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool vali
             const float si = fmaf(sfr[mi + 1] - sfr[mi], ri, sfr[mi]);         // SFR at the younger edge
             const float Pi = 0.5f * h * ri * (sfr[mi] + si);                     // int_{t_mi}^{tau_i}
             if (mo < 0) {
-                B = cum[mi] + Pi;
+                B = (ch[mi] + cl[mi]) + Pi;
             } else {
                 const float so = fmaf(sfr[mo + 1] - sfr[mo], ro, sfr[mo]);     // SFR at the older edge
                 const float w = __ldg(a.bwidth + i);                             // tau_i - tau_{i+1}, exact
@@ -186,12 +197,7 @@ __device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool vali
                     B = 0.5f * (w - yv) * (so + sfr[mi]) + 0.5f * yv * (sfr[mi] + si);
                 } else {
                     const float Qo = 0.5f * h * (1.f - ro) * (so + sfr[mo + 1]);  // int_{tau_o}^{t_mo+1}
-                    float mid = 0.f;
-                    if (mi - mo <= PREFIX_SPAN) {
-                        for (int j = mo + 1; j < mi; ++j) mid += itg[j];
-                    } else {
-                        mid = cum[mi] - cum[mo + 1];
-                    }
+                    const float mid = (ch[mi] - ch[mo + 1]) + (cl[mi] - cl[mo + 1]);
                     B = Qo + mid + Pi;
                 }
             }
@@ -199,21 +205,51 @@ __device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool vali
         bmass[i] = B;
         lsum += B;
     }
-    double msum = (double)lsum;
+    float msum = lsum;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, off);
-    valid = valid && msum > 0.0 && isfinite(msum);
-    const float inv_mtot = valid ? 1.f / (float)msum : 0.f;
+    valid = valid && msum > 0.f && isfinite(msum);
+    const float inv_mtot = valid ? 1.f / msum : 0.f;
     __syncwarp();
     for (int i = lane; i < a.n_age; i += 32) frac[i] = bmass[i] * inv_mtot;
     __syncwarp();
     msum_out = msum;
     return valid;
-
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
+// Stage 1 (Sec. 2.2), one thread per galaxy: t_obs(z) from the FP64 cosmology
+// table and its position on the SFR time grid, (t_obs - t0)/h = m_obs + f_obs
+// (split once in FP64), and the magnitude offset -2.5 logM + Dmod(z) - 2.5
+// log10(1+z).  Kept apart from the per-galaxy warps of the weights kernels so
+// that the FP64 arithmetic (slow on this GPU) runs one galaxy per lane.
+__global__ void galaxy_prep_kernel(WArgs a, GalPrep *out) {
+    const int64_t gl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gl >= a.n) return;
+    const int64_t g = a.g_begin + gl;
+    const float z = a.params[11 * a.G_stride + g];
+    GalPrep r;
+    r.m_obs = -1;
+    r.f_obs = 0.f;
+    r.magoff = __longlong_as_double(0x7ff8000000000000LL);
+    if (z > 0.f && (double)z <= a.zmax) {
+        const double x = (double)z * a.inv_dz;
+        const int i = min((int)x, a.n_lut - 2);
+        const double fr = x - i;
+        const double t_obs = a.tlut[i] + fr * (a.tlut[i + 1] - a.tlut[i]);
+        const double apos = (t_obs - a.t0) * a.inv_h;
+        if (apos > 0.0) {
+            r.m_obs = min((int)apos, a.n_t - 2);
+            r.f_obs = (float)(apos - r.m_obs);
+        }
+        const double gz = a.glut[i] + fr * (a.glut[i + 1] - a.glut[i]);
+        const float lm = a.params[10 * a.G_stride + g];
+        r.magoff = -2.5 * (double)lm + gz + (double)(5.f * log10f(z)) - (double)(2.5f * log10f(1.f + z));
+    }
+    out[gl] = r;
+}
+
+template <int MODE, int SFH, int MDF>
+__global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
@@ -232,10 +268,11 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
 
     const float z = p[11], sig = p[6];
     bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NPAR);
-    valid = valid && z > 0.f && (double)z <= a.zmax && sig > 0.f && p[0] > 0.f;
+    valid = valid && z > 0.f && z <= a.zmax_f && sig > 0.f && p[0] > 0.f;
+    const GalPrep gp = a.prep[gl];
 
-    double msum = 0.0;
-    valid = sfh_stage(a, p, valid, lane, sm, msum);
+    float msum = 0.f;
+    valid = sfh_stage<SFH>(a, p, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
     float *frac = sm.frac;
 
     // 5-6. metallicity weights and output.
@@ -244,57 +281,108 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
     const float s_shift = valid ? log1pf(z) / (float)a.dlnlam : 0.f;   // redshift shift in grid steps
     const int nz = a.n_z;
     if constexpr (MODE == W_OMEGA_BF16X2) {
-        // Metallicity-major kz = j * n_age + i, four consecutive kz per lane
-        // (each weight from its own two CDF values: consecutive kz are
-        // neighbouring ages).  The lane also keeps the first and last kz it
-        // wrote non-zero, for the tile's K range.
-        const int na = a.n_age;
-        int kz_min = INT_MAX, kz_max = -1;
-        for (int kz = 4 * lane; kz < a.K_pad; kz += 128) {
-            float om[4];
-            int j = kz / na, i = kz - j * na;
+        // Metallicity-major kz = j * A_pad + i.  Lane g takes the ages 4g ..
+        // 4g+3 and walks the metallicity bins upwards, carrying each age's CDF
+        // at the bin's lower edge (the previous bin's upper edge): one CDF
+        // evaluation per weight, the arithmetic of the age-major loop below.
+        // The four weights of one (g, j) are consecutive in kz: one 8-byte
+        // store each of hi and lo, a warp writing one contiguous run.
+        //
+        // An invalid galaxy or a padding age gets fraction 0 and finite
+        // standardised edges, so its weights come out exactly 0.  For the
+        // triweight, a group whose four bins all lie beyond +-3 standard
+        // deviations is exactly 0 without evaluating the CDF (its carried
+        // lower-edge value is then 0 below the support, -0 above).
+        //
+        // Each lane marks, in a 128-bit register mask, the kz blocks (KBLOCK
+        // wide) where it wrote a non-zero weight; the warp's OR goes into the
+        // tile's mask (grids of more than 128 blocks keep no mask).
+        constexpr bool tri = MDF == DSPS_MDF_TRIWEIGHT;
+        const float isg = valid ? inv_sig : 0.f;
+        uint4 bm = make_uint4(0u, 0u, 0u, 0u);
+        __nv_bfloat16 *rh = a.whi + gi * a.KZ_pad, *rl = a.wlo + gi * a.KZ_pad;
+        for (int gq = lane; 4 * gq < a.A_pad; gq += 32) {
+            float mu4[4], fr4[4], ulo[4], slo[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                om[c] = 0.f;
-                if (kz + c < a.K && valid) {
-                    const float mu_i = fmaf(p[7], __ldg(a.logage + i) - 9.f, p[5]);
-                    const bool first = j == 0, last = j == nz - 1;
-                    const float u_lo = first ? -1e30f : (__ldg(a.zedge + j) - mu_i) * inv_sig;
-                    const float u_hi = last ? 1e30f : (__ldg(a.zedge + j + 1) - mu_i) * inv_sig;
-                    om[c] = frac[i] * mdf_bin(a.mdf_kernel, u_lo, u_hi, first, last);
-                    if (om[c] != 0.f) {
-                        kz_min = min(kz_min, kz + c);
-                        kz_max = kz + c;
+                const int i = 4 * gq + c;
+                mu4[c] = valid ? fmaf(p[7], __ldg(a.logage + min(i, a.n_age - 1)) - 9.f, p[5]) : 0.f;
+                fr4[c] = valid && i < a.n_age ? frac[i] : 0.f;
+                ulo[c] = -1e30f;
+                slo[c] = 0.f;
+            }
+            for (int j = 0; j < nz; ++j) {
+                const bool last = j == nz - 1;
+                const float ze = last ? 0.f : __ldg(a.zedge + j + 1);
+                float uh[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) uh[c] = last ? 1e30f : (ze - mu4[c]) * isg;
+                const float uh_max = fmaxf(fmaxf(uh[0], uh[1]), fmaxf(uh[2], uh[3]));
+                const float ul_min = fminf(fminf(ulo[0], ulo[1]), fminf(ulo[2], ulo[3]));
+                float om[4] = {0.f, 0.f, 0.f, 0.f};
+                bool nzg = false;
+                if (tri && (uh_max <= -3.f || ul_min >= 3.f)) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        slo[c] = uh[c] > 0.f ? -0.f : 0.f;
+                        ulo[c] = uh[c];
                     }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float s_hi = last ? 0.f : mdf_s<MDF>(uh[c]);
+                        float pj = s_hi - slo[c];
+                        if (ulo[c] <= 0.f && uh[c] > 0.f) pj += 1.f;
+                        om[c] = fr4[c] * pj;
+                        slo[c] = s_hi;
+                        ulo[c] = uh[c];
+                    }
+                    nzg = (om[0] != 0.f) | (om[1] != 0.f) | (om[2] != 0.f) | (om[3] != 0.f);
                 }
-                if (++i == na) {
-                    i = 0;
-                    ++j;
+                const int kz = j * a.A_pad + 4 * gq;
+                if (nzg) {
+                    const int b = kz / KBLOCK, wi = b >> 5;
+                    const unsigned bit = 1u << (b & 31);
+                    bm.x |= wi == 0 ? bit : 0u;
+                    bm.y |= wi == 1 ? bit : 0u;
+                    bm.z |= wi == 2 ? bit : 0u;
+                    bm.w |= wi == 3 ? bit : 0u;
+                }
+                {
+                    const float4 wm = __ldg(reinterpret_cast<const float4 *>(a.wmul + kz));
+                    const float w0 = om[0] * wm.x, w1 = om[1] * wm.y, w2 = om[2] * wm.z, w3 = om[3] * wm.w;
+                    const __nv_bfloat162 h01 = __floats2bfloat162_rn(w0, w1), h23 = __floats2bfloat162_rn(w2, w3);
+                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(w0 - __low2float(h01), w1 - __high2float(h01));
+                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(w2 - __low2float(h23), w3 - __high2float(h23));
+                    uint2 hv, lv;
+                    hv.x = *reinterpret_cast<const unsigned *>(&h01);
+                    hv.y = *reinterpret_cast<const unsigned *>(&h23);
+                    lv.x = *reinterpret_cast<const unsigned *>(&l01);
+                    lv.y = *reinterpret_cast<const unsigned *>(&l23);
+                    *reinterpret_cast<uint2 *>(rh + kz) = hv;
+                    *reinterpret_cast<uint2 *>(rl + kz) = lv;
                 }
             }
-            const float4 wm = __ldg(reinterpret_cast<const float4 *>(a.wmul + kz));
-            const float w0 = om[0] * wm.x, w1 = om[1] * wm.y, w2 = om[2] * wm.z, w3 = om[3] * wm.w;
-            const __nv_bfloat162 h01 = __floats2bfloat162_rn(w0, w1), h23 = __floats2bfloat162_rn(w2, w3);
-            const __nv_bfloat162 l01 = __floats2bfloat162_rn(w0 - __low2float(h01), w1 - __high2float(h01));
-            const __nv_bfloat162 l23 = __floats2bfloat162_rn(w2 - __low2float(h23), w3 - __high2float(h23));
-            uint2 hv, lv;
-            hv.x = *reinterpret_cast<const unsigned *>(&h01);
-            hv.y = *reinterpret_cast<const unsigned *>(&h23);
-            lv.x = *reinterpret_cast<const unsigned *>(&l01);
-            lv.y = *reinterpret_cast<const unsigned *>(&l23);
-            *reinterpret_cast<uint2 *>(a.whi + gi * a.K_pad + kz) = hv;
-            *reinterpret_cast<uint2 *>(a.wlo + gi * a.K_pad + kz) = lv;
         }
-        kz_min = __reduce_min_sync(0xffffffffu, kz_min);
-        kz_max = __reduce_max_sync(0xffffffffu, kz_max);
-        if (lane == 0 && a.trange && valid) {
-            int4 *t = a.trange + (gi >> 7);
-            const int i0 = (int)floorf(s_shift);
-            atomicMin(&t->x, i0);
-            atomicMax(&t->y, i0);
-            if (kz_max >= 0) {
-                atomicMin(&t->z, kz_min);
-                atomicMax(&t->w, kz_max);
+        // padding columns [n_z * A_pad, KZ_pad)
+        for (int kz = nz * a.A_pad + 4 * lane; kz < a.KZ_pad; kz += 128) {
+            *reinterpret_cast<uint2 *>(rh + kz) = make_uint2(0u, 0u);
+            *reinterpret_cast<uint2 *>(rl + kz) = make_uint2(0u, 0u);
+        }
+        bm.x = __reduce_or_sync(0xffffffffu, bm.x);
+        bm.y = __reduce_or_sync(0xffffffffu, bm.y);
+        bm.z = __reduce_or_sync(0xffffffffu, bm.z);
+        bm.w = __reduce_or_sync(0xffffffffu, bm.w);
+        if (a.trange && valid) {
+            const int64_t t = gi >> 7;
+            if (lane < a.kmw && a.kmw <= 4) {
+                const unsigned v = lane == 0 ? bm.x : lane == 1 ? bm.y : lane == 2 ? bm.z : bm.w;
+                if (v) atomicOr(a.kmask + t * a.kmw + lane, v);
+            }
+            if (lane == 0) {
+                const int i0 = (int)floorf(s_shift);
+                atomicMin(&a.trange[t].x, i0);
+                atomicMax(&a.trange[t].y, i0);
             }
         }
     } else {
@@ -310,14 +398,14 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
             int i = i0, j = j0;
             float mu_i = fmaf(p[7], __ldg(a.logage + min(i, a.n_age - 1)) - 9.f, p[5]);
             float u_lo = (__ldg(a.zedge + j) - mu_i) * inv_sig;
-            float s_lo = j == 0 ? 0.f : mdf_s(a.mdf_kernel, u_lo);
+            float s_lo = j == 0 ? 0.f : mdf_s<MDF>(u_lo);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 om[c] = 0.f;
                 if (k + c < a.K && valid) {
                     const bool last = j == nz - 1;
                     const float u_hi = last ? 1e30f : (__ldg(a.zedge + j + 1) - mu_i) * inv_sig;
-                    const float s_hi = last ? 0.f : mdf_s(a.mdf_kernel, u_hi);
+                    const float s_hi = last ? 0.f : mdf_s<MDF>(u_hi);
                     float pj = s_hi - s_lo;
                     if (u_lo <= 0.f && u_hi > 0.f) pj += 1.f;
                     om[c] = frac[i] * pj;
@@ -358,15 +446,7 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
             ax[5] = p[9];
             ax[6] = 0.f;
             ax[7] = 0.f;
-            double magoff = __longlong_as_double(0x7ff8000000000000LL);
-            if (valid) {
-                double x = (double)z * a.inv_dz;
-                int i = min((int)x, a.n_lut - 2);
-                double fr = x - i;
-                double gz = a.glut[i] + fr * (a.glut[i + 1] - a.glut[i]);
-                magoff = -2.5 * (double)p[10] + gz + (double)(5.f * log10f(z)) - (double)(2.5f * log10f(1.f + z));
-            }
-            a.magoff[gi] = magoff;
+            a.magoff[gi] = valid ? gp.magoff : __longlong_as_double(0x7ff8000000000000LL);
         }
     }
 }
@@ -380,10 +460,11 @@ __global__ void __launch_bounds__(256) weights_kernel(WArgs a) {
 // ---------------------------------------------------------------------------
 
 // Sec. 3.1: dSFR/dp_k at time t (same parametrisation as sfr_f), k = 0..4.
-__device__ __forceinline__ void sfr_grad_f(int model, const float *p, float t, float (&gr)[5]) {
+template <int SFH>
+__device__ __forceinline__ void sfr_grad_f(const float *p, float t, float (&gr)[5]) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) gr[k] = 0.f;
-    if (model == DSPS_SFH_DELAYED_TAU) {
+    if constexpr (SFH == DSPS_SFH_DELAYED_TAU) {
         const float sv = t * expf(-t / p[0]);
         gr[0] = sv * t / (p[0] * p[0]);
         return;
@@ -402,14 +483,17 @@ __device__ __forceinline__ void sfr_grad_f(int model, const float *p, float t, f
     gr[4] = -ms * fq * 2.302585093f * P;
 }
 
-__device__ __forceinline__ float mdf_pdf(int kernel, float u) {
-    return kernel == DSPS_MDF_TRIWEIGHT ? triweight_f(u) : gauss_pdf_f(u);
+template <int MDF>
+__device__ __forceinline__ float mdf_pdf(float u) {
+    if constexpr (MDF == DSPS_MDF_TRIWEIGHT) return triweight_f(u);
+    else return gauss_pdf_f(u);
 }
 
 __host__ __device__ inline size_t weights_vjp_smem_per_warp(int n_t, int n_age) {
     return weights_smem_per_warp(n_t, n_age) + ((((size_t)n_t + (size_t)n_age) * 4 + 15) & ~(size_t)15);
 }
 
+template <int SFH, int MDF>
 __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *what, int scaled, float *pbar) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -429,9 +513,10 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     for (int r = 0; r < NPAR; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
     const float z = p[11], sig = p[6];
     bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NPAR);
-    valid = valid && z > 0.f && (double)z <= a.zmax && sig > 0.f && p[0] > 0.f;
-    double msum = 0.0;
-    valid = sfh_stage(a, p, valid, lane, sm, msum);
+    valid = valid && z > 0.f && z <= a.zmax_f && sig > 0.f && p[0] > 0.f;
+    const GalPrep gp = a.prep[gl];
+    float msum = 0.f;
+    valid = sfh_stage<SFH>(a, p, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
     const float *frac = sm.frac;
     for (int i = lane; i < a.n_age; i += 32) fracbar[i] = 0.f;
     for (int n = lane; n < a.n_t; n += 32) sbar[n] = 0.f;
@@ -474,9 +559,9 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
                 fb += wd;
             } else {
                 const float u = (__ldg(a.zedge + e) - mu_i) * inv_sig;
-                const float sv = mdf_s(a.mdf_kernel, u);
+                const float sv = mdf_s<MDF>(u);
                 fb = fmaf(wd, u > 0.f ? -sv : 1.f - sv, fb);
-                const float t = fr * wd * mdf_pdf(a.mdf_kernel, u) * inv_sig;
+                const float t = fr * wd * mdf_pdf<MDF>(u) * inv_sig;
                 mu_bar += t;
                 sig_bar = fmaf(t, u, sig_bar);
                 slope_bar = fmaf(t, xl, slope_bar);
@@ -509,7 +594,7 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     for (int i = lane; i < a.n_age; i += 32) dot = fmaf(fracbar[i], frac[i], dot);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-    const float inv_m = valid ? 1.f / (float)msum : 0.f;
+    const float inv_m = valid ? 1.f / msum : 0.f;
 
     // reverse of stages 3-4: each bin integral is linear in the node SFRs
     const float h = (float)a.h;
@@ -539,7 +624,7 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     float tb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int n = lane; n < a.n_t && valid; n += 32) {
         float gr[5];
-        sfr_grad_f(a.sfh_model, p, fmaf((float)n, h, (float)a.t0), gr);
+        sfr_grad_f<SFH>(p, fmaf((float)n, h, (float)a.t0), gr);
 #pragma unroll
         for (int q = 0; q < 5; ++q) tb[q] = fmaf(sbar[n], gr[q], tb[q]);
     }
@@ -566,6 +651,8 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.n_z = c.n_z;
     a.K = c.K;
     a.K_pad = c.K_pad;
+    a.A_pad = c.A_pad;
+    a.KZ_pad = c.KZ_pad;
     a.n_t = c.n_t;
     a.sfh_model = c.opts.sfh_model;
     a.mdf_kernel = c.opts.mdf_kernel;
@@ -589,10 +676,53 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.wlo = w.wlo;
     a.aux = w.aux;
     a.magoff = w.magoff;
+    a.prep = w.prep;
+    a.zmax_f = (float)c.opts.z_max;
+    if ((double)a.zmax_f > c.opts.z_max) a.zmax_f = std::nextafter(a.zmax_f, -INFINITY);
     a.err = c.d_err;
     return a;
 }
 
+namespace {
+
+// Launches K<SFH, MDF> for the context's model pair.
+template <template <int, int> class L, typename... Args>
+cudaError_t launch_models(const Ctx &c, Args... args) {
+    const int sfh = c.opts.sfh_model, mdf = c.opts.mdf_kernel;
+    if (sfh == DSPS_SFH_DELAYED_TAU)
+        return mdf == DSPS_MDF_TRIWEIGHT ? L<DSPS_SFH_DELAYED_TAU, DSPS_MDF_TRIWEIGHT>::run(args...)
+                                         : L<DSPS_SFH_DELAYED_TAU, DSPS_MDF_GAUSSIAN>::run(args...);
+    return mdf == DSPS_MDF_TRIWEIGHT ? L<DSPS_SFH_DPL_QUENCH, DSPS_MDF_TRIWEIGHT>::run(args...)
+                                     : L<DSPS_SFH_DPL_QUENCH, DSPS_MDF_GAUSSIAN>::run(args...);
+}
+
+template <int SFH, int MDF>
+struct VjpLaunch {
+    static cudaError_t run(const WArgs &a, const float *what, int scaled, float *pbar, unsigned grid, size_t smem,
+                           cudaStream_t s) {
+        cudaFuncSetAttribute(weights_vjp_kernel<SFH, MDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        weights_vjp_kernel<SFH, MDF><<<grid, 256, smem, s>>>(a, what, scaled, pbar);
+        return cudaGetLastError();
+    }
+};
+
+template <int MODE>
+struct WeightsLaunch {
+    template <int SFH, int MDF>
+    struct L {
+        static cudaError_t run(const WArgs &a, unsigned grid, size_t smem, cudaStream_t s) {
+            cudaFuncSetAttribute(weights_kernel<MODE, SFH, MDF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            weights_kernel<MODE, SFH, MDF><<<grid, 256, smem, s>>>(a);
+            return cudaGetLastError();
+        }
+    };
+};
+
+}  // namespace
+
+// The adjoint reads the per-galaxy scalars (w.prep) of the forward weights
+// launch that preceded it on the same chunk.
 cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride,
                                int64_t g_begin, int64_t n, bool sorted, bool scaled, float *param_bar,
                                cudaStream_t s) {
@@ -600,12 +730,10 @@ cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *pa
     WArgs a = make_wargs(c, w, params, G_stride, g_begin, n);
     a.perm = sorted ? w.perm : nullptr;
     a.wmul = c.d_wmul_d;
-    const int threads = 256, warps = threads / 32;
+    const int warps = 8;
     const size_t smem = weights_vjp_smem_per_warp(c.n_t, c.n_age) * warps;
-    cudaFuncSetAttribute(weights_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    weights_vjp_kernel<<<(unsigned)((n + warps - 1) / warps), threads, smem, s>>>(a, w.w32, scaled ? 1 : 0,
-                                                                                 param_bar);
-    return cudaGetLastError();
+    return launch_models<VjpLaunch>(c, a, static_cast<const float *>(w.w32), scaled ? 1 : 0, param_bar,
+                                    (unsigned)((n + warps - 1) / warps), smem, s);
 }
 
 cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const float *params, int64_t G_stride,
@@ -616,24 +744,17 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
     a.perm = sorted ? w.perm : nullptr;
     a.gidx = sorted ? w.gidx : nullptr;
     a.trange = sorted && mode == W_OMEGA_BF16X2 ? w.trange : nullptr;
-    const int threads = 256, warps = threads / 32;
+    a.kmask = w.kmask;
+    a.kmw = c.kmask_words;
+    const int warps = 8;
     const size_t smem = weights_smem_per_warp(c.n_t, c.n_age) * warps;
-    dim3 grid((unsigned)((n + warps - 1) / warps));
+    galaxy_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, w.prep);
+    const unsigned grid = (unsigned)((n + warps - 1) / warps);
     switch (mode) {
-    case W_MSUN:
-        cudaFuncSetAttribute(weights_kernel<W_MSUN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        weights_kernel<W_MSUN><<<grid, threads, smem, s>>>(a);
-        break;
-    case W_OMEGA_F32:
-        cudaFuncSetAttribute(weights_kernel<W_OMEGA_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        weights_kernel<W_OMEGA_F32><<<grid, threads, smem, s>>>(a);
-        break;
-    default:
-        cudaFuncSetAttribute(weights_kernel<W_OMEGA_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        weights_kernel<W_OMEGA_BF16X2><<<grid, threads, smem, s>>>(a);
-        break;
+    case W_MSUN: return launch_models<WeightsLaunch<W_MSUN>::L>(c, a, grid, smem, s);
+    case W_OMEGA_F32: return launch_models<WeightsLaunch<W_OMEGA_F32>::L>(c, a, grid, smem, s);
+    default: return launch_models<WeightsLaunch<W_OMEGA_BF16X2>::L>(c, a, grid, smem, s);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace dsps

@@ -5,9 +5,11 @@
 // Key: ZSORT_ZBINS coarse bins of the redshift shift s = ln(1+z)/dlnlam, and
 // inside each ZSORT_MUBINS bins of the galaxy's mean metallicity at the middle
 // log age.  Rows of one 128-galaxy tile then share a narrow redshift range (the
-// tile needs only the wavelength tiles inside the redshifted filter band, and
-// reads the filter table near one shift) and a narrow metallicity range (the
-// tile's non-zero weights fill only the K blocks of a few metallicity bins).
+// tile needs only the wavelength tiles inside the redshifted filter band) and a
+// narrow metallicity range (the tile's non-zero weights fill only the K blocks
+// of a few metallicity bins).  A last pass orders the rows inside each tile by
+// redshift, so that the 32 rows of one epilogue warp read the filter table at
+// nearby shifts.
 // Sorting is a scheduling device only: every galaxy's magnitudes come from its
 // own row, and skipped tiles and blocks hold exact zeros for every row, so the
 // order within a bucket (set by atomics) changes no result.
@@ -36,10 +38,15 @@ __device__ __forceinline__ int sort_key(const SortKey &k, int64_t i) {
     return zb * ZSORT_MUBINS + mb;
 }
 
-// Histogram of the keys; the first threads also reset the per-tile ranges.
-__global__ void zsort_hist_kernel(SortKey k, int64_t n, int *hist, int4 *trange, int n_tiles) {
+// Histogram of the keys; the first threads also reset the per-tile ranges
+// and block masks.
+__global__ void zsort_hist_kernel(SortKey k, int64_t n, int *hist, int2 *trange, unsigned *kmask, int n_tiles,
+                                  int kmw) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_tiles) trange[i] = make_int4(TRANGE_EMPTY_LO, TRANGE_EMPTY_HI, TRANGE_EMPTY_LO, TRANGE_EMPTY_HI);
+    if (i < n_tiles) {
+        trange[i] = make_int2(TRANGE_EMPTY_LO, TRANGE_EMPTY_HI);
+        for (int w = 0; w < kmw; ++w) kmask[i * kmw + w] = 0u;
+    }
     if (i < n) atomicAdd(hist + sort_key(k, i), 1);
 }
 
@@ -75,6 +82,31 @@ __global__ void zsort_scatter_kernel(SortKey k, int64_t n, int *offsets, int *pe
     if (i < n) perm[atomicAdd(offsets + sort_key(k, i), 1)] = (int)i;
 }
 
+// Orders the rows of each 128-row tile by redshift (rank sort in one block per
+// tile; ties by position), leaving the tile's set of galaxies unchanged.
+__global__ void __launch_bounds__(128) zsort_tile_kernel(SortKey k, int64_t n, int *perm) {
+    __shared__ float key[128];
+    __shared__ int idx[128];
+    const int64_t r0 = (int64_t)blockIdx.x * 128;
+    const int t = threadIdx.x;
+    const int rows = (int)min((int64_t)128, n - r0);
+    if (t < rows) {
+        idx[t] = perm[r0 + t];
+        const float z = k.z[idx[t]];
+        key[t] = z > 0.f && isfinite(z) ? z : 0.f;
+    }
+    __syncthreads();
+    if (t < rows) {
+        const float kt = key[t];
+        int rank = 0;
+        for (int j = 0; j < rows; ++j) {
+            const float kj = key[j];
+            rank += (kj < kt) || (kj == kt && j < t);
+        }
+        perm[r0 + rank] = idx[t];
+    }
+}
+
 // Sum of the parts in fixed order, then Sec. 2.2's magnitude; written to the
 // galaxy's own (unsorted) row.
 __global__ void combine_mags_kernel(const float *partial, int parts, int64_t n, int qs, int Q,
@@ -108,9 +140,10 @@ cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *params, 
     cudaError_t e = cudaMemsetAsync(w.hist, 0, ZSORT_BUCKETS * sizeof(int), s);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((n + 255) / 256);   // n >= n_tiles
-    zsort_hist_kernel<<<blocks, 256, 0, s>>>(k, n, w.hist, w.trange, n_tiles);
+    zsort_hist_kernel<<<blocks, 256, 0, s>>>(k, n, w.hist, w.trange, w.kmask, n_tiles, c.kmask_words);
     zsort_scan_kernel<<<1, 1024, 0, s>>>(w.hist);
     zsort_scatter_kernel<<<blocks, 256, 0, s>>>(k, n, w.hist, w.perm);
+    zsort_tile_kernel<<<(unsigned)n_tiles, 128, 0, s>>>(k, n, w.perm);
     return cudaGetLastError();
 }
 

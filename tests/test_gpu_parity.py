@@ -245,9 +245,10 @@ def test_block_skipping_removes_work(full):
     prof = dsps.dsps_profile_read(ctx.handle)
     dsps.dsps_profile_enable(ctx.handle, False)
     g = _util.ssp("full")
-    K_pad = -(-g.l_ssp.shape[0] * g.l_ssp.shape[1] // 64) * 64
+    a_pad = -(-g.l_ssp.shape[0] // 4) * 4          # metallicity-major K: ages padded to 4
+    kz_pad = -(-g.l_ssp.shape[1] * a_pad // 64) * 64
     N_pad = -(-(g.l_ssp.shape[2] + 1) // 256) * 256
-    dense_blocks = -(-n // 128) * (N_pad // 256) * (K_pad // 32)
+    dense_blocks = -(-n // 128) * (N_pad // 256) * (kz_pad // 32)
     frac = prof["tc_kblocks"] / dense_blocks
     print(f"executed {prof['tc_kblocks']} of {dense_blocks} block products ({frac:.3f})")
     assert 0 < frac < 0.30
