@@ -46,7 +46,7 @@ __global__ void combine_grad_kernel(const float *partial, int parts, int64_t n, 
         d_bar = fmaf(nb * kd * Av, D, d_bar);
         lm_bar = fmaf(-2.5f, mb, lm_bar);
         cq[r * QSTRIDE_MAX + q] = nb;
-        if (mags) mags[g * Q + q] = (float)(-2.5 * log10((double)N) + mo + offq[q]);
+        if (mags) mags[g * Q + q] = ab_mag(N, mo, offq[q]);
     }
     const float nan = __int_as_float(0x7fc00000);
     param_bar[8 * G_stride + g_begin + g] = valid ? av_bar : nan;

@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "dsps_internal.cuh"
+#include "epilogue.cuh"
 
 namespace dsps {
 
@@ -107,18 +108,41 @@ __global__ void __launch_bounds__(128) zsort_tile_kernel(SortKey k, int64_t n, i
     }
 }
 
-// Sum of the parts in fixed order, then Sec. 2.2's magnitude; written to the
-// galaxy's own (unsorted) row.
-__global__ void combine_mags_kernel(const float *partial, int parts, int64_t n, int qs, int Q,
-                                    const double *magoff, const double *offq, const int *gidx, float *mags) {
+// Sum of the parts in fixed order, then Sec. 2.2's magnitude (ab_mag),
+// written to the galaxy's own (unsorted) row.
+template <int Q4>
+__global__ void combine_mags_kernel(const float *partial, int parts, int64_t n, int Q, const double *magoff,
+                                    const double *offq, const int *gidx, float *mags) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
+    float acc[4 * Q4];
+#pragma unroll
+    for (int q = 0; q < 4 * Q4; ++q) acc[q] = 0.f;
+    for (int p = 0; p < parts; ++p) {
+        const float4 *src = reinterpret_cast<const float4 *>(partial + ((int64_t)p * n + r) * (4 * Q4));
+#pragma unroll
+        for (int qq = 0; qq < Q4; ++qq) {
+            const float4 v = src[qq];
+            acc[4 * qq] += v.x;
+            acc[4 * qq + 1] += v.y;
+            acc[4 * qq + 2] += v.z;
+            acc[4 * qq + 3] += v.w;
+        }
+    }
     const int64_t g = gidx[r];
     const double mo = magoff[r];
-    for (int q = 0; q < Q; ++q) {
-        float acc = 0.f;
-        for (int p = 0; p < parts; ++p) acc += partial[((int64_t)p * n + r) * qs + q];
-        mags[g * Q + q] = (float)(-2.5 * log10((double)acc) + mo + offq[q]);
+    float m[4 * Q4];
+#pragma unroll
+    for (int q = 0; q < 4 * Q4; ++q) m[q] = q < Q ? ab_mag(acc[q], mo, offq[q]) : 0.f;
+    float *dst = mags + g * Q;
+    if (Q == 4 * Q4) {
+#pragma unroll
+        for (int qq = 0; qq < Q4; ++qq)
+            reinterpret_cast<float4 *>(dst)[qq] = make_float4(m[4 * qq], m[4 * qq + 1], m[4 * qq + 2], m[4 * qq + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4 * Q4; ++q)
+            if (q < Q) dst[q] = m[q];
     }
 }
 
@@ -151,8 +175,13 @@ cudaError_t launch_combine(const Ctx &c, const Workspace &w, const FilterSet &fs
                            cudaStream_t s) {
     (void)c;
     if (n <= 0) return cudaSuccess;
-    combine_mags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.partial, parts, n, 4 * fs.Q4, fs.Q,
-                                                                      w.magoff, fs.d_offq, w.gidx, mags);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    switch (fs.Q4) {
+    case 1: combine_mags_kernel<1><<<blocks, 256, 0, s>>>(w.partial, parts, n, fs.Q, w.magoff, fs.d_offq, w.gidx, mags); break;
+    case 2: combine_mags_kernel<2><<<blocks, 256, 0, s>>>(w.partial, parts, n, fs.Q, w.magoff, fs.d_offq, w.gidx, mags); break;
+    case 3: combine_mags_kernel<3><<<blocks, 256, 0, s>>>(w.partial, parts, n, fs.Q, w.magoff, fs.d_offq, w.gidx, mags); break;
+    default: combine_mags_kernel<4><<<blocks, 256, 0, s>>>(w.partial, parts, n, fs.Q, w.magoff, fs.d_offq, w.gidx, mags); break;
+    }
     return cudaGetLastError();
 }
 
