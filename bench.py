@@ -47,6 +47,8 @@ def _args():
     ap.add_argument("--n-gal", type=int, default=N_GAL)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4096)
+    ap.add_argument("--precision-gal", type=int, default=1_000_000,
+                    help="population of the split-bf16 vs FP32 comparison arm (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson request stream (the serving workload is 60 s)")
     return ap.parse_args()
@@ -79,18 +81,53 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """SM clock and clock-event (throttle) reasons during the timed region:
+    read through NVML (read-only queries, every millisecond from a thread),
+    else from `nvidia-smi -lms 200`."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvml.h clock-event reason bits
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap"}
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.path = None
+        self.nvml = None
+        self.samples = []
+        self.thread = None
+        self.halt = False
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) == 0:
+                    self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                        lib.nvmlDeviceGetCurrentClocksThrottleReasons
+                    self.nvml, self.h, self.ct = lib, h, ctypes
+        except Exception:  # noqa: BLE001
+            self.nvml = None
+
+    def _poll(self):
+        ct, lib, h = self.ct, self.nvml, self.h
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.halt:
+            if lib.nvmlDeviceGetClockInfo(h, 1, ct.byref(mhz)) == 0 and self.reason_fn(h, ct.byref(rs)) == 0:
+                self.samples.append((mhz.value, rs.value))
+            time.sleep(0.001)
 
     def start(self):
+        if self.nvml is not None:
+            import threading
+            self.samples, self.halt = [], False
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            while not self.samples and self.thread.is_alive():
+                time.sleep(0.0005)
+            return
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -101,6 +138,17 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.halt = True
+            self.thread.join(timeout=5)
+            self.thread = None
+            if not self.samples:
+                return None
+            mx = self.ct.c_uint()
+            self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, self.ct.byref(mx))
+            reasons = sorted({n for _, r in self.samples for bit, n in self.REASONS.items() if r & bit})
+            return {"sm_mhz": float(np.median([m for m, _ in self.samples])), "sm_max_mhz": float(mx.value),
+                    "reasons": reasons, "samples": len(self.samples), "source": "nvml, 1 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -125,7 +173,8 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "source": "nvidia-smi, 200 ms"}
 
 
 def _dist():
@@ -150,9 +199,10 @@ def max_over_ranks(value: float, dist=None, device="cpu") -> float:
     return float(t.item())
 
 
-def _cpu_baseline(sample: int):
+def _cpu_baseline(sample: int, gpu_mags=None):
     """The FP64 oracle as it stands, on all host cores, over a bounded sample of
-    the same workload."""
+    the same workload; with the GPU's magnitudes of the same galaxies
+    ({form: [sample, Q] array}) it also reports their largest difference."""
     import oracle
     from paper_2112_06830_gb300 import synth
     ssp = synth.make_ssp(synth.FULL_GRID, 1)
@@ -161,11 +211,15 @@ def _cpu_baseline(sample: int):
     p = synth.make_population(synth.SFH_DPL_QUENCH, sample, 1).astype(np.float32).astype(np.float64)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.mags(grid, F, p, nthreads=cores)
+    ref = oracle.mags(grid, F, p, nthreads=cores)
     dt = time.perf_counter() - t0
-    return {"value": sample * N_FILT / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} galaxies of the 1e5-galaxy workload (107x22x5994 grid, 12 filters), "
-                      f"FP64, {cores} threads, {dt:.2f} s wall"}
+    out = {"value": sample * N_FILT / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+           "sample": f"first {sample} galaxies of the 1e5-galaxy workload (107x22x5994 grid, 12 filters), "
+                     f"FP64, {cores} threads, {dt:.2f} s wall"}
+    if gpu_mags:
+        out["gpu_max_abs_mag_error_on_sample"] = {k: float(np.abs(np.asarray(v, np.float64) - ref).max())
+                                                  for k, v in gpu_mags.items()}
+    return out
 
 
 def _serve_bench(ctx, sids, seconds, rate=200.0):
@@ -374,6 +428,40 @@ def run_ours(a):
     assert np.isfinite(h_mags.numpy()).all()
     assert ctx.device_error() == 0
 
+    # Precision forms at 1e6 galaxies (same grid and distributions): split-bf16
+    # against FP32 throughput, and their per-galaxy magnitude difference.
+    precision = None
+    if a.precision_gal > 0:
+        Gp = a.precision_gal
+        pp = synth.make_population(synth.SFH_DPL_QUENCH, Gp, 1, start=shard_start(rank, Gp)).astype(np.float32)
+        dp = torch.from_numpy(pp).cuda()
+        m_tc = torch.empty((Gp, N_FILT), dtype=torch.float32, device="cuda")
+        m_32 = torch.empty((Gp, N_FILT), dtype=torch.float32, device="cuda")
+
+        def timed_p(prec, out, steps):
+            for _ in range(a.warmup):
+                ctx.photometry(dp, sid, precision=prec, out=out, stream=stream)
+            barrier()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for e0, e1 in evs:
+                flush.fill_(1)
+                e0.record(stream)
+                ctx.photometry(dp, sid, precision=prec, out=out, stream=stream)
+                e1.record(stream)
+            barrier()
+            return max_over_ranks(float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs])), dist, "cuda")
+
+        ms_p_tc = timed_p(dsps.DSPS_PREC_BF16X3, m_tc, a.steps)
+        ms_p_32 = timed_p(dsps.DSPS_PREC_FP32, m_32, max(1, min(a.steps, 3)))
+        dmag = (m_tc - m_32).abs().flatten()
+        precision = {"n_gal_per_gpu": Gp, "bf16x3": {"value": ws * Gp * N_FILT / (ms_p_tc * 1e-3), "ms_per_step": ms_p_tc},
+                     "fp32": {"value": ws * Gp * N_FILT / (ms_p_32 * 1e-3), "ms_per_step": ms_p_32},
+                     "bf16x3_minus_fp32_abs_mag": {"max": float(dmag.max()),
+                                                   "p99": float(torch.quantile(dmag[::97].double(), 0.99))},
+                     "note": "per-galaxy error against the FP64 oracle on a 1e3 subsample is a GPU test "
+                             "(test_million_galaxy_precision_forms)"}
+        del dp, m_tc, m_32
+
     serve = None
     if a.serve_seconds > 0 and rank == 0:
         sids = {N_FILT: sid}
@@ -436,11 +524,15 @@ def run_ours(a):
         "e2e": {"value": ws * G * N_FILT / (ms_e2e * 1e-3), "unit": METRIC,
                 "h2d_bytes_per_step": int(params_h.nbytes), "d2h_bytes_per_step": int(G * N_FILT * 4)},
         "gpu_launches": int(total_launches),
+        "precision_forms_1e6": precision,
         "serve": serve,
         "clocks": clocks,
     }
     if not a.no_cpu_baseline:
-        out["cpu_baseline"] = _cpu_baseline(a.cpu_sample)
+        xs = d_params[:, :a.cpu_sample].contiguous()
+        gm = {name: ctx.photometry(xs, sid, precision=pr).cpu().numpy()
+              for name, pr in (("bf16x3", dsps.DSPS_PREC_BF16X3), ("fp32", dsps.DSPS_PREC_FP32))}
+        out["cpu_baseline"] = _cpu_baseline(a.cpu_sample, gm)
     print(json.dumps(out))
     ctx.close()
     if dist is not None:

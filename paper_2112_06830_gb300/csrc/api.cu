@@ -298,7 +298,8 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     up(c->d_logage, logage.data(), logage.size() * sizeof(float));
     up(c->d_zedge, zedge.data(), zedge.size() * sizeof(float));
     up(c->d_tlut, tl.data(), tl.size() * sizeof(double));
-    up(c->d_glut, gl.data(), gl.size() * sizeof(double));
+    std::vector<float> glf(gl.begin(), gl.end());
+    up(c->d_glut, glf.data(), glf.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = prepare_ssp_device(*c, g->l_ssp);
@@ -327,7 +328,7 @@ int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const 
     if (!c || !n_pts || !lam || !trans || !set_id) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: null argument%s");
     if (n_filt < 1 || n_filt > DSPS_MAX_FILTERS) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: 1..16 filters%s");
     double lmax = 0.0;
-    std::vector<double> offq(n_filt);
+    std::vector<float> offq(n_filt);
     for (int q = 0; q < n_filt; ++q) {
         if (n_pts[q] < 2 || !lam[q] || !trans[q]) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: bad table%s");
         double D = 0.0;
@@ -339,7 +340,7 @@ int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const 
             }
         }
         if (!(D > 0)) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: filter with zero transmission%s");
-        offq[q] = 2.5 * std::log10(AB0 * D);   // Eq. (restmag) denominator
+        offq[q] = (float)(2.5 * std::log10(AB0 * D));   // Eq. (restmag) denominator
         lmax = std::max(lmax, lam[q][n_pts[q] - 1]);
     }
     FilterSet fs;
@@ -370,7 +371,7 @@ int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const 
     if (dmalloc(&fs.d_tab, tab.size()) != DSPS_OK) return DSPS_ERR_CUDA;
     if (dmalloc(&fs.d_offq, (size_t)n_filt) != DSPS_OK) { cudaFree(fs.d_tab); return DSPS_ERR_CUDA; }
     cudaError_t e = cudaMemcpy(fs.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(fs.d_offq, offq.data(), offq.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fs.d_offq, offq.data(), offq.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(fs.d_tab); cudaFree(fs.d_offq); return cuda_fail(e, "dsps_filters_add upload"); }
     c->sets.push_back(fs);
     *set_id = (int32_t)c->sets.size() - 1;

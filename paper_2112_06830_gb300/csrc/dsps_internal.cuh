@@ -69,14 +69,14 @@ constexpr int KBLOCK = 32;   // kz block of the tensor-core contraction (one TMA
 //   2 s     = ln(1+z) / dlnlam      (observer-frame shift in grid steps)
 //   3 valid (1 or 0)
 //   4 Av, 5 delta  (gradient path)
-// magoff[g] (double) = -2.5 logM + Dmod(z) - 2.5 log10(1+z)
+// magoff[g] = -2.5 logM + Dmod(z) - 2.5 log10(1+z)
 
 struct FilterSet {
     int Q = 0, Q4 = 0;         // filters; float4 groups per table row
     int m_rows = 0;            // table rows; row m_rows-1 is all zero
     int m_nz_lo = 0, m_nz_hi = -1;  // first / last table row where some filter is non-zero
     float *d_tab = nullptr;    // [m_rows][4*Q4] T_q(lam0 exp(m dlnlam))
-    double *d_offq = nullptr;  // [Q] 2.5 log10(AB0 D_q)
+    float *d_offq = nullptr;   // [Q] 2.5 log10(AB0 D_q)
 };
 
 struct Serve;  // request loop (serve.cu)
@@ -85,7 +85,8 @@ struct Serve;  // request loop (serve.cu)
 struct GalPrep {
     int m_obs;       // interval of the SFR time grid holding t_obs(z); -1 if z is out of range
     float f_obs;     // position of t_obs inside that interval, [0, 1)
-    double magoff;   // -2.5 logM + Dmod(z) - 2.5 log10(1+z) (NaN if z is out of range)
+    float magoff;    // -2.5 logM + Dmod(z) - 2.5 log10(1+z) (NaN if z is out of range)
+    float pad;
 };
 
 // Per-launch work space of the photometry path (rows = galaxies of one chunk
@@ -97,7 +98,7 @@ struct Workspace {
     float *w32 = nullptr;                       // [cap][K_pad] FP32 weights / adjoint output
     __nv_bfloat16 *whi = nullptr, *wlo = nullptr;  // [cap][KZ_pad] split weights (metallicity-major)
     float *aux = nullptr;                       // [cap][AUX_STRIDE]
-    double *magoff = nullptr;                   // [cap]
+    float *magoff = nullptr;                    // [cap]
     GalPrep *prep = nullptr;                    // [cap] (chunk order)
     int *perm = nullptr, *gidx = nullptr;       // [cap]
     int *hist = nullptr;                        // [ZSORT_BUCKETS]
@@ -136,7 +137,7 @@ struct Ctx {
     float *d_bwidth = nullptr;              // [n_age] bin widths [Gyr]
     float *d_zedge = nullptr;               // [n_z+1] lgZ bin edges (+-1e30 outer)
     double *d_tlut = nullptr;               // [n_lut] t_obs(z) [Gyr]
-    double *d_glut = nullptr;               // [n_lut] Dmod(z) - 5 log10 z
+    float *d_glut = nullptr;                // [n_lut] Dmod(z) - 5 log10 z
     int n_lut = 0;
     double dz_lut = 0;
 

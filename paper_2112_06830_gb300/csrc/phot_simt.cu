@@ -23,9 +23,9 @@ struct SArgs {
     int K_pad, N_pad, Q, m_last;
     int64_t n;
     const float *aux;
-    const double *magoff;
+    const float *magoff;
     const float4 *tab;
-    const double *offq;
+    const float *offq;
     ColConst cc;
     float *mags;           // [n][Q]
     float *partial;        // gradient mode: [n][3 * 4 * Q4] sums N, A, D per filter

@@ -104,7 +104,7 @@ extern "C" int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const f
     const size_t off_aux = align256((size_t)cap * c->K_pad * 4);
     ws.aux = reinterpret_cast<float *>(base + off_aux);
     const size_t off_mo = off_aux + align256((size_t)cap * AUX_STRIDE * 4);
-    ws.magoff = reinterpret_cast<double *>(base + off_mo);
+    ws.magoff = reinterpret_cast<float *>(base + off_mo);
     ws.prep = reinterpret_cast<GalPrep *>(base + off_mo + align256((size_t)cap * 8));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const FilterSet &fs = c->sets[set_id];

@@ -20,15 +20,15 @@ namespace dsps {
 
 namespace {
 
-__global__ void combine_grad_kernel(const float *partial, int parts, int64_t n, int qs, int Q, const double *magoff,
-                                    const double *offq, const int *gidx, const float *aux, const float *mag_bar,
+__global__ void combine_grad_kernel(const float *partial, int parts, int64_t n, int qs, int Q, const float *magoff,
+                                    const float *offq, const int *gidx, const float *aux, const float *mag_bar,
                                     float *mags, float *param_bar, int64_t G_stride, int64_t g_begin, float *cq) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int64_t g = gidx ? (int64_t)gidx[r] : r;
     const bool valid = aux[r * AUX_STRIDE + 3] != 0.f;
     const float Av = aux[r * AUX_STRIDE + 4];
-    const double mo = magoff[r];
+    const float mo = magoff[r];
     const float k10 = -2.5f / 2.302585092994046f;
     const float kd = -0.4f * 2.302585092994046f;
     float av_bar = 0.f, d_bar = 0.f, lm_bar = 0.f;

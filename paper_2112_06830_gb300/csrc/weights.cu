@@ -31,16 +31,18 @@ struct WArgs {
     int n_age, n_z, K, K_pad, A_pad, KZ_pad, n_t, sfh_model, mdf_kernel, n_lut;
     double t0, h, inv_h, dz, inv_dz, zmax, dlnlam;
     float zmax_f;          // largest float <= zmax (z <= zmax_f iff (double)z <= zmax)
+    float t0_f, h_f, dlnlam_f;   // FP32 copies used by the per-galaxy warps
     const float *logage;
     const float *einh;     // [n_age+1] age-bin edge / h
     const float *bwidth;   // [n_age] e_{i+1} - e_i [Gyr]
     const float *zedge;
-    const double *tlut, *glut;
+    const double *tlut;    // [n_lut] t_obs(z) [Gyr]
+    const float *glut;     // [n_lut] Dmod(z) - 5 log10 z
     const float *wmul;
     float *w_msun, *w32;
     __nv_bfloat16 *whi, *wlo;
     float *aux;
-    double *magoff;
+    float *magoff;
     const int *perm;   // sorted row -> chunk-local galaxy, or nullptr
     int *gidx;         // out: sorted row -> chunk-local galaxy, or nullptr
     int2 *trange;      // out: per-tile redshift-shift ranges (atomics), or nullptr
@@ -123,9 +125,9 @@ __device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool vali
     valid = valid && m_obs >= 0;
 
     // 2. SFR at the time nodes (FP32) and the interval integrals I_j
-    const float h = (float)a.h;
+    const float h = a.h_f;
     for (int n = lane; n < a.n_t; n += 32)
-        sfr[n] = valid ? sfr_f<SFH>(p, fmaf((float)n, h, (float)a.t0)) : 0.f;
+        sfr[n] = valid ? sfr_f<SFH>(p, fmaf((float)n, h, a.t0_f)) : 0.f;
     __syncwarp();
     for (int j = lane; j < a.n_t - 1; j += 32) itg[j] = 0.5f * h * (sfr[j] + sfr[j + 1]);
     __syncwarp();
@@ -230,8 +232,11 @@ __global__ void galaxy_prep_kernel(WArgs a, GalPrep *out) {
     GalPrep r;
     r.m_obs = -1;
     r.f_obs = 0.f;
-    r.magoff = __longlong_as_double(0x7ff8000000000000LL);
-    if (z > 0.f && (double)z <= a.zmax) {
+    r.magoff = __int_as_float(0x7fc00000);
+    r.pad = 0.f;
+    if (z > 0.f && z <= a.zmax_f) {
+        // FP64 only where the integer part of (t_obs - t0)/h ~ 200 is split
+        // off: f_obs keeps its full FP32 precision.
         const double x = (double)z * a.inv_dz;
         const int i = min((int)x, a.n_lut - 2);
         const double fr = x - i;
@@ -241,9 +246,10 @@ __global__ void galaxy_prep_kernel(WArgs a, GalPrep *out) {
             r.m_obs = min((int)apos, a.n_t - 2);
             r.f_obs = (float)(apos - r.m_obs);
         }
-        const double gz = a.glut[i] + fr * (a.glut[i + 1] - a.glut[i]);
+        const float frf = (float)fr;
+        const float gz = fmaf(frf, a.glut[i + 1] - a.glut[i], a.glut[i]);
         const float lm = a.params[10 * a.G_stride + g];
-        r.magoff = -2.5 * (double)lm + gz + (double)(5.f * log10f(z)) - (double)(2.5f * log10f(1.f + z));
+        r.magoff = fmaf(-2.5f, lm, gz) + (5.f * log10f(z) - 2.5f * log10f(1.f + z));
     }
     out[gl] = r;
 }
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
     // 5-6. metallicity weights and output.
     const float inv_sig = 1.f / sig;
     const float mass = exp10f(p[10]);
-    const float s_shift = valid ? log1pf(z) / (float)a.dlnlam : 0.f;   // redshift shift in grid steps
+    const float s_shift = valid ? log1pf(z) / a.dlnlam_f : 0.f;   // redshift shift in grid steps
     const int nz = a.n_z;
     if constexpr (MODE == W_OMEGA_BF16X2) {
         // Metallicity-major kz = j * A_pad + i.  Lane g takes the ages 4g ..
@@ -446,7 +452,7 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
             ax[5] = p[9];
             ax[6] = 0.f;
             ax[7] = 0.f;
-            a.magoff[gi] = valid ? gp.magoff : __longlong_as_double(0x7ff8000000000000LL);
+            a.magoff[gi] = valid ? gp.magoff : __int_as_float(0x7fc00000);
         }
     }
 }
@@ -597,7 +603,7 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     const float inv_m = valid ? 1.f / msum : 0.f;
 
     // reverse of stages 3-4: each bin integral is linear in the node SFRs
-    const float h = (float)a.h;
+    const float h = a.h_f;
     for (int i = lane; i < a.n_age && valid; i += 32) {
         const float bb = (fracbar[i] - dot) * inv_m;
         const int mi = sm.em[i], mo = sm.em[i + 1];
@@ -624,7 +630,7 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     float tb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int n = lane; n < a.n_t && valid; n += 32) {
         float gr[5];
-        sfr_grad_f<SFH>(p, fmaf((float)n, h, (float)a.t0), gr);
+        sfr_grad_f<SFH>(p, fmaf((float)n, h, a.t0_f), gr);
 #pragma unroll
         for (int q = 0; q < 5; ++q) tb[q] = fmaf(sbar[n], gr[q], tb[q]);
     }
@@ -664,6 +670,9 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.inv_dz = 1.0 / c.dz_lut;
     a.zmax = c.opts.z_max;
     a.dlnlam = c.dlnlam;
+    a.t0_f = (float)a.t0;
+    a.h_f = (float)a.h;
+    a.dlnlam_f = (float)a.dlnlam;
     a.logage = c.d_logage;
     a.einh = c.d_einh;
     a.bwidth = c.d_bwidth;

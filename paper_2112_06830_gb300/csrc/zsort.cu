@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(128) zsort_tile_kernel(SortKey k, int64_t n, i
 // Sum of the parts in fixed order, then Sec. 2.2's magnitude (ab_mag),
 // written to the galaxy's own (unsorted) row.
 template <int Q4>
-__global__ void combine_mags_kernel(const float *partial, int parts, int64_t n, int Q, const double *magoff,
-                                    const double *offq, const int *gidx, float *mags) {
+__global__ void combine_mags_kernel(const float *partial, int parts, int64_t n, int Q, const float *magoff,
+                                    const float *offq, const int *gidx, float *mags) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     float acc[4 * Q4];
@@ -130,7 +130,7 @@ __global__ void combine_mags_kernel(const float *partial, int parts, int64_t n, 
         }
     }
     const int64_t g = gidx[r];
-    const double mo = magoff[r];
+    const float mo = magoff[r];
     float m[4 * Q4];
 #pragma unroll
     for (int q = 0; q < 4 * Q4; ++q) m[q] = q < Q ? ab_mag(acc[q], mo, offq[q]) : 0.f;

@@ -252,3 +252,29 @@ def test_block_skipping_removes_work(full):
     frac = prof["tc_kblocks"] / dense_blocks
     print(f"executed {prof['tc_kblocks']} of {dense_blocks} block products ({frac:.3f})")
     assert 0 < frac < 0.30
+
+
+def test_million_galaxy_precision_forms(full):
+    """10^6 galaxies of the full workload in both forms; per-galaxy magnitude
+    error against the oracle on a 10^3-galaxy subsample (every 1000th
+    galaxy), and the split-bf16 form against FP32 on all of them."""
+    ctx, sid, F = full
+    n = 1_000_000
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, n, 1))
+    x = torch.from_numpy(p32).cuda()
+    m_tc = ctx.photometry(x, sid, precision=1)
+    m_32 = ctx.photometry(x, sid, precision=0)
+    torch.cuda.synchronize()
+    m_tc, m_32 = m_tc.cpu().numpy().astype(np.float64), m_32.cpu().numpy().astype(np.float64)
+    idx = np.arange(0, n, 1000)
+    ref = oracle.mags(_util.oracle_grid("full", 1), F, np.ascontiguousarray(p64[:, idx]))
+    e_tc = np.abs(m_tc[idx] - ref).max(axis=1)
+    e_32 = np.abs(m_32[idx] - ref).max(axis=1)
+    d = np.abs(m_tc - m_32)
+    print(f"1e6 galaxies: per-galaxy max |dm| vs oracle on 1e3: bf16x3 max {e_tc.max():.2e} "
+          f"p50 {np.median(e_tc):.2e}; fp32 max {e_32.max():.2e} p50 {np.median(e_32):.2e}; "
+          f"bf16x3 - fp32 over 1e6: max {d.max():.2e} p99 {np.percentile(d, 99):.2e}")
+    assert np.isfinite(m_tc).all() and np.isfinite(m_32).all()
+    assert e_tc.max() <= _util.TOL_BF16X3
+    assert e_32.max() <= _util.TOL_FP32
+    assert d.max() <= _util.TOL_BF16X3 + _util.TOL_FP32

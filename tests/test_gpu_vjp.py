@@ -131,3 +131,32 @@ def test_autograd_function(full):
     torch.cuda.synchronize()
     torch.testing.assert_close(g[:11], pb, rtol=0, atol=0)
     assert (g[11] == 0).all()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vjp_of_squared_magnitude_loss(full, prec):
+    """The differentiation workload's loss: L = sum (m - t)^2 over galaxies and
+    filters, with targets t the magnitudes of perturbed parameters plus N(0,
+    0.05) noise, on 256 galaxies; dL/dm = 2 (m - t) is formed from the oracle's
+    magnitudes and fed to both sides, so the comparison is of the adjoints."""
+    ctx, sid, F = full
+    n = 256
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, n, 1, start=7000))
+    rng = np.random.default_rng(13)
+    pt = p64.copy()
+    pt[:5] *= 1.0 + 0.02 * rng.standard_normal((5, n))      # SFH parameters
+    pt[5] += 0.05 * rng.standard_normal(n)                     # MDF mean
+    pt[8] = np.clip(pt[8] + 0.05 * rng.standard_normal(n), 0.0, None)
+    pt[9] += 0.03 * rng.standard_normal(n)
+    pt[10] += 0.05 * rng.standard_normal(n)
+    grid = _util.oracle_grid("full", 1)
+    target = oracle.mags(grid, F, pt) + 0.05 * rng.standard_normal((n, 12))
+    m_ref = oracle.mags(grid, F, p64)
+    mbar = 2.0 * (m_ref - target)
+    _, pb_ref = oracle.mags_vjp(grid, F, p64, mbar)
+    m, pb = _vjp(ctx, sid, p32, mbar, prec)
+    err, where = _check(pb, pb_ref, prec)
+    loss = float(np.sum((m_ref - target) ** 2))
+    print(f"squared-magnitude loss {loss:.3f}, prec={prec}: max scaled gradient error {err:.2e} at {where}")
+    assert err <= 1e-3
+    assert np.abs(m - m_ref).max() <= (1e-4 if prec == 0 else 1e-3)
