@@ -257,10 +257,10 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_ws_block, workspace_bytes(*c, c->chunk, false)));
     chk(dmalloc(&c->d_err, 1));
     chk(dmalloc(&c->d_stats, 1));
-    chk(dmalloc(&c->d_L_hi, (size_t)c->K_pad * c->N_pad));
-    chk(dmalloc(&c->d_Ld32, (size_t)c->K_pad * c->N_pad));
-    chk(dmalloc(&c->d_wmul_d, (size_t)c->K_pad));
-    chk(dmalloc(&c->d_L_lo, (size_t)c->K_pad * c->N_pad));
+    chk(dmalloc(&c->d_L_hi, (size_t)c->KZ_pad * c->N_pad));
+    chk(dmalloc(&c->d_Ld32, (size_t)c->KZ_pad * c->N_pad));
+    chk(dmalloc(&c->d_wmul_d, (size_t)c->KZ_pad));
+    chk(dmalloc(&c->d_L_lo, (size_t)c->KZ_pad * c->N_pad));
     if (rc != DSPS_OK) { free_ctx(c); return rc; }
     c->ws = workspace_carve(*c, c->d_ws_block, c->chunk, false);
 

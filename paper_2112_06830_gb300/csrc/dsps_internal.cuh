@@ -95,7 +95,7 @@ struct GalPrep {
 // points one at its static array.
 struct Workspace {
     int64_t cap = 0;                            // rows
-    float *w32 = nullptr;                       // [cap][K_pad] FP32 weights / adjoint output
+    float *w32 = nullptr;                       // [cap][K_pad] FP32 weights / [cap][KZ_pad] adjoint output
     __nv_bfloat16 *whi = nullptr, *wlo = nullptr;  // [cap][KZ_pad] split weights (metallicity-major)
     float *aux = nullptr;                       // [cap][AUX_STRIDE]
     float *magoff = nullptr;                    // [cap]
@@ -146,10 +146,10 @@ struct Ctx {
     unsigned char *d_ws_block = nullptr;    // device block holding ws (without Shat)
     Workspace ws;
     unsigned long long *d_stats = nullptr;  // [1] tensor-core tiles executed (profiling)
-    float *d_Ld32 = nullptr;                // [K_pad][N_pad] metallicity-differenced block (FP32 adjoint)
-    float *d_wmul_d = nullptr;              // [K_pad] 2^E'_k of the differenced rows
-    __nv_bfloat16 *d_L_hi = nullptr;        // [K_pad][N_pad] differenced block, row-scaled hi (tensor adjoint)
-    __nv_bfloat16 *d_L_lo = nullptr;        // [K_pad][N_pad] row-scaled lo
+    float *d_Ld32 = nullptr;                // [KZ_pad][N_pad] metallicity-differenced block (FP32 adjoint)
+    float *d_wmul_d = nullptr;              // [KZ_pad] 2^E'_kz of the differenced rows
+    __nv_bfloat16 *d_L_hi = nullptr;        // [KZ_pad][N_pad] differenced block, row-scaled hi (tensor adjoint)
+    __nv_bfloat16 *d_L_lo = nullptr;        // [KZ_pad][N_pad] row-scaled lo
     unsigned *d_err = nullptr;              // sticky error word
 
     std::vector<FilterSet> sets;

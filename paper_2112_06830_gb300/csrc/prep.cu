@@ -4,10 +4,11 @@
 //   d_L32   [K_pad][N_pad] FP32, zero padded                (SIMT form)
 //   d_Lt_*  [N_pad][KZ_pad] bf16 hi / lo of L[k][n] 2^-E_k   (tensor form, K-contiguous
 //           rows, columns in the metallicity-major order kz = j * A_pad + i)
-//   d_Ld32  [K_pad][N_pad] FP32 metallicity-differenced block: row (i, 0) is
-//           L[i, 0], row (i, j >= 1) is L[i, j] - L[i, j-1]   (FP32 adjoint)
-//   d_L_*   [K_pad][N_pad] bf16 hi / lo of the differenced block scaled by
-//           2^-E'_k, with d_wmul_d = 2^E'_k               (tensor adjoint)
+//   d_Ld32  [KZ_pad][N_pad] FP32 metallicity-differenced block, rows in the
+//           metallicity-major order kz = j * A_pad + i: row (j = 0, i) is
+//           L[i, 0], row (j >= 1, i) is L[i, j] - L[i, j-1]   (FP32 adjoint)
+//   d_L_*   [KZ_pad][N_pad] bf16 hi / lo of the differenced block scaled by
+//           2^-E'_kz, with d_wmul_d = 2^E'_kz              (tensor adjoint)
 // The adjoint contracts with the differenced block so that the differences of
 // dLoss/domega between neighbouring metallicity bins -- all the metallicity
 // gradients need (summation by parts) -- come out at full relative precision.
@@ -78,13 +79,16 @@ __global__ void build_lt_kernel(const float *L, const float *rscale, int N, int 
     }
 }
 
-// Metallicity-differenced block, FP32 [K_pad][N_pad] (padding zero).
-__global__ void build_ldiff_kernel(const float *L, int K, int N, int n_z, int K_pad, int N_pad, float *Ld) {
+// Metallicity-differenced block, FP32 [KZ_pad][N_pad], metallicity-major rows
+// (padding zero).
+__global__ void build_ldiff_kernel(const float *L, int N, int a_pad, int n_age, int n_z, int KZ_pad, int N_pad,
+                                   float *Ld) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)K_pad * N_pad) return;
-    const int k = (int)(idx / N_pad), n = (int)(idx % N_pad);
+    if (idx >= (size_t)KZ_pad * N_pad) return;
+    const int kz = (int)(idx / N_pad), n = (int)(idx % N_pad);
+    const int k = kz_to_k(kz, a_pad, n_age, n_z);
     float v = 0.f;
-    if (k < K && n < N) {
+    if (k >= 0 && n < N) {
         v = L[(size_t)k * N + n];
         if (k % n_z != 0) v -= L[(size_t)(k - 1) * N + n];
     }
@@ -129,7 +133,7 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
     float *d_raw = nullptr, *d_rscale = nullptr;
     cudaError_t e = cudaMalloc(&d_raw, KN * sizeof(float));
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&d_rscale, (size_t)c.K_pad * sizeof(float));
+    e = cudaMalloc(&d_rscale, (size_t)(c.K_pad > c.KZ_pad ? c.K_pad : c.KZ_pad) * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(d_raw, h_lssp, KN * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c.d_wmul, 0, (size_t)c.KZ_pad * sizeof(float));
     if (e == cudaSuccess) {
@@ -139,10 +143,11 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
         dim3 g(c.N_pad / 32, c.KZ_pad / 32), b(32, 8);
         build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.n_lam, c.KZ_pad, c.N_pad, c.A_pad, c.n_age, c.n_z, c.d_Lt_hi,
                                   c.d_Lt_lo);
-        const unsigned blk = (unsigned)((tot + 255) / 256);
-        build_ldiff_kernel<<<blk, 256>>>(d_raw, c.K, c.n_lam, c.n_z, c.K_pad, c.N_pad, c.d_Ld32);
-        row_exponent_abs_kernel<<<c.K_pad, 256>>>(c.d_Ld32, c.K, c.N_pad, c.d_wmul_d, d_rscale);
-        build_split_kernel<<<blk, 256>>>(c.d_Ld32, d_rscale, c.K_pad, c.N_pad, c.d_L_hi, c.d_L_lo);
+        const size_t totz = (size_t)c.KZ_pad * c.N_pad;
+        const unsigned blkz = (unsigned)((totz + 255) / 256);
+        build_ldiff_kernel<<<blkz, 256>>>(d_raw, c.n_lam, c.A_pad, c.n_age, c.n_z, c.KZ_pad, c.N_pad, c.d_Ld32);
+        row_exponent_abs_kernel<<<c.KZ_pad, 256>>>(c.d_Ld32, c.KZ_pad, c.N_pad, c.d_wmul_d, d_rscale);
+        build_split_kernel<<<blkz, 256>>>(c.d_Ld32, d_rscale, c.KZ_pad, c.N_pad, c.d_L_hi, c.d_L_lo);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }

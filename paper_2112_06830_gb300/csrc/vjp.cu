@@ -6,8 +6,9 @@
 //   Av_bar  = sum_q Nbar_q (-0.4 ln 10) A_q,   delta_bar = sum_q Nbar_q (-0.4 ln 10 Av) D_q
 //   logM_bar = -2.5 sum_q mag_bar_q
 //   Shat[g, n] = kappa_n F_gn sum_q Nbar_q T_q((1+z_g) lam_n)  (= dLoss/dS[g, n])
-//   What[g, k] = sum_n Shat[g, n] Ld[k, n]
-// with Ld the metallicity-differenced SSP block (prep.cu), so What holds
+//   What[g, kz] = sum_n Shat[g, n] Ld[kz, n]
+// with Ld the metallicity-differenced SSP block (prep.cu; metallicity-major
+// rows kz = j * A_pad + i), so What holds
 // dLoss/domega[g, (i, 0)] and the differences dLoss/domega[g, (i, j)] -
 // dLoss/domega[g, (i, j-1)]; the weights adjoint (weights.cu) follows.  A_q, D_q come from the
 // forward kernels' gradient mode, so no spectrum is ever stored.
@@ -247,8 +248,8 @@ cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, i
 
 cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((n + BM - 1) / BM), (unsigned)((c.K_pad + BN - 1) / BN));
-    vjp_simt_kernel<<<grid, THREADS, 0, s>>>(reinterpret_cast<const float *>(w.shat), c.d_Ld32, n, c.K_pad,
+    dim3 grid((unsigned)((n + BM - 1) / BM), (unsigned)((c.KZ_pad + BN - 1) / BN));
+    vjp_simt_kernel<<<grid, THREADS, 0, s>>>(reinterpret_cast<const float *>(w.shat), c.d_Ld32, n, c.KZ_pad,
                                              c.N_pad, w.w32);
     return cudaGetLastError();
 }

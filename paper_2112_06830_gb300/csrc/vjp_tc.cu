@@ -37,7 +37,7 @@ struct VArgs {
     int n_mtiles, n_ktiles, n_units, N_pad, K_pad;
     int64_t n;
     int *sched;       // unit counter, zero at launch
-    float *out;       // [n][K_pad]
+    float *out;       // [n][K_pad] (K_pad = the context's KZ_pad: metallicity-major rows)
     unsigned *err;
 };
 
@@ -227,17 +227,17 @@ cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs,
     CUtensorMap ah, al, bh, bl;
     if (!make_tmap(&ah, hi, (uint64_t)c.N_pad, (uint64_t)n, BM) ||
         !make_tmap(&al, lo, (uint64_t)c.N_pad, (uint64_t)n, BM) ||
-        !make_tmap(&bh, c.d_L_hi, (uint64_t)c.N_pad, (uint64_t)c.K_pad, BN) ||
-        !make_tmap(&bl, c.d_L_lo, (uint64_t)c.N_pad, (uint64_t)c.K_pad, BN))
+        !make_tmap(&bh, c.d_L_hi, (uint64_t)c.N_pad, (uint64_t)c.KZ_pad, BN) ||
+        !make_tmap(&bl, c.d_L_lo, (uint64_t)c.N_pad, (uint64_t)c.KZ_pad, BN))
         return cudaErrorInvalidValue;
     VArgs a{};
     a.trange = w.trange;
     a.band = make_vjp_band(c, fs, c.opts.band_skip != 0);
     a.n_mtiles = (int)((n + BM - 1) / BM);
-    a.n_ktiles = (c.K_pad + BN - 1) / BN;
+    a.n_ktiles = (c.KZ_pad + BN - 1) / BN;
     a.n_units = a.n_mtiles * a.n_ktiles;
     a.N_pad = c.N_pad;
-    a.K_pad = c.K_pad;
+    a.K_pad = c.KZ_pad;
     a.n = n;
     a.sched = w.sched;
     a.out = w.w32;

@@ -124,10 +124,11 @@ __device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool vali
     int *em = sm.em;
     valid = valid && m_obs >= 0;
 
-    // 2. SFR at the time nodes (FP32) and the interval integrals I_j
+    // 2. SFR at the time nodes (FP32) and the interval integrals I_j; nodes
+    //    after t_obs (n > m_obs + 1) bound no age bin and stay 0.
     const float h = a.h_f;
     for (int n = lane; n < a.n_t; n += 32)
-        sfr[n] = valid ? sfr_f<SFH>(p, fmaf((float)n, h, a.t0_f)) : 0.f;
+        sfr[n] = valid && n <= m_obs + 1 ? sfr_f<SFH>(p, fmaf((float)n, h, a.t0_f)) : 0.f;
     __syncwarp();
     for (int j = lane; j < a.n_t - 1; j += 32) itg[j] = 0.5f * h * (sfr[j] + sfr[j + 1]);
     __syncwarp();
@@ -477,8 +478,8 @@ __device__ __forceinline__ void sfr_grad_f(const float *p, float t, float (&gr)[
     }
     const float lr = logf(t / p[0]);
     const float ra = expf(-p[1] * lr), rf = expf(-p[2] * lr);
-    const float D = ra + rf, invD2 = 1.f / (D * D);
-    const float ms = 1.f / D;
+    const float ms = 1.f / (ra + rf);
+    const float invD2 = ms * ms;
     const float zq = (t - (p[3] - 0.9f)) * (1.f / 0.3f);
     const float P = terf_f(zq);
     const float fq = exp10f(-p[4] * P);
@@ -538,54 +539,60 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     const float inv_sig = 1.f / sig;
     const int nz = a.n_z;
     float mu_bar = 0.f, sig_bar = 0.f, slope_bar = 0.f;
-    // Each lane takes runs of 8 consecutive bins (coalesced float4 loads); the
-    // row sum dLoss/dfrac_i is flushed with one shared atomic per row change.
-    for (int k0 = 8 * lane; k0 < a.K && valid; k0 += 256) {
-        int i = k0 / nz, e = k0 - i * nz;
-        const float4 *wp = reinterpret_cast<const float4 *>(what + gi * a.K_pad + k0);
-        float4 wa = wp[0], wb4 = wp[1];
-        float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb4.x, wb4.y, wb4.z, wb4.w};
-        if (scaled) {
-            const float4 *mp = reinterpret_cast<const float4 *>(a.wmul + k0);
-            const float4 ma = __ldg(mp), mb = __ldg(mp + 1);
-            const float mv[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+    // Metallicity-major What (kz = e * A_pad + i): lane g takes the ages 4g ..
+    // 4g+3 and walks the edges e upwards with one float4 load per edge, each
+    // age's dLoss/dfrac in a register.  Beyond the triweight's support the
+    // terms are exact: above it (u >= 3 for the four ages, and so for every
+    // higher edge) P(Z >= edge) and the density vanish, so the walk stops;
+    // below it (u <= -3) P(Z >= edge) = 1 and the density vanishes.
+    constexpr bool tri = MDF == DSPS_MDF_TRIWEIGHT;
+    const float *wrow = what + gi * a.KZ_pad;
+    for (int gq = lane; 4 * gq < a.A_pad && valid; gq += 32) {
+        float mu4[4], xl4[4], fr4[4], fb4[4];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) wv[c] *= mv[c];
+        for (int c = 0; c < 4; ++c) {
+            const int i = 4 * gq + c;
+            xl4[c] = __ldg(a.logage + min(i, a.n_age - 1)) - 9.f;
+            mu4[c] = fmaf(p[7], xl4[c], p[5]);
+            fr4[c] = i < a.n_age ? frac[i] : 0.f;
+            fb4[c] = 0.f;
         }
-        float xl = __ldg(a.logage + i) - 9.f;
-        float mu_i = fmaf(p[7], xl, p[5]);
-        float fr = frac[i];
-        float fb = 0.f;
-        bool open = false;
+        for (int e = 0; e < nz; ++e) {
+            const int kz = e * a.A_pad + 4 * gq;
+            float u[4];
+            if (e > 0) {
+                const float ze = __ldg(a.zedge + e);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            if (k0 + c >= a.K) break;
-            const float wd = wv[c];
-            if (e == 0) {
-                fb += wd;
-            } else {
-                const float u = (__ldg(a.zedge + e) - mu_i) * inv_sig;
-                const float sv = mdf_s<MDF>(u);
-                fb = fmaf(wd, u > 0.f ? -sv : 1.f - sv, fb);
-                const float t = fr * wd * mdf_pdf<MDF>(u) * inv_sig;
+                for (int c = 0; c < 4; ++c) u[c] = (ze - mu4[c]) * inv_sig;
+                if (tri && fminf(fminf(u[0], u[1]), fminf(u[2], u[3])) >= 3.f) break;
+            }
+            float4 wv = *reinterpret_cast<const float4 *>(wrow + kz);
+            if (scaled) {
+                const float4 m = __ldg(reinterpret_cast<const float4 *>(a.wmul + kz));
+                wv.x *= m.x;
+                wv.y *= m.y;
+                wv.z *= m.z;
+                wv.w *= m.w;
+            }
+            const float dw[4] = {wv.x, wv.y, wv.z, wv.w};
+            if (e == 0 || (tri && fmaxf(fmaxf(u[0], u[1]), fmaxf(u[2], u[3])) <= -3.f)) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) fb4[c] += dw[c];
+                continue;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float sv = mdf_s<MDF>(u[c]);
+                fb4[c] = fmaf(dw[c], u[c] > 0.f ? -sv : 1.f - sv, fb4[c]);
+                const float t = fr4[c] * dw[c] * mdf_pdf<MDF>(u[c]) * inv_sig;
                 mu_bar += t;
-                sig_bar = fmaf(t, u, sig_bar);
-                slope_bar = fmaf(t, xl, slope_bar);
-            }
-            open = true;
-            if (++e == nz) {
-                atomicAdd(fracbar + i, fb);
-                fb = 0.f;
-                open = false;
-                e = 0;
-                if (++i < a.n_age) {
-                    xl = __ldg(a.logage + i) - 9.f;
-                    mu_i = fmaf(p[7], xl, p[5]);
-                    fr = frac[i];
-                }
+                sig_bar = fmaf(t, u[c], sig_bar);
+                slope_bar = fmaf(t, xl4[c], slope_bar);
             }
         }
-        if (open) atomicAdd(fracbar + i, fb);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (4 * gq + c < a.n_age) fracbar[4 * gq + c] = fb4[c];
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -602,33 +609,57 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
     const float inv_m = valid ? 1.f / msum : 0.f;
 
-    // reverse of stages 3-4: each bin integral is linear in the node SFRs
+    // reverse of stages 3-4: each bin integral is linear in the node SFRs.
+    //  (a) the partial intervals at each bin's two edges (a few shared atomics
+    //      per bin);
+    //  (b) the whole intervals strictly inside bin i, em[i+1] < m < em[i]:
+    //      each lane finds the bin of each of its intervals by bisection on
+    //      the non-increasing em[], and each node takes half of the weight of
+    //      both intervals it bounds.
     const float h = a.h_f;
-    for (int i = lane; i < a.n_age && valid; i += 32) {
-        const float bb = (fracbar[i] - dot) * inv_m;
+    float *bbin = sm.bmass;   // dLoss/dB_i (the bin masses are not needed again)
+    float *cf = sm.itg;       // weight of each whole interval (likewise)
+    for (int i = lane; i < a.n_age; i += 32) {
+        const float bb = valid ? (fracbar[i] - dot) * inv_m : 0.f;
+        bbin[i] = bb;
         const int mi = sm.em[i], mo = sm.em[i + 1];
         const float ri = sm.er[i], ro = sm.er[i + 1];
-        if (mi < 0 || bb == 0.f) continue;
+        if (!valid || mi < 0 || bb == 0.f) continue;
         auto add = [&](int m, float len, float rbar) {
             atomicAdd(sbar + m, bb * len * (1.f - rbar));
             atomicAdd(sbar + m + 1, bb * len * rbar);
         };
         if (mo < 0) {
-            for (int m = 0; m < mi; ++m) add(m, h, 0.5f);
             add(mi, ri * h, 0.5f * ri);
         } else if (mi == mo) {
             add(mi, __ldg(a.bwidth + i), 0.5f * (ri + ro));
         } else {
             add(mo, mi == mo + 1 ? __ldg(a.bwidth + i) - ri * h : (1.f - ro) * h, 0.5f * (ro + 1.f));
-            for (int m = mo + 1; m < mi; ++m) add(m, h, 0.5f);
             add(mi, ri * h, 0.5f * ri);
         }
     }
     __syncwarp();
+    for (int m = lane; m < a.n_t - 1; m += 32) {
+        float v = 0.f;
+        if (valid) {
+            int lo = 0, hi = a.n_age + 1;   // first edge with em <= m
+            while (lo < hi) {
+                const int md = (lo + hi) >> 1;
+                if (sm.em[md] <= m) hi = md;
+                else lo = md + 1;
+            }
+            if (lo > 0 && lo <= a.n_age && sm.em[lo] < m) v = bbin[lo - 1] * h;
+        }
+        cf[m] = v;
+    }
+    __syncwarp();
+    for (int n = lane; n < a.n_t; n += 32)
+        sbar[n] += 0.5f * ((n > 0 ? cf[n - 1] : 0.f) + (n < a.n_t - 1 ? cf[n] : 0.f));
+    __syncwarp();
 
-    // reverse of stage 2: the SFR parameters
+    // reverse of stage 2: the SFR parameters (nodes after t_obs have no adjoint)
     float tb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int n = lane; n < a.n_t && valid; n += 32) {
+    for (int n = lane; n <= gp.m_obs + 1 && n < a.n_t && valid; n += 32) {
         float gr[5];
         sfr_grad_f<SFH>(p, fmaf((float)n, h, a.t0_f), gr);
 #pragma unroll
