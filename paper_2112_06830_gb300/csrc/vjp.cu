@@ -71,40 +71,26 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 
 #pragma unroll
     for (int q = 0; q < 4 * Q4; ++q) nb[q] = q < band.Q ? cq[r * QSTRIDE_MAX + q] : 0.f;
     // Grid indices col + i0 - 1 .. col + i0 + 2 are table rows col + i0 .. col +
-    // i0 + 3.  For the 32 columns of one pass the warp needs 35 consecutive
-    // rows: each lane reduces its own row (and lanes 0..2 the last three), the
-    // neighbours' come by shuffles.
-    for (int col0 = kb0 * 32; col0 < kb1 * 32; col0 += 32) {
-        const int col = col0 + lane;
-        float own = 0.f, extra = 0.f;
-        if (rc.valid) {
-            const float4 *tr = tab + (size_t)min(col + rc.i0, m_last) * Q4;
-            const float4 *te = tab + (size_t)min(col + rc.i0 + 32, m_last) * Q4;
+    // i0 + 3.  One pass covers 64 columns (two per lane, 32 apart), for which
+    // the warp needs 67 consecutive rows: each lane reduces its two rows (and
+    // lanes 0..2 the last three), the neighbours' come by shuffles.  The two
+    // halves' loads are independent, which hides the table latency.
+    auto reduce_row = [&](int row) {
+        const float4 *tr = tab + (size_t)min(row, m_last) * Q4;
+        float v = 0.f;
 #pragma unroll
-            for (int qq = 0; qq < Q4; ++qq) {
-                const float4 t = __ldg(tr + qq);
-                own = fmaf(nb[4 * qq + 0], t.x, fmaf(nb[4 * qq + 1], t.y, fmaf(nb[4 * qq + 2], t.z, fmaf(nb[4 * qq + 3], t.w, own))));
-                if (lane < 3) {
-                    const float4 x = __ldg(te + qq);
-                    extra = fmaf(nb[4 * qq + 0], x.x, fmaf(nb[4 * qq + 1], x.y, fmaf(nb[4 * qq + 2], x.z, fmaf(nb[4 * qq + 3], x.w, extra))));
-                }
-            }
+        for (int qq = 0; qq < Q4; ++qq) {
+            const float4 t = __ldg(tr + qq);
+            v = fmaf(nb[4 * qq + 0], t.x, fmaf(nb[4 * qq + 1], t.y, fmaf(nb[4 * qq + 2], t.z, fmaf(nb[4 * qq + 3], t.w, v))));
         }
-        float cm[4];
-        cm[0] = own;
-#pragma unroll
-        for (int d = 1; d < 4; ++d) {
-            const float a1 = __shfl_sync(0xffffffffu, own, (lane + d) & 31);
-            const float a2 = __shfl_sync(0xffffffffu, extra, (lane + d - 32) & 31);
-            cm[d] = lane + d < 32 ? a1 : a2;
-        }
-        float sh = 0.f;
-        if (rc.valid) {
-            const float ell = fmaf((float)col, cc.dell, cc.ell0);
-            const float F = exp2f(rc.alpha * exp2f(rc.beta * ell));
-            sh = col_kappa(cc, col) * F *
-                 fmaf(rc.w[0], cm[0], fmaf(rc.w[1], cm[1], fmaf(rc.w[2], cm[2], rc.w[3] * cm[3])));
-        }
+        return v;
+    };
+    auto shat_at = [&](int col, const float (&cm)[4]) {
+        const float ell = fmaf((float)col, cc.dell, cc.ell0);
+        const float F = exp2f(rc.alpha * exp2f(rc.beta * ell));
+        return col_kappa(cc, col) * F * fmaf(rc.w[0], cm[0], fmaf(rc.w[1], cm[1], fmaf(rc.w[2], cm[2], rc.w[3] * cm[3])));
+    };
+    auto store = [&](int col, float sh) {
         if (BF16) {
             const __nv_bfloat16 h = __float2bfloat16_rn(sh);
             out_hi[r * N_pad + col] = h;
@@ -112,6 +98,31 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 
         } else {
             out32[r * N_pad + col] = sh;
         }
+    };
+    const int cend = kb1 * 32;
+    for (int col0 = kb0 * 32; col0 < cend; col0 += 64) {
+        const bool two = col0 + 32 < cend;
+        const int ca = col0 + lane, cb = ca + 32;
+        float va = 0.f, vb = 0.f, ve = 0.f;
+        if (rc.valid) {
+            va = reduce_row(ca + rc.i0);
+            vb = reduce_row(cb + rc.i0);
+            if (two && lane < 3) ve = reduce_row(cb + 32 + rc.i0);
+        }
+        float cma[4], cmb[4];
+        cma[0] = va;
+        cmb[0] = vb;
+#pragma unroll
+        for (int d = 1; d < 4; ++d) {
+            const int src = (lane + d) & 31;
+            const float a1 = __shfl_sync(0xffffffffu, va, src);
+            const float b1 = __shfl_sync(0xffffffffu, vb, src);
+            const float e1 = __shfl_sync(0xffffffffu, ve, src);
+            cma[d] = lane + d < 32 ? a1 : b1;
+            cmb[d] = lane + d < 32 ? b1 : e1;
+        }
+        store(ca, rc.valid ? shat_at(ca, cma) : 0.f);
+        if (two) store(cb, rc.valid ? shat_at(cb, cmb) : 0.f);
     }
 }
 
