@@ -1,5 +1,5 @@
 // vjp_tc.cu -- tcgen05 form of the adjoint contraction
-//   What[g, k] = sum_n Shat[g, n] L[k, n]        (dLoss/domega, see vjp.cu)
+//   What[g, kz] = sum_n Shat[g, n] Ld[kz, n]      (dLoss/domega, see vjp.cu)
 // with Shat and the row-scaled SSP block both split into bf16 hi + lo
 // (hi*hi + hi*lo + lo*hi, FP32 accumulate in TMEM), written as FP32.
 //
@@ -9,7 +9,9 @@
 // epilogue.cuh: vjp_band).  Warp roles
 // as in phot_tc.cu: TMA producer, single-thread MMA issuer with a double
 // TMEM accumulator, eight epilogue warps that read rows with tcgen05.ld and
-// store them.  Every mbarrier wait is bounded.
+// write them as 32 x 32 blocks through shared memory and TMA stores (a row per
+// thread would scatter every warp store over 32 rows).  Every mbarrier wait is
+// bounded.
 #include "dsps_internal.cuh"
 #include "epilogue.cuh"
 #include "tc_common.cuh"
@@ -29,21 +31,22 @@ constexpr int NUM_EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
 constexpr uint32_t TMEM_COLS = 2 * BN;
 constexpr size_t BAR_BYTES = 1024;
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES;
+constexpr size_t STAGE_OUT_BYTES = 32 * 32 * 4;   // per epilogue warp: one 32 x 32 FP32 block
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + NUM_EPI_WARPS * STAGE_OUT_BYTES;
 
 struct VArgs {
     const int2 *trange;
     VjpBand band;
-    int n_mtiles, n_ktiles, n_units, N_pad, K_pad;
+    int n_mtiles, n_ktiles, n_units, N_pad, K_pad;   // K_pad: the context's KZ_pad (output row length)
     int64_t n;
     int *sched;       // unit counter, zero at launch
-    float *out;       // [n][K_pad] (K_pad = the context's KZ_pad: metallicity-major rows)
     unsigned *err;
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
 vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
-              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo, const VArgs a) {
+              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+              const __grid_constant__ CUtensorMap tmOut, const VArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -170,7 +173,10 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
         const int ew = warp - 2;
         const int qd = warp & 3;
         const int half = ew >> 2;
-        const int row = qd * 32 + lane;
+        // Each warp writes its 32 rows x 32 columns per step through a 4 KB
+        // shared-memory block (128-byte swizzle) and one TMA store.
+        unsigned char *outs = sm + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + (size_t)ew * STAGE_OUT_BYTES;
+        const uint32_t outs_u32 = smem_u32(outs);
         int as = 0;
         uint32_t aphase = 0;
         while (true) {
@@ -180,7 +186,6 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
             u = __shfl_sync(0xffffffffu, u, 0);
             if (!have || u < 0) break;
             const int mt = u / a.n_ktiles, kt = u - mt * a.n_ktiles;
-            const int64_t rowg = (int64_t)mt * BM + row;
             int got = 1;
             if (lane == 0) got = mbar_wait(accf0 + 8 * as, aphase, abort_flag, a.err) ? 1 : 0;
             got = __shfl_sync(0xffffffffu, got, 0);
@@ -197,16 +202,25 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
                     if (lane == 0) mbar_arrive(acce0 + 8 * as);
                 }
                 const int col0 = kt * BN + half * 128 + c * 32;
-                if (rowg < a.n && col0 < a.K_pad) {
-                    float4 *dst = reinterpret_cast<float4 *>(a.out + rowg * a.K_pad + col0);
+                if (col0 < a.K_pad && (int64_t)mt * BM + qd * 32 < a.n) {   // a box past the last row writes nothing
+                    if (lane == 0) bulk_wait_read();   // the previous store has read the block
+                    __syncwarp();
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                             __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                        *reinterpret_cast<float4 *>(outs + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                            make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                        __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&tmOut, outs_u32, col0, mt * BM + qd * 32);
+                        bulk_commit();
+                    }
                 }
             }
             if (++as == 2) { as = 0; aphase ^= 1u; }
         }
+        if (lane == 0) bulk_wait_all();
     }
 
     __syncwarp();
@@ -224,11 +238,12 @@ cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs,
     if (n <= 0) return cudaSuccess;
     const auto *hi = reinterpret_cast<const __nv_bfloat16 *>(w.shat);
     const __nv_bfloat16 *lo = hi + (size_t)w.cap * c.N_pad;
-    CUtensorMap ah, al, bh, bl;
+    CUtensorMap ah, al, bh, bl, ot;
     if (!make_tmap(&ah, hi, (uint64_t)c.N_pad, (uint64_t)n, BM) ||
         !make_tmap(&al, lo, (uint64_t)c.N_pad, (uint64_t)n, BM) ||
         !make_tmap(&bh, c.d_L_hi, (uint64_t)c.N_pad, (uint64_t)c.KZ_pad, BN) ||
-        !make_tmap(&bl, c.d_L_lo, (uint64_t)c.N_pad, (uint64_t)c.KZ_pad, BN))
+        !make_tmap(&bl, c.d_L_lo, (uint64_t)c.N_pad, (uint64_t)c.KZ_pad, BN) ||
+        !make_tmap_f32_store(&ot, w.w32, (uint64_t)c.KZ_pad, (uint64_t)n))
         return cudaErrorInvalidValue;
     VArgs a{};
     a.trange = w.trange;
@@ -240,13 +255,12 @@ cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs,
     a.K_pad = c.KZ_pad;
     a.n = n;
     a.sched = w.sched;
-    a.out = w.w32;
     a.err = c.d_err;
     const int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;
     cudaError_t e = cudaFuncSetAttribute(vjp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.sched, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    vjp_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
+    vjp_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, ot, a);
     return cudaGetLastError();
 }
 
