@@ -48,7 +48,8 @@ class _Grid(C.Structure):
                 ("lam", C.POINTER(C.c_double)), ("l_ssp", C.POINTER(C.c_double)),
                 ("t0", C.c_double), ("t1", C.c_double), ("n_t", C.c_int),
                 ("om0", C.c_double), ("w0", C.c_double), ("h", C.c_double),
-                ("sfh_model", C.c_int), ("mdf_kernel", C.c_int)]
+                ("sfh_model", C.c_int), ("mdf_kernel", C.c_int),
+                ("mdf_mean", C.c_int), ("mdf_x0", C.c_double), ("mdf_h", C.c_double)]
 
 
 class _Filters(C.Structure):
@@ -75,6 +76,8 @@ def _load():
             lib.orc_age_edges_gyr.argtypes = [C.POINTER(_Grid), dp]
             lib.orc_age_fracs_from_sfr.argtypes = [C.POINTER(_Grid), dp, C.c_double, dp]
             lib.orc_mdf.argtypes = [C.POINTER(_Grid), C.c_double, C.c_double, dp, dp, dp]
+            lib.orc_mdf_mean.restype = C.c_double
+            lib.orc_mdf_mean.argtypes = [C.POINTER(_Grid), dp, C.c_int, dp, dp]
             lib.orc_dust_trans.restype = C.c_double
             lib.orc_dust_trans.argtypes = [C.c_double] * 3
             lib.orc_filter_trans.restype = C.c_double
@@ -104,7 +107,7 @@ class Grid:
     """SSP grid + SFR time grid + cosmology + model switches, held as float64."""
 
     def __init__(self, log_age_yr, lgz, lam, l_ssp, t0=0.05, t1=13.8, n_t=200,
-                 om0=0.3, w0=-1.0, h=0.7, sfh_model=0, mdf_kernel=0):
+                 om0=0.3, w0=-1.0, h=0.7, sfh_model=0, mdf_kernel=0, mdf_mean=0, mdf_x0=9.0, mdf_h=0.5):
         self.log_age_yr = _f64(log_age_yr)
         self.lgz = _f64(lgz)
         self.lam = _f64(lam)
@@ -112,9 +115,11 @@ class Grid:
         self.t0, self.t1, self.n_t = float(t0), float(t1), int(n_t)
         self.om0, self.w0, self.h = float(om0), float(w0), float(h)
         self.sfh_model, self.mdf_kernel = int(sfh_model), int(mdf_kernel)
+        self.mdf_mean, self.mdf_x0, self.mdf_h = int(mdf_mean), float(mdf_x0), float(mdf_h)
         self._c = _Grid(len(self.log_age_yr), len(self.lgz), len(self.lam), _dp(self.log_age_yr),
                         _dp(self.lgz), _dp(self.lam), _dp(self.l_ssp), self.t0, self.t1, self.n_t,
-                        self.om0, self.w0, self.h, self.sfh_model, self.mdf_kernel)
+                        self.om0, self.w0, self.h, self.sfh_model, self.mdf_kernel,
+                        self.mdf_mean, self.mdf_x0, self.mdf_h)
 
     @property
     def n_age(self):
@@ -203,6 +208,14 @@ def age_fracs_from_sfr(grid: Grid, sfr_nodes, t_obs):
     out = np.zeros(grid.n_age)
     _load().orc_age_fracs_from_sfr(C.byref(grid._c), _dp(s), float(t_obs), _dp(out))
     return out
+
+
+def mdf_mean(grid: Grid, params, i):
+    """(mu_i, d mu_i / d p5, d mu_i / d p7) for age bin i of one galaxy's parameters."""
+    p = _f64(params)
+    d5, d7 = np.zeros(1), np.zeros(1)
+    mu = _load().orc_mdf_mean(C.byref(grid._c), _dp(p), int(i), _dp(d5), _dp(d7))
+    return mu, float(d5[0]), float(d7[0])
 
 
 def mdf(grid: Grid, mu_i, sigma):

@@ -18,9 +18,9 @@
  *              model 1 (double power law with quench):
  *                      p0 = t_peak [Gyr], p1 = alpha_rise, p2 = alpha_fall,
  *                      p3 = t_q [Gyr], p4 = q_drop [dex]
- *   row 5      mdf_mu     (log10 Z/Zsun at the 1 Gyr pivot)
+ *   row 5      mdf_mu     (log10 Z/Zsun at the 1 Gyr pivot; mu_young for mean model 1)
  *   row 6      mdf_sigma  [dex]
- *   row 7      mdf_slope  d mu / d log10(age/yr)
+ *   row 7      mdf_slope  d mu / d log10(age/yr) (mu_old for mean model 1)
  *   row 8      Av
  *   row 9      dust delta
  *   row 10     logM       log10 of the stellar mass formed by t_obs [Msun]
@@ -51,6 +51,8 @@ typedef struct {
     double om0, w0, h;         /* flat wCDM                                 */
     int sfh_model;             /* 0 delayed tau, 1 double power law+quench */
     int mdf_kernel;            /* 0 triweight, 1 Gaussian                  */
+    int mdf_mean;              /* 0 linear in log age, 1 T_erf transition  */
+    double mdf_x0, mdf_h;      /* transition centre [log10 yr] and width   */
 } orc_grid;
 
 typedef struct {
@@ -284,6 +286,28 @@ void orc_mdf(const orc_grid *g, double mu_i, double sigma, double *P /* n_z */,
     }
 }
 
+/* Mean lgZ of the MDF for age bin i (Sec. 3.2, Eq. agedep_mdf), and its
+ * derivatives with respect to parameter rows 5 and 7.
+ *   model 0 (linear reading): mu_i = p5 + p7 (log10 age_i - 9).
+ *   model 1 (the paper's form): the mean moves from a young-age value to an
+ *     old-age value along the triweight cumulative kernel in log age,
+ *     mu_i = (1 - T) p5 + T p7,  T = T_erf((log10 age_i - x0) / h),  p5 = mu_young,
+ *     p7 = mu_old; the transition's centre x0 and width h are not given in
+ *     the paper and are grid options (reading). */
+double orc_mdf_mean(const orc_grid *g, const double *par, int i, double *d5, double *d7)
+{
+    double x = g->log_age_yr[i];
+    if (g->mdf_mean == 1) {
+        double T = orc_triweight_cdf((x - g->mdf_x0) / g->mdf_h);
+        if (d5) *d5 = 1.0 - T;
+        if (d7) *d7 = T;
+        return (1.0 - T) * par[5] + T * par[7];
+    }
+    if (d5) *d5 = 1.0;
+    if (d7) *d7 = x - 9.0;
+    return par[5] + par[7] * (x - 9.0);
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 3.4: power-law dust attenuation (Eq. attenuation, simplified   */
 /* Eq. salim with k = 1 at lambda_V: A_lambda = Av (lam/5500)^(-0.7+d)) */
@@ -385,7 +409,7 @@ static void galaxy_weights(const orc_grid *g, const double *par /* 12 */, double
     for (int n = 0; n < g->n_t; ++n) sfr[n] = orc_sfr(g->sfh_model, par, g->t0 + n * h, NULL);
     orc_age_fracs_from_sfr(g, sfr, t_obs, frac);
     for (int i = 0; i < g->n_age; ++i) {
-        double mu_i = par[5] + par[7] * (g->log_age_yr[i] - 9.0);
+        double mu_i = orc_mdf_mean(g, par, i, NULL, NULL);
         orc_mdf(g, mu_i, par[6], P, NULL, NULL);
         for (int j = 0; j < g->n_z; ++j) omega[i * g->n_z + j] = frac[i] * P[j];
     }
@@ -414,8 +438,9 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
     double *frac = malloc(sizeof(double) * NA);
     for (int i = 0; i < NA; ++i) frac[i] = (Mhi[i] - Mhi[i + 1]) / Mtot;
     double *P = malloc(sizeof(double) * K), *dPmu = malloc(sizeof(double) * K), *dPsig = malloc(sizeof(double) * K);
+    double *dmu5 = malloc(sizeof(double) * NA), *dmu7 = malloc(sizeof(double) * NA);
     for (int i = 0; i < NA; ++i) {
-        double mu_i = par[5] + par[7] * (g->log_age_yr[i] - 9.0);
+        double mu_i = orc_mdf_mean(g, par, i, dmu5 + i, dmu7 + i);
         orc_mdf(g, mu_i, par[6], P + i * NZ, dPmu + i * NZ, dPsig + i * NZ);
     }
     double *S = calloc(N, sizeof(double));
@@ -472,9 +497,9 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
         int i = k / NZ;
         fracbar[i] += wbar * P[k];
         double Pbar = wbar * frac[i];
-        pbar[5] += Pbar * dPmu[k];
+        pbar[5] += Pbar * dPmu[k] * dmu5[i];
         pbar[6] += Pbar * dPsig[k];
-        pbar[7] += Pbar * dPmu[k] * (g->log_age_yr[i] - 9.0);
+        pbar[7] += Pbar * dPmu[k] * dmu7[i];
     }
     /* frac_i = (Mhi_i - Mhi_{i+1}) / Mtot with Mtot = Mhi_0 */
     double *Mbar = calloc(NA + 1, sizeof(double));
@@ -495,7 +520,7 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
 
     free(sfrbar); free(coef); free(Mbar); free(fracbar); free(Sbar); free(Nbar);
     free(Nq); free(T); free(off); free(u); free(F); free(S); free(dPsig); free(dPmu); free(P);
-    free(frac); free(Mhi); free(e); free(dsfr); free(sfr);
+    free(dmu7); free(dmu5); free(frac); free(Mhi); free(e); free(dsfr); free(sfr);
 }
 
 /* ------------------------------------------------------------------ */

@@ -335,7 +335,8 @@ def test_logm_shifts_all_bands():
 
 # ---------------------------------------------------------------- brute force
 
-def _brute_force_mags(log_age, lgz, lam, L, filters, par, sfh_model, kernel, om0=0.3, h=0.7):
+def _brute_force_mags(log_age, lgz, lam, L, filters, par, sfh_model, kernel, om0=0.3, h=0.7, mean=0,
+                      x0=9.0, hw=0.5):
     """Independent restatement on a tiny grid: scipy quadrature of the SFR
     function itself for every age bin, quadrature of the MDF density for every
     lgZ bin, scipy quadrature for the cosmology, and an explicit loop for the
@@ -356,8 +357,14 @@ def _brute_force_mags(log_age, lgz, lam, L, filters, par, sfh_model, kernel, om0
     zedges = np.concatenate([[-np.inf], 0.5 * (lgz[1:] + lgz[:-1]), [np.inf]])
     pdf = oracle.triweight_pdf if kernel == 0 else (lambda u: math.exp(-0.5 * u * u) / math.sqrt(2 * math.pi))
     S = np.zeros(len(lam))
+    tri = lambda u: 35.0 / 96.0 * (1.0 - u * u / 9.0) ** 3 if abs(u) < 3.0 else 0.0
     for i in range(len(log_age)):
-        mu = par[5] + par[7] * (log_age[i] - 9)
+        if mean == 0:
+            mu = par[5] + par[7] * (log_age[i] - 9)
+        else:   # transition young -> old along the quadrature of the triweight density
+            zt = (log_age[i] - x0) / hw
+            T = 0.0 if zt <= -3 else (1.0 if zt >= 3 else integrate.quad(tri, -3.0, zt, epsabs=1e-15)[0])
+            mu = (1.0 - T) * par[5] + T * par[7]
         sg = par[6]
         for j in range(len(lgz)):
             a = max((zedges[j] - mu) / sg, -8.0)
@@ -377,8 +384,8 @@ def _brute_force_mags(log_age, lgz, lam, L, filters, par, sfh_model, kernel, om0
     return np.array(out)
 
 
-@pytest.mark.parametrize("sfh_model,kernel", [(0, 0), (1, 0), (1, 1)])
-def test_brute_force_tiny_grid(sfh_model, kernel):
+@pytest.mark.parametrize("sfh_model,kernel,mean", [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 0, 1)])
+def test_brute_force_tiny_grid(sfh_model, kernel, mean):
     log_age = np.array([6.0, 7.5, 8.7, 9.6])
     lgz = np.array([-1.0, -0.4, 0.1])
     lam = np.geomspace(2000.0, 9000.0, 16)
@@ -386,25 +393,32 @@ def test_brute_force_tiny_grid(sfh_model, kernel):
     L = rng.uniform(0.5e-15, 2e-15, (4, 3, 16))
     filters = [synth.gaussian_filter(c, fwhm=600.0, step=5.0) for c in (4000.0, 6500.0)]
     n_t = 40001  # fine time grid: the piecewise-linear reading is then within 1e-7 of the quadrature
-    g = oracle.Grid(log_age, lgz, lam, L, n_t=n_t, sfh_model=sfh_model, mdf_kernel=kernel)
+    g = oracle.Grid(log_age, lgz, lam, L, n_t=n_t, sfh_model=sfh_model, mdf_kernel=kernel, mdf_mean=mean,
+                    mdf_x0=8.0, mdf_h=0.6)
     F = oracle.Filters(filters)
     p = synth.make_population(sfh_model, 3, 5)
     p[6] = 0.35
     p[11] = np.minimum(p[11], 0.6)
+    if mean == 1:
+        p[5], p[7] = [0.2, -0.1, 0.05], [-0.9, -0.6, -1.2]     # mu_young, mu_old
     m = oracle.mags(g, F, p)
     for gi in range(p.shape[1]):
-        ref = _brute_force_mags(log_age, lgz, lam, L, filters, p[:, gi], sfh_model, kernel)
+        ref = _brute_force_mags(log_age, lgz, lam, L, filters, p[:, gi], sfh_model, kernel, mean=mean, x0=8.0,
+                                hw=0.6)
         np.testing.assert_allclose(m[gi], ref, atol=2e-6)
 
 
 # ---------------------------------------------------------------- gradients
 
-@pytest.mark.parametrize("wl,model,kernel", [("small", 0, 0), ("small", 1, 0), ("small", 1, 1)])
-def test_adjoint_matches_central_differences(wl, model, kernel):
+@pytest.mark.parametrize("wl,model,kernel,mean", [("small", 0, 0, 0), ("small", 1, 0, 0), ("small", 1, 1, 0),
+                                                   ("small", 1, 0, 1)])
+def test_adjoint_matches_central_differences(wl, model, kernel, mean):
     g, f, _ = synth.workload_inputs(wl, n_gal=1)
-    G = oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, sfh_model=model, mdf_kernel=kernel)
+    G = oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, sfh_model=model, mdf_kernel=kernel, mdf_mean=mean)
     F = oracle.Filters(f)
     p = synth.make_population(model, 3, 21)
+    if mean == 1:
+        p[5], p[7] = [0.1, -0.2, 0.25], [-0.8, -1.1, -0.5]     # mu_young, mu_old
     rng = np.random.default_rng(0)
     mbar = rng.standard_normal((p.shape[1], F.n_filt))
     _, pb = oracle.mags_vjp(G, F, p, mbar)
@@ -440,3 +454,58 @@ def test_gradient_signs_follow_the_paper():
     mb[:, 0], mb[:, -1] = 1.0, -1.0          # blue minus red colour
     _, pb = oracle.mags_vjp(G, F, p, mb)
     assert (pb[5] > 0).all()
+
+
+# ---------------------------------------------------------------- age-dependent MDF, T_erf form
+
+def _terf_grid(x0=8.5, h=0.4):
+    xs = np.array([x0 - 3 * h - 0.2, x0 - 3 * h - 0.01, x0 - 0.7 * h, x0, x0 + 1.3 * h, x0 + 3 * h + 0.01,
+                   x0 + 3 * h + 0.3])
+    lam = np.geomspace(1e3, 1e5, 50)
+    L = np.ones((len(xs), 3, len(lam)))
+    return oracle.Grid(xs, [-1.0, -0.3, 0.2], lam, L, mdf_mean=1, mdf_x0=x0, mdf_h=h), xs
+
+
+def test_terf_mean_limits_midpoint_and_weights():
+    """Sec. 3.2: the mean is the young value for the youngest populations and
+    the old value for the oldest (the triweight CDF saturates at +-3 widths),
+    the average of the two at the transition centre, and its derivatives with
+    respect to the two values sum to one."""
+    g, xs = _terf_grid()
+    par = np.zeros(12)
+    par[5], par[7] = 0.3, -1.1
+    mus = [oracle.mdf_mean(g, par, i) for i in range(len(xs))]
+    assert mus[0][0] == 0.3 and mus[1][0] == 0.3
+    assert mus[-1][0] == -1.1 and mus[-2][0] == -1.1
+    assert mus[3][0] == pytest.approx(0.5 * (0.3 - 1.1), abs=1e-15)
+    for mu, d5, d7 in mus:
+        assert d5 + d7 == pytest.approx(1.0, abs=1e-15)
+        assert 0.0 <= d7 <= 1.0
+    # monotone from young to old
+    assert all(a[0] >= b[0] for a, b in zip(mus, mus[1:]))
+
+
+def test_terf_mean_derivatives_match_differences():
+    g, xs = _terf_grid()
+    par = np.zeros(12)
+    par[5], par[7] = 0.2, -0.9
+    for i in range(len(xs)):
+        _, d5, d7 = oracle.mdf_mean(g, par, i)
+        for k, d in ((5, d5), (7, d7)):
+            pp, pm = par.copy(), par.copy()
+            pp[k] += 1e-6
+            pm[k] -= 1e-6
+            fd = (oracle.mdf_mean(g, pp, i)[0] - oracle.mdf_mean(g, pm, i)[0]) / 2e-6
+            assert fd == pytest.approx(d, abs=1e-9)
+
+
+def test_terf_mean_with_equal_values_is_the_uncorrelated_mdf():
+    """mu_young = mu_old = mu gives the age-independent MDF (Eq. simple_mdf),
+    the linear form with zero slope."""
+    g, f, p = synth.workload_inputs("small", n_gal=4)
+    Gt = oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, mdf_mean=1, mdf_x0=8.0, mdf_h=0.7)
+    Gl = oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, mdf_mean=0)
+    pt, pl = p.copy(), p.copy()
+    pt[7] = pt[5]
+    pl[7] = 0.0
+    np.testing.assert_allclose(oracle.weights(Gt, pt), oracle.weights(Gl, pl), rtol=1e-9, atol=0)
