@@ -428,6 +428,29 @@ def run_ours(a):
     assert np.isfinite(h_mags.numpy()).all()
     assert ctx.device_error() == 0
 
+    # The paper's age-dependent MDF in its T_erf form (mu_young -> mu_old along the
+    # triweight CDF in log age), same galaxies otherwise: split-bf16 forward.
+    ctx_t = dsps.Context(ssp, sfh_model=synth.SFH_DPL_QUENCH, device=local, mdf_mean=dsps.DSPS_MDF_MEAN_TERF)
+    sid_t = ctx_t.add_filters(synth.make_filters(N_FILT))
+    d_params_t = torch.from_numpy(synth.with_terf_mdf(params_h, 1, shard_start(rank, G)).astype(np.float32)).cuda()
+
+    def step_t():
+        ctx_t.photometry(d_params_t, sid_t, precision=dsps.DSPS_PREC_BF16X3, out=d_mags, stream=stream)
+
+    for _ in range(a.warmup):
+        step_t()
+    barrier()
+    t_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    for e0, e1 in t_evs:
+        flush.fill_(1)
+        e0.record(stream)
+        step_t()
+        e1.record(stream)
+    barrier()
+    ms_terf = max_over_ranks(float(np.mean([e0.elapsed_time(e1) for e0, e1 in t_evs])), dist, "cuda")
+    ctx_t.close()
+    del d_params_t
+
     # Precision forms at 1e6 galaxies (same grid and distributions): split-bf16
     # against FP32 throughput, and their per-galaxy magnitude difference.
     precision = None
@@ -525,6 +548,8 @@ def run_ours(a):
                 "h2d_bytes_per_step": int(params_h.nbytes), "d2h_bytes_per_step": int(G * N_FILT * 4)},
         "gpu_launches": int(total_launches),
         "precision_forms_1e6": precision,
+        "mdf_terf": {"value": ws * G * N_FILT / (ms_terf * 1e-3), "ms_per_step": ms_terf,
+                     "note": "age-dependent MDF, T_erf transition mu_young -> mu_old (centre 1 Gyr, 0.5 dex)"},
         "serve": serve,
         "clocks": clocks,
     }

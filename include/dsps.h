@@ -44,9 +44,12 @@
  *                                 SFR ~ 1/[(t/tp)^-p1 + (t/tp)^-p2]
  *                                       * 10^(-q Terf(t | t_q - 0.9, 0.3))
  *                                 (quench floor reached at t_q, Sec. 3.1).
- *    5     mdf_mu     mean log10(Z/Zsun) at age 1 Gyr
+ *    5     mdf_mu     DSPS_MDF_MEAN_LINEAR: mean log10(Z/Zsun) at age 1 Gyr;
+ *                     DSPS_MDF_MEAN_TERF: mean of the youngest stars (mu_young)
  *    6     mdf_sigma  MDF width [dex], > 0
- *    7     mdf_slope  d mean / d log10(age/yr)  (0 = uncorrelated MDF)
+ *    7     mdf_slope  DSPS_MDF_MEAN_LINEAR: d mean / d log10(age/yr) (0 =
+ *                     uncorrelated MDF); DSPS_MDF_MEAN_TERF: mean of the
+ *                     oldest stars (mu_old)
  *    8     Av         V-band attenuation [mag]
  *    9     delta      dust slope: A(lam) = Av (lam/5500 A)^(-0.7 + delta)
  *    10    logM       log10 of the stellar mass formed by t_obs [Msun]
@@ -80,14 +83,21 @@ enum {
 
 enum { DSPS_SFH_DELAYED_TAU = 0, DSPS_SFH_DPL_QUENCH = 1 };
 enum { DSPS_MDF_TRIWEIGHT = 0, DSPS_MDF_GAUSSIAN = 1 };
+/* Age dependence of the MDF mean (Sec. 3.2, Eq. agedep_mdf), x = log10(age/yr):
+ *   DSPS_MDF_MEAN_LINEAR  mu(x) = p5 + p7 (x - 9)
+ *   DSPS_MDF_MEAN_TERF    mu(x) = (1 - T) p5 + T p7, T = Terf((x - x0) / h):
+ *                         the paper's transition from mu_young to mu_old along
+ *                         the triweight cumulative kernel (Appendix B). */
+enum { DSPS_MDF_MEAN_LINEAR = 0, DSPS_MDF_MEAN_TERF = 1 };
 
 /* Arithmetic of the contraction (Eq. full_mdf):
  *   DSPS_PREC_FP32   FP32 weights x FP32 SSP grid, FP32 FMA on the SIMT cores.
  *   DSPS_PREC_BF16X3 SSP rows scaled by powers of two and split into
  *                    bf16 hi + lo, weights likewise; hi*hi + hi*lo + lo*hi
  *                    products on the tcgen05 tensor cores, FP32 accumulate.
- * Both use the same weights kernel (FP64 cumulative SFH mass and age-bin
- * differencing) and the same FP32 epilogue. */
+ * Both use the same weights kernel (age-bin masses integrated directly, with a
+ * compensated FP32 node prefix; FP64 only for t_obs's position on the SFR time
+ * grid) and the same FP32 epilogue. */
 enum { DSPS_PREC_FP32 = 0, DSPS_PREC_BF16X3 = 1 };
 
 #define DSPS_NPAR 12
@@ -122,12 +132,16 @@ typedef struct {
     double z_max;              /* largest accepted redshift (cosmology table)    */
     int32_t band_skip;         /* 1: the tensor-core path skips wavelength tiles
                                   outside every redshifted filter of a tile's
-                                  galaxies (exact: their transmission is zero);
-                                  0: dense contraction over all wavelengths     */
+                                  galaxies and K blocks where every galaxy of a
+                                  tile has zero weight (exact: those terms are
+                                  zero); 0: dense contraction                   */
+    int32_t mdf_mean;          /* DSPS_MDF_MEAN_*                               */
+    double mdf_terf_x0;        /* DSPS_MDF_MEAN_TERF: transition centre x0 and   */
+    double mdf_terf_h;         /* width h [dex], h > 0 (defaults 9, 0.5)         */
 } dsps_opts;
 
 /* Fills *o with the defaults above (device 0, max_chunk 262144,
- * hbm_budget 8 GiB, 4 streams, z_max 10, band_skip 1). */
+ * hbm_budget 8 GiB, 4 streams, z_max 10, band_skip 1, linear MDF mean). */
 void dsps_default_opts(dsps_opts *o);
 
 /* Creates a context on o->device: uploads the SSP block (FP32 copy, and the

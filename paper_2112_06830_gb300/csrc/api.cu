@@ -133,7 +133,7 @@ void free_ctx(Ctx *c) {
         cudaFree(fs.d_tab);
         cudaFree(fs.d_offq);
     }
-    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_edges, c->d_einh, c->d_bwidth,
+    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_edges, c->d_einh, c->d_bwidth,
                     c->d_zedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->d_err, c->d_stats,
                     c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d};
     for (void *p : ptrs) cudaFree(p);
@@ -176,7 +176,21 @@ void dsps_default_opts(dsps_opts *o) {
     o->n_streams = 4;
     o->z_max = 10.0;
     o->band_skip = 1;
+    o->mdf_mean = DSPS_MDF_MEAN_LINEAR;
+    o->mdf_terf_x0 = 9.0;
+    o->mdf_terf_h = 0.5;
 }
+
+namespace {
+// Appendix B, Eq. (terf): the triweight cumulative kernel, 0 below -3 and 1
+// above 3.
+double terf_host(double z) {
+    if (z <= -3.0) return 0.0;
+    if (z >= 3.0) return 1.0;
+    const double z2 = z * z;
+    return 0.5 + z * (35.0 / 96.0 + z2 * (-35.0 / 864.0 + z2 * (7.0 / 2592.0 - z2 * 5.0 / 69984.0)));
+}
+}  // namespace
 
 const char *dsps_last_error_message(void) { return g_last_error.c_str(); }
 
@@ -203,8 +217,11 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
         if (std::fabs(g->lam[n] / expect - 1.0) > 1e-9)
             return fail(DSPS_ERR_UNSUPPORTED, "dsps_create: wavelength grid is not uniform in ln(lambda)%s");
     }
-    if (opts.sfh_model < 0 || opts.sfh_model > 1 || opts.mdf_kernel < 0 || opts.mdf_kernel > 1)
+    if (opts.sfh_model < 0 || opts.sfh_model > 1 || opts.mdf_kernel < 0 || opts.mdf_kernel > 1 ||
+        opts.mdf_mean < 0 || opts.mdf_mean > 1)
         return fail(DSPS_ERR_INVALID_ARG, "dsps_create: unknown model switch%s");
+    if (opts.mdf_mean == DSPS_MDF_MEAN_TERF && !(opts.mdf_terf_h > 0 && std::isfinite(opts.mdf_terf_x0)))
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_create: bad MDF transition%s");
     if (!(opts.z_max > 0) || opts.z_max > 50 || !(opts.om0 > 0) || !(opts.h > 0))
         return fail(DSPS_ERR_INVALID_ARG, "dsps_create: bad cosmology options%s");
     if (opts.max_chunk < 128) opts.max_chunk = 128;
@@ -239,7 +256,17 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     c->lnlam0 = std::log(g->lam[0]);
     c->dlnlam = dl;
     c->chunk = (opts.max_chunk + 127) / 128 * 128;
-    c->sort_xmid = (float)(0.5 * (g->log_age_yr[0] + g->log_age_yr[g->n_age - 1]) - 9.0);
+    {
+        const double xmid = 0.5 * (g->log_age_yr[0] + g->log_age_yr[g->n_age - 1]);
+        if (opts.mdf_mean == DSPS_MDF_MEAN_TERF) {
+            const double T = terf_host((xmid - opts.mdf_terf_x0) / opts.mdf_terf_h);
+            c->sort_mua = (float)(1.0 - T);
+            c->sort_mub = (float)T;
+        } else {
+            c->sort_mua = 1.f;
+            c->sort_mub = (float)(xmid - 9.0);
+        }
+    }
     c->sort_mu_lo = (float)g->lgz[0];
     c->sort_mu_scale = g->n_z > 1 ? (float)(ZSORT_MUBINS / (g->lgz[g->n_z - 1] - g->lgz[0])) : 0.f;
 
@@ -250,6 +277,8 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_Lt_lo, (size_t)c->KZ_pad * c->N_pad));
     chk(dmalloc(&c->d_wmul, (size_t)c->KZ_pad));
     chk(dmalloc(&c->d_logage, (size_t)c->n_age));
+    chk(dmalloc(&c->d_mua, (size_t)c->n_age));
+    chk(dmalloc(&c->d_mub, (size_t)c->n_age));
     chk(dmalloc(&c->d_edges, (size_t)c->n_age + 1));
     chk(dmalloc(&c->d_einh, (size_t)c->n_age + 1));
     chk(dmalloc(&c->d_bwidth, (size_t)c->n_age));
@@ -275,8 +304,19 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     std::vector<float> einh(c->n_age + 1), bwidth(c->n_age);
     for (int i = 0; i <= c->n_age; ++i) einh[i] = (float)(edges[i] / hstep);
     for (int i = 0; i < c->n_age; ++i) bwidth[i] = (float)(edges[i + 1] - edges[i]);
-    std::vector<float> logage(c->n_age);
+    std::vector<float> logage(c->n_age), mua(c->n_age), mub(c->n_age);
     for (int i = 0; i < c->n_age; ++i) logage[i] = (float)g->log_age_yr[i];
+    // MDF mean of age bin i: mu_i = mua_i p5 + mub_i p7 (dsps.h: DSPS_MDF_MEAN_*)
+    for (int i = 0; i < c->n_age; ++i) {
+        if (opts.mdf_mean == DSPS_MDF_MEAN_TERF) {
+            const double T = terf_host((g->log_age_yr[i] - opts.mdf_terf_x0) / opts.mdf_terf_h);
+            mua[i] = (float)(1.0 - T);
+            mub[i] = (float)T;
+        } else {
+            mua[i] = 1.f;
+            mub[i] = logage[i] - 9.f;   // the FP32 log age less the 1 Gyr pivot
+        }
+    }
     // lgZ bin edges: midpoints, outer edges at -/+ infinity (Sec. 3.2).
     std::vector<float> zedge(c->n_z + 1);
     zedge[0] = -1e30f;
@@ -296,6 +336,8 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     up(c->d_einh, einh.data(), einh.size() * sizeof(float));
     up(c->d_bwidth, bwidth.data(), bwidth.size() * sizeof(float));
     up(c->d_logage, logage.data(), logage.size() * sizeof(float));
+    up(c->d_mua, mua.data(), mua.size() * sizeof(float));
+    up(c->d_mub, mub.data(), mub.size() * sizeof(float));
     up(c->d_zedge, zedge.data(), zedge.size() * sizeof(float));
     up(c->d_tlut, tl.data(), tl.size() * sizeof(double));
     std::vector<float> glf(gl.begin(), gl.end());

@@ -120,9 +120,9 @@ struct Ctx {
     double t0 = 0, t1 = 0;
     double lnlam0 = 0, dlnlam = 0;
     int num_sms = 0;
-    // Sort key of the tensor-core path: mean metallicity at the middle log age,
-    // mu + slope * sort_xmid, binned from sort_mu_lo at sort_mu_scale bins per dex.
-    float sort_mu_lo = 0.f, sort_mu_scale = 0.f, sort_xmid = 0.f;
+    // Sort key of the tensor-core path: the MDF mean at the middle log age,
+    // sort_mua p5 + sort_mub p7, binned from sort_mu_lo at sort_mu_scale bins per dex.
+    float sort_mu_lo = 0.f, sort_mu_scale = 0.f, sort_mua = 1.f, sort_mub = 0.f;
 
     // Resident SSP copies.
     float *d_L32 = nullptr;                 // [K_pad][N_pad] fp32 (SIMT path)
@@ -132,6 +132,7 @@ struct Ctx {
 
     // Grids and tables.
     float *d_logage = nullptr;              // [n_age] log10(age/yr)
+    float *d_mua = nullptr, *d_mub = nullptr;   // [n_age] MDF mean of bin i: mua_i p5 + mub_i p7
     double *d_edges = nullptr;              // [n_age+1] age-bin edges [Gyr]
     float *d_einh = nullptr;                // [n_age+1] edge / time step
     float *d_bwidth = nullptr;              // [n_age] bin widths [Gyr]

@@ -33,6 +33,7 @@ struct WArgs {
     float zmax_f;          // largest float <= zmax (z <= zmax_f iff (double)z <= zmax)
     float t0_f, h_f, dlnlam_f;   // FP32 copies used by the per-galaxy warps
     const float *logage;
+    const float *mua, *mub;   // [n_age] MDF mean of bin i: mua_i p5 + mub_i p7 (dsps.h: DSPS_MDF_MEAN_*)
     const float *einh;     // [n_age+1] age-bin edge / h
     const float *bwidth;   // [n_age] e_{i+1} - e_i [Gyr]
     const float *zedge;
@@ -255,6 +256,13 @@ __global__ void galaxy_prep_kernel(WArgs a, GalPrep *out) {
     out[gl] = r;
 }
 
+// Sec. 3.2, Eq. agedep_mdf: mean lgZ of the MDF for age bin i, mua_i p5 +
+// mub_i p7 (linear in log age, or the T_erf transition from mu_young to
+// mu_old; the per-age coefficients are tabulated per context).
+__device__ __forceinline__ float mdf_mean_at(const WArgs &a, const float *p, int i) {
+    return fmaf(p[7], __ldg(a.mub + i), __ldg(a.mua + i) * p[5]);
+}
+
 template <int MODE, int SFH, int MDF>
 __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -313,7 +321,7 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int i = 4 * gq + c;
-                mu4[c] = valid ? fmaf(p[7], __ldg(a.logage + min(i, a.n_age - 1)) - 9.f, p[5]) : 0.f;
+                mu4[c] = valid ? mdf_mean_at(a, p, min(i, a.n_age - 1)) : 0.f;
                 fr4[c] = valid && i < a.n_age ? frac[i] : 0.f;
                 ulo[c] = -1e30f;
                 slo[c] = 0.f;
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
         for (; k < kend; k += 128) {
             float om[4];
             int i = i0, j = j0;
-            float mu_i = fmaf(p[7], __ldg(a.logage + min(i, a.n_age - 1)) - 9.f, p[5]);
+            float mu_i = mdf_mean_at(a, p, min(i, a.n_age - 1));
             float u_lo = (__ldg(a.zedge + j) - mu_i) * inv_sig;
             float s_lo = j == 0 ? 0.f : mdf_s<MDF>(u_lo);
 #pragma unroll
@@ -422,7 +430,7 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
                 if (++j == nz) {   // next age row: its lower edge is -inf
                     j = 0;
                     ++i;
-                    mu_i = fmaf(p[7], __ldg(a.logage + min(i, a.n_age - 1)) - 9.f, p[5]);
+                    mu_i = mdf_mean_at(a, p, min(i, a.n_age - 1));
                     u_lo = -1e30f;
                     s_lo = 0.f;
                 }
@@ -535,7 +543,8 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     //   dLoss/dfrac_i = sum_e dw_(i,e) P(Z >= edge e | i)
     //   dLoss/dmu_i   = frac_i / sigma sum_{e>=1} dw_(i,e) pdf(u_e)
     //   dLoss/dsigma  = sum_i frac_i / sigma sum_{e>=1} dw_(i,e) pdf(u_e) u_e
-    // (the MDF bin probabilities are CDF differences, Sec. 3.2 / Appendix B).
+    // (the MDF bin probabilities are CDF differences, Sec. 3.2 / Appendix B),
+    // and dLoss/dp5, dLoss/dp7 = sum_i dLoss/dmu_i (mua_i, mub_i).
     const float inv_sig = 1.f / sig;
     const int nz = a.n_z;
     float mu_bar = 0.f, sig_bar = 0.f, slope_bar = 0.f;
@@ -548,12 +557,13 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     constexpr bool tri = MDF == DSPS_MDF_TRIWEIGHT;
     const float *wrow = what + gi * a.KZ_pad;
     for (int gq = lane; 4 * gq < a.A_pad && valid; gq += 32) {
-        float mu4[4], xl4[4], fr4[4], fb4[4];
+        float mu4[4], xl4[4], xa4[4], fr4[4], fb4[4];   // xa4, xl4: d mu_i / d p5, d p7
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int i = 4 * gq + c;
-            xl4[c] = __ldg(a.logage + min(i, a.n_age - 1)) - 9.f;
-            mu4[c] = fmaf(p[7], xl4[c], p[5]);
+            xa4[c] = __ldg(a.mua + min(i, a.n_age - 1));
+            xl4[c] = __ldg(a.mub + min(i, a.n_age - 1));
+            mu4[c] = fmaf(p[7], xl4[c], xa4[c] * p[5]);
             fr4[c] = i < a.n_age ? frac[i] : 0.f;
             fb4[c] = 0.f;
         }
@@ -585,7 +595,7 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
                 const float sv = mdf_s<MDF>(u[c]);
                 fb4[c] = fmaf(dw[c], u[c] > 0.f ? -sv : 1.f - sv, fb4[c]);
                 const float t = fr4[c] * dw[c] * mdf_pdf<MDF>(u[c]) * inv_sig;
-                mu_bar += t;
+                mu_bar = fmaf(t, xa4[c], mu_bar);
                 sig_bar = fmaf(t, u[c], sig_bar);
                 slope_bar = fmaf(t, xl4[c], slope_bar);
             }
@@ -705,6 +715,8 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.h_f = (float)a.h;
     a.dlnlam_f = (float)a.dlnlam;
     a.logage = c.d_logage;
+    a.mua = c.d_mua;
+    a.mub = c.d_mub;
     a.einh = c.d_einh;
     a.bwidth = c.d_bwidth;
     a.zedge = c.d_zedge;

@@ -26,14 +26,15 @@ namespace {
 struct SortKey {
     const float *z, *mu, *slope;   // parameter rows 11, 5, 7 of the chunk
     float inv_dlnlam, zscale;      // s = log1p(z) * inv_dlnlam; z bin = floor(s * zscale)
-    float mu_lo, mu_scale, xmid;   // mu bin = floor((mu + slope * xmid - mu_lo) * mu_scale)
+    float mu_lo, mu_scale;         // mu bin = floor((mua p5 + mub p7 - mu_lo) * mu_scale)
+    float mua, mub;                // MDF mean at the middle log age
 };
 
 __device__ __forceinline__ int sort_key(const SortKey &k, int64_t i) {
     const float z = k.z[i];
     int zb = 0;
     if (z > 0.f && isfinite(z)) zb = min(max((int)(log1pf(z) * k.inv_dlnlam * k.zscale), 0), ZSORT_ZBINS - 1);
-    const float m = fmaf(k.slope[i], k.xmid, k.mu[i]);
+    const float m = fmaf(k.slope[i], k.mub, k.mua * k.mu[i]);
     int mb = 0;
     if (isfinite(m)) mb = (int)fminf(fmaxf((m - k.mu_lo) * k.mu_scale, 0.f), (float)(ZSORT_MUBINS - 1));
     return zb * ZSORT_MUBINS + mb;
@@ -159,7 +160,8 @@ cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *params, 
     k.zscale = (float)(ZSORT_ZBINS / (std::log1p(c.opts.z_max) / c.dlnlam + 1.0));
     k.mu_lo = c.sort_mu_lo;
     k.mu_scale = c.sort_mu_scale;
-    k.xmid = c.sort_xmid;
+    k.mua = c.sort_mua;
+    k.mub = c.sort_mub;
     const int n_tiles = (int)((n + 127) / 128);
     cudaError_t e = cudaMemsetAsync(w.hist, 0, ZSORT_BUCKETS * sizeof(int), s);
     if (e != cudaSuccess) return e;

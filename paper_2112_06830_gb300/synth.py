@@ -173,6 +173,24 @@ def make_population(sfh_model: int, n: int, seed: int, start: int = 0) -> np.nda
     return np.ascontiguousarray(allp[:, off:off + n])
 
 
+def with_terf_mdf(params: np.ndarray, seed: int, start: int = 0) -> np.ndarray:
+    """The same galaxies with the paper's age-dependent MDF in its T_erf form:
+    row 5 becomes mu_young ~ U[-0.5, 0.4] and row 7 mu_old ~ U[-1.6, -0.4]
+    (old stars metal-poor), galaxy i's draw depending only on (seed, i)."""
+    p = np.array(params, dtype=np.float64, copy=True)
+    n = p.shape[1]
+    if n == 0:
+        return p
+    b0, b1 = start // _BLOCK, (start + n - 1) // _BLOCK
+    draws = []
+    for b in range(b0, b1 + 1):
+        rng = np.random.default_rng([seed, b, 7])
+        draws.append(np.stack([rng.uniform(-0.5, 0.4, _BLOCK), rng.uniform(-1.6, -0.4, _BLOCK)]))
+    d = np.concatenate(draws, axis=1)[:, start - b0 * _BLOCK:start - b0 * _BLOCK + n]
+    p[5], p[7] = d[0], d[1]
+    return p
+
+
 def workload_inputs(name: str, n_gal: int | None = None, start: int = 0):
     """(grid, filters, params) for a named workload."""
     w = WORKLOADS[name]
