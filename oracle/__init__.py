@@ -49,7 +49,8 @@ class _Grid(C.Structure):
                 ("t0", C.c_double), ("t1", C.c_double), ("n_t", C.c_int),
                 ("om0", C.c_double), ("w0", C.c_double), ("h", C.c_double),
                 ("sfh_model", C.c_int), ("mdf_kernel", C.c_int),
-                ("mdf_mean", C.c_int), ("mdf_x0", C.c_double), ("mdf_h", C.c_double)]
+                ("mdf_mean", C.c_int), ("mdf_x0", C.c_double), ("mdf_h", C.c_double),
+                ("dust_bump", C.c_int)]
 
 
 class _Filters(C.Structure):
@@ -80,6 +81,10 @@ def _load():
             lib.orc_mdf_mean.argtypes = [C.POINTER(_Grid), dp, C.c_int, dp, dp]
             lib.orc_dust_trans.restype = C.c_double
             lib.orc_dust_trans.argtypes = [C.c_double] * 3
+            lib.orc_drude.restype = C.c_double
+            lib.orc_drude.argtypes = [C.c_double]
+            lib.orc_dust_curve.restype = C.c_double
+            lib.orc_dust_curve.argtypes = [C.POINTER(_Grid), C.c_double, C.c_double, dp]
             lib.orc_filter_trans.restype = C.c_double
             lib.orc_filter_trans.argtypes = [dp, dp, C.c_int, C.c_double]
             lib.orc_filter_norm.restype = C.c_double
@@ -107,7 +112,8 @@ class Grid:
     """SSP grid + SFR time grid + cosmology + model switches, held as float64."""
 
     def __init__(self, log_age_yr, lgz, lam, l_ssp, t0=0.05, t1=13.8, n_t=200,
-                 om0=0.3, w0=-1.0, h=0.7, sfh_model=0, mdf_kernel=0, mdf_mean=0, mdf_x0=9.0, mdf_h=0.5):
+                 om0=0.3, w0=-1.0, h=0.7, sfh_model=0, mdf_kernel=0, mdf_mean=0, mdf_x0=9.0, mdf_h=0.5,
+                 dust_bump=0):
         self.log_age_yr = _f64(log_age_yr)
         self.lgz = _f64(lgz)
         self.lam = _f64(lam)
@@ -116,10 +122,11 @@ class Grid:
         self.om0, self.w0, self.h = float(om0), float(w0), float(h)
         self.sfh_model, self.mdf_kernel = int(sfh_model), int(mdf_kernel)
         self.mdf_mean, self.mdf_x0, self.mdf_h = int(mdf_mean), float(mdf_x0), float(mdf_h)
+        self.dust_bump = int(dust_bump)
         self._c = _Grid(len(self.log_age_yr), len(self.lgz), len(self.lam), _dp(self.log_age_yr),
                         _dp(self.lgz), _dp(self.lam), _dp(self.l_ssp), self.t0, self.t1, self.n_t,
                         self.om0, self.w0, self.h, self.sfh_model, self.mdf_kernel,
-                        self.mdf_mean, self.mdf_x0, self.mdf_h)
+                        self.mdf_mean, self.mdf_x0, self.mdf_h, self.dust_bump)
 
     @property
     def n_age(self):
@@ -222,6 +229,17 @@ def mdf(grid: Grid, mu_i, sigma):
     P, dmu, dsig = np.zeros(grid.n_z), np.zeros(grid.n_z), np.zeros(grid.n_z)
     _load().orc_mdf(C.byref(grid._c), float(mu_i), float(sigma), _dp(P), _dp(dmu), _dp(dsig))
     return P, dmu, dsig
+
+
+def drude(lam):
+    return _load().orc_drude(float(lam))
+
+
+def dust_curve(grid: Grid, lam, delta):
+    """(A_lambda / Av, its derivative in delta) under the grid's dust options."""
+    d = np.zeros(1)
+    c = _load().orc_dust_curve(C.byref(grid._c), float(lam), float(delta), _dp(d))
+    return c, float(d[0])
 
 
 def dust_trans(lam, Av, delta):

@@ -53,6 +53,7 @@ typedef struct {
     int mdf_kernel;            /* 0 triweight, 1 Gaussian                  */
     int mdf_mean;              /* 0 linear in log age, 1 T_erf transition  */
     double mdf_x0, mdf_h;      /* transition centre [log10 yr] and width   */
+    int dust_bump;             /* 1: add the 2175 A Drude bump (Eq. uvbump) */
 } orc_grid;
 
 typedef struct {
@@ -317,6 +318,33 @@ double orc_dust_trans(double lam, double Av, double delta)
     return pow(10.0, -0.4 * Av * pow(lam / ORC_LAMV, -0.7 + delta));
 }
 
+/* Eq. (uvbump): the UV bump as a Drude profile of unit amplitude,
+ * D0 = (lam dlam)^2 / ((lam^2 - lam_b^2)^2 + (lam dlam)^2), lam_b = 2175 A,
+ * dlam = 350 A. */
+double orc_drude(double lam)
+{
+    const double lb = 2175.0, dl = 350.0;
+    double x = lam * dl, d = lam * lam - lb * lb;
+    return x * x / (d * d + x * x);
+}
+
+/* Attenuation curve A_lambda / Av.  Without the bump, the power law above;
+ * with it, Eq. (salim)'s k_lambda / 4.05 = k0 (lam/lam_V)^delta / 4.05 +
+ * D_lambda / 4.05 with the power law standing for k0 (lam/lam_V)^delta / 4.05
+ * and the bump amplitude E_b = 0.85 - 1.9 delta (Kriek & Conroy, as in the
+ * paper).  *dd: d(A_lambda / Av) / d delta. */
+double orc_dust_curve(const orc_grid *g, double lam, double delta, double *dd)
+{
+    double u = pow(lam / ORC_LAMV, -0.7 + delta), c = u, dc = u * log(lam / ORC_LAMV);
+    if (g->dust_bump) {
+        double D0 = orc_drude(lam);
+        c += (0.85 - 1.9 * delta) * D0 / 4.05;
+        dc += -1.9 * D0 / 4.05;
+    }
+    if (dd) *dd = dc;
+    return c;
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 2.2: filters                                                   */
 /* ------------------------------------------------------------------ */
@@ -388,7 +416,7 @@ void orc_mags_from_weights(const orc_grid *g, const orc_filters *f, const double
         for (int n = 0; n < N; ++n) {
             double T = orc_filter_trans(fl, ft, np, (1.0 + z) * g->lam[n]);
             if (T == 0.0) continue;
-            double F = orc_dust_trans(g->lam[n], Av, delta);
+            double F = pow(10.0, -0.4 * Av * orc_dust_curve(g, g->lam[n], delta, NULL));
             Nq += trap_w(g->lam, N, n) / g->lam[n] * T * F * S[n];
         }
         double Dq = orc_filter_norm(fl, ft, np);
@@ -449,9 +477,9 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
         const double *L = g->l_ssp + (size_t)k * N;
         for (int n = 0; n < N; ++n) S[n] += w * L[n];
     }
-    double *F = malloc(sizeof(double) * N), *u = malloc(sizeof(double) * N);
+    double *F = malloc(sizeof(double) * N), *u = malloc(sizeof(double) * N), *du = malloc(sizeof(double) * N);
     for (int n = 0; n < N; ++n) {
-        u[n] = pow(g->lam[n] / ORC_LAMV, -0.7 + delta);
+        u[n] = orc_dust_curve(g, g->lam[n], delta, du + n);   /* A_lambda / Av and its delta derivative */
         F[n] = pow(10.0, -0.4 * Av * u[n]);
     }
     int *off = malloc(sizeof(int) * (Q + 1));
@@ -485,7 +513,7 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
         Sbar[n] = c * sT * F[n];
         double Fbar = c * sT * S[n];
         double dF_dAv = F[n] * (-0.4 * log(10.0)) * u[n];
-        double dF_ddelta = F[n] * (-0.4 * log(10.0)) * Av * u[n] * log(g->lam[n] / ORC_LAMV);
+        double dF_ddelta = F[n] * (-0.4 * log(10.0)) * Av * du[n];
         pbar[8] += Fbar * dF_dAv;
         pbar[9] += Fbar * dF_ddelta;
     }
@@ -519,7 +547,7 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
         for (int k = 0; k < 5; ++k) pbar[k] += sfrbar[n] * dsfr[5 * n + k];
 
     free(sfrbar); free(coef); free(Mbar); free(fracbar); free(Sbar); free(Nbar);
-    free(Nq); free(T); free(off); free(u); free(F); free(S); free(dPsig); free(dPmu); free(P);
+    free(Nq); free(T); free(off); free(du); free(u); free(F); free(S); free(dPsig); free(dPmu); free(P);
     free(dmu7); free(dmu5); free(frac); free(Mhi); free(e); free(dsfr); free(sfr);
 }
 

@@ -336,7 +336,7 @@ def test_logm_shifts_all_bands():
 # ---------------------------------------------------------------- brute force
 
 def _brute_force_mags(log_age, lgz, lam, L, filters, par, sfh_model, kernel, om0=0.3, h=0.7, mean=0,
-                      x0=9.0, hw=0.5):
+                      x0=9.0, hw=0.5, bump=0):
     """Independent restatement on a tiny grid: scipy quadrature of the SFR
     function itself for every age bin, quadrature of the MDF density for every
     lgZ bin, scipy quadrature for the cosmology, and an explicit loop for the
@@ -377,15 +377,20 @@ def _brute_force_mags(log_age, lgz, lam, L, filters, par, sfh_model, kernel, om0
         for n in range(len(lam)):
             w = 0.5 * ((lam[min(n + 1, len(lam) - 1)] - lam[max(n - 1, 0)]))
             T = np.interp((1 + z) * lam[n], fl, ft, left=0.0, right=0.0)
-            F = 10 ** (-0.4 * par[8] * (lam[n] / 5500.0) ** (-0.7 + par[9]))
+            A = (lam[n] / 5500.0) ** (-0.7 + par[9])
+            if bump:   # Drude profile at 2175 A, width 350 A, amplitude 0.85 - 1.9 delta, over 4.05
+                x = lam[n] * 350.0
+                A += (0.85 - 1.9 * par[9]) * x * x / ((lam[n] ** 2 - 2175.0 ** 2) ** 2 + x * x) / 4.05
+            F = 10 ** (-0.4 * par[8] * A)
             tot += w / lam[n] * T * F * S[n]
         D = np.trapezoid(ft / fl, fl)
         out.append(-2.5 * math.log10(10 ** par[10] * tot / (oracle.AB0 * D)) + dmod - 2.5 * math.log10(1 + z))
     return np.array(out)
 
 
-@pytest.mark.parametrize("sfh_model,kernel,mean", [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 0, 1)])
-def test_brute_force_tiny_grid(sfh_model, kernel, mean):
+@pytest.mark.parametrize("sfh_model,kernel,mean,bump", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 1, 0, 0), (1, 0, 1, 0),
+                                                        (1, 0, 0, 1)])
+def test_brute_force_tiny_grid(sfh_model, kernel, mean, bump):
     log_age = np.array([6.0, 7.5, 8.7, 9.6])
     lgz = np.array([-1.0, -0.4, 0.1])
     lam = np.geomspace(2000.0, 9000.0, 16)
@@ -393,8 +398,10 @@ def test_brute_force_tiny_grid(sfh_model, kernel, mean):
     L = rng.uniform(0.5e-15, 2e-15, (4, 3, 16))
     filters = [synth.gaussian_filter(c, fwhm=600.0, step=5.0) for c in (4000.0, 6500.0)]
     n_t = 40001  # fine time grid: the piecewise-linear reading is then within 1e-7 of the quadrature
+    if bump:
+        lam = np.geomspace(1500.0, 9000.0, 16)      # across the 2175 A bump
     g = oracle.Grid(log_age, lgz, lam, L, n_t=n_t, sfh_model=sfh_model, mdf_kernel=kernel, mdf_mean=mean,
-                    mdf_x0=8.0, mdf_h=0.6)
+                    mdf_x0=8.0, mdf_h=0.6, dust_bump=bump)
     F = oracle.Filters(filters)
     p = synth.make_population(sfh_model, 3, 5)
     p[6] = 0.35
@@ -404,17 +411,19 @@ def test_brute_force_tiny_grid(sfh_model, kernel, mean):
     m = oracle.mags(g, F, p)
     for gi in range(p.shape[1]):
         ref = _brute_force_mags(log_age, lgz, lam, L, filters, p[:, gi], sfh_model, kernel, mean=mean, x0=8.0,
-                                hw=0.6)
+                                hw=0.6, bump=bump)
         np.testing.assert_allclose(m[gi], ref, atol=2e-6)
 
 
 # ---------------------------------------------------------------- gradients
 
-@pytest.mark.parametrize("wl,model,kernel,mean", [("small", 0, 0, 0), ("small", 1, 0, 0), ("small", 1, 1, 0),
-                                                   ("small", 1, 0, 1)])
-def test_adjoint_matches_central_differences(wl, model, kernel, mean):
+@pytest.mark.parametrize("wl,model,kernel,mean,bump", [("small", 0, 0, 0, 0), ("small", 1, 0, 0, 0),
+                                                        ("small", 1, 1, 0, 0), ("small", 1, 0, 1, 0),
+                                                        ("small", 1, 0, 0, 1)])
+def test_adjoint_matches_central_differences(wl, model, kernel, mean, bump):
     g, f, _ = synth.workload_inputs(wl, n_gal=1)
-    G = oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, sfh_model=model, mdf_kernel=kernel, mdf_mean=mean)
+    G = oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, sfh_model=model, mdf_kernel=kernel, mdf_mean=mean,
+                    dust_bump=bump)
     F = oracle.Filters(f)
     p = synth.make_population(model, 3, 21)
     if mean == 1:
@@ -509,3 +518,39 @@ def test_terf_mean_with_equal_values_is_the_uncorrelated_mdf():
     pt[7] = pt[5]
     pl[7] = 0.0
     np.testing.assert_allclose(oracle.weights(Gt, pt), oracle.weights(Gl, pl), rtol=1e-9, atol=0)
+
+
+# ---------------------------------------------------------------- UV bump (Eq. uvbump)
+
+def test_drude_peak_and_half_maximum():
+    """The Drude profile peaks at 1 (unit amplitude) at 2175 A and falls to
+    one half where |lam^2 - lam_b^2| = lam dlam, lam = (+-350 + sqrt(350^2 +
+    4 2175^2)) / 2."""
+    assert oracle.drude(2175.0) == 1.0
+    for sgn in (-1.0, 1.0):
+        lam = 0.5 * (sgn * 350.0 + math.sqrt(350.0 ** 2 + 4 * 2175.0 ** 2))
+        assert oracle.drude(lam) == pytest.approx(0.5, abs=1e-13)
+    assert oracle.drude(1.0e5) < 1e-4 and oracle.drude(1000.0) < 0.05
+
+
+def test_bump_amplitude_vanishes_at_its_zero():
+    """E_b = 0.85 - 1.9 delta: at delta = 0.85/1.9 the bump leaves the curve
+    unchanged; elsewhere it adds E_b D0 / 4.05 (largest at 2175 A)."""
+    lam = np.geomspace(1e3, 1e4, 7)
+    g0 = oracle.Grid([9.0], [0.0], lam, np.ones((1, 1, len(lam))))
+    g1 = oracle.Grid([9.0], [0.0], lam, np.ones((1, 1, len(lam))), dust_bump=1)
+    d0 = 0.85 / 1.9
+    for l in list(lam) + [2175.0]:
+        assert oracle.dust_curve(g1, l, d0)[0] == pytest.approx(oracle.dust_curve(g0, l, d0)[0], abs=1e-15)
+    diff = [oracle.dust_curve(g1, l, -0.2)[0] - oracle.dust_curve(g0, l, -0.2)[0] for l in (1500.0, 2175.0, 3500.0)]
+    assert diff[1] > diff[0] > 0 and diff[1] > diff[2] > 0
+    assert diff[1] == pytest.approx((0.85 + 0.38) / 4.05, rel=1e-14)
+
+
+def test_bump_curve_derivative_matches_differences():
+    lam = np.geomspace(1e3, 1e4, 5)
+    g1 = oracle.Grid([9.0], [0.0], lam, np.ones((1, 1, len(lam))), dust_bump=1)
+    for l in (1200.0, 2175.0, 2600.0, 5500.0):
+        c, dc = oracle.dust_curve(g1, l, -0.1)
+        fd = (oracle.dust_curve(g1, l, -0.1 + 1e-6)[0] - oracle.dust_curve(g1, l, -0.1 - 1e-6)[0]) / 2e-6
+        assert dc == pytest.approx(fd, rel=1e-7, abs=1e-10)
