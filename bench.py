@@ -451,6 +451,22 @@ def run_ours(a):
     ctx_t.close()
     del d_params_t
 
+    # The dust law with the 2175 A UV bump (Drude profile), same galaxies.
+    ctx_b = dsps.Context(ssp, sfh_model=synth.SFH_DPL_QUENCH, device=local, dust_bump=True)
+    sid_b = ctx_b.add_filters(synth.make_filters(N_FILT))
+    for _ in range(a.warmup):
+        ctx_b.photometry(d_params, sid_b, precision=dsps.DSPS_PREC_BF16X3, out=d_mags, stream=stream)
+    barrier()
+    b_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    for e0, e1 in b_evs:
+        flush.fill_(1)
+        e0.record(stream)
+        ctx_b.photometry(d_params, sid_b, precision=dsps.DSPS_PREC_BF16X3, out=d_mags, stream=stream)
+        e1.record(stream)
+    barrier()
+    ms_bump = max_over_ranks(float(np.mean([e0.elapsed_time(e1) for e0, e1 in b_evs])), dist, "cuda")
+    ctx_b.close()
+
     # Precision forms at 1e6 galaxies (same grid and distributions): split-bf16
     # against FP32 throughput, and their per-galaxy magnitude difference.
     precision = None
@@ -550,6 +566,8 @@ def run_ours(a):
         "precision_forms_1e6": precision,
         "mdf_terf": {"value": ws * G * N_FILT / (ms_terf * 1e-3), "ms_per_step": ms_terf,
                      "note": "age-dependent MDF, T_erf transition mu_young -> mu_old (centre 1 Gyr, 0.5 dex)"},
+        "dust_bump": {"value": ws * G * N_FILT / (ms_bump * 1e-3), "ms_per_step": ms_bump,
+                      "note": "attenuation with the 2175 A UV bump (Drude profile)"},
         "serve": serve,
         "clocks": clocks,
     }

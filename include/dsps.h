@@ -138,6 +138,11 @@ typedef struct {
     int32_t mdf_mean;          /* DSPS_MDF_MEAN_*                               */
     double mdf_terf_x0;        /* DSPS_MDF_MEAN_TERF: transition centre x0 and   */
     double mdf_terf_h;         /* width h [dex], h > 0 (defaults 9, 0.5)         */
+    int32_t dust_bump;         /* 1: add the 2175 A UV bump to the attenuation
+                                  curve (Sec. 3.4, Eq. uvbump: Drude profile of
+                                  width 350 A, amplitude E_b = 0.85 - 1.9 delta,
+                                  entering A_lambda as Av E_b D0(lam) / 4.05);
+                                  default 0                                      */
 } dsps_opts;
 
 /* Fills *o with the defaults above (device 0, max_chunk 262144,

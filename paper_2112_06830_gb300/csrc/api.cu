@@ -133,7 +133,7 @@ void free_ctx(Ctx *c) {
         cudaFree(fs.d_tab);
         cudaFree(fs.d_offq);
     }
-    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_edges, c->d_einh, c->d_bwidth,
+    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_edges, c->d_einh, c->d_bwidth,
                     c->d_zedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->d_err, c->d_stats,
                     c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d};
     for (void *p : ptrs) cudaFree(p);
@@ -179,6 +179,7 @@ void dsps_default_opts(dsps_opts *o) {
     o->mdf_mean = DSPS_MDF_MEAN_LINEAR;
     o->mdf_terf_x0 = 9.0;
     o->mdf_terf_h = 0.5;
+    o->dust_bump = 0;
 }
 
 namespace {
@@ -218,7 +219,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
             return fail(DSPS_ERR_UNSUPPORTED, "dsps_create: wavelength grid is not uniform in ln(lambda)%s");
     }
     if (opts.sfh_model < 0 || opts.sfh_model > 1 || opts.mdf_kernel < 0 || opts.mdf_kernel > 1 ||
-        opts.mdf_mean < 0 || opts.mdf_mean > 1)
+        opts.mdf_mean < 0 || opts.mdf_mean > 1 || opts.dust_bump < 0 || opts.dust_bump > 1)
         return fail(DSPS_ERR_INVALID_ARG, "dsps_create: unknown model switch%s");
     if (opts.mdf_mean == DSPS_MDF_MEAN_TERF && !(opts.mdf_terf_h > 0 && std::isfinite(opts.mdf_terf_x0)))
         return fail(DSPS_ERR_INVALID_ARG, "dsps_create: bad MDF transition%s");
@@ -278,6 +279,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_wmul, (size_t)c->KZ_pad));
     chk(dmalloc(&c->d_logage, (size_t)c->n_age));
     chk(dmalloc(&c->d_mua, (size_t)c->n_age));
+    chk(dmalloc(&c->d_bump, (size_t)c->N_pad));
     chk(dmalloc(&c->d_mub, (size_t)c->n_age));
     chk(dmalloc(&c->d_edges, (size_t)c->n_age + 1));
     chk(dmalloc(&c->d_einh, (size_t)c->n_age + 1));
@@ -338,6 +340,13 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     up(c->d_logage, logage.data(), logage.size() * sizeof(float));
     up(c->d_mua, mua.data(), mua.size() * sizeof(float));
     up(c->d_mub, mub.data(), mub.size() * sizeof(float));
+    // Eq. (uvbump): unit Drude profile at the grid's wavelengths
+    std::vector<float> bump(c->N_pad, 0.f);
+    for (int n = 0; n < c->n_lam; ++n) {
+        const double lam = g->lam[n], x = lam * 350.0, d = lam * lam - 2175.0 * 2175.0;
+        bump[n] = (float)(x * x / (d * d + x * x));
+    }
+    up(c->d_bump, bump.data(), bump.size() * sizeof(float));
     up(c->d_zedge, zedge.data(), zedge.size() * sizeof(float));
     up(c->d_tlut, tl.data(), tl.size() * sizeof(double));
     std::vector<float> glf(gl.begin(), gl.end());

@@ -69,6 +69,7 @@ constexpr int KBLOCK = 32;   // kz block of the tensor-core contraction (one TMA
 //   2 s     = ln(1+z) / dlnlam      (observer-frame shift in grid steps)
 //   3 valid (1 or 0)
 //   4 Av, 5 delta  (gradient path)
+//   6 e  = (0.85 - 1.9 delta) / 4.05, 7 de/ddelta = -1.9 / 4.05  (UV bump; 0 without)
 // magoff[g] = -2.5 logM + Dmod(z) - 2.5 log10(1+z)
 
 struct FilterSet {
@@ -133,6 +134,7 @@ struct Ctx {
     // Grids and tables.
     float *d_logage = nullptr;              // [n_age] log10(age/yr)
     float *d_mua = nullptr, *d_mub = nullptr;   // [n_age] MDF mean of bin i: mua_i p5 + mub_i p7
+    float *d_bump = nullptr;                // [N_pad] unit Drude profile at lam_n (Eq. uvbump), 0 past n_lam
     double *d_edges = nullptr;              // [n_age+1] age-bin edges [Gyr]
     float *d_einh = nullptr;                // [n_age+1] edge / time step
     float *d_bwidth = nullptr;              // [n_age] bin widths [Gyr]

@@ -4,7 +4,9 @@
 // For galaxy g and rest-frame wavelength node n with composite luminosity
 // S_gn (Eq. full_mdf, per unit formed mass):
 //   u    = (lam_n / 5500 A)^(delta - 0.7)             power-law attenuation curve
-//   F    = 10^(-0.4 Av u)                              Eq. (attenuation)
+//   c    = u + e D0_n                                  with the UV bump (Eq. uvbump):
+//          D0_n the unit Drude profile at lam_n, e = (0.85 - 1.9 delta) / 4.05
+//   F    = 10^(-0.4 Av c)                              Eq. (attenuation)
 //   v_n  = S_gn F c_n / lam_n                          rest-grid trapezoid of dlam/lam
 //   N_q += v_n T_q((1+z) lam_n)                        Eq. (restmag) in the observer frame
 // The filters are tabulated on the SSP grid's ln-lambda spacing, so the
@@ -29,10 +31,11 @@ struct RowConst {
     float w[4];   // Lagrange weights of grid indices i0-1, i0, i0+1, i0+2
     int i0;
     bool valid;
+    float e, ed;  // UV-bump amplitude / 4.05 and its delta derivative (0 without the bump)
 };
 
 __device__ __forceinline__ RowConst load_row_const(const float *aux, int64_t row, int64_t n_rows) {
-    RowConst rc{0.f, 0.f, {0.f, 1.f, 0.f, 0.f}, 0, false};
+    RowConst rc{0.f, 0.f, {0.f, 1.f, 0.f, 0.f}, 0, false, 0.f, 0.f};
     if (row < n_rows) {
         const float *ax = aux + row * AUX_STRIDE;
         rc.alpha = ax[0];
@@ -46,6 +49,8 @@ __device__ __forceinline__ RowConst load_row_const(const float *aux, int64_t row
         rc.w[2] = -(f + 1.f) * f * (f - 2.f) * 0.5f;
         rc.w[3] = (f + 1.f) * f * (f - 1.f) * (1.f / 6.f);
         rc.valid = ax[3] != 0.f;
+        rc.e = ax[6];
+        rc.ed = ax[7];
     }
     return rc;
 }
@@ -59,7 +64,13 @@ struct ColConst {
     float ell0, dell;          // log2(lam_n / 5500) = ell0 + n dell
     float kap0, kapmid, kapN;  // trapezoid weight / lambda at n = 0, interior, N-1
     int N;
+    const float *bump;         // [N_pad] unit Drude profile D0(lam_n), or nullptr (no UV bump)
 };
+
+// Attenuation curve A_lambda / Av at node n: u, plus the UV bump when on.
+__device__ __forceinline__ float dust_curve(const ColConst &cc, const RowConst &rc, float u, int n) {
+    return cc.bump ? fmaf(rc.e, __ldg(cc.bump + n), u) : u;
+}
 
 // Host: column constants of the context's wavelength grid (phot_simt.cu).
 ColConst make_col_const(const Ctx &c);
@@ -87,7 +98,7 @@ __device__ __forceinline__ void epi_node(float (&acc)[4 * Q4], Slide &sl, float 
                                          const ColConst &cc, const float4 *__restrict__ tab, int m_last) {
     const float ell = fmaf((float)n, cc.dell, cc.ell0);
     const float u = exp2f(rc.beta * ell);
-    const float F = exp2f(rc.alpha * u);
+    const float F = exp2f(rc.alpha * dust_curve(cc, rc, u, n));
     const float v = S * F * col_kappa(cc, n);
     const float y = fmaf(rc.w[0], v, fmaf(rc.w[1], sl.v1, fmaf(rc.w[2], sl.v2, rc.w[3] * sl.v3)));
     sl.v3 = sl.v2;
@@ -106,10 +117,10 @@ __device__ __forceinline__ void epi_close(float (&acc)[4 * Q4], const Slide &sl,
 }
 
 // Gradient mode: besides N_q (acc[0]) the same sliding sums accumulate
-//   A_q = sum_n v_n u_n T_q        (acc[1]),  d N_q / d Av    = -0.4 ln10 A_q
-//   D_q = sum_n v_n u_n l_n T_q    (acc[2]),  d N_q / d delta = -0.4 ln10 Av D_q
-// with l_n = ln(lam_n / 5500 A), since dF/dAv = -0.4 ln10 u F and
-// du/ddelta = u l_n (Sec. 3.4, Eq. attenuation).
+//   A_q = sum_n v_n c_n T_q                    (acc[1]),  d N_q / d Av    = -0.4 ln10 A_q
+//   D_q = sum_n v_n (u_n l_n + e' D0_n) T_q    (acc[2]),  d N_q / d delta = -0.4 ln10 Av D_q
+// with l_n = ln(lam_n / 5500 A) and e' = de/ddelta, since dF/dAv = -0.4 ln10 c F
+// and dc/ddelta = u l_n + e' D0_n (Sec. 3.4, Eqs. attenuation, uvbump).
 template <int Q4>
 __device__ __forceinline__ void acc_row3(float (&acc)[3][4 * Q4], const float4 *__restrict__ tab, int m,
                                          float y0, float y1, float y2) {
@@ -133,9 +144,11 @@ __device__ __forceinline__ void epi_node_grad(float (&acc)[3][4 * Q4], Slide (&s
                                               const float4 *__restrict__ tab, int m_last) {
     const float ell = fmaf((float)n, cc.dell, cc.ell0);
     const float u = exp2f(rc.beta * ell);
-    const float F = exp2f(rc.alpha * u);
+    const float d0 = cc.bump ? __ldg(cc.bump + n) : 0.f;
+    const float cn = fmaf(rc.e, d0, u);
+    const float F = exp2f(rc.alpha * cn);
     const float v = S * F * col_kappa(cc, n);
-    const float vv[3] = {v, v * u, v * u * (ell * 0.69314718055994531f)};
+    const float vv[3] = {v, v * cn, v * fmaf(u, ell * 0.69314718055994531f, rc.ed * d0)};
     float y[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {

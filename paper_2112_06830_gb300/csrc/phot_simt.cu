@@ -173,6 +173,7 @@ ColConst make_col_const(const Ctx &c) {
     cc.kapmid = (float)std::sinh(c.dlnlam);
     cc.kapN = (float)(-0.5 * std::expm1(-c.dlnlam));
     cc.N = c.n_lam;
+    cc.bump = c.opts.dust_bump ? c.d_bump : nullptr;
     return cc;
 }
 

@@ -28,7 +28,7 @@ namespace dsps {
 struct WArgs {
     const float *params;
     int64_t G_stride, g_begin, n;
-    int n_age, n_z, K, K_pad, A_pad, KZ_pad, n_t, sfh_model, mdf_kernel, n_lut;
+    int n_age, n_z, K, K_pad, A_pad, KZ_pad, n_t, sfh_model, mdf_kernel, n_lut, dust_bump;
     double t0, h, inv_h, dz, inv_dz, zmax, dlnlam;
     float zmax_f;          // largest float <= zmax (z <= zmax_f iff (double)z <= zmax)
     float t0_f, h_f, dlnlam_f;   // FP32 copies used by the per-galaxy warps
@@ -459,8 +459,8 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
             ax[3] = valid ? 1.f : 0.f;
             ax[4] = p[8];
             ax[5] = p[9];
-            ax[6] = 0.f;
-            ax[7] = 0.f;
+            ax[6] = a.dust_bump ? (0.85f - 1.9f * p[9]) * (1.f / 4.05f) : 0.f;
+            ax[7] = a.dust_bump ? -1.9f / 4.05f : 0.f;
             a.magoff[gi] = valid ? gp.magoff : __int_as_float(0x7fc00000);
         }
     }
@@ -703,6 +703,7 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.n_t = c.n_t;
     a.sfh_model = c.opts.sfh_model;
     a.mdf_kernel = c.opts.mdf_kernel;
+    a.dust_bump = c.opts.dust_bump;
     a.n_lut = c.n_lut;
     a.t0 = c.t0;
     a.h = (c.t1 - c.t0) / (c.n_t - 1);

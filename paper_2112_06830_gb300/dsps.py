@@ -53,7 +53,7 @@ class dsps_opts(C.Structure):
                 ("sfh_model", C.c_int32), ("mdf_kernel", C.c_int32), ("device", C.c_int32),
                 ("max_chunk", C.c_int64), ("hbm_budget_bytes", C.c_int64), ("n_streams", C.c_int32),
                 ("z_max", C.c_double), ("band_skip", C.c_int32), ("mdf_mean", C.c_int32),
-                ("mdf_terf_x0", C.c_double), ("mdf_terf_h", C.c_double)]
+                ("mdf_terf_x0", C.c_double), ("mdf_terf_h", C.c_double), ("dust_bump", C.c_int32)]
 
 
 DSPS_PROF_KINDS = 4
@@ -240,7 +240,8 @@ class Context:
 
     def __init__(self, ssp, sfh_model=DSPS_SFH_DELAYED_TAU, mdf_kernel=DSPS_MDF_TRIWEIGHT, device=0,
                  max_chunk=None, hbm_budget_bytes=None, n_streams=None, om0=0.3, w0=-1.0, h=0.7, z_max=10.0,
-                 band_skip=True, mdf_mean=DSPS_MDF_MEAN_LINEAR, mdf_terf_x0=None, mdf_terf_h=None):
+                 band_skip=True, mdf_mean=DSPS_MDF_MEAN_LINEAR, mdf_terf_x0=None, mdf_terf_h=None,
+                 dust_bump=False):
         self._keep = [np.ascontiguousarray(ssp.log_age_yr, dtype=np.float64),
                       np.ascontiguousarray(ssp.lgz, dtype=np.float64),
                       np.ascontiguousarray(ssp.lam, dtype=np.float64),
@@ -254,6 +255,7 @@ class Context:
         o.sfh_model, o.mdf_kernel, o.device = sfh_model, mdf_kernel, device
         o.band_skip = 1 if band_skip else 0
         o.mdf_mean = mdf_mean
+        o.dust_bump = 1 if dust_bump else 0
         if mdf_terf_x0 is not None:
             o.mdf_terf_x0 = mdf_terf_x0
         if mdf_terf_h is not None:
