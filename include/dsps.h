@@ -190,6 +190,34 @@ int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32
                         int32_t precision, const float *mag_bar, float *mags,
                         float *param_bar, dsps_stream_t stream);
 
+/* Population statistic of the paper's benchmark (Sec. 5.1): the galaxies whose
+ * colour m[band_a] - m[band_b] exceeds `cut` (the red side of a colour cut),
+ * counted in n_bins uniform bins of m[band_r] over [lo, hi).  Galaxies with a
+ * NaN magnitude, or m[band_r] outside [lo, hi), are not counted.  Binning is in
+ * FP32: bin = min(floor((m_r - lo) * (n_bins / (hi - lo))), n_bins - 1), the
+ * scale rounded once to FP32.  1 <= n_bins <= DSPS_MAX_HIST_BINS; bands index
+ * the filter set. */
+#define DSPS_MAX_HIST_BINS 4096
+typedef struct {
+    int32_t band_a, band_b;    /* colour m[band_a] - m[band_b]                   */
+    float cut;                 /* counted if the colour is > cut                 */
+    int32_t band_r;            /* band of the histogrammed magnitude             */
+    float lo, hi;              /* histogram range, lo < hi                       */
+    int32_t n_bins;
+} dsps_hist_spec;
+
+/* Photometry (as dsps_photometry) followed by the histogram above, fused: the
+ * magnitudes are binned where they are formed and never written.
+ * counts: device uint64 [n_bins], overwritten. */
+int dsps_photometry_histogram(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
+                              int32_t precision, const dsps_hist_spec *spec, uint64_t *counts,
+                              dsps_stream_t stream);
+
+/* The same histogram of magnitudes already on the device: mags device float32
+ * [n_gal][n_filt]; counts device uint64 [n_bins], overwritten. */
+int dsps_histogram(dsps_ctx *ctx, int64_t n_gal, const float *mags, int32_t n_filt,
+                   const dsps_hist_spec *spec, uint64_t *counts, dsps_stream_t stream);
+
 /* FP32 photometry that allocates no device memory, for callers that cannot
  * call cudaMalloc at the time they need magnitudes (for example a worker of a
  * framework whose device memory belongs to its own pooling allocator, or a

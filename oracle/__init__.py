@@ -242,6 +242,17 @@ def dust_curve(grid: Grid, lam, delta):
     return c, float(d[0])
 
 
+def colour_cut_histogram(mags, band_a, band_b, cut, band_r, lo, hi, n_bins):
+    """Sec. 5.1's population statistic: galaxies with colour m_a - m_b > cut,
+    counted in n_bins uniform bins of m_r on [lo, hi) (float64, plain
+    definition; NaN rows and values outside the range are not counted)."""
+    m = np.asarray(mags, dtype=np.float64)
+    sel = (m[:, band_a] - m[:, band_b]) > cut
+    r = m[sel, band_r]
+    r = r[(r >= lo) & (r < hi)]
+    return np.histogram(r, bins=n_bins, range=(lo, hi))[0].astype(np.int64)
+
+
 def dust_trans(lam, Av, delta):
     return _load().orc_dust_trans(float(lam), float(Av), float(delta))
 

@@ -460,6 +460,41 @@ int dsps_photometry(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t s
     return run_photometry(c, n_gal, params, set_id, precision, mags, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int dsps_photometry_histogram(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
+                              const dsps_hist_spec *spec, uint64_t *counts, dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || n_gal < 0 || (n_gal > 0 && !params)) return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry_histogram: bad argument%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (set_id < 0 || set_id >= (int)c->sets.size())
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry_histogram: unknown filter set%s");
+    if (precision != DSPS_PREC_FP32 && precision != DSPS_PREC_BF16X3)
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry_histogram: unknown precision%s");
+    const FilterSet &fs = c->sets[set_id];
+    HistArgs h;
+    const int rc = make_hist_args(spec, fs.Q, reinterpret_cast<unsigned long long *>(counts), &h);
+    if (rc != DSPS_OK) return rc;
+    DSPS_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DSPS_CUDA(cudaMemsetAsync(counts, 0, (size_t)h.n_bins * sizeof(uint64_t), s));
+    if (n_gal == 0) return DSPS_OK;
+    return run_photometry_ws(c, c->ws, n_gal, params, fs, precision, nullptr, s, true, &h);
+}
+
+int dsps_histogram(dsps_ctx *ctx, int64_t n_gal, const float *mags, int32_t n_filt, const dsps_hist_spec *spec,
+                   uint64_t *counts, dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || n_gal < 0 || (n_gal > 0 && !mags) || n_filt < 1 || n_filt > DSPS_MAX_FILTERS)
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_histogram: bad argument%s");
+    HistArgs h;
+    const int rc = make_hist_args(spec, n_filt, reinterpret_cast<unsigned long long *>(counts), &h);
+    if (rc != DSPS_OK) return rc;
+    DSPS_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DSPS_CUDA(cudaMemsetAsync(counts, 0, (size_t)h.n_bins * sizeof(uint64_t), s));
+    DSPS_CUDA(launch_histogram(mags, n_gal, n_filt, h, s));
+    return DSPS_OK;
+}
+
 int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
                         const float *mag_bar, float *mags, float *param_bar, dsps_stream_t stream) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);

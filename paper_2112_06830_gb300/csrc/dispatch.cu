@@ -53,7 +53,7 @@ Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint) 
 }
 
 int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *params, const FilterSet &fs,
-                      int32_t precision, float *mags, cudaStream_t s, bool profile) {
+                      int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist) {
     Workspace w = w0;
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;
@@ -66,8 +66,11 @@ int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *p
                 e = launch_weights(*c, w, W_OMEGA_F32, params, n_gal, g0, n, nullptr, s);
             }
             if (e == cudaSuccess) {
+                // with a histogram, the chunk's magnitudes go to the (otherwise
+                // unused) [cap][16] scratch and are binned from there
                 ProfScope ps(*c, 1, s, prof);
-                e = launch_phot_simt(*c, w, fs, n, mags + g0 * fs.Q, s);
+                e = launch_phot_simt(*c, w, fs, n, hist ? w.cq : mags + g0 * fs.Q, s);
+                if (e == cudaSuccess && hist) e = launch_histogram(w.cq, n, fs.Q, *hist, s);
             }
         } else {
             int parts = 0;
@@ -82,7 +85,7 @@ int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *p
             }
             if (e == cudaSuccess) {
                 ProfScope ps(*c, 0, s, prof);
-                e = launch_combine(*c, w, fs, n, parts, mags + g0 * fs.Q, s);
+                e = launch_combine(*c, w, fs, n, parts, hist ? nullptr : mags + g0 * fs.Q, s, hist);
             }
         }
         if (e != cudaSuccess) {

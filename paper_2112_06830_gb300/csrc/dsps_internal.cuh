@@ -82,6 +82,14 @@ struct FilterSet {
 
 struct Serve;  // request loop (serve.cu)
 
+// Colour-cut histogram of the magnitudes (dsps.h: dsps_hist_spec), as used by
+// the kernels; counts == nullptr disables it.
+struct HistArgs {
+    int band_a = 0, band_b = 0, band_r = 0, n_bins = 0;
+    float cut = 0.f, lo = 0.f, hi = 0.f, scale = 0.f;   // scale = n_bins / (hi - lo) in FP32
+    unsigned long long *counts = nullptr;
+};
+
 // Per-galaxy scalars of the cosmology (weights.cu: galaxy_prep_kernel).
 struct GalPrep {
     int m_obs;       // interval of the SFR time grid holding t_obs(z); -1 if z is out of range
@@ -217,9 +225,13 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
 // mean metallicity); also resets w.trange and w.kmask.
 cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride, int64_t g_begin,
                          int64_t n, cudaStream_t s);
-// Sums the tensor-core kernel's per-part filter sums and writes magnitudes.
+// Sums the tensor-core kernel's per-part filter sums and writes magnitudes
+// (mags may be nullptr), or bins them into hist->counts.
 cudaError_t launch_combine(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts, float *mags,
-                           cudaStream_t s);
+                           cudaStream_t s, const HistArgs *hist = nullptr);
+// Colour-cut histogram of device magnitudes [n][Q] (histogram.cu).
+cudaError_t launch_histogram(const float *mags, int64_t n, int Q, const HistArgs &h, cudaStream_t s);
+int make_hist_args(const dsps_hist_spec *spec, int n_filt, unsigned long long *counts, HistArgs *out);
 
 // grad: instead of magnitudes, writes the sums N, A, D per filter (see
 // epilogue.cuh) to ctx.d_partial as a single part.
@@ -248,7 +260,7 @@ cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *pa
 // Whole photometry / adjoint of a population on one stream with one work space
 // (dispatch.cu); mags/param_bar are the caller's device pointers.
 int run_photometry_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
-                      int32_t precision, float *mags, cudaStream_t s, bool profile);
+                      int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist = nullptr);
 int run_photometry_vjp_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
                           int32_t precision, const float *mag_bar, float *mags, float *param_bar, cudaStream_t s,
                           bool profile);

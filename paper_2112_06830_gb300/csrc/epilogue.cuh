@@ -209,6 +209,15 @@ __device__ __forceinline__ float ab_mag(float flux, float magoff, float offq) {
     return -2.5f * log10f(flux) + (magoff + offq);
 }
 
+// The benchmark's colour cut and magnitude bin (dsps.h: dsps_hist_spec), in
+// FP32; NaN magnitudes fail every comparison and are not counted.
+__device__ __forceinline__ bool hist_bin(const HistArgs &h, float ma, float mb, float mr, int &bin) {
+    const float colour = ma - mb;
+    if (!(colour > h.cut) || !(mr >= h.lo) || !(mr < h.hi)) return false;
+    bin = min((int)((mr - h.lo) * h.scale), h.n_bins - 1);
+    return true;
+}
+
 template <int Q4>
 __device__ __forceinline__ void write_mags(const float (&acc)[4 * Q4], int Q, float magoff,
                                            const float *__restrict__ offq, float *out) {

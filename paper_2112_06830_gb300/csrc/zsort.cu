@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(128) zsort_tile_kernel(SortKey k, int64_t n, i
 // written to the galaxy's own (unsorted) row.
 template <int Q4>
 __global__ void combine_mags_kernel(const float *partial, int parts, int64_t n, int Q, const float *magoff,
-                                    const float *offq, const int *gidx, float *mags) {
+                                    const float *offq, const int *gidx, float *mags, HistArgs h) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     float acc[4 * Q4];
@@ -135,6 +135,11 @@ __global__ void combine_mags_kernel(const float *partial, int parts, int64_t n, 
     float m[4 * Q4];
 #pragma unroll
     for (int q = 0; q < 4 * Q4; ++q) m[q] = q < Q ? ab_mag(acc[q], mo, offq[q]) : 0.f;
+    if (h.counts) {
+        int bin;
+        if (hist_bin(h, m[h.band_a], m[h.band_b], m[h.band_r], bin)) atomicAdd(h.counts + bin, 1ull);
+    }
+    if (!mags) return;
     float *dst = mags + g * Q;
     if (Q == 4 * Q4) {
 #pragma unroll
@@ -174,16 +179,20 @@ cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *params, 
 }
 
 cudaError_t launch_combine(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts, float *mags,
-                           cudaStream_t s) {
+                           cudaStream_t s, const HistArgs *hist) {
     (void)c;
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + 255) / 256);
+    const HistArgs h = hist ? *hist : HistArgs{};
+#define DSPS_COMBINE(Q4)                                                                                      \
+    combine_mags_kernel<Q4><<<blocks, 256, 0, s>>>(w.partial, parts, n, fs.Q, w.magoff, fs.d_offq, w.gidx, mags, h)
     switch (fs.Q4) {
-    case 1: combine_mags_kernel<1><<<blocks, 256, 0, s>>>(w.partial, parts, n, fs.Q, w.magoff, fs.d_offq, w.gidx, mags); break;
-    case 2: combine_mags_kernel<2><<<blocks, 256, 0, s>>>(w.partial, parts, n, fs.Q, w.magoff, fs.d_offq, w.gidx, mags); break;
-    case 3: combine_mags_kernel<3><<<blocks, 256, 0, s>>>(w.partial, parts, n, fs.Q, w.magoff, fs.d_offq, w.gidx, mags); break;
-    default: combine_mags_kernel<4><<<blocks, 256, 0, s>>>(w.partial, parts, n, fs.Q, w.magoff, fs.d_offq, w.gidx, mags); break;
+    case 1: DSPS_COMBINE(1); break;
+    case 2: DSPS_COMBINE(2); break;
+    case 3: DSPS_COMBINE(3); break;
+    default: DSPS_COMBINE(4); break;
     }
+#undef DSPS_COMBINE
     return cudaGetLastError();
 }
 

@@ -64,6 +64,14 @@ class dsps_profile_t(C.Structure):
                 ("tc_kblocks", C.c_int64)]
 
 
+DSPS_MAX_HIST_BINS = 4096
+
+
+class dsps_hist_spec(C.Structure):
+    _fields_ = [("band_a", C.c_int32), ("band_b", C.c_int32), ("cut", C.c_float), ("band_r", C.c_int32),
+                ("lo", C.c_float), ("hi", C.c_float), ("n_bins", C.c_int32)]
+
+
 class dsps_request(C.Structure):
     _fields_ = [("n_gal", C.c_int64), ("params", C.c_void_p), ("set_id", C.c_int32),
                 ("precision", C.c_int32), ("want_grad", C.c_int32), ("mag_bar", C.c_void_p),
@@ -89,6 +97,10 @@ _SIGS = [
                                       C.c_void_p, C.c_void_p, C.c_void_p]),
     ("dsps_photometry_fp32_static", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
                                               C.c_void_p]),
+    ("dsps_photometry_histogram", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_int32,
+                                            C.POINTER(dsps_hist_spec), C.c_void_p, C.c_void_p]),
+    ("dsps_histogram", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.POINTER(dsps_hist_spec),
+                                 C.c_void_p, C.c_void_p]),
     ("dsps_submit", C.c_int, [C.c_void_p, C.POINTER(dsps_request), C.POINTER(C.c_uint64)]),
     ("dsps_poll", C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(C.c_double)]),
     ("dsps_device_error", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -184,6 +196,16 @@ def dsps_photometry_vjp(ctx, n_gal, params_ptr, set_id, precision, mag_bar_ptr, 
                         stream=0):
     return _check(load().dsps_photometry_vjp(ctx, n_gal, params_ptr, set_id, precision, mag_bar_ptr,
                                              mags_ptr, param_bar_ptr, stream), "dsps_photometry_vjp")
+
+
+def dsps_photometry_histogram(ctx, n_gal, params_ptr, set_id, precision, spec, counts_ptr, stream=0):
+    return _check(load().dsps_photometry_histogram(ctx, n_gal, params_ptr, set_id, precision, C.byref(spec),
+                                                   counts_ptr, stream), "dsps_photometry_histogram")
+
+
+def dsps_histogram(ctx, n_gal, mags_ptr, n_filt, spec, counts_ptr, stream=0):
+    return _check(load().dsps_histogram(ctx, n_gal, mags_ptr, n_filt, C.byref(spec), counts_ptr, stream),
+                  "dsps_histogram")
 
 
 def dsps_photometry_fp32_static(ctx, n_gal, params_ptr, set_id, mags_ptr, stream=0):
@@ -320,6 +342,25 @@ class Context:
                             mags.data_ptr() if mags is not None else None, pbar.data_ptr(),
                             _stream_handle(stream))
         return mags, pbar
+
+    def photometry_histogram(self, params, set_id, spec, precision=DSPS_PREC_BF16X3, stream=None):
+        """Counts (device int64 [n_bins]) of the colour-cut magnitude histogram
+        (spec: dsps_hist_spec), the magnitudes never written."""
+        import torch
+        params = params.contiguous()
+        counts = torch.empty(spec.n_bins, dtype=torch.int64, device=params.device)
+        dsps_photometry_histogram(self.handle, params.shape[1], params.data_ptr(), set_id, precision, spec,
+                                  counts.data_ptr(), _stream_handle(stream))
+        return counts
+
+    def histogram(self, mags, spec, stream=None):
+        """The same histogram of magnitudes already on the device ([G, Q] float32)."""
+        import torch
+        mags = mags.contiguous()
+        counts = torch.empty(spec.n_bins, dtype=torch.int64, device=mags.device)
+        dsps_histogram(self.handle, mags.shape[0], mags.data_ptr(), mags.shape[1], spec, counts.data_ptr(),
+                       _stream_handle(stream))
+        return counts
 
     def device_error(self, stream=None):
         return dsps_device_error(self.handle, _stream_handle(stream))

@@ -554,3 +554,16 @@ def test_bump_curve_derivative_matches_differences():
         c, dc = oracle.dust_curve(g1, l, -0.1)
         fd = (oracle.dust_curve(g1, l, -0.1 + 1e-6)[0] - oracle.dust_curve(g1, l, -0.1 - 1e-6)[0]) / 2e-6
         assert dc == pytest.approx(fd, rel=1e-7, abs=1e-10)
+
+
+# ---------------------------------------------------------------- population statistic (Sec. 5.1)
+
+def test_colour_cut_histogram_counts_a_hand_made_population():
+    m = np.array([[20.0, 19.0, 18.5],    # colour 1.0, r 18.5 -> bin 1 of [18, 20) x 4
+                  [20.0, 19.9, 19.9],    # colour 0.1: cut
+                  [21.0, 20.0, 17.9],    # r below range
+                  [22.0, 20.5, 19.99],   # colour 1.5, bin 3
+                  [np.nan, 19.0, 18.6],  # NaN colour
+                  [23.0, 21.0, 18.0]])   # colour 2.0, r on the lower edge -> bin 0
+    h = oracle.colour_cut_histogram(m, 0, 1, 0.5, 2, 18.0, 20.0, 4)
+    np.testing.assert_array_equal(h, [1, 1, 0, 1])
