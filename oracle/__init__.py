@@ -58,6 +58,10 @@ class _Filters(C.Structure):
                 ("lam", C.POINTER(C.c_double)), ("trans", C.POINTER(C.c_double))]
 
 
+class _Line(C.Structure):
+    _fields_ = [("lam_c", C.c_double), ("half_width", C.c_double), ("cont_width", C.c_double)]
+
+
 def _load():
     global _lib
     with _lock:
@@ -94,6 +98,10 @@ def _load():
                                                   C.c_double, dp]
             lib.orc_weights.argtypes = [C.POINTER(_Grid), C.c_long, dp, dp, C.c_int]
             lib.orc_mags.argtypes = [C.POINTER(_Grid), C.POINTER(_Filters), C.c_long, dp, dp, C.c_int]
+            lib.orc_ew_from_spectrum.argtypes = [dp, dp, C.c_int, C.POINTER(_Line), dp]
+            lib.orc_ew_from_spectrum.restype = C.c_double
+            lib.orc_spectra.argtypes = [C.POINTER(_Grid), C.c_long, dp, dp, C.c_int]
+            lib.orc_line_ew.argtypes = [C.POINTER(_Grid), C.POINTER(_Line), C.c_long, dp, dp, dp, dp, C.c_int]
             lib.orc_mags_vjp.argtypes = [C.POINTER(_Grid), C.POINTER(_Filters), C.c_long, dp, dp,
                                          dp, dp, C.c_int]
             _lib = lib
@@ -305,3 +313,48 @@ def mags_vjp(grid: Grid, filters: Filters, params, mag_bar, nthreads=None):
     _load().orc_mags_vjp(C.byref(grid._c), C.byref(filters._c), G, _dp(p), _dp(mb), _dp(m), _dp(pb),
                          _nthreads(nthreads))
     return m, pb
+
+
+# ---- emission-line equivalent width (Sec. 2.2, Eq. eqw) --------------------
+
+def ew_from_spectrum(lam, L, lam_c, half_width, cont_width):
+    """(W [A], dW/dL) of a tabulated spectrum: quadratic continuum fitted on
+    half_width < |lam - lam_c| <= half_width + cont_width, trapezoid of
+    (L - L0)/L0 over |lam - lam_c| <= half_width."""
+    l, v = _f64(lam), _f64(L)
+    lb = np.zeros(len(l))
+    ln = _Line(float(lam_c), float(half_width), float(cont_width))
+    w = _load().orc_ew_from_spectrum(_dp(l), _dp(v), len(l), C.byref(ln), _dp(lb))
+    return w, lb
+
+
+def spectra(grid: Grid, params, nthreads=None):
+    """Rest-frame attenuated spectra 10^logM F S, shape [G, n_lam] [Lsun/Hz]."""
+    p = _f64(params)
+    G = p.shape[1]
+    out = np.zeros((G, grid.n_lam))
+    _load().orc_spectra(C.byref(grid._c), G, _dp(p), _dp(out), _nthreads(nthreads))
+    return out
+
+
+def line_ew(grid: Grid, params, lam_c, half_width, cont_width, nthreads=None):
+    """Equivalent widths [G] of the galaxies' rest-frame spectra."""
+    p = _f64(params)
+    G = p.shape[1]
+    ew = np.zeros(G)
+    ln = _Line(float(lam_c), float(half_width), float(cont_width))
+    _load().orc_line_ew(C.byref(grid._c), C.byref(ln), G, _dp(p), None, _dp(ew), None, _nthreads(nthreads))
+    return ew
+
+
+def line_ew_vjp(grid: Grid, params, ew_bar, lam_c, half_width, cont_width, nthreads=None):
+    """(ew [G], param_bar [11, G]) with param_bar[k, g] = ew_bar[g] dW_g/dp_k."""
+    p = _f64(params)
+    G = p.shape[1]
+    eb = _f64(ew_bar).reshape(G)
+    ew = np.zeros(G)
+    pb = np.zeros((NGRAD, G))
+    ln = _Line(float(lam_c), float(half_width), float(cont_width))
+    _load().orc_line_ew(C.byref(grid._c), C.byref(ln), G, _dp(p), _dp(eb), _dp(ew), _dp(pb),
+                        _nthreads(nthreads))
+    return ew, pb

@@ -26,6 +26,10 @@
  *   row 10     logM       log10 of the stellar mass formed by t_obs [Msun]
  *   row 11     z          redshift
  * Gradient layout (11 rows): rows 0..10 of the above (z gets no gradient).
+ *
+ * Besides the magnitudes, the oracle gives the rest-frame attenuated spectrum
+ * and the equivalent width of an emission line (Sec. 2.2, Eq. eqw) with their
+ * adjoints.
  */
 #include <math.h>
 #include <pthread.h>
@@ -447,41 +451,109 @@ static void galaxy_weights(const orc_grid *g, const double *par /* 12 */, double
 /* ------------------------------------------------------------------ */
 /* Adjoint of the per-galaxy model (reverse of the steps above)        */
 /* ------------------------------------------------------------------ */
+
+/* Forward intermediates of one galaxy that the reverse sweeps need. */
+typedef struct {
+    double *sfr, *dsfr;        /* [n_t], [n_t][5] SFR at the nodes and dSFR/dp      */
+    double *e, *Mhi;           /* [n_age+1] age-bin edges, M(t_obs - e_i)            */
+    double Mtot;
+    double *frac;              /* [n_age]                                            */
+    double *P, *dPmu, *dPsig;  /* [n_age][n_z] MDF bin probabilities and derivatives */
+    double *dmu5, *dmu7;       /* [n_age] d mu_i / d p5, d p7                       */
+    double *S;                 /* [n_lam] sum_ij omega_ij L_ijn (per unit mass)      */
+    double *F, *u, *du;        /* [n_lam] dust transmission, A/Av, d(A/Av)/d delta   */
+} gal_state;
+
+static void gal_forward(const orc_grid *g, const double *par, double t_obs, gal_state *st)
+{
+    int N = g->n_lam, NA = g->n_age, NZ = g->n_z, K = NA * NZ, NT = g->n_t;
+    double Av = par[8], delta = par[9];
+    double h = (g->t1 - g->t0) / (NT - 1);
+    st->sfr = malloc(sizeof(double) * NT);
+    st->dsfr = malloc(sizeof(double) * NT * 5);
+    for (int n = 0; n < NT; ++n) st->sfr[n] = orc_sfr(g->sfh_model, par, g->t0 + n * h, st->dsfr + 5 * n);
+    st->e = malloc(sizeof(double) * (NA + 1));
+    orc_age_edges_gyr(g, st->e);
+    st->Mhi = malloc(sizeof(double) * (NA + 1));
+    for (int i = 0; i <= NA; ++i) st->Mhi[i] = orc_cum_mass(st->sfr, NT, g->t0, g->t1, t_obs - st->e[i], NULL);
+    st->Mtot = st->Mhi[0];
+    st->frac = malloc(sizeof(double) * NA);
+    for (int i = 0; i < NA; ++i) st->frac[i] = (st->Mhi[i] - st->Mhi[i + 1]) / st->Mtot;
+    st->P = malloc(sizeof(double) * K);
+    st->dPmu = malloc(sizeof(double) * K);
+    st->dPsig = malloc(sizeof(double) * K);
+    st->dmu5 = malloc(sizeof(double) * NA);
+    st->dmu7 = malloc(sizeof(double) * NA);
+    for (int i = 0; i < NA; ++i) {
+        double mu_i = orc_mdf_mean(g, par, i, st->dmu5 + i, st->dmu7 + i);
+        orc_mdf(g, mu_i, par[6], st->P + i * NZ, st->dPmu + i * NZ, st->dPsig + i * NZ);
+    }
+    st->S = calloc(N, sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        double w = st->frac[k / NZ] * st->P[k];
+        const double *L = g->l_ssp + (size_t)k * N;
+        for (int n = 0; n < N; ++n) st->S[n] += w * L[n];
+    }
+    st->F = malloc(sizeof(double) * N);
+    st->u = malloc(sizeof(double) * N);
+    st->du = malloc(sizeof(double) * N);
+    for (int n = 0; n < N; ++n) {
+        st->u[n] = orc_dust_curve(g, g->lam[n], delta, st->du + n);   /* A_lambda / Av and its delta derivative */
+        st->F[n] = pow(10.0, -0.4 * Av * st->u[n]);
+    }
+}
+
+static void gal_free(gal_state *st)
+{
+    free(st->du); free(st->u); free(st->F); free(st->S); free(st->dmu7); free(st->dmu5);
+    free(st->dPsig); free(st->dPmu); free(st->P); free(st->frac); free(st->Mhi); free(st->e);
+    free(st->dsfr); free(st->sfr);
+}
+
+/* Reverse of the weights and the contraction: given Sbar_n = dLoss/dS_n (S the
+ * per-unit-mass spectrum before dust), adds dLoss/dp_k for k = 0..7 to pbar. */
+static void gal_reverse_sbar(const orc_grid *g, const gal_state *st, double t_obs, const double *Sbar,
+                             double *pbar)
+{
+    int N = g->n_lam, NA = g->n_age, NZ = g->n_z, K = NA * NZ, NT = g->n_t;
+    double *fracbar = calloc(NA, sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        const double *L = g->l_ssp + (size_t)k * N;
+        double wbar = 0.0;
+        for (int n = 0; n < N; ++n) wbar += Sbar[n] * L[n];
+        int i = k / NZ;
+        fracbar[i] += wbar * st->P[k];
+        double Pbar = wbar * st->frac[i];
+        pbar[5] += Pbar * st->dPmu[k] * st->dmu5[i];
+        pbar[6] += Pbar * st->dPsig[k];
+        pbar[7] += Pbar * st->dPmu[k] * st->dmu7[i];
+    }
+    /* frac_i = (Mhi_i - Mhi_{i+1}) / Mtot with Mtot = Mhi_0 */
+    double *Mbar = calloc(NA + 1, sizeof(double));
+    for (int i = 0; i < NA; ++i) {
+        Mbar[i] += fracbar[i] / st->Mtot;
+        Mbar[i + 1] -= fracbar[i] / st->Mtot;
+        Mbar[0] -= fracbar[i] * st->frac[i] / st->Mtot;
+    }
+    double *coef = malloc(sizeof(double) * NT);
+    double *sfrbar = calloc(NT, sizeof(double));
+    for (int i = 0; i <= NA; ++i) {
+        if (Mbar[i] == 0.0) continue;
+        orc_cum_mass(st->sfr, NT, g->t0, g->t1, t_obs - st->e[i], coef);
+        for (int n = 0; n < NT; ++n) sfrbar[n] += Mbar[i] * coef[n];
+    }
+    for (int n = 0; n < NT; ++n)
+        for (int k = 0; k < 5; ++k) pbar[k] += sfrbar[n] * st->dsfr[5 * n + k];
+    free(sfrbar); free(coef); free(Mbar); free(fracbar);
+}
+
 static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const double *par, double t_obs,
                             double dmod, const double *mbar, double *mags, double *pbar /* 11 */)
 {
-    int N = g->n_lam, NA = g->n_age, NZ = g->n_z, K = NA * NZ, Q = f->n_filt, NT = g->n_t;
-    double Av = par[8], delta = par[9], logM = par[10], z = par[11];
-    double h = (g->t1 - g->t0) / (NT - 1);
-
-    /* forward intermediates */
-    double *sfr = malloc(sizeof(double) * NT);
-    double *dsfr = malloc(sizeof(double) * NT * 5);
-    for (int n = 0; n < NT; ++n) sfr[n] = orc_sfr(g->sfh_model, par, g->t0 + n * h, dsfr + 5 * n);
-    double *e = malloc(sizeof(double) * (NA + 1));
-    orc_age_edges_gyr(g, e);
-    double *Mhi = malloc(sizeof(double) * (NA + 1));   /* M(t_obs - e_i) */
-    for (int i = 0; i <= NA; ++i) Mhi[i] = orc_cum_mass(sfr, NT, g->t0, g->t1, t_obs - e[i], NULL);
-    double Mtot = Mhi[0];
-    double *frac = malloc(sizeof(double) * NA);
-    for (int i = 0; i < NA; ++i) frac[i] = (Mhi[i] - Mhi[i + 1]) / Mtot;
-    double *P = malloc(sizeof(double) * K), *dPmu = malloc(sizeof(double) * K), *dPsig = malloc(sizeof(double) * K);
-    double *dmu5 = malloc(sizeof(double) * NA), *dmu7 = malloc(sizeof(double) * NA);
-    for (int i = 0; i < NA; ++i) {
-        double mu_i = orc_mdf_mean(g, par, i, dmu5 + i, dmu7 + i);
-        orc_mdf(g, mu_i, par[6], P + i * NZ, dPmu + i * NZ, dPsig + i * NZ);
-    }
-    double *S = calloc(N, sizeof(double));
-    for (int k = 0; k < K; ++k) {
-        double w = frac[k / NZ] * P[k];
-        const double *L = g->l_ssp + (size_t)k * N;
-        for (int n = 0; n < N; ++n) S[n] += w * L[n];
-    }
-    double *F = malloc(sizeof(double) * N), *u = malloc(sizeof(double) * N), *du = malloc(sizeof(double) * N);
-    for (int n = 0; n < N; ++n) {
-        u[n] = orc_dust_curve(g, g->lam[n], delta, du + n);   /* A_lambda / Av and its delta derivative */
-        F[n] = pow(10.0, -0.4 * Av * u[n]);
-    }
+    int N = g->n_lam, Q = f->n_filt;
+    double Av = par[8], logM = par[10], z = par[11];
+    gal_state st;
+    gal_forward(g, par, t_obs, &st);
     int *off = malloc(sizeof(int) * (Q + 1));
     filter_offsets(f, off);
     double *T = malloc(sizeof(double) * (size_t)Q * N);
@@ -491,7 +563,7 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
         double acc = 0.0;
         for (int n = 0; n < N; ++n) {
             T[(size_t)q * N + n] = orc_filter_trans(fl, ft, f->n_pts[q], (1.0 + z) * g->lam[n]);
-            acc += trap_w(g->lam, N, n) / g->lam[n] * T[(size_t)q * N + n] * F[n] * S[n];
+            acc += trap_w(g->lam, N, n) / g->lam[n] * T[(size_t)q * N + n] * st.F[n] * st.S[n];
         }
         Nq[q] = acc;
         double Dq = orc_filter_norm(fl, ft, f->n_pts[q]);
@@ -510,45 +582,163 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
         double c = trap_w(g->lam, N, n) / g->lam[n];
         double sT = 0.0;
         for (int q = 0; q < Q; ++q) sT += Nbar[q] * T[(size_t)q * N + n];
-        Sbar[n] = c * sT * F[n];
-        double Fbar = c * sT * S[n];
-        double dF_dAv = F[n] * (-0.4 * log(10.0)) * u[n];
-        double dF_ddelta = F[n] * (-0.4 * log(10.0)) * Av * du[n];
+        Sbar[n] = c * sT * st.F[n];
+        double Fbar = c * sT * st.S[n];
+        double dF_dAv = st.F[n] * (-0.4 * log(10.0)) * st.u[n];
+        double dF_ddelta = st.F[n] * (-0.4 * log(10.0)) * Av * st.du[n];
         pbar[8] += Fbar * dF_dAv;
         pbar[9] += Fbar * dF_ddelta;
     }
-    double *fracbar = calloc(NA, sizeof(double));
-    for (int k = 0; k < K; ++k) {
-        const double *L = g->l_ssp + (size_t)k * N;
-        double wbar = 0.0;
-        for (int n = 0; n < N; ++n) wbar += Sbar[n] * L[n];
-        int i = k / NZ;
-        fracbar[i] += wbar * P[k];
-        double Pbar = wbar * frac[i];
-        pbar[5] += Pbar * dPmu[k] * dmu5[i];
-        pbar[6] += Pbar * dPsig[k];
-        pbar[7] += Pbar * dPmu[k] * dmu7[i];
-    }
-    /* frac_i = (Mhi_i - Mhi_{i+1}) / Mtot with Mtot = Mhi_0 */
-    double *Mbar = calloc(NA + 1, sizeof(double));
-    for (int i = 0; i < NA; ++i) {
-        Mbar[i] += fracbar[i] / Mtot;
-        Mbar[i + 1] -= fracbar[i] / Mtot;
-        Mbar[0] -= fracbar[i] * frac[i] / Mtot;
-    }
-    double *coef = malloc(sizeof(double) * NT);
-    double *sfrbar = calloc(NT, sizeof(double));
-    for (int i = 0; i <= NA; ++i) {
-        if (Mbar[i] == 0.0) continue;
-        orc_cum_mass(sfr, NT, g->t0, g->t1, t_obs - e[i], coef);
-        for (int n = 0; n < NT; ++n) sfrbar[n] += Mbar[i] * coef[n];
-    }
-    for (int n = 0; n < NT; ++n)
-        for (int k = 0; k < 5; ++k) pbar[k] += sfrbar[n] * dsfr[5 * n + k];
+    gal_reverse_sbar(g, &st, t_obs, Sbar, pbar);
+    free(Sbar); free(Nbar); free(Nq); free(T); free(off);
+    gal_free(&st);
+}
 
-    free(sfrbar); free(coef); free(Mbar); free(fracbar); free(Sbar); free(Nbar);
-    free(Nq); free(T); free(off); free(du); free(u); free(F); free(S); free(dPsig); free(dPmu); free(P);
-    free(dmu7); free(dmu5); free(frac); free(Mhi); free(e); free(dsfr); free(sfr);
+/* ------------------------------------------------------------------ */
+/* Sec. 2.2, Eq. (eqw): emission-line equivalent width                 */
+/* ------------------------------------------------------------------ */
+
+/* Line window [lam_c - hw, lam_c + hw] and the continuum on both sides of it,
+ * hw < |lam - lam_c| <= hw + cw (reading: the paper fits the neighbourhood of
+ * the line with the line's range masked, and gives no window sizes). */
+typedef struct {
+    double lam_c, half_width, cont_width;
+} orc_line;
+
+/* Solves the 3x3 system A x = b (Gaussian elimination, partial pivoting). */
+static int solve3(const double A_in[3][3], const double b_in[3], double x[3])
+{
+    double A[3][3], b[3];
+    memcpy(A, A_in, sizeof(A));
+    memcpy(b, b_in, sizeof(b));
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return -1;
+        if (piv != c) {
+            for (int k = 0; k < 3; ++k) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < 3; ++r) {
+            double m = A[r][c] / A[c][c];
+            for (int k = c; k < 3; ++k) A[r][k] -= m * A[c][k];
+            b[r] -= m * b[c];
+        }
+    }
+    for (int c = 2; c >= 0; --c) {
+        double v = b[c];
+        for (int k = c + 1; k < 3; ++k) v -= A[c][k] * x[k];
+        x[c] = v / A[c][c];
+    }
+    return 0;
+}
+
+/* Eq. (eqw) on a tabulated spectrum L(lam_n):
+ *   L0   the quadratic in lam fitted by least squares to the continuum points
+ *        (the line's own range masked), evaluated at each point of the line
+ *        window (reading: the continuum at the line, point by point);
+ *   W    = int over the line window of (L - L0) / L0 dlam, trapezoid rule on
+ *        the grid points inside the window.
+ * Returns W [A] (NaN with fewer than 3 continuum or 2 line points); Lbar
+ * (optional, [n]) receives dW/dL_n. */
+double orc_ew_from_spectrum(const double *lam, const double *L, int n, const orc_line *ln, double *Lbar)
+{
+    double hw = ln->half_width, cw = ln->cont_width, xs = hw + cw;
+    double M[3][3] = {{0}}, r[3] = {0}, beta[3];
+    int n_cont = 0, n_line = 0;
+    for (int k = 0; k < n; ++k) {
+        double d = fabs(lam[k] - ln->lam_c);
+        if (d <= hw) ++n_line;
+        else if (d <= hw + cw) {
+            double x = (lam[k] - ln->lam_c) / xs, phi[3] = {1.0, x, x * x};
+            for (int a = 0; a < 3; ++a) {
+                r[a] += phi[a] * L[k];
+                for (int b = 0; b < 3; ++b) M[a][b] += phi[a] * phi[b];
+            }
+            ++n_cont;
+        }
+    }
+    if (Lbar) for (int k = 0; k < n; ++k) Lbar[k] = 0.0;
+    if (n_cont < 3 || n_line < 2 || solve3(M, r, beta) != 0) return NAN;
+    double W = 0.0, gam[3] = {0, 0, 0};
+    int prev = -1;
+    for (int k = 0; k < n; ++k) {
+        if (fabs(lam[k] - ln->lam_c) > hw) continue;
+        if (prev >= 0) {
+            double dl = lam[k] - lam[prev];
+            double fa[2];
+            int idx[2] = {prev, k};
+            for (int s = 0; s < 2; ++s) {
+                double x = (lam[idx[s]] - ln->lam_c) / xs;
+                double L0 = beta[0] + beta[1] * x + beta[2] * x * x;
+                fa[s] = (L[idx[s]] - L0) / L0;
+                if (Lbar) {
+                    /* d/dL of 0.5 dl (L/L0 - 1), and its L0 part through beta */
+                    Lbar[idx[s]] += 0.5 * dl / L0;
+                    double g0 = -0.5 * dl * L[idx[s]] / (L0 * L0);
+                    gam[0] += g0;
+                    gam[1] += g0 * x;
+                    gam[2] += g0 * x * x;
+                }
+            }
+            W += 0.5 * dl * (fa[0] + fa[1]);
+        }
+        prev = k;
+    }
+    if (Lbar) {
+        /* beta = M^-1 r, r = sum_cont phi L:  dW/dL_m = phi_m^T M^-1 gamma */
+        double rho[3];
+        solve3(M, gam, rho);
+        for (int k = 0; k < n; ++k) {
+            double d = fabs(lam[k] - ln->lam_c);
+            if (d <= hw || d > hw + cw) continue;
+            double x = (lam[k] - ln->lam_c) / xs;
+            Lbar[k] += rho[0] + rho[1] * x + rho[2] * x * x;
+        }
+    }
+    return W;
+}
+
+/* Rest-frame attenuated spectrum of one galaxy (Eq. cspdef with the weights
+ * of Eq. agedep_mdf, times Eq. attenuation): L_n = 10^logM F_n S_n [Lsun/Hz]. */
+static void galaxy_spectrum(const orc_grid *g, const double *par, double t_obs, double *out)
+{
+    gal_state st;
+    gal_forward(g, par, t_obs, &st);
+    double M = pow(10.0, par[10]);
+    for (int n = 0; n < g->n_lam; ++n) out[n] = M * st.F[n] * st.S[n];
+    gal_free(&st);
+}
+
+/* Equivalent width of one galaxy's spectrum and, with ewbar, its adjoint
+ * pbar[k] = ewbar dW/dp_k (k = 0..10). */
+static double galaxy_ew(const orc_grid *g, const orc_line *ln, const double *par, double t_obs, double ewbar,
+                        double *pbar)
+{
+    int N = g->n_lam;
+    gal_state st;
+    gal_forward(g, par, t_obs, &st);
+    double M = pow(10.0, par[10]), Av = par[8];
+    double *L = malloc(sizeof(double) * N), *Lbar = malloc(sizeof(double) * N);
+    for (int n = 0; n < N; ++n) L[n] = M * st.F[n] * st.S[n];
+    double W = orc_ew_from_spectrum(g->lam, L, N, ln, pbar ? Lbar : NULL);
+    if (pbar) {
+        for (int k = 0; k < ORC_NGRAD; ++k) pbar[k] = 0.0;
+        double *Sbar = malloc(sizeof(double) * N);
+        for (int n = 0; n < N; ++n) {
+            double lb = ewbar * Lbar[n];
+            Sbar[n] = lb * M * st.F[n];
+            pbar[8] += lb * L[n] * (-0.4 * log(10.0)) * st.u[n];
+            pbar[9] += lb * L[n] * (-0.4 * log(10.0)) * Av * st.du[n];
+            pbar[10] += lb * L[n] * log(10.0);
+        }
+        gal_reverse_sbar(g, &st, t_obs, Sbar, pbar);
+        free(Sbar);
+    }
+    free(Lbar); free(L);
+    gal_free(&st);
+    return W;
 }
 
 /* ------------------------------------------------------------------ */
@@ -561,7 +751,9 @@ typedef struct {
     long n_gal, begin, end;
     const double *params, *mbar;
     double *w_out, *mags, *pbar;
-    int mode;  /* 0 weights, 1 mags, 2 vjp */
+    int mode;  /* 0 weights, 1 mags, 2 vjp, 3 spectrum, 4 line EW (+ adjoint with pbar) */
+    const orc_line *line;
+    double *out;   /* mode 3: [G][n_lam]; mode 4: [G] */
 } orc_job;
 
 static void *orc_worker(void *arg)
@@ -584,6 +776,13 @@ static void *orc_worker(void *arg)
             galaxy_weights(g, par, t_obs, omega);
             orc_mags_from_weights(g, j->f, omega, par[8], par[9], par[10], z, dmod,
                                   j->mags + (size_t)gi * j->f->n_filt);
+        } else if (j->mode == 3) {
+            galaxy_spectrum(g, par, t_obs, j->out + (size_t)gi * g->n_lam);
+        } else if (j->mode == 4) {
+            double pb[ORC_NGRAD];
+            j->out[gi] = galaxy_ew(g, j->line, par, t_obs, j->mbar ? j->mbar[gi] : 0.0, j->pbar ? pb : NULL);
+            if (j->pbar)
+                for (int k = 0; k < ORC_NGRAD; ++k) j->pbar[(size_t)k * j->n_gal + gi] = pb[k];
         } else {
             double dmod = orc_dist_mod(g->om0, g->w0, g->h, z);
             double pb[ORC_NGRAD];
@@ -616,7 +815,7 @@ static int orc_run(orc_job proto, int nthreads)
 /* Per-galaxy SSP weights in Msun: w[g][i][j] = 10^logM frac_i P[j|i]. */
 int orc_weights(const orc_grid *g, long n_gal, const double *params, double *w_out, int nthreads)
 {
-    orc_job j = {g, NULL, n_gal, 0, n_gal, params, NULL, w_out, NULL, NULL, 0};
+    orc_job j = {g, NULL, n_gal, 0, n_gal, params, NULL, w_out, NULL, NULL, 0, NULL, NULL};
     return orc_run(j, nthreads);
 }
 
@@ -624,7 +823,7 @@ int orc_weights(const orc_grid *g, long n_gal, const double *params, double *w_o
 int orc_mags(const orc_grid *g, const orc_filters *f, long n_gal, const double *params, double *mags,
              int nthreads)
 {
-    orc_job j = {g, f, n_gal, 0, n_gal, params, NULL, NULL, mags, NULL, 1};
+    orc_job j = {g, f, n_gal, 0, n_gal, params, NULL, NULL, mags, NULL, 1, NULL, NULL};
     return orc_run(j, nthreads);
 }
 
@@ -632,6 +831,21 @@ int orc_mags(const orc_grid *g, const orc_filters *f, long n_gal, const double *
 int orc_mags_vjp(const orc_grid *g, const orc_filters *f, long n_gal, const double *params,
                  const double *mbar, double *mags, double *pbar, int nthreads)
 {
-    orc_job j = {g, f, n_gal, 0, n_gal, params, mbar, NULL, mags, pbar, 2};
+    orc_job j = {g, f, n_gal, 0, n_gal, params, mbar, NULL, mags, pbar, 2, NULL, NULL};
+    return orc_run(j, nthreads);
+}
+
+/* Rest-frame attenuated spectra out[g][n] [Lsun/Hz]. */
+int orc_spectra(const orc_grid *g, long n_gal, const double *params, double *out, int nthreads)
+{
+    orc_job j = {g, NULL, n_gal, 0, n_gal, params, NULL, NULL, NULL, NULL, 3, NULL, out};
+    return orc_run(j, nthreads);
+}
+
+/* Equivalent widths ew[g] [A] and, if pbar != NULL, pbar[k][g] = ewbar[g] dW_g/dp_k. */
+int orc_line_ew(const orc_grid *g, const orc_line *line, long n_gal, const double *params, const double *ewbar,
+                double *ew, double *pbar, int nthreads)
+{
+    orc_job j = {g, NULL, n_gal, 0, n_gal, params, ewbar, NULL, NULL, pbar, 4, line, ew};
     return orc_run(j, nthreads);
 }

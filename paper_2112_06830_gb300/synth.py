@@ -114,6 +114,29 @@ def make_ssp(spec: GridSpec, seed: int) -> SSPGrid:
     return SSPGrid(log_age, lgz, lam, (base * noise).astype(np.float32), spec.t0, spec.t1, spec.n_t)
 
 
+def with_emission_line(ssp: SSPGrid, lam_line: float = 5007.0, sigma: float = 8.0, amp: float = 30.0,
+                       age_scale: float = 5e6) -> SSPGrid:
+    """The same SSP block with a Gaussian emission line of width ``sigma`` [A] at
+    ``lam_line`` added to the young populations, as the stand-in for the nebular
+    lines the paper's SSPs carry: row (i, j) gains
+    a_i L_ij(lam_line) exp(-(lam - lam_line)^2 / (2 sigma^2)) with
+    a_i = amp / (1 + (age_i / age_scale)^2), L_ij(lam_line) the row's value at the
+    grid point nearest the line."""
+    lam = ssp.lam
+    n_l = int(np.argmin(np.abs(lam - lam_line)))
+    age = 10.0 ** ssp.log_age_yr
+    a = amp / (1.0 + (age / age_scale) ** 2)
+    prof = np.exp(-0.5 * ((lam - lam_line) / sigma) ** 2)
+    base = ssp.l_ssp.astype(np.float64)
+    add = a[:, None, None] * base[:, :, n_l:n_l + 1] * prof[None, None, :]
+    return SSPGrid(ssp.log_age_yr, ssp.lgz, lam, (base + add).astype(np.float32), ssp.t0, ssp.t1, ssp.n_t)
+
+
+# Line-strength workload: [OIII] 5007 A (the line of the paper's Sec. 3.3 example),
+# line window +-30 A, continuum 100 A on each side.
+EW_LINE = (5007.0, 30.0, 100.0)
+
+
 def gaussian_filter(center: float, fwhm: float = 800.0, step: float = 2.0):
     """Gaussian transmission curve with unit peak, tabulated every ``step`` A and
     truncated at center +- 4 FWHM."""
