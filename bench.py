@@ -467,6 +467,34 @@ def run_ours(a):
     ms_bump = max_over_ranks(float(np.mean([e0.elapsed_time(e1) for e0, e1 in b_evs])), dist, "cuda")
     ctx_b.close()
 
+    # Line strength (Sec. 2.2, Eq. eqw): equivalent width of a [OIII] 5007 A
+    # stand-in line (synthetic, young populations) with a fitted quadratic
+    # continuum, FP32; forward, and forward + gradient for a given dLoss/dW.
+    def timed_fn(fn):
+        for _ in range(a.warmup):
+            fn()
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        for e0, e1 in evs:
+            flush.fill_(1)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        barrier()
+        return max_over_ranks(float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs])), dist, "cuda")
+
+    ctx_e = dsps.Context(synth.with_emission_line(ssp), sfh_model=synth.SFH_DPL_QUENCH, device=local)
+    lid = ctx_e.add_line(*synth.EW_LINE)
+    d_ew = torch.empty(G, dtype=torch.float32, device="cuda")
+    d_ewbar = torch.from_numpy(np.random.default_rng(7 + rank).standard_normal(G).astype(np.float32)).cuda()
+    ms_ew = timed_fn(lambda: dsps.dsps_line_ew(ctx_e.handle, G, d_params.data_ptr(), lid, d_ew.data_ptr(),
+                                               stream.cuda_stream))
+    ms_ew_grad = timed_fn(lambda: dsps.dsps_line_ew_vjp(ctx_e.handle, G, d_params.data_ptr(), lid,
+                                                        d_ewbar.data_ptr(), d_ew.data_ptr(), d_pbar.data_ptr(),
+                                                        stream.cuda_stream))
+    assert torch.isfinite(d_ew).all() and torch.isfinite(d_pbar).all()
+    ctx_e.close()
+
     # The paper's benchmark step (Sec. 5.1) on these galaxies: photometry through
     # six bands, a colour cut selecting the red side, and a histogram of the
     # r-band magnitude of the selection, fused (the magnitudes are not written).
@@ -600,6 +628,10 @@ def run_ours(a):
                                          "the paper's A100 figure for its whole step is 2.4 s (context only)"},
         "dust_bump": {"value": ws * G * N_FILT / (ms_bump * 1e-3), "ms_per_step": ms_bump,
                       "note": "attenuation with the 2175 A UV bump (Drude profile)"},
+        "line_ew": {"value": ws * G / (ms_ew * 1e-3), "unit": "galaxy-EWs/s", "ms_per_step": ms_ew,
+                    "fwd_grad": {"value": ws * G / (ms_ew_grad * 1e-3), "ms_per_step": ms_ew_grad},
+                    "note": "equivalent width of a 5007 A line (window +-30 A, continuum 100 A each side, "
+                            "quadratic fit), FP32; gradient: d(loss)/d(11 parameters)"},
         "serve": serve,
         "clocks": clocks,
     }

@@ -218,6 +218,48 @@ int dsps_photometry_histogram(dsps_ctx *ctx, int64_t n_gal, const float *params,
 int dsps_histogram(dsps_ctx *ctx, int64_t n_gal, const float *mags, int32_t n_filt,
                    const dsps_hist_spec *spec, uint64_t *counts, dsps_stream_t stream);
 
+/* Rest-frame attenuated spectra on the SSP grid's own wavelengths (Sec. 2.1,
+ * Eq. cspdef with the weights of Eq. agedep_mdf, times Eq. attenuation):
+ *   out[g][n - n0] = 10^logM F_g(lam_n) sum_ij omega_gij L_ijn   [Lsun/Hz],
+ * for grid columns n0 <= n < n1 (0 <= n0 < n1 <= n_lam), FP32 weights and FP32
+ * contraction.  A galaxy with out-of-range parameters gets a NaN row.
+ * params: device float32 [12][n_gal]; out: device float32 [n_gal][n1 - n0]. */
+int dsps_spectra(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t n0, int32_t n1,
+                 float *out, dsps_stream_t stream);
+
+/* Emission-line equivalent width (Sec. 2.2, Eq. eqw) of the rest-frame
+ * attenuated spectrum L(lam) above, on the SSP grid's wavelengths lam_n:
+ *   continuum points  half_width < |lam_n - lam_line| <= half_width + cont_width
+ *   L0(lam)           the quadratic in lam fitted to L at the continuum points by
+ *                     least squares (the line's range masked)
+ *   W                 trapezoid over the line points |lam_n - lam_line| <=
+ *                     half_width of (L - L0) / L0, in Angstrom (> 0 for emission).
+ * W does not depend on the mass.  Computed in FP32: FP32 weights and window
+ * contraction; the fit's operator (M^-1 phi for each continuum point, M the
+ * normal matrix of the quadratic) is formed in FP64 when the line is added. */
+#define DSPS_MAX_LINE_POINTS 4096
+typedef struct {
+    double lam_line;           /* rest wavelength of the line [A]               */
+    double half_width;         /* of the line window [A], > 0                   */
+    double cont_width;         /* of each continuum window [A], > 0             */
+} dsps_line_spec;
+
+/* Registers a line; *line_id receives a small non-negative id.  INVALID_ARG if
+ * the grid holds fewer than 3 continuum or 2 line points for it, or more than
+ * DSPS_MAX_LINE_POINTS points in the whole window. */
+int dsps_line_add(dsps_ctx *ctx, const dsps_line_spec *spec, int32_t *line_id);
+
+/* ew: device float32 [n_gal] (NaN for out-of-range parameters). */
+int dsps_line_ew(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line_id, float *ew,
+                 dsps_stream_t stream);
+
+/* Vector-Jacobian product of the equivalent widths:
+ *   param_bar[k][g] = ew_bar[g] dW_g / d params[k][g],  k = 0..10
+ * (row 10, logM, is exactly 0).  ew_bar: device float32 [n_gal]; ew: device
+ * float32 [n_gal] or NULL; param_bar: device float32 [11][n_gal]. */
+int dsps_line_ew_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line_id,
+                     const float *ew_bar, float *ew, float *param_bar, dsps_stream_t stream);
+
 /* FP32 photometry that allocates no device memory, for callers that cannot
  * call cudaMalloc at the time they need magnitudes (for example a worker of a
  * framework whose device memory belongs to its own pooling allocator, or a

@@ -133,6 +133,7 @@ void free_ctx(Ctx *c) {
         cudaFree(fs.d_tab);
         cudaFree(fs.d_offq);
     }
+    for (auto &ls : c->lines) cudaFree(ls.d_tab);
     void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_edges, c->d_einh, c->d_bwidth,
                     c->d_zedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->d_err, c->d_stats,
                     c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d};
@@ -256,6 +257,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     c->t1 = g->t1_gyr;
     c->lnlam0 = std::log(g->lam[0]);
     c->dlnlam = dl;
+    c->h_lam.assign(g->lam, g->lam + g->n_lam);
     c->chunk = (opts.max_chunk + 127) / 128 * 128;
     {
         const double xmid = 0.5 * (g->log_age_yr[0] + g->log_age_yr[g->n_age - 1]);
@@ -502,6 +504,119 @@ int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32
     std::lock_guard<std::mutex> lk(c->mu);
     return run_photometry_vjp(c, n_gal, params, set_id, precision, mag_bar, mags, param_bar,
                               reinterpret_cast<cudaStream_t>(stream));
+}
+
+int dsps_spectra(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t n0, int32_t n1, float *out,
+                 dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || n_gal < 0 || (n_gal > 0 && (!params || !out))) return fail(DSPS_ERR_INVALID_ARG, "dsps_spectra: bad argument%s");
+    if (n0 < 0 || n1 <= n0 || n1 > c->n_lam) return fail(DSPS_ERR_INVALID_ARG, "dsps_spectra: need 0 <= n0 < n1 <= n_lam%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (n_gal == 0) return DSPS_OK;
+    DSPS_CUDA(cudaSetDevice(c->device));
+    return run_spectra_ws(c, c->ws, n_gal, params, n0, n1, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int dsps_line_add(dsps_ctx *ctx, const dsps_line_spec *spec, int32_t *line_id) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !spec || !line_id) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_add: null argument%s");
+    const double lc = spec->lam_line, hw = spec->half_width, cw = spec->cont_width;
+    if (!(lc > 0) || !(hw > 0) || !(cw > 0) || !std::isfinite(lc + hw + cw))
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_line_add: need lam_line, half_width, cont_width > 0%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    const std::vector<double> &lam = c->h_lam;
+    int first = -1, last = -1, l0 = -1, l1 = -1, n_cont = 0;
+    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const double xs = hw + cw;
+    for (int n = 0; n < c->n_lam; ++n) {
+        const double d = std::fabs(lam[n] - lc);
+        if (d > hw + cw) continue;
+        if (first < 0) first = n;
+        last = n;
+        if (d <= hw) {
+            if (l0 < 0) l0 = n;
+            l1 = n;
+        } else {
+            const double x = (lam[n] - lc) / xs, phi[3] = {1.0, x, x * x};
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) M[a][b] += phi[a] * phi[b];
+            ++n_cont;
+        }
+    }
+    if (n_cont < 3 || l0 < 0 || l1 == l0)
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_line_add: fewer than 3 continuum or 2 line points on the grid%s");
+    const int n_pts = last - first + 1;
+    if (n_pts > DSPS_MAX_LINE_POINTS) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_add: window too wide%s");
+    // M^-1 by cofactors (M is symmetric positive definite for >= 3 distinct x)
+    const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                       M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                       M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    if (!(det > 0)) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_add: singular continuum fit%s");
+    double Mi[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const int a1 = (b + 1) % 3, a2 = (b + 2) % 3, b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+            Mi[a][b] = (M[a1][b1] * M[a2][b2] - M[a1][b2] * M[a2][b1]) / det;
+        }
+    std::vector<float4> tab((size_t)2 * n_pts);
+    for (int j = 0; j < n_pts; ++j) {
+        const int n = first + j;
+        const double x = (lam[n] - lc) / xs, phi[3] = {1.0, x, x * x};
+        if (n >= l0 && n <= l1) {
+            const double t = (n > l0 ? 0.5 * (lam[n] - lam[n - 1]) : 0.0) + (n < l1 ? 0.5 * (lam[n + 1] - lam[n]) : 0.0);
+            tab[2 * j] = make_float4((float)t, (float)x, (float)(x * x), 0.f);
+            tab[2 * j + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            double psi[3];
+            for (int a = 0; a < 3; ++a) psi[a] = Mi[a][0] * phi[0] + Mi[a][1] * phi[1] + Mi[a][2] * phi[2];
+            tab[2 * j] = make_float4(0.f, (float)x, (float)(x * x), 1.f);
+            tab[2 * j + 1] = make_float4((float)psi[0], (float)psi[1], (float)psi[2], 0.f);
+        }
+    }
+    LineSet ls;
+    ls.c0 = first;
+    ls.n_pts = n_pts;
+    ls.cs = first & ~15;
+    ls.ce = std::min((last + 1 + 15) & ~15, c->N_pad);
+    DSPS_CUDA(cudaSetDevice(c->device));
+    if (dmalloc(&ls.d_tab, tab.size()) != DSPS_OK) return DSPS_ERR_CUDA;
+    cudaError_t e = cudaMemcpy(ls.d_tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(ls.d_tab);
+        return cuda_fail(e, "dsps_line_add upload");
+    }
+    *line_id = (int32_t)c->lines.size();
+    c->lines.push_back(ls);
+    return DSPS_OK;
+}
+
+int dsps_line_ew(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line_id, float *ew,
+                 dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || n_gal < 0 || (n_gal > 0 && (!params || !ew))) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew: bad argument%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (line_id < 0 || line_id >= (int)c->lines.size()) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew: unknown line%s");
+    if (n_gal == 0) return DSPS_OK;
+    DSPS_CUDA(cudaSetDevice(c->device));
+    const int rc = ensure_shat(c);
+    if (rc != DSPS_OK) return rc;
+    return run_line_ew_ws(c, c->ws, n_gal, params, c->lines[line_id], nullptr, ew, nullptr,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+int dsps_line_ew_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line_id, const float *ew_bar,
+                     float *ew, float *param_bar, dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || n_gal < 0 || (n_gal > 0 && (!params || !ew_bar || !param_bar)))
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew_vjp: bad argument%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (line_id < 0 || line_id >= (int)c->lines.size()) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew_vjp: unknown line%s");
+    if (n_gal == 0) return DSPS_OK;
+    DSPS_CUDA(cudaSetDevice(c->device));
+    const int rc = ensure_shat(c);
+    if (rc != DSPS_OK) return rc;
+    return run_line_ew_ws(c, c->ws, n_gal, params, c->lines[line_id], ew_bar, ew, param_bar,
+                          reinterpret_cast<cudaStream_t>(stream));
 }
 
 int dsps_submit(dsps_ctx *ctx, const dsps_request *req, uint64_t *ticket) {

@@ -133,6 +133,20 @@ int run_photometry_vjp_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const floa
     return DSPS_OK;
 }
 
+int ensure_shat(Ctx *c) {
+    if (c->ws.shat) return DSPS_OK;
+    // [chunk][N_pad] x 4 bytes, made on the first call that needs it: Shat of
+    // the adjoint (FP32, or bf16 hi + lo), the window spectra of the line widths.
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, (size_t)c->chunk * c->N_pad * 4);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DSPS_ERR_CUDA;
+    }
+    c->ws.shat = p;
+    return DSPS_OK;
+}
+
 int run_photometry(Ctx *c, int64_t n_gal, const float *params, int32_t set_id, int32_t precision, float *mags,
                    cudaStream_t s) {
     if (n_gal < 0 || (n_gal > 0 && (!params || !mags))) {
@@ -168,16 +182,8 @@ int run_photometry_vjp(Ctx *c, int64_t n_gal, const float *params, int32_t set_i
     }
     if (n_gal == 0) return DSPS_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return DSPS_ERR_CUDA;
-    if (!c->ws.shat) {
-        // Adjoint work space, made on the first gradient call (FP32, or bf16 hi + lo).
-        void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, (size_t)c->chunk * c->N_pad * 4);
-        if (e != cudaSuccess) {
-            set_last_error(cudaGetErrorString(e));
-            return DSPS_ERR_CUDA;
-        }
-        c->ws.shat = p;
-    }
+    const int rc = ensure_shat(c);
+    if (rc != DSPS_OK) return rc;
     return run_photometry_vjp_ws(c, c->ws, n_gal, params, c->sets[set_id], precision, mag_bar, mags, param_bar, s,
                                  true);
 }

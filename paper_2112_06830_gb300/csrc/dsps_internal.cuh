@@ -80,6 +80,18 @@ struct FilterSet {
     float *d_offq = nullptr;   // [Q] 2.5 log10(AB0 D_q)
 };
 
+// A registered emission line (spectrum.cu): the window of grid columns
+// [c0, c0 + n_pts) holding its continuum and line points, and per point j
+// two float4: {t_j, x_j, x_j^2, 1 for a continuum point} and {psi_j, 0} with
+// t_j the trapezoid weight of a line point (0 for continuum points), x_j =
+// (lam_j - lam_line) / (half_width + cont_width), and psi_j = M^-1 (1, x_j,
+// x_j^2) the fit operator of a continuum point (0 for line points).
+struct LineSet {
+    int c0 = 0, n_pts = 0;
+    int cs = 0, ce = 0;        // [c0, c0 + n_pts) widened to multiples of 16 columns
+    float4 *d_tab = nullptr;   // [n_pts][2]
+};
+
 struct Serve;  // request loop (serve.cu)
 
 // Colour-cut histogram of the magnitudes (dsps.h: dsps_hist_spec), as used by
@@ -164,6 +176,8 @@ struct Ctx {
     unsigned *d_err = nullptr;              // sticky error word
 
     std::vector<FilterSet> sets;
+    std::vector<LineSet> lines;
+    std::vector<double> h_lam;              // [n_lam] the caller's rest wavelengths [A]
     std::mutex mu;
     Serve *serve = nullptr;
 
@@ -251,7 +265,9 @@ cudaError_t launch_combine_grad(const Ctx &c, const Workspace &w, const FilterSe
                                 int64_t g_begin, cudaStream_t s);
 cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, bool bf16, bool band,
                         cudaStream_t s);
-cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s);
+// col0/col1: the Shat columns that take part (multiples of 16; 0, N_pad for all).
+cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s, int col0 = 0,
+                            int col1 = -1);
 cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, cudaStream_t s);
 cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride,
                                int64_t g_begin, int64_t n, bool sorted, bool scaled, float *param_bar,
@@ -261,6 +277,13 @@ cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *pa
 // (dispatch.cu); mags/param_bar are the caller's device pointers.
 int run_photometry_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
                       int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist = nullptr);
+// Allocates ctx.ws.shat if it is not there yet (dispatch.cu).
+int ensure_shat(Ctx *c);
+// Spectra and line widths (spectrum.cu); w.shat must be allocated.
+int run_spectra_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, int n0, int n1, float *out,
+                   cudaStream_t s);
+int run_line_ew_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const LineSet &ls,
+                   const float *ew_bar, float *ew, float *param_bar, cudaStream_t s);
 int run_photometry_vjp_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
                           int32_t precision, const float *mag_bar, float *mags, float *param_bar, cudaStream_t s,
                           bool profile);

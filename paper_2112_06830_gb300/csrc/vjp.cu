@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 
 constexpr int BM = 128, BN = 128, BK = 16, THREADS = 256, AS_LD = BM + 4;
 
 __global__ void __launch_bounds__(THREADS, 2) vjp_simt_kernel(const float *A, const float *B, int64_t n, int K_pad,
-                                                              int N_pad, float *C) {
+                                                              int N_pad, int col0, int col1, float *C) {
     __shared__ __align__(16) float As[2][BK][AS_LD];
     __shared__ __align__(16) float Bs[2][BK][AS_LD];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -170,13 +170,14 @@ __global__ void __launch_bounds__(THREADS, 2) vjp_simt_kernel(const float *A, co
             Bs[buf][q + 3][row] = rb[t].w;
         }
     };
-    const int KT = N_pad / BK;
-    gload(0);
+    // contraction over the Shat columns [col0, col1) (multiples of BK)
+    const int KT = (col1 - col0) / BK;
+    gload(col0);
     sstore(0);
     __syncthreads();
     for (int kt = 0; kt < KT; ++kt) {
         const int buf = kt & 1;
-        if (kt + 1 < KT) gload((kt + 1) * BK);
+        if (kt + 1 < KT) gload(col0 + (kt + 1) * BK);
 #pragma unroll
         for (int k = 0; k < BK; ++k) {
             const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
@@ -257,11 +258,13 @@ cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s) {
+cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s, int col0, int col1) {
     if (n <= 0) return cudaSuccess;
+    if (col1 < 0) col1 = c.N_pad;
+    if (col0 < 0 || col1 > c.N_pad || col0 % BK || col1 % BK || col1 <= col0) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((n + BM - 1) / BM), (unsigned)((c.KZ_pad + BN - 1) / BN));
     vjp_simt_kernel<<<grid, THREADS, 0, s>>>(reinterpret_cast<const float *>(w.shat), c.d_Ld32, n, c.KZ_pad,
-                                             c.N_pad, w.w32);
+                                             c.N_pad, col0, col1, w.w32);
     return cudaGetLastError();
 }
 

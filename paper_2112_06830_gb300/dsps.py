@@ -72,6 +72,13 @@ class dsps_hist_spec(C.Structure):
                 ("lo", C.c_float), ("hi", C.c_float), ("n_bins", C.c_int32)]
 
 
+DSPS_MAX_LINE_POINTS = 4096
+
+
+class dsps_line_spec(C.Structure):
+    _fields_ = [("lam_line", C.c_double), ("half_width", C.c_double), ("cont_width", C.c_double)]
+
+
 class dsps_request(C.Structure):
     _fields_ = [("n_gal", C.c_int64), ("params", C.c_void_p), ("set_id", C.c_int32),
                 ("precision", C.c_int32), ("want_grad", C.c_int32), ("mag_bar", C.c_void_p),
@@ -101,6 +108,11 @@ _SIGS = [
                                             C.POINTER(dsps_hist_spec), C.c_void_p, C.c_void_p]),
     ("dsps_histogram", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.POINTER(dsps_hist_spec),
                                  C.c_void_p, C.c_void_p]),
+    ("dsps_spectra", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("dsps_line_add", C.c_int, [C.c_void_p, C.POINTER(dsps_line_spec), C.POINTER(C.c_int32)]),
+    ("dsps_line_ew", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("dsps_line_ew_vjp", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p]),
     ("dsps_submit", C.c_int, [C.c_void_p, C.POINTER(dsps_request), C.POINTER(C.c_uint64)]),
     ("dsps_poll", C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(C.c_double)]),
     ("dsps_device_error", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -212,6 +224,25 @@ def dsps_photometry_fp32_static(ctx, n_gal, params_ptr, set_id, mags_ptr, stream
     """FP32 photometry with no device allocation (fixed in-library scratch)."""
     return _check(load().dsps_photometry_fp32_static(ctx, n_gal, params_ptr, set_id, mags_ptr, stream),
                   "dsps_photometry_fp32_static")
+
+
+def dsps_spectra(ctx, n_gal, params_ptr, n0, n1, out_ptr, stream=0):
+    return _check(load().dsps_spectra(ctx, n_gal, params_ptr, n0, n1, out_ptr, stream), "dsps_spectra")
+
+
+def dsps_line_add(ctx, spec: dsps_line_spec):
+    lid = C.c_int32(-1)
+    _check(load().dsps_line_add(ctx, C.byref(spec), C.byref(lid)), "dsps_line_add")
+    return lid.value
+
+
+def dsps_line_ew(ctx, n_gal, params_ptr, line_id, ew_ptr, stream=0):
+    return _check(load().dsps_line_ew(ctx, n_gal, params_ptr, line_id, ew_ptr, stream), "dsps_line_ew")
+
+
+def dsps_line_ew_vjp(ctx, n_gal, params_ptr, line_id, ew_bar_ptr, ew_ptr, param_bar_ptr, stream=0):
+    return _check(load().dsps_line_ew_vjp(ctx, n_gal, params_ptr, line_id, ew_bar_ptr, ew_ptr, param_bar_ptr,
+                                          stream), "dsps_line_ew_vjp")
 
 
 def dsps_submit(ctx, req: dsps_request):
@@ -361,6 +392,39 @@ class Context:
         dsps_histogram(self.handle, mags.shape[0], mags.data_ptr(), mags.shape[1], spec, counts.data_ptr(),
                        _stream_handle(stream))
         return counts
+
+    def spectra(self, params, n0, n1, stream=None):
+        """Rest-frame attenuated spectra [G, n1 - n0] on grid columns [n0, n1)."""
+        import torch
+        params = params.contiguous()
+        G = params.shape[1]
+        out = torch.empty((G, n1 - n0), dtype=torch.float32, device=params.device)
+        dsps_spectra(self.handle, G, params.data_ptr(), n0, n1, out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def add_line(self, lam_line, half_width, cont_width) -> int:
+        return dsps_line_add(self.handle, dsps_line_spec(float(lam_line), float(half_width), float(cont_width)))
+
+    def line_ew(self, params, line_id, stream=None):
+        """Equivalent widths [G] [A] of a registered line."""
+        import torch
+        params = params.contiguous()
+        G = params.shape[1]
+        ew = torch.empty(G, dtype=torch.float32, device=params.device)
+        dsps_line_ew(self.handle, G, params.data_ptr(), line_id, ew.data_ptr(), _stream_handle(stream))
+        return ew
+
+    def line_ew_vjp(self, params, line_id, ew_bar, stream=None):
+        """(ew [G], param_bar [11, G]) with param_bar = ew_bar dW/dparams."""
+        import torch
+        params = params.contiguous()
+        ew_bar = ew_bar.contiguous().to(torch.float32)
+        G = params.shape[1]
+        ew = torch.empty(G, dtype=torch.float32, device=params.device)
+        pbar = torch.empty((DSPS_NGRAD, G), dtype=torch.float32, device=params.device)
+        dsps_line_ew_vjp(self.handle, G, params.data_ptr(), line_id, ew_bar.data_ptr(), ew.data_ptr(),
+                         pbar.data_ptr(), _stream_handle(stream))
+        return ew, pbar
 
     def device_error(self, stream=None):
         return dsps_device_error(self.handle, _stream_handle(stream))
