@@ -50,7 +50,7 @@ class _Grid(C.Structure):
                 ("om0", C.c_double), ("w0", C.c_double), ("h", C.c_double),
                 ("sfh_model", C.c_int), ("mdf_kernel", C.c_int),
                 ("mdf_mean", C.c_int), ("mdf_x0", C.c_double), ("mdf_h", C.c_double),
-                ("dust_bump", C.c_int)]
+                ("dust_bump", C.c_int), ("n_u", C.c_int), ("lgu", C.POINTER(C.c_double))]
 
 
 class _Filters(C.Structure):
@@ -84,6 +84,8 @@ def _load():
             lib.orc_mdf_mean.restype = C.c_double
             lib.orc_mdf_mean.argtypes = [C.POINTER(_Grid), dp, C.c_int, dp, dp]
             lib.orc_dust_trans.restype = C.c_double
+            lib.orc_pneb.argtypes = [C.POINTER(_Grid), C.c_double, C.c_double, dp, dp, dp]
+            lib.orc_pneb.restype = None
             lib.orc_dust_trans.argtypes = [C.c_double] * 3
             lib.orc_drude.restype = C.c_double
             lib.orc_drude.argtypes = [C.c_double]
@@ -121,11 +123,13 @@ class Grid:
 
     def __init__(self, log_age_yr, lgz, lam, l_ssp, t0=0.05, t1=13.8, n_t=200,
                  om0=0.3, w0=-1.0, h=0.7, sfh_model=0, mdf_kernel=0, mdf_mean=0, mdf_x0=9.0, mdf_h=0.5,
-                 dust_bump=0):
+                 dust_bump=0, lgu=None):
         self.log_age_yr = _f64(log_age_yr)
         self.lgz = _f64(lgz)
         self.lam = _f64(lam)
-        self.l_ssp = _f64(l_ssp).reshape(len(self.log_age_yr), len(self.lgz), len(self.lam))
+        self.lgu = _f64(lgu) if lgu is not None and len(lgu) > 1 else None
+        nu = len(self.lgu) if self.lgu is not None else 1
+        self.l_ssp = _f64(l_ssp).reshape(len(self.log_age_yr), len(self.lgz), nu, len(self.lam))
         self.t0, self.t1, self.n_t = float(t0), float(t1), int(n_t)
         self.om0, self.w0, self.h = float(om0), float(w0), float(h)
         self.sfh_model, self.mdf_kernel = int(sfh_model), int(mdf_kernel)
@@ -134,7 +138,8 @@ class Grid:
         self._c = _Grid(len(self.log_age_yr), len(self.lgz), len(self.lam), _dp(self.log_age_yr),
                         _dp(self.lgz), _dp(self.lam), _dp(self.l_ssp), self.t0, self.t1, self.n_t,
                         self.om0, self.w0, self.h, self.sfh_model, self.mdf_kernel,
-                        self.mdf_mean, self.mdf_x0, self.mdf_h, self.dust_bump)
+                        self.mdf_mean, self.mdf_x0, self.mdf_h, self.dust_bump, nu,
+                        _dp(self.lgu) if self.lgu is not None else None)
 
     @property
     def n_age(self):
@@ -147,6 +152,18 @@ class Grid:
     @property
     def n_lam(self):
         return len(self.lam)
+
+    @property
+    def n_u(self):
+        return len(self.lgu) if self.lgu is not None else 1
+
+    @property
+    def npar(self):
+        return NPAR + 2 if self.n_u > 1 else NPAR
+
+    @property
+    def ngrad(self):
+        return NGRAD + 2 if self.n_u > 1 else NGRAD
 
 
 class Filters:
@@ -233,6 +250,14 @@ def mdf_mean(grid: Grid, params, i):
     return mu, float(d5[0]), float(d7[0])
 
 
+def pneb(grid: Grid, u_mean, u_sigma):
+    """(P[n_u], dP/du_mean, dP/du_sigma) of the nebular log U bins (Eq. nebsed)."""
+    n = grid.n_u
+    P, d1, d2 = np.zeros(n), np.zeros(n), np.zeros(n)
+    _load().orc_pneb(C.byref(grid._c), float(u_mean), float(u_sigma), _dp(P), _dp(d1), _dp(d2))
+    return P, d1, d2
+
+
 def mdf(grid: Grid, mu_i, sigma):
     P, dmu, dsig = np.zeros(grid.n_z), np.zeros(grid.n_z), np.zeros(grid.n_z)
     _load().orc_mdf(C.byref(grid._c), float(mu_i), float(sigma), _dp(P), _dp(dmu), _dp(dsig))
@@ -286,10 +311,10 @@ def mags_from_weights(grid: Grid, filters: Filters, omega, Av, delta, logM, z, d
 # ---- batched entry points ---------------------------------------------------
 
 def weights(grid: Grid, params, nthreads=None):
-    """SSP weights in Msun, shape [G, n_age, n_z]."""
+    """SSP weights in Msun, shape [G, n_age, n_z] (or [G, n_age, n_z, n_u])."""
     p = _f64(params)
     G = p.shape[1]
-    out = np.zeros((G, grid.n_age, grid.n_z))
+    out = np.zeros((G, grid.n_age, grid.n_z) + ((grid.n_u,) if grid.n_u > 1 else ()))
     _load().orc_weights(C.byref(grid._c), G, _dp(p), _dp(out), _nthreads(nthreads))
     return out
 
@@ -309,7 +334,7 @@ def mags_vjp(grid: Grid, filters: Filters, params, mag_bar, nthreads=None):
     G = p.shape[1]
     mb = _f64(mag_bar).reshape(G, filters.n_filt)
     m = np.zeros((G, filters.n_filt))
-    pb = np.zeros((NGRAD, G))
+    pb = np.zeros((grid.ngrad, G))
     _load().orc_mags_vjp(C.byref(grid._c), C.byref(filters._c), G, _dp(p), _dp(mb), _dp(m), _dp(pb),
                          _nthreads(nthreads))
     return m, pb
@@ -353,7 +378,7 @@ def line_ew_vjp(grid: Grid, params, ew_bar, lam_c, half_width, cont_width, nthre
     G = p.shape[1]
     eb = _f64(ew_bar).reshape(G)
     ew = np.zeros(G)
-    pb = np.zeros((NGRAD, G))
+    pb = np.zeros((grid.ngrad, G))
     ln = _Line(float(lam_c), float(half_width), float(cont_width))
     _load().orc_line_ew(C.byref(grid._c), C.byref(ln), G, _dp(p), _dp(eb), _dp(ew), _dp(pb),
                         _nthreads(nthreads))

@@ -25,7 +25,11 @@
  *   row 9      dust delta
  *   row 10     logM       log10 of the stellar mass formed by t_obs [Msun]
  *   row 11     z          redshift
- * Gradient layout (11 rows): rows 0..10 of the above (z gets no gradient).
+ *   rows 12,13 (grids with a nebular axis, n_u > 1 log U values, Sec. 3.3)
+ *              u_mean, u_sigma: mean and width [dex] of the triweight
+ *              distribution of log10 U
+ * Gradient layout (11 rows): rows 0..10 of the above (z gets no gradient);
+ * with a nebular axis 13 rows, rows 11, 12 = u_mean, u_sigma.
  *
  * Besides the magnitudes, the oracle gives the rest-frame attenuated spectrum
  * and the equivalent width of an emission line (Sec. 2.2, Eq. eqw) with their
@@ -38,6 +42,8 @@
 
 #define ORC_NPAR 12
 #define ORC_NGRAD 11
+#define ORC_NPAR_MAX 14              /* with the nebular axis (rows 12, 13) */
+#define ORC_NGRAD_MAX 13
 #define ORC_AB0 1.13492e-13          /* Sec. 2.2, Eq. (restmag): AB zero point at 10 pc, Lsun/Hz */
 #define ORC_LAMV 5500.0              /* Sec. 3.4, Eq. (salim): lambda_V in Angstrom */
 #define ORC_SIGQ 0.3                 /* width of the quench transition [Gyr] (reading) */
@@ -58,7 +64,14 @@ typedef struct {
     int mdf_mean;              /* 0 linear in log age, 1 T_erf transition  */
     double mdf_x0, mdf_h;      /* transition centre [log10 yr] and width   */
     int dust_bump;             /* 1: add the 2175 A Drude bump (Eq. uvbump) */
+    int n_u;                   /* log U values of the nebular axis (<= 1: none) */
+    const double *lgu;         /* [n_u] log10 U, increasing; l_ssp is then
+                                  [n_age][n_z][n_u][n_lam]                  */
 } orc_grid;
+
+static int orc_nu(const orc_grid *g) { return g->n_u > 1 ? g->n_u : 1; }
+static int orc_npar(const orc_grid *g) { return g->n_u > 1 ? ORC_NPAR_MAX : ORC_NPAR; }
+static int orc_ngrad(const orc_grid *g) { return g->n_u > 1 ? ORC_NGRAD_MAX : ORC_NGRAD; }
 
 typedef struct {
     int n_filt;
@@ -313,6 +326,38 @@ double orc_mdf_mean(const orc_grid *g, const double *par, int i, double *d5, dou
     return par[5] + par[7] * (x - 9.0);
 }
 
+/* Sec. 3.3, Eq. (nebsed): probability of log U bin k for a galaxy whose
+ * log10 U follows the triweight kernel of mean us and width su (Appendix B),
+ * P[k] = T_erf((E_{k+1} - us)/su) - T_erf((E_k - us)/su), with bin edges at
+ * grid midpoints and outer edges at -inf/+inf (reading, as for the MDF), and
+ * its derivatives in us and su.  Without a nebular axis P = {1}. */
+void orc_pneb(const orc_grid *g, double us, double su, double *P, double *dP_dus, double *dP_dsu)
+{
+    int nu = orc_nu(g);
+    if (nu == 1) {
+        P[0] = 1.0;
+        if (dP_dus) dP_dus[0] = 0.0;
+        if (dP_dsu) dP_dsu[0] = 0.0;
+        return;
+    }
+    for (int k = 0; k < nu; ++k) {
+        double c_hi = 1.0, c_lo = 0.0, d_hi = 0.0, d_lo = 0.0, x_hi = 0.0, x_lo = 0.0;
+        if (k < nu - 1) {
+            x_hi = (0.5 * (g->lgu[k] + g->lgu[k + 1]) - us) / su;
+            c_hi = orc_triweight_cdf(x_hi);
+            d_hi = orc_triweight_pdf(x_hi);
+        }
+        if (k > 0) {
+            x_lo = (0.5 * (g->lgu[k - 1] + g->lgu[k]) - us) / su;
+            c_lo = orc_triweight_cdf(x_lo);
+            d_lo = orc_triweight_pdf(x_lo);
+        }
+        P[k] = c_hi - c_lo;
+        if (dP_dus) dP_dus[k] = -(d_hi - d_lo) / su;
+        if (dP_dsu) dP_dsu[k] = -(d_hi * x_hi - d_lo * x_lo) / su;
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 3.4: power-law dust attenuation (Eq. attenuation, simplified   */
 /* Eq. salim with k = 1 at lambda_V: A_lambda = Av (lam/5500)^(-0.7+d)) */
@@ -403,7 +448,7 @@ void orc_mags_from_weights(const orc_grid *g, const orc_filters *f, const double
                            double Av, double delta, double logM, double z, double dmod,
                            double *mags)
 {
-    int N = g->n_lam, K = g->n_age * g->n_z;
+    int N = g->n_lam, K = g->n_age * g->n_z * orc_nu(g);
     double *S = calloc(N, sizeof(double));
     for (int k = 0; k < K; ++k) {
         double w = omega[k];
@@ -431,21 +476,26 @@ void orc_mags_from_weights(const orc_grid *g, const orc_filters *f, const double
 }
 
 /* Joint SSP weights of one galaxy, per unit formed mass:
- * omega[i][j] = frac_i * P[j | i]   (Eq. agedep_mdf). */
-static void galaxy_weights(const orc_grid *g, const double *par /* 12 */, double t_obs, double *omega)
+ * omega[i][j] = frac_i * P[j | i]   (Eq. agedep_mdf), and with a nebular axis
+ * omega[i][j][k] = frac_i * P[j | i] * P_neb[k]   (Eq. nebsed). */
+static void galaxy_weights(const orc_grid *g, const double *par, double t_obs, double *omega)
 {
+    int nu = orc_nu(g);
     double *sfr = malloc(sizeof(double) * g->n_t);
     double *frac = malloc(sizeof(double) * g->n_age);
     double *P = malloc(sizeof(double) * g->n_z);
+    double *Pu = malloc(sizeof(double) * nu);
     double h = (g->t1 - g->t0) / (g->n_t - 1);
     for (int n = 0; n < g->n_t; ++n) sfr[n] = orc_sfr(g->sfh_model, par, g->t0 + n * h, NULL);
     orc_age_fracs_from_sfr(g, sfr, t_obs, frac);
+    orc_pneb(g, nu > 1 ? par[12] : 0.0, nu > 1 ? par[13] : 1.0, Pu, NULL, NULL);
     for (int i = 0; i < g->n_age; ++i) {
         double mu_i = orc_mdf_mean(g, par, i, NULL, NULL);
         orc_mdf(g, mu_i, par[6], P, NULL, NULL);
-        for (int j = 0; j < g->n_z; ++j) omega[i * g->n_z + j] = frac[i] * P[j];
+        for (int j = 0; j < g->n_z; ++j)
+            for (int k = 0; k < nu; ++k) omega[(i * g->n_z + j) * nu + k] = frac[i] * P[j] * Pu[k];
     }
-    free(P); free(frac); free(sfr);
+    free(Pu); free(P); free(frac); free(sfr);
 }
 
 /* ------------------------------------------------------------------ */
@@ -460,13 +510,14 @@ typedef struct {
     double *frac;              /* [n_age]                                            */
     double *P, *dPmu, *dPsig;  /* [n_age][n_z] MDF bin probabilities and derivatives */
     double *dmu5, *dmu7;       /* [n_age] d mu_i / d p5, d p7                       */
+    double *Pu, *dPu_us, *dPu_su; /* [n_u] nebular bin probabilities and derivatives */
     double *S;                 /* [n_lam] sum_ij omega_ij L_ijn (per unit mass)      */
     double *F, *u, *du;        /* [n_lam] dust transmission, A/Av, d(A/Av)/d delta   */
 } gal_state;
 
 static void gal_forward(const orc_grid *g, const double *par, double t_obs, gal_state *st)
 {
-    int N = g->n_lam, NA = g->n_age, NZ = g->n_z, K = NA * NZ, NT = g->n_t;
+    int N = g->n_lam, NA = g->n_age, NZ = g->n_z, NU = orc_nu(g), K = NA * NZ * NU, NT = g->n_t;
     double Av = par[8], delta = par[9];
     double h = (g->t1 - g->t0) / (NT - 1);
     st->sfr = malloc(sizeof(double) * NT);
@@ -488,9 +539,13 @@ static void gal_forward(const orc_grid *g, const double *par, double t_obs, gal_
         double mu_i = orc_mdf_mean(g, par, i, st->dmu5 + i, st->dmu7 + i);
         orc_mdf(g, mu_i, par[6], st->P + i * NZ, st->dPmu + i * NZ, st->dPsig + i * NZ);
     }
+    st->Pu = malloc(sizeof(double) * NU);
+    st->dPu_us = malloc(sizeof(double) * NU);
+    st->dPu_su = malloc(sizeof(double) * NU);
+    orc_pneb(g, NU > 1 ? par[12] : 0.0, NU > 1 ? par[13] : 1.0, st->Pu, st->dPu_us, st->dPu_su);
     st->S = calloc(N, sizeof(double));
     for (int k = 0; k < K; ++k) {
-        double w = st->frac[k / NZ] * st->P[k];
+        double w = st->frac[k / (NZ * NU)] * st->P[k / NU] * st->Pu[k % NU];
         const double *L = g->l_ssp + (size_t)k * N;
         for (int n = 0; n < N; ++n) st->S[n] += w * L[n];
     }
@@ -506,28 +561,38 @@ static void gal_forward(const orc_grid *g, const double *par, double t_obs, gal_
 static void gal_free(gal_state *st)
 {
     free(st->du); free(st->u); free(st->F); free(st->S); free(st->dmu7); free(st->dmu5);
+    free(st->Pu); free(st->dPu_us); free(st->dPu_su);
     free(st->dPsig); free(st->dPmu); free(st->P); free(st->frac); free(st->Mhi); free(st->e);
     free(st->dsfr); free(st->sfr);
 }
 
 /* Reverse of the weights and the contraction: given Sbar_n = dLoss/dS_n (S the
- * per-unit-mass spectrum before dust), adds dLoss/dp_k for k = 0..7 to pbar. */
+ * per-unit-mass spectrum before dust), adds dLoss/dp_k for k = 0..7 to pbar
+ * (and 11, 12 with a nebular axis). */
 static void gal_reverse_sbar(const orc_grid *g, const gal_state *st, double t_obs, const double *Sbar,
                              double *pbar)
 {
-    int N = g->n_lam, NA = g->n_age, NZ = g->n_z, K = NA * NZ, NT = g->n_t;
+    int N = g->n_lam, NA = g->n_age, NZ = g->n_z, NU = orc_nu(g), K = NA * NZ * NU, NT = g->n_t;
     double *fracbar = calloc(NA, sizeof(double));
+    double *Pubar = calloc(NU, sizeof(double));
     for (int k = 0; k < K; ++k) {
         const double *L = g->l_ssp + (size_t)k * N;
         double wbar = 0.0;
         for (int n = 0; n < N; ++n) wbar += Sbar[n] * L[n];
-        int i = k / NZ;
-        fracbar[i] += wbar * st->P[k];
-        double Pbar = wbar * st->frac[i];
-        pbar[5] += Pbar * st->dPmu[k] * st->dmu5[i];
-        pbar[6] += Pbar * st->dPsig[k];
-        pbar[7] += Pbar * st->dPmu[k] * st->dmu7[i];
+        int ij = k / NU, u = k % NU, i = ij / NZ;
+        fracbar[i] += wbar * st->P[ij] * st->Pu[u];
+        double Pbar = wbar * st->frac[i] * st->Pu[u];
+        pbar[5] += Pbar * st->dPmu[ij] * st->dmu5[i];
+        pbar[6] += Pbar * st->dPsig[ij];
+        pbar[7] += Pbar * st->dPmu[ij] * st->dmu7[i];
+        Pubar[u] += wbar * st->frac[i] * st->P[ij];
     }
+    if (NU > 1)
+        for (int u = 0; u < NU; ++u) {
+            pbar[11] += Pubar[u] * st->dPu_us[u];
+            pbar[12] += Pubar[u] * st->dPu_su[u];
+        }
+    free(Pubar);
     /* frac_i = (Mhi_i - Mhi_{i+1}) / Mtot with Mtot = Mhi_0 */
     double *Mbar = calloc(NA + 1, sizeof(double));
     for (int i = 0; i < NA; ++i) {
@@ -548,7 +613,7 @@ static void gal_reverse_sbar(const orc_grid *g, const gal_state *st, double t_ob
 }
 
 static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const double *par, double t_obs,
-                            double dmod, const double *mbar, double *mags, double *pbar /* 11 */)
+                            double dmod, const double *mbar, double *mags, double *pbar /* 11, or 13 */)
 {
     int N = g->n_lam, Q = f->n_filt;
     double Av = par[8], logM = par[10], z = par[11];
@@ -571,7 +636,7 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
     }
 
     /* reverse sweep */
-    for (int k = 0; k < ORC_NGRAD; ++k) pbar[k] = 0.0;
+    for (int k = 0; k < orc_ngrad(g); ++k) pbar[k] = 0.0;
     double *Nbar = malloc(sizeof(double) * Q);
     for (int q = 0; q < Q; ++q) {
         pbar[10] += -2.5 * mbar[q];
@@ -724,7 +789,7 @@ static double galaxy_ew(const orc_grid *g, const orc_line *ln, const double *par
     for (int n = 0; n < N; ++n) L[n] = M * st.F[n] * st.S[n];
     double W = orc_ew_from_spectrum(g->lam, L, N, ln, pbar ? Lbar : NULL);
     if (pbar) {
-        for (int k = 0; k < ORC_NGRAD; ++k) pbar[k] = 0.0;
+        for (int k = 0; k < orc_ngrad(g); ++k) pbar[k] = 0.0;
         double *Sbar = malloc(sizeof(double) * N);
         for (int n = 0; n < N; ++n) {
             double lb = ewbar * Lbar[n];
@@ -760,11 +825,11 @@ static void *orc_worker(void *arg)
 {
     orc_job *j = (orc_job *)arg;
     const orc_grid *g = j->g;
-    int K = g->n_age * g->n_z;
-    double par[ORC_NPAR];
+    int K = g->n_age * g->n_z * orc_nu(g), npar = orc_npar(g), ngrad = orc_ngrad(g);
+    double par[ORC_NPAR_MAX];
     double *omega = malloc(sizeof(double) * K);
     for (long gi = j->begin; gi < j->end; ++gi) {
-        for (int r = 0; r < ORC_NPAR; ++r) par[r] = j->params[(size_t)r * j->n_gal + gi];
+        for (int r = 0; r < npar; ++r) par[r] = j->params[(size_t)r * j->n_gal + gi];
         double z = par[11];
         double t_obs = orc_age_gyr(g->om0, g->w0, g->h, z);
         if (j->mode == 0) {
@@ -779,16 +844,16 @@ static void *orc_worker(void *arg)
         } else if (j->mode == 3) {
             galaxy_spectrum(g, par, t_obs, j->out + (size_t)gi * g->n_lam);
         } else if (j->mode == 4) {
-            double pb[ORC_NGRAD];
+            double pb[ORC_NGRAD_MAX];
             j->out[gi] = galaxy_ew(g, j->line, par, t_obs, j->mbar ? j->mbar[gi] : 0.0, j->pbar ? pb : NULL);
             if (j->pbar)
-                for (int k = 0; k < ORC_NGRAD; ++k) j->pbar[(size_t)k * j->n_gal + gi] = pb[k];
+                for (int k = 0; k < ngrad; ++k) j->pbar[(size_t)k * j->n_gal + gi] = pb[k];
         } else {
             double dmod = orc_dist_mod(g->om0, g->w0, g->h, z);
-            double pb[ORC_NGRAD];
+            double pb[ORC_NGRAD_MAX];
             galaxy_mags_vjp(g, j->f, par, t_obs, dmod, j->mbar + (size_t)gi * j->f->n_filt,
                             j->mags ? j->mags + (size_t)gi * j->f->n_filt : NULL, pb);
-            for (int k = 0; k < ORC_NGRAD; ++k) j->pbar[(size_t)k * j->n_gal + gi] = pb[k];
+            for (int k = 0; k < ngrad; ++k) j->pbar[(size_t)k * j->n_gal + gi] = pb[k];
         }
     }
     free(omega);

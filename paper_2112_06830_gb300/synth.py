@@ -17,7 +17,8 @@ synthetic stand-ins):
 * ``serve``   Poisson request stream over the ``full`` grid.
 
 Parameter rows (structure of arrays, ``params[12, G]`` float):
-    0..4 SFH, 5 mdf_mu, 6 mdf_sigma, 7 mdf_slope, 8 Av, 9 delta, 10 logM, 11 z.
+    0..4 SFH, 5 mdf_mu, 6 mdf_sigma, 7 mdf_slope, 8 Av, 9 delta, 10 logM, 11 z;
+    with a nebular axis ``params[14, G]``: 12 u_mean, 13 u_sigma.
 """
 from __future__ import annotations
 
@@ -82,10 +83,11 @@ class SSPGrid:
     log_age_yr: np.ndarray   # [n_age] float64
     lgz: np.ndarray          # [n_z]   float64, log10(Z/0.019)
     lam: np.ndarray          # [n_lam] float64, Angstrom
-    l_ssp: np.ndarray        # [n_age, n_z, n_lam] float32, Lsun/Hz/Msun
+    l_ssp: np.ndarray        # [n_age, n_z, n_lam] (or [n_age, n_z, n_u, n_lam]) float32, Lsun/Hz/Msun
     t0: float
     t1: float
     n_t: int
+    lgu: np.ndarray | None = None   # [n_u] log10 U of the nebular axis, or None
 
 
 def _planck_lambda(lam_aa: np.ndarray, T: np.ndarray) -> np.ndarray:
@@ -130,6 +132,53 @@ def with_emission_line(ssp: SSPGrid, lam_line: float = 5007.0, sigma: float = 8.
     base = ssp.l_ssp.astype(np.float64)
     add = a[:, None, None] * base[:, :, n_l:n_l + 1] * prof[None, None, :]
     return SSPGrid(ssp.log_age_yr, ssp.lgz, lam, (base + add).astype(np.float32), ssp.t0, ssp.t1, ssp.n_t)
+
+
+# Nebular axis (Sec. 3.3): log U grid of the stand-in SSPs (FSPS's range and step).
+LGU_GRID = np.linspace(-4.0, -1.0, 7)
+NPAR_NEB = NPAR + 2
+
+
+def make_ssp_nebular(spec: GridSpec, seed: int, lgu=LGU_GRID, age_scale: float = 5e6) -> SSPGrid:
+    """SSP block with a nebular axis, l_ssp [n_age, n_z, n_u, n_lam]: the
+    continuum of ``make_ssp`` (the same for every U) plus Gaussian emission
+    lines on the young populations whose strengths depend on the ionisation
+    parameter u = log10 U, standing in for FSPS's nebular lines: a 5007 A line
+    growing with u (amplitude 10 * 10^(0.6 (u + 2.5))), a 3727 A line falling
+    with u (8 * 10^(-0.4 (u + 2.5))) and a 6563 A line independent of u (20),
+    each times a_i = 1 / (1 + (age_i / age_scale)^2) and the row's continuum at
+    the line (sigma 8 A)."""
+    base = make_ssp(spec, seed)
+    lam = base.lam
+    lgu = np.asarray(lgu, dtype=np.float64)
+    age = 10.0 ** base.log_age_yr
+    a = 1.0 / (1.0 + (age / age_scale) ** 2)
+    cont = base.l_ssp.astype(np.float64)
+    out = np.repeat(cont[:, :, None, :], len(lgu), axis=2)
+    for lam_l, amp in ((5007.0, 10.0 * 10.0 ** (0.6 * (lgu + 2.5))), (3727.0, 8.0 * 10.0 ** (-0.4 * (lgu + 2.5))),
+                       (6563.0, np.full(len(lgu), 20.0))):
+        n_l = int(np.argmin(np.abs(lam - lam_l)))
+        prof = np.exp(-0.5 * ((lam - lam_l) / 8.0) ** 2)
+        out += (a[:, None, None, None] * amp[None, None, :, None] * cont[:, :, None, n_l:n_l + 1]
+                * prof[None, None, None, :])
+    return SSPGrid(base.log_age_yr, base.lgz, lam, out.astype(np.float32), base.t0, base.t1, base.n_t, lgu)
+
+
+def with_nebular(params: np.ndarray, seed: int, start: int = 0) -> np.ndarray:
+    """The same galaxies with the nebular rows appended: row 12 u_mean ~
+    U[-3.5, -1.5], row 13 u_sigma = 0.25 dex (the paper's Sec. 3.3 example
+    scatter); galaxy i's draw depends only on (seed, i)."""
+    p = np.asarray(params, dtype=np.float64)
+    n = p.shape[1]
+    out = np.zeros((NPAR_NEB, n))
+    out[:NPAR] = p
+    if n == 0:
+        return out
+    b0, b1 = start // _BLOCK, (start + n - 1) // _BLOCK
+    draws = [np.random.default_rng([seed, b, 13]).uniform(-3.5, -1.5, _BLOCK) for b in range(b0, b1 + 1)]
+    out[12] = np.concatenate(draws)[start - b0 * _BLOCK:start - b0 * _BLOCK + n]
+    out[13] = 0.25
+    return out
 
 
 # Line-strength workload: [OIII] 5007 A (the line of the paper's Sec. 3.3 example),
