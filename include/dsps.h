@@ -55,6 +55,15 @@
  *    10    logM       log10 of the stellar mass formed by t_obs [Msun]
  *    11    z          redshift, 0 < z <= z_max
  * Gradient rows (param_bar, float32 [11][G]) are rows 0..10 above.
+ *
+ * Grids with a nebular axis (dsps_grid.n_u > 1 values of log10 U, Sec. 3.3,
+ * Eq. nebsed) take two more rows, params float32 [14][G]:
+ *    12    u_mean     mean of log10 U
+ *    13    u_sigma    width [dex] of its triweight distribution, > 0
+ * and return 13 gradient rows: rows 0..10 above, then 11 = u_mean, 12 = u_sigma.
+ * The probability of log U bin k is the triweight CDF difference over the
+ * bin's edges (midpoints of the grid, outer edges at -inf / +inf), and the SSP
+ * weights become omega_ijk = P_SFH(i) P_met(j | i) P_neb(k).
  */
 #ifndef DSPS_H
 #define DSPS_H
@@ -102,11 +111,16 @@ enum { DSPS_PREC_FP32 = 0, DSPS_PREC_BF16X3 = 1 };
 
 #define DSPS_NPAR 12
 #define DSPS_NGRAD 11
+#define DSPS_NPAR_NEB 14           /* parameter rows with a nebular axis      */
+#define DSPS_NGRAD_NEB 13          /* gradient rows with a nebular axis       */
+#define DSPS_MAX_NU 8              /* log U values of the nebular axis        */
 #define DSPS_MAX_FILTERS 16
 
 /* SSP block and grids (host memory, copied at dsps_create).
  * Sec. 2.1 (Eq. cspdef: the SSP block is precomputed and held fixed) and
- * Sec. 3.1 (age grid), Sec. 3.2 (metallicity grid). */
+ * Sec. 3.1 (age grid), Sec. 3.2 (metallicity grid), Sec. 3.3 (the optional
+ * nebular ionisation axis).  Zero-initialise the struct: n_u = 0 means no
+ * nebular axis. */
 typedef struct {
     int32_t n_age;             /* >= 2                                          */
     int32_t n_z;               /* >= 1                                          */
@@ -116,9 +130,12 @@ typedef struct {
     const double *lam;         /* [n_lam] rest wavelength [A], uniform in ln
                                   lambda to 1e-9 relative (DSPS_ERR_UNSUPPORTED
                                   otherwise)                                    */
-    const float *l_ssp;        /* [n_age][n_z][n_lam] L_nu [Lsun/Hz/Msun], >= 0  */
+    const float *l_ssp;        /* [n_age][n_z][n_lam] L_nu [Lsun/Hz/Msun], >= 0;
+                                  [n_age][n_z][n_u][n_lam] with a nebular axis  */
     double t0_gyr, t1_gyr;     /* uniform cosmic-time grid of the SFR           */
     int32_t n_t;               /* nodes, 2..1024                                */
+    int32_t n_u;               /* log U values, 2..DSPS_MAX_NU; 0 or 1: none    */
+    const double *lgu;         /* [n_u] log10 U, strictly increasing (n_u > 1)  */
 } dsps_grid;
 
 typedef struct {
@@ -126,7 +143,9 @@ typedef struct {
     int32_t sfh_model;         /* DSPS_SFH_*                                    */
     int32_t mdf_kernel;        /* DSPS_MDF_*                                    */
     int32_t device;            /* CUDA device ordinal                            */
-    int64_t max_chunk;         /* galaxies per internal launch (work space size) */
+    int64_t max_chunk;         /* galaxies per internal launch (work space size;
+                                  lowered so that the work space stays under
+                                  16 GiB)                                        */
     int64_t hbm_budget_bytes;  /* admission budget of the request loop          */
     int32_t n_streams;         /* streams of the request loop                    */
     double z_max;              /* largest accepted redshift (cosmology table)    */
@@ -169,13 +188,16 @@ int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts,
 int dsps_filters_count(dsps_ctx *ctx, int32_t set_id, int32_t *n_filt);
 
 /* SSP weights in Msun, w_out[g][i][j] = 10^logM * P_SFH(age_i) * P_met(Z_j | age_i)
- * (Sec. 3.1 Eq. cspsum with P_SFH, Sec. 3.2 Eq. agedep_mdf).
- * params: device float32 [12][n_gal]; w_out: device float32 [n_gal][n_age][n_z]. */
+ * (Sec. 3.1 Eq. cspsum with P_SFH, Sec. 3.2 Eq. agedep_mdf), times P_neb(u_k)
+ * with a nebular axis (Eq. nebsed).
+ * params: device float32 [12][n_gal] ([14][n_gal] with a nebular axis);
+ * w_out: device float32 [n_gal][n_age][n_z] ([n_gal][n_age][n_z][n_u]). */
 int dsps_weights(dsps_ctx *ctx, int64_t n_gal, const float *params, float *w_out,
                  dsps_stream_t stream);
 
 /* Observer-frame AB magnitudes (Sec. 2.2): mags[g][q], device float32
- * [n_gal][n_filt of set_id].  params: device float32 [12][n_gal].
+ * [n_gal][n_filt of set_id].  params: device float32 [12][n_gal] ([14][n_gal]
+ * with a nebular axis, as everywhere below).
  * precision: DSPS_PREC_FP32 or DSPS_PREC_BF16X3. */
 int dsps_photometry(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
                     int32_t precision, float *mags, dsps_stream_t stream);
@@ -185,7 +207,7 @@ int dsps_photometry(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t s
  *   param_bar[k][g] = sum_q mag_bar[g][q] d mags[g][q] / d params[k][g],  k = 0..10.
  * mag_bar: device float32 [n_gal][n_filt]; mags: device float32
  * [n_gal][n_filt] or NULL (forward magnitudes written as a by-product);
- * param_bar: device float32 [11][n_gal]. */
+ * param_bar: device float32 [11][n_gal] ([13][n_gal] with a nebular axis). */
 int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
                         int32_t precision, const float *mag_bar, float *mags,
                         float *param_bar, dsps_stream_t stream);
@@ -256,7 +278,8 @@ int dsps_line_ew(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line
 /* Vector-Jacobian product of the equivalent widths:
  *   param_bar[k][g] = ew_bar[g] dW_g / d params[k][g],  k = 0..10
  * (row 10, logM, is exactly 0).  ew_bar: device float32 [n_gal]; ew: device
- * float32 [n_gal] or NULL; param_bar: device float32 [11][n_gal]. */
+ * float32 [n_gal] or NULL; param_bar: device float32 [11][n_gal] ([13][n_gal] with
+ * a nebular axis). */
 int dsps_line_ew_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line_id,
                      const float *ew_bar, float *ew, float *param_bar, dsps_stream_t stream);
 
@@ -287,13 +310,13 @@ int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const float *param
  * dsps_photometry(_vjp) call on the same inputs. */
 typedef struct {
     int64_t n_gal;
-    const float *params;       /* host [12][n_gal]                              */
+    const float *params;       /* host [12][n_gal] ([14][n_gal], nebular axis)  */
     int32_t set_id;
     int32_t precision;
     int32_t want_grad;         /* 0: mags only; 1: also param_bar                */
     const float *mag_bar;      /* host [n_gal][n_filt], if want_grad             */
     float *mags;               /* host [n_gal][n_filt]                           */
-    float *param_bar;          /* host [11][n_gal], if want_grad                 */
+    float *param_bar;          /* host [11][n_gal] ([13][n_gal]), if want_grad   */
 } dsps_request;
 
 /* Queues a request; *ticket identifies it.  The host buffers must stay valid

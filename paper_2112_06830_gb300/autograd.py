@@ -2,7 +2,8 @@
 
 ``photometry(ctx, params, set_id, precision)`` returns AB magnitudes [G, Q] and
 is differentiable with respect to ``params`` [12, G] (rows 0..10; the redshift
-row 11 gets a zero gradient).  Forward and backward both run in libdsps: the
+row 11 gets a zero gradient), or [14, G] on a grid with a nebular axis (rows
+12, 13 take gradient rows 11, 12).  Forward and backward both run in libdsps: the
 backward calls dsps_photometry_vjp, which recomputes the forward sums it needs
 instead of storing spectra.
 """
@@ -29,7 +30,9 @@ class DSPSPhotometry(torch.autograd.Function):
         _, pbar = fctx.context.photometry_vjp(params, fctx.set_id, grad_mags.contiguous(),
                                               precision=fctx.precision, want_mags=False)
         grad = torch.zeros_like(params)
-        grad[: dsps.DSPS_NGRAD] = pbar
+        grad[: dsps.DSPS_NGRAD] = pbar[: dsps.DSPS_NGRAD]
+        if pbar.shape[0] > dsps.DSPS_NGRAD:
+            grad[12:14] = pbar[dsps.DSPS_NGRAD:]
         return grad, None, None, None
 
 

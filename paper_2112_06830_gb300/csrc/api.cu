@@ -135,7 +135,7 @@ void free_ctx(Ctx *c) {
     }
     for (auto &ls : c->lines) cudaFree(ls.d_tab);
     void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_edges, c->d_einh, c->d_bwidth,
-                    c->d_zedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->d_err, c->d_stats,
+                    c->d_zedge, c->d_uedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->d_err, c->d_stats,
                     c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d};
     for (void *p : ptrs) cudaFree(p);
     for (auto &r : c->prof_recs) {
@@ -211,6 +211,11 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
         if (!(g->log_age_yr[i] > g->log_age_yr[i - 1])) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: ages not increasing%s");
     for (int j = 1; j < g->n_z; ++j)
         if (!(g->lgz[j] > g->lgz[j - 1])) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: lgZ not increasing%s");
+    const int n_u = g->n_u > 1 ? g->n_u : 1;
+    if (g->n_u > DSPS_MAX_NU || g->n_u < 0 || (n_u > 1 && !g->lgu))
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_create: nebular axis needs 2..8 log U values%s");
+    for (int k = 1; k < n_u; ++k)
+        if (!(g->lgu[k] > g->lgu[k - 1])) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: log U not increasing%s");
     if (!(g->lam[0] > 0)) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: wavelengths must be positive%s");
     const double dl = std::log(g->lam[g->n_lam - 1] / g->lam[0]) / (g->n_lam - 1);
     if (!(dl > 0)) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: wavelengths not increasing%s");
@@ -246,11 +251,16 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     c->n_age = g->n_age;
     c->n_z = g->n_z;
     c->n_lam = g->n_lam;
-    c->K = g->n_age * g->n_z;
+    c->n_u = n_u;
+    c->npar = n_u > 1 ? NPAR_MAX : NPAR;
+    c->ngrad = n_u > 1 ? DSPS_NGRAD_NEB : NGRAD;
+    c->u_ref = n_u / 2;
+    c->K = g->n_age * g->n_z * n_u;
     c->K_pad = (c->K + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
     c->A_pad = (c->n_age + 3) / 4 * 4;
-    c->KZ_pad = (c->n_z * c->A_pad + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
-    c->kmask_words = (c->KZ_pad / KBLOCK + 31) / 32;
+    c->SEC = (c->n_z * c->A_pad + KBLOCK - 1) / KBLOCK * KBLOCK;
+    c->KZ_pad = (n_u * c->SEC + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
+    c->kmask_words = (c->SEC / KBLOCK + 31) / 32;
     c->N_pad = (c->n_lam + 1 + N_ALIGN - 1) / N_ALIGN * N_ALIGN;   // >= n_lam + 1: room for the closing term
     c->n_t = g->n_t;
     c->t0 = g->t0_gyr;
@@ -259,6 +269,13 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     c->dlnlam = dl;
     c->h_lam.assign(g->lam, g->lam + g->n_lam);
     c->chunk = (opts.max_chunk + 127) / 128 * 128;
+    {
+        // keep the context's work space under 16 GiB (grids with a nebular axis
+        // have n_u times longer weight rows)
+        const size_t cap = (size_t)16 << 30, per = workspace_bytes(*c, 128, false) / 128 + 1;
+        const int64_t fit = (int64_t)(cap / per) / 128 * 128;
+        if (fit >= 128 && c->chunk > fit) c->chunk = fit;
+    }
     {
         const double xmid = 0.5 * (g->log_age_yr[0] + g->log_age_yr[g->n_age - 1]);
         if (opts.mdf_mean == DSPS_MDF_MEAN_TERF) {
@@ -269,6 +286,10 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
             c->sort_mua = 1.f;
             c->sort_mub = (float)(xmid - 9.0);
         }
+    }
+    if (n_u > 1) {
+        c->sort_u_lo = (float)g->lgu[0];
+        c->sort_u_scale = (float)(8.0 / (g->lgu[n_u - 1] - g->lgu[0]));
     }
     c->sort_mu_lo = (float)g->lgz[0];
     c->sort_mu_scale = g->n_z > 1 ? (float)(ZSORT_MUBINS / (g->lgz[g->n_z - 1] - g->lgz[0])) : 0.f;
@@ -287,6 +308,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_einh, (size_t)c->n_age + 1));
     chk(dmalloc(&c->d_bwidth, (size_t)c->n_age));
     chk(dmalloc(&c->d_zedge, (size_t)c->n_z + 1));
+    chk(dmalloc(&c->d_uedge, (size_t)c->n_u + 1));
     chk(dmalloc(&c->d_ws_block, workspace_bytes(*c, c->chunk, false)));
     chk(dmalloc(&c->d_err, 1));
     chk(dmalloc(&c->d_stats, 1));
@@ -326,6 +348,11 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     zedge[0] = -1e30f;
     zedge[c->n_z] = 1e30f;
     for (int j = 1; j < c->n_z; ++j) zedge[j] = (float)(0.5 * (g->lgz[j - 1] + g->lgz[j]));
+    // log U bin edges, likewise (Sec. 3.3)
+    std::vector<float> uedge(c->n_u + 1);
+    uedge[0] = -1e30f;
+    uedge[c->n_u] = 1e30f;
+    for (int k = 1; k < c->n_u; ++k) uedge[k] = (float)(0.5 * (g->lgu[k - 1] + g->lgu[k]));
     std::vector<double> tl, gl;
     c->dz_lut = 1e-3;
     build_cosmology(opts.om0, opts.w0, opts.h, opts.z_max, c->dz_lut, tl, gl);
@@ -350,6 +377,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     }
     up(c->d_bump, bump.data(), bump.size() * sizeof(float));
     up(c->d_zedge, zedge.data(), zedge.size() * sizeof(float));
+    up(c->d_uedge, uedge.data(), uedge.size() * sizeof(float));
     up(c->d_tlut, tl.data(), tl.size() * sizeof(double));
     std::vector<float> glf(gl.begin(), gl.end());
     up(c->d_glut, glf.data(), glf.size() * sizeof(float));

@@ -19,7 +19,7 @@ size_t workspace_bytes(const Ctx &c, int64_t rows, bool adjoint) {
     const size_t W32 = (size_t)(c.K_pad > c.KZ_pad ? c.K_pad : c.KZ_pad);
     size_t b = al256(R * W32 * 4) + 2 * al256(R * c.KZ_pad * 2) + al256(R * AUX_STRIDE * 4) + al256(R * 4) + al256(R * sizeof(GalPrep)) +
                2 * al256(R * 4) + al256((size_t)ZSORT_BUCKETS * 4) + al256((size_t)TC_PARTS * R * 3 * QSTRIDE_MAX * 4) +
-               al256(R * QSTRIDE_MAX * 4) + al256((R / 128 + 1) * sizeof(int2)) + al256((R / 128 + 1) * c.kmask_words * 4) + al256(sizeof(int));
+               al256(R * QSTRIDE_MAX * 4) + 2 * al256((R / 128 + 1) * sizeof(int2)) + al256((R / 128 + 1) * c.kmask_words * 4) + al256(sizeof(int));
     if (adjoint) b += al256(R * c.N_pad * 4);
     return b;
 }
@@ -46,6 +46,7 @@ Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint) 
     w.partial = static_cast<float *>(take((size_t)TC_PARTS * R * 3 * QSTRIDE_MAX * 4));
     w.cq = static_cast<float *>(take(R * QSTRIDE_MAX * 4));
     w.trange = static_cast<int2 *>(take((R / 128 + 1) * sizeof(int2)));
+    w.urange = static_cast<int2 *>(take((R / 128 + 1) * sizeof(int2)));
     w.kmask = static_cast<unsigned *>(take((R / 128 + 1) * c.kmask_words * 4));
     w.sched = static_cast<int *>(take(sizeof(int)));
     w.shat = adjoint ? take(R * c.N_pad * 4) : nullptr;

@@ -16,6 +16,8 @@ namespace dsps {
 
 constexpr int NPAR = DSPS_NPAR;
 constexpr int NGRAD = DSPS_NGRAD;
+constexpr int NPAR_MAX = DSPS_NPAR_NEB;   // parameter rows with a nebular axis
+constexpr int MAX_NU = DSPS_MAX_NU;
 constexpr int K_ALIGN = 64;      // K (= n_age * n_z) padding: multiple of the 32-wide TMA box
 constexpr int N_ALIGN = 256;     // wavelength padding: multiple of the 256-wide MMA tile
 constexpr int MAX_NT = 1024;     // SFR time nodes
@@ -35,22 +37,29 @@ constexpr double AB0 = 1.13492e-13;     // Sec. 2.2, Eq. (restmag)
 constexpr double LAM_V = 5500.0;        // Sec. 3.4, Eq. (salim)
 constexpr double SIG_Q = 0.3;           // quench transition width [Gyr]
 
-// Order of the K = n_age * n_z axis.  The SSP block, dsps_weights and the FP32
-// and adjoint paths use the age-major k = i * n_z + j.  The tensor-core forward
-// operands (split weights and d_Lt_*) use the metallicity-major kz = j * A_pad
-// + i, A_pad = n_age rounded up to 4 (so that every metallicity row starts on a
-// 16-byte boundary; ages n_age .. A_pad-1 are zero columns), in rows of KZ_pad
-// = n_z * A_pad rounded up to K_ALIGN.  The triweight metallicity kernel has
+// Order of the K = n_age * n_z * n_u axis (n_u = 1 without a nebular axis).
+// The SSP block, dsps_weights and the FP32 paths use the age-major
+// k = (i * n_z + j) * n_u + u.  The tensor-core operands (split weights,
+// d_Lt_*) and the adjoint's differenced block use the metallicity-major
+// kz = u * SEC + j * A_pad + i: A_pad = n_age rounded up to 4 (every
+// metallicity row starts on a 16-byte boundary; ages n_age .. A_pad-1 are zero
+// columns), one section of SEC = n_z * A_pad rounded up to 32 per log U value,
+// rows of KZ_pad = n_u * SEC rounded up to K_ALIGN.  The triweight kernels have
 // compact support, so a galaxy's non-zero weights fill one contiguous run of
-// kz, and a tile of galaxies with similar metallicity needs only the K blocks
-// of that run.
-__host__ __device__ inline int kz_to_k(int kz, int a_pad, int n_age, int n_z) {   // -1: padding
-    const int j = kz / a_pad, i = kz - j * a_pad;
-    return (j < n_z && i < n_age) ? i * n_z + j : -1;
+// each section, for a contiguous range of sections; a tile of galaxies with
+// similar metallicity needs only the K blocks of that run.
+struct KzLayout {
+    int a_pad, sec, n_age, n_z, n_u;
+};
+__host__ __device__ inline int kz_to_k(int kz, const KzLayout &l) {   // -1: padding
+    const int u = kz / l.sec, r = kz - u * l.sec;
+    const int j = r / l.a_pad, i = r - j * l.a_pad;
+    return (u < l.n_u && j < l.n_z && i < l.n_age) ? (i * l.n_z + j) * l.n_u + u : -1;
 }
-__host__ __device__ inline int k_to_kz(int k, int a_pad, int n_z) {
-    const int i = k / n_z;
-    return (k - i * n_z) * a_pad + i;
+__host__ __device__ inline int k_to_kz(int k, const KzLayout &l) {
+    const int u = k % l.n_u, ij = k / l.n_u;
+    const int i = ij / l.n_z, j = ij - i * l.n_z;
+    return u * l.sec + j * l.a_pad + i;
 }
 
 // Per 128-row tile of sorted galaxies, reduced with atomics by the weights
@@ -58,7 +67,10 @@ __host__ __device__ inline int k_to_kz(int k, int a_pad, int n_z) {
 //   Workspace::trange  {smallest, largest} floor(s) (s = aux[.+2], the
 //                      redshift shift); an empty tile keeps {INT_MAX, INT_MIN}
 //   Workspace::kmask   Ctx::kmask_words words: bit b set if some row's split
-//                      weights are non-zero in kz block [32 b, 32 b + 32)
+//                      weights are non-zero in kz block [32 b, 32 b + 32) of
+//                      some section (blocks counted inside a section)
+//   Workspace::urange  {lowest, highest} section (log U bin) where some row
+//                      has non-zero weight; an empty tile keeps {n_u, -1}
 constexpr int TRANGE_EMPTY_LO = 0x7fffffff;
 constexpr int TRANGE_EMPTY_HI = (int)0x80000000;
 constexpr int KBLOCK = 32;   // kz block of the tensor-core contraction (one TMA box)
@@ -125,6 +137,7 @@ struct Workspace {
     int *hist = nullptr;                        // [ZSORT_BUCKETS]
     float *partial = nullptr;                   // [TC_PARTS][cap][3 * QSTRIDE_MAX]
     int2 *trange = nullptr;                     // [cap/128 + 1] per sorted 128-row tile (see above)
+    int2 *urange = nullptr;                     // [cap/128 + 1] per tile (see above)
     unsigned *kmask = nullptr;                  // [cap/128 + 1][kmask_words]
     int *sched = nullptr;                       // [1] work-unit counter of the tensor-core kernels
     float *cq = nullptr;                        // [cap][QSTRIDE_MAX]
@@ -137,13 +150,16 @@ struct Ctx {
     dsps_opts opts{};
     int n_age = 0, n_z = 0, n_lam = 0, K = 0, K_pad = 0, N_pad = 0, n_t = 0;
     int A_pad = 0, KZ_pad = 0;              // metallicity-major K: n_age padded to 4, row length
-    int kmask_words = 0;                    // ceil(KZ_pad / KBLOCK / 32)
+    int n_u = 1, SEC = 0, u_ref = 0;        // nebular axis: log U values, section length, reference section
+    int npar = NPAR, ngrad = NGRAD;         // parameter and gradient rows
+    int kmask_words = 0;                    // ceil(SEC / KBLOCK / 32)
     double t0 = 0, t1 = 0;
     double lnlam0 = 0, dlnlam = 0;
     int num_sms = 0;
     // Sort key of the tensor-core path: the MDF mean at the middle log age,
     // sort_mua p5 + sort_mub p7, binned from sort_mu_lo at sort_mu_scale bins per dex.
     float sort_mu_lo = 0.f, sort_mu_scale = 0.f, sort_mua = 1.f, sort_mub = 0.f;
+    float sort_u_lo = 0.f, sort_u_scale = 0.f;   // nebular axis: 8 bins of the mean log U
 
     // Resident SSP copies.
     float *d_L32 = nullptr;                 // [K_pad][N_pad] fp32 (SIMT path)
@@ -159,6 +175,7 @@ struct Ctx {
     float *d_einh = nullptr;                // [n_age+1] edge / time step
     float *d_bwidth = nullptr;              // [n_age] bin widths [Gyr]
     float *d_zedge = nullptr;               // [n_z+1] lgZ bin edges (+-1e30 outer)
+    float *d_uedge = nullptr;               // [n_u+1] log U bin edges (+-1e30 outer)
     double *d_tlut = nullptr;               // [n_lut] t_obs(z) [Gyr]
     float *d_glut = nullptr;                // [n_lut] Dmod(z) - 5 log10 z
     int n_lut = 0;
@@ -169,11 +186,13 @@ struct Ctx {
     unsigned char *d_ws_block = nullptr;    // device block holding ws (without Shat)
     Workspace ws;
     unsigned long long *d_stats = nullptr;  // [1] tensor-core tiles executed (profiling)
-    float *d_Ld32 = nullptr;                // [KZ_pad][N_pad] metallicity-differenced block (FP32 adjoint)
+    float *d_Ld32 = nullptr;                // [KZ_pad][N_pad] differenced block (FP32 adjoint; prep.cu)
     float *d_wmul_d = nullptr;              // [KZ_pad] 2^E'_kz of the differenced rows
     __nv_bfloat16 *d_L_hi = nullptr;        // [KZ_pad][N_pad] differenced block, row-scaled hi (tensor adjoint)
     __nv_bfloat16 *d_L_lo = nullptr;        // [KZ_pad][N_pad] row-scaled lo
     unsigned *d_err = nullptr;              // sticky error word
+
+    KzLayout kzl() const { return KzLayout{A_pad, SEC, n_age, n_z, n_u}; }
 
     std::vector<FilterSet> sets;
     std::vector<LineSet> lines;

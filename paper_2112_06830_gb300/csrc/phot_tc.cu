@@ -56,6 +56,8 @@ struct TArgs {
     const int2 *trange;             // per-tile redshift-shift ranges from the weights kernel
     const unsigned *kmask;          // per-tile kz-block masks from the weights kernel, or nullptr
     int kmw;                        // mask words per tile
+    const int2 *urange;             // per-tile log U section ranges from the weights kernel
+    int sec_blocks, n_sec;          // K blocks per section, sections (log U bins)
     const float4 *tab;
     ColConst cc;
     int m_last, n_mtiles, n_ntiles, kblocks, parts, n_units;
@@ -67,25 +69,41 @@ struct TArgs {
     unsigned *err;
 };
 
+// K blocks of a tile: the blocks set in a mask of one section's blocks (up to
+// 128, held in registers) in each section (log U bin) of the tile's range,
+// which spans the K blocks [lo, hi) (whole sections).
+struct TileMask {
+    uint4 w;
+    int lo, hi;
+};
+
 // Wavelength tiles [nt0, nt1) that galaxy tile mt needs and its K-block mask
-// (up to 128 blocks, held in registers; all ones without skipping), from the
-// tile's exact ranges over its valid rows.  A wavelength tile whose
-// interpolation rows (grid indices n + i0 - 1 .. n + i0 + 2) fall outside the
-// band [m_nz_lo, m_nz_hi] of non-zero transmission for every i0 of the tile,
-// and a K block where every row's weights are zero, contribute exact zeros and
-// are skipped.  A tile with no non-zero weight does no work.
-__device__ __forceinline__ void tile_ranges(const TArgs &a, int mt, int &nt0, int &nt1, uint4 &km) {
+// (all blocks without skipping), from the tile's exact ranges over its valid
+// rows.  A wavelength tile whose interpolation rows (grid indices n + i0 - 1
+// .. n + i0 + 2) fall outside the band [m_nz_lo, m_nz_hi] of non-zero
+// transmission for every i0 of the tile, and a K block where every row's
+// weights are zero, contribute exact zeros and are skipped.  A tile with no
+// non-zero weight does no work.
+__device__ __forceinline__ void tile_ranges(const TArgs &a, int mt, int &nt0, int &nt1, TileMask &km) {
     nt0 = 0;
     nt1 = a.n_ntiles;
-    km = make_uint4(~0u, ~0u, ~0u, ~0u);
+    km.w = make_uint4(~0u, ~0u, ~0u, ~0u);
+    km.lo = 0;
+    km.hi = a.n_sec * a.sec_blocks;
     if (!a.band_skip) return;
     const int2 r = a.trange[mt];
     if (a.kmask) {
         const unsigned *m = a.kmask + (size_t)mt * a.kmw;
-        km = make_uint4(__ldg(m), a.kmw > 1 ? __ldg(m + 1) : 0u, a.kmw > 2 ? __ldg(m + 2) : 0u,
-                        a.kmw > 3 ? __ldg(m + 3) : 0u);
+        km.w = make_uint4(__ldg(m), a.kmw > 1 ? __ldg(m + 1) : 0u, a.kmw > 2 ? __ldg(m + 2) : 0u,
+                          a.kmw > 3 ? __ldg(m + 3) : 0u);
     }
-    if (r.y < r.x || a.m_nz_hi < a.m_nz_lo || (km.x | km.y | km.z | km.w) == 0u) { nt1 = nt0; return; }
+    const int2 ur = a.urange[mt];
+    km.lo = ur.x * a.sec_blocks;
+    km.hi = (ur.y + 1) * a.sec_blocks;
+    if (r.y < r.x || a.m_nz_hi < a.m_nz_lo || (km.w.x | km.w.y | km.w.z | km.w.w) == 0u || ur.y < ur.x) {
+        nt1 = nt0;
+        return;
+    }
     const int n_lo = a.m_nz_lo - r.y - 2;
     const int n_hi = a.m_nz_hi - r.x + 1;
     if (n_hi < 0) { nt1 = nt0; return; }
@@ -94,16 +112,39 @@ __device__ __forceinline__ void tile_ranges(const TArgs &a, int mt, int &nt0, in
     if (nt1 < nt0) nt1 = nt0;
 }
 
-// First K block >= kb set in the tile's mask (a.kblocks if none).
-__device__ __forceinline__ int next_kb(const TArgs &a, const uint4 &km, int kb) {
-    while (kb < a.kblocks) {
-        const int wi = kb >> 5;
-        const unsigned w = (wi == 0 ? km.x : wi == 1 ? km.y : wi == 2 ? km.z : km.w) >> (kb & 31);
-        if (w) return min(kb + __ffs(w) - 1, a.kblocks);
-        kb = (kb | 31) + 1;
+// The tile's K blocks in increasing order: block base + b for the sections
+// base = lo, lo + sec_blocks, .. < hi and the bits b < sec_blocks of the mask.
+// The producer and the MMA issuer step it once per K block, so a step keeps
+// the current mask word and clears its lowest bit (a few instructions).
+struct KbIter {
+    uint4 w;
+    int base, hi, sb, wi, kblocks;
+    unsigned cur;
+    __device__ __forceinline__ KbIter(const TArgs &a, const TileMask &km)
+        : w(km.w), base(km.lo), hi(km.hi), sb(a.sec_blocks), wi(0), kblocks(a.kblocks), cur(km.w.x) {}
+    __device__ __forceinline__ unsigned word(int i) const {
+        return i == 0 ? w.x : i == 1 ? w.y : i == 2 ? w.z : w.w;
     }
-    return a.kblocks;
-}
+    // next block, a.kblocks after the last
+    __device__ __forceinline__ int next() {
+        while (base < hi) {
+            if (cur) {
+                const int b = (wi << 5) + __ffs(cur) - 1;
+                cur &= cur - 1;
+                if (b < sb) return base + b;
+                cur = 0;   // the rest of this section's mask lies beyond its blocks
+                wi = 3;
+            } else if (wi < 3 && ((wi + 1) << 5) < sb) {
+                cur = word(++wi);
+            } else {
+                base += sb;
+                wi = 0;
+                cur = w.x;
+            }
+        }
+        return kblocks;
+    }
+};
 
 // Wavelength tile nt belongs to part nt mod parts, whatever the tile's range:
 // every galaxy's partial sums then add the same non-zero terms in the same
@@ -181,10 +222,11 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                 if (u < 0) break;
                 const int mt = u / a.parts, part = u - mt * a.parts;
                 int nt0, nt1;
-                uint4 km;
+                TileMask km;
                 tile_ranges(a, mt, nt0, nt1, km);
-                for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts)
-                    for (int kb = next_kb(a, km, 0); kb < a.kblocks; kb = next_kb(a, km, kb + 1)) {
+                for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
+                    KbIter it(a, km);
+                    for (int kb = it.next(); kb < a.kblocks; kb = it.next()) {
                         if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                         const uint32_t fb = full0 + 8 * stage;
                         const uint32_t st = sbase + stage * STAGE_BYTES;
@@ -196,6 +238,7 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                         armed[stage] = (int)phase;
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
+                }
             }
             // Let every armed copy land before the CTA can exit.
             for (int s = 0; s < STAGES; ++s)
@@ -217,14 +260,15 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                 if (!ring_next(ring, u, abort_flag, a.err) || u < 0) break;
                 const int mt = u / a.parts, part = u - mt * a.parts;
                 int nt0, nt1;
-                uint4 km;
+                TileMask km;
                 tile_ranges(a, mt, nt0, nt1, km);
-                const int kb_first = next_kb(a, km, 0);
                 for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
                     if (!mbar_wait(acce0 + 8 * as, aphase ^ 1u, abort_flag, a.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d = tmem_base + (uint32_t)(as * BN);
-                    for (int kb = kb_first; kb < a.kblocks; kb = next_kb(a, km, kb + 1)) {
+                    KbIter it(a, km);
+                    bool first = true;
+                    for (int kb = it.next(); kb < a.kblocks; kb = it.next()) {
                         if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, a.err)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t st = sbase + stage * STAGE_BYTES;
@@ -234,13 +278,14 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                             const uint64_t al = sdesc_sw64(st + A_BYTES + kk * 32);
                             const uint64_t bh = sdesc_sw64(st + 2 * A_BYTES + kk * 32);
                             const uint64_t bl = sdesc_sw64(st + 2 * A_BYTES + B_BYTES + kk * 32);
-                            mma_bf16(d, ah, bh, (kb != kb_first || kk != 0) ? 1u : 0u);
+                            mma_bf16(d, ah, bh, (!first || kk != 0) ? 1u : 0u);
                             mma_bf16(d, ah, bl, 1u);
                             mma_bf16(d, al, bh, 1u);
                         }
                         mma_commit(empty0 + 8 * stage);
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                         ++nblk;
+                        first = false;
                     }
                     if (!ok) break;
                     mma_commit(accf0 + 8 * as);
@@ -271,7 +316,7 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
             if (!have || u < 0) break;
             const int mt = u / a.parts, part = u - mt * a.parts;
             int nt0, nt1;
-            uint4 km;
+            TileMask km;
             tile_ranges(a, mt, nt0, nt1, km);
             const int64_t rowg = (int64_t)mt * BM + row;
             const RowConst rc = load_row_const(a.aux, rowg, a.n);
@@ -393,6 +438,9 @@ cudaError_t launch_phot_tc(const Ctx &c, const Workspace &w, const FilterSet &fs
     a.trange = w.trange;
     a.kmask = c.kmask_words <= 4 ? w.kmask : nullptr;   // larger grids contract every K block
     a.kmw = c.kmask_words;
+    a.urange = w.urange;
+    a.sec_blocks = c.SEC / BK;
+    a.n_sec = c.n_u;
     a.tab = reinterpret_cast<const float4 *>(fs.d_tab);
     a.cc = make_col_const(c);
     a.m_last = fs.m_rows - 1;

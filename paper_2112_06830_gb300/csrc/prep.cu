@@ -1,17 +1,21 @@
 // prep.cu -- one-time preparation of the resident SSP block (Sec. 2.1: the SSP
 // spectra are computed in advance, loaded once as a contiguous block and held
-// fixed).  Builds, from the caller's FP32 L[k][n] (k = i * n_z + j):
+// fixed).  Builds, from the caller's FP32 L[k][n] (k = (i * n_z + j) * n_u + u,
+// n_u = 1 without a nebular axis):
 //   d_L32   [K_pad][N_pad] FP32, zero padded                (SIMT form)
 //   d_Lt_*  [N_pad][KZ_pad] bf16 hi / lo of L[k][n] 2^-E_k   (tensor form, K-contiguous
-//           rows, columns in the metallicity-major order kz = j * A_pad + i)
-//   d_Ld32  [KZ_pad][N_pad] FP32 metallicity-differenced block, rows in the
-//           metallicity-major order kz = j * A_pad + i: row (j = 0, i) is
-//           L[i, 0], row (j >= 1, i) is L[i, j] - L[i, j-1]   (FP32 adjoint)
+//           rows, columns in the metallicity-major order kz = u * SEC + j * A_pad + i)
+//   d_Ld32  [KZ_pad][N_pad] FP32 differenced block, rows in the same order:
+//           with D_j L = L[i, j, u] - L[i, j-1, u] (L[i, 0, u] for j = 0), row
+//           (u_ref, j, i) is D_j L[i, j, u_ref] and row (u != u_ref, j, i) is
+//           D_j L[i, j, u] - D_j L[i, j, u_ref]             (FP32 adjoint)
 //   d_L_*   [KZ_pad][N_pad] bf16 hi / lo of the differenced block scaled by
 //           2^-E'_kz, with d_wmul_d = 2^E'_kz              (tensor adjoint)
 // The adjoint contracts with the differenced block so that the differences of
 // dLoss/domega between neighbouring metallicity bins -- all the metallicity
-// gradients need (summation by parts) -- come out at full relative precision.
+// gradients need (summation by parts) -- and, with a nebular axis, between each
+// log U bin and the reference one -- all the log U gradients need, since the
+// bin probabilities sum to 1 -- come out at full relative precision.
 //   d_wmul  [KZ_pad] 2^E_k, the factor folded into the weights, so that
 //           sum_k (omega_k 2^E_k)(L_kn 2^-E_k) = sum_k omega_k L_kn exactly
 //           (indexed by kz, like d_Lt_*).
@@ -24,7 +28,7 @@ namespace dsps {
 namespace {
 
 // wmul is written at the metallicity-major position of row k, rscale at k.
-__global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, int a_pad, int n_z, float *wmul,
+__global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, KzLayout kl, float *wmul,
                                     float *rscale) {
     const int k = blockIdx.x;
     if (k >= K_pad) return;
@@ -41,7 +45,7 @@ __global__ void row_exponent_kernel(const float *L, int K, int N, int K_pad, int
         int E = 0;
         if (mm > 0.f) E = ilogbf(mm);
         E = max(-120, min(120, E));
-        if (k < K) wmul[k_to_kz(k, a_pad, n_z)] = ldexpf(1.f, E);
+        if (k < K) wmul[k_to_kz(k, kl)] = ldexpf(1.f, E);
         rscale[k] = k < K ? ldexpf(1.f, -E) : 0.f;
     }
 }
@@ -57,14 +61,14 @@ __global__ void build_l32_kernel(const float *L, int K, int N, int K_pad, int N_
 // Transposing split: tile of 32 (kz) x 32 (n) through shared memory; column
 // kz of the output [N_pad][KZ_pad] takes SSP row k = kz_to_k(kz) (zero for
 // padding columns).
-__global__ void build_lt_kernel(const float *L, const float *rscale, int N, int KZ_pad, int N_pad, int a_pad,
-                                int n_age, int n_z, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+__global__ void build_lt_kernel(const float *L, const float *rscale, int N, int KZ_pad, int N_pad, KzLayout kl,
+                                __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
     __shared__ float t[32][33];
     const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     for (int r = ty; r < 32; r += 8) {
         const int kz = k0 + r, n = n0 + tx;
-        const int k = kz_to_k(kz, a_pad, n_age, n_z);
+        const int k = kz_to_k(kz, kl);
         t[r][tx] = (k >= 0 && n < N) ? L[(size_t)k * N + n] * rscale[k] : 0.f;
     }
     __syncthreads();
@@ -79,18 +83,26 @@ __global__ void build_lt_kernel(const float *L, const float *rscale, int N, int 
     }
 }
 
-// Metallicity-differenced block, FP32 [KZ_pad][N_pad], metallicity-major rows
-// (padding zero).
-__global__ void build_ldiff_kernel(const float *L, int N, int a_pad, int n_age, int n_z, int KZ_pad, int N_pad,
+// Differenced block (see the top of the file), FP32 [KZ_pad][N_pad],
+// metallicity-major rows (padding zero).
+__global__ void build_ldiff_kernel(const float *L, int N, KzLayout kl, int u_ref, int KZ_pad, int N_pad,
                                    float *Ld) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)KZ_pad * N_pad) return;
     const int kz = (int)(idx / N_pad), n = (int)(idx % N_pad);
-    const int k = kz_to_k(kz, a_pad, n_age, n_z);
+    const int k = kz_to_k(kz, kl);
     float v = 0.f;
     if (k >= 0 && n < N) {
-        v = L[(size_t)k * N + n];
-        if (k % n_z != 0) v -= L[(size_t)(k - 1) * N + n];
+        const int u = k % kl.n_u, j = (k / kl.n_u) % kl.n_z;
+        // D_j L at log U bin uu
+        auto dj = [&](int uu) {
+            const int kk = k - u + uu;
+            float d = L[(size_t)kk * N + n];
+            if (j > 0) d -= L[(size_t)(kk - kl.n_u) * N + n];
+            return d;
+        };
+        v = dj(u);
+        if (u != u_ref) v -= dj(u_ref);
     }
     Ld[idx] = v;
 }
@@ -137,15 +149,15 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
     if (e == cudaSuccess) e = cudaMemcpy(d_raw, h_lssp, KN * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c.d_wmul, 0, (size_t)c.KZ_pad * sizeof(float));
     if (e == cudaSuccess) {
-        row_exponent_kernel<<<c.K_pad, 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.A_pad, c.n_z, c.d_wmul, d_rscale);
+        const KzLayout kl = c.kzl();
+        row_exponent_kernel<<<c.K_pad, 256>>>(d_raw, c.K, c.n_lam, c.K_pad, kl, c.d_wmul, d_rscale);
         const size_t tot = (size_t)c.K_pad * c.N_pad;
         build_l32_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.N_pad, c.d_L32);
         dim3 g(c.N_pad / 32, c.KZ_pad / 32), b(32, 8);
-        build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.n_lam, c.KZ_pad, c.N_pad, c.A_pad, c.n_age, c.n_z, c.d_Lt_hi,
-                                  c.d_Lt_lo);
+        build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.n_lam, c.KZ_pad, c.N_pad, kl, c.d_Lt_hi, c.d_Lt_lo);
         const size_t totz = (size_t)c.KZ_pad * c.N_pad;
         const unsigned blkz = (unsigned)((totz + 255) / 256);
-        build_ldiff_kernel<<<blkz, 256>>>(d_raw, c.n_lam, c.A_pad, c.n_age, c.n_z, c.KZ_pad, c.N_pad, c.d_Ld32);
+        build_ldiff_kernel<<<blkz, 256>>>(d_raw, c.n_lam, kl, c.u_ref, c.KZ_pad, c.N_pad, c.d_Ld32);
         row_exponent_abs_kernel<<<c.KZ_pad, 256>>>(c.d_Ld32, c.KZ_pad, c.N_pad, c.d_wmul_d, d_rscale);
         build_split_kernel<<<blkz, 256>>>(c.d_Ld32, d_rscale, c.KZ_pad, c.N_pad, c.d_L_hi, c.d_L_lo);
         e = cudaGetLastError();

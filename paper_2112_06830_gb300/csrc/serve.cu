@@ -144,13 +144,13 @@ struct Serve {
     int64_t fault_delay_us = 0;
 
     size_t dev_bytes(int64_t G, int Q, bool grad) const {
-        size_t b = workspace_bytes(*c, G, grad) + al256(G * 48) + al256(G * Q * 4);
-        if (grad) b += al256(G * Q * 4) + al256(G * 44);
+        size_t b = workspace_bytes(*c, G, grad) + al256(G * c->npar * 4) + al256(G * Q * 4);
+        if (grad) b += al256(G * Q * 4) + al256(G * c->ngrad * 4);
         return b;
     }
     size_t host_bytes(int64_t G, int Q, bool grad) const {
-        size_t b = al256(G * 48) + al256(G * Q * 4);
-        if (grad) b += al256(G * Q * 4) + al256(G * 44);
+        size_t b = al256(G * c->npar * 4) + al256(G * Q * 4);
+        if (grad) b += al256(G * Q * 4) + al256(G * c->ngrad * 4);
         return b;
     }
     void loop();
@@ -224,11 +224,11 @@ void serve_stop(Ctx *c) {
 }
 
 void Serve::launch(Batch &b) {
-    // Host staging: params [12][G] SoA and, for the gradient, mag_bar [G][Q].
+    // Host staging: params [npar][G] SoA and, for the gradient, mag_bar [G][Q].
     for (size_t i = 0; i < b.pieces.size(); ++i) {
         const Piece &p = b.pieces[i];
         const dsps_request &r = p.req->r;
-        for (int row = 0; row < NPAR; ++row)
+        for (int row = 0; row < c->npar; ++row)
             std::memcpy(b.h_params + (size_t)row * b.G + b.off[i], r.params + (size_t)row * r.n_gal + p.start,
                         (size_t)p.n * 4);
         if (b.grad)
@@ -239,15 +239,15 @@ void Serve::launch(Batch &b) {
     Workspace w = workspace_carve(*c, b.dev, b.G, grad);
     unsigned char *io = b.dev + workspace_bytes(*c, b.G, grad);
     float *d_params = reinterpret_cast<float *>(io);
-    float *d_mags = reinterpret_cast<float *>(io + al256(b.G * 48));
-    float *d_mbar = grad ? reinterpret_cast<float *>(io + al256(b.G * 48) + al256(b.G * b.Q * 4)) : nullptr;
-    float *d_pbar = grad ? reinterpret_cast<float *>(io + al256(b.G * 48) + 2 * al256(b.G * b.Q * 4)) : nullptr;
+    float *d_mags = reinterpret_cast<float *>(io + al256(b.G * c->npar * 4));
+    float *d_mbar = grad ? reinterpret_cast<float *>(io + al256(b.G * c->npar * 4) + al256(b.G * b.Q * 4)) : nullptr;
+    float *d_pbar = grad ? reinterpret_cast<float *>(io + al256(b.G * c->npar * 4) + 2 * al256(b.G * b.Q * 4)) : nullptr;
     FilterSet fs;
     {
         std::lock_guard<std::mutex> lk(c->mu);
         fs = c->sets[b.set_id];
     }
-    cudaError_t e = cudaMemcpyAsync(d_params, b.h_params, (size_t)b.G * 48, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(d_params, b.h_params, (size_t)b.G * c->npar * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && grad)
         e = cudaMemcpyAsync(d_mbar, b.h_mbar, (size_t)b.G * b.Q * 4, cudaMemcpyHostToDevice, st);
     int rc = e == cudaSuccess ? DSPS_OK : DSPS_ERR_CUDA;
@@ -258,7 +258,7 @@ void Serve::launch(Batch &b) {
     if (rc == DSPS_OK) {
         e = cudaMemcpyAsync(b.h_mags, d_mags, (size_t)b.G * b.Q * 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && grad)
-            e = cudaMemcpyAsync(b.h_pbar, d_pbar, (size_t)b.G * 44, cudaMemcpyDeviceToHost, st);
+            e = cudaMemcpyAsync(b.h_pbar, d_pbar, (size_t)b.G * c->ngrad * 4, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) rc = DSPS_ERR_CUDA;
     }
     b.status = rc;
@@ -274,7 +274,7 @@ void Serve::finish(Batch &b) {
             const dsps_request &r = p.req->r;
             std::memcpy(r.mags + (size_t)p.start * b.Q, b.h_mags + (size_t)b.off[i] * b.Q, (size_t)p.n * b.Q * 4);
             if (b.grad)
-                for (int k = 0; k < NGRAD; ++k)
+                for (int k = 0; k < c->ngrad; ++k)
                     std::memcpy(r.param_bar + (size_t)k * r.n_gal + p.start, b.h_pbar + (size_t)k * b.G + b.off[i],
                                 (size_t)p.n * 4);
         }
@@ -331,10 +331,10 @@ bool Serve::try_launch(std::unique_lock<std::mutex> &lk) {
     b.host = h;
     b.G = G;
     b.h_params = reinterpret_cast<float *>(h);
-    b.h_mags = reinterpret_cast<float *>(h + al256(G * 48));
+    b.h_mags = reinterpret_cast<float *>(h + al256(G * c->npar * 4));
     if (b.grad) {
-        b.h_mbar = reinterpret_cast<float *>(h + al256(G * 48) + al256(G * b.Q * 4));
-        b.h_pbar = reinterpret_cast<float *>(h + al256(G * 48) + 2 * al256(G * b.Q * 4));
+        b.h_mbar = reinterpret_cast<float *>(h + al256(G * c->npar * 4) + al256(G * b.Q * 4));
+        b.h_pbar = reinterpret_cast<float *>(h + al256(G * c->npar * 4) + 2 * al256(G * b.Q * 4));
     }
     int64_t o = 0;
     for (size_t k = 0; k < take.size(); ++k) {

@@ -14,10 +14,14 @@
 //   5. Metallicity weights P_met(j | i) as differences of the triweight
 //      (Appendix B, Eq. terf) or Gaussian CDF over lgZ bin edges, with the mean
 //      moving linearly in log age (Sec. 3.2, Eq. agedep_mdf), FP32.
-//   6. Joint weights omega_ij = P_SFH(i) P_met(j | i) (Eq. full_mdf), written as
-//      Msun (dsps_weights), FP32 per unit mass (SIMT photometry) or scaled by
-//      the SSP row multiplier and split into bf16 hi + lo (tensor photometry,
-//      metallicity-major K, with the per-tile ranges and kz-block masks).
+//   6. Joint weights omega_ij = P_SFH(i) P_met(j | i) (Eq. full_mdf), times
+//      P_neb(u) with a nebular axis (Sec. 3.3, Eq. nebsed: triweight CDF
+//      differences over the log U bins), written as Msun (dsps_weights), FP32
+//      per unit mass (SIMT photometry) or scaled by the SSP row multiplier and
+//      split into bf16 hi + lo (tensor photometry, metallicity-major K, with
+//      the per-tile ranges and kz-block masks).
+// The kernels are instantiated with and without the nebular axis (NEB), so
+// that grids without one run the code of the two-dimensional weights.
 #include <climits>
 #include <cmath>
 
@@ -29,6 +33,9 @@ struct WArgs {
     const float *params;
     int64_t G_stride, g_begin, n;
     int n_age, n_z, K, K_pad, A_pad, KZ_pad, n_t, sfh_model, mdf_kernel, n_lut, dust_bump;
+    int n_u, SEC, u_ref, npar;   // nebular axis (n_u = 1: none), section length, reference bin, parameter rows
+    const float *uedge;          // [n_u + 1] log U bin edges (+-1e30 outer)
+    int2 *urange;                // out: per-tile log U bin ranges (atomics), with trange
     double t0, h, inv_h, dz, inv_dz, zmax, dlnlam;
     float zmax_f;          // largest float <= zmax (z <= zmax_f iff (double)z <= zmax)
     float t0_f, h_f, dlnlam_f;   // FP32 copies used by the per-galaxy warps
@@ -263,7 +270,33 @@ __device__ __forceinline__ float mdf_mean_at(const WArgs &a, const float *p, int
     return fmaf(p[7], __ldg(a.mub + i), __ldg(a.mua + i) * p[5]);
 }
 
-template <int MODE, int SFH, int MDF>
+// Sec. 3.3, Eq. nebsed: this lane's log U bin probability (lane k < n_u holds
+// P_neb(k), the triweight CDF difference over the bin's edges, in the same
+// S-form as the metallicity bins), and the galaxy's non-zero range [lo, hi]
+// (empty: {n_u, -1}).  An invalid galaxy gets {1, 0, ...} and range {0, 0}.
+__device__ __forceinline__ float pneb_lane(const WArgs &a, const float *p, bool valid, int lane, int &lo, int &hi) {
+    float pu = 0.f;
+    if (!valid) {
+        lo = hi = 0;
+        return lane == 0 ? 1.f : 0.f;
+    }
+    if (lane < a.n_u) {
+        const float isu = 1.f / p[13];
+        const bool first = lane == 0, last = lane == a.n_u - 1;
+        const float xl = first ? -1e30f : (__ldg(a.uedge + lane) - p[12]) * isu;
+        const float xh = last ? 1e30f : (__ldg(a.uedge + lane + 1) - p[12]) * isu;
+        const float sl = first ? 0.f : mdf_s<DSPS_MDF_TRIWEIGHT>(xl);
+        const float sh = last ? 0.f : mdf_s<DSPS_MDF_TRIWEIGHT>(xh);
+        pu = sh - sl;
+        if (xl <= 0.f && xh > 0.f) pu += 1.f;
+    }
+    const unsigned nzm = __ballot_sync(0xffffffffu, pu != 0.f);
+    lo = nzm ? __ffs(nzm) - 1 : a.n_u;
+    hi = nzm ? 31 - __clz(nzm) : -1;
+    return pu;
+}
+
+template <int MODE, int SFH, int MDF, bool NEB>
 __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -276,19 +309,32 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
     const int64_t gl = a.perm ? (int64_t)a.perm[gi] : gi;
     const int64_t g = a.g_begin + gl;
 
-    float mine = lane < NPAR ? a.params[(int64_t)lane * a.G_stride + g] : 0.f;
-    float p[NPAR];
+    constexpr int NP = NEB ? NPAR_MAX : NPAR;
+    constexpr int NU = NEB ? MAX_NU : 1;
+    float mine = lane < NP ? a.params[(int64_t)lane * a.G_stride + g] : 0.f;
+    float p[NP];
 #pragma unroll
-    for (int r = 0; r < NPAR; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
+    for (int r = 0; r < NP; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
 
     const float z = p[11], sig = p[6];
-    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NPAR);
+    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NP);
     valid = valid && z > 0.f && z <= a.zmax_f && sig > 0.f && p[0] > 0.f;
+    if constexpr (NEB) valid = valid && p[13] > 0.f;
     const GalPrep gp = a.prep[gl];
 
     float msum = 0.f;
     valid = sfh_stage<SFH>(a, p, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
     float *frac = sm.frac;
+    // log U bin probabilities, in every lane's registers
+    int u_lo = 0, u_hi = 0;
+    float pu[NU];
+    if constexpr (NEB) {
+        const float pu_l = pneb_lane(a, p, valid, lane, u_lo, u_hi);
+#pragma unroll
+        for (int u = 0; u < NU; ++u) pu[u] = __shfl_sync(0xffffffffu, pu_l, u);
+    } else {
+        pu[0] = 1.f;
+    }
 
     // 5-6. metallicity weights and output.
     const float inv_sig = 1.f / sig;
@@ -363,9 +409,16 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
                     bm.z |= wi == 2 ? bit : 0u;
                     bm.w |= wi == 3 ? bit : 0u;
                 }
-                {
-                    const float4 wm = __ldg(reinterpret_cast<const float4 *>(a.wmul + kz));
-                    const float w0 = om[0] * wm.x, w1 = om[1] * wm.y, w2 = om[2] * wm.z, w3 = om[3] * wm.w;
+                // one section per log U bin: omega_ij P_neb(u) at kz + u SEC
+#pragma unroll
+                for (int u = 0; u < NU; ++u) {
+                    if (NEB && u >= a.n_u) break;
+                    const int kzu = kz + u * a.SEC;
+                    const float4 wm = __ldg(reinterpret_cast<const float4 *>(a.wmul + kzu));
+                    float o[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) o[c] = NEB ? om[c] * pu[u] : om[c];
+                    const float w0 = o[0] * wm.x, w1 = o[1] * wm.y, w2 = o[2] * wm.z, w3 = o[3] * wm.w;
                     const __nv_bfloat162 h01 = __floats2bfloat162_rn(w0, w1), h23 = __floats2bfloat162_rn(w2, w3);
                     const __nv_bfloat162 l01 = __floats2bfloat162_rn(w0 - __low2float(h01), w1 - __high2float(h01));
                     const __nv_bfloat162 l23 = __floats2bfloat162_rn(w2 - __low2float(h23), w3 - __high2float(h23));
@@ -374,13 +427,19 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
                     hv.y = *reinterpret_cast<const unsigned *>(&h23);
                     lv.x = *reinterpret_cast<const unsigned *>(&l01);
                     lv.y = *reinterpret_cast<const unsigned *>(&l23);
-                    *reinterpret_cast<uint2 *>(rh + kz) = hv;
-                    *reinterpret_cast<uint2 *>(rl + kz) = lv;
+                    *reinterpret_cast<uint2 *>(rh + kzu) = hv;
+                    *reinterpret_cast<uint2 *>(rl + kzu) = lv;
                 }
             }
         }
-        // padding columns [n_z * A_pad, KZ_pad)
-        for (int kz = nz * a.A_pad + 4 * lane; kz < a.KZ_pad; kz += 128) {
+        // padding columns [n_z * A_pad, SEC) of every section but the last,
+        // then [(n_u - 1) * SEC + n_z * A_pad, KZ_pad)
+        for (int u = 0; u + 1 < (NEB ? a.n_u : 1); ++u)
+            for (int kz = u * a.SEC + nz * a.A_pad + 4 * lane; kz < (u + 1) * a.SEC; kz += 128) {
+                *reinterpret_cast<uint2 *>(rh + kz) = make_uint2(0u, 0u);
+                *reinterpret_cast<uint2 *>(rl + kz) = make_uint2(0u, 0u);
+            }
+        for (int kz = ((NEB ? a.n_u : 1) - 1) * a.SEC + nz * a.A_pad + 4 * lane; kz < a.KZ_pad; kz += 128) {
             *reinterpret_cast<uint2 *>(rh + kz) = make_uint2(0u, 0u);
             *reinterpret_cast<uint2 *>(rl + kz) = make_uint2(0u, 0u);
         }
@@ -398,8 +457,37 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
                 const int i0 = (int)floorf(s_shift);
                 atomicMin(&a.trange[t].x, i0);
                 atomicMax(&a.trange[t].y, i0);
+                atomicMin(&a.urange[t].x, u_lo);
+                atomicMax(&a.urange[t].y, u_hi);
             }
         }
+    } else if constexpr (NEB) {
+        // Age-major k = (i * n_z + j) * n_u + u: each lane takes (i, j) pairs,
+        // the metallicity bin probability from its two edges' CDFs, and writes
+        // its n_u log U bins.
+        for (int ij = lane; ij < a.n_age * nz; ij += 32) {
+            const int i = ij / nz, j = ij - i * nz;
+            float om = 0.f;
+            if (valid) {
+                const float mu_i = mdf_mean_at(a, p, i);
+                const float ul = (__ldg(a.zedge + j) - mu_i) * inv_sig;
+                const float uh = j == nz - 1 ? 1e30f : (__ldg(a.zedge + j + 1) - mu_i) * inv_sig;
+                const float sl = j == 0 ? 0.f : mdf_s<MDF>(ul);
+                const float sh = j == nz - 1 ? 0.f : mdf_s<MDF>(uh);
+                float pj = sh - sl;
+                if (ul <= 0.f && uh > 0.f) pj += 1.f;
+                om = frac[i] * pj;
+            }
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                if (u >= a.n_u) break;
+                const int k = ij * a.n_u + u;
+                if (MODE == W_MSUN) a.w_msun[gi * a.K + k] = mass * (om * pu[u]);
+                else a.w32[gi * a.K_pad + k] = om * pu[u];
+            }
+        }
+        if (MODE != W_MSUN)
+            for (int k = a.K + lane; k < a.K_pad; k += 32) a.w32[gi * a.K_pad + k] = 0.f;
     } else {
         // Age-major k, four consecutive k per lane.  The CDF at the upper edge
         // of bin j is the lower edge of bin j+1, and the outer edges (-inf,
@@ -508,7 +596,7 @@ __host__ __device__ inline size_t weights_vjp_smem_per_warp(int n_t, int n_age) 
     return weights_smem_per_warp(n_t, n_age) + ((((size_t)n_t + (size_t)n_age) * 4 + 15) & ~(size_t)15);
 }
 
-template <int SFH, int MDF>
+template <int SFH, int MDF, bool NEB>
 __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *what, int scaled, float *pbar) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -522,13 +610,15 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     if (gi >= a.n) return;
     const int64_t gl = a.perm ? (int64_t)a.perm[gi] : gi;
     const int64_t g = a.g_begin + gl;
-    float mine = lane < NPAR ? a.params[(int64_t)lane * a.G_stride + g] : 0.f;
-    float p[NPAR];
+    constexpr int NP = NEB ? NPAR_MAX : NPAR;
+    float mine = lane < NP ? a.params[(int64_t)lane * a.G_stride + g] : 0.f;
+    float p[NP];
 #pragma unroll
-    for (int r = 0; r < NPAR; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
+    for (int r = 0; r < NP; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
     const float z = p[11], sig = p[6];
-    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NPAR);
+    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NP);
     valid = valid && z > 0.f && z <= a.zmax_f && sig > 0.f && p[0] > 0.f;
+    if constexpr (NEB) valid = valid && p[13] > 0.f;
     const GalPrep gp = a.prep[gl];
     float msum = 0.f;
     valid = sfh_stage<SFH>(a, p, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
@@ -556,7 +646,127 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
     // below it (u <= -3) P(Z >= edge) = 1 and the density vanishes.
     constexpr bool tri = MDF == DSPS_MDF_TRIWEIGHT;
     const float *wrow = what + gi * a.KZ_pad;
-    for (int gq = lane; 4 * gq < a.A_pad && valid; gq += 32) {
+    float ubar_mean = 0.f, ubar_sig = 0.f;
+    if constexpr (NEB) {
+        // With a nebular axis the adjoint rows are (section u, edge e, age i):
+        // D2_u = D_u - D_ref for u != u_ref and D_ref itself, D_u the
+        // metallicity difference of dLoss/domega in log U bin u.  The walk
+        // takes D_u = D2_u + D2_ref over the galaxy's log U support, uses
+        // dw = sum_u P_u D_u where the MDF adjoint used dw, and accumulates
+        //   hd_u = sum_i frac_i sum_e P(Z >= edge e | i) D2_(u, e, i)
+        //        = dLoss/dP_u - dLoss/dP_ref,
+        // which gives the log U gradients (the P_u sum to 1, so the reference
+        // bin drops out of sum_u dLoss/dP_u dP_u/dtheta).
+        int u_lo, u_hi;
+        const float pu_l = pneb_lane(a, p, valid, lane, u_lo, u_hi);
+        float pu[MAX_NU], hd[MAX_NU];
+#pragma unroll
+        for (int u = 0; u < MAX_NU; ++u) {
+            pu[u] = __shfl_sync(0xffffffffu, pu_l, u);
+            hd[u] = 0.f;
+        }
+        const int uref = a.u_ref;
+        auto ld4 = [&](int kz) {
+            float4 v = *reinterpret_cast<const float4 *>(wrow + kz);
+            if (scaled) {
+                const float4 m = __ldg(reinterpret_cast<const float4 *>(a.wmul + kz));
+                v.x *= m.x;
+                v.y *= m.y;
+                v.z *= m.z;
+                v.w *= m.w;
+            }
+            return v;
+        };
+        for (int gq = lane; 4 * gq < a.A_pad && valid; gq += 32) {
+            float mu4[4], xl4[4], xa4[4], fr4[4], fb4[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int i = 4 * gq + c;
+                xa4[c] = __ldg(a.mua + min(i, a.n_age - 1));
+                xl4[c] = __ldg(a.mub + min(i, a.n_age - 1));
+                mu4[c] = fmaf(p[7], xl4[c], xa4[c] * p[5]);
+                fr4[c] = i < a.n_age ? frac[i] : 0.f;
+                fb4[c] = 0.f;
+            }
+            for (int e = 0; e < nz; ++e) {
+                const int kz = e * a.A_pad + 4 * gq;
+                float u[4], se[4];   // standardised edge, P(Z >= edge e | i)
+                bool dens = false;   // some age's density may be non-zero at the edge
+                if (e == 0) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) u[c] = se[c] = 1.f;
+                } else {
+                    const float ze = __ldg(a.zedge + e);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) u[c] = (ze - mu4[c]) * inv_sig;
+                    if (tri && fminf(fminf(u[0], u[1]), fminf(u[2], u[3])) >= 3.f) break;
+                    if (tri && fmaxf(fmaxf(u[0], u[1]), fmaxf(u[2], u[3])) <= -3.f) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) se[c] = 1.f;
+                    } else {
+                        dens = true;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float sv = mdf_s<MDF>(u[c]);
+                            se[c] = u[c] > 0.f ? -sv : 1.f - sv;
+                        }
+                    }
+                }
+                const float4 r = ld4(uref * a.SEC + kz);
+                float dw[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int uu = 0; uu < MAX_NU; ++uu) {
+                    if (uu >= a.n_u) break;
+                    if (uu < u_lo || uu > u_hi) continue;
+                    if (uu == uref) {
+                        dw[0] = fmaf(pu[uu], r.x, dw[0]);
+                        dw[1] = fmaf(pu[uu], r.y, dw[1]);
+                        dw[2] = fmaf(pu[uu], r.z, dw[2]);
+                        dw[3] = fmaf(pu[uu], r.w, dw[3]);
+                        continue;
+                    }
+                    const float4 v = ld4(uu * a.SEC + kz);
+                    dw[0] = fmaf(pu[uu], v.x + r.x, dw[0]);
+                    dw[1] = fmaf(pu[uu], v.y + r.y, dw[1]);
+                    dw[2] = fmaf(pu[uu], v.z + r.z, dw[2]);
+                    dw[3] = fmaf(pu[uu], v.w + r.w, dw[3]);
+                    hd[uu] = fmaf(fr4[0] * se[0], v.x,
+                                  fmaf(fr4[1] * se[1], v.y, fmaf(fr4[2] * se[2], v.z, fmaf(fr4[3] * se[3], v.w, hd[uu]))));
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) fb4[c] = fmaf(dw[c], se[c], fb4[c]);
+                if (!dens) continue;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float t = fr4[c] * dw[c] * mdf_pdf<MDF>(u[c]) * inv_sig;
+                    mu_bar = fmaf(t, xa4[c], mu_bar);
+                    sig_bar = fmaf(t, u[c], sig_bar);
+                    slope_bar = fmaf(t, xl4[c], slope_bar);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (4 * gq + c < a.n_age) fracbar[4 * gq + c] = fb4[c];
+        }
+        // dP_u/du_mean = -(pdf(x_hi) - pdf(x_lo)) / u_sigma, dP_u/du_sigma =
+        // -(pdf(x_hi) x_hi - pdf(x_lo) x_lo) / u_sigma over the bin's edges
+        // (outer edges at +-infinity contribute nothing)
+        const float isu = valid ? 1.f / p[13] : 0.f;
+#pragma unroll
+        for (int uu = 0; uu < MAX_NU; ++uu) {
+            float h = hd[uu];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) h += __shfl_xor_sync(0xffffffffu, h, off);
+            if (uu >= a.n_u || uu == uref) continue;
+            const bool first = uu == 0, last = uu == a.n_u - 1;
+            const float xl = first ? 0.f : (__ldg(a.uedge + uu) - p[12]) * isu;
+            const float xh = last ? 0.f : (__ldg(a.uedge + uu + 1) - p[12]) * isu;
+            const float dl = first ? 0.f : triweight_f(xl), dh = last ? 0.f : triweight_f(xh);
+            ubar_mean = fmaf(h, -(dh - dl) * isu, ubar_mean);
+            ubar_sig = fmaf(h, -(dh * xh - dl * xl) * isu, ubar_sig);
+        }
+    }
+    for (int gq = lane; !NEB && 4 * gq < a.A_pad && valid; gq += 32) {
         float mu4[4], xl4[4], xa4[4], fr4[4], fb4[4];   // xa4, xl4: d mu_i / d p5, d p7
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -685,6 +895,10 @@ __global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *
         const float out[8] = {tb[0], tb[1], tb[2], tb[3], tb[4], mu_bar, sig_bar, slope_bar};
 #pragma unroll
         for (int q = 0; q < 8; ++q) pbar[(int64_t)q * a.G_stride + g] = valid ? out[q] : nan;
+        if constexpr (NEB) {
+            pbar[(int64_t)11 * a.G_stride + g] = valid ? ubar_mean : nan;
+            pbar[(int64_t)12 * a.G_stride + g] = valid ? ubar_sig : nan;
+        }
     }
 }
 
@@ -696,6 +910,11 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.n = n;
     a.n_age = c.n_age;
     a.n_z = c.n_z;
+    a.n_u = c.n_u;
+    a.SEC = c.SEC;
+    a.u_ref = c.u_ref;
+    a.npar = c.npar;
+    a.uedge = c.d_uedge;
     a.K = c.K;
     a.K_pad = c.K_pad;
     a.A_pad = c.A_pad;
@@ -738,35 +957,40 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
 
 namespace {
 
-// Launches K<SFH, MDF> for the context's model pair.
-template <template <int, int> class L, typename... Args>
-cudaError_t launch_models(const Ctx &c, Args... args) {
+// Launches K<SFH, MDF, NEB> for the context's model pair and grid.
+template <template <int, int, bool> class L, bool NEB, typename... Args>
+cudaError_t launch_models_n(const Ctx &c, Args... args) {
     const int sfh = c.opts.sfh_model, mdf = c.opts.mdf_kernel;
     if (sfh == DSPS_SFH_DELAYED_TAU)
-        return mdf == DSPS_MDF_TRIWEIGHT ? L<DSPS_SFH_DELAYED_TAU, DSPS_MDF_TRIWEIGHT>::run(args...)
-                                         : L<DSPS_SFH_DELAYED_TAU, DSPS_MDF_GAUSSIAN>::run(args...);
-    return mdf == DSPS_MDF_TRIWEIGHT ? L<DSPS_SFH_DPL_QUENCH, DSPS_MDF_TRIWEIGHT>::run(args...)
-                                     : L<DSPS_SFH_DPL_QUENCH, DSPS_MDF_GAUSSIAN>::run(args...);
+        return mdf == DSPS_MDF_TRIWEIGHT ? L<DSPS_SFH_DELAYED_TAU, DSPS_MDF_TRIWEIGHT, NEB>::run(args...)
+                                         : L<DSPS_SFH_DELAYED_TAU, DSPS_MDF_GAUSSIAN, NEB>::run(args...);
+    return mdf == DSPS_MDF_TRIWEIGHT ? L<DSPS_SFH_DPL_QUENCH, DSPS_MDF_TRIWEIGHT, NEB>::run(args...)
+                                     : L<DSPS_SFH_DPL_QUENCH, DSPS_MDF_GAUSSIAN, NEB>::run(args...);
+}
+template <template <int, int, bool> class L, typename... Args>
+cudaError_t launch_models(const Ctx &c, Args... args) {
+    return c.n_u > 1 ? launch_models_n<L, true>(c, args...) : launch_models_n<L, false>(c, args...);
 }
 
-template <int SFH, int MDF>
+template <int SFH, int MDF, bool NEB>
 struct VjpLaunch {
     static cudaError_t run(const WArgs &a, const float *what, int scaled, float *pbar, unsigned grid, size_t smem,
                            cudaStream_t s) {
-        cudaFuncSetAttribute(weights_vjp_kernel<SFH, MDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        weights_vjp_kernel<SFH, MDF><<<grid, 256, smem, s>>>(a, what, scaled, pbar);
+        cudaFuncSetAttribute(weights_vjp_kernel<SFH, MDF, NEB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        weights_vjp_kernel<SFH, MDF, NEB><<<grid, 256, smem, s>>>(a, what, scaled, pbar);
         return cudaGetLastError();
     }
 };
 
 template <int MODE>
 struct WeightsLaunch {
-    template <int SFH, int MDF>
+    template <int SFH, int MDF, bool NEB>
     struct L {
         static cudaError_t run(const WArgs &a, unsigned grid, size_t smem, cudaStream_t s) {
-            cudaFuncSetAttribute(weights_kernel<MODE, SFH, MDF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(weights_kernel<MODE, SFH, MDF, NEB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
-            weights_kernel<MODE, SFH, MDF><<<grid, 256, smem, s>>>(a);
+            weights_kernel<MODE, SFH, MDF, NEB><<<grid, 256, smem, s>>>(a);
             return cudaGetLastError();
         }
     };
@@ -797,6 +1021,7 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
     a.perm = sorted ? w.perm : nullptr;
     a.gidx = sorted ? w.gidx : nullptr;
     a.trange = sorted && mode == W_OMEGA_BF16X2 ? w.trange : nullptr;
+    a.urange = w.urange;
     a.kmask = w.kmask;
     a.kmw = c.kmask_words;
     const int warps = 8;

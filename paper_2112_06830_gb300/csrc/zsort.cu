@@ -7,7 +7,9 @@
 // log age.  Rows of one 128-galaxy tile then share a narrow redshift range (the
 // tile needs only the wavelength tiles inside the redshifted filter band) and a
 // narrow metallicity range (the tile's non-zero weights fill only the K blocks
-// of a few metallicity bins).  A last pass orders the rows inside each tile by
+// of a few metallicity bins).  With a nebular axis the inner key is 8 bins of
+// the mean log U times 16 metallicity bins, so that a tile also spans few log U
+// sections.  A last pass orders the rows inside each tile by
 // redshift, so that the 32 rows of one epilogue warp read the filter table at
 // nearby shifts.
 // Sorting is a scheduling device only: every galaxy's magnitudes come from its
@@ -28,6 +30,8 @@ struct SortKey {
     float inv_dlnlam, zscale;      // s = log1p(z) * inv_dlnlam; z bin = floor(s * zscale)
     float mu_lo, mu_scale;         // mu bin = floor((mua p5 + mub p7 - mu_lo) * mu_scale)
     float mua, mub;                // MDF mean at the middle log age
+    const float *um;               // parameter row 12 (nebular axis), or nullptr
+    float u_lo, u_scale;           // u bin = floor((u_mean - u_lo) * u_scale), 8 bins
 };
 
 __device__ __forceinline__ int sort_key(const SortKey &k, int64_t i) {
@@ -37,16 +41,24 @@ __device__ __forceinline__ int sort_key(const SortKey &k, int64_t i) {
     const float m = fmaf(k.slope[i], k.mub, k.mua * k.mu[i]);
     int mb = 0;
     if (isfinite(m)) mb = (int)fminf(fmaxf((m - k.mu_lo) * k.mu_scale, 0.f), (float)(ZSORT_MUBINS - 1));
+    if (k.um) {
+        constexpr int UB = 8, MB = ZSORT_MUBINS / UB;
+        const float u = k.um[i];
+        int ub = 0;
+        if (isfinite(u)) ub = (int)fminf(fmaxf((u - k.u_lo) * k.u_scale, 0.f), (float)(UB - 1));
+        mb = ub * MB + mb / UB;
+    }
     return zb * ZSORT_MUBINS + mb;
 }
 
 // Histogram of the keys; the first threads also reset the per-tile ranges
 // and block masks.
-__global__ void zsort_hist_kernel(SortKey k, int64_t n, int *hist, int2 *trange, unsigned *kmask, int n_tiles,
-                                  int kmw) {
+__global__ void zsort_hist_kernel(SortKey k, int64_t n, int *hist, int2 *trange, int2 *urange, int n_u,
+                                  unsigned *kmask, int n_tiles, int kmw) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_tiles) {
         trange[i] = make_int2(TRANGE_EMPTY_LO, TRANGE_EMPTY_HI);
+        urange[i] = make_int2(n_u, -1);
         for (int w = 0; w < kmw; ++w) kmask[i * kmw + w] = 0u;
     }
     if (i < n) atomicAdd(hist + sort_key(k, i), 1);
@@ -167,11 +179,15 @@ cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *params, 
     k.mu_scale = c.sort_mu_scale;
     k.mua = c.sort_mua;
     k.mub = c.sort_mub;
+    k.um = c.n_u > 1 ? params + 12 * G_stride + g_begin : nullptr;
+    k.u_lo = c.sort_u_lo;
+    k.u_scale = c.sort_u_scale;
     const int n_tiles = (int)((n + 127) / 128);
     cudaError_t e = cudaMemsetAsync(w.hist, 0, ZSORT_BUCKETS * sizeof(int), s);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((n + 255) / 256);   // n >= n_tiles
-    zsort_hist_kernel<<<blocks, 256, 0, s>>>(k, n, w.hist, w.trange, w.kmask, n_tiles, c.kmask_words);
+    zsort_hist_kernel<<<blocks, 256, 0, s>>>(k, n, w.hist, w.trange, w.urange, c.n_u, w.kmask, n_tiles,
+                                             c.kmask_words);
     zsort_scan_kernel<<<1, 1024, 0, s>>>(w.hist);
     zsort_scatter_kernel<<<blocks, 256, 0, s>>>(k, n, w.hist, w.perm);
     zsort_tile_kernel<<<(unsigned)n_tiles, 128, 0, s>>>(k, n, w.perm);

@@ -38,6 +38,9 @@ DSPS_PREC_FP32 = 0
 DSPS_PREC_BF16X3 = 1
 DSPS_NPAR = 12
 DSPS_NGRAD = 11
+DSPS_NPAR_NEB = 14
+DSPS_NGRAD_NEB = 13
+DSPS_MAX_NU = 8
 DSPS_MAX_FILTERS = 16
 
 
@@ -45,7 +48,8 @@ class dsps_grid(C.Structure):
     _fields_ = [("n_age", C.c_int32), ("n_z", C.c_int32), ("n_lam", C.c_int32),
                 ("log_age_yr", C.POINTER(C.c_double)), ("lgz", C.POINTER(C.c_double)),
                 ("lam", C.POINTER(C.c_double)), ("l_ssp", C.POINTER(C.c_float)),
-                ("t0_gyr", C.c_double), ("t1_gyr", C.c_double), ("n_t", C.c_int32)]
+                ("t0_gyr", C.c_double), ("t1_gyr", C.c_double), ("n_t", C.c_int32),
+                ("n_u", C.c_int32), ("lgu", C.POINTER(C.c_double))]
 
 
 class dsps_opts(C.Structure):
@@ -300,9 +304,14 @@ class Context:
                       np.ascontiguousarray(ssp.lam, dtype=np.float64),
                       np.ascontiguousarray(ssp.l_ssp, dtype=np.float32)]
         la, lz, lm, ls = self._keep
+        lgu = getattr(ssp, "lgu", None)
+        lu = np.ascontiguousarray(lgu, dtype=np.float64) if lgu is not None and len(lgu) > 1 else None
+        self._keep.append(lu)
         g = dsps_grid(len(la), len(lz), len(lm), la.ctypes.data_as(C.POINTER(C.c_double)),
                       lz.ctypes.data_as(C.POINTER(C.c_double)), lm.ctypes.data_as(C.POINTER(C.c_double)),
-                      ls.ctypes.data_as(C.POINTER(C.c_float)), float(ssp.t0), float(ssp.t1), int(ssp.n_t))
+                      ls.ctypes.data_as(C.POINTER(C.c_float)), float(ssp.t0), float(ssp.t1), int(ssp.n_t),
+                      len(lu) if lu is not None else 0,
+                      lu.ctypes.data_as(C.POINTER(C.c_double)) if lu is not None else None)
         o = dsps_default_opts()
         o.om0, o.w0, o.h, o.z_max = om0, w0, h, z_max
         o.sfh_model, o.mdf_kernel, o.device = sfh_model, mdf_kernel, device
@@ -321,6 +330,9 @@ class Context:
             o.n_streams = n_streams
         self.device = device
         self.n_age, self.n_z = len(la), len(lz)
+        self.n_u = len(lu) if lu is not None else 1
+        self.npar = DSPS_NPAR_NEB if self.n_u > 1 else DSPS_NPAR      # parameter rows
+        self.ngrad = DSPS_NGRAD_NEB if self.n_u > 1 else DSPS_NGRAD   # gradient rows
         self.handle = dsps_create(g, o)
         self.n_filt = {}
 
@@ -342,16 +354,17 @@ class Context:
 
     def weights(self, params, stream=None):
         import torch
-        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == DSPS_NPAR
+        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == self.npar
         params = params.contiguous()
         G = params.shape[1]
-        out = torch.empty((G, self.n_age, self.n_z), dtype=torch.float32, device=params.device)
+        shape = (G, self.n_age, self.n_z) + ((self.n_u,) if self.n_u > 1 else ())
+        out = torch.empty(shape, dtype=torch.float32, device=params.device)
         dsps_weights(self.handle, G, params.data_ptr(), out.data_ptr(), _stream_handle(stream))
         return out
 
     def photometry(self, params, set_id, precision=DSPS_PREC_BF16X3, out=None, stream=None):
         import torch
-        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == DSPS_NPAR
+        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == self.npar
         params = params.contiguous()
         G = params.shape[1]
         Q = self.n_filt[set_id]
@@ -368,7 +381,7 @@ class Context:
         G = params.shape[1]
         Q = self.n_filt[set_id]
         mags = torch.empty((G, Q), dtype=torch.float32, device=params.device) if want_mags else None
-        pbar = torch.empty((DSPS_NGRAD, G), dtype=torch.float32, device=params.device)
+        pbar = torch.empty((self.ngrad, G), dtype=torch.float32, device=params.device)
         dsps_photometry_vjp(self.handle, G, params.data_ptr(), set_id, precision, mag_bar.data_ptr(),
                             mags.data_ptr() if mags is not None else None, pbar.data_ptr(),
                             _stream_handle(stream))
@@ -421,7 +434,7 @@ class Context:
         ew_bar = ew_bar.contiguous().to(torch.float32)
         G = params.shape[1]
         ew = torch.empty(G, dtype=torch.float32, device=params.device)
-        pbar = torch.empty((DSPS_NGRAD, G), dtype=torch.float32, device=params.device)
+        pbar = torch.empty((self.ngrad, G), dtype=torch.float32, device=params.device)
         dsps_line_ew_vjp(self.handle, G, params.data_ptr(), line_id, ew_bar.data_ptr(), ew.data_ptr(),
                          pbar.data_ptr(), _stream_handle(stream))
         return ew, pbar
@@ -431,7 +444,8 @@ class Context:
 
     # ---- request loop (host buffers) ----
     def submit(self, params, set_id, precision=DSPS_PREC_BF16X3, mag_bar=None):
-        """Queues a population held in host memory (numpy float32 [12, G]); the
+        """Queues a population held in host memory (numpy float32 [12, G], or
+        [14, G] with a nebular axis); the
         returned Ticket keeps the host buffers alive until it is polled."""
         params = np.ascontiguousarray(params, dtype=np.float32)
         G = params.shape[1]
@@ -440,7 +454,7 @@ class Context:
         req = dsps_request(G, params.ctypes.data, set_id, precision, 0, None, t.mags.ctypes.data, None)
         if mag_bar is not None:
             t.mag_bar = np.ascontiguousarray(mag_bar, dtype=np.float32).reshape(G, Q)
-            t.param_bar = np.empty((DSPS_NGRAD, G), dtype=np.float32)
+            t.param_bar = np.empty((self.ngrad, G), dtype=np.float32)
             req.want_grad = 1
             req.mag_bar = t.mag_bar.ctypes.data
             req.param_bar = t.param_bar.ctypes.data
