@@ -50,7 +50,8 @@ class _Grid(C.Structure):
                 ("om0", C.c_double), ("w0", C.c_double), ("h", C.c_double),
                 ("sfh_model", C.c_int), ("mdf_kernel", C.c_int),
                 ("mdf_mean", C.c_int), ("mdf_x0", C.c_double), ("mdf_h", C.c_double),
-                ("dust_bump", C.c_int), ("n_u", C.c_int), ("lgu", C.POINTER(C.c_double))]
+                ("dust_bump", C.c_int), ("n_u", C.c_int), ("lgu", C.POINTER(C.c_double)),
+                ("dust_law", C.c_int)]
 
 
 class _Filters(C.Structure):
@@ -86,6 +87,8 @@ def _load():
             lib.orc_dust_trans.restype = C.c_double
             lib.orc_pneb.argtypes = [C.POINTER(_Grid), C.c_double, C.c_double, dp, dp, dp]
             lib.orc_pneb.restype = None
+            lib.orc_k0.argtypes = [C.c_double]
+            lib.orc_k0.restype = C.c_double
             lib.orc_dust_trans.argtypes = [C.c_double] * 3
             lib.orc_drude.restype = C.c_double
             lib.orc_drude.argtypes = [C.c_double]
@@ -123,7 +126,7 @@ class Grid:
 
     def __init__(self, log_age_yr, lgz, lam, l_ssp, t0=0.05, t1=13.8, n_t=200,
                  om0=0.3, w0=-1.0, h=0.7, sfh_model=0, mdf_kernel=0, mdf_mean=0, mdf_x0=9.0, mdf_h=0.5,
-                 dust_bump=0, lgu=None):
+                 dust_bump=0, lgu=None, dust_law=0):
         self.log_age_yr = _f64(log_age_yr)
         self.lgz = _f64(lgz)
         self.lam = _f64(lam)
@@ -135,11 +138,12 @@ class Grid:
         self.sfh_model, self.mdf_kernel = int(sfh_model), int(mdf_kernel)
         self.mdf_mean, self.mdf_x0, self.mdf_h = int(mdf_mean), float(mdf_x0), float(mdf_h)
         self.dust_bump = int(dust_bump)
+        self.dust_law = int(dust_law)
         self._c = _Grid(len(self.log_age_yr), len(self.lgz), len(self.lam), _dp(self.log_age_yr),
                         _dp(self.lgz), _dp(self.lam), _dp(self.l_ssp), self.t0, self.t1, self.n_t,
                         self.om0, self.w0, self.h, self.sfh_model, self.mdf_kernel,
                         self.mdf_mean, self.mdf_x0, self.mdf_h, self.dust_bump, nu,
-                        _dp(self.lgu) if self.lgu is not None else None)
+                        _dp(self.lgu) if self.lgu is not None else None, self.dust_law)
 
     @property
     def n_age(self):
@@ -284,6 +288,11 @@ def colour_cut_histogram(mags, band_a, band_b, cut, band_r, lo, hi, n_bins):
     r = m[sel, band_r]
     r = r[(r >= lo) & (r < hi)]
     return np.histogram(r, bins=n_bins, range=(lo, hi))[0].astype(np.int64)
+
+
+def k0(lam):
+    """The starburst curve k0 of Eq. (kzero) at lam [A]."""
+    return _load().orc_k0(float(lam))
 
 
 def dust_trans(lam, Av, delta):

@@ -67,6 +67,8 @@ typedef struct {
     int n_u;                   /* log U values of the nebular axis (<= 1: none) */
     const double *lgu;         /* [n_u] log10 U, increasing; l_ssp is then
                                   [n_age][n_z][n_u][n_lam]                  */
+    int dust_law;              /* 0: power-law stand-in for k0 (lam/lam_V)^delta / 4.05,
+                                  1: Eq. (salim) with the piecewise k0 (Eq. kzero) */
 } orc_grid;
 
 static int orc_nu(const orc_grid *g) { return g->n_u > 1 ? g->n_u : 1; }
@@ -377,14 +379,41 @@ double orc_drude(double lam)
     return x * x / (d * d + x * x);
 }
 
-/* Attenuation curve A_lambda / Av.  Without the bump, the power law above;
- * with it, Eq. (salim)'s k_lambda / 4.05 = k0 (lam/lam_V)^delta / 4.05 +
- * D_lambda / 4.05 with the power law standing for k0 (lam/lam_V)^delta / 4.05
- * and the bump amplitude E_b = 0.85 - 1.9 delta (Kriek & Conroy, as in the
- * paper).  *dd: d(A_lambda / Av) / d delta. */
+/* Eq. (kzero): the starburst curve k0(lam), lam in Angstrom.  The paper takes
+ * it from Calzetti et al. (2000) and Leitherer et al. (2002) without
+ * printing either; the published fits are
+ *   Leitherer:  5.472 + 0.671/x - 9.218e-3/x^2 + 2.620e-3/x^3       (0.097-0.18 um)
+ *   Calzetti:   2.659 (-2.156 + 1.509/x - 0.198/x^2 + 0.011/x^3) + 4.05  (0.12-0.63 um)
+ *               2.659 (-1.857 + 1.040/x) + 4.05                        (0.63-2.2 um)
+ * with x = lam in um.  Reading: Leitherer below 0.15 um and Calzetti above
+ * (the printed assignment is the other way round, outside both fits' ranges),
+ * each extrapolated beyond its range, k0 clipped at 0 (the Calzetti fit
+ * crosses 0 near 3.1 um). */
+double orc_k0(double lam)
+{
+    double x = lam * 1e-4, k;
+    if (x < 0.15) k = 5.472 + 0.671 / x - 9.218e-3 / (x * x) + 2.620e-3 / (x * x * x);
+    else if (x < 0.63) k = 2.659 * (-2.156 + 1.509 / x - 0.198 / (x * x) + 0.011 / (x * x * x)) + 4.05;
+    else k = 2.659 * (-1.857 + 1.040 / x) + 4.05;
+    return k > 0.0 ? k : 0.0;
+}
+
+/* Attenuation curve A_lambda / Av = k_lambda / 4.05 (Eq. salim),
+ * k_lambda = k0 (lam/lam_V)^delta + E_b D0 with the bump of amplitude
+ * E_b = 0.85 - 1.9 delta (Kriek & Conroy, as in the paper) when it is on.
+ * dust_law 0 replaces k0 (lam/lam_V)^delta / 4.05 by the power law
+ * (lam/lam_V)^(-0.7 + delta) (k = 1 at lam_V); dust_law 1 takes Eq. (kzero).
+ * *dd: d(A_lambda / Av) / d delta. */
 double orc_dust_curve(const orc_grid *g, double lam, double delta, double *dd)
 {
-    double u = pow(lam / ORC_LAMV, -0.7 + delta), c = u, dc = u * log(lam / ORC_LAMV);
+    double u, c, dc;
+    if (g->dust_law == 1) {
+        u = orc_k0(lam) / 4.05 * pow(lam / ORC_LAMV, delta);
+    } else {
+        u = pow(lam / ORC_LAMV, -0.7 + delta);
+    }
+    c = u;
+    dc = u * log(lam / ORC_LAMV);
     if (g->dust_bump) {
         double D0 = orc_drude(lam);
         c += (0.85 - 1.9 * delta) * D0 / 4.05;

@@ -336,7 +336,7 @@ def test_logm_shifts_all_bands():
 # ---------------------------------------------------------------- brute force
 
 def _brute_force_mags(log_age, lgz, lam, L, filters, par, sfh_model, kernel, om0=0.3, h=0.7, mean=0,
-                      x0=9.0, hw=0.5, bump=0):
+                      x0=9.0, hw=0.5, bump=0, law=0):
     """Independent restatement on a tiny grid: scipy quadrature of the SFR
     function itself for every age bin, quadrature of the MDF density for every
     lgZ bin, scipy quadrature for the cosmology, and an explicit loop for the
@@ -378,6 +378,15 @@ def _brute_force_mags(log_age, lgz, lam, L, filters, par, sfh_model, kernel, om0
             w = 0.5 * ((lam[min(n + 1, len(lam) - 1)] - lam[max(n - 1, 0)]))
             T = np.interp((1 + z) * lam[n], fl, ft, left=0.0, right=0.0)
             A = (lam[n] / 5500.0) ** (-0.7 + par[9])
+            if law:    # Eq. (salim): k0 (lam/lam_V)^delta / 4.05, k0 of Eq. (kzero)
+                x = lam[n] * 1e-4
+                if x < 0.15:
+                    k0 = 5.472 + 0.671 / x - 9.218e-3 / x ** 2 + 2.620e-3 / x ** 3
+                elif x < 0.63:
+                    k0 = 2.659 * (-2.156 + 1.509 / x - 0.198 / x ** 2 + 0.011 / x ** 3) + 4.05
+                else:
+                    k0 = 2.659 * (-1.857 + 1.040 / x) + 4.05
+                A = max(k0, 0.0) / 4.05 * (lam[n] / 5500.0) ** par[9]
             if bump:   # Drude profile at 2175 A, width 350 A, amplitude 0.85 - 1.9 delta, over 4.05
                 x = lam[n] * 350.0
                 A += (0.85 - 1.9 * par[9]) * x * x / ((lam[n] ** 2 - 2175.0 ** 2) ** 2 + x * x) / 4.05
@@ -388,9 +397,9 @@ def _brute_force_mags(log_age, lgz, lam, L, filters, par, sfh_model, kernel, om0
     return np.array(out)
 
 
-@pytest.mark.parametrize("sfh_model,kernel,mean,bump", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 1, 0, 0), (1, 0, 1, 0),
-                                                        (1, 0, 0, 1)])
-def test_brute_force_tiny_grid(sfh_model, kernel, mean, bump):
+@pytest.mark.parametrize("sfh_model,kernel,mean,bump,law", [(0, 0, 0, 0, 0), (1, 0, 0, 0, 0), (1, 1, 0, 0, 0),
+                                                            (1, 0, 1, 0, 0), (1, 0, 0, 1, 0), (1, 0, 0, 1, 1)])
+def test_brute_force_tiny_grid(sfh_model, kernel, mean, bump, law):
     log_age = np.array([6.0, 7.5, 8.7, 9.6])
     lgz = np.array([-1.0, -0.4, 0.1])
     lam = np.geomspace(2000.0, 9000.0, 16)
@@ -399,9 +408,9 @@ def test_brute_force_tiny_grid(sfh_model, kernel, mean, bump):
     filters = [synth.gaussian_filter(c, fwhm=600.0, step=5.0) for c in (4000.0, 6500.0)]
     n_t = 40001  # fine time grid: the piecewise-linear reading is then within 1e-7 of the quadrature
     if bump:
-        lam = np.geomspace(1500.0, 9000.0, 16)      # across the 2175 A bump
+        lam = np.geomspace(1200.0, 9000.0, 16)      # across the 2175 A bump (and 0.15 um, 0.63 um)
     g = oracle.Grid(log_age, lgz, lam, L, n_t=n_t, sfh_model=sfh_model, mdf_kernel=kernel, mdf_mean=mean,
-                    mdf_x0=8.0, mdf_h=0.6, dust_bump=bump)
+                    mdf_x0=8.0, mdf_h=0.6, dust_bump=bump, dust_law=law)
     F = oracle.Filters(filters)
     p = synth.make_population(sfh_model, 3, 5)
     p[6] = 0.35
@@ -411,19 +420,19 @@ def test_brute_force_tiny_grid(sfh_model, kernel, mean, bump):
     m = oracle.mags(g, F, p)
     for gi in range(p.shape[1]):
         ref = _brute_force_mags(log_age, lgz, lam, L, filters, p[:, gi], sfh_model, kernel, mean=mean, x0=8.0,
-                                hw=0.6, bump=bump)
+                                hw=0.6, bump=bump, law=law)
         np.testing.assert_allclose(m[gi], ref, atol=2e-6)
 
 
 # ---------------------------------------------------------------- gradients
 
-@pytest.mark.parametrize("wl,model,kernel,mean,bump", [("small", 0, 0, 0, 0), ("small", 1, 0, 0, 0),
-                                                        ("small", 1, 1, 0, 0), ("small", 1, 0, 1, 0),
-                                                        ("small", 1, 0, 0, 1)])
-def test_adjoint_matches_central_differences(wl, model, kernel, mean, bump):
+@pytest.mark.parametrize("wl,model,kernel,mean,bump,law", [("small", 0, 0, 0, 0, 0), ("small", 1, 0, 0, 0, 0),
+                                                            ("small", 1, 1, 0, 0, 0), ("small", 1, 0, 1, 0, 0),
+                                                            ("small", 1, 0, 0, 1, 0), ("small", 1, 0, 0, 1, 1)])
+def test_adjoint_matches_central_differences(wl, model, kernel, mean, bump, law):
     g, f, _ = synth.workload_inputs(wl, n_gal=1)
     G = oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, sfh_model=model, mdf_kernel=kernel, mdf_mean=mean,
-                    dust_bump=bump)
+                    dust_bump=bump, dust_law=law)
     F = oracle.Filters(f)
     p = synth.make_population(model, 3, 21)
     if mean == 1:
@@ -567,3 +576,31 @@ def test_colour_cut_histogram_counts_a_hand_made_population():
                   [23.0, 21.0, 18.0]])   # colour 2.0, r on the lower edge -> bin 0
     h = oracle.colour_cut_histogram(m, 0, 1, 0.5, 2, 18.0, 20.0, 4)
     np.testing.assert_array_equal(h, [1, 1, 0, 1])
+
+
+# ---------------------------------------------------------------- Eq. (salim) with Eq. (kzero)
+
+def test_k0_is_normalised_at_v_and_continuous_where_the_fits_meet():
+    """The starburst curve is built so that k(V) = R_V = 4.05; the Leitherer
+    and Calzetti fits meet at 0.15 um to a few tenths of a per cent, and the two
+    Calzetti pieces at 0.63 um to about 1 per cent."""
+    assert oracle.k0(5500.0) == pytest.approx(4.05, rel=1e-3)
+    lo, hi = oracle.k0(1500.0 - 1e-6), oracle.k0(1500.0)
+    assert abs(lo - hi) / hi < 3e-3
+    lo, hi = oracle.k0(6300.0 - 1e-6), oracle.k0(6300.0)
+    assert abs(lo - hi) / hi < 1e-2
+    ks = [oracle.k0(l) for l in np.geomspace(912.0, 3.0e4, 400)]
+    assert all(a >= b for a, b in zip(ks, ks[1:]))          # decreasing with wavelength
+    assert oracle.k0(3.2e4) == 0.0 and oracle.k0(1e5) == 0.0  # clipped where the fit turns negative
+
+
+def test_salim_curve_at_v_is_av_for_every_delta():
+    lam = np.geomspace(1000.0, 1e5, 50)
+    g = oracle.Grid([9.0], [0.0], lam, np.ones((1, 1, len(lam))), dust_law=1)
+    for d in (-0.6, -0.2, 0.0, 0.3):
+        c, dc = oracle.dust_curve(g, 5500.0, d)
+        assert c == pytest.approx(oracle.k0(5500.0) / 4.05, rel=1e-14)
+        assert dc == pytest.approx(0.0, abs=1e-15)           # the tilt pivots at lambda_V
+        for l in (1200.0, 3000.0, 9000.0):
+            fd = (oracle.dust_curve(g, l, d + 1e-6)[0] - oracle.dust_curve(g, l, d - 1e-6)[0]) / 2e-6
+            assert oracle.dust_curve(g, l, d)[1] == pytest.approx(fd, rel=1e-7)
