@@ -51,7 +51,8 @@ class _Grid(C.Structure):
                 ("sfh_model", C.c_int), ("mdf_kernel", C.c_int),
                 ("mdf_mean", C.c_int), ("mdf_x0", C.c_double), ("mdf_h", C.c_double),
                 ("dust_bump", C.c_int), ("n_u", C.c_int), ("lgu", C.POINTER(C.c_double)),
-                ("dust_law", C.c_int)]
+                ("dust_law", C.c_int), ("dust_agedep", C.c_int), ("dust_x0", C.c_double),
+                ("dust_h", C.c_double)]
 
 
 class _Filters(C.Structure):
@@ -126,7 +127,7 @@ class Grid:
 
     def __init__(self, log_age_yr, lgz, lam, l_ssp, t0=0.05, t1=13.8, n_t=200,
                  om0=0.3, w0=-1.0, h=0.7, sfh_model=0, mdf_kernel=0, mdf_mean=0, mdf_x0=9.0, mdf_h=0.5,
-                 dust_bump=0, lgu=None, dust_law=0):
+                 dust_bump=0, lgu=None, dust_law=0, dust_agedep=0, dust_x0=7.0, dust_h=0.1):
         self.log_age_yr = _f64(log_age_yr)
         self.lgz = _f64(lgz)
         self.lam = _f64(lam)
@@ -139,11 +140,13 @@ class Grid:
         self.mdf_mean, self.mdf_x0, self.mdf_h = int(mdf_mean), float(mdf_x0), float(mdf_h)
         self.dust_bump = int(dust_bump)
         self.dust_law = int(dust_law)
+        self.dust_agedep, self.dust_x0, self.dust_h = int(dust_agedep), float(dust_x0), float(dust_h)
         self._c = _Grid(len(self.log_age_yr), len(self.lgz), len(self.lam), _dp(self.log_age_yr),
                         _dp(self.lgz), _dp(self.lam), _dp(self.l_ssp), self.t0, self.t1, self.n_t,
                         self.om0, self.w0, self.h, self.sfh_model, self.mdf_kernel,
                         self.mdf_mean, self.mdf_x0, self.mdf_h, self.dust_bump, nu,
-                        _dp(self.lgu) if self.lgu is not None else None, self.dust_law)
+                        _dp(self.lgu) if self.lgu is not None else None, self.dust_law,
+                        self.dust_agedep, self.dust_x0, self.dust_h)
 
     @property
     def n_age(self):
@@ -163,11 +166,11 @@ class Grid:
 
     @property
     def npar(self):
-        return NPAR + 2 if self.n_u > 1 else NPAR
+        return NPAR + (2 if self.n_u > 1 else 0) + (2 if self.dust_agedep else 0)
 
     @property
     def ngrad(self):
-        return NGRAD + 2 if self.n_u > 1 else NGRAD
+        return NGRAD + (2 if self.n_u > 1 else 0) + (2 if self.dust_agedep else 0)
 
 
 class Filters:

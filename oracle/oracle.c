@@ -28,8 +28,11 @@
  *   rows 12,13 (grids with a nebular axis, n_u > 1 log U values, Sec. 3.3)
  *              u_mean, u_sigma: mean and width [dex] of the triweight
  *              distribution of log10 U
+ *   next 2     (age-dependent dust, Sec. 3.4.1) Av_old, delta_old: rows 8, 9
+ *              then hold the young-star values
  * Gradient layout (11 rows): rows 0..10 of the above (z gets no gradient);
- * with a nebular axis 13 rows, rows 11, 12 = u_mean, u_sigma.
+ * with a nebular axis 13 rows, rows 11, 12 = u_mean, u_sigma; with
+ * age-dependent dust two more rows at the end, Av_old and delta_old.
  *
  * Besides the magnitudes, the oracle gives the rest-frame attenuated spectrum
  * and the equivalent width of an emission line (Sec. 2.2, Eq. eqw) with their
@@ -42,8 +45,8 @@
 
 #define ORC_NPAR 12
 #define ORC_NGRAD 11
-#define ORC_NPAR_MAX 14              /* with the nebular axis (rows 12, 13) */
-#define ORC_NGRAD_MAX 13
+#define ORC_NPAR_MAX 16              /* with the nebular axis and age-dependent dust */
+#define ORC_NGRAD_MAX 15
 #define ORC_AB0 1.13492e-13          /* Sec. 2.2, Eq. (restmag): AB zero point at 10 pc, Lsun/Hz */
 #define ORC_LAMV 5500.0              /* Sec. 3.4, Eq. (salim): lambda_V in Angstrom */
 #define ORC_SIGQ 0.3                 /* width of the quench transition [Gyr] (reading) */
@@ -69,11 +72,14 @@ typedef struct {
                                   [n_age][n_z][n_u][n_lam]                  */
     int dust_law;              /* 0: power-law stand-in for k0 (lam/lam_V)^delta / 4.05,
                                   1: Eq. (salim) with the piecewise k0 (Eq. kzero) */
+    int dust_agedep;           /* 1: Av, delta move from young to old values (Sec. 3.4.1) */
+    double dust_x0, dust_h;    /* centre [log10 yr] and width of that transition */
 } orc_grid;
 
 static int orc_nu(const orc_grid *g) { return g->n_u > 1 ? g->n_u : 1; }
-static int orc_npar(const orc_grid *g) { return g->n_u > 1 ? ORC_NPAR_MAX : ORC_NPAR; }
-static int orc_ngrad(const orc_grid *g) { return g->n_u > 1 ? ORC_NGRAD_MAX : ORC_NGRAD; }
+static int orc_row_dust_old(const orc_grid *g) { return ORC_NPAR + (g->n_u > 1 ? 2 : 0); }
+static int orc_npar(const orc_grid *g) { return orc_row_dust_old(g) + (g->dust_agedep ? 2 : 0); }
+static int orc_ngrad(const orc_grid *g) { return ORC_NGRAD + (g->n_u > 1 ? 2 : 0) + (g->dust_agedep ? 2 : 0); }
 
 typedef struct {
     int n_filt;
@@ -540,14 +546,31 @@ typedef struct {
     double *P, *dPmu, *dPsig;  /* [n_age][n_z] MDF bin probabilities and derivatives */
     double *dmu5, *dmu7;       /* [n_age] d mu_i / d p5, d p7                       */
     double *Pu, *dPu_us, *dPu_su; /* [n_u] nebular bin probabilities and derivatives */
-    double *S;                 /* [n_lam] sum_ij omega_ij L_ijn (per unit mass)      */
-    double *F, *u, *du;        /* [n_lam] dust transmission, A/Av, d(A/Av)/d delta   */
+    /* Dust groups: every age bin with age-dependent dust (Sec. 3.4.1,
+     * Eq. agedep_dust_csp), else one group of all ages. */
+    int ND;
+    double *Sd;                /* [ND][n_lam] sum over the group's ages of omega_k L_kn (per unit mass) */
+    double *Fd, *ud, *dud;     /* [ND][n_lam] transmission, A/Av, d(A/Av)/d delta     */
+    double *Avd, *Td;          /* [ND] the group's Av and its weight T on the old values */
+    double *L;                 /* [n_lam] sum_d F_d S_d: attenuated spectrum per unit mass */
 } gal_state;
+
+/* Dust of age bin i (Sec. 3.4.1): Av and delta move from the young values
+ * (rows 8, 9) to the old ones along T = T_erf((log10 age_i - x0) / h), like
+ * the MDF mean of Eq. (agedep_mdf); without age dependence T = 0. */
+static void orc_dust_at_age(const orc_grid *g, const double *par, int i, double *Av, double *delta, double *T)
+{
+    double t = 0.0;
+    if (g->dust_agedep) t = orc_triweight_cdf((g->log_age_yr[i] - g->dust_x0) / g->dust_h);
+    int r = orc_row_dust_old(g);
+    *T = t;
+    *Av = g->dust_agedep ? (1.0 - t) * par[8] + t * par[r] : par[8];
+    *delta = g->dust_agedep ? (1.0 - t) * par[9] + t * par[r + 1] : par[9];
+}
 
 static void gal_forward(const orc_grid *g, const double *par, double t_obs, gal_state *st)
 {
     int N = g->n_lam, NA = g->n_age, NZ = g->n_z, NU = orc_nu(g), K = NA * NZ * NU, NT = g->n_t;
-    double Av = par[8], delta = par[9];
     double h = (g->t1 - g->t0) / (NT - 1);
     st->sfr = malloc(sizeof(double) * NT);
     st->dsfr = malloc(sizeof(double) * NT * 5);
@@ -572,32 +595,73 @@ static void gal_forward(const orc_grid *g, const double *par, double t_obs, gal_
     st->dPu_us = malloc(sizeof(double) * NU);
     st->dPu_su = malloc(sizeof(double) * NU);
     orc_pneb(g, NU > 1 ? par[12] : 0.0, NU > 1 ? par[13] : 1.0, st->Pu, st->dPu_us, st->dPu_su);
-    st->S = calloc(N, sizeof(double));
+    int ND = g->dust_agedep ? NA : 1;
+    st->ND = ND;
+    st->Sd = calloc((size_t)ND * N, sizeof(double));
     for (int k = 0; k < K; ++k) {
-        double w = st->frac[k / (NZ * NU)] * st->P[k / NU] * st->Pu[k % NU];
+        int i = k / (NZ * NU), d = ND > 1 ? i : 0;
+        double w = st->frac[i] * st->P[k / NU] * st->Pu[k % NU];
         const double *L = g->l_ssp + (size_t)k * N;
-        for (int n = 0; n < N; ++n) st->S[n] += w * L[n];
+        for (int n = 0; n < N; ++n) st->Sd[(size_t)d * N + n] += w * L[n];
     }
-    st->F = malloc(sizeof(double) * N);
-    st->u = malloc(sizeof(double) * N);
-    st->du = malloc(sizeof(double) * N);
-    for (int n = 0; n < N; ++n) {
-        st->u[n] = orc_dust_curve(g, g->lam[n], delta, st->du + n);   /* A_lambda / Av and its delta derivative */
-        st->F[n] = pow(10.0, -0.4 * Av * st->u[n]);
+    st->Fd = malloc(sizeof(double) * (size_t)ND * N);
+    st->ud = malloc(sizeof(double) * (size_t)ND * N);
+    st->dud = malloc(sizeof(double) * (size_t)ND * N);
+    st->Avd = malloc(sizeof(double) * ND);
+    st->Td = malloc(sizeof(double) * ND);
+    st->L = calloc(N, sizeof(double));
+    for (int d = 0; d < ND; ++d) {
+        double Av, delta;
+        orc_dust_at_age(g, par, d, &Av, &delta, st->Td + d);
+        st->Avd[d] = Av;
+        for (int n = 0; n < N; ++n) {
+            size_t x = (size_t)d * N + n;
+            st->ud[x] = orc_dust_curve(g, g->lam[n], delta, st->dud + x);   /* A_lambda / Av, d/d delta */
+            st->Fd[x] = pow(10.0, -0.4 * Av * st->ud[x]);
+            st->L[n] += st->Fd[x] * st->Sd[x];
+        }
     }
+}
+
+/* Given Lbar_n = dLoss/dL_n (L the attenuated spectrum per unit mass), the
+ * per-group Sbar_d = Lbar F_d ([ND][n_lam]) and the dust gradients
+ * (rows 8, 9 and, with age-dependent dust, the old-star rows). */
+static double *gal_reverse_dust(const orc_grid *g, const gal_state *st, const double *Lbar, double *pbar)
+{
+    int N = g->n_lam, ND = st->ND, ng = orc_ngrad(g);
+    double *Sbar = malloc(sizeof(double) * (size_t)ND * N);
+    for (int d = 0; d < ND; ++d) {
+        double gav = 0.0, gdl = 0.0;
+        for (int n = 0; n < N; ++n) {
+            size_t x = (size_t)d * N + n;
+            Sbar[x] = Lbar[n] * st->Fd[x];
+            double Fbar = Lbar[n] * st->Sd[x];
+            gav += Fbar * st->Fd[x] * (-0.4 * log(10.0)) * st->ud[x];
+            gdl += Fbar * st->Fd[x] * (-0.4 * log(10.0)) * st->Avd[d] * st->dud[x];
+        }
+        double T = st->Td[d];
+        pbar[8] += (1.0 - T) * gav;
+        pbar[9] += (1.0 - T) * gdl;
+        if (g->dust_agedep) {
+            pbar[ng - 2] += T * gav;
+            pbar[ng - 1] += T * gdl;
+        }
+    }
+    return Sbar;
 }
 
 static void gal_free(gal_state *st)
 {
-    free(st->du); free(st->u); free(st->F); free(st->S); free(st->dmu7); free(st->dmu5);
+    free(st->dud); free(st->ud); free(st->Fd); free(st->Sd); free(st->Avd); free(st->Td); free(st->L);
+    free(st->dmu7); free(st->dmu5);
     free(st->Pu); free(st->dPu_us); free(st->dPu_su);
     free(st->dPsig); free(st->dPmu); free(st->P); free(st->frac); free(st->Mhi); free(st->e);
     free(st->dsfr); free(st->sfr);
 }
 
-/* Reverse of the weights and the contraction: given Sbar_n = dLoss/dS_n (S the
- * per-unit-mass spectrum before dust), adds dLoss/dp_k for k = 0..7 to pbar
- * (and 11, 12 with a nebular axis). */
+/* Reverse of the weights and the contraction: given Sbar = dLoss/dS_d for every
+ * dust group ([ND][n_lam], S_d the group's per-unit-mass spectrum before dust),
+ * adds dLoss/dp_k for k = 0..7 to pbar (and 11, 12 with a nebular axis). */
 static void gal_reverse_sbar(const orc_grid *g, const gal_state *st, double t_obs, const double *Sbar,
                              double *pbar)
 {
@@ -607,8 +671,9 @@ static void gal_reverse_sbar(const orc_grid *g, const gal_state *st, double t_ob
     for (int k = 0; k < K; ++k) {
         const double *L = g->l_ssp + (size_t)k * N;
         double wbar = 0.0;
-        for (int n = 0; n < N; ++n) wbar += Sbar[n] * L[n];
         int ij = k / NU, u = k % NU, i = ij / NZ;
+        const double *sb = Sbar + (size_t)(st->ND > 1 ? i : 0) * N;
+        for (int n = 0; n < N; ++n) wbar += sb[n] * L[n];
         fracbar[i] += wbar * st->P[ij] * st->Pu[u];
         double Pbar = wbar * st->frac[i] * st->Pu[u];
         pbar[5] += Pbar * st->dPmu[ij] * st->dmu5[i];
@@ -645,7 +710,7 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
                             double dmod, const double *mbar, double *mags, double *pbar /* 11, or 13 */)
 {
     int N = g->n_lam, Q = f->n_filt;
-    double Av = par[8], logM = par[10], z = par[11];
+    double logM = par[10], z = par[11];
     gal_state st;
     gal_forward(g, par, t_obs, &st);
     int *off = malloc(sizeof(int) * (Q + 1));
@@ -657,7 +722,7 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
         double acc = 0.0;
         for (int n = 0; n < N; ++n) {
             T[(size_t)q * N + n] = orc_filter_trans(fl, ft, f->n_pts[q], (1.0 + z) * g->lam[n]);
-            acc += trap_w(g->lam, N, n) / g->lam[n] * T[(size_t)q * N + n] * st.F[n] * st.S[n];
+            acc += trap_w(g->lam, N, n) / g->lam[n] * T[(size_t)q * N + n] * st.L[n];
         }
         Nq[q] = acc;
         double Dq = orc_filter_norm(fl, ft, f->n_pts[q]);
@@ -671,20 +736,41 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
         pbar[10] += -2.5 * mbar[q];
         Nbar[q] = mbar[q] * (-2.5 / log(10.0)) / Nq[q];
     }
-    double *Sbar = calloc(N, sizeof(double));
+    double *Lbar = calloc(N, sizeof(double));
     for (int n = 0; n < N; ++n) {
         double c = trap_w(g->lam, N, n) / g->lam[n];
         double sT = 0.0;
         for (int q = 0; q < Q; ++q) sT += Nbar[q] * T[(size_t)q * N + n];
-        Sbar[n] = c * sT * st.F[n];
-        double Fbar = c * sT * st.S[n];
-        double dF_dAv = st.F[n] * (-0.4 * log(10.0)) * st.u[n];
-        double dF_ddelta = st.F[n] * (-0.4 * log(10.0)) * Av * st.du[n];
-        pbar[8] += Fbar * dF_dAv;
-        pbar[9] += Fbar * dF_ddelta;
+        Lbar[n] = c * sT;
     }
+    double *Sbar = gal_reverse_dust(g, &st, Lbar, pbar);
     gal_reverse_sbar(g, &st, t_obs, Sbar, pbar);
-    free(Sbar); free(Nbar); free(Nq); free(T); free(off);
+    free(Sbar); free(Lbar); free(Nbar); free(Nq); free(T); free(off);
+    gal_free(&st);
+}
+
+/* Magnitudes with age-dependent dust (Sec. 3.4.1, Eq. agedep_dust_csp): the
+ * attenuated spectrum sum_i F_i S_i through Eq. (restmag) as above. */
+static void galaxy_mags_agedep(const orc_grid *g, const orc_filters *f, const double *par, double t_obs,
+                               double dmod, double *mags)
+{
+    int N = g->n_lam, Q = f->n_filt;
+    double logM = par[10], z = par[11];
+    gal_state st;
+    gal_forward(g, par, t_obs, &st);
+    int *off = malloc(sizeof(int) * (Q + 1));
+    filter_offsets(f, off);
+    for (int q = 0; q < Q; ++q) {
+        const double *fl = f->lam + off[q], *ft = f->trans + off[q];
+        double acc = 0.0;
+        for (int n = 0; n < N; ++n) {
+            double T = orc_filter_trans(fl, ft, f->n_pts[q], (1.0 + z) * g->lam[n]);
+            acc += trap_w(g->lam, N, n) / g->lam[n] * T * st.L[n];
+        }
+        double Dq = orc_filter_norm(fl, ft, f->n_pts[q]);
+        mags[q] = -2.5 * log10(pow(10.0, logM) * acc / (ORC_AB0 * Dq)) + dmod - 2.5 * log10(1.0 + z);
+    }
+    free(off);
     gal_free(&st);
 }
 
@@ -801,7 +887,7 @@ static void galaxy_spectrum(const orc_grid *g, const double *par, double t_obs, 
     gal_state st;
     gal_forward(g, par, t_obs, &st);
     double M = pow(10.0, par[10]);
-    for (int n = 0; n < g->n_lam; ++n) out[n] = M * st.F[n] * st.S[n];
+    for (int n = 0; n < g->n_lam; ++n) out[n] = M * st.L[n];
     gal_free(&st);
 }
 
@@ -813,22 +899,21 @@ static double galaxy_ew(const orc_grid *g, const orc_line *ln, const double *par
     int N = g->n_lam;
     gal_state st;
     gal_forward(g, par, t_obs, &st);
-    double M = pow(10.0, par[10]), Av = par[8];
+    double M = pow(10.0, par[10]);
     double *L = malloc(sizeof(double) * N), *Lbar = malloc(sizeof(double) * N);
-    for (int n = 0; n < N; ++n) L[n] = M * st.F[n] * st.S[n];
+    for (int n = 0; n < N; ++n) L[n] = M * st.L[n];
     double W = orc_ew_from_spectrum(g->lam, L, N, ln, pbar ? Lbar : NULL);
     if (pbar) {
         for (int k = 0; k < orc_ngrad(g); ++k) pbar[k] = 0.0;
-        double *Sbar = malloc(sizeof(double) * N);
+        /* L = 10^logM sum_d F_d S_d: cotangent of the per-unit-mass spectrum */
+        double *lbu = malloc(sizeof(double) * N);
         for (int n = 0; n < N; ++n) {
-            double lb = ewbar * Lbar[n];
-            Sbar[n] = lb * M * st.F[n];
-            pbar[8] += lb * L[n] * (-0.4 * log(10.0)) * st.u[n];
-            pbar[9] += lb * L[n] * (-0.4 * log(10.0)) * Av * st.du[n];
-            pbar[10] += lb * L[n] * log(10.0);
+            lbu[n] = ewbar * Lbar[n] * M;
+            pbar[10] += ewbar * Lbar[n] * L[n] * log(10.0);
         }
+        double *Sbar = gal_reverse_dust(g, &st, lbu, pbar);
         gal_reverse_sbar(g, &st, t_obs, Sbar, pbar);
-        free(Sbar);
+        free(Sbar); free(lbu);
     }
     free(Lbar); free(L);
     gal_free(&st);
@@ -865,6 +950,10 @@ static void *orc_worker(void *arg)
             galaxy_weights(g, par, t_obs, omega);
             double M = pow(10.0, par[10]);
             for (int k = 0; k < K; ++k) j->w_out[(size_t)gi * K + k] = M * omega[k];
+        } else if (j->mode == 1 && g->dust_agedep) {
+            /* one curve per age bin: through the per-group forward state */
+            double dmod = orc_dist_mod(g->om0, g->w0, g->h, z);
+            galaxy_mags_agedep(g, j->f, par, t_obs, dmod, j->mags + (size_t)gi * j->f->n_filt);
         } else if (j->mode == 1) {
             double dmod = orc_dist_mod(g->om0, g->w0, g->h, z);
             galaxy_weights(g, par, t_obs, omega);

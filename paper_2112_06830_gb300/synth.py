@@ -181,6 +181,28 @@ def with_nebular(params: np.ndarray, seed: int, start: int = 0) -> np.ndarray:
     return out
 
 
+def with_agedep_dust(params: np.ndarray, seed: int, start: int = 0) -> np.ndarray:
+    """The same galaxies with age-dependent dust (Sec. 3.4.1): rows 8, 9 become
+    the young-star values Av_young ~ U[0.4, 2.0], delta_young ~ U[-0.6, 0.0],
+    and two rows are appended, Av_old ~ U[0, 0.8], delta_old ~ U[-0.4, 0.3];
+    galaxy i's draw depends only on (seed, i)."""
+    p = np.asarray(params, dtype=np.float64)
+    n = p.shape[1]
+    out = np.zeros((p.shape[0] + 2, n))
+    out[:p.shape[0]] = p
+    if n == 0:
+        return out
+    b0, b1 = start // _BLOCK, (start + n - 1) // _BLOCK
+    draws = []
+    for b in range(b0, b1 + 1):
+        rng = np.random.default_rng([seed, b, 17])
+        draws.append(np.stack([rng.uniform(0.4, 2.0, _BLOCK), rng.uniform(-0.6, 0.0, _BLOCK),
+                               rng.uniform(0.0, 0.8, _BLOCK), rng.uniform(-0.4, 0.3, _BLOCK)]))
+    d = np.concatenate(draws, axis=1)[:, start - b0 * _BLOCK:start - b0 * _BLOCK + n]
+    out[8], out[9], out[-2], out[-1] = d
+    return out
+
+
 # Line-strength workload: [OIII] 5007 A (the line of the paper's Sec. 3.3 example),
 # line window +-30 A, continuum 100 A on each side.
 EW_LINE = (5007.0, 30.0, 100.0)
