@@ -51,7 +51,8 @@
  *                     uncorrelated MDF); DSPS_MDF_MEAN_TERF: mean of the
  *                     oldest stars (mu_old)
  *    8     Av         V-band attenuation [mag]
- *    9     delta      dust slope: A(lam) = Av (lam/5500 A)^(-0.7 + delta)
+ *    9     delta      dust slope: A(lam) = Av (lam/5500 A)^(-0.7 + delta), or
+ *                     Av k0(lam) (lam/5500 A)^delta / 4.05 (DSPS_DUST_*)
  *    10    logM       log10 of the stellar mass formed by t_obs [Msun]
  *    11    z          redshift, 0 < z <= z_max
  * Gradient rows (param_bar, float32 [11][G]) are rows 0..10 above.
@@ -64,6 +65,13 @@
  * The probability of log U bin k is the triweight CDF difference over the
  * bin's edges (midpoints of the grid, outer edges at -inf / +inf), and the SSP
  * weights become omega_ijk = P_SFH(i) P_met(j | i) P_neb(k).
+ *
+ * With age-dependent dust (dsps_opts.dust_agedep, Sec. 3.4.1, Eq.
+ * agedep_dust_csp) rows 8 and 9 hold the young-star Av and delta and two more
+ * rows follow the others (rows 12, 13, or 14, 15 with a nebular axis): Av_old,
+ * delta_old.  Age bin i is attenuated with Av_i = (1 - T_i) Av + T_i Av_old,
+ * delta_i likewise, T_i = Terf((log10 age_i - x0) / h); the gradient gains two
+ * rows at its end (Av_old, delta_old).
  */
 #ifndef DSPS_H
 #define DSPS_H
@@ -98,6 +106,16 @@ enum { DSPS_MDF_TRIWEIGHT = 0, DSPS_MDF_GAUSSIAN = 1 };
  *                         the paper's transition from mu_young to mu_old along
  *                         the triweight cumulative kernel (Appendix B). */
 enum { DSPS_MDF_MEAN_LINEAR = 0, DSPS_MDF_MEAN_TERF = 1 };
+/* Attenuation curve A_lambda / Av (Sec. 3.4, Eq. salim), x = lam / 5500 A:
+ *   DSPS_DUST_POWERLAW  x^(-0.7 + delta): a power law standing for
+ *                       k0 x^delta / 4.05, equal to 1 at 5500 A
+ *   DSPS_DUST_SALIM     k0(lam) x^delta / 4.05 with the starburst curve k0 of
+ *                       Eq. kzero: the published fits of Leitherer et al. (2002)
+ *                       below 0.15 um and Calzetti et al. (2000) above (the
+ *                       two curves' own ranges; the printed equation lists them
+ *                       the other way round), clipped at 0 past ~3.1 um.
+ * Either adds the UV bump E_b D0 / 4.05 when dsps_opts.dust_bump is set. */
+enum { DSPS_DUST_POWERLAW = 0, DSPS_DUST_SALIM = 1 };
 
 /* Arithmetic of the contraction (Eq. full_mdf):
  *   DSPS_PREC_FP32   FP32 weights x FP32 SSP grid, FP32 FMA on the SIMT cores.
@@ -162,6 +180,13 @@ typedef struct {
                                   width 350 A, amplitude E_b = 0.85 - 1.9 delta,
                                   entering A_lambda as Av E_b D0(lam) / 4.05);
                                   default 0                                      */
+    int32_t dust_law;          /* DSPS_DUST_*; default DSPS_DUST_POWERLAW        */
+    int32_t dust_agedep;       /* 1: age-dependent dust (see the parameter rows
+                                  above); spectra, line widths and
+                                  dsps_photometry_fp32_static then return
+                                  DSPS_ERR_UNSUPPORTED; default 0                */
+    double dust_agedep_x0;     /* transition centre [log10 yr] and width h [dex], */
+    double dust_agedep_h;      /* h > 0 (defaults 7, 0.1: the birth-cloud age)    */
 } dsps_opts;
 
 /* Fills *o with the defaults above (device 0, max_chunk 262144,

@@ -2,8 +2,8 @@
 
 ``photometry(ctx, params, set_id, precision)`` returns AB magnitudes [G, Q] and
 is differentiable with respect to ``params`` [12, G] (rows 0..10; the redshift
-row 11 gets a zero gradient), or [14, G] on a grid with a nebular axis (rows
-12, 13 take gradient rows 11, 12).  Forward and backward both run in libdsps: the
+row 11 gets a zero gradient); the rows after z (nebular axis, old-star dust)
+take the gradient rows after row 10.  Forward and backward both run in libdsps: the
 backward calls dsps_photometry_vjp, which recomputes the forward sums it needs
 instead of storing spectra.
 """
@@ -30,9 +30,12 @@ class DSPSPhotometry(torch.autograd.Function):
         _, pbar = fctx.context.photometry_vjp(params, fctx.set_id, grad_mags.contiguous(),
                                               precision=fctx.precision, want_mags=False)
         grad = torch.zeros_like(params)
+        # gradient rows 0..10 are parameter rows 0..10; the rows after them
+        # (nebular axis, old-star dust) are the parameter rows after z (row 11)
         grad[: dsps.DSPS_NGRAD] = pbar[: dsps.DSPS_NGRAD]
-        if pbar.shape[0] > dsps.DSPS_NGRAD:
-            grad[12:14] = pbar[dsps.DSPS_NGRAD:]
+        extra = pbar.shape[0] - dsps.DSPS_NGRAD
+        if extra:
+            grad[12:12 + extra] = pbar[dsps.DSPS_NGRAD:]
         return grad, None, None, None
 
 

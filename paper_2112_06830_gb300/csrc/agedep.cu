@@ -1,0 +1,277 @@
+// agedep.cu -- age-dependent dust attenuation (Sec. 3.4.1, Eq.
+// agedep_dust_csp): age bin i is attenuated by its own curve, with
+// Av_i = (1 - T_i) Av_young + T_i Av_old and delta_i likewise,
+// T_i = T_erf((log10 age_i - x0) / h) (Appendix B).
+//
+// The contraction no longer factorises into one GEMM followed by one
+// attenuation, but it does by groups of age bins that share a curve: the young
+// bins with T = 0, each bin of the transition, and the old bins with T = 1
+// (Ctx::dust_groups).  Each group runs the ordinary fused path -- weights of
+// the group's ages only, with the group's dust constants, then the tensor-core
+// (or FP32) contraction with its fused epilogue -- and the groups' filter sums
+// are added in a fixed order before the magnitudes are formed.  Every group
+// keeps the chunk's sort, so rows line up; skipped K blocks (ages outside the
+// group) hold exact zeros.
+//
+// Gradient: the filter sums of the dust derivatives are accumulated per group
+// with the weights (1 - T, T) of the young and old values; the adjoint of the
+// weights runs the adjoint contraction once per group, with the group's
+// attenuation in Shat, keeps the adjoint rows of the group's ages, and then
+// runs the weights adjoint once on the merged rows.
+#include "dsps_internal.cuh"
+#include "epilogue.cuh"
+
+namespace dsps {
+
+void set_last_error(const char *msg);
+
+namespace {
+
+constexpr int QS = QSTRIDE_MAX;
+
+// Tile ranges and masks back to empty before the next group's weights (the
+// chunk's sort is kept).
+__global__ void tile_reset_kernel(int2 *trange, int2 *urange, int n_u, unsigned *kmask, int kmw, int n_tiles) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tiles) return;
+    trange[i] = make_int2(TRANGE_EMPTY_LO, TRANGE_EMPTY_HI);
+    urange[i] = make_int2(n_u, -1);
+    for (int w = 0; w < kmw; ++w) kmask[(size_t)i * kmw + w] = 0u;
+}
+
+// Adds one group's filter sums (its parts in a fixed order) to
+// gacc[r] = {N, A_young, A_old, D_young, D_old} (QS floats each), with
+// A_* weighted by (1 - T, T) and D_* by (1 - T, T) Av_group (the delta
+// derivative of the flux carries the group's Av).
+__global__ void group_acc_kernel(const float *partial, int parts, int nr, int64_t n, int qs, int Q, float T,
+                                 const float *aux, bool grad, bool first, float *gacc) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float Av = aux[r * AUX_STRIDE + 4];
+    float *ga = gacc + r * 5 * QS;
+    for (int q = 0; q < Q; ++q) {
+        float N = 0.f, A = 0.f, D = 0.f;
+        for (int p = 0; p < parts; ++p) {
+            const float *src = partial + ((int64_t)p * n + r) * (nr * qs);
+            N += src[q];
+            if (grad) {
+                A += src[qs + q];
+                D += src[2 * qs + q];
+            }
+        }
+        const float v[5] = {N, (1.f - T) * A, T * A, (1.f - T) * Av * D, T * Av * D};
+        for (int k = 0; k < (grad ? 5 : 1); ++k) ga[k * QS + q] = first ? v[k] : ga[k * QS + q] + v[k];
+    }
+}
+
+struct FinalArgs {
+    const float *gacc;
+    int64_t n, G_stride, g_begin;
+    int Q, ngrad;
+    const float *magoff, *offq, *aux;
+    const int *gidx;          // sorted row -> chunk galaxy, or nullptr
+    float *mags;              // [G][Q] of the chunk, or nullptr
+    HistArgs hist;
+    const float *mag_bar;     // [G][Q] of the chunk (gradient), or nullptr
+    float *cq;                // [n][QS] Nbar (gradient)
+    float *param_bar;         // [ngrad][G_stride] (gradient)
+};
+
+// Magnitudes (or histogram counts) from the summed fluxes; with the gradient,
+// Nbar_q and the dust and mass rows of param_bar.
+__global__ void agedep_final_kernel(FinalArgs a) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.n) return;
+    const int64_t g = a.gidx ? (int64_t)a.gidx[r] : r;
+    const float *ga = a.gacc + r * 5 * QS;
+    const float mo = a.magoff[r];
+    float m[DSPS_MAX_FILTERS];
+    for (int q = 0; q < a.Q; ++q) m[q] = ab_mag(ga[q], mo, a.offq[q]);
+    if (a.hist.counts) {
+        int bin;
+        if (hist_bin(a.hist, m[a.hist.band_a], m[a.hist.band_b], m[a.hist.band_r], bin))
+            atomicAdd(a.hist.counts + bin, 1ull);
+    }
+    if (a.mags)
+        for (int q = 0; q < a.Q; ++q) a.mags[g * a.Q + q] = m[q];
+    if (!a.mag_bar) return;
+    const bool valid = a.aux[r * AUX_STRIDE + 3] != 0.f;
+    const float k10 = -2.5f / 2.302585092994046f, kd = -0.4f * 2.302585092994046f;
+    float avy = 0.f, avo = 0.f, dly = 0.f, dlo = 0.f, lm = 0.f;
+    for (int q = 0; q < a.Q; ++q) {
+        const float mb = a.mag_bar[g * a.Q + q];
+        const float nb = valid ? mb * k10 / ga[q] : 0.f;
+        a.cq[r * QS + q] = nb;
+        avy = fmaf(nb * kd, ga[QS + q], avy);
+        avo = fmaf(nb * kd, ga[2 * QS + q], avo);
+        dly = fmaf(nb * kd, ga[3 * QS + q], dly);
+        dlo = fmaf(nb * kd, ga[4 * QS + q], dlo);
+        lm = fmaf(-2.5f, mb, lm);
+    }
+    const float nan = __int_as_float(0x7fc00000);
+    const int64_t col = a.g_begin + g;
+    a.param_bar[8 * a.G_stride + col] = valid ? avy : nan;
+    a.param_bar[9 * a.G_stride + col] = valid ? dly : nan;
+    a.param_bar[10 * a.G_stride + col] = valid ? lm : nan;
+    a.param_bar[(int64_t)(a.ngrad - 2) * a.G_stride + col] = valid ? avo : nan;
+    a.param_bar[(int64_t)(a.ngrad - 1) * a.G_stride + col] = valid ? dlo : nan;
+}
+
+// Keeps, in the merged adjoint rows, the columns of the group's ages
+// (kz = u SEC + j A_pad + i with i in [i0, i1)); the first group also zeroes
+// the padding columns.
+__global__ void merge_rows_kernel(const float *src, float *dst, int64_t n, int KZ_pad, int SEC, int A_pad, int nzA,
+                                  int n_u, int n_age, int i0, int i1, bool first) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * KZ_pad) return;
+    const int kz = (int)(idx % KZ_pad);
+    const int u = kz / SEC, rr = kz - u * SEC;
+    const bool pad = u >= n_u || rr >= nzA;
+    const int i = pad ? -1 : rr % A_pad;
+    if (!pad && i >= i0 && i < i1) dst[idx] = src[idx];
+    else if (first && (pad || i >= n_age)) dst[idx] = 0.f;
+}
+
+cudaError_t launch_tile_reset(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s) {
+    const int n_tiles = (int)((n + 127) / 128);
+    tile_reset_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(w.trange, w.urange, c.n_u, w.kmask, c.kmask_words,
+                                                            n_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_acc(const Workspace &w, const FilterSet &fs, int64_t n, int parts, int nr, float T,
+                             bool grad, bool first, cudaStream_t s) {
+    group_acc_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.partial, parts, nr, n, 4 * fs.Q4, fs.Q, T, w.aux,
+                                                                 grad, first, w.gacc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, bool sorted, float *mags,
+                         const HistArgs *hist, const float *mag_bar, float *param_bar, int64_t G_stride,
+                         int64_t g_begin, cudaStream_t s) {
+    FinalArgs a{};
+    a.gacc = w.gacc;
+    a.n = n;
+    a.G_stride = G_stride;
+    a.g_begin = g_begin;
+    a.Q = fs.Q;
+    a.ngrad = c.ngrad;
+    a.magoff = w.magoff;
+    a.offq = fs.d_offq;
+    a.aux = w.aux;
+    a.gidx = sorted ? w.gidx : nullptr;
+    a.mags = mags;
+    if (hist) a.hist = *hist;
+    a.mag_bar = mag_bar;
+    a.cq = w.cq;
+    a.param_bar = param_bar;
+    agedep_final_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const Ctx &c, const Workspace &w, int64_t n, const DustGroup &gr, bool first,
+                         cudaStream_t s) {
+    const int64_t tot = n * c.KZ_pad;
+    merge_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(w.w32, w.what2, n, c.KZ_pad, c.SEC, c.A_pad,
+                                                                    c.n_z * c.A_pad, c.n_u, c.n_age, gr.i0, gr.i1,
+                                                                    first);
+    return cudaGetLastError();
+}
+
+int fail_cuda(cudaError_t e) {
+    set_last_error(cudaGetErrorString(e));
+    return DSPS_ERR_CUDA;
+}
+
+// Forward of one chunk over all dust groups, leaving the summed fluxes (and,
+// with grad, the dust-derivative sums) in w.gacc.
+cudaError_t groups_forward(Ctx *c, const Workspace &w, int64_t n_gal, int64_t g0, int64_t n, const float *params,
+                           const FilterSet &fs, bool tc, bool grad, cudaStream_t s, bool prof) {
+    cudaError_t e = cudaSuccess;
+    if (tc) {
+        ProfScope ps(*c, 0, s, prof);
+        e = launch_zsort(*c, w, params, n_gal, g0, n, s);
+    }
+    for (size_t k = 0; k < c->dust_groups.size() && e == cudaSuccess; ++k) {
+        const DustGroup &gr = c->dust_groups[k];
+        {
+            ProfScope ps(*c, 0, s, prof);
+            if (tc && k > 0) e = launch_tile_reset(*c, w, n, s);
+            if (e == cudaSuccess)
+                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, tc,
+                                   &gr);
+        }
+        int parts = 1;
+        if (e == cudaSuccess) {
+            ProfScope ps(*c, tc ? 2 : 1, s, prof);
+            // the FP32 form's sums come from its gradient mode (N, A, D per filter)
+            e = tc ? launch_phot_tc(*c, w, fs, n, &parts, s, grad) : launch_phot_simt(*c, w, fs, n, nullptr, s, true);
+        }
+        if (e == cudaSuccess) {
+            ProfScope ps(*c, 0, s, prof);
+            e = launch_group_acc(w, fs, n, parts, (tc && !grad) ? 1 : 3, gr.T, grad, k == 0, s);
+        }
+    }
+    return e;
+}
+
+}  // namespace
+
+int run_photometry_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *params, const FilterSet &fs,
+                             int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist) {
+    Workspace w = w0;
+    w.stats = (profile && c->prof) ? c->d_stats : nullptr;
+    const bool prof = profile && c->prof;
+    const bool tc = precision == DSPS_PREC_BF16X3;
+    for (int64_t g0 = 0; g0 < n_gal; g0 += w.cap) {
+        const int64_t n = n_gal - g0 < w.cap ? n_gal - g0 : w.cap;
+        cudaError_t e = groups_forward(c, w, n_gal, g0, n, params, fs, tc, false, s, prof);
+        if (e == cudaSuccess) {
+            ProfScope ps(*c, 0, s, prof);
+            e = launch_final(*c, w, fs, n, tc, hist ? nullptr : mags + g0 * fs.Q, hist, nullptr, nullptr, n_gal, g0,
+                             s);
+        }
+        if (e != cudaSuccess) return fail_cuda(e);
+    }
+    return DSPS_OK;
+}
+
+int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *params,
+                                 const FilterSet &fs, int32_t precision, const float *mag_bar, float *mags,
+                                 float *param_bar, cudaStream_t s, bool profile) {
+    Workspace w = w0;
+    w.stats = (profile && c->prof) ? c->d_stats : nullptr;
+    const bool prof = profile && c->prof;
+    const bool tc = precision == DSPS_PREC_BF16X3;
+    for (int64_t g0 = 0; g0 < n_gal; g0 += w.cap) {
+        const int64_t n = n_gal - g0 < w.cap ? n_gal - g0 : w.cap;
+        cudaError_t e = groups_forward(c, w, n_gal, g0, n, params, fs, tc, true, s, prof);
+        if (e == cudaSuccess) {
+            ProfScope ps(*c, 3, s, prof);
+            e = launch_final(*c, w, fs, n, tc, mags ? mags + g0 * fs.Q : nullptr, nullptr, mag_bar + g0 * fs.Q,
+                             param_bar, n_gal, g0, s);
+        }
+        // adjoint of the weights: one adjoint contraction per group, merged rows
+        for (size_t k = 0; k < c->dust_groups.size() && e == cudaSuccess; ++k) {
+            const DustGroup &gr = c->dust_groups[k];
+            ProfScope ps(*c, 3, s, prof);
+            if (tc) e = launch_tile_reset(*c, w, n, s);
+            if (e == cudaSuccess)
+                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, tc,
+                                   &gr);
+            if (e == cudaSuccess) e = launch_shat(*c, w, fs, n, tc, tc && c->opts.band_skip, s);
+            if (e == cudaSuccess) e = tc ? launch_vjp_tc(*c, w, fs, n, s) : launch_vjp_simt(*c, w, n, s);
+            if (e == cudaSuccess) e = launch_merge(*c, w, n, gr, k == 0, s);
+        }
+        if (e == cudaSuccess) {
+            ProfScope ps(*c, 3, s, prof);
+            Workspace wm = w;
+            wm.w32 = w.what2;
+            e = launch_weights_vjp(*c, wm, params, n_gal, g0, n, tc, tc, param_bar, s);
+        }
+        if (e != cudaSuccess) return fail_cuda(e);
+    }
+    return DSPS_OK;
+}
+
+}  // namespace dsps

@@ -134,7 +134,7 @@ void free_ctx(Ctx *c) {
         cudaFree(fs.d_offq);
     }
     for (auto &ls : c->lines) cudaFree(ls.d_tab);
-    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_edges, c->d_einh, c->d_bwidth,
+    void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_k0, c->d_edges, c->d_einh, c->d_bwidth,
                     c->d_zedge, c->d_uedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->d_err, c->d_stats,
                     c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d};
     for (void *p : ptrs) cudaFree(p);
@@ -181,6 +181,10 @@ void dsps_default_opts(dsps_opts *o) {
     o->mdf_terf_x0 = 9.0;
     o->mdf_terf_h = 0.5;
     o->dust_bump = 0;
+    o->dust_law = DSPS_DUST_POWERLAW;
+    o->dust_agedep = 0;
+    o->dust_agedep_x0 = 7.0;
+    o->dust_agedep_h = 0.1;
 }
 
 namespace {
@@ -225,8 +229,12 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
             return fail(DSPS_ERR_UNSUPPORTED, "dsps_create: wavelength grid is not uniform in ln(lambda)%s");
     }
     if (opts.sfh_model < 0 || opts.sfh_model > 1 || opts.mdf_kernel < 0 || opts.mdf_kernel > 1 ||
-        opts.mdf_mean < 0 || opts.mdf_mean > 1 || opts.dust_bump < 0 || opts.dust_bump > 1)
+        opts.mdf_mean < 0 || opts.mdf_mean > 1 || opts.dust_bump < 0 || opts.dust_bump > 1 || opts.dust_law < 0 ||
+        opts.dust_law > 1)
         return fail(DSPS_ERR_INVALID_ARG, "dsps_create: unknown model switch%s");
+    if (opts.dust_agedep < 0 || opts.dust_agedep > 1 ||
+        (opts.dust_agedep && !(opts.dust_agedep_h > 0 && std::isfinite(opts.dust_agedep_x0))))
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_create: bad age-dependent dust options%s");
     if (opts.mdf_mean == DSPS_MDF_MEAN_TERF && !(opts.mdf_terf_h > 0 && std::isfinite(opts.mdf_terf_x0)))
         return fail(DSPS_ERR_INVALID_ARG, "dsps_create: bad MDF transition%s");
     if (!(opts.z_max > 0) || opts.z_max > 50 || !(opts.om0 > 0) || !(opts.h > 0))
@@ -252,8 +260,23 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     c->n_z = g->n_z;
     c->n_lam = g->n_lam;
     c->n_u = n_u;
-    c->npar = n_u > 1 ? NPAR_MAX : NPAR;
-    c->ngrad = n_u > 1 ? DSPS_NGRAD_NEB : NGRAD;
+    c->npar = (n_u > 1 ? NPAR_MAX : NPAR) + (opts.dust_agedep ? 2 : 0);
+    c->ngrad = (n_u > 1 ? DSPS_NGRAD_NEB : NGRAD) + (opts.dust_agedep ? 2 : 0);
+    if (opts.dust_agedep) {
+        c->row_dust_old = n_u > 1 ? NPAR_MAX : NPAR;
+        // groups of age bins sharing one attenuation curve (Sec. 3.4.1): runs
+        // of bins with T = 0 or T = 1, every bin of the transition on its own
+        for (int i = 0; i < g->n_age;) {
+            const double T = terf_host((g->log_age_yr[i] - opts.dust_agedep_x0) / opts.dust_agedep_h);
+            int j = i + 1;
+            if (T == 0.0 || T == 1.0)
+                while (j < g->n_age &&
+                       terf_host((g->log_age_yr[j] - opts.dust_agedep_x0) / opts.dust_agedep_h) == T)
+                    ++j;
+            c->dust_groups.push_back(DustGroup{i, j, (float)T});
+            i = j;
+        }
+    }
     c->u_ref = n_u / 2;
     c->K = g->n_age * g->n_z * n_u;
     c->K_pad = (c->K + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
@@ -303,6 +326,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_logage, (size_t)c->n_age));
     chk(dmalloc(&c->d_mua, (size_t)c->n_age));
     chk(dmalloc(&c->d_bump, (size_t)c->N_pad));
+    chk(dmalloc(&c->d_k0, (size_t)c->N_pad));
     chk(dmalloc(&c->d_mub, (size_t)c->n_age));
     chk(dmalloc(&c->d_edges, (size_t)c->n_age + 1));
     chk(dmalloc(&c->d_einh, (size_t)c->n_age + 1));
@@ -376,6 +400,18 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
         bump[n] = (float)(x * x / (d * d + x * x));
     }
     up(c->d_bump, bump.data(), bump.size() * sizeof(float));
+    // Eq. (kzero): starburst curve over 4.05 at the grid's wavelengths (the
+    // published Leitherer fit below 0.15 um, Calzetti above, clipped at 0)
+    std::vector<float> k0t(c->N_pad, 0.f);
+    for (int n = 0; n < c->n_lam; ++n) {
+        const double x = g->lam[n] * 1e-4;
+        double k;
+        if (x < 0.15) k = 5.472 + 0.671 / x - 9.218e-3 / (x * x) + 2.620e-3 / (x * x * x);
+        else if (x < 0.63) k = 2.659 * (-2.156 + 1.509 / x - 0.198 / (x * x) + 0.011 / (x * x * x)) + 4.05;
+        else k = 2.659 * (-1.857 + 1.040 / x) + 4.05;
+        k0t[n] = (float)(k > 0.0 ? k / 4.05 : 0.0);
+    }
+    up(c->d_k0, k0t.data(), k0t.size() * sizeof(float));
     up(c->d_zedge, zedge.data(), zedge.size() * sizeof(float));
     up(c->d_uedge, uedge.data(), uedge.size() * sizeof(float));
     up(c->d_tlut, tl.data(), tl.size() * sizeof(double));
@@ -539,6 +575,7 @@ int dsps_spectra(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t n0, 
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !out))) return fail(DSPS_ERR_INVALID_ARG, "dsps_spectra: bad argument%s");
     if (n0 < 0 || n1 <= n0 || n1 > c->n_lam) return fail(DSPS_ERR_INVALID_ARG, "dsps_spectra: need 0 <= n0 < n1 <= n_lam%s");
+    if (c->opts.dust_agedep) return fail(DSPS_ERR_UNSUPPORTED, "dsps_spectra: not with age-dependent dust%s");
     std::lock_guard<std::mutex> lk(c->mu);
     if (n_gal == 0) return DSPS_OK;
     DSPS_CUDA(cudaSetDevice(c->device));
@@ -624,6 +661,7 @@ int dsps_line_ew(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !ew))) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew: bad argument%s");
     std::lock_guard<std::mutex> lk(c->mu);
     if (line_id < 0 || line_id >= (int)c->lines.size()) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew: unknown line%s");
+    if (c->opts.dust_agedep) return fail(DSPS_ERR_UNSUPPORTED, "dsps_line_ew: not with age-dependent dust%s");
     if (n_gal == 0) return DSPS_OK;
     DSPS_CUDA(cudaSetDevice(c->device));
     const int rc = ensure_shat(c);
@@ -639,6 +677,7 @@ int dsps_line_ew_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t 
         return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew_vjp: bad argument%s");
     std::lock_guard<std::mutex> lk(c->mu);
     if (line_id < 0 || line_id >= (int)c->lines.size()) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew_vjp: unknown line%s");
+    if (c->opts.dust_agedep) return fail(DSPS_ERR_UNSUPPORTED, "dsps_line_ew_vjp: not with age-dependent dust%s");
     if (n_gal == 0) return DSPS_OK;
     DSPS_CUDA(cudaSetDevice(c->device));
     const int rc = ensure_shat(c);

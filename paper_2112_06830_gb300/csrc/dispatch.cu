@@ -21,6 +21,7 @@ size_t workspace_bytes(const Ctx &c, int64_t rows, bool adjoint) {
                2 * al256(R * 4) + al256((size_t)ZSORT_BUCKETS * 4) + al256((size_t)TC_PARTS * R * 3 * QSTRIDE_MAX * 4) +
                al256(R * QSTRIDE_MAX * 4) + 2 * al256((R / 128 + 1) * sizeof(int2)) + al256((R / 128 + 1) * c.kmask_words * 4) + al256(sizeof(int));
     if (adjoint) b += al256(R * c.N_pad * 4);
+    if (c.opts.dust_agedep) b += al256(R * 5 * QSTRIDE_MAX * 4) + al256(R * c.KZ_pad * 4);
     return b;
 }
 
@@ -50,11 +51,16 @@ Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint) 
     w.kmask = static_cast<unsigned *>(take((R / 128 + 1) * c.kmask_words * 4));
     w.sched = static_cast<int *>(take(sizeof(int)));
     w.shat = adjoint ? take(R * c.N_pad * 4) : nullptr;
+    if (c.opts.dust_agedep) {
+        w.gacc = static_cast<float *>(take(R * 5 * QSTRIDE_MAX * 4));
+        w.what2 = static_cast<float *>(take(R * c.KZ_pad * 4));
+    }
     return w;
 }
 
 int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *params, const FilterSet &fs,
                       int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist) {
+    if (c->opts.dust_agedep) return run_photometry_agedep_ws(c, w0, n_gal, params, fs, precision, mags, s, profile, hist);
     Workspace w = w0;
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;
@@ -100,6 +106,8 @@ int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *p
 int run_photometry_vjp_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *params, const FilterSet &fs,
                           int32_t precision, const float *mag_bar, float *mags, float *param_bar, cudaStream_t s,
                           bool profile) {
+    if (c->opts.dust_agedep)
+        return run_photometry_vjp_agedep_ws(c, w0, n_gal, params, fs, precision, mag_bar, mags, param_bar, s, profile);
     Workspace w = w0;
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;

@@ -77,7 +77,7 @@ constexpr int KBLOCK = 32;   // kz block of the tensor-core contraction (one TMA
 
 // Per-galaxy epilogue constants (aux[g*AUX_STRIDE + .]):
 //   0 alpha = -0.4 log2(10) Av      (F = 2^(alpha u))
-//   1 beta  = delta - 0.7           (u = 2^(beta log2(lam/5500)))
+//   1 beta  = delta - 0.7, or delta with the starburst curve (u = [k0/4.05] 2^(beta log2(lam/5500)))
 //   2 s     = ln(1+z) / dlnlam      (observer-frame shift in grid steps)
 //   3 valid (1 or 0)
 //   4 Av, 5 delta  (gradient path)
@@ -102,6 +102,14 @@ struct LineSet {
     int c0 = 0, n_pts = 0;
     int cs = 0, ce = 0;        // [c0, c0 + n_pts) widened to multiples of 16 columns
     float4 *d_tab = nullptr;   // [n_pts][2]
+};
+
+// Age-dependent dust (agedep.cu): the age bins split into groups of one
+// attenuation curve each -- the young bins with T = 0, every bin of the
+// transition, the old bins with T = 1 -- contracted one group at a time.
+struct DustGroup {
+    int i0, i1;     // age bins [i0, i1)
+    float T;        // weight of the old-star values
 };
 
 struct Serve;  // request loop (serve.cu)
@@ -141,6 +149,8 @@ struct Workspace {
     unsigned *kmask = nullptr;                  // [cap/128 + 1][kmask_words]
     int *sched = nullptr;                       // [1] work-unit counter of the tensor-core kernels
     float *cq = nullptr;                        // [cap][QSTRIDE_MAX]
+    float *gacc = nullptr;                      // [cap][5 * QSTRIDE_MAX] sums over dust groups (age-dependent dust)
+    float *what2 = nullptr;                     // [cap][KZ_pad] adjoint rows merged over dust groups (likewise)
     void *shat = nullptr;                       // [cap][N_pad] x 4 bytes (adjoint only)
     unsigned long long *stats = nullptr;        // tensor-core tile counter, or nullptr
 };
@@ -152,6 +162,8 @@ struct Ctx {
     int A_pad = 0, KZ_pad = 0;              // metallicity-major K: n_age padded to 4, row length
     int n_u = 1, SEC = 0, u_ref = 0;        // nebular axis: log U values, section length, reference section
     int npar = NPAR, ngrad = NGRAD;         // parameter and gradient rows
+    int row_dust_old = -1;                  // age-dependent dust: parameter row of Av_old (delta_old next)
+    std::vector<DustGroup> dust_groups;     // age-dependent dust: the groups of age bins
     int kmask_words = 0;                    // ceil(SEC / KBLOCK / 32)
     double t0 = 0, t1 = 0;
     double lnlam0 = 0, dlnlam = 0;
@@ -171,6 +183,7 @@ struct Ctx {
     float *d_logage = nullptr;              // [n_age] log10(age/yr)
     float *d_mua = nullptr, *d_mub = nullptr;   // [n_age] MDF mean of bin i: mua_i p5 + mub_i p7
     float *d_bump = nullptr;                // [N_pad] unit Drude profile at lam_n (Eq. uvbump), 0 past n_lam
+    float *d_k0 = nullptr;                  // [N_pad] k0(lam_n) / 4.05 (Eq. kzero), 0 past n_lam
     double *d_edges = nullptr;              // [n_age+1] age-bin edges [Gyr]
     float *d_einh = nullptr;                // [n_age+1] edge / time step
     float *d_bwidth = nullptr;              // [n_age] bin widths [Gyr]
@@ -251,8 +264,11 @@ size_t workspace_bytes(const Ctx &c, int64_t rows, bool adjoint);
 // Carves a work space for `rows` galaxies out of [base, base + workspace_bytes).
 Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint);
 
+// group: with age-dependent dust, the weights of the group's ages only and its
+// dust constants in aux (nullptr: all ages, one curve).
 cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const float *params, int64_t G_stride,
-                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted = false);
+                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted = false,
+                           const DustGroup *group = nullptr);
 
 // Counting sort of the chunk's galaxies into w.perm by (coarse redshift shift,
 // mean metallicity); also resets w.trange and w.kmask.
@@ -303,6 +319,12 @@ int run_spectra_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *param
                    cudaStream_t s);
 int run_line_ew_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const LineSet &ls,
                    const float *ew_bar, float *ew, float *param_bar, cudaStream_t s);
+// Age-dependent dust (agedep.cu): the same calls, one dust group at a time.
+int run_photometry_agedep_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
+                             int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist);
+int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params,
+                                 const FilterSet &fs, int32_t precision, const float *mag_bar, float *mags,
+                                 float *param_bar, cudaStream_t s, bool profile);
 int run_photometry_vjp_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
                           int32_t precision, const float *mag_bar, float *mags, float *param_bar, cudaStream_t s,
                           bool profile);

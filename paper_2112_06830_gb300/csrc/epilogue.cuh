@@ -65,7 +65,17 @@ struct ColConst {
     float kap0, kapmid, kapN;  // trapezoid weight / lambda at n = 0, interior, N-1
     int N;
     const float *bump;         // [N_pad] unit Drude profile D0(lam_n), or nullptr (no UV bump)
+    const float *k0;           // [N_pad] k0(lam_n) / 4.05 (Eq. kzero), or nullptr (power-law stand-in)
 };
+
+// The tilted term of the attenuation curve at node n (ell = log2(lam_n / 5500)):
+// k0_n / 4.05 (lam_n / lam_V)^delta with the paper's starburst curve (Eq.
+// salim; rc.beta = delta), or the stand-in (lam_n / lam_V)^(delta - 0.7)
+// (rc.beta = delta - 0.7).  Its delta derivative is the term times ell ln 2.
+__device__ __forceinline__ float dust_pow(const ColConst &cc, const RowConst &rc, float ell, int n) {
+    const float p = exp2f(rc.beta * ell);
+    return cc.k0 ? __ldg(cc.k0 + n) * p : p;
+}
 
 // Attenuation curve A_lambda / Av at node n: u, plus the UV bump when on.
 __device__ __forceinline__ float dust_curve(const ColConst &cc, const RowConst &rc, float u, int n) {
@@ -97,7 +107,7 @@ template <int Q4>
 __device__ __forceinline__ void epi_node(float (&acc)[4 * Q4], Slide &sl, float S, int n, const RowConst &rc,
                                          const ColConst &cc, const float4 *__restrict__ tab, int m_last) {
     const float ell = fmaf((float)n, cc.dell, cc.ell0);
-    const float u = exp2f(rc.beta * ell);
+    const float u = dust_pow(cc, rc, ell, n);
     const float F = exp2f(rc.alpha * dust_curve(cc, rc, u, n));
     const float v = S * F * col_kappa(cc, n);
     const float y = fmaf(rc.w[0], v, fmaf(rc.w[1], sl.v1, fmaf(rc.w[2], sl.v2, rc.w[3] * sl.v3)));
@@ -143,7 +153,7 @@ __device__ __forceinline__ void epi_node_grad(float (&acc)[3][4 * Q4], Slide (&s
                                               const RowConst &rc, const ColConst &cc,
                                               const float4 *__restrict__ tab, int m_last) {
     const float ell = fmaf((float)n, cc.dell, cc.ell0);
-    const float u = exp2f(rc.beta * ell);
+    const float u = dust_pow(cc, rc, ell, n);
     const float d0 = cc.bump ? __ldg(cc.bump + n) : 0.f;
     const float cn = fmaf(rc.e, d0, u);
     const float F = exp2f(rc.alpha * cn);

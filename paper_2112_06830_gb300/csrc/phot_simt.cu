@@ -174,6 +174,7 @@ ColConst make_col_const(const Ctx &c) {
     cc.kapN = (float)(-0.5 * std::expm1(-c.dlnlam));
     cc.N = c.n_lam;
     cc.bump = c.opts.dust_bump ? c.d_bump : nullptr;
+    cc.k0 = c.opts.dust_law == DSPS_DUST_SALIM ? c.d_k0 : nullptr;
     return cc;
 }
 

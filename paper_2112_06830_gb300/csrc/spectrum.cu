@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(THREADS, 2) spec_window_kernel(SwArgs a) {
                 float v = __int_as_float(0x7fc00000);
                 if (rc.valid) {
                     const float ell = fmaf((float)col, a.cc.dell, a.cc.ell0);
-                    const float F = exp2f(rc.alpha * dust_curve(a.cc, rc, exp2f(rc.beta * ell), col));
+                    const float F = exp2f(rc.alpha * dust_curve(a.cc, rc, dust_pow(a.cc, rc, ell, col), col));
                     v = mass * F * c[i][j];
                 }
                 a.out[r * a.ld + (col - a.o0)] = v;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) ew_kernel(EwArgs a) {
     auto curve = [&](int j, float &u, float &du) {
         const int col = a.c0 + j;
         const float ell = fmaf((float)col, a.cc.dell, a.cc.ell0);
-        const float v = exp2f(rc.beta * ell);
+        const float v = dust_pow(a.cc, rc, ell, col);
         u = dust_curve(a.cc, rc, v, col);
         du = v * ell * 0.69314718055994531f;
         if (a.cc.bump) du = fmaf(rc.ed, __ldg(a.cc.bump + col), du);

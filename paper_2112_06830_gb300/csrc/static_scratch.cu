@@ -79,6 +79,10 @@ extern "C" int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const f
         set_last_error("dsps_photometry_fp32_static: unknown filter set");
         return DSPS_ERR_INVALID_ARG;
     }
+    if (c->opts.dust_agedep) {
+        set_last_error("dsps_photometry_fp32_static: not with age-dependent dust");
+        return DSPS_ERR_UNSUPPORTED;
+    }
     const int64_t cap = max_rows(c->K_pad);
     if (n_gal > cap) {
         char buf[256];

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 
     };
     auto shat_at = [&](int col, const float (&cm)[4]) {
         const float ell = fmaf((float)col, cc.dell, cc.ell0);
-        const float F = exp2f(rc.alpha * dust_curve(cc, rc, exp2f(rc.beta * ell), col));
+        const float F = exp2f(rc.alpha * dust_curve(cc, rc, dust_pow(cc, rc, ell, col), col));
         return col_kappa(cc, col) * F * fmaf(rc.w[0], cm[0], fmaf(rc.w[1], cm[1], fmaf(rc.w[2], cm[2], rc.w[3] * cm[3])));
     };
     auto store = [&](int col, float sh) {

@@ -32,10 +32,13 @@ namespace dsps {
 struct WArgs {
     const float *params;
     int64_t G_stride, g_begin, n;
-    int n_age, n_z, K, K_pad, A_pad, KZ_pad, n_t, sfh_model, mdf_kernel, n_lut, dust_bump;
+    int n_age, n_z, K, K_pad, A_pad, KZ_pad, n_t, sfh_model, mdf_kernel, n_lut, dust_bump, dust_law;
     int n_u, SEC, u_ref, npar;   // nebular axis (n_u = 1: none), section length, reference bin, parameter rows
     const float *uedge;          // [n_u + 1] log U bin edges (+-1e30 outer)
     int2 *urange;                // out: per-tile log U bin ranges (atomics), with trange
+    int age_lo, age_hi;          // age bins whose weights are written (the others are 0): a dust group
+    float dust_T;                // the group's weight of the old-star dust values
+    int dust_row_old;            // parameter row of Av_old (delta_old next), or -1: one curve
     double t0, h, inv_h, dz, inv_dz, zmax, dlnlam;
     float zmax_f;          // largest float <= zmax (z <= zmax_f iff (double)z <= zmax)
     float t0_f, h_f, dlnlam_f;   // FP32 copies used by the per-galaxy warps
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
             for (int c = 0; c < 4; ++c) {
                 const int i = 4 * gq + c;
                 mu4[c] = valid ? mdf_mean_at(a, p, min(i, a.n_age - 1)) : 0.f;
-                fr4[c] = valid && i < a.n_age ? frac[i] : 0.f;
+                fr4[c] = valid && i < a.n_age && i >= a.age_lo && i < a.age_hi ? frac[i] : 0.f;
                 ulo[c] = -1e30f;
                 slo[c] = 0.f;
             }
@@ -476,7 +479,7 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
                 const float sh = j == nz - 1 ? 0.f : mdf_s<MDF>(uh);
                 float pj = sh - sl;
                 if (ul <= 0.f && uh > 0.f) pj += 1.f;
-                om = frac[i] * pj;
+                om = i >= a.age_lo && i < a.age_hi ? frac[i] * pj : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < NU; ++u) {
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
                     const float s_hi = last ? 0.f : mdf_s<MDF>(u_hi);
                     float pj = s_hi - s_lo;
                     if (u_lo <= 0.f && u_hi > 0.f) pj += 1.f;
-                    om[c] = frac[i] * pj;
+                    om[c] = i >= a.age_lo && i < a.age_hi ? frac[i] * pj : 0.f;
                     s_lo = s_hi;
                     u_lo = u_hi;
                 }
@@ -537,17 +540,27 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
     }
 
     if (lane == 0) {
-        if (!valid) atomicOr(a.err, DERR_PARAM);
         if (a.gidx) a.gidx[gi] = (int)gl;
+        // the dust of this call: rows 8, 9, or with age-dependent dust the
+        // group's Av = (1 - T) Av_young + T Av_old, delta likewise (Sec. 3.4.1)
+        float Av = p[8], dl = p[9];
+        if (a.dust_row_old >= 0 && MODE != W_MSUN) {
+            const float avo = a.params[(int64_t)a.dust_row_old * a.G_stride + g];
+            const float dlo = a.params[(int64_t)(a.dust_row_old + 1) * a.G_stride + g];
+            if (!isfinite(avo) || !isfinite(dlo)) valid = false;
+            Av = fmaf(a.dust_T, avo - p[8], p[8]);
+            dl = fmaf(a.dust_T, dlo - p[9], p[9]);
+        }
+        if (!valid) atomicOr(a.err, DERR_PARAM);
         if (MODE != W_MSUN) {
             float *ax = a.aux + gi * AUX_STRIDE;
-            ax[0] = -0.4f * 3.32192809488736235f * p[8];
-            ax[1] = p[9] - 0.7f;
+            ax[0] = -0.4f * 3.32192809488736235f * Av;
+            ax[1] = a.dust_law == DSPS_DUST_SALIM ? dl : dl - 0.7f;
             ax[2] = s_shift;
             ax[3] = valid ? 1.f : 0.f;
-            ax[4] = p[8];
-            ax[5] = p[9];
-            ax[6] = a.dust_bump ? (0.85f - 1.9f * p[9]) * (1.f / 4.05f) : 0.f;
+            ax[4] = Av;
+            ax[5] = dl;
+            ax[6] = a.dust_bump ? (0.85f - 1.9f * dl) * (1.f / 4.05f) : 0.f;
             ax[7] = a.dust_bump ? -1.9f / 4.05f : 0.f;
             a.magoff[gi] = valid ? gp.magoff : __int_as_float(0x7fc00000);
         }
@@ -910,6 +923,10 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.n = n;
     a.n_age = c.n_age;
     a.n_z = c.n_z;
+    a.age_lo = 0;
+    a.age_hi = c.n_age;
+    a.dust_T = 0.f;
+    a.dust_row_old = -1;
     a.n_u = c.n_u;
     a.SEC = c.SEC;
     a.u_ref = c.u_ref;
@@ -923,6 +940,7 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.sfh_model = c.opts.sfh_model;
     a.mdf_kernel = c.opts.mdf_kernel;
     a.dust_bump = c.opts.dust_bump;
+    a.dust_law = c.opts.dust_law;
     a.n_lut = c.n_lut;
     a.t0 = c.t0;
     a.h = (c.t1 - c.t0) / (c.n_t - 1);
@@ -1014,9 +1032,16 @@ cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *pa
 }
 
 cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const float *params, int64_t G_stride,
-                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted) {
+                           int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted,
+                           const DustGroup *group) {
     if (n <= 0) return cudaSuccess;
     WArgs a = make_wargs(c, w, params, G_stride, g_begin, n);
+    if (group) {
+        a.age_lo = group->i0;
+        a.age_hi = group->i1;
+        a.dust_T = group->T;
+        a.dust_row_old = c.row_dust_old;
+    }
     a.w_msun = w_msun;
     a.perm = sorted ? w.perm : nullptr;
     a.gidx = sorted ? w.gidx : nullptr;

@@ -34,6 +34,8 @@ DSPS_MDF_TRIWEIGHT = 0
 DSPS_MDF_GAUSSIAN = 1
 DSPS_MDF_MEAN_LINEAR = 0
 DSPS_MDF_MEAN_TERF = 1
+DSPS_DUST_POWERLAW = 0
+DSPS_DUST_SALIM = 1
 DSPS_PREC_FP32 = 0
 DSPS_PREC_BF16X3 = 1
 DSPS_NPAR = 12
@@ -57,7 +59,9 @@ class dsps_opts(C.Structure):
                 ("sfh_model", C.c_int32), ("mdf_kernel", C.c_int32), ("device", C.c_int32),
                 ("max_chunk", C.c_int64), ("hbm_budget_bytes", C.c_int64), ("n_streams", C.c_int32),
                 ("z_max", C.c_double), ("band_skip", C.c_int32), ("mdf_mean", C.c_int32),
-                ("mdf_terf_x0", C.c_double), ("mdf_terf_h", C.c_double), ("dust_bump", C.c_int32)]
+                ("mdf_terf_x0", C.c_double), ("mdf_terf_h", C.c_double), ("dust_bump", C.c_int32),
+                ("dust_law", C.c_int32), ("dust_agedep", C.c_int32), ("dust_agedep_x0", C.c_double),
+                ("dust_agedep_h", C.c_double)]
 
 
 DSPS_PROF_KINDS = 4
@@ -298,7 +302,8 @@ class Context:
     def __init__(self, ssp, sfh_model=DSPS_SFH_DELAYED_TAU, mdf_kernel=DSPS_MDF_TRIWEIGHT, device=0,
                  max_chunk=None, hbm_budget_bytes=None, n_streams=None, om0=0.3, w0=-1.0, h=0.7, z_max=10.0,
                  band_skip=True, mdf_mean=DSPS_MDF_MEAN_LINEAR, mdf_terf_x0=None, mdf_terf_h=None,
-                 dust_bump=False):
+                 dust_bump=False, dust_law=DSPS_DUST_POWERLAW, dust_agedep=False, dust_agedep_x0=None,
+                 dust_agedep_h=None):
         self._keep = [np.ascontiguousarray(ssp.log_age_yr, dtype=np.float64),
                       np.ascontiguousarray(ssp.lgz, dtype=np.float64),
                       np.ascontiguousarray(ssp.lam, dtype=np.float64),
@@ -318,6 +323,12 @@ class Context:
         o.band_skip = 1 if band_skip else 0
         o.mdf_mean = mdf_mean
         o.dust_bump = 1 if dust_bump else 0
+        o.dust_law = int(dust_law)
+        o.dust_agedep = 1 if dust_agedep else 0
+        if dust_agedep_x0 is not None:
+            o.dust_agedep_x0 = dust_agedep_x0
+        if dust_agedep_h is not None:
+            o.dust_agedep_h = dust_agedep_h
         if mdf_terf_x0 is not None:
             o.mdf_terf_x0 = mdf_terf_x0
         if mdf_terf_h is not None:
@@ -331,8 +342,9 @@ class Context:
         self.device = device
         self.n_age, self.n_z = len(la), len(lz)
         self.n_u = len(lu) if lu is not None else 1
-        self.npar = DSPS_NPAR_NEB if self.n_u > 1 else DSPS_NPAR      # parameter rows
-        self.ngrad = DSPS_NGRAD_NEB if self.n_u > 1 else DSPS_NGRAD   # gradient rows
+        extra = 2 if dust_agedep else 0                                # Av_old, delta_old
+        self.npar = (DSPS_NPAR_NEB if self.n_u > 1 else DSPS_NPAR) + extra      # parameter rows
+        self.ngrad = (DSPS_NGRAD_NEB if self.n_u > 1 else DSPS_NGRAD) + extra   # gradient rows
         self.handle = dsps_create(g, o)
         self.n_filt = {}
 

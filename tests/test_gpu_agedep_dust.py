@@ -1,0 +1,134 @@
+"""Parity of age-dependent dust (Sec. 3.4.1, Eq. agedep_dust_csp: each age bin
+attenuated with Av and delta moving from young-star to old-star values along
+T_erf in log age) between the CUDA path and the FP64 oracle: magnitudes and
+gradients (rows 11, 12 = Av_old, delta_old) in both precision forms, the
+equal-values limit, batch invariance and the request loop."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_06830_gb300 import synth
+
+import _util
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = {"birthcloud": dict(x0=7.0, h=0.1, law=0, bump=0), "wide_salim": dict(x0=8.0, h=0.3, law=1, bump=1)}
+
+
+def _ctx(case, **kw):
+    from paper_2112_06830_gb300 import dsps
+    c = CASES[case]
+    return dsps.Context(_util.ssp("full"), sfh_model=synth.SFH_DPL_QUENCH, dust_agedep=True, dust_agedep_x0=c["x0"],
+                        dust_agedep_h=c["h"], dust_law=c["law"], dust_bump=bool(c["bump"]), **kw)
+
+
+def _ogrid(case):
+    c = CASES[case]
+    g = _util.ssp("full")
+    return oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, t0=g.t0, t1=g.t1, n_t=g.n_t,
+                       sfh_model=synth.SFH_DPL_QUENCH, dust_agedep=1, dust_x0=c["x0"], dust_h=c["h"],
+                       dust_law=c["law"], dust_bump=c["bump"])
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def agedep(request):
+    c = _ctx(request.param)
+    f = synth.make_filters(12)
+    yield request.param, c, c.add_filters(f), oracle.Filters(f), _ogrid(request.param)
+    c.close()
+
+
+def _pop(n, seed, start=0):
+    p = synth.with_agedep_dust(synth.make_population(synth.SFH_DPL_QUENCH, n, seed, start), seed, start)
+    return _util.params_f32(p)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, _util.TOL_FP32), (1, _util.TOL_BF16X3)])
+def test_photometry_matches_oracle(agedep, prec, tol):
+    case, ctx, sid, F, grid = agedep
+    assert (ctx.npar, ctx.ngrad) == (14, 13)
+    p32, p64 = _pop(400, 61)
+    m = ctx.photometry(torch.from_numpy(p32).cuda(), sid, precision=prec).cpu().numpy().astype(np.float64)
+    idx = np.r_[0:8, 200:206, 390:400]
+    ref = oracle.mags(grid, F, p64[:, idx])
+    err = np.abs(m[idx] - ref)
+    print(f"age-dependent dust {case} prec={prec}: max |dm| = {err.max():.3e}")
+    assert err.max() <= tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gradients_match_oracle(agedep, prec):
+    case, ctx, sid, F, grid = agedep
+    n = 160
+    p32, p64 = _pop(n, 62, 700)
+    mbar = np.random.default_rng(8).standard_normal((n, 12))
+    _, pb = ctx.photometry_vjp(torch.from_numpy(p32).cuda(), sid, torch.from_numpy(mbar.astype(np.float32)).cuda(),
+                               precision=prec)
+    pb = pb.cpu().numpy().astype(np.float64)
+    assert pb.shape == (13, n)
+    idx = np.r_[0:6, 128:134, 154:160]
+    _, ref = oracle.mags_vjp(grid, F, p64[:, idx], mbar[idx])
+    floor = {0: 1e-3, 1: 1e-2}[prec]
+    scale = np.maximum(np.abs(ref), floor * np.abs(ref).max(axis=0, keepdims=True))
+    rel = np.abs(pb[:, idx] - ref) / scale
+    where = np.unravel_index(np.argmax(rel), rel.shape)
+    print(f"age-dependent dust {case} prec={prec}: max scaled gradient error {rel.max():.2e} at {where}")
+    assert rel.max() <= 1e-3
+
+
+def test_equal_young_and_old_values_match_one_curve():
+    from paper_2112_06830_gb300 import dsps
+    ctx = _ctx("birthcloud")
+    plain = dsps.Context(_util.ssp("full"), sfh_model=synth.SFH_DPL_QUENCH)
+    f = synth.make_filters(12)
+    s1, s0 = ctx.add_filters(f), plain.add_filters(f)
+    p32, _ = _pop(300, 63)
+    p32[12], p32[13] = p32[8], p32[9]
+    p = torch.from_numpy(p32).cuda()
+    mb = torch.from_numpy(np.random.default_rng(9).standard_normal((300, 12)).astype(np.float32)).cuda()
+    for prec, tol in ((0, 2e-5), (1, 2e-4)):
+        m1, g1 = ctx.photometry_vjp(p, s1, mb, precision=prec)
+        m0, g0 = plain.photometry_vjp(p[:12].contiguous(), s0, mb, precision=prec)
+        assert (m1 - m0).abs().max().item() <= tol
+        gsum = g1[:11].clone()
+        gsum[8] += g1[11]
+        gsum[9] += g1[12]
+        scale = torch.clamp(g0.abs(), min=1e-3 * g0.abs().max().item())
+        assert ((gsum - g0).abs() / scale).max().item() <= 2e-3
+    ctx.close()
+    plain.close()
+
+
+def test_batch_invariance_and_request_loop():
+    from paper_2112_06830_gb300 import dsps
+    big, small = _ctx("birthcloud"), _ctx("birthcloud", max_chunk=256)
+    f = synth.make_filters(8)
+    sb, ss = big.add_filters(f), small.add_filters(f)
+    p32, _ = _pop(900, 64)
+    p = torch.from_numpy(p32).cuda()
+    mb = np.random.default_rng(10).standard_normal((900, 8)).astype(np.float32)
+    for prec in (0, 1):
+        m1, g1 = big.photometry_vjp(p, sb, torch.from_numpy(mb).cuda(), precision=prec)
+        m2, g2 = small.photometry_vjp(p, ss, torch.from_numpy(mb).cuda(), precision=prec)
+        assert torch.equal(m1, m2) and torch.equal(g1, g2)
+        assert torch.equal(big.photometry(p, sb, precision=prec), m1)
+    t = big.submit(p32, sb, precision=1, mag_bar=mb)
+    while big.poll(t, 100000) == dsps.DSPS_PENDING:
+        pass
+    m, g = big.photometry_vjp(p, sb, torch.from_numpy(mb).cuda(), precision=1)
+    assert np.array_equal(t.mags, m.cpu().numpy()) and np.array_equal(t.param_bar, g.cpu().numpy())
+    big.close()
+    small.close()
+
+
+def test_unsupported_calls_are_refused(agedep):
+    from paper_2112_06830_gb300 import dsps
+    _, ctx, sid, _, _ = agedep
+    p = torch.zeros((14, 4), device="cuda")
+    with pytest.raises(dsps.DSPSError):
+        ctx.spectra(p, 0, 100)
+    out = torch.empty((4, 12), device="cuda")
+    rc = dsps.load().dsps_photometry_fp32_static(ctx.handle, 4, p.data_ptr(), sid, out.data_ptr(), None)
+    assert rc == dsps.DSPS_ERR_UNSUPPORTED
