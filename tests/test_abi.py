@@ -39,6 +39,30 @@ def test_default_opts():
     o = dsps.dsps_default_opts()
     assert (o.om0, o.w0, o.h) == (0.3, -1.0, 0.7)
     assert o.max_chunk == 262144 and o.z_max == 10.0 and o.n_streams == 4
+    assert (o.dust_bump, o.dust_law, o.dust_agedep) == (0, dsps.DSPS_DUST_POWERLAW, 0)
+    assert (o.dust_agedep_x0, o.dust_agedep_h) == (7.0, 0.1)
+    assert (o.mdf_mean, o.mdf_terf_x0, o.mdf_terf_h) == (dsps.DSPS_MDF_MEAN_LINEAR, 9.0, 0.5)
+
+
+def test_struct_layouts_match_the_header():
+    """The ctypes mirrors of dsps_grid / dsps_opts end with the fields the
+    header declares last (a mismatch would shift every later field)."""
+    import re
+    from paper_2112_06830_gb300 import dsps
+    hdr = open(os.path.join(ROOT, "include", "dsps.h")).read()
+    for cname, pyc in (("dsps_grid", dsps.dsps_grid), ("dsps_opts", dsps.dsps_opts),
+                       ("dsps_line_spec", dsps.dsps_line_spec), ("dsps_hist_spec", dsps.dsps_hist_spec)):
+        body = re.search(r"typedef struct \{([^{}]*)\} " + cname + ";", hdr).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        names = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            decl = re.sub(r"\bconst\b|\*", " ", decl)
+            parts = decl.split()
+            names += [n.strip() for n in " ".join(parts[1:]).split(",")]
+        assert [f[0] for f in pyc._fields_] == names, cname
 
 
 def test_create_without_gpu_fails_cleanly():
