@@ -300,7 +300,7 @@ __device__ __forceinline__ float pneb_lane(const WArgs &a, const float *p, bool 
 }
 
 template <int MODE, int SFH, int MDF, bool NEB>
-__global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
+__global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
@@ -417,6 +417,11 @@ __global__ void __launch_bounds__(256, 4) weights_kernel(WArgs a) {
                 for (int u = 0; u < NU; ++u) {
                     if (NEB && u >= a.n_u) break;
                     const int kzu = kz + u * a.SEC;
+                    if (NEB && pu[u] == 0.f) {   // outside the galaxy's log U support
+                        *reinterpret_cast<uint2 *>(rh + kzu) = make_uint2(0u, 0u);
+                        *reinterpret_cast<uint2 *>(rl + kzu) = make_uint2(0u, 0u);
+                        continue;
+                    }
                     const float4 wm = __ldg(reinterpret_cast<const float4 *>(a.wmul + kzu));
                     float o[4];
 #pragma unroll
