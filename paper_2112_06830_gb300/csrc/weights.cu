@@ -615,7 +615,7 @@ __host__ __device__ inline size_t weights_vjp_smem_per_warp(int n_t, int n_age) 
 }
 
 template <int SFH, int MDF, bool NEB>
-__global__ void __launch_bounds__(256) weights_vjp_kernel(WArgs a, const float *what, int scaled, float *pbar) {
+__global__ void __launch_bounds__(256, NEB ? 2 : 4) weights_vjp_kernel(WArgs a, const float *what, int scaled, float *pbar) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
