@@ -70,13 +70,14 @@ int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *p
         if (precision == DSPS_PREC_FP32) {
             {
                 ProfScope ps(*c, 0, s, prof);
-                e = launch_weights(*c, w, W_OMEGA_F32, params, n_gal, g0, n, nullptr, s);
+                e = launch_zsort(*c, w, params, n_gal, g0, n, s);
+                if (e == cudaSuccess) e = launch_weights(*c, w, W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, true);
             }
             if (e == cudaSuccess) {
                 // with a histogram, the chunk's magnitudes go to the (otherwise
                 // unused) [cap][16] scratch and are binned from there
                 ProfScope ps(*c, 1, s, prof);
-                e = launch_phot_simt(*c, w, fs, n, hist ? w.cq : mags + g0 * fs.Q, s);
+                e = launch_phot_simt(*c, w, fs, n, hist ? w.cq : mags + g0 * fs.Q, s, false, true);
                 if (e == cudaSuccess && hist) e = launch_histogram(w.cq, n, fs.Q, *hist, s);
             }
         } else {
@@ -118,21 +119,22 @@ int run_photometry_vjp_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const floa
         int parts = 1;
         {
             ProfScope ps(*c, 0, s, prof);
-            if (tc) e = launch_zsort(*c, w, params, n_gal, g0, n, s);
+            e = launch_zsort(*c, w, params, n_gal, g0, n, s);
             if (e == cudaSuccess)
-                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, tc);
+                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, true);
         }
         if (e == cudaSuccess) {
             ProfScope ps(*c, tc ? 2 : 1, s, prof);
-            e = tc ? launch_phot_tc(*c, w, fs, n, &parts, s, true) : launch_phot_simt(*c, w, fs, n, nullptr, s, true);
+            e = tc ? launch_phot_tc(*c, w, fs, n, &parts, s, true)
+                   : launch_phot_simt(*c, w, fs, n, nullptr, s, true, true);
         }
         if (e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);
-            e = launch_combine_grad(*c, w, fs, n, parts, tc, mag_bar + g0 * fs.Q, mags ? mags + g0 * fs.Q : nullptr,
+            e = launch_combine_grad(*c, w, fs, n, parts, true, mag_bar + g0 * fs.Q, mags ? mags + g0 * fs.Q : nullptr,
                                     param_bar, n_gal, g0, s);
-            if (e == cudaSuccess) e = launch_shat(*c, w, fs, n, tc, tc && c->opts.band_skip, s);
-            if (e == cudaSuccess) e = tc ? launch_vjp_tc(*c, w, fs, n, s) : launch_vjp_simt(*c, w, n, s);
-            if (e == cudaSuccess) e = launch_weights_vjp(*c, w, params, n_gal, g0, n, tc, tc, param_bar, s);
+            if (e == cudaSuccess) e = launch_shat(*c, w, fs, n, tc, c->opts.band_skip != 0, s);
+            if (e == cudaSuccess) e = tc ? launch_vjp_tc(*c, w, fs, n, s) : launch_vjp_simt(*c, w, n, s, 0, -1, &fs);
+            if (e == cudaSuccess) e = launch_weights_vjp(*c, w, params, n_gal, g0, n, true, tc, param_bar, s);
         }
         if (e != cudaSuccess) {
             set_last_error(cudaGetErrorString(e));

@@ -284,8 +284,10 @@ int make_hist_args(const dsps_hist_spec *spec, int n_filt, unsigned long long *c
 
 // grad: instead of magnitudes, writes the sums N, A, D per filter (see
 // epilogue.cuh) to ctx.d_partial as a single part.
+// sorted: rows in the order of launch_zsort (magnitudes written through
+// w.gidx), each 128-row tile contracting only the wavelength tiles of its band.
 cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, float *mags,
-                             cudaStream_t s, bool grad = false);
+                             cudaStream_t s, bool grad = false, bool sorted = false);
 
 // Writes per-part filter sums to ctx.d_partial (sorted rows); returns the
 // number of parts through *parts.
@@ -300,9 +302,10 @@ cudaError_t launch_combine_grad(const Ctx &c, const Workspace &w, const FilterSe
                                 int64_t g_begin, cudaStream_t s);
 cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, bool bf16, bool band,
                         cudaStream_t s);
-// col0/col1: the Shat columns that take part (multiples of 16; 0, N_pad for all).
+// col0/col1: the Shat columns that take part (multiples of 16; 0, N_pad for all);
+// fs: with sorted rows and band skipping, each 128-row tile's band only.
 cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s, int col0 = 0,
-                            int col1 = -1);
+                            int col1 = -1, const FilterSet *fs = nullptr);
 cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, cudaStream_t s);
 cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride,
                                int64_t g_begin, int64_t n, bool sorted, bool scaled, float *param_bar,

@@ -1,7 +1,9 @@
 // phot_simt.cu -- FP32 SIMT form of the fused photometry kernel.
 //
 // S = omega . L (Eq. full_mdf) as a register-tiled FP32 GEMM: each CTA owns 128
-// galaxies and walks every 128-wide wavelength tile; after the K loop of a tile
+// galaxies and walks the 128-wide wavelength tiles -- with sorted rows, only
+// those inside the tile's redshifted filter band (the others contribute exact
+// zeros, as in the tensor-core form); after the K loop of a tile
 // the 128x128 block of S goes through shared memory to the epilogue, where two
 // threads per galaxy row apply dust, the redshifted filter lookup and the
 // wavelength reduction (epilogue.cuh).  Per-(galaxy, filter) sums stay in
@@ -27,8 +29,11 @@ struct SArgs {
     const float4 *tab;
     const float *offq;
     ColConst cc;
-    float *mags;           // [n][Q]
+    float *mags;           // [n][Q] (row gidx[r] with sorted rows)
     float *partial;        // gradient mode: [n][3 * 4 * Q4] sums N, A, D per filter
+    const int2 *trange;    // per 128-row tile redshift-shift range (sorted rows), or nullptr: every tile
+    const int *gidx;       // sorted row -> chunk galaxy, or nullptr
+    int m_nz_lo, m_nz_hi;  // filter table rows with non-zero transmission
 };
 
 template <int Q4, bool GRAD>
@@ -51,7 +56,20 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
         for (int q = 0; q < 4 * Q4; ++q) acc[r3][q] = 0.f;
 
     const int KT = a.K_pad / BK;
-    for (int n0 = 0; n0 < a.N_pad; n0 += BN) {
+    // wavelength tiles whose interpolation rows can meet the filters' band for
+    // some shift of this tile's rows (all tiles without ranges)
+    int nbeg = 0, nend = a.N_pad;
+    if (a.trange) {
+        const int2 r = a.trange[blockIdx.x];
+        const int n_lo = a.m_nz_lo - r.y - 2, n_hi = a.m_nz_hi - r.x + 1;
+        if (r.y < r.x || a.m_nz_hi < a.m_nz_lo || n_hi < 0) {
+            nend = 0;
+        } else {
+            nbeg = max(n_lo, 0) / BN * BN;
+            nend = min(a.N_pad, (n_hi / BN + 1) * BN);
+        }
+    }
+    for (int n0 = nbeg; n0 < nend; n0 += BN) {
         float c[8][8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
@@ -149,7 +167,7 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
 #pragma unroll
                 for (int q = 0; q < 4 * Q4; ++q) dst[r3 * 4 * Q4 + q] = acc[r3][q];
         } else {
-            write_mags<Q4>(acc[0], a.Q, a.magoff[row], a.offq, a.mags + row * a.Q);
+            write_mags<Q4>(acc[0], a.Q, a.magoff[row], a.offq, a.mags + (a.gidx ? (int64_t)a.gidx[row] : row) * a.Q);
         }
     }
 }
@@ -179,7 +197,7 @@ ColConst make_col_const(const Ctx &c) {
 }
 
 cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, float *mags,
-                             cudaStream_t s, bool grad) {
+                             cudaStream_t s, bool grad, bool sorted) {
     if (n <= 0) return cudaSuccess;
     SArgs a{};
     a.W = w.w32;
@@ -196,6 +214,10 @@ cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &
     a.cc = make_col_const(c);
     a.mags = mags;
     a.partial = w.partial;
+    a.trange = sorted && c.opts.band_skip ? w.trange : nullptr;
+    a.gidx = sorted ? w.gidx : nullptr;
+    a.m_nz_lo = fs.m_nz_lo;
+    a.m_nz_hi = fs.m_nz_hi;
     if (grad) {
         switch (fs.Q4) {
         case 1: return launch_q4<1, true>(a, n, s);

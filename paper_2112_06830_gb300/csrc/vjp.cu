@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 
 constexpr int BM = 128, BN = 128, BK = 16, THREADS = 256, AS_LD = BM + 4;
 
 __global__ void __launch_bounds__(THREADS, 2) vjp_simt_kernel(const float *A, const float *B, int64_t n, int K_pad,
-                                                              int N_pad, int col0, int col1, float *C) {
+                                                              int N_pad, int col0, int col1, const int2 *trange,
+                                                              VjpBand band, float *C) {
     __shared__ __align__(16) float As[2][BK][AS_LD];
     __shared__ __align__(16) float Bs[2][BK][AS_LD];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -170,7 +171,15 @@ __global__ void __launch_bounds__(THREADS, 2) vjp_simt_kernel(const float *A, co
             Bs[buf][q + 3][row] = rb[t].w;
         }
     };
-    // contraction over the Shat columns [col0, col1) (multiples of BK)
+    // contraction over the Shat columns [col0, col1) (multiples of BK), and over
+    // the row tile's band only when it has one (Shat is zero outside it)
+    if (band.on) {
+        int kb0, kb1;
+        vjp_band(band, trange, blockIdx.x, N_pad, kb0, kb1);
+        col0 = max(col0, kb0 * 32);
+        col1 = min(col1, kb1 * 32);
+        if (col1 < col0) col1 = col0;
+    }
     const int KT = (col1 - col0) / BK;
     gload(col0);
     sstore(0);
@@ -258,13 +267,15 @@ cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s, int col0, int col1) {
+cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s, int col0, int col1,
+                            const FilterSet *fs) {
     if (n <= 0) return cudaSuccess;
     if (col1 < 0) col1 = c.N_pad;
     if (col0 < 0 || col1 > c.N_pad || col0 % BK || col1 % BK || col1 <= col0) return cudaErrorInvalidValue;
+    const VjpBand b = fs ? make_vjp_band(c, *fs, c.opts.band_skip != 0) : VjpBand{0, 0, -1, 0};
     dim3 grid((unsigned)((n + BM - 1) / BM), (unsigned)((c.KZ_pad + BN - 1) / BN));
     vjp_simt_kernel<<<grid, THREADS, 0, s>>>(reinterpret_cast<const float *>(w.shat), c.d_Ld32, n, c.KZ_pad,
-                                             c.N_pad, col0, col1, w.w32);
+                                             c.N_pad, col0, col1, w.trange, b, w.w32);
     return cudaGetLastError();
 }
 

@@ -546,6 +546,11 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
 
     if (lane == 0) {
         if (a.gidx) a.gidx[gi] = (int)gl;
+        if (MODE == W_OMEGA_F32 && a.trange && valid) {   // the FP32 form's band ranges (no K masks)
+            const int i0 = (int)floorf(s_shift);
+            atomicMin(&a.trange[gi >> 7].x, i0);
+            atomicMax(&a.trange[gi >> 7].y, i0);
+        }
         // the dust of this call: rows 8, 9, or with age-dependent dust the
         // group's Av = (1 - T) Av_young + T Av_old, delta likewise (Sec. 3.4.1)
         float Av = p[8], dl = p[9];
@@ -1050,7 +1055,7 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
     a.w_msun = w_msun;
     a.perm = sorted ? w.perm : nullptr;
     a.gidx = sorted ? w.gidx : nullptr;
-    a.trange = sorted && mode == W_OMEGA_BF16X2 ? w.trange : nullptr;
+    a.trange = sorted && mode != W_MSUN ? w.trange : nullptr;
     a.urange = w.urange;
     a.kmask = w.kmask;
     a.kmw = c.kmask_words;
