@@ -8,7 +8,8 @@
 // bins with T = 0, each bin of the transition, and the old bins with T = 1
 // (Ctx::dust_groups).  Each group runs the ordinary fused path -- weights of
 // the group's ages only, with the group's dust constants, then the tensor-core
-// (or FP32) contraction with its fused epilogue -- and the groups' filter sums
+// (or FP32) contraction with its fused epilogue, both on the chunk's sorted
+// rows -- and the groups' filter sums
 // are added in a fixed order before the magnitudes are formed.  Every group
 // keeps the chunk's sort, so rows line up; skipped K blocks (ages outside the
 // group) hold exact zeros.
@@ -188,7 +189,7 @@ int fail_cuda(cudaError_t e) {
 cudaError_t groups_forward(Ctx *c, const Workspace &w, int64_t n_gal, int64_t g0, int64_t n, const float *params,
                            const FilterSet &fs, bool tc, bool grad, cudaStream_t s, bool prof) {
     cudaError_t e = cudaSuccess;
-    if (tc) {
+    {
         ProfScope ps(*c, 0, s, prof);
         e = launch_zsort(*c, w, params, n_gal, g0, n, s);
     }
@@ -198,14 +199,15 @@ cudaError_t groups_forward(Ctx *c, const Workspace &w, int64_t n_gal, int64_t g0
             ProfScope ps(*c, 0, s, prof);
             if (tc && k > 0) e = launch_tile_reset(*c, w, n, s);
             if (e == cudaSuccess)
-                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, tc,
+                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, true,
                                    &gr);
         }
         int parts = 1;
         if (e == cudaSuccess) {
             ProfScope ps(*c, tc ? 2 : 1, s, prof);
             // the FP32 form's sums come from its gradient mode (N, A, D per filter)
-            e = tc ? launch_phot_tc(*c, w, fs, n, &parts, s, grad) : launch_phot_simt(*c, w, fs, n, nullptr, s, true);
+            e = tc ? launch_phot_tc(*c, w, fs, n, &parts, s, grad)
+                   : launch_phot_simt(*c, w, fs, n, nullptr, s, true, true);
         }
         if (e == cudaSuccess) {
             ProfScope ps(*c, 0, s, prof);
@@ -228,7 +230,7 @@ int run_photometry_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const f
         cudaError_t e = groups_forward(c, w, n_gal, g0, n, params, fs, tc, false, s, prof);
         if (e == cudaSuccess) {
             ProfScope ps(*c, 0, s, prof);
-            e = launch_final(*c, w, fs, n, tc, hist ? nullptr : mags + g0 * fs.Q, hist, nullptr, nullptr, n_gal, g0,
+            e = launch_final(*c, w, fs, n, true, hist ? nullptr : mags + g0 * fs.Q, hist, nullptr, nullptr, n_gal, g0,
                              s);
         }
         if (e != cudaSuccess) return fail_cuda(e);
@@ -248,7 +250,7 @@ int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, con
         cudaError_t e = groups_forward(c, w, n_gal, g0, n, params, fs, tc, true, s, prof);
         if (e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);
-            e = launch_final(*c, w, fs, n, tc, mags ? mags + g0 * fs.Q : nullptr, nullptr, mag_bar + g0 * fs.Q,
+            e = launch_final(*c, w, fs, n, true, mags ? mags + g0 * fs.Q : nullptr, nullptr, mag_bar + g0 * fs.Q,
                              param_bar, n_gal, g0, s);
         }
         // adjoint of the weights: one adjoint contraction per group, merged rows
@@ -257,17 +259,17 @@ int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, con
             ProfScope ps(*c, 3, s, prof);
             if (tc) e = launch_tile_reset(*c, w, n, s);
             if (e == cudaSuccess)
-                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, tc,
+                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, true,
                                    &gr);
-            if (e == cudaSuccess) e = launch_shat(*c, w, fs, n, tc, tc && c->opts.band_skip, s);
-            if (e == cudaSuccess) e = tc ? launch_vjp_tc(*c, w, fs, n, s) : launch_vjp_simt(*c, w, n, s);
+            if (e == cudaSuccess) e = launch_shat(*c, w, fs, n, tc, c->opts.band_skip != 0, s);
+            if (e == cudaSuccess) e = tc ? launch_vjp_tc(*c, w, fs, n, s) : launch_vjp_simt(*c, w, n, s, 0, -1, &fs);
             if (e == cudaSuccess) e = launch_merge(*c, w, n, gr, k == 0, s);
         }
         if (e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);
             Workspace wm = w;
             wm.w32 = w.what2;
-            e = launch_weights_vjp(*c, wm, params, n_gal, g0, n, tc, tc, param_bar, s);
+            e = launch_weights_vjp(*c, wm, params, n_gal, g0, n, true, tc, param_bar, s);
         }
         if (e != cudaSuccess) return fail_cuda(e);
     }
