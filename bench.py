@@ -548,6 +548,18 @@ def run_ours(a):
                                                             stream.cuda_stream))
     assert torch.isfinite(d_pbar_a).all()
     ctx_a.close()
+    # the line width under the same dust: a window spectrum per group,
+    # attenuated and summed before the width is formed
+    ctx_ae = dsps.Context(synth.with_emission_line(ssp), sfh_model=synth.SFH_DPL_QUENCH, device=local,
+                          dust_agedep=True)
+    lid_a = ctx_ae.add_line(*synth.EW_LINE)
+    ms_age_ew = timed_fn(lambda: dsps.dsps_line_ew(ctx_ae.handle, G, d_params_a.data_ptr(), lid_a, d_ew.data_ptr(),
+                                                   stream.cuda_stream))
+    ms_age_ew_grad = timed_fn(lambda: dsps.dsps_line_ew_vjp(ctx_ae.handle, G, d_params_a.data_ptr(), lid_a,
+                                                            d_ewbar.data_ptr(), d_ew.data_ptr(), d_pbar_a.data_ptr(),
+                                                            stream.cuda_stream))
+    assert torch.isfinite(d_ew).all() and torch.isfinite(d_pbar_a).all()
+    ctx_ae.close()
     del d_params_a, d_pbar_a
 
     # The paper's benchmark step (Sec. 5.1) on these galaxies: photometry through
@@ -701,8 +713,13 @@ def run_ours(a):
                             "split-bf16; gradient with d/du_mean, d/du_sigma"},
         "agedep_dust": {"value": ws * G * N_FILT / (ms_age * 1e-3), "ms_per_step": ms_age,
                         "fwd_grad": {"value": ws * G * N_FILT / (ms_age_grad * 1e-3), "ms_per_step": ms_age_grad},
+                        "line_ew": {"value": ws * G / (ms_age_ew * 1e-3), "unit": "galaxy-EWs/s",
+                                    "ms_per_step": ms_age_ew,
+                                    "fwd_grad": {"value": ws * G / (ms_age_ew_grad * 1e-3),
+                                                 "ms_per_step": ms_age_ew_grad}},
                         "note": "age-dependent dust, T_erf transition at 10 Myr over 0.1 dex: one split-bf16 "
-                                "contraction per group of age bins sharing a curve (young, each transition bin, old)"},
+                                "contraction per group of age bins sharing a curve (young, each transition bin, old); "
+                                "line width: FP32 window spectrum per group over the group's ages"},
         "serve": serve,
         "clocks": clocks,
     }

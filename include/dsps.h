@@ -182,9 +182,8 @@ typedef struct {
                                   default 0                                      */
     int32_t dust_law;          /* DSPS_DUST_*; default DSPS_DUST_POWERLAW        */
     int32_t dust_agedep;       /* 1: age-dependent dust (see the parameter rows
-                                  above); spectra, line widths and
-                                  dsps_photometry_fp32_static then return
-                                  DSPS_ERR_UNSUPPORTED; default 0                */
+                                  above); dsps_photometry_fp32_static then
+                                  returns DSPS_ERR_UNSUPPORTED; default 0        */
     double dust_agedep_x0;     /* transition centre [log10 yr] and width h [dex], */
     double dust_agedep_h;      /* h > 0 (defaults 7, 0.1: the birth-cloud age)    */
 } dsps_opts;
@@ -269,8 +268,10 @@ int dsps_histogram(dsps_ctx *ctx, int64_t n_gal, const float *mags, int32_t n_fi
  * Eq. cspdef with the weights of Eq. agedep_mdf, times Eq. attenuation):
  *   out[g][n - n0] = 10^logM F_g(lam_n) sum_ij omega_gij L_ijn   [Lsun/Hz],
  * for grid columns n0 <= n < n1 (0 <= n0 < n1 <= n_lam), FP32 weights and FP32
- * contraction.  A galaxy with out-of-range parameters gets a NaN row.
- * params: device float32 [12][n_gal]; out: device float32 [n_gal][n1 - n0]. */
+ * contraction.  With age-dependent dust (Sec. 3.4.1) each age bin i takes its
+ * own curve F_gi, summed over the context's groups of bins in a fixed order.
+ * A galaxy with out-of-range parameters gets a NaN row.
+ * params: device float32 [npar][n_gal]; out: device float32 [n_gal][n1 - n0]. */
 int dsps_spectra(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t n0, int32_t n1,
                  float *out, dsps_stream_t stream);
 
@@ -301,10 +302,11 @@ int dsps_line_ew(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line
                  dsps_stream_t stream);
 
 /* Vector-Jacobian product of the equivalent widths:
- *   param_bar[k][g] = ew_bar[g] dW_g / d params[k][g],  k = 0..10
- * (row 10, logM, is exactly 0).  ew_bar: device float32 [n_gal]; ew: device
- * float32 [n_gal] or NULL; param_bar: device float32 [11][n_gal] ([13][n_gal] with
- * a nebular axis). */
+ *   param_bar[k][g] = ew_bar[g] dW_g / d params[k][g]
+ * over the context's gradient rows (row 10, logM, is exactly 0).  ew_bar:
+ * device float32 [n_gal]; ew: device float32 [n_gal] or NULL; param_bar:
+ * device float32 [11][n_gal], two more rows with a nebular axis and two more
+ * (Av_old, delta_old, last) with age-dependent dust. */
 int dsps_line_ew_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line_id,
                      const float *ew_bar, float *ew, float *param_bar, dsps_stream_t stream);
 

@@ -17,7 +17,8 @@
 // Gradient: the filter sums of the dust derivatives are accumulated per group
 // with the weights (1 - T, T) of the young and old values; the adjoint of the
 // weights runs the adjoint contraction once per group, with the group's
-// attenuation in Shat, keeps the adjoint rows of the group's ages, and then
+// attenuation in Shat (its dust constants rewritten in aux; the weights are
+// not needed again), keeps the adjoint rows of the group's ages, and then
 // runs the weights adjoint once on the merged rows.
 #include "dsps_internal.cuh"
 #include "epilogue.cuh"
@@ -120,17 +121,58 @@ __global__ void agedep_final_kernel(FinalArgs a) {
 
 // Keeps, in the merged adjoint rows, the columns of the group's ages
 // (kz = u SEC + j A_pad + i with i in [i0, i1)); the first group also zeroes
-// the padding columns.
-__global__ void merge_rows_kernel(const float *src, float *dst, int64_t n, int KZ_pad, int SEC, int A_pad, int nzA,
-                                  int n_u, int n_age, int i0, int i1, bool first) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * KZ_pad) return;
-    const int kz = (int)(idx % KZ_pad);
-    const int u = kz / SEC, rr = kz - u * SEC;
-    const bool pad = u >= n_u || rr >= nzA;
-    const int i = pad ? -1 : rr % A_pad;
-    if (!pad && i >= i0 && i < i1) dst[idx] = src[idx];
-    else if (first && (pad || i >= n_age)) dst[idx] = 0.f;
+// the padding columns.  A thread decodes four consecutive columns once and
+// walks a strip of rows, touching memory only where one of its columns is
+// kept or (first group) zeroed: a one-age group moves about 1 % of the rows.
+__global__ void merge_rows_kernel(const float *__restrict__ src, float *__restrict__ dst, int64_t n, int rows,
+                                  int KZ_pad, int SEC, int A_pad, int nzA, int n_u, int n_age, int i0, int i1,
+                                  bool first) {
+    const int kz0 = 4 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (kz0 >= KZ_pad) return;
+    unsigned keep = 0u, zero = 0u;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int kz = kz0 + c;
+        const int u = kz / SEC, rr = kz - u * SEC;
+        const bool pad = u >= n_u || rr >= nzA;
+        const int i = pad ? -1 : rr % A_pad;
+        if (!pad && i >= i0 && i < i1) keep |= 1u << c;
+        else if (first && (pad || i >= n_age)) zero |= 1u << c;
+    }
+    if (!(keep | zero)) return;
+    const int64_t r0 = (int64_t)blockIdx.y * rows;
+    const int64_t r1 = r0 + rows < n ? r0 + rows : n;
+#pragma unroll 4
+    for (int64_t r = r0; r < r1; ++r) {
+        const int64_t o = r * KZ_pad + kz0;
+        float4 v = keep ? *reinterpret_cast<const float4 *>(src + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!(keep & 1u)) v.x = 0.f;
+        if (!(keep & 2u)) v.y = 0.f;
+        if (!(keep & 4u)) v.z = 0.f;
+        if (!(keep & 8u)) v.w = 0.f;
+        if ((keep | zero) == 0xFu) {
+            *reinterpret_cast<float4 *>(dst + o) = v;
+        } else {
+            const unsigned m = keep | zero;
+            if (m & 1u) dst[o] = v.x;
+            if (m & 2u) dst[o + 1] = v.y;
+            if (m & 4u) dst[o + 2] = v.z;
+            if (m & 8u) dst[o + 3] = v.w;
+        }
+    }
+}
+
+// The group's dust constants in aux, for the chunk's sorted rows: the
+// adjoint passes need the group's curve but not its weights.
+__global__ void group_aux_kernel(const float *params, int64_t G_stride, int64_t g_begin, const int *gidx, int64_t n,
+                                 int row_old, float T, int dust_law, int bump, float *aux) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t g = g_begin + gidx[r];
+    const float avy = params[8 * G_stride + g], dly = params[9 * G_stride + g];
+    const float avo = params[(int64_t)row_old * G_stride + g], dlo = params[(int64_t)(row_old + 1) * G_stride + g];
+    store_dust_aux(aux + r * AUX_STRIDE, group_dust_value(T, avy, avo), group_dust_value(T, dly, dlo), dust_law,
+                   bump);
 }
 
 cudaError_t launch_tile_reset(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s) {
@@ -170,12 +212,11 @@ cudaError_t launch_final(const Ctx &c, const Workspace &w, const FilterSet &fs, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge(const Ctx &c, const Workspace &w, int64_t n, const DustGroup &gr, bool first,
-                         cudaStream_t s) {
-    const int64_t tot = n * c.KZ_pad;
-    merge_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(w.w32, w.what2, n, c.KZ_pad, c.SEC, c.A_pad,
-                                                                    c.n_z * c.A_pad, c.n_u, c.n_age, gr.i0, gr.i1,
-                                                                    first);
+cudaError_t launch_group_aux(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride,
+                             int64_t g_begin, int64_t n, const DustGroup &gr, cudaStream_t s) {
+    group_aux_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(params, G_stride, g_begin, w.gidx, n,
+                                                                 c.row_dust_old, gr.T, c.opts.dust_law,
+                                                                 c.opts.dust_bump, w.aux);
     return cudaGetLastError();
 }
 
@@ -219,6 +260,17 @@ cudaError_t groups_forward(Ctx *c, const Workspace &w, int64_t n_gal, int64_t g0
 
 }  // namespace
 
+cudaError_t launch_merge_rows(const Ctx &c, const Workspace &w, int64_t n, const DustGroup &gr, bool first,
+                         cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int rows = 64;
+    while ((n + rows - 1) / rows > 65535) rows *= 2;
+    const dim3 grid((unsigned)((c.KZ_pad / 4 + 127) / 128), (unsigned)((n + rows - 1) / rows));
+    merge_rows_kernel<<<grid, 128, 0, s>>>(w.w32, w.what2, n, rows, c.KZ_pad, c.SEC, c.A_pad, c.n_z * c.A_pad, c.n_u,
+                                          c.n_age, gr.i0, gr.i1, first);
+    return cudaGetLastError();
+}
+
 int run_photometry_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *params, const FilterSet &fs,
                              int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist) {
     Workspace w = w0;
@@ -253,17 +305,16 @@ int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, con
             e = launch_final(*c, w, fs, n, true, mags ? mags + g0 * fs.Q : nullptr, nullptr, mag_bar + g0 * fs.Q,
                              param_bar, n_gal, g0, s);
         }
-        // adjoint of the weights: one adjoint contraction per group, merged rows
+        // adjoint of the weights: one adjoint contraction per group, with the
+        // group's curve in aux (the tile ranges depend on z alone and stay),
+        // merged rows
         for (size_t k = 0; k < c->dust_groups.size() && e == cudaSuccess; ++k) {
             const DustGroup &gr = c->dust_groups[k];
             ProfScope ps(*c, 3, s, prof);
-            if (tc) e = launch_tile_reset(*c, w, n, s);
-            if (e == cudaSuccess)
-                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, true,
-                                   &gr);
+            e = launch_group_aux(*c, w, params, n_gal, g0, n, gr, s);
             if (e == cudaSuccess) e = launch_shat(*c, w, fs, n, tc, c->opts.band_skip != 0, s);
             if (e == cudaSuccess) e = tc ? launch_vjp_tc(*c, w, fs, n, s) : launch_vjp_simt(*c, w, n, s, 0, -1, &fs);
-            if (e == cudaSuccess) e = launch_merge(*c, w, n, gr, k == 0, s);
+            if (e == cudaSuccess) e = launch_merge_rows(*c, w, n, gr, k == 0, s);
         }
         if (e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);

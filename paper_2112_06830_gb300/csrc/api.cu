@@ -135,7 +135,7 @@ void free_ctx(Ctx *c) {
     }
     for (auto &ls : c->lines) cudaFree(ls.d_tab);
     void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_k0, c->d_edges, c->d_einh, c->d_bwidth,
-                    c->d_zedge, c->d_uedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->d_err, c->d_stats,
+                    c->d_zedge, c->d_uedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->ws.ewacc, c->d_err, c->d_stats,
                     c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d};
     for (void *p : ptrs) cudaFree(p);
     for (auto &r : c->prof_recs) {
@@ -575,7 +575,6 @@ int dsps_spectra(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t n0, 
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !out))) return fail(DSPS_ERR_INVALID_ARG, "dsps_spectra: bad argument%s");
     if (n0 < 0 || n1 <= n0 || n1 > c->n_lam) return fail(DSPS_ERR_INVALID_ARG, "dsps_spectra: need 0 <= n0 < n1 <= n_lam%s");
-    if (c->opts.dust_agedep) return fail(DSPS_ERR_UNSUPPORTED, "dsps_spectra: not with age-dependent dust%s");
     std::lock_guard<std::mutex> lk(c->mu);
     if (n_gal == 0) return DSPS_OK;
     DSPS_CUDA(cudaSetDevice(c->device));
@@ -661,10 +660,9 @@ int dsps_line_ew(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !ew))) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew: bad argument%s");
     std::lock_guard<std::mutex> lk(c->mu);
     if (line_id < 0 || line_id >= (int)c->lines.size()) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew: unknown line%s");
-    if (c->opts.dust_agedep) return fail(DSPS_ERR_UNSUPPORTED, "dsps_line_ew: not with age-dependent dust%s");
     if (n_gal == 0) return DSPS_OK;
     DSPS_CUDA(cudaSetDevice(c->device));
-    const int rc = ensure_shat(c);
+    const int rc = ensure_shat(c, c->opts.dust_agedep != 0);
     if (rc != DSPS_OK) return rc;
     return run_line_ew_ws(c, c->ws, n_gal, params, c->lines[line_id], nullptr, ew, nullptr,
                           reinterpret_cast<cudaStream_t>(stream));
@@ -677,10 +675,9 @@ int dsps_line_ew_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t 
         return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew_vjp: bad argument%s");
     std::lock_guard<std::mutex> lk(c->mu);
     if (line_id < 0 || line_id >= (int)c->lines.size()) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew_vjp: unknown line%s");
-    if (c->opts.dust_agedep) return fail(DSPS_ERR_UNSUPPORTED, "dsps_line_ew_vjp: not with age-dependent dust%s");
     if (n_gal == 0) return DSPS_OK;
     DSPS_CUDA(cudaSetDevice(c->device));
-    const int rc = ensure_shat(c);
+    const int rc = ensure_shat(c, c->opts.dust_agedep != 0);
     if (rc != DSPS_OK) return rc;
     return run_line_ew_ws(c, c->ws, n_gal, params, c->lines[line_id], ew_bar, ew, param_bar,
                           reinterpret_cast<cudaStream_t>(stream));

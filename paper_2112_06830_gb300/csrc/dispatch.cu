@@ -144,17 +144,21 @@ int run_photometry_vjp_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const floa
     return DSPS_OK;
 }
 
-int ensure_shat(Ctx *c) {
-    if (c->ws.shat) return DSPS_OK;
-    // [chunk][N_pad] x 4 bytes, made on the first call that needs it: Shat of
-    // the adjoint (FP32, or bf16 hi + lo), the window spectra of the line widths.
-    void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, (size_t)c->chunk * c->N_pad * 4);
-    if (e != cudaSuccess) {
-        set_last_error(cudaGetErrorString(e));
-        return DSPS_ERR_CUDA;
+int ensure_shat(Ctx *c, bool ewacc) {
+    // [chunk][N_pad] x 4 bytes each, made on the first call that needs them:
+    // Shat of the adjoint (FP32, or bf16 hi + lo), the window spectra of the
+    // line widths; and the line widths' summed window under age-dependent dust.
+    void **slots[2] = {&c->ws.shat, reinterpret_cast<void **>(&c->ws.ewacc)};
+    for (int i = 0; i < (ewacc ? 2 : 1); ++i) {
+        if (*slots[i]) continue;
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)c->chunk * c->N_pad * 4);
+        if (e != cudaSuccess) {
+            set_last_error(cudaGetErrorString(e));
+            return DSPS_ERR_CUDA;
+        }
+        *slots[i] = p;
     }
-    c->ws.shat = p;
     return DSPS_OK;
 }
 

@@ -84,6 +84,22 @@ constexpr int KBLOCK = 32;   // kz block of the tensor-core contraction (one TMA
 //   6 e  = (0.85 - 1.9 delta) / 4.05, 7 de/ddelta = -1.9 / 4.05  (UV bump; 0 without)
 // magoff[g] = -2.5 logM + Dmod(z) - 2.5 log10(1+z)
 
+// Entries 0, 1, 4-7 of aux from the curve's Av and delta (Sec. 3.4): the one
+// definition the weights kernel and the age-dependent dust passes share.
+__device__ __forceinline__ void store_dust_aux(float *ax, float Av, float dl, int dust_law, int bump) {
+    ax[0] = -0.4f * 3.32192809488736235f * Av;
+    ax[1] = dust_law == DSPS_DUST_SALIM ? dl : dl - 0.7f;
+    ax[4] = Av;
+    ax[5] = dl;
+    ax[6] = bump ? (0.85f - 1.9f * dl) * (1.f / 4.05f) : 0.f;
+    ax[7] = bump ? -1.9f / 4.05f : 0.f;
+}
+
+// Sec. 3.4.1: a dust value of an age group, (1 - T) young + T old.
+__device__ __forceinline__ float group_dust_value(float T, float young, float old) {
+    return fmaf(T, old - young, young);
+}
+
 struct FilterSet {
     int Q = 0, Q4 = 0;         // filters; float4 groups per table row
     int m_rows = 0;            // table rows; row m_rows-1 is all zero
@@ -152,6 +168,8 @@ struct Workspace {
     float *gacc = nullptr;                      // [cap][5 * QSTRIDE_MAX] sums over dust groups (age-dependent dust)
     float *what2 = nullptr;                     // [cap][KZ_pad] adjoint rows merged over dust groups (likewise)
     void *shat = nullptr;                       // [cap][N_pad] x 4 bytes (adjoint only)
+    float *ewacc = nullptr;                     // [cap][N_pad] summed attenuated window of the line widths
+                                                // (age-dependent dust; made on first use)
     unsigned long long *stats = nullptr;        // tensor-core tile counter, or nullptr
 };
 
@@ -315,8 +333,14 @@ cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *pa
 // (dispatch.cu); mags/param_bar are the caller's device pointers.
 int run_photometry_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
                       int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist = nullptr);
-// Allocates ctx.ws.shat if it is not there yet (dispatch.cu).
-int ensure_shat(Ctx *c);
+// Allocates ctx.ws.shat (and, with ewacc, ctx.ws.ewacc) if it is not there
+// yet (dispatch.cu).
+int ensure_shat(Ctx *c, bool ewacc = false);
+
+// Age-dependent dust (agedep.cu): keeps, in w.what2, the adjoint rows of w.w32
+// at the columns of the group's ages (the first group also zeroes padding).
+cudaError_t launch_merge_rows(const Ctx &c, const Workspace &w, int64_t n, const DustGroup &gr, bool first,
+                              cudaStream_t s);
 // Spectra and line widths (spectrum.cu); w.shat must be allocated.
 int run_spectra_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, int n0, int n1, float *out,
                    cudaStream_t s);

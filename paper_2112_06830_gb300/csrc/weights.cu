@@ -558,20 +558,15 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
             const float avo = a.params[(int64_t)a.dust_row_old * a.G_stride + g];
             const float dlo = a.params[(int64_t)(a.dust_row_old + 1) * a.G_stride + g];
             if (!isfinite(avo) || !isfinite(dlo)) valid = false;
-            Av = fmaf(a.dust_T, avo - p[8], p[8]);
-            dl = fmaf(a.dust_T, dlo - p[9], p[9]);
+            Av = group_dust_value(a.dust_T, p[8], avo);
+            dl = group_dust_value(a.dust_T, p[9], dlo);
         }
         if (!valid) atomicOr(a.err, DERR_PARAM);
         if (MODE != W_MSUN) {
             float *ax = a.aux + gi * AUX_STRIDE;
-            ax[0] = -0.4f * 3.32192809488736235f * Av;
-            ax[1] = a.dust_law == DSPS_DUST_SALIM ? dl : dl - 0.7f;
+            store_dust_aux(ax, Av, dl, a.dust_law, a.dust_bump);
             ax[2] = s_shift;
             ax[3] = valid ? 1.f : 0.f;
-            ax[4] = Av;
-            ax[5] = dl;
-            ax[6] = a.dust_bump ? (0.85f - 1.9f * dl) * (1.f / 4.05f) : 0.f;
-            ax[7] = a.dust_bump ? -1.9f / 4.05f : 0.f;
             a.magoff[gi] = valid ? gp.magoff : __int_as_float(0x7fc00000);
         }
     }

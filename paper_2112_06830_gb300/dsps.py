@@ -440,7 +440,7 @@ class Context:
         return ew
 
     def line_ew_vjp(self, params, line_id, ew_bar, stream=None):
-        """(ew [G], param_bar [11, G]) with param_bar = ew_bar dW/dparams."""
+        """(ew [G], param_bar [ngrad, G]) with param_bar = ew_bar dW/dparams."""
         import torch
         params = params.contiguous()
         ew_bar = ew_bar.contiguous().to(torch.float32)

@@ -2,7 +2,10 @@
 attenuated with Av and delta moving from young-star to old-star values along
 T_erf in log age) between the CUDA path and the FP64 oracle: magnitudes and
 gradients (rows 11, 12 = Av_old, delta_old) in both precision forms, the
-equal-values limit, batch invariance and the request loop."""
+equal-values limit, batch invariance and the request loop; spectra and the
+emission-line width with its gradient."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -123,12 +126,104 @@ def test_batch_invariance_and_request_loop():
     small.close()
 
 
-def test_unsupported_calls_are_refused(agedep):
+def test_static_entry_is_refused(agedep):
     from paper_2112_06830_gb300 import dsps
     _, ctx, sid, _, _ = agedep
     p = torch.zeros((14, 4), device="cuda")
-    with pytest.raises(dsps.DSPSError):
-        ctx.spectra(p, 0, 100)
     out = torch.empty((4, 12), device="cuda")
     rc = dsps.load().dsps_photometry_fp32_static(ctx.handle, 4, p.data_ptr(), sid, out.data_ptr(), None)
     assert rc == dsps.DSPS_ERR_UNSUPPORTED
+
+
+# ---- spectra and the line width (Sec. 2.2, Eq. eqw) under age-dependent dust ----
+# Tolerances as in test_gpu_ew.py: the spectra's FP32 rounding (2e-5 relative),
+# the width's 2e-5 (2 hw + |W|) A, and gradients within 1e-3 of max(|g|,
+# 1e-2 max|g|).
+
+LC, HW, CW = synth.EW_LINE
+
+
+@functools.lru_cache(maxsize=None)
+def _ssp_line():
+    return synth.with_emission_line(_util.ssp("full"))
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def agedep_line(request):
+    from paper_2112_06830_gb300 import dsps
+    c = CASES[request.param]
+    g = _ssp_line()
+    ctx = dsps.Context(g, sfh_model=synth.SFH_DPL_QUENCH, dust_agedep=True, dust_agedep_x0=c["x0"],
+                       dust_agedep_h=c["h"], dust_law=c["law"], dust_bump=bool(c["bump"]))
+    grid = oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, t0=g.t0, t1=g.t1, n_t=g.n_t,
+                       sfh_model=synth.SFH_DPL_QUENCH, dust_agedep=1, dust_x0=c["x0"], dust_h=c["h"],
+                       dust_law=c["law"], dust_bump=c["bump"])
+    yield request.param, ctx, ctx.add_line(LC, HW, CW), grid
+    ctx.close()
+
+
+def _line_pop(n, seed, start=0):
+    p = synth.with_agedep_dust(synth.make_population(synth.SFH_DPL_QUENCH, n, seed, start), seed, start)
+    return _util.params_f32(p)
+
+
+def test_spectra_match_oracle(agedep_line):
+    case, ctx, _, grid = agedep_line
+    p32, p64 = _line_pop(150, 81)
+    n0, n1 = 1703, 2891   # ragged at both ends
+    s = ctx.spectra(torch.from_numpy(p32).cuda(), n0, n1).cpu().numpy().astype(np.float64)
+    ref = oracle.spectra(grid, p64[:, ::10])[:, n0:n1]
+    rel = np.abs(s[::10] - ref) / ref
+    print(f"age-dependent dust {case} spectra: max relative error {rel.max():.2e}")
+    assert rel.max() <= 2e-5
+
+
+def test_line_width_matches_oracle(agedep_line):
+    case, ctx, lid, grid = agedep_line
+    n = 600
+    p32, p64 = _line_pop(n, 82)
+    ew = ctx.line_ew(torch.from_numpy(p32).cuda(), lid).cpu().numpy().astype(np.float64)
+    idx = np.r_[0:8, 128:136, 590:600]
+    ref = oracle.line_ew(grid, p64[:, idx], LC, HW, CW)
+    err = np.abs(ew[idx] - ref)
+    print(f"age-dependent dust {case} EW: max |dW| = {err.max():.3e} A (W in [{ref.min():.1f}, {ref.max():.1f}])")
+    assert np.all(err <= 2e-5 * (2 * HW + np.abs(ref)))
+
+
+def test_line_width_gradient_matches_oracle(agedep_line):
+    case, ctx, lid, grid = agedep_line
+    n = 150
+    p32, p64 = _line_pop(n, 83, 400)
+    eb = np.random.default_rng(12).standard_normal(n)
+    ew, pb = ctx.line_ew_vjp(torch.from_numpy(p32).cuda(), lid, torch.from_numpy(eb.astype(np.float32)).cuda())
+    pb = pb.cpu().numpy().astype(np.float64)
+    assert pb.shape == (13, n)
+    idx = np.r_[0:10, 128:140, 140:150]
+    ref_ew, ref = oracle.line_ew_vjp(grid, p64[:, idx], eb[idx], LC, HW, CW)
+    assert np.all(np.abs(ew.cpu().numpy()[idx] - ref_ew) <= 2e-5 * (2 * HW + np.abs(ref_ew)))
+    assert np.all(pb[10] == 0.0)    # the mass cancels in W
+    rows = [r for r in range(13) if r != 10]
+    g, r = pb[rows][:, idx], ref[rows]
+    scale = np.maximum(np.abs(r), 1e-2 * np.abs(r).max(axis=0, keepdims=True))
+    rel = np.abs(g - r) / scale
+    where = np.unravel_index(np.argmax(rel), rel.shape)
+    print(f"age-dependent dust {case} EW gradient: max scaled error {rel.max():.2e} at {where}")
+    assert rel.max() <= 1e-3
+
+
+def test_line_width_chunk_invariance_and_forward_agreement():
+    from paper_2112_06830_gb300 import dsps
+    c = CASES["birthcloud"]
+    kw = dict(sfh_model=synth.SFH_DPL_QUENCH, dust_agedep=True, dust_agedep_x0=c["x0"], dust_agedep_h=c["h"])
+    big, small = dsps.Context(_ssp_line(), **kw), dsps.Context(_ssp_line(), max_chunk=256, **kw)
+    lb, ls = big.add_line(LC, HW, CW), small.add_line(LC, HW, CW)
+    p32, _ = _line_pop(500, 84)
+    p = torch.from_numpy(p32).cuda()
+    eb = torch.linspace(-1, 1, 500, device="cuda")
+    e1, g1 = big.line_ew_vjp(p, lb, eb)
+    e2, g2 = small.line_ew_vjp(p, ls, eb)
+    assert torch.equal(e1, e2) and torch.equal(g1, g2)
+    assert torch.equal(big.line_ew(p, lb), e1)
+    assert torch.equal(big.spectra(p, 100, 900), small.spectra(p, 100, 900))
+    big.close()
+    small.close()

@@ -153,3 +153,54 @@ def test_galaxy_ew_adjoint_matches_finite_differences(bump):
         np.testing.assert_allclose(pb[r], fd, rtol=2e-4, atol=1e-6 * scale.max(), err_msg=f"row {r}")
     # W is a ratio of spectra: the mass drops out
     assert np.all(np.abs(pb[10]) <= 1e-9 * np.abs(pb).max(axis=0))
+
+
+# ---- age-dependent dust (Sec. 3.4.1) ----------------------------------------
+
+
+def _agedep_pop(n, seed):
+    p = synth.with_agedep_dust(synth.make_population(synth.SFH_DPL_QUENCH, n, seed), seed)
+    p[3], p[4] = 13.8, 0.0            # still forming stars: the young bins carry the line
+    return p
+
+
+@pytest.mark.parametrize("law,bump", [(0, 0), (1, 1)])
+def test_agedep_ew_adjoint_matches_finite_differences(law, bump):
+    _, g = _grid(dust_agedep=1, dust_x0=7.2, dust_h=0.4, dust_law=law, dust_bump=bump)
+    p = _agedep_pop(3, 15)
+    eb = np.array([0.7, -1.2, 1.5])
+    ew, pb = oracle.line_ew_vjp(g, p, eb, LC, HW, CW)
+    assert pb.shape == (13, 3)
+    np.testing.assert_allclose(ew, oracle.line_ew(g, p, LC, HW, CW), rtol=1e-14)
+    rows = list(range(11)) + [12, 13]
+    scale = np.abs(pb).max()
+    for gi, r in enumerate(rows):
+        h = 1e-5 * max(1.0, abs(p[r]).max())
+        pp, pm = p.copy(), p.copy()
+        pp[r] += h
+        pm[r] -= h
+        fd = eb * (oracle.line_ew(g, pp, LC, HW, CW) - oracle.line_ew(g, pm, LC, HW, CW)) / (2 * h)
+        np.testing.assert_allclose(pb[gi], fd, rtol=2e-4, atol=1e-6 * scale, err_msg=f"param row {r}")
+
+
+def test_agedep_dust_changes_the_width_and_reduces_to_one_curve():
+    # Young stars behind more dust than old ones dim the line against the
+    # continuum; equal young and old values give the one-curve spectrum and
+    # width, and the old-star gradient rows add to the one-curve ones.
+    _, g = _grid(dust_agedep=1, dust_x0=7.2, dust_h=0.4)
+    _, g0 = _grid()
+    p = _agedep_pop(3, 16)
+    p[12], p[13] = p[8], p[9]
+    q = p[:12]
+    np.testing.assert_allclose(oracle.spectra(g, p), oracle.spectra(g0, q), rtol=1e-12)
+    eb = np.array([1.0, 2.0, -1.0])
+    ew, pb = oracle.line_ew_vjp(g, p, eb, LC, HW, CW)
+    ew0, pb0 = oracle.line_ew_vjp(g0, q, eb, LC, HW, CW)
+    np.testing.assert_allclose(ew, ew0, rtol=1e-12)
+    tol = 1e-9 * np.abs(pb0).max()
+    np.testing.assert_allclose(pb[:8], pb0[:8], rtol=1e-9, atol=tol)
+    np.testing.assert_allclose(pb[8] + pb[11], pb0[8], rtol=1e-9, atol=tol)
+    np.testing.assert_allclose(pb[9] + pb[12], pb0[9], rtol=1e-9, atol=tol)
+    dusty = p.copy()
+    dusty[8] = p[12] + 1.0            # young stars behind one more magnitude of Av
+    assert np.all(oracle.line_ew(g, dusty, LC, HW, CW) < ew)
