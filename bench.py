@@ -542,6 +542,8 @@ def run_ours(a):
     d_pbar_a = torch.empty((ctx_a.ngrad, G), dtype=torch.float32, device="cuda")
     ms_age = timed_fn(lambda: ctx_a.photometry(d_params_a, sid_a, precision=dsps.DSPS_PREC_BF16X3, out=d_mags,
                                                stream=stream))
+    ms_age_fp32 = timed_fn(lambda: ctx_a.photometry(d_params_a, sid_a, precision=dsps.DSPS_PREC_FP32, out=d_mags,
+                                                    stream=stream))
     ms_age_grad = timed_fn(lambda: dsps.dsps_photometry_vjp(ctx_a.handle, G, d_params_a.data_ptr(), sid_a,
                                                             dsps.DSPS_PREC_BF16X3, d_mbar.data_ptr(),
                                                             d_mags.data_ptr(), d_pbar_a.data_ptr(),
@@ -713,6 +715,7 @@ def run_ours(a):
                             "split-bf16; gradient with d/du_mean, d/du_sigma"},
         "agedep_dust": {"value": ws * G * N_FILT / (ms_age * 1e-3), "ms_per_step": ms_age,
                         "fwd_grad": {"value": ws * G * N_FILT / (ms_age_grad * 1e-3), "ms_per_step": ms_age_grad},
+                        "fp32": {"value": ws * G * N_FILT / (ms_age_fp32 * 1e-3), "ms_per_step": ms_age_fp32},
                         "line_ew": {"value": ws * G / (ms_age_ew * 1e-3), "unit": "galaxy-EWs/s",
                                     "ms_per_step": ms_age_ew,
                                     "fwd_grad": {"value": ws * G / (ms_age_ew_grad * 1e-3),

@@ -304,8 +304,24 @@ int make_hist_args(const dsps_hist_spec *spec, int n_filt, unsigned long long *c
 // epilogue.cuh) to ctx.d_partial as a single part.
 // sorted: rows in the order of launch_zsort (magnitudes written through
 // w.gidx), each 128-row tile contracting only the wavelength tiles of its band.
+// group: weights of one dust group's ages only (age-dependent dust), so the
+// contraction runs over the group's k range alone.
 cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, float *mags,
-                             cudaStream_t s, bool grad = false, bool sorted = false);
+                             cudaStream_t s, bool grad = false, bool sorted = false,
+                             const DustGroup *group = nullptr);
+
+// The k range [k_lo, k_hi) of the FP32 (age-major, k = (i n_z + j) n_u + u)
+// weights of a dust group's ages, widened to multiples of bk (all of
+// [0, K_pad) without a group).
+inline void group_k_range(const Ctx &c, const DustGroup *gr, int bk, int &k_lo, int &k_hi) {
+    k_lo = 0;
+    k_hi = c.K_pad;
+    if (!gr) return;
+    const int per_age = c.n_z * c.n_u;
+    k_lo = gr->i0 * per_age / bk * bk;
+    const int hi = (gr->i1 * per_age + bk - 1) / bk * bk;
+    k_hi = hi < c.K_pad ? hi : c.K_pad;
+}
 
 // Writes per-part filter sums to ctx.d_partial (sorted rows); returns the
 // number of parts through *parts.

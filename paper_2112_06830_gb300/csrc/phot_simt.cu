@@ -23,6 +23,7 @@ struct SArgs {
     const float *W;        // [n][K_pad]
     const float *L;        // [K_pad][N_pad]
     int K_pad, N_pad, Q, m_last;
+    int k_lo, k_hi;        // contracted k range (multiples of BK): a dust group's ages, or all
     int64_t n;
     const float *aux;
     const float *magoff;
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
 #pragma unroll
         for (int q = 0; q < 4 * Q4; ++q) acc[r3][q] = 0.f;
 
-    const int KT = a.K_pad / BK;
+    const int KT = (a.k_hi - a.k_lo) / BK;   // the weights vanish outside [k_lo, k_hi)
     // wavelength tiles whose interpolation rows can meet the filters' band for
     // some shift of this tile's rows (all tiles without ranges)
     int nbeg = 0, nend = a.N_pad;
@@ -103,12 +104,12 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
             }
         };
 
-        gload(0);
+        gload(a.k_lo);
         sstore(0);
         __syncthreads();
         for (int kt = 0; kt < KT; ++kt) {
             const int buf = kt & 1;
-            if (kt + 1 < KT) gload((kt + 1) * BK);
+            if (kt + 1 < KT) gload(a.k_lo + (kt + 1) * BK);
 #pragma unroll
             for (int k = 0; k < BK; ++k) {
                 float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
@@ -197,12 +198,13 @@ ColConst make_col_const(const Ctx &c) {
 }
 
 cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, float *mags,
-                             cudaStream_t s, bool grad, bool sorted) {
+                             cudaStream_t s, bool grad, bool sorted, const DustGroup *group) {
     if (n <= 0) return cudaSuccess;
     SArgs a{};
     a.W = w.w32;
     a.L = c.d_L32;
     a.K_pad = c.K_pad;
+    group_k_range(c, group, BK, a.k_lo, a.k_hi);
     a.N_pad = c.N_pad;
     a.Q = fs.Q;
     a.m_last = fs.m_rows - 1;

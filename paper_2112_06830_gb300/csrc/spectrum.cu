@@ -360,15 +360,7 @@ cudaError_t launch_spec_window(const Ctx &c, const Workspace &w, int64_t n, int 
     a.W = w.w32;
     a.L = c.d_L32;
     a.K_pad = c.K_pad;
-    // FP32 weights are age-major (k = (i n_z + j) n_u + u): a group's ages
-    // are one k range
-    a.k_lo = 0;
-    a.k_hi = c.K_pad;
-    if (gr) {
-        const int per_age = c.n_z * (c.n_u > 1 ? c.n_u : 1);
-        a.k_lo = (gr->i0 * per_age) / BK * BK;
-        a.k_hi = min((gr->i1 * per_age + BK - 1) / BK * BK, c.K_pad);
-    }
+    group_k_range(c, gr, BK, a.k_lo, a.k_hi);
     a.N_pad = c.N_pad;
     a.n = n;
     a.cs = cs;
