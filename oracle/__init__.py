@@ -28,6 +28,7 @@ _lib = None
 
 NPAR = 12
 NGRAD = 11
+SFH_TABLE = 2   # sfh_model: SFR tabulated at the n_t time nodes (the last n_t parameter rows)
 AB0 = 1.13492e-13
 
 
@@ -164,13 +165,24 @@ class Grid:
     def n_u(self):
         return len(self.lgu) if self.lgu is not None else 1
 
+    # Parameter rows: 0-11, then (nebular axis) log U mean and width, then
+    # (age-dependent dust) Av_old and delta_old, then (tabulated SFH) the SFR at
+    # the n_t time nodes; gradient rows: 0-10, then the same blocks in order.
     @property
-    def npar(self):
+    def row_sfr(self):
         return NPAR + (2 if self.n_u > 1 else 0) + (2 if self.dust_agedep else 0)
 
     @property
-    def ngrad(self):
+    def grow_sfr(self):
         return NGRAD + (2 if self.n_u > 1 else 0) + (2 if self.dust_agedep else 0)
+
+    @property
+    def npar(self):
+        return self.row_sfr + (self.n_t if self.sfh_model == SFH_TABLE else 0)
+
+    @property
+    def ngrad(self):
+        return self.grow_sfr + (self.n_t if self.sfh_model == SFH_TABLE else 0)
 
 
 class Filters:
@@ -322,9 +334,16 @@ def mags_from_weights(grid: Grid, filters: Filters, omega, Av, delta, logM, z, d
 
 # ---- batched entry points ---------------------------------------------------
 
+def _params(grid: Grid, params) -> np.ndarray:
+    p = _f64(params)
+    if p.ndim != 2 or p.shape[0] < grid.npar:
+        raise ValueError(f"params must be [{grid.npar}, G] for this grid, got {p.shape}")
+    return p
+
+
 def weights(grid: Grid, params, nthreads=None):
     """SSP weights in Msun, shape [G, n_age, n_z] (or [G, n_age, n_z, n_u])."""
-    p = _f64(params)
+    p = _params(grid, params)
     G = p.shape[1]
     out = np.zeros((G, grid.n_age, grid.n_z) + ((grid.n_u,) if grid.n_u > 1 else ()))
     _load().orc_weights(C.byref(grid._c), G, _dp(p), _dp(out), _nthreads(nthreads))
@@ -333,7 +352,7 @@ def weights(grid: Grid, params, nthreads=None):
 
 def mags(grid: Grid, filters: Filters, params, nthreads=None):
     """Observer-frame AB magnitudes, shape [G, Q]."""
-    p = _f64(params)
+    p = _params(grid, params)
     G = p.shape[1]
     out = np.zeros((G, filters.n_filt))
     _load().orc_mags(C.byref(grid._c), C.byref(filters._c), G, _dp(p), _dp(out), _nthreads(nthreads))
@@ -342,7 +361,7 @@ def mags(grid: Grid, filters: Filters, params, nthreads=None):
 
 def mags_vjp(grid: Grid, filters: Filters, params, mag_bar, nthreads=None):
     """Returns (mags [G, Q], param_bar [11, G]) with param_bar = J^T mag_bar."""
-    p = _f64(params)
+    p = _params(grid, params)
     G = p.shape[1]
     mb = _f64(mag_bar).reshape(G, filters.n_filt)
     m = np.zeros((G, filters.n_filt))
@@ -367,7 +386,7 @@ def ew_from_spectrum(lam, L, lam_c, half_width, cont_width):
 
 def spectra(grid: Grid, params, nthreads=None):
     """Rest-frame attenuated spectra 10^logM F S, shape [G, n_lam] [Lsun/Hz]."""
-    p = _f64(params)
+    p = _params(grid, params)
     G = p.shape[1]
     out = np.zeros((G, grid.n_lam))
     _load().orc_spectra(C.byref(grid._c), G, _dp(p), _dp(out), _nthreads(nthreads))
@@ -376,7 +395,7 @@ def spectra(grid: Grid, params, nthreads=None):
 
 def line_ew(grid: Grid, params, lam_c, half_width, cont_width, nthreads=None):
     """Equivalent widths [G] of the galaxies' rest-frame spectra."""
-    p = _f64(params)
+    p = _params(grid, params)
     G = p.shape[1]
     ew = np.zeros(G)
     ln = _Line(float(lam_c), float(half_width), float(cont_width))
@@ -386,7 +405,7 @@ def line_ew(grid: Grid, params, lam_c, half_width, cont_width, nthreads=None):
 
 def line_ew_vjp(grid: Grid, params, ew_bar, lam_c, half_width, cont_width, nthreads=None):
     """(ew [G], param_bar [11, G]) with param_bar[k, g] = ew_bar[g] dW_g/dp_k."""
-    p = _f64(params)
+    p = _params(grid, params)
     G = p.shape[1]
     eb = _f64(ew_bar).reshape(G)
     ew = np.zeros(G)

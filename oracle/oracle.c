@@ -45,8 +45,7 @@
 
 #define ORC_NPAR 12
 #define ORC_NGRAD 11
-#define ORC_NPAR_MAX 16              /* with the nebular axis and age-dependent dust */
-#define ORC_NGRAD_MAX 15
+#define ORC_SFH_TABLE 2              /* SFR given at the n_t time nodes */
 #define ORC_AB0 1.13492e-13          /* Sec. 2.2, Eq. (restmag): AB zero point at 10 pc, Lsun/Hz */
 #define ORC_LAMV 5500.0              /* Sec. 3.4, Eq. (salim): lambda_V in Angstrom */
 #define ORC_SIGQ 0.3                 /* width of the quench transition [Gyr] (reading) */
@@ -62,7 +61,9 @@ typedef struct {
     double t0, t1;             /* cosmic-time grid for SFR, Gyr            */
     int n_t;
     double om0, w0, h;         /* flat wCDM                                 */
-    int sfh_model;             /* 0 delayed tau, 1 double power law+quench */
+    int sfh_model;             /* 0 delayed tau, 1 double power law+quench,
+                                  2 tabulated: SFR at the n_t time nodes in the
+                                  last n_t parameter rows (rows 0-4 unused)   */
     int mdf_kernel;            /* 0 triweight, 1 Gaussian                  */
     int mdf_mean;              /* 0 linear in log age, 1 T_erf transition  */
     double mdf_x0, mdf_h;      /* transition centre [log10 yr] and width   */
@@ -76,10 +77,16 @@ typedef struct {
     double dust_x0, dust_h;    /* centre [log10 yr] and width of that transition */
 } orc_grid;
 
+/* Parameter rows: 0-11, then log U mean and width (nebular axis), then
+ * Av_old and delta_old (age-dependent dust), then the SFR table; gradient
+ * rows: 0-10, then the same optional blocks in the same order. */
 static int orc_nu(const orc_grid *g) { return g->n_u > 1 ? g->n_u : 1; }
 static int orc_row_dust_old(const orc_grid *g) { return ORC_NPAR + (g->n_u > 1 ? 2 : 0); }
-static int orc_npar(const orc_grid *g) { return orc_row_dust_old(g) + (g->dust_agedep ? 2 : 0); }
-static int orc_ngrad(const orc_grid *g) { return ORC_NGRAD + (g->n_u > 1 ? 2 : 0) + (g->dust_agedep ? 2 : 0); }
+static int orc_row_sfr(const orc_grid *g) { return orc_row_dust_old(g) + (g->dust_agedep ? 2 : 0); }
+static int orc_npar(const orc_grid *g) { return orc_row_sfr(g) + (g->sfh_model == ORC_SFH_TABLE ? g->n_t : 0); }
+static int orc_grow_dust_old(const orc_grid *g) { return ORC_NGRAD + (g->n_u > 1 ? 2 : 0); }
+static int orc_grow_sfr(const orc_grid *g) { return orc_grow_dust_old(g) + (g->dust_agedep ? 2 : 0); }
+static int orc_ngrad(const orc_grid *g) { return orc_grow_sfr(g) + (g->sfh_model == ORC_SFH_TABLE ? g->n_t : 0); }
 
 typedef struct {
     int n_filt;
@@ -225,6 +232,24 @@ double orc_sfr(int model, const double *p, double t, double *grad)
         grad[4] = ms * fq * (-log(10.0) * P);
     }
     return s;
+}
+
+/* SFR at the n_t time nodes t0 + n h (Sec. 3.1: the history the weights
+ * integrate) and, if dsfr != NULL, dSFR_n/dp[k] for k = 0..4 ([n_t][5]): the
+ * parametric models evaluated at the nodes, or the table itself (whose rows
+ * are their own parameters; dsfr then 0). */
+static void orc_sfr_nodes(const orc_grid *g, const double *par, double *sfr, double *dsfr)
+{
+    double h = (g->t1 - g->t0) / (g->n_t - 1);
+    for (int n = 0; n < g->n_t; ++n) {
+        if (g->sfh_model == ORC_SFH_TABLE) {
+            sfr[n] = par[orc_row_sfr(g) + n];
+            if (dsfr)
+                for (int k = 0; k < 5; ++k) dsfr[5 * n + k] = 0.0;
+        } else {
+            sfr[n] = orc_sfr(g->sfh_model, par, g->t0 + n * h, dsfr ? dsfr + 5 * n : NULL);
+        }
+    }
 }
 
 /* Cumulative formed mass M(tau) = int_{t0}^{tau} SFR (Eq. mstartot), with SFR
@@ -520,8 +545,7 @@ static void galaxy_weights(const orc_grid *g, const double *par, double t_obs, d
     double *frac = malloc(sizeof(double) * g->n_age);
     double *P = malloc(sizeof(double) * g->n_z);
     double *Pu = malloc(sizeof(double) * nu);
-    double h = (g->t1 - g->t0) / (g->n_t - 1);
-    for (int n = 0; n < g->n_t; ++n) sfr[n] = orc_sfr(g->sfh_model, par, g->t0 + n * h, NULL);
+    orc_sfr_nodes(g, par, sfr, NULL);
     orc_age_fracs_from_sfr(g, sfr, t_obs, frac);
     orc_pneb(g, nu > 1 ? par[12] : 0.0, nu > 1 ? par[13] : 1.0, Pu, NULL, NULL);
     for (int i = 0; i < g->n_age; ++i) {
@@ -571,10 +595,9 @@ static void orc_dust_at_age(const orc_grid *g, const double *par, int i, double 
 static void gal_forward(const orc_grid *g, const double *par, double t_obs, gal_state *st)
 {
     int N = g->n_lam, NA = g->n_age, NZ = g->n_z, NU = orc_nu(g), K = NA * NZ * NU, NT = g->n_t;
-    double h = (g->t1 - g->t0) / (NT - 1);
     st->sfr = malloc(sizeof(double) * NT);
     st->dsfr = malloc(sizeof(double) * NT * 5);
-    for (int n = 0; n < NT; ++n) st->sfr[n] = orc_sfr(g->sfh_model, par, g->t0 + n * h, st->dsfr + 5 * n);
+    orc_sfr_nodes(g, par, st->sfr, st->dsfr);
     st->e = malloc(sizeof(double) * (NA + 1));
     orc_age_edges_gyr(g, st->e);
     st->Mhi = malloc(sizeof(double) * (NA + 1));
@@ -628,7 +651,7 @@ static void gal_forward(const orc_grid *g, const double *par, double t_obs, gal_
  * (rows 8, 9 and, with age-dependent dust, the old-star rows). */
 static double *gal_reverse_dust(const orc_grid *g, const gal_state *st, const double *Lbar, double *pbar)
 {
-    int N = g->n_lam, ND = st->ND, ng = orc_ngrad(g);
+    int N = g->n_lam, ND = st->ND;
     double *Sbar = malloc(sizeof(double) * (size_t)ND * N);
     for (int d = 0; d < ND; ++d) {
         double gav = 0.0, gdl = 0.0;
@@ -643,8 +666,8 @@ static double *gal_reverse_dust(const orc_grid *g, const gal_state *st, const do
         pbar[8] += (1.0 - T) * gav;
         pbar[9] += (1.0 - T) * gdl;
         if (g->dust_agedep) {
-            pbar[ng - 2] += T * gav;
-            pbar[ng - 1] += T * gdl;
+            pbar[orc_grow_dust_old(g)] += T * gav;
+            pbar[orc_grow_dust_old(g) + 1] += T * gdl;
         }
     }
     return Sbar;
@@ -703,6 +726,8 @@ static void gal_reverse_sbar(const orc_grid *g, const gal_state *st, double t_ob
     }
     for (int n = 0; n < NT; ++n)
         for (int k = 0; k < 5; ++k) pbar[k] += sfrbar[n] * st->dsfr[5 * n + k];
+    if (g->sfh_model == ORC_SFH_TABLE)   /* the table rows are the node SFRs themselves */
+        for (int n = 0; n < NT; ++n) pbar[orc_grow_sfr(g) + n] += sfrbar[n];
     free(sfrbar); free(coef); free(Mbar); free(fracbar);
 }
 
@@ -940,7 +965,8 @@ static void *orc_worker(void *arg)
     orc_job *j = (orc_job *)arg;
     const orc_grid *g = j->g;
     int K = g->n_age * g->n_z * orc_nu(g), npar = orc_npar(g), ngrad = orc_ngrad(g);
-    double par[ORC_NPAR_MAX];
+    double *par = malloc(sizeof(double) * npar);
+    double *pb = malloc(sizeof(double) * ngrad);
     double *omega = malloc(sizeof(double) * K);
     for (long gi = j->begin; gi < j->end; ++gi) {
         for (int r = 0; r < npar; ++r) par[r] = j->params[(size_t)r * j->n_gal + gi];
@@ -962,19 +988,17 @@ static void *orc_worker(void *arg)
         } else if (j->mode == 3) {
             galaxy_spectrum(g, par, t_obs, j->out + (size_t)gi * g->n_lam);
         } else if (j->mode == 4) {
-            double pb[ORC_NGRAD_MAX];
             j->out[gi] = galaxy_ew(g, j->line, par, t_obs, j->mbar ? j->mbar[gi] : 0.0, j->pbar ? pb : NULL);
             if (j->pbar)
                 for (int k = 0; k < ngrad; ++k) j->pbar[(size_t)k * j->n_gal + gi] = pb[k];
         } else {
             double dmod = orc_dist_mod(g->om0, g->w0, g->h, z);
-            double pb[ORC_NGRAD_MAX];
             galaxy_mags_vjp(g, j->f, par, t_obs, dmod, j->mbar + (size_t)gi * j->f->n_filt,
                             j->mags ? j->mags + (size_t)gi * j->f->n_filt : NULL, pb);
             for (int k = 0; k < ngrad; ++k) j->pbar[(size_t)k * j->n_gal + gi] = pb[k];
         }
     }
-    free(omega);
+    free(omega); free(pb); free(par);
     return NULL;
 }
 

@@ -33,6 +33,7 @@ PARAM_NAMES = ("sfh0", "sfh1", "sfh2", "sfh3", "sfh4", "mdf_mu", "mdf_sigma", "m
 
 SFH_DELAYED_TAU = 0
 SFH_DPL_QUENCH = 1
+SFH_TABLE = 2          # SFR tabulated at the n_t time nodes (the last n_t parameter rows)
 MDF_TRIWEIGHT = 0
 MDF_GAUSSIAN = 1
 
@@ -200,6 +201,48 @@ def with_agedep_dust(params: np.ndarray, seed: int, start: int = 0) -> np.ndarra
                                rng.uniform(0.0, 0.8, _BLOCK), rng.uniform(-0.4, 0.3, _BLOCK)]))
     d = np.concatenate(draws, axis=1)[:, start - b0 * _BLOCK:start - b0 * _BLOCK + n]
     out[8], out[9], out[-2], out[-1] = d
+    return out
+
+
+def with_sfr_table(params: np.ndarray, n_t: int, seed: int, start: int = 0) -> np.ndarray:
+    """The same galaxies with a tabulated star formation history appended as
+    the last n_t rows (the SFR at the n_t time nodes, in arbitrary units) and
+    rows 0-4 set to 0 (unused).  The histories are random, not of any
+    parametric form, standing in for tabulated ones such as simulation
+    outputs: log SFR is a rise-and-fall curve (peak at a random node) plus a
+    Gaussian random walk of 0.08 dex per node, with two bursts of up to 10x
+    lasting one to three nodes, and a third of the galaxies drop to exactly 0
+    after a random node in the second half of the grid.  Galaxy i's draw
+    depends only on (seed, i)."""
+    p = np.asarray(params, dtype=np.float64)
+    n = p.shape[1]
+    out = np.zeros((p.shape[0] + n_t, n))
+    out[:p.shape[0]] = p
+    out[:5] = 0.0
+    if n == 0:
+        return out
+    b0, b1 = start // _BLOCK, (start + n - 1) // _BLOCK
+    x = np.arange(n_t) / (n_t - 1)
+    tabs = []
+    for b in range(b0, b1 + 1):
+        rng = np.random.default_rng([seed, b, 19])
+        xp = rng.uniform(0.1, 0.8, _BLOCK)[:, None]
+        wd = rng.uniform(0.15, 0.5, _BLOCK)[:, None]
+        lg = -((x[None, :] - xp) / wd) ** 2 * 0.5
+        lg = lg + np.cumsum(rng.normal(0.0, 0.08, (_BLOCK, n_t)), axis=1)
+        t = 10.0 ** np.clip(lg, -4.0, 2.0)
+        for _ in range(2):
+            at = rng.integers(0, n_t, _BLOCK)
+            ln = rng.integers(1, 4, _BLOCK)
+            amp = rng.uniform(1.0, 10.0, _BLOCK)
+            m = (np.arange(n_t)[None, :] >= at[:, None]) & (np.arange(n_t)[None, :] < (at + ln)[:, None])
+            t = np.where(m, t * amp[:, None], t)
+        cut = rng.integers(n_t // 2, n_t, _BLOCK)
+        quench = rng.uniform(0.0, 1.0, _BLOCK) < 1.0 / 3.0
+        t = np.where(quench[:, None] & (np.arange(n_t)[None, :] > cut[:, None]), 0.0, t)
+        tabs.append(t)
+    tab = np.concatenate(tabs, axis=0)[start - b0 * _BLOCK:start - b0 * _BLOCK + n]
+    out[p.shape[0]:] = tab.T
     return out
 
 
