@@ -564,6 +564,24 @@ def run_ours(a):
     ctx_ae.close()
     del d_params_a, d_pbar_a
 
+    # Tabulated star formation histories (Sec. 3.1): the SFR at the 200 time
+    # nodes given per galaxy (random bursty histories) instead of a model;
+    # split-bf16 forward, and forward + gradient with d/dSFR at every node.
+    ctx_s = dsps.Context(ssp, sfh_model=dsps.DSPS_SFH_TABLE, device=local)
+    sid_s = ctx_s.add_filters(synth.make_filters(N_FILT))
+    d_params_s = torch.from_numpy(synth.with_sfr_table(params_h, ssp.n_t, 1, shard_start(rank, G))
+                                  .astype(np.float32)).cuda()
+    d_pbar_s = torch.empty((ctx_s.ngrad, G), dtype=torch.float32, device="cuda")
+    ms_tab = timed_fn(lambda: ctx_s.photometry(d_params_s, sid_s, precision=dsps.DSPS_PREC_BF16X3, out=d_mags,
+                                               stream=stream))
+    ms_tab_grad = timed_fn(lambda: dsps.dsps_photometry_vjp(ctx_s.handle, G, d_params_s.data_ptr(), sid_s,
+                                                            dsps.DSPS_PREC_BF16X3, d_mbar.data_ptr(),
+                                                            d_mags.data_ptr(), d_pbar_s.data_ptr(),
+                                                            stream.cuda_stream))
+    assert torch.isfinite(d_mags).all() and torch.isfinite(d_pbar_s).all()
+    ctx_s.close()
+    del d_params_s, d_pbar_s
+
     # The paper's benchmark step (Sec. 5.1) on these galaxies: photometry through
     # six bands, a colour cut selecting the red side, and a histogram of the
     # r-band magnitude of the selection, fused (the magnitudes are not written).
@@ -723,6 +741,10 @@ def run_ours(a):
                         "note": "age-dependent dust, T_erf transition at 10 Myr over 0.1 dex: one split-bf16 "
                                 "contraction per group of age bins sharing a curve (young, each transition bin, old); "
                                 "line width: FP32 window spectrum per group over the group's ages"},
+        "sfh_table": {"value": ws * G * N_FILT / (ms_tab * 1e-3), "ms_per_step": ms_tab,
+                      "fwd_grad": {"value": ws * G * N_FILT / (ms_tab_grad * 1e-3), "ms_per_step": ms_tab_grad},
+                      "note": "tabulated star formation histories: SFR at the 200 time nodes per galaxy (random "
+                              "bursty histories), split-bf16; gradient with d/dSFR at every node (211 rows)"},
         "serve": serve,
         "clocks": clocks,
     }

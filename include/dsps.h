@@ -71,7 +71,21 @@
  * rows follow the others (rows 12, 13, or 14, 15 with a nebular axis): Av_old,
  * delta_old.  Age bin i is attenuated with Av_i = (1 - T_i) Av + T_i Av_old,
  * delta_i likewise, T_i = Terf((log10 age_i - x0) / h); the gradient gains two
- * rows at its end (Av_old, delta_old).
+ * rows after the others (Av_old, delta_old).
+ *
+ * A tabulated star formation history (dsps_opts.sfh_model = DSPS_SFH_TABLE,
+ * Sec. 3.1: the history enters only through its values on the cosmic-time
+ * grid) takes n_t more rows after all the others: the SFR at the time nodes
+ * t0 + n (t1 - t0)/(n_t - 1), in any units (piecewise linear between the
+ * nodes, like the parametric forms; logM, row 10, still sets the mass formed
+ * by t_obs).  Rows 0..4 are then unused and ignored, and their gradient rows
+ * are 0; the gradient gains n_t rows after all the others, dLoss/dSFR_n
+ * (0 for nodes after t_obs).  Node values must be finite and >= 0 up to the
+ * first node at or after t_obs, with some mass formed before t_obs.
+ *
+ * Row order, all options together: 0..11, [u_mean, u_sigma], [Av_old,
+ * delta_old], [SFR_0 .. SFR_{n_t - 1}]; gradient rows 0..10 and the same
+ * blocks in the same order.
  */
 #ifndef DSPS_H
 #define DSPS_H
@@ -98,7 +112,7 @@ enum {
     DSPS_ERR_NOT_FOUND = -7
 };
 
-enum { DSPS_SFH_DELAYED_TAU = 0, DSPS_SFH_DPL_QUENCH = 1 };
+enum { DSPS_SFH_DELAYED_TAU = 0, DSPS_SFH_DPL_QUENCH = 1, DSPS_SFH_TABLE = 2 };
 enum { DSPS_MDF_TRIWEIGHT = 0, DSPS_MDF_GAUSSIAN = 1 };
 /* Age dependence of the MDF mean (Sec. 3.2, Eq. agedep_mdf), x = log10(age/yr):
  *   DSPS_MDF_MEAN_LINEAR  mu(x) = p5 + p7 (x - 9)

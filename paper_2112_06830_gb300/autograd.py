@@ -2,8 +2,8 @@
 
 ``photometry(ctx, params, set_id, precision)`` returns AB magnitudes [G, Q] and
 is differentiable with respect to ``params`` [12, G] (rows 0..10; the redshift
-row 11 gets a zero gradient); the rows after z (nebular axis, old-star dust)
-take the gradient rows after row 10.  Forward and backward both run in libdsps: the
+row 11 gets a zero gradient); the rows after z (nebular axis, old-star dust,
+tabulated SFR) take the gradient rows after row 10.  Forward and backward both run in libdsps: the
 backward calls dsps_photometry_vjp, which recomputes the forward sums it needs
 instead of storing spectra.
 """
@@ -31,7 +31,8 @@ class DSPSPhotometry(torch.autograd.Function):
                                               precision=fctx.precision, want_mags=False)
         grad = torch.zeros_like(params)
         # gradient rows 0..10 are parameter rows 0..10; the rows after them
-        # (nebular axis, old-star dust) are the parameter rows after z (row 11)
+        # (nebular axis, old-star dust, SFR table) are the parameter rows after
+        # z (row 11)
         grad[: dsps.DSPS_NGRAD] = pbar[: dsps.DSPS_NGRAD]
         extra = pbar.shape[0] - dsps.DSPS_NGRAD
         if extra:

@@ -69,7 +69,7 @@ __global__ void group_acc_kernel(const float *partial, int parts, int nr, int64_
 struct FinalArgs {
     const float *gacc;
     int64_t n, G_stride, g_begin;
-    int Q, ngrad;
+    int Q, grow_old;          // gradient row of Av_old (delta_old next)
     const float *magoff, *offq, *aux;
     const int *gidx;          // sorted row -> chunk galaxy, or nullptr
     float *mags;              // [G][Q] of the chunk, or nullptr
@@ -115,8 +115,8 @@ __global__ void agedep_final_kernel(FinalArgs a) {
     a.param_bar[8 * a.G_stride + col] = valid ? avy : nan;
     a.param_bar[9 * a.G_stride + col] = valid ? dly : nan;
     a.param_bar[10 * a.G_stride + col] = valid ? lm : nan;
-    a.param_bar[(int64_t)(a.ngrad - 2) * a.G_stride + col] = valid ? avo : nan;
-    a.param_bar[(int64_t)(a.ngrad - 1) * a.G_stride + col] = valid ? dlo : nan;
+    a.param_bar[(int64_t)a.grow_old * a.G_stride + col] = valid ? avo : nan;
+    a.param_bar[(int64_t)(a.grow_old + 1) * a.G_stride + col] = valid ? dlo : nan;
 }
 
 // Keeps, in the merged adjoint rows, the columns of the group's ages
@@ -198,7 +198,7 @@ cudaError_t launch_final(const Ctx &c, const Workspace &w, const FilterSet &fs, 
     a.G_stride = G_stride;
     a.g_begin = g_begin;
     a.Q = fs.Q;
-    a.ngrad = c.ngrad;
+    a.grow_old = c.grow_dust_old;
     a.magoff = w.magoff;
     a.offq = fs.d_offq;
     a.aux = w.aux;

@@ -228,7 +228,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
         if (std::fabs(g->lam[n] / expect - 1.0) > 1e-9)
             return fail(DSPS_ERR_UNSUPPORTED, "dsps_create: wavelength grid is not uniform in ln(lambda)%s");
     }
-    if (opts.sfh_model < 0 || opts.sfh_model > 1 || opts.mdf_kernel < 0 || opts.mdf_kernel > 1 ||
+    if (opts.sfh_model < 0 || opts.sfh_model > 2 || opts.mdf_kernel < 0 || opts.mdf_kernel > 1 ||
         opts.mdf_mean < 0 || opts.mdf_mean > 1 || opts.dust_bump < 0 || opts.dust_bump > 1 || opts.dust_law < 0 ||
         opts.dust_law > 1)
         return fail(DSPS_ERR_INVALID_ARG, "dsps_create: unknown model switch%s");
@@ -260,10 +260,19 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     c->n_z = g->n_z;
     c->n_lam = g->n_lam;
     c->n_u = n_u;
-    c->npar = (n_u > 1 ? NPAR_MAX : NPAR) + (opts.dust_agedep ? 2 : 0);
-    c->ngrad = (n_u > 1 ? DSPS_NGRAD_NEB : NGRAD) + (opts.dust_agedep ? 2 : 0);
+    {
+        // rows: 0..11, [u_mean, u_sigma], [Av_old, delta_old], [SFR table]
+        const int p_neb = n_u > 1 ? NPAR_MAX : NPAR, g_neb = n_u > 1 ? DSPS_NGRAD_NEB : NGRAD;
+        const int p_dust = p_neb + (opts.dust_agedep ? 2 : 0), g_dust = g_neb + (opts.dust_agedep ? 2 : 0);
+        const bool table = opts.sfh_model == DSPS_SFH_TABLE;
+        c->row_dust_old = opts.dust_agedep ? p_neb : -1;
+        c->grow_dust_old = opts.dust_agedep ? g_neb : -1;
+        c->row_sfr = table ? p_dust : -1;
+        c->grow_sfr = table ? g_dust : -1;
+        c->npar = p_dust + (table ? g->n_t : 0);
+        c->ngrad = g_dust + (table ? g->n_t : 0);
+    }
     if (opts.dust_agedep) {
-        c->row_dust_old = n_u > 1 ? NPAR_MAX : NPAR;
         // groups of age bins sharing one attenuation curve (Sec. 3.4.1): runs
         // of bins with T = 0 or T = 1, every bin of the transition on its own
         for (int i = 0; i < g->n_age;) {

@@ -179,8 +179,12 @@ struct Ctx {
     int n_age = 0, n_z = 0, n_lam = 0, K = 0, K_pad = 0, N_pad = 0, n_t = 0;
     int A_pad = 0, KZ_pad = 0;              // metallicity-major K: n_age padded to 4, row length
     int n_u = 1, SEC = 0, u_ref = 0;        // nebular axis: log U values, section length, reference section
+    // Parameter rows 0..11, [u_mean, u_sigma], [Av_old, delta_old], [SFR table];
+    // gradient rows 0..10 and the same optional blocks in the same order.
     int npar = NPAR, ngrad = NGRAD;         // parameter and gradient rows
     int row_dust_old = -1;                  // age-dependent dust: parameter row of Av_old (delta_old next)
+    int grow_dust_old = -1;                 //   and its gradient row
+    int row_sfr = -1, grow_sfr = -1;        // tabulated SFH: rows of the node SFRs and of their gradient
     std::vector<DustGroup> dust_groups;     // age-dependent dust: the groups of age bins
     int kmask_words = 0;                    // ceil(SEC / KBLOCK / 32)
     double t0 = 0, t1 = 0;

@@ -159,7 +159,7 @@ struct EwArgs {
     float *ew;               // [n] or nullptr
     float *param_bar;        // [ngrad][G_stride] (GRAD)
     int pre;                 // S holds the attenuated window (age-dependent dust): no dust here
-    int ngrad;
+    int grow_old;            // gradient row of Av_old (delta_old next), age-dependent dust
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -348,8 +348,8 @@ __global__ void __launch_bounds__(256) ew_group_grad_kernel(EwArgs a, const floa
     const int64_t g = a.g_begin + r;
     a.param_bar[8 * a.G_stride + g] = rc.valid ? gs[0] : nan;
     a.param_bar[9 * a.G_stride + g] = rc.valid ? gs[2] : nan;
-    a.param_bar[(int64_t)(a.ngrad - 2) * a.G_stride + g] = rc.valid ? gs[1] : nan;
-    a.param_bar[(int64_t)(a.ngrad - 1) * a.G_stride + g] = rc.valid ? gs[3] : nan;
+    a.param_bar[(int64_t)a.grow_old * a.G_stride + g] = rc.valid ? gs[1] : nan;
+    a.param_bar[(int64_t)(a.grow_old + 1) * a.G_stride + g] = rc.valid ? gs[3] : nan;
 }
 
 cudaError_t launch_spec_window(const Ctx &c, const Workspace &w, int64_t n, int cs, int ce, bool final_out,
@@ -431,7 +431,7 @@ int run_line_ew_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *param
         a.ew_bar = grad ? ew_bar + g0 : nullptr;
         a.ew = ew ? ew + g0 : nullptr;
         a.param_bar = param_bar;
-        a.ngrad = c->ngrad;
+        a.grow_old = c->grow_dust_old;
         const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
         cudaError_t e = cudaSuccess;
         // the window spectrum of the whole population, or of one dust group

@@ -22,6 +22,7 @@
 //      the per-tile ranges and kz-block masks).
 // The kernels are instantiated with and without the nebular axis (NEB), so
 // that grids without one run the code of the two-dimensional weights.
+#include <cfloat>
 #include <climits>
 #include <cmath>
 
@@ -34,6 +35,7 @@ struct WArgs {
     int64_t G_stride, g_begin, n;
     int n_age, n_z, K, K_pad, A_pad, KZ_pad, n_t, sfh_model, mdf_kernel, n_lut, dust_bump, dust_law;
     int n_u, SEC, u_ref, npar;   // nebular axis (n_u = 1: none), section length, reference bin, parameter rows
+    int row_sfr, grow_sfr;       // tabulated SFH: parameter rows of the node SFRs and their gradient rows
     const float *uedge;          // [n_u + 1] log U bin edges (+-1e30 outer)
     int2 *urange;                // out: per-tile log U bin ranges (atomics), with trange
     int age_lo, age_hi;          // age bins whose weights are written (the others are 0): a dust group
@@ -128,18 +130,30 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // masses and their fractions of the total; returns the galaxy's validity and
 // the total formed mass through msum_out.
 template <int SFH>
-__device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, bool valid, int m_obs, float f_obs, int lane,
-                                       const SfhSmem &sm, float &msum_out) {
+__device__ __noinline__ bool sfh_stage(const WArgs &a, const float *p, int64_t g, bool valid, int m_obs, float f_obs,
+                                       int lane, const SfhSmem &sm, float &msum_out) {
     float *sfr = sm.sfr, *itg = sm.itg, *er = sm.er, *bmass = sm.bmass, *frac = sm.frac;
     float *ch = sm.cum_hi, *cl = sm.cum_lo;
     int *em = sm.em;
     valid = valid && m_obs >= 0;
 
     // 2. SFR at the time nodes (FP32) and the interval integrals I_j; nodes
-    //    after t_obs (n > m_obs + 1) bound no age bin and stay 0.
+    //    after t_obs (n > m_obs + 1) bound no age bin and stay 0.  A tabulated
+    //    history reads its nodes from its parameter rows (finite, >= 0).
     const float h = a.h_f;
-    for (int n = lane; n < a.n_t; n += 32)
-        sfr[n] = valid && n <= m_obs + 1 ? sfr_f<SFH>(p, fmaf((float)n, h, a.t0_f)) : 0.f;
+    if constexpr (SFH == DSPS_SFH_TABLE) {
+        const float *tab = a.params + (int64_t)a.row_sfr * a.G_stride + g;
+        bool bad = false;
+        for (int n = lane; n < a.n_t; n += 32) {
+            const float v = valid && n <= m_obs + 1 ? tab[(int64_t)n * a.G_stride] : 0.f;
+            bad = bad || !(v >= 0.f && v <= FLT_MAX);
+            sfr[n] = v;
+        }
+        valid = valid && !__any_sync(0xffffffffu, bad);
+    } else {
+        for (int n = lane; n < a.n_t; n += 32)
+            sfr[n] = valid && n <= m_obs + 1 ? sfr_f<SFH>(p, fmaf((float)n, h, a.t0_f)) : 0.f;
+    }
     __syncwarp();
     for (int j = lane; j < a.n_t - 1; j += 32) itg[j] = 0.5f * h * (sfr[j] + sfr[j + 1]);
     __syncwarp();
@@ -320,13 +334,14 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
     for (int r = 0; r < NP; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
 
     const float z = p[11], sig = p[6];
-    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NP);
-    valid = valid && z > 0.f && z <= a.zmax_f && sig > 0.f && p[0] > 0.f;
+    constexpr bool TAB = SFH == DSPS_SFH_TABLE;   // rows 0..4 unused
+    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NP || (TAB && lane < 5));
+    valid = valid && z > 0.f && z <= a.zmax_f && sig > 0.f && (TAB || p[0] > 0.f);
     if constexpr (NEB) valid = valid && p[13] > 0.f;
     const GalPrep gp = a.prep[gl];
 
     float msum = 0.f;
-    valid = sfh_stage<SFH>(a, p, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
+    valid = sfh_stage<SFH>(a, p, g, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
     float *frac = sm.frac;
     // log U bin probabilities, in every lane's registers
     int u_lo = 0, u_hi = 0;
@@ -634,12 +649,13 @@ __global__ void __launch_bounds__(256, NEB ? 2 : 4) weights_vjp_kernel(WArgs a, 
 #pragma unroll
     for (int r = 0; r < NP; ++r) p[r] = __shfl_sync(0xffffffffu, mine, r);
     const float z = p[11], sig = p[6];
-    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NP);
-    valid = valid && z > 0.f && z <= a.zmax_f && sig > 0.f && p[0] > 0.f;
+    constexpr bool TAB = SFH == DSPS_SFH_TABLE;   // rows 0..4 unused
+    bool valid = __all_sync(0xffffffffu, isfinite(mine) || lane >= NP || (TAB && lane < 5));
+    valid = valid && z > 0.f && z <= a.zmax_f && sig > 0.f && (TAB || p[0] > 0.f);
     if constexpr (NEB) valid = valid && p[13] > 0.f;
     const GalPrep gp = a.prep[gl];
     float msum = 0.f;
-    valid = sfh_stage<SFH>(a, p, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
+    valid = sfh_stage<SFH>(a, p, g, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
     const float *frac = sm.frac;
     for (int i = lane; i < a.n_age; i += 32) fracbar[i] = 0.f;
     for (int n = lane; n < a.n_t; n += 32) sbar[n] = 0.f;
@@ -895,13 +911,20 @@ __global__ void __launch_bounds__(256, NEB ? 2 : 4) weights_vjp_kernel(WArgs a, 
         sbar[n] += 0.5f * ((n > 0 ? cf[n - 1] : 0.f) + (n < a.n_t - 1 ? cf[n] : 0.f));
     __syncwarp();
 
-    // reverse of stage 2: the SFR parameters (nodes after t_obs have no adjoint)
+    // reverse of stage 2: the SFR parameters (nodes after t_obs have no
+    // adjoint), or for a tabulated history the node SFRs themselves
     float tb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int n = lane; n <= gp.m_obs + 1 && n < a.n_t && valid; n += 32) {
-        float gr[5];
-        sfr_grad_f<SFH>(p, fmaf((float)n, h, a.t0_f), gr);
+    if constexpr (TAB) {
+        const float nan = __int_as_float(0x7fc00000);
+        for (int n = lane; n < a.n_t; n += 32)
+            pbar[(int64_t)(a.grow_sfr + n) * a.G_stride + g] = valid ? (n <= gp.m_obs + 1 ? sbar[n] : 0.f) : nan;
+    } else {
+        for (int n = lane; n <= gp.m_obs + 1 && n < a.n_t && valid; n += 32) {
+            float gr[5];
+            sfr_grad_f<SFH>(p, fmaf((float)n, h, a.t0_f), gr);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) tb[q] = fmaf(sbar[n], gr[q], tb[q]);
+            for (int q = 0; q < 5; ++q) tb[q] = fmaf(sbar[n], gr[q], tb[q]);
+        }
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q)
@@ -936,6 +959,8 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.SEC = c.SEC;
     a.u_ref = c.u_ref;
     a.npar = c.npar;
+    a.row_sfr = c.row_sfr;
+    a.grow_sfr = c.grow_sfr;
     a.uedge = c.d_uedge;
     a.K = c.K;
     a.K_pad = c.K_pad;
@@ -987,6 +1012,9 @@ cudaError_t launch_models_n(const Ctx &c, Args... args) {
     if (sfh == DSPS_SFH_DELAYED_TAU)
         return mdf == DSPS_MDF_TRIWEIGHT ? L<DSPS_SFH_DELAYED_TAU, DSPS_MDF_TRIWEIGHT, NEB>::run(args...)
                                          : L<DSPS_SFH_DELAYED_TAU, DSPS_MDF_GAUSSIAN, NEB>::run(args...);
+    if (sfh == DSPS_SFH_TABLE)
+        return mdf == DSPS_MDF_TRIWEIGHT ? L<DSPS_SFH_TABLE, DSPS_MDF_TRIWEIGHT, NEB>::run(args...)
+                                         : L<DSPS_SFH_TABLE, DSPS_MDF_GAUSSIAN, NEB>::run(args...);
     return mdf == DSPS_MDF_TRIWEIGHT ? L<DSPS_SFH_DPL_QUENCH, DSPS_MDF_TRIWEIGHT, NEB>::run(args...)
                                      : L<DSPS_SFH_DPL_QUENCH, DSPS_MDF_GAUSSIAN, NEB>::run(args...);
 }

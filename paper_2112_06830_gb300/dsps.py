@@ -30,6 +30,7 @@ DSPS_ERR_NOT_FOUND = -7
 
 DSPS_SFH_DELAYED_TAU = 0
 DSPS_SFH_DPL_QUENCH = 1
+DSPS_SFH_TABLE = 2
 DSPS_MDF_TRIWEIGHT = 0
 DSPS_MDF_GAUSSIAN = 1
 DSPS_MDF_MEAN_LINEAR = 0
@@ -342,9 +343,14 @@ class Context:
         self.device = device
         self.n_age, self.n_z = len(la), len(lz)
         self.n_u = len(lu) if lu is not None else 1
+        # rows 0..11, [u_mean, u_sigma], [Av_old, delta_old], [SFR table];
+        # gradient rows 0..10 and the same blocks in the same order
         extra = 2 if dust_agedep else 0                                # Av_old, delta_old
-        self.npar = (DSPS_NPAR_NEB if self.n_u > 1 else DSPS_NPAR) + extra      # parameter rows
-        self.ngrad = (DSPS_NGRAD_NEB if self.n_u > 1 else DSPS_NGRAD) + extra   # gradient rows
+        self.row_sfr = (DSPS_NPAR_NEB if self.n_u > 1 else DSPS_NPAR) + extra
+        self.grow_sfr = (DSPS_NGRAD_NEB if self.n_u > 1 else DSPS_NGRAD) + extra
+        n_tab = int(ssp.n_t) if sfh_model == DSPS_SFH_TABLE else 0     # SFR at the time nodes
+        self.npar = self.row_sfr + n_tab                               # parameter rows
+        self.ngrad = self.grow_sfr + n_tab                             # gradient rows
         self.handle = dsps_create(g, o)
         self.n_filt = {}
 
@@ -421,6 +427,7 @@ class Context:
     def spectra(self, params, n0, n1, stream=None):
         """Rest-frame attenuated spectra [G, n1 - n0] on grid columns [n0, n1)."""
         import torch
+        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == self.npar
         params = params.contiguous()
         G = params.shape[1]
         out = torch.empty((G, n1 - n0), dtype=torch.float32, device=params.device)
@@ -433,6 +440,7 @@ class Context:
     def line_ew(self, params, line_id, stream=None):
         """Equivalent widths [G] [A] of a registered line."""
         import torch
+        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == self.npar
         params = params.contiguous()
         G = params.shape[1]
         ew = torch.empty(G, dtype=torch.float32, device=params.device)
@@ -442,6 +450,7 @@ class Context:
     def line_ew_vjp(self, params, line_id, ew_bar, stream=None):
         """(ew [G], param_bar [ngrad, G]) with param_bar = ew_bar dW/dparams."""
         import torch
+        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == self.npar
         params = params.contiguous()
         ew_bar = ew_bar.contiguous().to(torch.float32)
         G = params.shape[1]
@@ -456,10 +465,12 @@ class Context:
 
     # ---- request loop (host buffers) ----
     def submit(self, params, set_id, precision=DSPS_PREC_BF16X3, mag_bar=None):
-        """Queues a population held in host memory (numpy float32 [12, G], or
-        [14, G] with a nebular axis); the
-        returned Ticket keeps the host buffers alive until it is polled."""
+        """Queues a population held in host memory (numpy float32 [npar, G]:
+        12 rows, more with the optional blocks); the returned Ticket keeps the
+        host buffers alive until it is polled."""
         params = np.ascontiguousarray(params, dtype=np.float32)
+        if params.ndim != 2 or params.shape[0] != self.npar:
+            raise ValueError(f"params must be [{self.npar}, G], got {params.shape}")
         G = params.shape[1]
         Q = self.n_filt[set_id]
         t = Ticket(params, np.empty((G, Q), dtype=np.float32))
