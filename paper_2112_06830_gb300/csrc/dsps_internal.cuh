@@ -279,7 +279,9 @@ struct ProfScope {
 // ----------------------------------------------------------------------------
 // Kernel launch wrappers (defined in the .cu files)
 // ----------------------------------------------------------------------------
-enum WeightsMode { W_MSUN = 0, W_OMEGA_F32 = 1, W_OMEGA_BF16X2 = 2 };
+// W_OMEGA_BF16X2_AGE1: the split weights of one age bin (an age-dependent dust
+// group of the transition), written only in the kz blocks holding that age.
+enum WeightsMode { W_MSUN = 0, W_OMEGA_F32 = 1, W_OMEGA_BF16X2 = 2, W_OMEGA_BF16X2_AGE1 = 3 };
 
 // Bytes of a work space for `rows` galaxies (what = 1: forward only, 2: with adjoint).
 size_t workspace_bytes(const Ctx &c, int64_t rows, bool adjoint);

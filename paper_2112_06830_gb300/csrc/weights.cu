@@ -359,112 +359,156 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
     const float mass = exp10f(p[10]);
     const float s_shift = valid ? log1pf(z) / a.dlnlam_f : 0.f;   // redshift shift in grid steps
     const int nz = a.n_z;
-    if constexpr (MODE == W_OMEGA_BF16X2) {
-        // Metallicity-major kz = j * A_pad + i.  Lane g takes the ages 4g ..
-        // 4g+3 and walks the metallicity bins upwards, carrying each age's CDF
-        // at the bin's lower edge (the previous bin's upper edge): one CDF
-        // evaluation per weight, the arithmetic of the age-major loop below.
-        // The four weights of one (g, j) are consecutive in kz: one 8-byte
-        // store each of hi and lo, a warp writing one contiguous run.
-        //
-        // An invalid galaxy or a padding age gets fraction 0 and finite
-        // standardised edges, so its weights come out exactly 0.  For the
-        // triweight, a group whose four bins all lie beyond +-3 standard
-        // deviations is exactly 0 without evaluating the CDF (its carried
-        // lower-edge value is then 0 below the support, -0 above).
-        //
-        // Each lane marks, in a 128-bit register mask, the kz blocks (KBLOCK
-        // wide) where it wrote a non-zero weight; the warp's OR goes into the
-        // tile's mask (grids of more than 128 blocks keep no mask).
-        constexpr bool tri = MDF == DSPS_MDF_TRIWEIGHT;
-        const float isg = valid ? inv_sig : 0.f;
+    if constexpr (MODE == W_OMEGA_BF16X2 || MODE == W_OMEGA_BF16X2_AGE1) {
         uint4 bm = make_uint4(0u, 0u, 0u, 0u);
         __nv_bfloat16 *rh = a.whi + gi * a.KZ_pad, *rl = a.wlo + gi * a.KZ_pad;
-        for (int gq = lane; 4 * gq < a.A_pad; gq += 32) {
-            float mu4[4], fr4[4], ulo[4], slo[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int i = 4 * gq + c;
-                mu4[c] = valid ? mdf_mean_at(a, p, min(i, a.n_age - 1)) : 0.f;
-                fr4[c] = valid && i < a.n_age && i >= a.age_lo && i < a.age_hi ? frac[i] : 0.f;
-                ulo[c] = -1e30f;
-                slo[c] = 0.f;
-            }
-            for (int j = 0; j < nz; ++j) {
-                const bool last = j == nz - 1;
-                const float ze = last ? 0.f : __ldg(a.zedge + j + 1);
-                float uh[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) uh[c] = last ? 1e30f : (ze - mu4[c]) * isg;
-                const float uh_max = fmaxf(fmaxf(uh[0], uh[1]), fmaxf(uh[2], uh[3]));
-                const float ul_min = fminf(fminf(ulo[0], ulo[1]), fminf(ulo[2], ulo[3]));
-                float om[4] = {0.f, 0.f, 0.f, 0.f};
-                bool nzg = false;
-                if (tri && (uh_max <= -3.f || ul_min >= 3.f)) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        slo[c] = uh[c] > 0.f ? -0.f : 0.f;
-                        ulo[c] = uh[c];
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float s_hi = last ? 0.f : mdf_s<MDF>(uh[c]);
-                        float pj = s_hi - slo[c];
-                        if (ulo[c] <= 0.f && uh[c] > 0.f) pj += 1.f;
-                        om[c] = fr4[c] * pj;
-                        slo[c] = s_hi;
-                        ulo[c] = uh[c];
-                    }
-                    nzg = (om[0] != 0.f) | (om[1] != 0.f) | (om[2] != 0.f) | (om[3] != 0.f);
-                }
-                const int kz = j * a.A_pad + 4 * gq;
-                if (nzg) {
-                    const int b = kz / KBLOCK, wi = b >> 5;
+        if constexpr (MODE == W_OMEGA_BF16X2_AGE1) {
+            // One age bin i: lane j < n_z takes metallicity bin j (both edges'
+            // CDFs, the arithmetic of the loop below), and the warp writes, in
+            // every section, the 32-wide kz block holding (j, i) -- the weight
+            // there, zeros elsewhere.  Those are the only blocks of the row that
+            // the contraction reads: every row of the tile writes the same blocks,
+            // and the tile's K-block mask holds no other bit.
+            const int i = a.age_lo;
+            float om = 0.f;
+            if (lane < nz) {
+                const float isg = valid ? inv_sig : 0.f;
+                const float mu = valid ? mdf_mean_at(a, p, i) : 0.f;
+                const bool first = lane == 0, last = lane == nz - 1;
+                const float ul = first ? -1e30f : (__ldg(a.zedge + lane) - mu) * isg;
+                const float uh = last ? 1e30f : (__ldg(a.zedge + lane + 1) - mu) * isg;
+                const float sl = first ? 0.f : mdf_s<MDF>(ul);
+                const float sh = last ? 0.f : mdf_s<MDF>(uh);
+                float pj = sh - sl;
+                if (ul <= 0.f && uh > 0.f) pj += 1.f;
+                om = valid ? frac[i] * pj : 0.f;
+                if (om != 0.f) {
+                    const int b = (lane * a.A_pad + i) / KBLOCK, wi = b >> 5;
                     const unsigned bit = 1u << (b & 31);
                     bm.x |= wi == 0 ? bit : 0u;
                     bm.y |= wi == 1 ? bit : 0u;
                     bm.z |= wi == 2 ? bit : 0u;
                     bm.w |= wi == 3 ? bit : 0u;
                 }
-                // one section per log U bin: omega_ij P_neb(u) at kz + u SEC
-#pragma unroll
-                for (int u = 0; u < NU; ++u) {
-                    if (NEB && u >= a.n_u) break;
-                    const int kzu = kz + u * a.SEC;
-                    if (NEB && pu[u] == 0.f) {   // outside the galaxy's log U support
-                        *reinterpret_cast<uint2 *>(rh + kzu) = make_uint2(0u, 0u);
-                        *reinterpret_cast<uint2 *>(rl + kzu) = make_uint2(0u, 0u);
-                        continue;
-                    }
-                    const float4 wm = __ldg(reinterpret_cast<const float4 *>(a.wmul + kzu));
-                    float o[4];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) o[c] = NEB ? om[c] * pu[u] : om[c];
-                    const float w0 = o[0] * wm.x, w1 = o[1] * wm.y, w2 = o[2] * wm.z, w3 = o[3] * wm.w;
-                    const __nv_bfloat162 h01 = __floats2bfloat162_rn(w0, w1), h23 = __floats2bfloat162_rn(w2, w3);
-                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(w0 - __low2float(h01), w1 - __high2float(h01));
-                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(w2 - __low2float(h23), w3 - __high2float(h23));
-                    uint2 hv, lv;
-                    hv.x = *reinterpret_cast<const unsigned *>(&h01);
-                    hv.y = *reinterpret_cast<const unsigned *>(&h23);
-                    lv.x = *reinterpret_cast<const unsigned *>(&l01);
-                    lv.y = *reinterpret_cast<const unsigned *>(&l23);
-                    *reinterpret_cast<uint2 *>(rh + kzu) = hv;
-                    *reinterpret_cast<uint2 *>(rl + kzu) = lv;
+            }
+    #pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                if (NEB && u >= a.n_u) break;
+                for (int j = 0; j < nz; ++j) {
+                    const float o = __shfl_sync(0xffffffffu, om, j);
+                    const int kt = u * a.SEC + j * a.A_pad + i;                 // the weight's column
+                    const int kz = u * a.SEC + ((j * a.A_pad + i) & ~(KBLOCK - 1)) + lane;
+                    const float w = kz == kt ? (NEB ? o * pu[u] : o) * __ldg(a.wmul + kt) : 0.f;
+                    const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                    rh[kz] = h;
+                    rl[kz] = __float2bfloat16_rn(w - __bfloat162float(h));
                 }
             }
-        }
-        // padding columns [n_z * A_pad, SEC) of every section but the last,
-        // then [(n_u - 1) * SEC + n_z * A_pad, KZ_pad)
-        for (int u = 0; u + 1 < (NEB ? a.n_u : 1); ++u)
-            for (int kz = u * a.SEC + nz * a.A_pad + 4 * lane; kz < (u + 1) * a.SEC; kz += 128) {
+        } else {
+            // Metallicity-major kz = j * A_pad + i.  Lane g takes the ages 4g ..
+            // 4g+3 and walks the metallicity bins upwards, carrying each age's CDF
+            // at the bin's lower edge (the previous bin's upper edge): one CDF
+            // evaluation per weight, the arithmetic of the age-major loop below.
+            // The four weights of one (g, j) are consecutive in kz: one 8-byte
+            // store each of hi and lo, a warp writing one contiguous run.
+            //
+            // An invalid galaxy or a padding age gets fraction 0 and finite
+            // standardised edges, so its weights come out exactly 0.  For the
+            // triweight, a group whose four bins all lie beyond +-3 standard
+            // deviations is exactly 0 without evaluating the CDF (its carried
+            // lower-edge value is then 0 below the support, -0 above).
+            //
+            // Each lane marks, in a 128-bit register mask, the kz blocks (KBLOCK
+            // wide) where it wrote a non-zero weight; the warp's OR goes into the
+            // tile's mask (grids of more than 128 blocks keep no mask).
+            constexpr bool tri = MDF == DSPS_MDF_TRIWEIGHT;
+            const float isg = valid ? inv_sig : 0.f;
+            for (int gq = lane; 4 * gq < a.A_pad; gq += 32) {
+                float mu4[4], fr4[4], ulo[4], slo[4];
+    #pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int i = 4 * gq + c;
+                    mu4[c] = valid ? mdf_mean_at(a, p, min(i, a.n_age - 1)) : 0.f;
+                    fr4[c] = valid && i < a.n_age && i >= a.age_lo && i < a.age_hi ? frac[i] : 0.f;
+                    ulo[c] = -1e30f;
+                    slo[c] = 0.f;
+                }
+                for (int j = 0; j < nz; ++j) {
+                    const bool last = j == nz - 1;
+                    const float ze = last ? 0.f : __ldg(a.zedge + j + 1);
+                    float uh[4];
+    #pragma unroll
+                    for (int c = 0; c < 4; ++c) uh[c] = last ? 1e30f : (ze - mu4[c]) * isg;
+                    const float uh_max = fmaxf(fmaxf(uh[0], uh[1]), fmaxf(uh[2], uh[3]));
+                    const float ul_min = fminf(fminf(ulo[0], ulo[1]), fminf(ulo[2], ulo[3]));
+                    float om[4] = {0.f, 0.f, 0.f, 0.f};
+                    bool nzg = false;
+                    if (tri && (uh_max <= -3.f || ul_min >= 3.f)) {
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            slo[c] = uh[c] > 0.f ? -0.f : 0.f;
+                            ulo[c] = uh[c];
+                        }
+                    } else {
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float s_hi = last ? 0.f : mdf_s<MDF>(uh[c]);
+                            float pj = s_hi - slo[c];
+                            if (ulo[c] <= 0.f && uh[c] > 0.f) pj += 1.f;
+                            om[c] = fr4[c] * pj;
+                            slo[c] = s_hi;
+                            ulo[c] = uh[c];
+                        }
+                        nzg = (om[0] != 0.f) | (om[1] != 0.f) | (om[2] != 0.f) | (om[3] != 0.f);
+                    }
+                    const int kz = j * a.A_pad + 4 * gq;
+                    if (nzg) {
+                        const int b = kz / KBLOCK, wi = b >> 5;
+                        const unsigned bit = 1u << (b & 31);
+                        bm.x |= wi == 0 ? bit : 0u;
+                        bm.y |= wi == 1 ? bit : 0u;
+                        bm.z |= wi == 2 ? bit : 0u;
+                        bm.w |= wi == 3 ? bit : 0u;
+                    }
+                    // one section per log U bin: omega_ij P_neb(u) at kz + u SEC
+    #pragma unroll
+                    for (int u = 0; u < NU; ++u) {
+                        if (NEB && u >= a.n_u) break;
+                        const int kzu = kz + u * a.SEC;
+                        if (NEB && pu[u] == 0.f) {   // outside the galaxy's log U support
+                            *reinterpret_cast<uint2 *>(rh + kzu) = make_uint2(0u, 0u);
+                            *reinterpret_cast<uint2 *>(rl + kzu) = make_uint2(0u, 0u);
+                            continue;
+                        }
+                        const float4 wm = __ldg(reinterpret_cast<const float4 *>(a.wmul + kzu));
+                        float o[4];
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c) o[c] = NEB ? om[c] * pu[u] : om[c];
+                        const float w0 = o[0] * wm.x, w1 = o[1] * wm.y, w2 = o[2] * wm.z, w3 = o[3] * wm.w;
+                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(w0, w1), h23 = __floats2bfloat162_rn(w2, w3);
+                        const __nv_bfloat162 l01 = __floats2bfloat162_rn(w0 - __low2float(h01), w1 - __high2float(h01));
+                        const __nv_bfloat162 l23 = __floats2bfloat162_rn(w2 - __low2float(h23), w3 - __high2float(h23));
+                        uint2 hv, lv;
+                        hv.x = *reinterpret_cast<const unsigned *>(&h01);
+                        hv.y = *reinterpret_cast<const unsigned *>(&h23);
+                        lv.x = *reinterpret_cast<const unsigned *>(&l01);
+                        lv.y = *reinterpret_cast<const unsigned *>(&l23);
+                        *reinterpret_cast<uint2 *>(rh + kzu) = hv;
+                        *reinterpret_cast<uint2 *>(rl + kzu) = lv;
+                    }
+                }
+            }
+            // padding columns [n_z * A_pad, SEC) of every section but the last,
+            // then [(n_u - 1) * SEC + n_z * A_pad, KZ_pad)
+            for (int u = 0; u + 1 < (NEB ? a.n_u : 1); ++u)
+                for (int kz = u * a.SEC + nz * a.A_pad + 4 * lane; kz < (u + 1) * a.SEC; kz += 128) {
+                    *reinterpret_cast<uint2 *>(rh + kz) = make_uint2(0u, 0u);
+                    *reinterpret_cast<uint2 *>(rl + kz) = make_uint2(0u, 0u);
+                }
+            for (int kz = ((NEB ? a.n_u : 1) - 1) * a.SEC + nz * a.A_pad + 4 * lane; kz < a.KZ_pad; kz += 128) {
                 *reinterpret_cast<uint2 *>(rh + kz) = make_uint2(0u, 0u);
                 *reinterpret_cast<uint2 *>(rl + kz) = make_uint2(0u, 0u);
             }
-        for (int kz = ((NEB ? a.n_u : 1) - 1) * a.SEC + nz * a.A_pad + 4 * lane; kz < a.KZ_pad; kz += 128) {
-            *reinterpret_cast<uint2 *>(rh + kz) = make_uint2(0u, 0u);
-            *reinterpret_cast<uint2 *>(rl + kz) = make_uint2(0u, 0u);
         }
         bm.x = __reduce_or_sync(0xffffffffu, bm.x);
         bm.y = __reduce_or_sync(0xffffffffu, bm.y);
@@ -1086,9 +1130,15 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
     const size_t smem = weights_smem_per_warp(c.n_t, c.n_age) * warps;
     galaxy_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, w.prep);
     const unsigned grid = (unsigned)((n + warps - 1) / warps);
+    // a one-age dust group writes only its age's K blocks, which are all the
+    // contraction reads when it skips by the tiles' K-block masks
+    if (mode == W_OMEGA_BF16X2 && group && group->i1 - group->i0 == 1 && sorted && c.kmask_words <= 4 &&
+        c.opts.band_skip)
+        mode = W_OMEGA_BF16X2_AGE1;
     switch (mode) {
     case W_MSUN: return launch_models<WeightsLaunch<W_MSUN>::L>(c, a, grid, smem, s);
     case W_OMEGA_F32: return launch_models<WeightsLaunch<W_OMEGA_F32>::L>(c, a, grid, smem, s);
+    case W_OMEGA_BF16X2_AGE1: return launch_models<WeightsLaunch<W_OMEGA_BF16X2_AGE1>::L>(c, a, grid, smem, s);
     default: return launch_models<WeightsLaunch<W_OMEGA_BF16X2>::L>(c, a, grid, smem, s);
     }
 }

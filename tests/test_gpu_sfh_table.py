@@ -165,3 +165,26 @@ def test_batch_invariance_request_loop_and_autograd():
     assert torch.all(x.grad[11] == 0)
     big.close()
     small.close()
+
+
+def test_weights_and_the_static_entry(table_ctx):
+    import ctypes
+    from paper_2112_06830_gb300 import dsps
+    ctx, sid, _ = table_ctx
+    p32, p64 = _pop(300, 46)
+    d = torch.from_numpy(p32).cuda()
+    w = ctx.weights(d).cpu().numpy().astype(np.float64)
+    idx = [0, 1, 2, 150, 298, 299]
+    ref = oracle.weights(_ogrid(), p64[:, idx])
+    mass = 10.0 ** p64[10, idx]
+    err = np.abs(w[idx] - ref)
+    assert (err <= 2e-5 * np.abs(ref) + 1e-6 * mass[:, None, None]).all(), err.max()
+    # the allocation-free FP32 entry on the same table
+    lib = dsps.load()
+    out = torch.full((300, 12), float("nan"), device="cuda")
+    rc = lib.dsps_photometry_fp32_static(ctx.handle, 300, ctypes.c_void_p(d.data_ptr()), sid,
+                                         ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == dsps.DSPS_OK, lib.dsps_last_error_message()
+    want = ctx.photometry(d, sid, precision=dsps.DSPS_PREC_FP32)
+    assert (out - want).abs().max().item() <= _util.TOL_FP32
