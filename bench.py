@@ -680,12 +680,30 @@ def run_ours(a):
                 "ms_per_launch": per_launch_ms, "kblocks_per_launch": kblocks,
                 "dense_equivalent_tflops": dense_flops / (per_launch_ms * 1e-3) / 1e12}
 
+    def simt_roofline(prof):
+        launches, kms = prof[1]
+        per_launch_ms = kms / max(launches, 1)
+        steps = prof["simt_steps"] / max(launches, 1)
+        # each executed 128 x 128 x 16 tile step is 2^18 FP32 multiply-adds
+        # (one FFMA each); the FP32 peak from the unit counts: SMs x 128 FP32
+        # lanes x 2 flops per FFMA x the maximum SM clock
+        flops = steps * 128 * 128 * 16 * 2.0
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        alu_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "phot_simt_kernel (FP32 SIMT contraction + fused epilogue)",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 (FFMA) x {mhz:.0f} MHz",
+                "ms_per_launch": per_launch_ms, "steps_per_launch": steps}
+
     roof = tc_roofline(prof_tc)
     out_neb_roof = tc_roofline(prof_neb)
     roof["traffic"] = _traffic("phot_tc_kernel")
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof_dense = tc_roofline(prof_dense)
-    total_launches = sum(v[0] for k, v in prof_tc.items() if k != "tc_kblocks")
+    total_launches = sum(v[0] for v in prof_tc.values() if isinstance(v, tuple))
     value = ws * G * N_FILT / (ms_tc * 1e-3)
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
@@ -698,7 +716,8 @@ def run_ours(a):
                    "global_batch": ws * G, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single"},
         "fp32": {"value": ws * G * N_FILT / (ms_fp32 * 1e-3), "ms_per_step": ms_fp32,
-                 "kernel_ms_per_launch": prof_fp32[1][1] / max(prof_fp32[1][0], 1)},
+                 "kernel_ms_per_launch": prof_fp32[1][1] / max(prof_fp32[1][0], 1),
+                 "roofline": simt_roofline(prof_fp32)},
         "kernels": {"weights_sort_combine_ms_per_step": prof_tc[0][1] / a.steps,
                     "phot_tc_ms_per_launch": roof["ms_per_launch"]},
         "roofline": roof,

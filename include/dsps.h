@@ -389,6 +389,8 @@ typedef struct {
     int64_t launches[DSPS_PROF_KINDS];
     double ms[DSPS_PROF_KINDS];
     int64_t tc_kblocks;        /* 128 x 256 x 32 split-bf16 tensor-core block products executed */
+    int64_t simt_steps;        /* 128 x 128 x 16 FP32 multiply-add tile steps of the FP32 form's
+                                  photometry contraction executed */
 } dsps_profile_t;
 int dsps_profile_enable(dsps_ctx *ctx, int32_t enable);
 int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out);

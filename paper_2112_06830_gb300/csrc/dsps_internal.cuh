@@ -170,7 +170,7 @@ struct Workspace {
     void *shat = nullptr;                       // [cap][N_pad] x 4 bytes (adjoint only)
     float *ewacc = nullptr;                     // [cap][N_pad] summed attenuated window of the line widths
                                                 // (age-dependent dust; made on first use)
-    unsigned long long *stats = nullptr;        // tensor-core tile counter, or nullptr
+    unsigned long long *stats = nullptr;        // [2] executed-work counters (profiling), or nullptr
 };
 
 struct Ctx {
@@ -220,7 +220,7 @@ struct Ctx {
     int64_t chunk = 0;                      // galaxies per chunk (multiple of 128)
     unsigned char *d_ws_block = nullptr;    // device block holding ws (without Shat)
     Workspace ws;
-    unsigned long long *d_stats = nullptr;  // [1] tensor-core tiles executed (profiling)
+    unsigned long long *d_stats = nullptr;  // [2] tensor-core blocks, FP32 tile steps executed (profiling)
     float *d_Ld32 = nullptr;                // [KZ_pad][N_pad] differenced block (FP32 adjoint; prep.cu)
     float *d_wmul_d = nullptr;              // [KZ_pad] 2^E'_kz of the differenced rows
     __nv_bfloat16 *d_L_hi = nullptr;        // [KZ_pad][N_pad] differenced block, row-scaled hi (tensor adjoint)

@@ -35,6 +35,7 @@ struct SArgs {
     const int2 *trange;    // per 128-row tile redshift-shift range (sorted rows), or nullptr: every tile
     const int *gidx;       // sorted row -> chunk galaxy, or nullptr
     int m_nz_lo, m_nz_hi;  // filter table rows with non-zero transmission
+    unsigned long long *steps;   // BM x BN x BK tile steps executed (profiling), or nullptr
 };
 
 template <int Q4, bool GRAD>
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
             nend = min(a.N_pad, (n_hi / BN + 1) * BN);
         }
     }
+    if (a.steps && tid == 0 && nend > nbeg) atomicAdd(a.steps, (unsigned long long)((nend - nbeg) / BN) * KT);
     for (int n0 = nbeg; n0 < nend; n0 += BN) {
         float c[8][8];
 #pragma unroll
@@ -220,6 +222,7 @@ cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &
     a.gidx = sorted ? w.gidx : nullptr;
     a.m_nz_lo = fs.m_nz_lo;
     a.m_nz_hi = fs.m_nz_hi;
+    a.steps = w.stats ? w.stats + 1 : nullptr;
     if (grad) {
         switch (fs.Q4) {
         case 1: return launch_q4<1, true>(a, n, s);

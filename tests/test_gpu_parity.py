@@ -252,6 +252,18 @@ def test_block_skipping_removes_work(full):
     frac = prof["tc_kblocks"] / dense_blocks
     print(f"executed {prof['tc_kblocks']} of {dense_blocks} block products ({frac:.3f})")
     assert 0 < frac < 0.30
+    assert prof["simt_steps"] == 0
+    # the FP32 form counts its 128 x 128 x 16 tile steps: each tile's band only
+    dsps.dsps_profile_enable(ctx.handle, True)
+    ctx.photometry(x, sid, precision=0)
+    torch.cuda.synchronize()
+    prof = dsps.dsps_profile_read(ctx.handle)
+    dsps.dsps_profile_enable(ctx.handle, False)
+    k_pad = -(-g.l_ssp.shape[0] * g.l_ssp.shape[1] // 64) * 64
+    dense_steps = -(-n // 128) * (N_pad // 128) * (k_pad // 16)
+    frac32 = prof["simt_steps"] / dense_steps
+    print(f"FP32 form: {prof['simt_steps']} of {dense_steps} tile steps ({frac32:.3f})")
+    assert prof["tc_kblocks"] == 0 and 0 < frac32 < 0.6
 
 
 def test_million_galaxy_precision_forms(full):
