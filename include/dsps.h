@@ -242,10 +242,12 @@ int dsps_photometry(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t s
 
 /* Vector-Jacobian product of the magnitudes (Sec. 2.1: gradients of the SED
  * follow from dP(x_i)/dtheta; Sec. 3 per ingredient):
- *   param_bar[k][g] = sum_q mag_bar[g][q] d mags[g][q] / d params[k][g],  k = 0..10.
+ *   param_bar[k][g] = sum_q mag_bar[g][q] d mags[g][q] / d params[k][g]
+ * over the context's gradient rows (0..10, then the optional blocks above).
  * mag_bar: device float32 [n_gal][n_filt]; mags: device float32
  * [n_gal][n_filt] or NULL (forward magnitudes written as a by-product);
- * param_bar: device float32 [11][n_gal] ([13][n_gal] with a nebular axis). */
+ * param_bar: device float32 [ngrad][n_gal] (11 rows, 13 with a nebular axis,
+ * two more with age-dependent dust, n_t more with a tabulated SFH). */
 int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
                         int32_t precision, const float *mag_bar, float *mags,
                         float *param_bar, dsps_stream_t stream);
@@ -351,13 +353,13 @@ int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const float *param
  * dsps_photometry(_vjp) call on the same inputs. */
 typedef struct {
     int64_t n_gal;
-    const float *params;       /* host [12][n_gal] ([14][n_gal], nebular axis)  */
+    const float *params;       /* host [npar][n_gal] (12 rows + optional blocks) */
     int32_t set_id;
     int32_t precision;
     int32_t want_grad;         /* 0: mags only; 1: also param_bar                */
     const float *mag_bar;      /* host [n_gal][n_filt], if want_grad             */
     float *mags;               /* host [n_gal][n_filt]                           */
-    float *param_bar;          /* host [11][n_gal] ([13][n_gal]), if want_grad   */
+    float *param_bar;          /* host [ngrad][n_gal], if want_grad             */
 } dsps_request;
 
 /* Queues a request; *ticket identifies it.  The host buffers must stay valid

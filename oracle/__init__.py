@@ -8,7 +8,8 @@ each function citing the equation of Hearin et al. 2021, arXiv:2112.06830 it
 follows).  This module compiles it with gcc on first use and marshals numpy
 arrays through ctypes.  Parameters use the structure-of-arrays layout described
 in ``oracle.c``: ``params[12, G]`` (sfh0..4, mdf_mu, mdf_sigma, mdf_slope, Av,
-delta, logM, z) and gradients ``[11, G]`` (the same rows without z).
+delta, logM, z) and gradients ``[11, G]`` (the same rows without z), each with
+the grid's optional blocks after them (``Grid.npar``, ``Grid.ngrad``).
 """
 from __future__ import annotations
 
@@ -360,7 +361,7 @@ def mags(grid: Grid, filters: Filters, params, nthreads=None):
 
 
 def mags_vjp(grid: Grid, filters: Filters, params, mag_bar, nthreads=None):
-    """Returns (mags [G, Q], param_bar [11, G]) with param_bar = J^T mag_bar."""
+    """Returns (mags [G, Q], param_bar [ngrad, G]) with param_bar = J^T mag_bar."""
     p = _params(grid, params)
     G = p.shape[1]
     mb = _f64(mag_bar).reshape(G, filters.n_filt)
@@ -404,7 +405,7 @@ def line_ew(grid: Grid, params, lam_c, half_width, cont_width, nthreads=None):
 
 
 def line_ew_vjp(grid: Grid, params, ew_bar, lam_c, half_width, cont_width, nthreads=None):
-    """(ew [G], param_bar [11, G]) with param_bar[k, g] = ew_bar[g] dW_g/dp_k."""
+    """(ew [G], param_bar [ngrad, G]) with param_bar[k, g] = ew_bar[g] dW_g/dp_k."""
     p = _params(grid, params)
     G = p.shape[1]
     eb = _f64(ew_bar).reshape(G)
