@@ -162,6 +162,142 @@ __global__ void merge_rows_kernel(const float *__restrict__ src, float *__restri
     }
 }
 
+// Adjoint rows of the one-age groups (age bin i each) written straight into
+// the merged rows: for each group, section u and metallicity bin j,
+//   What[r, u SEC + j A_pad + i] = sum_n G[r, n] F_g[r, n] Ld[u SEC + j A_pad + i, n]
+// over the row tile's band, with G the dust-free Shat (FP32, one pass for all
+// one-age groups) and F_g the group's attenuation -- FP32 products in place
+// of an adjoint contraction over every K column of which a group keeps n_z.
+// Stored divided by wmul_d (a power of two) when the weights adjoint expects
+// the tensor form's scaled rows.  One block per (128-row tile, group,
+// section): the group's dust constants of each row come from its parameters
+// (Sec. 3.4.1), the band is walked in 16-column chunks with the next chunk's
+// G and Ld loaded into registers while the current one is contracted, G F_g
+// (each thread staging eight columns of one row, whose group curve it keeps
+// in registers) and the group's n_z rows of Ld staged in shared memory; thread t
+// accumulates rows t / 4 and t / 4 + 64 over the metallicity bins
+// j = (t & 3) + 4 m, m < MAXM / 2, in increasing column order.  The groups
+// (and sections) are the grid's fastest index, so a tile's blocks run
+// together and share its G in L2.
+constexpr int A1_ROWS = 128, A1_CHUNK = 16, A1_THREADS = 256, A1_LD = A1_CHUNK + 4, A1_MAXG = 64;
+
+struct Age1Set {
+    int n;                   // one-age groups (<= A1_MAXG per launch)
+    int age[A1_MAXG];        // their age bins
+    float T[A1_MAXG];        // their weights of the old-star dust values
+};
+
+struct Age1Args {
+    const float *G, *params, *Ld, *wmul_d;
+    const int *gidx;
+    const int2 *trange;
+    VjpBand band;
+    ColConst cc;
+    int64_t n, G_stride, g_begin;
+    int N_pad, KZ_pad, SEC, A_pad, n_z, n_u, row_old, dust_law, bump, scaled;
+    float *out;
+};
+
+template <int MAXM>
+__global__ void __launch_bounds__(A1_THREADS, 3) age1_adjoint_kernel(const Age1Args a, const Age1Set set) {
+    __shared__ __align__(16) float As[A1_ROWS][A1_LD];    // G F_g, [row][column]
+    __shared__ __align__(16) float Bs[2 * MAXM][A1_LD];   // Ld rows of the group's columns, [j][column]
+    constexpr int LPT = (2 * MAXM * A1_CHUNK + A1_THREADS - 1) / A1_THREADS;   // Ld values per thread
+    constexpr int SPT = A1_ROWS * A1_CHUNK / A1_THREADS;                       // G values per thread (8)
+    const int tid = threadIdx.x, mt = blockIdx.y;
+    const int gi = blockIdx.x / a.n_u, u = blockIdx.x - gi * a.n_u;
+    const int i_age = set.age[gi];
+    const float T = set.T[gi];
+    const int64_t r0 = (int64_t)mt * A1_ROWS;
+    for (int e = tid; e < 2 * MAXM * A1_LD; e += A1_THREADS) (&Bs[0][0])[e] = 0.f;   // rows j >= n_z stay 0
+    // staging role: row sq of the tile, columns sk .. sk + 7 of each chunk,
+    // with the row's group curve in registers
+    const int sq = tid >> 1, sk = (tid & 1) * SPT;
+    const int64_t sr = r0 + sq;
+    RowConst rc{0.f, 0.f, {0.f, 1.f, 0.f, 0.f}, 0, true, 0.f, 0.f};
+    if (sr < a.n) {
+        float ax[AUX_STRIDE] = {};
+        const int64_t g = a.g_begin + a.gidx[sr];
+        const float avy = a.params[8 * a.G_stride + g], dly = a.params[9 * a.G_stride + g];
+        const float avo = a.params[(int64_t)a.row_old * a.G_stride + g];
+        const float dlo = a.params[(int64_t)(a.row_old + 1) * a.G_stride + g];
+        store_dust_aux(ax, group_dust_value(T, avy, avo), group_dust_value(T, dly, dlo), a.dust_law, a.bump);
+        rc.alpha = ax[0];
+        rc.beta = ax[1];
+        rc.e = ax[6];
+    }
+    int kb0, kb1;
+    vjp_band(a.band, a.trange, mt, a.N_pad, kb0, kb1);
+    const int colz = u * a.SEC + i_age;   // column of metallicity bin 0 in this section
+    float4 gv[SPT / 4];
+    float lv[LPT];
+    auto load = [&](int c0) {
+        const float4 *src = reinterpret_cast<const float4 *>(a.G + sr * a.N_pad + c0 + sk);
+#pragma unroll
+        for (int s = 0; s < SPT / 4; ++s) gv[s] = sr < a.n ? src[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < LPT; ++t) {
+            const int e = tid + t * A1_THREADS, j = e / A1_CHUNK, k = e % A1_CHUNK;
+            lv[t] = j < a.n_z ? __ldg(a.Ld + (size_t)(colz + j * a.A_pad) * a.N_pad + c0 + k) : 0.f;
+        }
+    };
+    auto stage = [&](int c0) {
+#pragma unroll
+        for (int s = 0; s < SPT / 4; ++s) {
+            const float g4[4] = {gv[s].x, gv[s].y, gv[s].z, gv[s].w};
+            float o4[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int col = c0 + sk + 4 * s + c;
+                const float ell = fmaf((float)col, a.cc.dell, a.cc.ell0);
+                o4[c] = g4[c] * exp2f(rc.alpha * dust_curve(a.cc, rc, dust_pow(a.cc, rc, ell, col), col));
+            }
+            *reinterpret_cast<float4 *>(&As[sq][sk + 4 * s]) = make_float4(o4[0], o4[1], o4[2], o4[3]);
+        }
+#pragma unroll
+        for (int t = 0; t < LPT; ++t) {
+            const int e = tid + t * A1_THREADS, j = e / A1_CHUNK, k = e % A1_CHUNK;
+            if (j < 2 * MAXM) Bs[j][k] = lv[t];
+        }
+    };
+    constexpr int M2 = MAXM / 2;
+    const int row = tid >> 2, qt = tid & 3;   // rows row, row + 64; bins qt + 4 m
+    float acc[2][M2];
+#pragma unroll
+    for (int m = 0; m < M2; ++m) acc[0][m] = acc[1][m] = 0.f;
+    const int cbeg = kb0 * 32, cend = kb1 * 32;   // the band in columns (vjp_band counts 32-column blocks)
+    if (cbeg < cend) load(cbeg);
+    for (int c0 = cbeg; c0 < cend; c0 += A1_CHUNK) {
+        __syncthreads();   // the previous chunk's reads are done
+        stage(c0);
+        __syncthreads();
+        if (c0 + A1_CHUNK < cend) load(c0 + A1_CHUNK);
+#pragma unroll
+        for (int k = 0; k < A1_CHUNK; k += 4) {
+            const float4 x0 = *reinterpret_cast<const float4 *>(&As[row][k]);
+            const float4 x1 = *reinterpret_cast<const float4 *>(&As[row + 64][k]);
+#pragma unroll
+            for (int m = 0; m < M2; ++m) {
+                const float4 y = *reinterpret_cast<const float4 *>(&Bs[qt + 4 * m][k]);
+                acc[0][m] = fmaf(x0.w, y.w, fmaf(x0.z, y.z, fmaf(x0.y, y.y, fmaf(x0.x, y.x, acc[0][m]))));
+                acc[1][m] = fmaf(x1.w, y.w, fmaf(x1.z, y.z, fmaf(x1.y, y.y, fmaf(x1.x, y.x, acc[1][m]))));
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t r = r0 + row + 64 * h;
+        if (r >= a.n) break;
+#pragma unroll
+        for (int m = 0; m < M2; ++m) {
+            const int j = qt + 4 * m;
+            if (j >= a.n_z) break;
+            const int kz = colz + j * a.A_pad;
+            a.out[r * a.KZ_pad + kz] = a.scaled ? acc[h][m] / __ldg(a.wmul_d + kz) : acc[h][m];
+        }
+    }
+}
+
 // The group's dust constants in aux, for the chunk's sorted rows: the
 // adjoint passes need the group's curve but not its weights.
 __global__ void group_aux_kernel(const float *params, int64_t G_stride, int64_t g_begin, const int *gidx, int64_t n,
@@ -210,6 +346,61 @@ cudaError_t launch_final(const Ctx &c, const Workspace &w, const FilterSet &fs, 
     a.param_bar = param_bar;
     agedep_final_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+// One-age groups take the direct adjoint when the accumulators fit (n_z <= 32).
+bool age1_direct(const Ctx &c, const DustGroup &gr) { return gr.i1 - gr.i0 == 1 && c.n_z <= 32; }
+
+// The direct adjoint of every one-age group (A1_MAXG per launch), from the
+// dust-free Shat in w.shat into w.what2.
+cudaError_t launch_age1_adjoint(const Ctx &c, const Workspace &w, const FilterSet &fs, const float *params,
+                                int64_t G_stride, int64_t g_begin, int64_t n, bool scaled, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if ((n + A1_ROWS - 1) / A1_ROWS > 65535) return cudaErrorInvalidValue;   // row tiles are the grid's y
+    Age1Args a{};
+    a.G = reinterpret_cast<const float *>(w.shat);
+    a.params = params;
+    a.Ld = c.d_Ld32;
+    a.wmul_d = c.d_wmul_d;
+    a.gidx = w.gidx;
+    a.trange = w.trange;
+    a.band = make_vjp_band(c, fs, c.opts.band_skip != 0);
+    a.cc = make_col_const(c);
+    a.n = n;
+    a.G_stride = G_stride;
+    a.g_begin = g_begin;
+    a.N_pad = c.N_pad;
+    a.KZ_pad = c.KZ_pad;
+    a.SEC = c.SEC;
+    a.A_pad = c.A_pad;
+    a.n_z = c.n_z;
+    a.n_u = c.n_u;
+    a.row_old = c.row_dust_old;
+    a.dust_law = c.opts.dust_law;
+    a.bump = c.opts.dust_bump;
+    a.scaled = scaled ? 1 : 0;
+    a.out = w.what2;
+    const int mm = (c.n_z + 1) / 2;
+    Age1Set set{};
+    size_t k = 0;
+    while (true) {
+        set.n = 0;
+        for (; k < c.dust_groups.size() && set.n < A1_MAXG; ++k)
+            if (age1_direct(c, c.dust_groups[k])) {
+                set.age[set.n] = c.dust_groups[k].i0;
+                set.T[set.n] = c.dust_groups[k].T;
+                ++set.n;
+            }
+        if (set.n == 0) break;
+        const dim3 grid((unsigned)(set.n * c.n_u), (unsigned)((n + A1_ROWS - 1) / A1_ROWS));
+        if (mm <= 4) age1_adjoint_kernel<4><<<grid, A1_THREADS, 0, s>>>(a, set);
+        else if (mm <= 8) age1_adjoint_kernel<8><<<grid, A1_THREADS, 0, s>>>(a, set);
+        else if (mm <= 12) age1_adjoint_kernel<12><<<grid, A1_THREADS, 0, s>>>(a, set);
+        else age1_adjoint_kernel<16><<<grid, A1_THREADS, 0, s>>>(a, set);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_group_aux(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride,
@@ -305,16 +496,30 @@ int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, con
             e = launch_final(*c, w, fs, n, true, mags ? mags + g0 * fs.Q : nullptr, nullptr, mag_bar + g0 * fs.Q,
                              param_bar, n_gal, g0, s);
         }
-        // adjoint of the weights: one adjoint contraction per group, with the
-        // group's curve in aux (the tile ranges depend on z alone and stay),
-        // merged rows
+        // adjoint of the weights, merged over the groups (the group's curve in
+        // aux; the tile ranges depend on z alone and stay): padding columns
+        // zeroed once; the one-age groups from one dust-free Shat, their n_z
+        // columns each; the other groups by an adjoint contraction each,
+        // keeping their ages' columns
+        bool any1 = false;
+        for (const DustGroup &gr : c->dust_groups) any1 = any1 || age1_direct(*c, gr);
+        if (e == cudaSuccess) {
+            ProfScope ps(*c, 3, s, prof);
+            e = launch_merge_rows(*c, w, n, DustGroup{0, 0, 0.f}, true, s);
+            if (any1 && e == cudaSuccess) e = launch_shat(*c, w, fs, n, false, c->opts.band_skip != 0, s, false);
+        }
+        if (any1 && e == cudaSuccess) {
+            ProfScope ps(*c, 3, s, prof);
+            e = launch_age1_adjoint(*c, w, fs, params, n_gal, g0, n, tc, s);
+        }
         for (size_t k = 0; k < c->dust_groups.size() && e == cudaSuccess; ++k) {
             const DustGroup &gr = c->dust_groups[k];
+            if (age1_direct(*c, gr)) continue;
             ProfScope ps(*c, 3, s, prof);
             e = launch_group_aux(*c, w, params, n_gal, g0, n, gr, s);
             if (e == cudaSuccess) e = launch_shat(*c, w, fs, n, tc, c->opts.band_skip != 0, s);
             if (e == cudaSuccess) e = tc ? launch_vjp_tc(*c, w, fs, n, s) : launch_vjp_simt(*c, w, n, s, 0, -1, &fs);
-            if (e == cudaSuccess) e = launch_merge_rows(*c, w, n, gr, k == 0, s);
+            if (e == cudaSuccess) e = launch_merge_rows(*c, w, n, gr, false, s);
         }
         if (e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);

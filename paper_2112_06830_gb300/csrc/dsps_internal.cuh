@@ -340,8 +340,10 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp);
 cudaError_t launch_combine_grad(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts,
                                 bool sorted, const float *mag_bar, float *mags, float *param_bar, int64_t G_stride,
                                 int64_t g_begin, cudaStream_t s);
+// dust = false: FP32 Shat without the dust factor (age-dependent dust's
+// one-age groups apply their own curves).
 cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, bool bf16, bool band,
-                        cudaStream_t s);
+                        cudaStream_t s, bool dust = true);
 // col0/col1: the Shat columns that take part (multiples of 16; 0, N_pad for all);
 // fs: with sorted rows and band skipping, each 128-row tile's band only.
 cudaError_t launch_vjp_simt(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s, int col0 = 0,

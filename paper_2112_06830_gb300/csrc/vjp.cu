@@ -55,8 +55,9 @@ __global__ void combine_grad_kernel(const float *partial, int parts, int64_t n, 
     param_bar[10 * G_stride + g_begin + g] = valid ? lm_bar : nan;
 }
 
-// One warp per (sorted) row: Shat over the row's band columns [32 kb0, 32 kb1).
-template <int Q4, bool BF16>
+// One warp per (sorted) row: Shat over the row's band columns [32 kb0, 32 kb1)
+// (without DUST the factor F is left out: the part all dust curves share).
+template <int Q4, bool BF16, bool DUST = true>
 __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 *trange, const float *cq,
                                                    const float4 *tab, int m_last, ColConst cc, int64_t n, int N_pad,
                                                    VjpBand band, float *out32,
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 
     };
     auto shat_at = [&](int col, const float (&cm)[4]) {
         const float ell = fmaf((float)col, cc.dell, cc.ell0);
-        const float F = exp2f(rc.alpha * dust_curve(cc, rc, dust_pow(cc, rc, ell, col), col));
+        const float F = DUST ? exp2f(rc.alpha * dust_curve(cc, rc, dust_pow(cc, rc, ell, col), col)) : 1.f;
         return col_kappa(cc, col) * F * fmaf(rc.w[0], cm[0], fmaf(rc.w[1], cm[1], fmaf(rc.w[2], cm[2], rc.w[3] * cm[3])));
     };
     auto store = [&](int col, float sh) {
@@ -240,7 +241,7 @@ cudaError_t launch_combine_grad(const Ctx &c, const Workspace &w, const FilterSe
 }
 
 cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, bool bf16, bool band,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool dust) {
     if (n <= 0) return cudaSuccess;
     const VjpBand b = make_vjp_band(c, fs, band);
     const ColConst cc = make_col_const(c);
@@ -251,7 +252,10 @@ cudaError_t launch_shat(const Ctx &c, const Workspace &w, const FilterSet &fs, i
     __nv_bfloat16 *olo = ohi + (size_t)w.cap * c.N_pad;
     const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
 #define DSPS_SHAT(Q4)                                                                                              \
-    if (bf16)                                                                                                      \
+    if (!dust)                                                                                                     \
+        shat_kernel<Q4, false, false><<<blocks, 256, 0, s>>>(w.aux, w.trange, w.cq, tab, m_last, cc, n, c.N_pad, b,\
+                                                             o32, ohi, olo);                                       \
+    else if (bf16)                                                                                                 \
         shat_kernel<Q4, true><<<blocks, 256, 0, s>>>(w.aux, w.trange, w.cq, tab, m_last, cc, n, c.N_pad, b, o32,   \
                                                      ohi, olo);                                                    \
     else                                                                                                           \
