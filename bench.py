@@ -693,7 +693,7 @@ def run_ours(a):
         alu_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak, "traffic": _traffic("phot_simt_kernel"),
                 "kernel": "phot_simt_kernel (FP32 SIMT contraction + fused epilogue)",
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 (FFMA) x {mhz:.0f} MHz",
                 "ms_per_launch": per_launch_ms, "steps_per_launch": steps}
