@@ -195,6 +195,7 @@ struct Age1Args {
     ColConst cc;
     int64_t n, G_stride, g_begin;
     int N_pad, KZ_pad, SEC, A_pad, n_z, n_u, row_old, dust_law, bump, scaled;
+    int col0, col1;          // contracted columns, or (col1 <= col0) each row tile's band
     float *out;
 };
 
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(A1_THREADS, 3) age1_adjoint_kernel(const Age1A
     RowConst rc{0.f, 0.f, {0.f, 1.f, 0.f, 0.f}, 0, true, 0.f, 0.f};
     if (sr < a.n) {
         float ax[AUX_STRIDE] = {};
-        const int64_t g = a.g_begin + a.gidx[sr];
+        const int64_t g = a.g_begin + (a.gidx ? a.gidx[sr] : sr);
         const float avy = a.params[8 * a.G_stride + g], dly = a.params[9 * a.G_stride + g];
         const float avo = a.params[(int64_t)a.row_old * a.G_stride + g];
         const float dlo = a.params[(int64_t)(a.row_old + 1) * a.G_stride + g];
@@ -229,6 +230,8 @@ __global__ void __launch_bounds__(A1_THREADS, 3) age1_adjoint_kernel(const Age1A
     int kb0, kb1;
     vjp_band(a.band, a.trange, mt, a.N_pad, kb0, kb1);
     const int colz = u * a.SEC + i_age;   // column of metallicity bin 0 in this section
+    // the band in columns (vjp_band counts 32-column blocks), or the given range
+    const int cbeg = a.col1 > a.col0 ? a.col0 : kb0 * 32, cend = a.col1 > a.col0 ? a.col1 : kb1 * 32;
     float4 gv[SPT / 4];
     float lv[LPT];
     auto load = [&](int c0) {
@@ -265,7 +268,6 @@ __global__ void __launch_bounds__(A1_THREADS, 3) age1_adjoint_kernel(const Age1A
     float acc[2][M2];
 #pragma unroll
     for (int m = 0; m < M2; ++m) acc[0][m] = acc[1][m] = 0.f;
-    const int cbeg = kb0 * 32, cend = kb1 * 32;   // the band in columns (vjp_band counts 32-column blocks)
     if (cbeg < cend) load(cbeg);
     for (int c0 = cbeg; c0 < cend; c0 += A1_CHUNK) {
         __syncthreads();   // the previous chunk's reads are done
@@ -348,61 +350,6 @@ cudaError_t launch_final(const Ctx &c, const Workspace &w, const FilterSet &fs, 
     return cudaGetLastError();
 }
 
-// One-age groups take the direct adjoint when the accumulators fit (n_z <= 32).
-bool age1_direct(const Ctx &c, const DustGroup &gr) { return gr.i1 - gr.i0 == 1 && c.n_z <= 32; }
-
-// The direct adjoint of every one-age group (A1_MAXG per launch), from the
-// dust-free Shat in w.shat into w.what2.
-cudaError_t launch_age1_adjoint(const Ctx &c, const Workspace &w, const FilterSet &fs, const float *params,
-                                int64_t G_stride, int64_t g_begin, int64_t n, bool scaled, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    if ((n + A1_ROWS - 1) / A1_ROWS > 65535) return cudaErrorInvalidValue;   // row tiles are the grid's y
-    Age1Args a{};
-    a.G = reinterpret_cast<const float *>(w.shat);
-    a.params = params;
-    a.Ld = c.d_Ld32;
-    a.wmul_d = c.d_wmul_d;
-    a.gidx = w.gidx;
-    a.trange = w.trange;
-    a.band = make_vjp_band(c, fs, c.opts.band_skip != 0);
-    a.cc = make_col_const(c);
-    a.n = n;
-    a.G_stride = G_stride;
-    a.g_begin = g_begin;
-    a.N_pad = c.N_pad;
-    a.KZ_pad = c.KZ_pad;
-    a.SEC = c.SEC;
-    a.A_pad = c.A_pad;
-    a.n_z = c.n_z;
-    a.n_u = c.n_u;
-    a.row_old = c.row_dust_old;
-    a.dust_law = c.opts.dust_law;
-    a.bump = c.opts.dust_bump;
-    a.scaled = scaled ? 1 : 0;
-    a.out = w.what2;
-    const int mm = (c.n_z + 1) / 2;
-    Age1Set set{};
-    size_t k = 0;
-    while (true) {
-        set.n = 0;
-        for (; k < c.dust_groups.size() && set.n < A1_MAXG; ++k)
-            if (age1_direct(c, c.dust_groups[k])) {
-                set.age[set.n] = c.dust_groups[k].i0;
-                set.T[set.n] = c.dust_groups[k].T;
-                ++set.n;
-            }
-        if (set.n == 0) break;
-        const dim3 grid((unsigned)(set.n * c.n_u), (unsigned)((n + A1_ROWS - 1) / A1_ROWS));
-        if (mm <= 4) age1_adjoint_kernel<4><<<grid, A1_THREADS, 0, s>>>(a, set);
-        else if (mm <= 8) age1_adjoint_kernel<8><<<grid, A1_THREADS, 0, s>>>(a, set);
-        else if (mm <= 12) age1_adjoint_kernel<12><<<grid, A1_THREADS, 0, s>>>(a, set);
-        else age1_adjoint_kernel<16><<<grid, A1_THREADS, 0, s>>>(a, set);
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 cudaError_t launch_group_aux(const Ctx &c, const Workspace &w, const float *params, int64_t G_stride,
                              int64_t g_begin, int64_t n, const DustGroup &gr, cudaStream_t s) {
     group_aux_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(params, G_stride, g_begin, w.gidx, n,
@@ -450,6 +397,61 @@ cudaError_t groups_forward(Ctx *c, const Workspace &w, int64_t n_gal, int64_t g0
 }
 
 }  // namespace
+
+bool age1_direct(const Ctx &c, const DustGroup &gr) { return gr.i1 - gr.i0 == 1 && c.n_z <= 32; }
+
+cudaError_t launch_age1_adjoint(const Ctx &c, const Workspace &w, const FilterSet *fs, const float *params,
+                                int64_t G_stride, int64_t g_begin, int64_t n, bool scaled, cudaStream_t s,
+                                const float *G, int col0, int col1, const DustGroup *only) {
+    if (n <= 0) return cudaSuccess;
+    if ((n + A1_ROWS - 1) / A1_ROWS > 65535) return cudaErrorInvalidValue;   // row tiles are the grid's y
+    Age1Args a{};
+    a.G = G ? G : reinterpret_cast<const float *>(w.shat);
+    a.params = params;
+    a.Ld = c.d_Ld32;
+    a.wmul_d = c.d_wmul_d;
+    a.gidx = G ? nullptr : w.gidx;
+    a.trange = w.trange;
+    a.band = fs ? make_vjp_band(c, *fs, c.opts.band_skip != 0) : VjpBand{0, 0, -1, 0};
+    a.col0 = col0;
+    a.col1 = col1;
+    a.cc = make_col_const(c);
+    a.n = n;
+    a.G_stride = G_stride;
+    a.g_begin = g_begin;
+    a.N_pad = c.N_pad;
+    a.KZ_pad = c.KZ_pad;
+    a.SEC = c.SEC;
+    a.A_pad = c.A_pad;
+    a.n_z = c.n_z;
+    a.n_u = c.n_u;
+    a.row_old = c.row_dust_old;
+    a.dust_law = c.opts.dust_law;
+    a.bump = c.opts.dust_bump;
+    a.scaled = scaled ? 1 : 0;
+    a.out = w.what2;
+    const int mm = (c.n_z + 1) / 2;
+    Age1Set set{};
+    size_t k = 0;
+    while (true) {
+        set.n = 0;
+        for (; k < c.dust_groups.size() && set.n < A1_MAXG; ++k)
+            if (age1_direct(c, c.dust_groups[k]) && (!only || &c.dust_groups[k] == only)) {
+                set.age[set.n] = c.dust_groups[k].i0;
+                set.T[set.n] = c.dust_groups[k].T;
+                ++set.n;
+            }
+        if (set.n == 0) break;
+        const dim3 grid((unsigned)(set.n * c.n_u), (unsigned)((n + A1_ROWS - 1) / A1_ROWS));
+        if (mm <= 4) age1_adjoint_kernel<4><<<grid, A1_THREADS, 0, s>>>(a, set);
+        else if (mm <= 8) age1_adjoint_kernel<8><<<grid, A1_THREADS, 0, s>>>(a, set);
+        else if (mm <= 12) age1_adjoint_kernel<12><<<grid, A1_THREADS, 0, s>>>(a, set);
+        else age1_adjoint_kernel<16><<<grid, A1_THREADS, 0, s>>>(a, set);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_merge_rows(const Ctx &c, const Workspace &w, int64_t n, const DustGroup &gr, bool first,
                          cudaStream_t s) {
@@ -510,7 +512,7 @@ int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, con
         }
         if (any1 && e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);
-            e = launch_age1_adjoint(*c, w, fs, params, n_gal, g0, n, tc, s);
+            e = launch_age1_adjoint(*c, w, &fs, params, n_gal, g0, n, tc, s);
         }
         for (size_t k = 0; k < c->dust_groups.size() && e == cudaSuccess; ++k) {
             const DustGroup &gr = c->dust_groups[k];

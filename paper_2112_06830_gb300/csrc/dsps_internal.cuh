@@ -361,8 +361,21 @@ int run_photometry_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *pa
 // yet (dispatch.cu).
 int ensure_shat(Ctx *c, bool ewacc = false);
 
-// Age-dependent dust (agedep.cu): keeps, in w.what2, the adjoint rows of w.w32
-// at the columns of the group's ages (the first group also zeroes padding).
+// Age-dependent dust (agedep.cu).  A one-age group whose n_z adjoint columns
+// are formed directly (n_z <= 32) instead of by an adjoint contraction:
+bool age1_direct(const Ctx &c, const DustGroup &gr);
+// those columns, in w.what2, for every such group (or only *only): the FP32
+// dot products of G (w.shat, the dust-free Shat, when G is null) times the
+// group's attenuation with the group's rows of the differenced block, over
+// each row tile's band of fs (sorted rows) or over columns [col0, col1)
+// (multiples of 16; rows in chunk order when G is given); divided by wmul_d
+// when scaled.
+cudaError_t launch_age1_adjoint(const Ctx &c, const Workspace &w, const FilterSet *fs, const float *params,
+                                int64_t G_stride, int64_t g_begin, int64_t n, bool scaled, cudaStream_t s,
+                                const float *G = nullptr, int col0 = 0, int col1 = 0,
+                                const DustGroup *only = nullptr);
+// Keeps, in w.what2, the adjoint rows of w.w32 at the columns of the group's
+// ages (first: also zeroes the padding columns).
 cudaError_t launch_merge_rows(const Ctx &c, const Workspace &w, int64_t n, const DustGroup &gr, bool first,
                               cudaStream_t s);
 // Spectra and line widths (spectrum.cu); w.shat must be allocated.

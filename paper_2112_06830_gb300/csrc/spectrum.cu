@@ -269,6 +269,9 @@ __global__ void __launch_bounds__(256) ew_kernel(EwArgs a) {
             db = fmaf(lb * L, du - duc, db);
         }
         if (a.pre) {
+            // the direct adjoint of a one-age group reads lb over [cs, ce)
+            for (int col = a.cs + lane; col < a.ce; col += 32)
+                if (col < a.c0 || col >= a.c0 + a.n_pts) srow[col] = 0.f;
             if (lane == 0) a.param_bar[10 * a.G_stride + a.g_begin + r] = rc.valid ? 0.f : nan;
             return;
         }
@@ -465,6 +468,10 @@ int run_line_ew_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *param
             p.S = w.ewacc;
             p.pre = 1;
             if (e == cudaSuccess) e = width(p);
+            // the merged adjoint rows: padding columns zeroed once; a one-age
+            // group's n_z columns formed directly from lb and its curve, the
+            // other groups' by the adjoint contraction over the window
+            if (grad && e == cudaSuccess) e = launch_merge_rows(*c, w, n, DustGroup{0, 0, 0.f}, true, s);
             for (size_t k = 0; grad && k < G && e == cudaSuccess; ++k) {
                 const DustGroup &gr = c->dust_groups[k];
                 e = window(&gr);
@@ -472,8 +479,14 @@ int run_line_ew_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *param
                     ew_group_grad_kernel<<<blocks, 256, 0, s>>>(a, w.ewacc, w.gacc, gr.T, k == 0, k + 1 == G);
                     e = cudaGetLastError();
                 }
-                if (e == cudaSuccess) e = launch_vjp_simt(*c, w, n, s, ls.cs, ls.ce);
-                if (e == cudaSuccess) e = launch_merge_rows(*c, w, n, gr, k == 0, s);
+                if (age1_direct(*c, gr)) {
+                    if (e == cudaSuccess)
+                        e = launch_age1_adjoint(*c, w, nullptr, params, n_gal, g0, n, false, s, w.ewacc, ls.cs, ls.ce,
+                                                &gr);
+                } else {
+                    if (e == cudaSuccess) e = launch_vjp_simt(*c, w, n, s, ls.cs, ls.ce);
+                    if (e == cudaSuccess) e = launch_merge_rows(*c, w, n, gr, false, s);
+                }
             }
             if (grad && e == cudaSuccess) {
                 Workspace wm = w;
