@@ -59,7 +59,7 @@ class _Grid(C.Structure):
 
 class _Filters(C.Structure):
     _fields_ = [("n_filt", C.c_int), ("n_pts", C.POINTER(C.c_int)),
-                ("lam", C.POINTER(C.c_double)), ("trans", C.POINTER(C.c_double))]
+                ("lam", C.POINTER(C.c_double)), ("trans", C.POINTER(C.c_double)), ("rest", C.c_int)]
 
 
 class _Line(C.Structure):
@@ -187,15 +187,18 @@ class Grid:
 
 
 class Filters:
-    """A list of (lambda [A], transmission) tables."""
+    """A list of (lambda [A], transmission) tables; rest=True gives rest-frame
+    absolute magnitudes M_Q (Eq. restmag) instead of observer-frame apparent
+    ones."""
 
-    def __init__(self, tables):
+    def __init__(self, tables, rest=False):
         self.tables = [(_f64(l), _f64(t)) for l, t in tables]
+        self.rest = bool(rest)
         self.n_pts = np.array([len(l) for l, _ in self.tables], dtype=np.int32)
         self.lam = _f64(np.concatenate([l for l, _ in self.tables]))
         self.trans = _f64(np.concatenate([t for _, t in self.tables]))
         self._c = _Filters(len(self.tables), self.n_pts.ctypes.data_as(C.POINTER(C.c_int)),
-                           _dp(self.lam), _dp(self.trans))
+                           _dp(self.lam), _dp(self.trans), 1 if rest else 0)
 
     @property
     def n_filt(self):

@@ -93,7 +93,19 @@ typedef struct {
     const int *n_pts;          /* [n_filt]                                  */
     const double *lam;         /* concatenated tables, Angstrom, increasing */
     const double *trans;       /* concatenated transmissions                */
+    int rest;                  /* 1: rest-frame absolute magnitudes M_Q (Eq.
+                                  restmag: the filters at the rest wavelength,
+                                  no distance modulus or (1+z) term); 0: the
+                                  observer-frame apparent magnitudes m_Q      */
 } orc_filters;
+
+/* The redshift the filters see (0 in the rest frame) and the magnitude term
+ * Dmod(z) - 2.5 log10(1+z) of the observer frame (Sec. 2.2). */
+static double orc_filter_z(const orc_filters *f, double z) { return f->rest ? 0.0 : z; }
+static double orc_frame_offset(const orc_filters *f, double z, double dmod)
+{
+    return f->rest ? 0.0 : dmod - 2.5 * log10(1.0 + z);
+}
 
 /* ------------------------------------------------------------------ */
 /* Appendix B: triweight kernel and its cumulative integral            */
@@ -503,7 +515,8 @@ static void filter_offsets(const orc_filters *f, int *off)
  * galaxy given its per-unit-mass SSP weights omega[i][j] (sum = 1):
  *   S_n   = sum_ij omega_ij L_ijn                         (Eq. full_mdf)
  *   N_q   = sum_n c_n/lam_n T_q((1+z) lam_n) F_n S_n      (rest-grid trapezoid)
- *   m_q   = -2.5 log10(10^logM N_q / (AB0 D_q)) + Dmod(z) - 2.5 log10(1+z). */
+ *   m_q   = -2.5 log10(10^logM N_q / (AB0 D_q)) + Dmod(z) - 2.5 log10(1+z)
+ * (rest frame: T_q(lam_n) and M_q = -2.5 log10(10^logM N_q / (AB0 D_q))). */
 void orc_mags_from_weights(const orc_grid *g, const orc_filters *f, const double *omega,
                            double Av, double delta, double logM, double z, double dmod,
                            double *mags)
@@ -523,13 +536,13 @@ void orc_mags_from_weights(const orc_grid *g, const orc_filters *f, const double
         int np = f->n_pts[q];
         double Nq = 0.0;
         for (int n = 0; n < N; ++n) {
-            double T = orc_filter_trans(fl, ft, np, (1.0 + z) * g->lam[n]);
+            double T = orc_filter_trans(fl, ft, np, (1.0 + orc_filter_z(f, z)) * g->lam[n]);
             if (T == 0.0) continue;
             double F = pow(10.0, -0.4 * Av * orc_dust_curve(g, g->lam[n], delta, NULL));
             Nq += trap_w(g->lam, N, n) / g->lam[n] * T * F * S[n];
         }
         double Dq = orc_filter_norm(fl, ft, np);
-        mags[q] = -2.5 * log10(pow(10.0, logM) * Nq / (ORC_AB0 * Dq)) + dmod - 2.5 * log10(1.0 + z);
+        mags[q] = -2.5 * log10(pow(10.0, logM) * Nq / (ORC_AB0 * Dq)) + orc_frame_offset(f, z, dmod);
     }
     free(off);
     free(S);
@@ -746,12 +759,12 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
         const double *fl = f->lam + off[q], *ft = f->trans + off[q];
         double acc = 0.0;
         for (int n = 0; n < N; ++n) {
-            T[(size_t)q * N + n] = orc_filter_trans(fl, ft, f->n_pts[q], (1.0 + z) * g->lam[n]);
+            T[(size_t)q * N + n] = orc_filter_trans(fl, ft, f->n_pts[q], (1.0 + orc_filter_z(f, z)) * g->lam[n]);
             acc += trap_w(g->lam, N, n) / g->lam[n] * T[(size_t)q * N + n] * st.L[n];
         }
         Nq[q] = acc;
         double Dq = orc_filter_norm(fl, ft, f->n_pts[q]);
-        if (mags) mags[q] = -2.5 * log10(pow(10.0, logM) * acc / (ORC_AB0 * Dq)) + dmod - 2.5 * log10(1.0 + z);
+        if (mags) mags[q] = -2.5 * log10(pow(10.0, logM) * acc / (ORC_AB0 * Dq)) + orc_frame_offset(f, z, dmod);
     }
 
     /* reverse sweep */
@@ -789,11 +802,11 @@ static void galaxy_mags_agedep(const orc_grid *g, const orc_filters *f, const do
         const double *fl = f->lam + off[q], *ft = f->trans + off[q];
         double acc = 0.0;
         for (int n = 0; n < N; ++n) {
-            double T = orc_filter_trans(fl, ft, f->n_pts[q], (1.0 + z) * g->lam[n]);
+            double T = orc_filter_trans(fl, ft, f->n_pts[q], (1.0 + orc_filter_z(f, z)) * g->lam[n]);
             acc += trap_w(g->lam, N, n) / g->lam[n] * T * st.L[n];
         }
         double Dq = orc_filter_norm(fl, ft, f->n_pts[q]);
-        mags[q] = -2.5 * log10(pow(10.0, logM) * acc / (ORC_AB0 * Dq)) + dmod - 2.5 * log10(1.0 + z);
+        mags[q] = -2.5 * log10(pow(10.0, logM) * acc / (ORC_AB0 * Dq)) + orc_frame_offset(f, z, dmod);
     }
     free(off);
     gal_free(&st);
