@@ -223,6 +223,21 @@ int dsps_destroy(dsps_ctx *ctx);
  * *set_id receives a small non-negative id. */
 int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts,
                      const double *const *lam, const double *const *trans, int32_t *set_id);
+
+/* The same with the frame of the set's magnitudes.  DSPS_FRAME_OBSERVER (what
+ * dsps_filters_add registers): observer-frame apparent magnitudes
+ *   m_Q = M'_Q + Dmod(z) - 2.5 log10(1+z),
+ * M'_Q Eq. restmag with the filter at (1+z) lambda (Sec. 2.2).
+ * DSPS_FRAME_REST: the rest-frame absolute magnitude M_Q of Eq. restmag, the
+ * filter at the rest wavelength and no distance terms; z still sets the age
+ * of the universe at which the galaxy is seen (t_obs), and so its SED.  Every
+ * call taking a set id (photometry, gradient, histogram, request loop, the
+ * allocation-free entry) follows the set's frame.  INVALID_ARG for another
+ * frame value. */
+enum { DSPS_FRAME_OBSERVER = 0, DSPS_FRAME_REST = 1 };
+int dsps_filters_add_frame(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts,
+                           const double *const *lam, const double *const *trans, int32_t frame,
+                           int32_t *set_id);
 int dsps_filters_count(dsps_ctx *ctx, int32_t set_id, int32_t *n_filt);
 
 /* SSP weights in Msun, w_out[g][i][j] = 10^logM * P_SFH(age_i) * P_met(Z_j | age_i)

@@ -467,6 +467,7 @@ cudaError_t launch_merge_rows(const Ctx &c, const Workspace &w, int64_t n, const
 int run_photometry_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *params, const FilterSet &fs,
                              int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist) {
     Workspace w = w0;
+    w.rest = fs.rest;
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;
     const bool tc = precision == DSPS_PREC_BF16X3;
@@ -487,6 +488,7 @@ int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, con
                                  const FilterSet &fs, int32_t precision, const float *mag_bar, float *mags,
                                  float *param_bar, cudaStream_t s, bool profile) {
     Workspace w = w0;
+    w.rest = fs.rest;
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;
     const bool tc = precision == DSPS_PREC_BF16X3;

@@ -450,8 +450,15 @@ int dsps_destroy(dsps_ctx *ctx) {
 
 int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const double *const *lam,
                      const double *const *trans, int32_t *set_id) {
+    return dsps_filters_add_frame(ctx, n_filt, n_pts, lam, trans, DSPS_FRAME_OBSERVER, set_id);
+}
+
+int dsps_filters_add_frame(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const double *const *lam,
+                           const double *const *trans, int32_t frame, int32_t *set_id) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !n_pts || !lam || !trans || !set_id) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: null argument%s");
+    if (frame != DSPS_FRAME_OBSERVER && frame != DSPS_FRAME_REST)
+        return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: unknown frame%s");
     if (n_filt < 1 || n_filt > DSPS_MAX_FILTERS) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: 1..16 filters%s");
     double lmax = 0.0;
     std::vector<float> offq(n_filt);
@@ -472,6 +479,7 @@ int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const 
     FilterSet fs;
     fs.Q = n_filt;
     fs.Q4 = (n_filt + 3) / 4;
+    fs.rest = frame == DSPS_FRAME_REST ? 1 : 0;
     const double l0 = std::exp(c->lnlam0);
     // Grid samples m = -1 .. M-1 at l0 exp(m dlnlam) in table rows t = m + 1,
     // then three zero rows (the 4-point interpolation reads up to m + 2).

@@ -62,6 +62,7 @@ int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *p
                       int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist) {
     if (c->opts.dust_agedep) return run_photometry_agedep_ws(c, w0, n_gal, params, fs, precision, mags, s, profile, hist);
     Workspace w = w0;
+    w.rest = fs.rest;
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;
     for (int64_t g0 = 0; g0 < n_gal; g0 += w.cap) {
@@ -110,6 +111,7 @@ int run_photometry_vjp_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const floa
     if (c->opts.dust_agedep)
         return run_photometry_vjp_agedep_ws(c, w0, n_gal, params, fs, precision, mag_bar, mags, param_bar, s, profile);
     Workspace w = w0;
+    w.rest = fs.rest;
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;
     const bool tc = precision == DSPS_PREC_BF16X3;

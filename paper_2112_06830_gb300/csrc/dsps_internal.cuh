@@ -106,6 +106,7 @@ struct FilterSet {
     int m_nz_lo = 0, m_nz_hi = -1;  // first / last table row where some filter is non-zero
     float *d_tab = nullptr;    // [m_rows][4*Q4] T_q(lam0 exp(m dlnlam))
     float *d_offq = nullptr;   // [Q] 2.5 log10(AB0 D_q)
+    int rest = 0;              // 1: rest-frame absolute magnitudes (Eq. restmag: no shift, no distance terms)
 };
 
 // A registered emission line (spectrum.cu): the window of grid columns
@@ -171,6 +172,7 @@ struct Workspace {
     float *ewacc = nullptr;                     // [cap][N_pad] summed attenuated window of the line widths
                                                 // (age-dependent dust; made on first use)
     unsigned long long *stats = nullptr;        // [2] executed-work counters (profiling), or nullptr
+    int rest = 0;                               // this call's filter set is rest-frame (FilterSet::rest)
 };
 
 struct Ctx {

@@ -112,6 +112,7 @@ extern "C" int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const f
     ws.prep = reinterpret_cast<GalPrep *>(base + off_mo + align256((size_t)cap * 8));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const FilterSet &fs = c->sets[set_id];
+    ws.rest = fs.rest;
     e = launch_weights(*c, ws, W_OMEGA_F32, params, n_gal, 0, n_gal, nullptr, s);
     if (e == cudaSuccess) e = launch_phot_simt(*c, ws, fs, n_gal, mags, s);
     if (e != cudaSuccess) {

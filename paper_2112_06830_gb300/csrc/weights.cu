@@ -36,6 +36,7 @@ struct WArgs {
     int n_age, n_z, K, K_pad, A_pad, KZ_pad, n_t, sfh_model, mdf_kernel, n_lut, dust_bump, dust_law;
     int n_u, SEC, u_ref, npar;   // nebular axis (n_u = 1: none), section length, reference bin, parameter rows
     int row_sfr, grow_sfr;       // tabulated SFH: parameter rows of the node SFRs and their gradient rows
+    int rest;                    // rest-frame magnitudes: no redshift shift, no distance terms
     const float *uedge;          // [n_u + 1] log U bin edges (+-1e30 outer)
     int2 *urange;                // out: per-tile log U bin ranges (atomics), with trange
     int age_lo, age_hi;          // age bins whose weights are written (the others are 0): a dust group
@@ -275,7 +276,8 @@ __global__ void galaxy_prep_kernel(WArgs a, GalPrep *out) {
         const float frf = (float)fr;
         const float gz = fmaf(frf, a.glut[i + 1] - a.glut[i], a.glut[i]);
         const float lm = a.params[10 * a.G_stride + g];
-        r.magoff = fmaf(-2.5f, lm, gz) + (5.f * log10f(z) - 2.5f * log10f(1.f + z));
+        // Sec. 2.2: m_q = M'_q + Dmod(z) - 2.5 log10(1+z); rest frame: M_q alone
+        r.magoff = a.rest ? -2.5f * lm : fmaf(-2.5f, lm, gz) + (5.f * log10f(z) - 2.5f * log10f(1.f + z));
     }
     out[gl] = r;
 }
@@ -357,7 +359,8 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
     // 5-6. metallicity weights and output.
     const float inv_sig = 1.f / sig;
     const float mass = exp10f(p[10]);
-    const float s_shift = valid ? log1pf(z) / a.dlnlam_f : 0.f;   // redshift shift in grid steps
+    // redshift shift in grid steps (none for rest-frame filters)
+    const float s_shift = valid && !a.rest ? log1pf(z) / a.dlnlam_f : 0.f;
     const int nz = a.n_z;
     if constexpr (MODE == W_OMEGA_BF16X2 || MODE == W_OMEGA_BF16X2_AGE1) {
         uint4 bm = make_uint4(0u, 0u, 0u, 0u);
@@ -1005,6 +1008,7 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.npar = c.npar;
     a.row_sfr = c.row_sfr;
     a.grow_sfr = c.grow_sfr;
+    a.rest = w.rest;
     a.uedge = c.d_uedge;
     a.K = c.K;
     a.K_pad = c.K_pad;

@@ -31,6 +31,8 @@ DSPS_ERR_NOT_FOUND = -7
 DSPS_SFH_DELAYED_TAU = 0
 DSPS_SFH_DPL_QUENCH = 1
 DSPS_SFH_TABLE = 2
+DSPS_FRAME_OBSERVER = 0
+DSPS_FRAME_REST = 1
 DSPS_MDF_TRIWEIGHT = 0
 DSPS_MDF_GAUSSIAN = 1
 DSPS_MDF_MEAN_LINEAR = 0
@@ -105,6 +107,9 @@ _SIGS = [
     ("dsps_filters_add", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
                                    C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.POINTER(C.c_double)),
                                    C.POINTER(C.c_int32)]),
+    ("dsps_filters_add_frame", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
+                                         C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.POINTER(C.c_double)),
+                                         C.c_int32, C.POINTER(C.c_int32)]),
     ("dsps_filters_count", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     ("dsps_weights", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("dsps_photometry", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
@@ -186,7 +191,9 @@ def dsps_destroy(ctx):
     return _check(load().dsps_destroy(ctx), "dsps_destroy")
 
 
-def dsps_filters_add(ctx, tables):
+def dsps_filters_add(ctx, tables, frame=None):
+    """Registers a filter set; frame DSPS_FRAME_REST gives rest-frame absolute
+    magnitudes (Eq. restmag), the default observer-frame apparent ones."""
     n = len(tables)
     lam = [np.ascontiguousarray(l, dtype=np.float64) for l, _ in tables]
     tr = [np.ascontiguousarray(t, dtype=np.float64) for _, t in tables]
@@ -194,7 +201,10 @@ def dsps_filters_add(ctx, tables):
     lp = (C.POINTER(C.c_double) * n)(*[x.ctypes.data_as(C.POINTER(C.c_double)) for x in lam])
     tp = (C.POINTER(C.c_double) * n)(*[x.ctypes.data_as(C.POINTER(C.c_double)) for x in tr])
     sid = C.c_int32()
-    _check(load().dsps_filters_add(ctx, n, n_pts, lp, tp, C.byref(sid)), "dsps_filters_add")
+    if frame is None:
+        _check(load().dsps_filters_add(ctx, n, n_pts, lp, tp, C.byref(sid)), "dsps_filters_add")
+    else:
+        _check(load().dsps_filters_add_frame(ctx, n, n_pts, lp, tp, int(frame), C.byref(sid)), "dsps_filters_add")
     return sid.value
 
 
@@ -367,8 +377,9 @@ class Context:
         except Exception:  # noqa: BLE001
             pass
 
-    def add_filters(self, tables) -> int:
-        sid = dsps_filters_add(self.handle, tables)
+    def add_filters(self, tables, rest_frame=False) -> int:
+        """A filter set; rest_frame=True for rest-frame absolute magnitudes."""
+        sid = dsps_filters_add(self.handle, tables, DSPS_FRAME_REST if rest_frame else None)
         self.n_filt[sid] = len(tables)
         return sid
 
