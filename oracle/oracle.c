@@ -771,8 +771,10 @@ static void galaxy_mags_vjp(const orc_grid *g, const orc_filters *f, const doubl
     for (int k = 0; k < orc_ngrad(g); ++k) pbar[k] = 0.0;
     double *Nbar = malloc(sizeof(double) * Q);
     for (int q = 0; q < Q; ++q) {
-        pbar[10] += -2.5 * mbar[q];
-        Nbar[q] = mbar[q] * (-2.5 / log(10.0)) / Nq[q];
+        /* a band without flux (its filter off the SSP grid at this redshift)
+         * has m = +inf and no gradient term */
+        if (Nq[q] > 0.0) pbar[10] += -2.5 * mbar[q];
+        Nbar[q] = Nq[q] > 0.0 ? mbar[q] * (-2.5 / log(10.0)) / Nq[q] : 0.0;
     }
     double *Lbar = calloc(N, sizeof(double));
     for (int n = 0; n < N; ++n) {

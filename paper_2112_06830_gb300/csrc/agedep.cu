@@ -102,13 +102,13 @@ __global__ void agedep_final_kernel(FinalArgs a) {
     float avy = 0.f, avo = 0.f, dly = 0.f, dlo = 0.f, lm = 0.f;
     for (int q = 0; q < a.Q; ++q) {
         const float mb = a.mag_bar[g * a.Q + q];
-        const float nb = valid ? mb * k10 / ga[q] : 0.f;
+        const float nb = valid && ga[q] > 0.f ? mb * k10 / ga[q] : 0.f;   // no flux: no gradient term
         a.cq[r * QS + q] = nb;
         avy = fmaf(nb * kd, ga[QS + q], avy);
         avo = fmaf(nb * kd, ga[2 * QS + q], avo);
         dly = fmaf(nb * kd, ga[3 * QS + q], dly);
         dlo = fmaf(nb * kd, ga[4 * QS + q], dlo);
-        lm = fmaf(-2.5f, mb, lm);
+        if (ga[q] > 0.f) lm = fmaf(-2.5f, mb, lm);
     }
     const float nan = __int_as_float(0x7fc00000);
     const int64_t col = a.g_begin + g;

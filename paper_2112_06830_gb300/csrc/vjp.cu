@@ -42,10 +42,11 @@ __global__ void combine_grad_kernel(const float *partial, int parts, int64_t n, 
             D += src[2 * qs + q];
         }
         const float mb = mag_bar[g * Q + q];
-        const float nb = valid ? mb * k10 / N : 0.f;
+        // a band without flux (filter off the SSP grid at this z): m = +inf, no gradient term
+        const float nb = valid && N > 0.f ? mb * k10 / N : 0.f;
         av_bar = fmaf(nb * kd, A, av_bar);
         d_bar = fmaf(nb * kd * Av, D, d_bar);
-        lm_bar = fmaf(-2.5f, mb, lm_bar);
+        if (N > 0.f) lm_bar = fmaf(-2.5f, mb, lm_bar);
         cq[r * QSTRIDE_MAX + q] = nb;
         if (mags) mags[g * Q + q] = ab_mag(N, mo, offq[q]);
     }
