@@ -11,7 +11,7 @@
 // (tc::UnitRing), so that units of unequal cost balance across SMs; each tile sweeps the
 // 256-wide wavelength tiles inside its redshifted filter band, and contracts
 // only the K blocks (metallicity-major K) where some row's weights are non-zero
-// (tile_ranges, next_kb).  Warp roles:
+// (tile_ranges, KbIter).  Warp roles:
 //   warp 0      TMA producer: 4-stage ring of {W_hi, W_lo, L_hi, L_lo} K-slices
 //               (32 bf16 = 64 B rows, 64-byte swizzle), one mbarrier per stage.
 //   warp 1      TMEM allocator and single-thread MMA issuer: per K-slice six
