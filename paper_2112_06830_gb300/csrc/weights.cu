@@ -25,6 +25,7 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <type_traits>
 
 #include "dsps_internal.cuh"
 
@@ -436,8 +437,10 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                     ulo[c] = -1e30f;
                     slo[c] = 0.f;
                 }
-                for (int j = 0; j < nz; ++j) {
-                    const bool last = j == nz - 1;
+                // metallicity bin j; LAST: the top bin, whose upper edge is +inf
+                // (peeled off so that the other bins carry no selects for it)
+                auto bin = [&](int j, auto last_c) {
+                    constexpr bool last = decltype(last_c)::value;
                     const float ze = last ? 0.f : __ldg(a.zedge + j + 1);
                     float uh[4];
     #pragma unroll
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                     for (int u = 0; u < NU; ++u) {
                         if (NEB && u >= a.n_u) break;
                         const int kzu = kz + u * a.SEC;
-                        if (NEB && pu[u] == 0.f) {   // outside the galaxy's log U support
+                        if (!nzg || (NEB && pu[u] == 0.f)) {   // all four zero, or outside the log U support
                             *reinterpret_cast<uint2 *>(rh + kzu) = make_uint2(0u, 0u);
                             *reinterpret_cast<uint2 *>(rl + kzu) = make_uint2(0u, 0u);
                             continue;
@@ -499,7 +502,9 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                         *reinterpret_cast<uint2 *>(rh + kzu) = hv;
                         *reinterpret_cast<uint2 *>(rl + kzu) = lv;
                     }
-                }
+                };
+                for (int j = 0; j + 1 < nz; ++j) bin(j, std::false_type{});
+                bin(nz - 1, std::true_type{});
             }
             // padding columns [n_z * A_pad, SEC) of every section but the last,
             // then [(n_u - 1) * SEC + n_z * A_pad, KZ_pad)
