@@ -32,12 +32,12 @@ namespace {
 constexpr int QS = QSTRIDE_MAX;
 
 // Tile ranges and masks back to empty before the next group's weights (the
-// chunk's sort is kept).
-__global__ void tile_reset_kernel(int2 *trange, int2 *urange, int n_u, unsigned *kmask, int kmw, int n_tiles) {
+// chunk's sort is kept; the log U ranges depend on the log U parameters alone
+// and stay -- with the nebular axis they are preset by the sort).
+__global__ void tile_reset_kernel(int2 *trange, unsigned *kmask, int kmw, int n_tiles) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tiles) return;
     trange[i] = make_int2(TRANGE_EMPTY_LO, TRANGE_EMPTY_HI);
-    urange[i] = make_int2(n_u, -1);
     for (int w = 0; w < kmw; ++w) kmask[(size_t)i * kmw + w] = 0u;
 }
 
@@ -315,8 +315,7 @@ __global__ void group_aux_kernel(const float *params, int64_t G_stride, int64_t 
 
 cudaError_t launch_tile_reset(const Ctx &c, const Workspace &w, int64_t n, cudaStream_t s) {
     const int n_tiles = (int)((n + 127) / 128);
-    tile_reset_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(w.trange, w.urange, c.n_u, w.kmask, c.kmask_words,
-                                                            n_tiles);
+    tile_reset_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(w.trange, w.kmask, c.kmask_words, n_tiles);
     return cudaGetLastError();
 }
 

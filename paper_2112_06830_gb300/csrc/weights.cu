@@ -38,6 +38,7 @@ struct WArgs {
     int n_u, SEC, u_ref, npar;   // nebular axis (n_u = 1: none), section length, reference bin, parameter rows
     int row_sfr, grow_sfr;       // tabulated SFH: parameter rows of the node SFRs and their gradient rows
     int rest;                    // rest-frame magnitudes: no redshift shift, no distance terms
+    int urange_pre;              // tiles' log U ranges preset by the sort: write only those sections
     const float *uedge;          // [n_u + 1] log U bin edges (+-1e30 outer)
     int2 *urange;                // out: per-tile log U bin ranges (atomics), with trange
     int age_lo, age_hi;          // age bins whose weights are written (the others are 0): a dust group
@@ -427,6 +428,9 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
             // tile's mask (grids of more than 128 blocks keep no mask).
             constexpr bool tri = MDF == DSPS_MDF_TRIWEIGHT;
             const float isg = valid ? inv_sig : 0.f;
+            // with the nebular axis and preset tile ranges, only the sections
+            // the tile's contraction reads are written (the others stay unread)
+            const int2 ur = NEB && a.urange_pre ? a.urange[gi >> 7] : make_int2(0, NEB ? a.n_u - 1 : 0);
             for (int gq = lane; 4 * gq < a.A_pad; gq += 32) {
                 float mu4[4], fr4[4], ulo[4], slo[4];
     #pragma unroll
@@ -481,6 +485,7 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                     for (int u = 0; u < NU; ++u) {
                         if (NEB && u >= a.n_u) break;
                         const int kzu = kz + u * a.SEC;
+                        if (NEB && (u < ur.x || u > ur.y)) continue;   // a section the tile does not read
                         if (!nzg || (NEB && pu[u] == 0.f)) {   // all four zero, or outside the log U support
                             *reinterpret_cast<uint2 *>(rh + kzu) = make_uint2(0u, 0u);
                             *reinterpret_cast<uint2 *>(rl + kzu) = make_uint2(0u, 0u);
@@ -506,17 +511,18 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                 for (int j = 0; j + 1 < nz; ++j) bin(j, std::false_type{});
                 bin(nz - 1, std::true_type{});
             }
-            // padding columns [n_z * A_pad, SEC) of every section but the last,
-            // then [(n_u - 1) * SEC + n_z * A_pad, KZ_pad)
-            for (int u = 0; u + 1 < (NEB ? a.n_u : 1); ++u)
+            // padding columns [n_z * A_pad, SEC) of every written section but
+            // the last, then [(n_u - 1) * SEC + n_z * A_pad, KZ_pad)
+            for (int u = ur.x; u + 1 < (NEB ? a.n_u : 1) && u <= ur.y; ++u)
                 for (int kz = u * a.SEC + nz * a.A_pad + 4 * lane; kz < (u + 1) * a.SEC; kz += 128) {
                     *reinterpret_cast<uint2 *>(rh + kz) = make_uint2(0u, 0u);
                     *reinterpret_cast<uint2 *>(rl + kz) = make_uint2(0u, 0u);
                 }
-            for (int kz = ((NEB ? a.n_u : 1) - 1) * a.SEC + nz * a.A_pad + 4 * lane; kz < a.KZ_pad; kz += 128) {
-                *reinterpret_cast<uint2 *>(rh + kz) = make_uint2(0u, 0u);
-                *reinterpret_cast<uint2 *>(rl + kz) = make_uint2(0u, 0u);
-            }
+            if (ur.y >= (NEB ? a.n_u : 1) - 1)
+                for (int kz = ((NEB ? a.n_u : 1) - 1) * a.SEC + nz * a.A_pad + 4 * lane; kz < a.KZ_pad; kz += 128) {
+                    *reinterpret_cast<uint2 *>(rh + kz) = make_uint2(0u, 0u);
+                    *reinterpret_cast<uint2 *>(rl + kz) = make_uint2(0u, 0u);
+                }
         }
         bm.x = __reduce_or_sync(0xffffffffu, bm.x);
         bm.y = __reduce_or_sync(0xffffffffu, bm.y);
@@ -1139,6 +1145,7 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
     const size_t smem = weights_smem_per_warp(c.n_t, c.n_age) * warps;
     galaxy_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, w.prep);
     const unsigned grid = (unsigned)((n + warps - 1) / warps);
+    a.urange_pre = mode == W_OMEGA_BF16X2 && sorted && c.n_u > 1 && c.opts.band_skip ? 1 : 0;
     // a one-age dust group writes only its age's K blocks, which are all the
     // contraction reads when it skips by the tiles' K-block masks
     if (mode == W_OMEGA_BF16X2 && group && group->i1 - group->i0 == 1 && sorted && c.kmask_words <= 4 &&

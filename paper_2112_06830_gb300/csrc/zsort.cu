@@ -32,6 +32,10 @@ struct SortKey {
     float mua, mub;                // MDF mean at the middle log age
     const float *um;               // parameter row 12 (nebular axis), or nullptr
     float u_lo, u_scale;           // u bin = floor((u_mean - u_lo) * u_scale), 8 bins
+    const float *us;               // parameter row 13 (u_sigma), with um
+    const float *uedge;            // [n_u + 1] log U bin edges (+-1e30 outer)
+    int n_u;
+    int2 *urange;                  // tiles' log U section ranges to preset, or nullptr
 };
 
 __device__ __forceinline__ int sort_key(const SortKey &k, int64_t i) {
@@ -104,12 +108,42 @@ __global__ void __launch_bounds__(128) zsort_tile_kernel(SortKey k, int64_t n, i
     const int64_t r0 = (int64_t)blockIdx.x * 128;
     const int t = threadIdx.x;
     const int rows = (int)min((int64_t)128, n - r0);
+    __shared__ int ulo, uhi;
+    if (t == 0) {
+        ulo = k.n_u;
+        uhi = -1;
+    }
+    __syncthreads();
     if (t < rows) {
         idx[t] = perm[r0 + t];
         const float z = k.z[idx[t]];
         key[t] = z > 0.f && isfinite(z) ? z : 0.f;
+        if (k.urange) {
+            // the log U bins a row can weight (Sec. 3.3, Eq. nebsed: the
+            // triweight CDF differences vanish for a bin wholly beyond +-3
+            // widths), widened by 1e-3 width against rounding: a superset of
+            // the bins the weights kernel finds non-zero
+            const float um = k.um[idx[t]], us = k.us[idx[t]];
+            if (us > 0.f && isfinite(um) && isfinite(us)) {
+                const float isu = 1.f / us;
+                int lo = k.n_u, hi = -1;
+                for (int b = 0; b < k.n_u; ++b) {
+                    const float xl = b == 0 ? -1e30f : (__ldg(k.uedge + b) - um) * isu;
+                    const float xh = b == k.n_u - 1 ? 1e30f : (__ldg(k.uedge + b + 1) - um) * isu;
+                    if (xl < 3.001f && xh > -3.001f) {
+                        lo = min(lo, b);
+                        hi = b;
+                    }
+                }
+                if (hi >= lo) {
+                    atomicMin(&ulo, lo);
+                    atomicMax(&uhi, hi);
+                }
+            }
+        }
     }
     __syncthreads();
+    if (k.urange && t == 0) k.urange[blockIdx.x] = make_int2(ulo, uhi);
     if (t < rows) {
         const float kt = key[t];
         int rank = 0;
@@ -182,6 +216,12 @@ cudaError_t launch_zsort(const Ctx &c, const Workspace &w, const float *params, 
     k.um = c.n_u > 1 ? params + 12 * G_stride + g_begin : nullptr;
     k.u_lo = c.sort_u_lo;
     k.u_scale = c.sort_u_scale;
+    // with the nebular axis and tile skipping, the tiles' log U ranges are set
+    // here, before the weights, which then write only those sections
+    k.us = c.n_u > 1 ? params + 13 * G_stride + g_begin : nullptr;
+    k.uedge = c.d_uedge;
+    k.n_u = c.n_u;
+    k.urange = c.n_u > 1 && c.opts.band_skip ? w.urange : nullptr;
     const int n_tiles = (int)((n + 127) / 128);
     cudaError_t e = cudaMemsetAsync(w.hist, 0, ZSORT_BUCKETS * sizeof(int), s);
     if (e != cudaSuccess) return e;
