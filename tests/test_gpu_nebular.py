@@ -119,6 +119,44 @@ def test_section_skipping_is_exact(neb):
     dense.close()
 
 
+def test_section_ranges_at_the_support_edges(neb):
+    # Log U distributions whose support ends exactly on a section edge
+    # (edges at the midpoints -3.75, -3.25, .., -1.25), very narrow and very
+    # wide ones, means off the grid, and invalid log U rows among valid
+    # galaxies: the skipping context equals the dense one bit for bit, and
+    # the valid galaxies match the oracle.
+    from paper_2112_06830_gb300 import dsps
+    ctx, sid, F = neb
+    n = 700
+    p32, p64 = _pop(n, 45)
+    cases = [(-2.5, 0.25), (-3.0, 0.25), (-2.25, 1e-3), (-3.25, 1e-6), (-2.5, 10.0),
+             (-8.0, 0.25), (2.0, 0.25), (-1.0 - 0.75, 0.25), (np.nan, 0.25), (-2.5, 0.0), (-2.5, -0.1),
+             (-2.5, np.inf)]
+    for k, (um, us) in enumerate(cases):
+        p32[12, k::len(cases)] = um
+        p32[13, k::len(cases)] = us
+    p64 = p32.astype(np.float64)
+    bad = ~(np.isfinite(p64[12]) & np.isfinite(p64[13]) & (p64[13] > 0))
+    d = torch.from_numpy(p32).cuda()
+    dense = dsps.Context(_ssp(), sfh_model=synth.SFH_DPL_QUENCH, max_chunk=32768, band_skip=False)
+    sd = dense.add_filters(synth.make_filters(12))
+    for prec in (0, 1):
+        a = ctx.photometry(d, sid, precision=prec).cpu().numpy()
+        b = dense.photometry(d, sd, precision=prec).cpu().numpy()
+        assert np.array_equal(a, b, equal_nan=True)
+        assert np.all(np.isnan(a[bad])) and np.all(np.isfinite(a[~bad]))
+    assert ctx.device_error() == dsps.DSPS_ERR_INVALID_ARG
+    assert ctx.device_error() == 0
+    dense.device_error()
+    dense.close()
+    idx = np.array([k for k in range(0, 96) if not bad[k]] + [n - 4, n - 3])
+    idx = idx[~bad[idx]]
+    ref = oracle.mags(_ogrid(), F, p64[:, idx])
+    err = np.abs(a[idx].astype(np.float64) - ref).max()
+    print(f"nebular support edges: max |dm| = {err:.2e} over {len(idx)} galaxies")
+    assert err <= _util.TOL_BF16X3
+
+
 def test_line_width_and_its_u_gradient(neb):
     ctx, _, _ = neb
     lid = ctx.add_line(LC, HW, CW)
