@@ -6,7 +6,9 @@
 // Work unit = (128-galaxy tile, 256-wide block of SSP indices k), claimed from
 // a global counter (tc::UnitRing); the reduction runs only over the wavelength
 // blocks where the tile's Shat can be non-zero (the redshifted filter band,
-// epilogue.cuh: vjp_band).  Warp roles
+// epilogue.cuh: vjp_band).  With the nebular axis, a unit whose columns meet
+// neither the tile's log U sections nor the reference section is skipped by
+// every role (no galaxy of the tile reads those columns).  Warp roles
 // as in phot_tc.cu: TMA producer, single-thread MMA issuer with a double
 // TMEM accumulator, eight epilogue warps that read rows with tcgen05.ld and
 // write them as 32 x 32 blocks through shared memory and TMA stores (a row per
@@ -36,12 +38,26 @@ constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + 
 
 struct VArgs {
     const int2 *trange;
+    const int2 *urange;   // per-tile log U section ranges (a superset of each row's), or nullptr
+    int sec, u_ref;       // section length (columns), reference section
     VjpBand band;
     int n_mtiles, n_ktiles, n_units, N_pad, K_pad;   // K_pad: the context's KZ_pad (output row length)
     int64_t n;
     int *sched;       // unit counter, zero at launch
     unsigned *err;
 };
+
+// Whether unit (mt, kt) writes columns that the tile's weights adjoint reads:
+// the log U sections of the tile's range, and the reference section, which
+// every galaxy reads (Sec. 3.3: the P_u sum to one).
+__device__ __forceinline__ bool unit_live(const VArgs &a, int mt, int kt) {
+    if (!a.urange) return true;
+    const int2 ur = a.urange[mt];
+    const int c0 = kt * BN, c1 = c0 + BN;
+    const bool in_range = ur.y >= ur.x && c0 < (ur.y + 1) * a.sec && c1 > ur.x * a.sec;
+    const bool in_ref = c0 < (a.u_ref + 1) * a.sec && c1 > a.u_ref * a.sec;
+    return in_range || in_ref;
+}
 
 __global__ void __launch_bounds__(THREADS, 1)
 vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
@@ -105,6 +121,7 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
                 int u;
                 if (!ring_claim(ring, a.sched, a.n_units, u, abort_flag, a.err) || u < 0) break;
                 const int mt = u / a.n_ktiles, kt = u - mt * a.n_ktiles;
+                if (!unit_live(a, mt, kt)) continue;
                 int kb0, kb1;
                 vjp_band(a.band, a.trange, mt, a.N_pad, kb0, kb1);
                 for (int kb = kb0; kb < kb1; ++kb) {
@@ -136,7 +153,8 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
             while (ok) {
                 int u;
                 if (!ring_next(ring, u, abort_flag, a.err) || u < 0) break;
-                const int mt = u / a.n_ktiles;
+                const int mt = u / a.n_ktiles, kt = u - mt * a.n_ktiles;
+                if (!unit_live(a, mt, kt)) continue;
                 int kb0, kb1;
                 vjp_band(a.band, a.trange, mt, a.N_pad, kb0, kb1);
                 if (!mbar_wait(acce0 + 8 * as, aphase ^ 1u, abort_flag, a.err)) { ok = false; break; }
@@ -186,6 +204,7 @@ vjp_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant_
             u = __shfl_sync(0xffffffffu, u, 0);
             if (!have || u < 0) break;
             const int mt = u / a.n_ktiles, kt = u - mt * a.n_ktiles;
+            if (!unit_live(a, mt, kt)) continue;
             int got = 1;
             if (lane == 0) got = mbar_wait(accf0 + 8 * as, aphase, abort_flag, a.err) ? 1 : 0;
             got = __shfl_sync(0xffffffffu, got, 0);
@@ -247,6 +266,11 @@ cudaError_t launch_vjp_tc(const Ctx &c, const Workspace &w, const FilterSet &fs,
         return cudaErrorInvalidValue;
     VArgs a{};
     a.trange = w.trange;
+    // the rows are sorted and, with skipping on, the sort presets the tiles'
+    // log U ranges before the weights run
+    a.urange = c.n_u > 1 && c.opts.band_skip ? w.urange : nullptr;
+    a.sec = c.SEC;
+    a.u_ref = c.u_ref;
     a.band = make_vjp_band(c, fs, c.opts.band_skip != 0);
     a.n_mtiles = (int)((n + BM - 1) / BM);
     a.n_ktiles = (c.KZ_pad + BN - 1) / BN;

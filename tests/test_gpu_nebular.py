@@ -147,6 +147,17 @@ def test_section_ranges_at_the_support_edges(neb):
         assert np.all(np.isnan(a[bad])) and np.all(np.isfinite(a[~bad]))
     assert ctx.device_error() == dsps.DSPS_ERR_INVALID_ARG
     assert ctx.device_error() == 0
+    # the adjoint contraction skips the column blocks outside each tile's log U
+    # sections and the reference section: the same gradients as the dense path
+    mbar = np.random.default_rng(17).standard_normal((n, 12))
+    mb = torch.from_numpy(mbar.astype(np.float32)).cuda()
+    _, ga = ctx.photometry_vjp(d, sid, mb, precision=1)
+    _, gb = dense.photometry_vjp(d, sd, mb, precision=1)
+    ga, gb = ga.cpu().numpy().astype(np.float64), gb.cpu().numpy().astype(np.float64)
+    scale = np.abs(gb[:, ~bad]).max(axis=1, keepdims=True)
+    assert np.abs(ga[:, ~bad] - gb[:, ~bad]).max(axis=1).max() <= 1e-5 * scale.max()
+    assert (np.abs(ga[:, ~bad] - gb[:, ~bad]) <= 1e-5 * scale).all()
+    ctx.device_error()
     dense.device_error()
     dense.close()
     idx = np.array([k for k in range(0, 96) if not bad[k]] + [n - 4, n - 3])
@@ -155,6 +166,12 @@ def test_section_ranges_at_the_support_edges(neb):
     err = np.abs(a[idx].astype(np.float64) - ref).max()
     print(f"nebular support edges: max |dm| = {err:.2e} over {len(idx)} galaxies")
     assert err <= _util.TOL_BF16X3
+    sub = idx[:24]
+    _, gref = oracle.mags_vjp(_ogrid(), F, p64[:, sub], mbar[sub])
+    sc = np.maximum(np.abs(gref), 1e-2 * np.abs(gref).max(axis=0, keepdims=True))
+    rel = np.abs(ga[:, sub] - gref) / np.where(sc > 0, sc, 1.0)
+    print(f"nebular support edges: max scaled gradient error {rel.max():.2e}")
+    assert rel.max() <= 1e-3
 
 
 def test_line_width_and_its_u_gradient(neb):
