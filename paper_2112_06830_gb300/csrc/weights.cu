@@ -804,7 +804,17 @@ __global__ void __launch_bounds__(256, NEB ? 2 : 4) weights_vjp_kernel(WArgs a, 
                         }
                     }
                 }
+                // every section's load issued before any is used (the loads
+                // are independent; one after another they leave the warp
+                // waiting on memory latency once per section)
                 const float4 r = ld4(uref * a.SEC + kz);
+                float4 vs[MAX_NU];
+#pragma unroll
+                for (int uu = 0; uu < MAX_NU; ++uu) {
+                    const bool live = uu < a.n_u && uu >= u_lo && uu <= u_hi && uu != uref;
+                    vs[uu] = live ? *reinterpret_cast<const float4 *>(wrow + uu * a.SEC + kz)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 float dw[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int uu = 0; uu < MAX_NU; ++uu) {
@@ -817,7 +827,14 @@ __global__ void __launch_bounds__(256, NEB ? 2 : 4) weights_vjp_kernel(WArgs a, 
                         dw[3] = fmaf(pu[uu], r.w, dw[3]);
                         continue;
                     }
-                    const float4 v = ld4(uu * a.SEC + kz);
+                    float4 v = vs[uu];
+                    if (scaled) {
+                        const float4 m = __ldg(reinterpret_cast<const float4 *>(a.wmul + uu * a.SEC + kz));
+                        v.x *= m.x;
+                        v.y *= m.y;
+                        v.z *= m.z;
+                        v.w *= m.w;
+                    }
                     dw[0] = fmaf(pu[uu], v.x + r.x, dw[0]);
                     dw[1] = fmaf(pu[uu], v.y + r.y, dw[1]);
                     dw[2] = fmaf(pu[uu], v.z + r.z, dw[2]);
