@@ -371,15 +371,26 @@ cudaError_t groups_forward(Ctx *c, const Workspace &w, int64_t n_gal, int64_t g0
         ProfScope ps(*c, 0, s, prof);
         e = launch_zsort(*c, w, params, n_gal, g0, n, s);
     }
+    // split-bf16: the first multi-age group's weights cache the galaxies' age
+    // fractions in w32 (unused until the adjoint; [n][n_age] <= [cap][KZ_pad]),
+    // and the one-age groups after it read theirs instead of recomputing the SFH
+    bool cached = false;
     for (size_t k = 0; k < c->dust_groups.size() && e == cudaSuccess; ++k) {
         const DustGroup &gr = c->dust_groups[k];
+        Workspace wk = w;
+        const bool multi = gr.i1 - gr.i0 > 1;
+        if (tc && (cached || multi)) {
+            wk.fcache = w.w32;
+            wk.fcache_mode = cached ? 2 : 1;
+        }
         {
             ProfScope ps(*c, 0, s, prof);
             if (tc && k > 0) e = launch_tile_reset(*c, w, n, s);
             if (e == cudaSuccess)
-                e = launch_weights(*c, w, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, true,
+                e = launch_weights(*c, wk, tc ? W_OMEGA_BF16X2 : W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, true,
                                    &gr);
         }
+        cached = cached || wk.fcache_mode == 1;
         int parts = 1;
         if (e == cudaSuccess) {
             ProfScope ps(*c, tc ? 2 : 1, s, prof);

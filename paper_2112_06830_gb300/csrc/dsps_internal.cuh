@@ -173,6 +173,11 @@ struct Workspace {
                                                 // (age-dependent dust; made on first use)
     unsigned long long *stats = nullptr;        // [2] executed-work counters (profiling), or nullptr
     int rest = 0;                               // this call's filter set is rest-frame (FilterSet::rest)
+    // age-dependent dust, split-bf16: the chunk's age fractions [cap][n_age]
+    // (NaN for an invalid galaxy), written by the first multi-age group's
+    // weights (fcache_mode 1) and read by the one-age groups' (fcache_mode 2)
+    float *fcache = nullptr;
+    int fcache_mode = 0;
 };
 
 struct Ctx {

@@ -39,6 +39,8 @@ struct WArgs {
     int row_sfr, grow_sfr;       // tabulated SFH: parameter rows of the node SFRs and their gradient rows
     int rest;                    // rest-frame magnitudes: no redshift shift, no distance terms
     int urange_pre;              // tiles' log U ranges preset by the sort: write only those sections
+    float *fcache_wr;            // out: the age fractions by sorted row [n][n_age] (NaN: invalid), or nullptr
+    const float *fcache_rd;      // a one-age launch: its age's fraction from there instead of the SFH, or nullptr
     const float *uedge;          // [n_u + 1] log U bin edges (+-1e30 outer)
     int2 *urange;                // out: per-tile log U bin ranges (atomics), with trange
     int age_lo, age_hi;          // age bins whose weights are written (the others are 0): a dust group
@@ -345,7 +347,15 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
     const GalPrep gp = a.prep[gl];
 
     float msum = 0.f;
-    valid = sfh_stage<SFH>(a, p, g, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
+    float frac1 = 0.f;   // a one-age launch's fraction from the chunk's cache
+    if (MODE == W_OMEGA_BF16X2_AGE1 && a.fcache_rd) {
+        frac1 = valid ? a.fcache_rd[gi * a.n_age + a.age_lo] : 0.f;
+        valid = valid && !isnan(frac1);
+    } else {
+        valid = sfh_stage<SFH>(a, p, g, valid, gp.m_obs, gp.f_obs, lane, sm, msum);
+        if (MODE == W_OMEGA_BF16X2 && a.fcache_wr)
+            for (int i = lane; i < a.n_age; i += 32) a.fcache_wr[gi * a.n_age + i] = valid ? sm.frac[i] : __int_as_float(0x7fc00000);
+    }
     float *frac = sm.frac;
     // log U bin probabilities, in every lane's registers
     int u_lo = 0, u_hi = 0;
@@ -386,7 +396,7 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                 const float sh = last ? 0.f : mdf_s<MDF>(uh);
                 float pj = sh - sl;
                 if (ul <= 0.f && uh > 0.f) pj += 1.f;
-                om = valid ? frac[i] * pj : 0.f;
+                om = valid ? (a.fcache_rd ? frac1 : frac[i]) * pj : 0.f;
                 if (om != 0.f) {
                     const int b = (lane * a.A_pad + i) / KBLOCK, wi = b >> 5;
                     const unsigned bit = 1u << (b & 31);
@@ -1168,6 +1178,9 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
     if (mode == W_OMEGA_BF16X2 && group && group->i1 - group->i0 == 1 && sorted && c.kmask_words <= 4 &&
         c.opts.band_skip)
         mode = W_OMEGA_BF16X2_AGE1;
+    // the chunk's age fractions: cached by a multi-age group, read by one-age ones
+    a.fcache_wr = w.fcache && w.fcache_mode == 1 && mode == W_OMEGA_BF16X2 && sorted ? w.fcache : nullptr;
+    a.fcache_rd = w.fcache && w.fcache_mode == 2 && mode == W_OMEGA_BF16X2_AGE1 ? w.fcache : nullptr;
     switch (mode) {
     case W_MSUN: return launch_models<WeightsLaunch<W_MSUN>::L>(c, a, grid, smem, s);
     case W_OMEGA_F32: return launch_models<WeightsLaunch<W_OMEGA_F32>::L>(c, a, grid, smem, s);
