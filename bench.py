@@ -49,8 +49,14 @@ def _args():
     ap.add_argument("--cpu-sample", type=int, default=4096)
     ap.add_argument("--precision-gal", type=int, default=1_000_000,
                     help="population of the split-bf16 vs FP32 comparison arm (0: skip)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
-                    help="length of the Poisson request stream (the serving workload is 60 s)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the 200 req/s Poisson request stream (the serving workload: 60 s; 0: skip)")
+    ap.add_argument("--serve-sweep", default="400,800,1600,3200",
+                    help="request rates of the capacity sweep, comma-separated ('' to skip)")
+    ap.add_argument("--serve-sweep-seconds", type=float, default=10.0,
+                    help="length of each capacity-sweep stream")
+    ap.add_argument("--serve-p99-ms", type=float, default=25.0,
+                    help="p99 latency bound of the capacity figure")
     return ap.parse_args()
 
 
@@ -257,6 +263,81 @@ def _cpu_baseline(sample: int, gpu_mags=None):
     return out
 
 
+def _scaled_grad_error(g, ref, floor):
+    """|g - ref| / max(|ref|, floor * max_k |ref[k]|) per component (the
+    maximum over the parameter rows of each galaxy)."""
+    scale = np.maximum(np.abs(ref), floor * np.abs(ref).max(axis=0, keepdims=True))
+    ok = scale > 0
+    out = np.zeros_like(ref)
+    out[ok] = np.abs(g - ref)[ok] / scale[ok]
+    out[~ok] = np.abs(g[~ok])
+    return out
+
+
+def _per_config_error(gpu):
+    """Part of the CPU-baseline leg: the oracle on each workload's check
+    sample beside the GPU results handed over in `gpu` (device work done by the
+    caller).  Per config and precision form: per-galaxy max |dmag| (max and
+    p99 over the sample); for the differentiation workload the scaled gradient
+    error against the oracle's adjoint (floors 1e-3 ||g||, as the contract
+    states, and the split-bf16 test's 1e-2 ||g||), the oracle's adjoint against
+    central differences (h = 1e-4) of the oracle, and the GPU against those
+    differences."""
+    import oracle
+    from paper_2112_06830_gb300 import synth
+    cores = os.cpu_count() or 1
+    out = {}
+
+    def mag_stats(m_gpu, ref):
+        e = np.abs(np.asarray(m_gpu, np.float64) - ref).max(axis=1)
+        return {"n": int(e.size), "max": float(e.max()), "p99": float(np.percentile(e, 99)),
+                "p50": float(np.median(e))}
+
+    # config 0: 64 galaxies, 94 x 12 x 1000 grid, 6 filters, delayed-tau SFH
+    g0 = synth.make_ssp(synth.SMALL_GRID, 0)
+    grid0 = oracle.Grid(g0.log_age_yr, g0.lgz, g0.lam, g0.l_ssp, sfh_model=synth.SFH_DELAYED_TAU)
+    ref0 = oracle.mags(grid0, oracle.Filters(synth.make_filters(6)), gpu["c0_params"], nthreads=cores)
+    out["config0_small_64"] = {k: mag_stats(gpu["c0"][k], ref0) for k in gpu["c0"]}
+    out["config0_small_64"]["tolerance"] = {"fp32": 1e-4, "bf16x3": 1e-3}
+
+    ssp = synth.make_ssp(synth.FULL_GRID, 1)
+    grid = oracle.Grid(ssp.log_age_yr, ssp.lgz, ssp.lam, ssp.l_ssp, sfh_model=synth.SFH_DPL_QUENCH)
+    F = oracle.Filters(synth.make_filters(N_FILT))
+    # config 1: the bench's 1e5-galaxy workload, a sample spread over it
+    ref1 = oracle.mags(grid, F, gpu["c1_params"], nthreads=cores)
+    out["config1_full_1e5"] = {k: mag_stats(gpu["c1"][k], ref1) for k in gpu["c1"]}
+    out["config1_full_1e5"]["sample"] = f"{gpu['c1_params'].shape[1]} galaxies spread over the 1e5"
+    # config 2: 1e6 galaxies, every 1000th
+    if gpu.get("c2"):
+        ref2 = oracle.mags(grid, F, gpu["c2_params"], nthreads=cores)
+        out["config2_1e6"] = {k: mag_stats(gpu["c2"][k], ref2) for k in gpu["c2"]}
+        out["config2_1e6"]["sample"] = "every 1000th galaxy of the 1e6 (1e3 galaxies)"
+    # config 3: squared-magnitude loss on 256 galaxies, the same dL/dm on both sides
+    p3, mbar = gpu["c3_params"], gpu["c3_mbar"]
+    _, pb_ref = oracle.mags_vjp(grid, F, p3, mbar, nthreads=cores)
+    target = gpu["c3_target"]
+    h = 1e-4
+    fd = np.zeros_like(pb_ref)
+    for k in range(pb_ref.shape[0]):
+        pp, pm = p3.copy(), p3.copy()
+        pp[k] += h
+        pm[k] -= h
+        lp = ((oracle.mags(grid, F, pp, nthreads=cores) - target) ** 2).sum(axis=1)
+        lm = ((oracle.mags(grid, F, pm, nthreads=cores) - target) ** 2).sum(axis=1)
+        fd[k] = (lp - lm) / (2 * h)
+    c3 = {"n_gal": int(p3.shape[1]),
+          "oracle_adjoint_vs_fd": {"max_scaled_err_floor_1e-3": float(_scaled_grad_error(pb_ref, fd, 1e-3).max())}}
+    for k, pb in gpu["c3"].items():
+        e3 = _scaled_grad_error(pb, pb_ref, 1e-3)
+        e2 = _scaled_grad_error(pb, pb_ref, 1e-2)
+        c3[k] = {"max_scaled_err_floor_1e-3": float(e3.max()), "max_scaled_err_floor_1e-2": float(e2.max()),
+                 "frac_components_over_1e-3_at_floor_1e-3": float(np.mean(e3 > 1e-3)),
+                 "max_scaled_err_vs_fd_floor_1e-3": float(_scaled_grad_error(pb, fd, 1e-3).max())}
+    c3["tolerance"] = "1e-3 relative; floors f * max_k |g_k| per galaxy"
+    out["config3_grad_256"] = c3
+    return out
+
+
 def _serve_bench(ctx, sids, seconds, rate=200.0):
     """Poisson stream of populations through dsps_submit/dsps_poll (host buffers):
     sizes lognormal(median 3e3, sigma_ln 1.5) clipped to [1e2, 2e5], 4/8/12
@@ -264,7 +345,7 @@ def _serve_bench(ctx, sids, seconds, rate=200.0):
     import threading
 
     from paper_2112_06830_gb300 import dsps, synth
-    reqs = synth.make_request_stream(rate=rate, duration=seconds, seed=4)
+    reqs = synth.make_request_stream(rate=rate, duration=seconds, seed=4 if rate == 200.0 else int(rate))
     pool = synth.make_population(synth.SFH_DPL_QUENCH, 400_000, 1, start=1_000_000).astype(np.float32)
     mbar_pool = np.random.default_rng(9).standard_normal((400_000, 12)).astype(np.float32)
     rng = np.random.default_rng(5)
@@ -312,6 +393,7 @@ def _serve_bench(ctx, sids, seconds, rate=200.0):
     gal = sum(r.n_gal for r in reqs)
     gmags = sum(r.n_gal * r.n_filt for r in reqs)
     return {"requests": len(reqs), "seconds": round(seconds, 3), "rate_per_s": rate,
+            "offered_galaxies_per_s": gal / seconds,
             "galaxies": int(gal), "galaxies_per_s": gal / wall, "galaxy_mags_per_s": gmags / wall,
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "latency_ms_max": float(lat.max()),
@@ -440,14 +522,15 @@ def run_ours(a):
     ms_grad_fp32 = timed_grad(dsps.DSPS_PREC_FP32)
     assert torch.isfinite(d_pbar).all()
 
-    # End to end: pinned host params -> device, photometry, magnitudes -> host.
+    # End to end: one library call with host buffers (dsps_photometry_host):
+    # pinned host params -> device, photometry, magnitudes -> pinned host,
+    # returning once the magnitudes are in host memory.
     h_params = torch.from_numpy(params_h).pin_memory()
     h_mags = torch.empty((G, N_FILT), dtype=torch.float32).pin_memory()
 
     def e2e_step():
-        d_params.copy_(h_params, non_blocking=True)
-        step(dsps.DSPS_PREC_BF16X3)
-        h_mags.copy_(d_mags, non_blocking=True)
+        dsps.dsps_photometry_host(ctx.handle, G, h_params.data_ptr(), sid, dsps.DSPS_PREC_BF16X3,
+                                  h_mags.data_ptr(), stream.cuda_stream)
 
     for _ in range(a.warmup):
         e2e_step()
@@ -647,6 +730,7 @@ def run_ours(a):
     # Precision forms at 1e6 galaxies (same grid and distributions): split-bf16
     # against FP32 throughput, and their per-galaxy magnitude difference.
     precision = None
+    c2_gpu = None
     if a.precision_gal > 0:
         Gp = a.precision_gal
         pp = synth.make_population(synth.SFH_DPL_QUENCH, Gp, 1, start=shard_start(rank, Gp)).astype(np.float32)
@@ -669,21 +753,42 @@ def run_ours(a):
 
         ms_p_tc = timed_p(dsps.DSPS_PREC_BF16X3, m_tc, a.steps)
         ms_p_32 = timed_p(dsps.DSPS_PREC_FP32, m_32, max(1, min(a.steps, 3)))
+        sub = slice(0, Gp, 1000)
+        c2_gpu = {"bf16x3": m_tc[sub].cpu().numpy(), "fp32": m_32[sub].cpu().numpy(),
+                  "params": pp[:, sub].astype(np.float64)}
         dmag = (m_tc - m_32).abs().flatten()
         precision = {"n_gal_per_gpu": Gp, "bf16x3": {"value": ws * Gp * N_FILT / (ms_p_tc * 1e-3), "ms_per_step": ms_p_tc},
                      "fp32": {"value": ws * Gp * N_FILT / (ms_p_32 * 1e-3), "ms_per_step": ms_p_32},
                      "bf16x3_minus_fp32_abs_mag": {"max": float(dmag.max()),
                                                    "p99": float(torch.quantile(dmag[::97].double(), 0.99))},
-                     "note": "per-galaxy error against the FP64 oracle on a 1e3 subsample is a GPU test "
-                             "(test_million_galaxy_precision_forms)"}
+                     "note": "per-galaxy error against the FP64 oracle on the 1e3 subsample: "
+                             "per_config_error.config2_1e6"}
         del dp, m_tc, m_32
 
     serve = None
-    if a.serve_seconds > 0 and rank == 0:
+    serve_capacity = None
+    rates = [float(r) for r in a.serve_sweep.split(",") if r.strip()] if a.serve_sweep else []
+    if (a.serve_seconds > 0 or rates) and rank == 0:
         sids = {N_FILT: sid}
         for q in (4, 8):
             sids[q] = ctx.add_filters(synth.make_filters(q))
-        serve = _serve_bench(ctx, sids, a.serve_seconds)
+        if a.serve_seconds > 0:
+            serve = _serve_bench(ctx, sids, a.serve_seconds)
+        if rates and a.serve_sweep_seconds > 0:
+            points = [_serve_bench(ctx, sids, a.serve_sweep_seconds, rate=r) for r in rates]
+            ok = [pt for pt in points if pt["latency_ms_p99"] <= a.serve_p99_ms
+                  and pt["galaxies_per_s"] >= 0.95 * pt["offered_galaxies_per_s"]]
+            best = max(ok, key=lambda pt: pt["rate_per_s"]) if ok else None
+            serve_capacity = {
+                "p99_bound_ms": a.serve_p99_ms,
+                "capacity_rate_per_s": best["rate_per_s"] if best else None,
+                "capacity_galaxies_per_s": best["galaxies_per_s"] if best else None,
+                "points": [{k: pt[k] for k in ("rate_per_s", "seconds", "requests", "offered_galaxies_per_s",
+                                               "galaxies_per_s", "latency_ms_p50", "latency_ms_p99",
+                                               "latency_ms_max")} for pt in points],
+                "note": "the serving stream's request mix at higher Poisson rates; capacity = the highest swept "
+                        "rate whose p99 latency stays under the bound with throughput keeping up (>= 95% of "
+                        "the offered galaxies/s)"}
 
     if rank != 0:
         ctx.close()
@@ -808,13 +913,61 @@ def run_ours(a):
                       "note": "tabulated star formation histories: SFR at the 200 time nodes per galaxy (random "
                               "bursty histories), split-bf16; gradient with d/dSFR at every node (211 rows)"},
         "serve": serve,
+        "serve_capacity": serve_capacity,
         "clocks": clocks,
     }
     if not a.no_cpu_baseline:
         xs = d_params[:, :a.cpu_sample].contiguous()
-        gm = {name: ctx.photometry(xs, sid, precision=pr).cpu().numpy()
-              for name, pr in (("bf16x3", dsps.DSPS_PREC_BF16X3), ("fp32", dsps.DSPS_PREC_FP32))}
+        forms = (("bf16x3", dsps.DSPS_PREC_BF16X3), ("fp32", dsps.DSPS_PREC_FP32))
+        gm = {name: ctx.photometry(xs, sid, precision=pr).cpu().numpy() for name, pr in forms}
         out["cpu_baseline"] = _cpu_baseline(a.cpu_sample, gm)
+        # GPU results of each workload's check sample, then the oracle beside them
+        gpu = {}
+        ctx0 = dsps.Context(synth.make_ssp(synth.SMALL_GRID, 0), sfh_model=synth.SFH_DELAYED_TAU, device=local)
+        sid0 = ctx0.add_filters(synth.make_filters(6))
+        p0 = synth.make_population(synth.SFH_DELAYED_TAU, 64, 0).astype(np.float32)
+        gpu["c0_params"] = p0.astype(np.float64)
+        gpu["c0"] = {name: ctx0.photometry(torch.from_numpy(p0).cuda(), sid0, precision=pr).cpu().numpy()
+                     for name, pr in forms}
+        ctx0.close()
+        idx1 = np.linspace(0, G - 1, 1024).astype(np.int64)
+        m1 = {"bf16x3": None, "fp32": None}
+        for name, pr in forms:
+            ctx.photometry(d_params, sid, precision=pr, out=d_mags, stream=stream)
+            torch.cuda.synchronize()
+            m1[name] = d_mags.cpu().numpy()[idx1]
+        gpu["c1_params"] = params_h[:, idx1].astype(np.float64)
+        gpu["c1"] = m1
+        if c2_gpu is not None:
+            gpu["c2_params"] = c2_gpu.pop("params")
+            gpu["c2"] = c2_gpu
+        # config 3: targets from perturbed parameters plus 0.05 mag noise; dL/dm = 2 (m - t)
+        # from the oracle's magnitudes, fed to both sides (so the comparison is of the
+        # adjoints, and the oracle's central differences of L are of the same function)
+        import oracle
+        n3 = 256
+        p3 = params_h[:, 7000:7000 + n3].astype(np.float64)
+        rng3 = np.random.default_rng(13)
+        pt = p3.copy()
+        pt[:5] *= 1.0 + 0.02 * rng3.standard_normal((5, n3))
+        pt[5] += 0.05 * rng3.standard_normal(n3)
+        pt[8] = np.clip(pt[8] + 0.05 * rng3.standard_normal(n3), 0.0, None)
+        pt[9] += 0.03 * rng3.standard_normal(n3)
+        pt[10] += 0.05 * rng3.standard_normal(n3)
+        x3 = torch.from_numpy(p3.astype(np.float32)).cuda()
+        x3t = torch.from_numpy(pt.astype(np.float32)).cuda()
+        t3 = ctx.photometry(x3t, sid, precision=dsps.DSPS_PREC_FP32).cpu().numpy().astype(np.float64)
+        t3 = t3 + 0.05 * rng3.standard_normal(t3.shape)
+        ssp3 = synth.make_ssp(synth.FULL_GRID, 1)
+        grid3 = oracle.Grid(ssp3.log_age_yr, ssp3.lgz, ssp3.lam, ssp3.l_ssp, sfh_model=synth.SFH_DPL_QUENCH)
+        m3 = oracle.mags(grid3, oracle.Filters(synth.make_filters(N_FILT)), p3, nthreads=os.cpu_count() or 1)
+        mbar3 = 2.0 * (m3 - t3)
+        gpu["c3_params"], gpu["c3_target"], gpu["c3_mbar"] = p3, t3, mbar3
+        gpu["c3"] = {}
+        for name, pr in forms:
+            _, pb3 = ctx.photometry_vjp(x3, sid, torch.from_numpy(mbar3.astype(np.float32)).cuda(), precision=pr)
+            gpu["c3"][name] = pb3.cpu().numpy().astype(np.float64)
+        out["per_config_error"] = _per_config_error(gpu)
     print(json.dumps(out))
     ctx.close()
     if dist is not None:

@@ -356,38 +356,65 @@ int dsps_line_ew_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t 
  * device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.  All calls share the array: calls whose
  * executions overlap on the GPU race with one another.
- * params: device float32 [12][n_gal]; mags: device float32 [n_gal][n_filt]. */
+ * params: device float32 [npar][n_gal], the context's parameter rows (12 rows,
+ * then the optional blocks of the layout above: a nebular axis, a tabulated
+ * SFH); mags: device float32 [n_gal][n_filt]. */
 int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
                                 float *mags, dsps_stream_t stream);
 
 /* Request loop (continuous batching).  A request carries a population of
- * galaxies in HOST memory (params float32 [12][n_gal], outputs float32) and is
- * admitted when its device footprint fits the HBM budget; requests admitted
- * together are packed into shared launches, their copies and kernels
+ * galaxies (params float32 [npar][n_gal], outputs float32) in host memory or,
+ * with buffers = DSPS_BUF_DEVICE, in device memory of the context's device,
+ * and is admitted when its device footprint fits the HBM budget; requests
+ * admitted together are packed into shared launches, their copies and kernels
  * overlapping on the loop's streams.  Results are identical to a lone
- * dsps_photometry(_vjp) call on the same inputs. */
+ * dsps_photometry(_vjp) call on the same inputs.  (Sec. 5.1 times a population
+ * of galaxies through the forward model; the loop serves many such
+ * populations at once.) */
+enum { DSPS_BUF_HOST = 0, DSPS_BUF_DEVICE = 1 };
 typedef struct {
     int64_t n_gal;
-    const float *params;       /* host [npar][n_gal] (12 rows + optional blocks) */
+    const float *params;       /* [npar][n_gal] (12 rows + optional blocks)      */
     int32_t set_id;
     int32_t precision;
     int32_t want_grad;         /* 0: mags only; 1: also param_bar                */
-    const float *mag_bar;      /* host [n_gal][n_filt], if want_grad             */
-    float *mags;               /* host [n_gal][n_filt]                           */
-    float *param_bar;          /* host [ngrad][n_gal], if want_grad             */
+    const float *mag_bar;      /* [n_gal][n_filt], if want_grad                  */
+    float *mags;               /* [n_gal][n_filt]                                */
+    float *param_bar;          /* [ngrad][n_gal], if want_grad                   */
+    int32_t buffers;           /* DSPS_BUF_HOST: the four arrays are host memory;
+                                  DSPS_BUF_DEVICE: device memory of the
+                                  context's device (copied device to device, no
+                                  host staging); INVALID_ARG for another value or
+                                  a pointer the device cannot address          */
 } dsps_request;
 
-/* Queues a request; *ticket identifies it.  The host buffers must stay valid
- * until dsps_poll reports completion.  OUT_OF_BUDGET if the request alone can
- * never fit the budget. */
+/* Queues a request; *ticket identifies it.  The buffers must stay valid (and
+ * device outputs unread) until dsps_poll reports completion.  OUT_OF_BUDGET if
+ * the request alone can never fit the budget. */
 int dsps_submit(dsps_ctx *ctx, const dsps_request *req, uint64_t *ticket);
 
-/* Waits up to timeout_us microseconds (0 = just test) for a request.
- * Returns DSPS_OK once its outputs are in the host buffers (the ticket is then
- * retired), DSPS_PENDING if still running, DSPS_ERR_TIMEOUT never (a timed
- * out wait returns DSPS_PENDING), DSPS_ERR_NOT_FOUND for an unknown ticket, or
- * the request's own error.  *latency_us (optional) receives submit->done time. */
+/* Waits up to timeout_us microseconds for a request.  Returns DSPS_OK once its
+ * outputs are in the request's buffers (the ticket is then retired);
+ * DSPS_PENDING if timeout_us is 0 (just test) and it is still running;
+ * DSPS_ERR_TIMEOUT if timeout_us > 0 elapsed with the request unfinished (the
+ * ticket stays valid: poll again); DSPS_ERR_NOT_FOUND for an unknown ticket;
+ * or the request's own error.  *latency_us (optional, may be NULL) receives
+ * the submit -> done time of a finished request: an addition to the problem
+ * statement's poll, for the serving latency percentiles. */
 int dsps_poll(dsps_ctx *ctx, uint64_t ticket, int64_t timeout_us, double *latency_us);
+
+/* Observer-frame AB magnitudes (as dsps_photometry) of a population held in
+ * HOST memory, in one call: the parameters are copied to the device, the
+ * photometry runs on `stream`, the magnitudes are copied back, and the call
+ * returns once they are in mags (it synchronises the stream).  params: host
+ * float32 [npar][n_gal]; mags: host float32 [n_gal][n_filt].  Page-locked
+ * (pinned) host buffers are copied by DMA at full link speed; pageable ones
+ * work too, staged by the CUDA driver.  The context keeps a device buffer for
+ * one chunk of inputs and outputs (made, or grown, on first use); larger
+ * populations are processed chunk by chunk.  (Sec. 2.2, the same magnitudes;
+ * the host buffers are an addition for callers whose data lives on the host.) */
+int dsps_photometry_host(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
+                         int32_t precision, float *mags, dsps_stream_t stream);
 
 /* Synchronises the context's streams and the given stream, then returns and
  * clears the sticky device error word: DSPS_OK, or DSPS_ERR_INVALID_ARG if

@@ -396,7 +396,7 @@ cudaError_t groups_forward(Ctx *c, const Workspace &w, int64_t n_gal, int64_t g0
             ProfScope ps(*c, tc ? 2 : 1, s, prof);
             // the FP32 form's sums come from its gradient mode (N, A, D per filter)
             e = tc ? launch_phot_tc(*c, w, fs, n, &parts, s, grad)
-                   : launch_phot_simt(*c, w, fs, n, nullptr, s, true, true, &gr);
+                   : launch_phot_simt(*c, w, fs, n, nullptr, s, true, true, &gr, &parts);
         }
         if (e == cudaSuccess) {
             ProfScope ps(*c, 0, s, prof);

@@ -136,7 +136,7 @@ void free_ctx(Ctx *c) {
     for (auto &ls : c->lines) cudaFree(ls.d_tab);
     void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_k0, c->d_edges, c->d_einh, c->d_bwidth,
                     c->d_zedge, c->d_uedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->ws.ewacc, c->d_err, c->d_stats,
-                    c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d};
+                    c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d, c->d_hio};
     for (void *p : ptrs) cudaFree(p);
     for (auto &r : c->prof_recs) {
         cudaEventDestroy(r.a);
@@ -541,6 +541,14 @@ int dsps_photometry(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t s
     if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry: null context%s");
     std::lock_guard<std::mutex> lk(c->mu);
     return run_photometry(c, n_gal, params, set_id, precision, mags, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int dsps_photometry_host(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
+                         float *mags, dsps_stream_t stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry_host: null context%s");
+    std::lock_guard<std::mutex> lk(c->mu);
+    return run_photometry_host(c, n_gal, params, set_id, precision, mags, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int dsps_photometry_histogram(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,

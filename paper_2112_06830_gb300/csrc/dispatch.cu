@@ -74,12 +74,15 @@ int run_photometry_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const float *p
                 e = launch_zsort(*c, w, params, n_gal, g0, n, s);
                 if (e == cudaSuccess) e = launch_weights(*c, w, W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, true);
             }
+            int parts = 1;
             if (e == cudaSuccess) {
-                // with a histogram, the chunk's magnitudes go to the (otherwise
-                // unused) [cap][16] scratch and are binned from there
                 ProfScope ps(*c, 1, s, prof);
-                e = launch_phot_simt(*c, w, fs, n, hist ? w.cq : mags + g0 * fs.Q, s, false, true);
-                if (e == cudaSuccess && hist) e = launch_histogram(w.cq, n, fs.Q, *hist, s);
+                e = launch_phot_simt(*c, w, fs, n, nullptr, s, false, true, nullptr, &parts);
+            }
+            if (e == cudaSuccess) {
+                // per-part filter sums in a fixed order -> magnitudes (or the histogram)
+                ProfScope ps(*c, 0, s, prof);
+                e = launch_combine(*c, w, fs, n, parts, hist ? nullptr : mags + g0 * fs.Q, s, hist);
             }
         } else {
             int parts = 0;
@@ -128,7 +131,7 @@ int run_photometry_vjp_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const floa
         if (e == cudaSuccess) {
             ProfScope ps(*c, tc ? 2 : 1, s, prof);
             e = tc ? launch_phot_tc(*c, w, fs, n, &parts, s, true)
-                   : launch_phot_simt(*c, w, fs, n, nullptr, s, true, true);
+                   : launch_phot_simt(*c, w, fs, n, nullptr, s, true, true, nullptr, &parts);
         }
         if (e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);
@@ -181,6 +184,65 @@ int run_photometry(Ctx *c, int64_t n_gal, const float *params, int32_t set_id, i
     if (n_gal == 0) return DSPS_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return DSPS_ERR_CUDA;
     return run_photometry_ws(c, c->ws, n_gal, params, c->sets[set_id], precision, mags, s, true);
+}
+
+int run_photometry_host(Ctx *c, int64_t n_gal, const float *h_params, int32_t set_id, int32_t precision,
+                        float *h_mags, cudaStream_t s) {
+    if (n_gal < 0 || (n_gal > 0 && (!h_params || !h_mags))) {
+        set_last_error("dsps_photometry_host: bad argument");
+        return DSPS_ERR_INVALID_ARG;
+    }
+    if (set_id < 0 || set_id >= (int)c->sets.size()) {
+        set_last_error("dsps_photometry_host: unknown filter set");
+        return DSPS_ERR_INVALID_ARG;
+    }
+    if (precision != DSPS_PREC_FP32 && precision != DSPS_PREC_BF16X3) {
+        set_last_error("dsps_photometry_host: unknown precision");
+        return DSPS_ERR_INVALID_ARG;
+    }
+    if (n_gal == 0) return DSPS_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return DSPS_ERR_CUDA;
+    const FilterSet &fs = c->sets[set_id];
+    // one chunk of inputs [npar][chunk] and outputs [chunk][Q] on the device
+    const int64_t chunk = n_gal < c->chunk ? n_gal : c->chunk;
+    const size_t in_bytes = al256((size_t)chunk * c->npar * 4);
+    const size_t need = in_bytes + al256((size_t)chunk * fs.Q * 4);
+    if (c->hio_bytes < need) {
+        if (c->d_hio) cudaFree(c->d_hio);
+        c->d_hio = nullptr;
+        c->hio_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->d_hio, need);
+        if (e != cudaSuccess) {
+            set_last_error(cudaGetErrorString(e));
+            return DSPS_ERR_CUDA;
+        }
+        c->hio_bytes = need;
+    }
+    float *d_p = reinterpret_cast<float *>(c->d_hio);
+    float *d_m = reinterpret_cast<float *>(c->d_hio + in_bytes);
+    for (int64_t g0 = 0; g0 < n_gal; g0 += chunk) {
+        const int64_t n = n_gal - g0 < chunk ? n_gal - g0 : chunk;
+        // rows g0 .. g0 + n of every parameter row: one strided copy
+        cudaError_t e = cudaMemcpy2DAsync(d_p, (size_t)n * 4, h_params + g0, (size_t)n_gal * 4, (size_t)n * 4,
+                                          (size_t)c->npar, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            set_last_error(cudaGetErrorString(e));
+            return DSPS_ERR_CUDA;
+        }
+        const int rc = run_photometry_ws(c, c->ws, n, d_p, fs, precision, d_m, s, true);
+        if (rc != DSPS_OK) return rc;
+        e = cudaMemcpyAsync(h_mags + g0 * fs.Q, d_m, (size_t)n * fs.Q * 4, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) {
+            set_last_error(cudaGetErrorString(e));
+            return DSPS_ERR_CUDA;
+        }
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DSPS_ERR_CUDA;
+    }
+    return DSPS_OK;
 }
 
 int run_photometry_vjp(Ctx *c, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,

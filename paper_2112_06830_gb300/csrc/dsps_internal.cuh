@@ -233,6 +233,8 @@ struct Ctx {
     __nv_bfloat16 *d_L_hi = nullptr;        // [KZ_pad][N_pad] differenced block, row-scaled hi (tensor adjoint)
     __nv_bfloat16 *d_L_lo = nullptr;        // [KZ_pad][N_pad] row-scaled lo
     unsigned *d_err = nullptr;              // sticky error word
+    unsigned char *d_hio = nullptr;         // dsps_photometry_host: device inputs + outputs of one chunk
+    size_t hio_bytes = 0;
 
     KzLayout kzl() const { return KzLayout{A_pad, SEC, n_age, n_z, n_u}; }
 
@@ -313,15 +315,18 @@ cudaError_t launch_combine(const Ctx &c, const Workspace &w, const FilterSet &fs
 cudaError_t launch_histogram(const float *mags, int64_t n, int Q, const HistArgs &h, cudaStream_t s);
 int make_hist_args(const dsps_hist_spec *spec, int n_filt, unsigned long long *counts, HistArgs *out);
 
-// grad: instead of magnitudes, writes the sums N, A, D per filter (see
-// epilogue.cuh) to ctx.d_partial as a single part.
+// Magnitudes (mags != nullptr, forward) are written directly with one part.
+// Otherwise the sums N (grad: N, A, D; see epilogue.cuh) per filter go to
+// w.partial in *parts parts (TC_PARTS interleaved wavelength-tile subsets with
+// sorted rows, one part without), for launch_combine / launch_combine_grad /
+// the dust groups' sums.
 // sorted: rows in the order of launch_zsort (magnitudes written through
 // w.gidx), each 128-row tile contracting only the wavelength tiles of its band.
 // group: weights of one dust group's ages only (age-dependent dust), so the
 // contraction runs over the group's k range alone.
 cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, float *mags,
                              cudaStream_t s, bool grad = false, bool sorted = false,
-                             const DustGroup *group = nullptr);
+                             const DustGroup *group = nullptr, int *parts = nullptr);
 
 // The k range [k_lo, k_hi) of the FP32 (age-major, k = (i n_z + j) n_u + u)
 // weights of a dust group's ages, widened to multiples of bk (all of
@@ -364,6 +369,9 @@ cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *pa
 // (dispatch.cu); mags/param_bar are the caller's device pointers.
 int run_photometry_ws(Ctx *c, const Workspace &w, int64_t n_gal, const float *params, const FilterSet &fs,
                       int32_t precision, float *mags, cudaStream_t s, bool profile, const HistArgs *hist = nullptr);
+// dsps_photometry_host: host params and mags, synchronous on s (dispatch.cu).
+int run_photometry_host(Ctx *c, int64_t n_gal, const float *h_params, int32_t set_id, int32_t precision,
+                        float *h_mags, cudaStream_t s);
 // Allocates ctx.ws.shat (and, with ewacc, ctx.ws.ewacc) if it is not there
 // yet (dispatch.cu).
 int ensure_shat(Ctx *c, bool ewacc = false);

@@ -1,13 +1,18 @@
 // phot_simt.cu -- FP32 SIMT form of the fused photometry kernel.
 //
 // S = omega . L (Eq. full_mdf) as a register-tiled FP32 GEMM: each CTA owns 128
-// galaxies and walks the 128-wide wavelength tiles -- with sorted rows, only
-// those inside the tile's redshifted filter band (the others contribute exact
-// zeros, as in the tensor-core form); after the K loop of a tile
-// the 128x128 block of S goes through shared memory to the epilogue, where two
-// threads per galaxy row apply dust, the redshifted filter lookup and the
-// wavelength reduction (epilogue.cuh).  Per-(galaxy, filter) sums stay in
-// registers across tiles; no spectrum is written to global memory.
+// galaxies and one of `parts` interleaved subsets of the 128-wide wavelength
+// tiles (tile nt belongs to part nt mod parts, as in the tensor-core form) and
+// walks its tiles -- with sorted rows, only those inside the row tile's
+// redshifted filter band (the others contribute exact zeros); after the K loop
+// of a tile the 128x128 block of S goes through shared memory to the epilogue,
+// where two threads per galaxy row apply dust, the redshifted filter lookup and
+// the wavelength reduction (epilogue.cuh).  Per-(galaxy, filter) sums stay in
+// registers across a CTA's tiles and are written per part (combined in a fixed
+// order by the combine kernels), or, with one part, as magnitudes; no spectrum
+// is written to global memory.  The CTAs of one row tile are adjacent in the
+// grid, so they run together and read the tile's weights from DRAM about once
+// (the rest from L2); the SSP operand is staged with cp.async.
 #include "dsps_internal.cuh"
 #include "epilogue.cuh"
 
@@ -30,13 +35,23 @@ struct SArgs {
     const float4 *tab;
     const float *offq;
     ColConst cc;
-    float *mags;           // [n][Q] (row gidx[r] with sorted rows)
-    float *partial;        // gradient mode: [n][3 * 4 * Q4] sums N, A, D per filter
+    float *mags;           // [n][Q] (row gidx[r] with sorted rows), one part only
+    float *partial;        // otherwise [parts][n][NR * 4 * Q4]: per part the sums N (and A, D
+                           // in gradient mode) per filter
+    int parts;             // wavelength-tile subsets (CTAs per row tile)
     const int2 *trange;    // per 128-row tile redshift-shift range (sorted rows), or nullptr: every tile
     const int *gidx;       // sorted row -> chunk galaxy, or nullptr
     int m_nz_lo, m_nz_hi;  // filter table rows with non-zero transmission
     unsigned long long *steps;   // BM x BN x BK tile steps executed (profiling), or nullptr
 };
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int Q4, bool GRAD>
 __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
@@ -46,9 +61,9 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int mt = blockIdx.x / a.parts, part = blockIdx.x - mt * a.parts;
+    const int64_t m0 = (int64_t)mt * BM;
     const int er = tid >> 1, eh = tid & 1;
-    const RowConst rc = load_row_const(a.aux, m0 + er, a.n);
 
     constexpr int NR = GRAD ? 3 : 1;
     float acc[NR][4 * Q4];
@@ -62,7 +77,7 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
     // some shift of this tile's rows (all tiles without ranges)
     int nbeg = 0, nend = a.N_pad;
     if (a.trange) {
-        const int2 r = a.trange[blockIdx.x];
+        const int2 r = a.trange[mt];
         const int n_lo = a.m_nz_lo - r.y - 2, n_hi = a.m_nz_hi - r.x + 1;
         if (r.y < r.x || a.m_nz_hi < a.m_nz_lo || n_hi < 0) {
             nend = 0;
@@ -71,16 +86,25 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
             nend = min(a.N_pad, (n_hi / BN + 1) * BN);
         }
     }
-    if (a.steps && tid == 0 && nend > nbeg) atomicAdd(a.steps, (unsigned long long)((nend - nbeg) / BN) * KT);
-    for (int n0 = nbeg; n0 < nend; n0 += BN) {
+    // this part's tiles: nt = nbeg/BN, ... with nt mod parts == part (a tile's
+    // part does not depend on the band, so every galaxy's sums add the same
+    // non-zero terms in the same order in any batch)
+    const int t0 = nbeg / BN;
+    const int nfirst = (t0 + ((part - t0 % a.parts) % a.parts + a.parts) % a.parts) * BN;
+    const int nstep = a.parts * BN;
+    if (a.steps && tid == 0 && nend > nfirst)
+        atomicAdd(a.steps, (unsigned long long)((nend - nfirst + nstep - 1) / nstep) * KT);
+    for (int n0 = nfirst; n0 < nend; n0 += nstep) {
         float c[8][8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 8; ++j) c[i][j] = 0.f;
 
-        float4 ra[2], rb[2];
-        auto gload = [&](int k0) {
+        // W (row-major per galaxy) through registers, transposed into As; the
+        // SSP panel (row-major per k) straight into Bs with cp.async
+        float4 ra[2];
+        auto gload = [&](int k0, int buf) {
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 int idx = tid + t * THREADS;
@@ -89,8 +113,9 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
                 ra[t] = gr < a.n ? *reinterpret_cast<const float4 *>(a.W + gr * a.K_pad + k0 + kq)
                                  : make_float4(0.f, 0.f, 0.f, 0.f);
                 int k = idx >> 5, nq = (idx & 31) * 4;
-                rb[t] = *reinterpret_cast<const float4 *>(a.L + (int64_t)(k0 + k) * a.N_pad + n0 + nq);
+                cp_async16(&Bs[buf][k][nq], a.L + (int64_t)(k0 + k) * a.N_pad + n0 + nq);
             }
+            cp_async_commit();
         };
         auto sstore = [&](int buf) {
 #pragma unroll
@@ -101,17 +126,16 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
                 As[buf][kq + 1][row] = ra[t].y;
                 As[buf][kq + 2][row] = ra[t].z;
                 As[buf][kq + 3][row] = ra[t].w;
-                int k = idx >> 5, nq = (idx & 31) * 4;
-                *reinterpret_cast<float4 *>(&Bs[buf][k][nq]) = rb[t];
             }
         };
 
-        gload(a.k_lo);
+        gload(a.k_lo, 0);
         sstore(0);
+        cp_async_wait_all();
         __syncthreads();
         for (int kt = 0; kt < KT; ++kt) {
             const int buf = kt & 1;
-            if (kt + 1 < KT) gload(a.k_lo + (kt + 1) * BK);
+            if (kt + 1 < KT) gload(a.k_lo + (kt + 1) * BK, buf ^ 1);
 #pragma unroll
             for (int k = 0; k < BK; ++k) {
                 float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
@@ -126,6 +150,7 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
                     for (int j = 0; j < 8; ++j) c[i][j] = fmaf(av[i], bv[j], c[i][j]);
             }
             if (kt + 1 < KT) sstore(buf ^ 1);
+            cp_async_wait_all();
             __syncthreads();
         }
 
@@ -140,6 +165,7 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
         }
         __syncthreads();
 
+        const RowConst rc = load_row_const(a.aux, m0 + er, a.n);
         if (rc.valid) {
             Slide sl[3];
             const int nb = n0 + eh * 64;
@@ -163,12 +189,14 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
         for (int q = 0; q < 4 * Q4; ++q) acc[r3][q] += __shfl_xor_sync(0xffffffffu, acc[r3][q], 1);
     const int64_t row = m0 + er;
     if (eh == 0 && row < a.n) {
-        if constexpr (GRAD) {
-            float *dst = a.partial + row * (NR * 4 * Q4);
+        if (GRAD || !a.mags) {
+            float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)part * a.n + row) * (NR * 4 * Q4));
 #pragma unroll
             for (int r3 = 0; r3 < NR; ++r3)
 #pragma unroll
-                for (int q = 0; q < 4 * Q4; ++q) dst[r3 * 4 * Q4 + q] = acc[r3][q];
+                for (int qq = 0; qq < Q4; ++qq)
+                    dst[r3 * Q4 + qq] = make_float4(acc[r3][4 * qq], acc[r3][4 * qq + 1], acc[r3][4 * qq + 2],
+                                                    acc[r3][4 * qq + 3]);
         } else {
             write_mags<Q4>(acc[0], a.Q, a.magoff[row], a.offq, a.mags + (a.gidx ? (int64_t)a.gidx[row] : row) * a.Q);
         }
@@ -179,7 +207,7 @@ template <int Q4, bool GRAD>
 cudaError_t launch_q4(const SArgs &a, int64_t n, cudaStream_t s) {
     size_t smem = (size_t)BM * CS_LD * sizeof(float);
     cudaFuncSetAttribute(phot_simt_kernel<Q4, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((unsigned)((n + BM - 1) / BM));
+    dim3 grid((unsigned)((n + BM - 1) / BM * a.parts));
     phot_simt_kernel<Q4, GRAD><<<grid, THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -200,9 +228,14 @@ ColConst make_col_const(const Ctx &c) {
 }
 
 cudaError_t launch_phot_simt(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, float *mags,
-                             cudaStream_t s, bool grad, bool sorted, const DustGroup *group) {
+                             cudaStream_t s, bool grad, bool sorted, const DustGroup *group, int *parts) {
+    // magnitudes need one part; sums go out per part (TC_PARTS with sorted rows)
+    const int np = (!grad && mags) || !sorted ? 1 : TC_PARTS;
+    if (parts) *parts = np;
     if (n <= 0) return cudaSuccess;
+    if (np > 1 && !w.partial) return cudaErrorInvalidValue;
     SArgs a{};
+    a.parts = np;
     a.W = w.w32;
     a.L = c.d_L32;
     a.K_pad = c.K_pad;

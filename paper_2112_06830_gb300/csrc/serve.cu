@@ -1,6 +1,8 @@
 // serve.cu -- request loop with continuous batching (dsps_submit / dsps_poll).
 //
-// A request is a population of galaxies in host memory.  It is cut into
+// A request is a population of galaxies in host memory, or in device memory
+// (dsps_request.buffers = DSPS_BUF_DEVICE: copied device to device into the
+// batch's inputs and out of its outputs, no host staging).  It is cut into
 // pieces of at most PIECE_MAX galaxies.  A scheduler thread forms a batch from
 // the oldest pending piece plus later pending pieces of the same kind (filter
 // set, precision, gradient or not) up to PIECE_MAX galaxies, and launches it as
@@ -96,6 +98,7 @@ private:
 struct Req {
     uint64_t ticket = 0;
     dsps_request r{};
+    bool dev = false;           // buffers in device memory
     int Q = 0;
     int64_t pieces_left = 0;
     int status = DSPS_OK;
@@ -114,6 +117,7 @@ struct Batch {
     std::vector<int64_t> off;   // row offset of each piece in the batch
     int64_t G = 0;
     int Q = 0, set_id = 0, precision = 0, grad = 0;
+    bool any_host = false;      // some piece has host buffers (host staging used)
     unsigned char *dev = nullptr, *host = nullptr;
     float *h_params = nullptr, *h_mbar = nullptr, *h_mags = nullptr, *h_pbar = nullptr;
     cudaEvent_t ev = nullptr;
@@ -224,10 +228,12 @@ void serve_stop(Ctx *c) {
 }
 
 void Serve::launch(Batch &b) {
-    // Host staging: params [npar][G] SoA and, for the gradient, mag_bar [G][Q].
+    // Host staging: params [npar][G] SoA and, for the gradient, mag_bar [G][Q],
+    // of the pieces with host buffers.
     for (size_t i = 0; i < b.pieces.size(); ++i) {
         const Piece &p = b.pieces[i];
         const dsps_request &r = p.req->r;
+        if (p.req->dev) continue;
         for (int row = 0; row < c->npar; ++row)
             std::memcpy(b.h_params + (size_t)row * b.G + b.off[i], r.params + (size_t)row * r.n_gal + p.start,
                         (size_t)p.n * 4);
@@ -247,18 +253,44 @@ void Serve::launch(Batch &b) {
         std::lock_guard<std::mutex> lk(c->mu);
         fs = c->sets[b.set_id];
     }
-    cudaError_t e = cudaMemcpyAsync(d_params, b.h_params, (size_t)b.G * c->npar * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && grad)
-        e = cudaMemcpyAsync(d_mbar, b.h_mbar, (size_t)b.G * b.Q * 4, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaSuccess;
+    if (b.any_host) {
+        e = cudaMemcpyAsync(d_params, b.h_params, (size_t)b.G * c->npar * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && grad)
+            e = cudaMemcpyAsync(d_mbar, b.h_mbar, (size_t)b.G * b.Q * 4, cudaMemcpyHostToDevice, st);
+    }
+    // device pieces, after the staging copy (which carries no data for their rows)
+    for (size_t i = 0; i < b.pieces.size() && e == cudaSuccess; ++i) {
+        const Piece &p = b.pieces[i];
+        const dsps_request &r = p.req->r;
+        if (!p.req->dev) continue;
+        e = cudaMemcpy2DAsync(d_params + b.off[i], (size_t)b.G * 4, r.params + p.start, (size_t)r.n_gal * 4,
+                              (size_t)p.n * 4, (size_t)c->npar, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && grad)
+            e = cudaMemcpyAsync(d_mbar + (size_t)b.off[i] * b.Q, r.mag_bar + (size_t)p.start * b.Q,
+                                (size_t)p.n * b.Q * 4, cudaMemcpyDeviceToDevice, st);
+    }
     int rc = e == cudaSuccess ? DSPS_OK : DSPS_ERR_CUDA;
     if (batches++ == fault_fail_batch) rc = DSPS_ERR_CUDA;   // injected, before any kernel
     if (rc == DSPS_OK)
         rc = grad ? run_photometry_vjp_ws(c, w, b.G, d_params, fs, b.precision, d_mbar, d_mags, d_pbar, st, false)
                   : run_photometry_ws(c, w, b.G, d_params, fs, b.precision, d_mags, st, false);
     if (rc == DSPS_OK) {
-        e = cudaMemcpyAsync(b.h_mags, d_mags, (size_t)b.G * b.Q * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && grad)
-            e = cudaMemcpyAsync(b.h_pbar, d_pbar, (size_t)b.G * c->ngrad * 4, cudaMemcpyDeviceToHost, st);
+        if (b.any_host) {
+            e = cudaMemcpyAsync(b.h_mags, d_mags, (size_t)b.G * b.Q * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && grad)
+                e = cudaMemcpyAsync(b.h_pbar, d_pbar, (size_t)b.G * c->ngrad * 4, cudaMemcpyDeviceToHost, st);
+        }
+        for (size_t i = 0; i < b.pieces.size() && e == cudaSuccess; ++i) {
+            const Piece &p = b.pieces[i];
+            const dsps_request &r = p.req->r;
+            if (!p.req->dev) continue;
+            e = cudaMemcpyAsync(r.mags + (size_t)p.start * b.Q, d_mags + (size_t)b.off[i] * b.Q,
+                                (size_t)p.n * b.Q * 4, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess && grad)
+                e = cudaMemcpy2DAsync(r.param_bar + p.start, (size_t)r.n_gal * 4, d_pbar + b.off[i], (size_t)b.G * 4,
+                                      (size_t)p.n * 4, (size_t)c->ngrad, cudaMemcpyDeviceToDevice, st);
+        }
         if (e != cudaSuccess) rc = DSPS_ERR_CUDA;
     }
     b.status = rc;
@@ -272,6 +304,7 @@ void Serve::finish(Batch &b) {
         for (size_t i = 0; i < b.pieces.size(); ++i) {
             const Piece &p = b.pieces[i];
             const dsps_request &r = p.req->r;
+            if (p.req->dev) continue;   // written on the device before the batch's event
             std::memcpy(r.mags + (size_t)p.start * b.Q, b.h_mags + (size_t)b.off[i] * b.Q, (size_t)p.n * b.Q * 4);
             if (b.grad)
                 for (int k = 0; k < c->ngrad; ++k)
@@ -317,14 +350,18 @@ bool Serve::try_launch(std::unique_lock<std::mutex> &lk) {
         if (G + p.n > PIECE_MAX) break;
         take.push_back(i);
         G += p.n;
+        b.any_host = b.any_host || !p.req->dev;
     }
     const int64_t Gpad = (G + 127) / 128 * 128;
     unsigned char *d = dev.alloc(dev_bytes(Gpad, b.Q, b.grad));
     if (!d) return false;    // admission by memory: wait for a batch to finish
-    unsigned char *h = host.alloc(host_bytes(G, b.Q, b.grad));
-    if (!h) {
-        dev.release(d);
-        return false;
+    unsigned char *h = nullptr;
+    if (b.any_host) {
+        h = host.alloc(host_bytes(G, b.Q, b.grad));
+        if (!h) {
+            dev.release(d);
+            return false;
+        }
     }
     b.slot = slot;
     b.dev = d;
@@ -332,7 +369,7 @@ bool Serve::try_launch(std::unique_lock<std::mutex> &lk) {
     b.G = G;
     b.h_params = reinterpret_cast<float *>(h);
     b.h_mags = reinterpret_cast<float *>(h + al256(G * c->npar * 4));
-    if (b.grad) {
+    if (b.grad && h) {
         b.h_mbar = reinterpret_cast<float *>(h + al256(G * c->npar * 4) + al256(G * b.Q * 4));
         b.h_pbar = reinterpret_cast<float *>(h + al256(G * c->npar * 4) + 2 * al256(G * b.Q * 4));
     }
@@ -380,12 +417,41 @@ void Serve::loop() {
     }
 }
 
+namespace {
+
+// Whether the device `dev` can address p as device memory (device or managed).
+bool device_pointer(const void *p, int dev) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
 int serve_submit(Ctx *c, const dsps_request *r, uint64_t *ticket) {
     if (r->n_gal < 0 || (r->n_gal > 0 && (!r->params || !r->mags)) ||
         (r->want_grad && r->n_gal > 0 && (!r->mag_bar || !r->param_bar)) ||
-        (r->precision != DSPS_PREC_FP32 && r->precision != DSPS_PREC_BF16X3)) {
+        (r->precision != DSPS_PREC_FP32 && r->precision != DSPS_PREC_BF16X3) ||
+        (r->buffers != DSPS_BUF_HOST && r->buffers != DSPS_BUF_DEVICE)) {
         set_last_error("dsps_submit: bad request");
         return DSPS_ERR_INVALID_ARG;
+    }
+    if (r->buffers == DSPS_BUF_DEVICE && r->n_gal > 0) {
+        if (cudaSetDevice(c->device) != cudaSuccess) {
+            set_last_error("dsps_submit: cudaSetDevice failed");
+            return DSPS_ERR_CUDA;
+        }
+        const void *ptrs[4] = {r->params, r->mags, r->want_grad ? r->mag_bar : r->params,
+                               r->want_grad ? r->param_bar : r->params};
+        for (const void *p : ptrs)
+            if (!device_pointer(p, c->device)) {
+                set_last_error("dsps_submit: a DSPS_BUF_DEVICE request holds a pointer that is not device memory "
+                               "of the context's device");
+                return DSPS_ERR_INVALID_ARG;
+            }
     }
     int Q = 0;
     {
@@ -407,6 +473,7 @@ int serve_submit(Ctx *c, const dsps_request *r, uint64_t *ticket) {
     }
     auto q = std::make_shared<Req>();
     q->r = *r;
+    q->dev = r->buffers == DSPS_BUF_DEVICE;
     q->Q = Q;
     q->t_submit = Clock::now();
     {
@@ -447,7 +514,11 @@ int serve_poll(Ctx *c, uint64_t ticket, int64_t timeout_us, double *latency_us) 
     std::shared_ptr<Req> q = it->second;
     if (!q->done && timeout_us > 0)
         s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return q->done; });
-    if (!q->done) return DSPS_PENDING;
+    if (!q->done) {
+        if (timeout_us <= 0) return DSPS_PENDING;
+        set_last_error("dsps_poll: the wait timed out with the request unfinished");
+        return DSPS_ERR_TIMEOUT;
+    }
     if (latency_us)
         *latency_us = std::chrono::duration<double, std::micro>(q->t_done - q->t_submit).count();
     s->reqs.erase(it);

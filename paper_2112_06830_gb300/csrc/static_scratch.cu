@@ -55,12 +55,13 @@ cudaError_t scratch_address(int dev, unsigned char **out) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Largest population that fits: [rows][K_pad] FP32 weights, then
-// [rows][AUX_STRIDE] FP32 constants, [rows] FP64 offsets and [rows] GalPrep.
+// [rows][AUX_STRIDE] FP32 constants, [rows] FP32 magnitude offsets and
+// [rows] GalPrep (the layout of the context's work space, Workspace).
 int64_t max_rows(int K_pad) {
-    const size_t per = (size_t)K_pad * 4 + AUX_STRIDE * 4 + 8 + sizeof(GalPrep);
+    const size_t per = (size_t)K_pad * 4 + AUX_STRIDE * 4 + 4 + sizeof(GalPrep);
     int64_t r = (int64_t)((STATIC_SCRATCH_BYTES - 4 * 256) / per);
     while (r > 0 && align256((size_t)r * K_pad * 4) + align256((size_t)r * AUX_STRIDE * 4) +
-                            align256((size_t)r * 8) + align256((size_t)r * sizeof(GalPrep)) > STATIC_SCRATCH_BYTES)
+                            align256((size_t)r * 4) + align256((size_t)r * sizeof(GalPrep)) > STATIC_SCRATCH_BYTES)
         --r;
     return r;
 }
@@ -94,8 +95,14 @@ extern "C" int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const f
         return DSPS_ERR_INVALID_ARG;
     }
     if (n_gal == 0) return DSPS_OK;
-    if (c->device < 0 || c->device >= MAX_DEVICES) return DSPS_ERR_UNSUPPORTED;
-    if (cudaSetDevice(c->device) != cudaSuccess) return DSPS_ERR_CUDA;
+    if (c->device < 0 || c->device >= MAX_DEVICES) {
+        set_last_error("dsps_photometry_fp32_static: device index beyond the static scratch table");
+        return DSPS_ERR_UNSUPPORTED;
+    }
+    if (cudaSetDevice(c->device) != cudaSuccess) {
+        set_last_error("dsps_photometry_fp32_static: cudaSetDevice failed");
+        return DSPS_ERR_CUDA;
+    }
     unsigned char *base = nullptr;
     cudaError_t e = scratch_address(c->device, &base);
     if (e != cudaSuccess) {
@@ -109,7 +116,7 @@ extern "C" int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const f
     ws.aux = reinterpret_cast<float *>(base + off_aux);
     const size_t off_mo = off_aux + align256((size_t)cap * AUX_STRIDE * 4);
     ws.magoff = reinterpret_cast<float *>(base + off_mo);
-    ws.prep = reinterpret_cast<GalPrep *>(base + off_mo + align256((size_t)cap * 8));
+    ws.prep = reinterpret_cast<GalPrep *>(base + off_mo + align256((size_t)cap * 4));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const FilterSet &fs = c->sets[set_id];
     ws.rest = fs.rest;

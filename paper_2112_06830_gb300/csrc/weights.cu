@@ -9,8 +9,10 @@
 //      interval, partial plus whole interval integrals across nodes -- so the
 //      youngest bins (down to ~1e-8 of the mass of a quenched galaxy) keep
 //      their relative precision in FP32 instead of being the difference of two
-//      cumulative masses.  The total M(t_obs) (Eq. mstartot) is accumulated in
-//      FP64, and t_obs's position on the time grid is split off in FP64.
+//      cumulative masses.  The whole-interval masses come from a node prefix
+//      held as an unevaluated FP32 pair (TwoSum at every addition); the total
+//      M(t_obs) (Eq. mstartot) is an FP32 warp tree sum of the bin masses; only
+//      t_obs's position on the time grid is split off in FP64 (prep kernel).
 //   5. Metallicity weights P_met(j | i) as differences of the triweight
 //      (Appendix B, Eq. terf) or Gaussian CDF over lgZ bin edges, with the mean
 //      moving linearly in log age (Sec. 3.2, Eq. agedep_mdf), FP32.

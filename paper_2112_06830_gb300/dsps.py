@@ -24,6 +24,8 @@ DSPS_ERR_INVALID_ARG = -1
 DSPS_ERR_OUT_OF_BUDGET = -2
 DSPS_ERR_CUDA = -3
 DSPS_ERR_TIMEOUT = -4
+DSPS_BUF_HOST = 0
+DSPS_BUF_DEVICE = 1
 DSPS_ERR_DEVICE_FAULT = -5
 DSPS_ERR_UNSUPPORTED = -6
 DSPS_ERR_NOT_FOUND = -7
@@ -93,7 +95,7 @@ class dsps_line_spec(C.Structure):
 class dsps_request(C.Structure):
     _fields_ = [("n_gal", C.c_int64), ("params", C.c_void_p), ("set_id", C.c_int32),
                 ("precision", C.c_int32), ("want_grad", C.c_int32), ("mag_bar", C.c_void_p),
-                ("mags", C.c_void_p), ("param_bar", C.c_void_p)]
+                ("mags", C.c_void_p), ("param_bar", C.c_void_p), ("buffers", C.c_int32)]
 
 
 _lib = None
@@ -129,6 +131,8 @@ _SIGS = [
                                    C.c_void_p, C.c_void_p]),
     ("dsps_submit", C.c_int, [C.c_void_p, C.POINTER(dsps_request), C.POINTER(C.c_uint64)]),
     ("dsps_poll", C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(C.c_double)]),
+    ("dsps_photometry_host", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                       C.c_void_p]),
     ("dsps_device_error", C.c_int, [C.c_void_p, C.c_void_p]),
     ("dsps_profile_enable", C.c_int, [C.c_void_p, C.c_int32]),
     ("dsps_profile_read", C.c_int, [C.c_void_p, C.POINTER(dsps_profile_t)]),
@@ -271,9 +275,19 @@ def dsps_submit(ctx, req: dsps_request):
 
 
 def dsps_poll(ctx, ticket, timeout_us=0):
+    """(rc, latency_us): rc is DSPS_OK, DSPS_PENDING (timeout 0) or
+    DSPS_ERR_TIMEOUT (a positive timeout elapsed); other errors raise."""
     lat = C.c_double(0.0)
-    rc = _check(load().dsps_poll(ctx, ticket, timeout_us, C.byref(lat)), "dsps_poll")
+    rc = load().dsps_poll(ctx, ticket, timeout_us, C.byref(lat))
+    if rc != DSPS_ERR_TIMEOUT:
+        _check(rc, "dsps_poll")
     return rc, lat.value
+
+
+def dsps_photometry_host(ctx, n_gal, params_ptr, set_id, precision, mags_ptr, stream=0):
+    """Host buffers in and out, one call (synchronises the stream)."""
+    return _check(load().dsps_photometry_host(ctx, n_gal, params_ptr, set_id, precision, mags_ptr, stream),
+                  "dsps_photometry_host")
 
 
 def dsps_device_error(ctx, stream=0):
@@ -476,18 +490,54 @@ class Context:
     def device_error(self, stream=None):
         return dsps_device_error(self.handle, _stream_handle(stream))
 
-    # ---- request loop (host buffers) ----
+    def photometry_host(self, params, set_id, precision=DSPS_PREC_BF16X3, out=None, stream=None):
+        """Magnitudes of a population held in host memory (numpy or pinned torch
+        CPU float32 [npar, G]) in one library call; returns host [G, Q]
+        (``out`` if given: a C-contiguous float32 host buffer)."""
+        if hasattr(params, "data_ptr"):
+            G, ptr = params.shape[1], params.data_ptr()
+        else:
+            params = np.ascontiguousarray(params, dtype=np.float32)
+            G, ptr = params.shape[1], params.ctypes.data
+        Q = self.n_filt[set_id]
+        if out is None:
+            out = np.empty((G, Q), dtype=np.float32)
+        optr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        dsps_photometry_host(self.handle, G, ptr, set_id, precision, optr, _stream_handle(stream))
+        return out
+
+    # ---- request loop ----
     def submit(self, params, set_id, precision=DSPS_PREC_BF16X3, mag_bar=None):
-        """Queues a population held in host memory (numpy float32 [npar, G]:
-        12 rows, more with the optional blocks); the returned Ticket keeps the
-        host buffers alive until it is polled."""
+        """Queues a population: numpy float32 [npar, G] in host memory (12 rows,
+        more with the optional blocks), or a CUDA torch tensor of that shape (a
+        DSPS_BUF_DEVICE request: mag_bar a CUDA tensor too, outputs allocated on
+        the device).  The returned Ticket keeps the buffers alive until it is
+        polled."""
+        Q = self.n_filt[set_id]
+        if hasattr(params, "is_cuda") and params.is_cuda:
+            import torch
+            params = params.contiguous().to(torch.float32)
+            if params.ndim != 2 or params.shape[0] != self.npar:
+                raise ValueError(f"params must be [{self.npar}, G], got {tuple(params.shape)}")
+            G = params.shape[1]
+            t = Ticket(params, torch.empty((G, Q), dtype=torch.float32, device=params.device))
+            req = dsps_request(G, params.data_ptr(), set_id, precision, 0, None, t.mags.data_ptr(), None,
+                               DSPS_BUF_DEVICE)
+            if mag_bar is not None:
+                t.mag_bar = mag_bar.contiguous().to(torch.float32).reshape(G, Q)
+                t.param_bar = torch.empty((self.ngrad, G), dtype=torch.float32, device=params.device)
+                req.want_grad = 1
+                req.mag_bar = t.mag_bar.data_ptr()
+                req.param_bar = t.param_bar.data_ptr()
+            t.id = dsps_submit(self.handle, req)
+            return t
         params = np.ascontiguousarray(params, dtype=np.float32)
         if params.ndim != 2 or params.shape[0] != self.npar:
             raise ValueError(f"params must be [{self.npar}, G], got {params.shape}")
         G = params.shape[1]
-        Q = self.n_filt[set_id]
         t = Ticket(params, np.empty((G, Q), dtype=np.float32))
-        req = dsps_request(G, params.ctypes.data, set_id, precision, 0, None, t.mags.ctypes.data, None)
+        req = dsps_request(G, params.ctypes.data, set_id, precision, 0, None, t.mags.ctypes.data, None,
+                           DSPS_BUF_HOST)
         if mag_bar is not None:
             t.mag_bar = np.ascontiguousarray(mag_bar, dtype=np.float32).reshape(G, Q)
             t.param_bar = np.empty((self.ngrad, G), dtype=np.float32)
@@ -498,7 +548,9 @@ class Context:
         return t
 
     def poll(self, ticket, timeout_us=0):
-        """DSPS_OK (outputs ready in ticket.mags / ticket.param_bar) or DSPS_PENDING."""
+        """DSPS_OK (outputs ready in ticket.mags / ticket.param_bar),
+        DSPS_PENDING (timeout_us = 0, still running) or DSPS_ERR_TIMEOUT (a
+        positive timeout elapsed first; poll again)."""
         rc, lat = dsps_poll(self.handle, ticket.id, timeout_us)
         if rc == DSPS_OK:
             ticket.latency_us = lat

@@ -118,7 +118,7 @@ def test_batch_invariance_and_request_loop():
         assert torch.equal(m1, m2) and torch.equal(g1, g2)
         assert torch.equal(big.photometry(p, sb, precision=prec), m1)
     t = big.submit(p32, sb, precision=1, mag_bar=mb)
-    while big.poll(t, 100000) == dsps.DSPS_PENDING:
+    while big.poll(t, 100000) in (dsps.DSPS_PENDING, dsps.DSPS_ERR_TIMEOUT):
         pass
     m, g = big.photometry_vjp(p, sb, torch.from_numpy(mb).cuda(), precision=1)
     assert np.array_equal(t.mags, m.cpu().numpy()) and np.array_equal(t.param_bar, g.cpu().numpy())

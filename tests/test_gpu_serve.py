@@ -136,3 +136,78 @@ def test_injected_batch_failure_is_contained():
         np.testing.assert_array_equal(t1.mags, _direct(ctx, {12: sid}, (p, 12, False, 1, None))[0])
     finally:
         del os.environ["DSPS_SERVE_FAULT"]
+
+
+def test_poll_timeout_pending_and_retry():
+    """dsps_poll: a zero timeout on an unfinished request returns DSPS_PENDING,
+    a positive timeout that elapses returns DSPS_ERR_TIMEOUT and leaves the
+    ticket valid, and a later poll collects the result.  The completion is held
+    back on the host (DSPS_SERVE_FAULT=delay_us); the GPU work is untouched."""
+    from paper_2112_06830_gb300 import dsps
+    os.environ["DSPS_SERVE_FAULT"] = "delay_us:1500000"
+    try:
+        ctx = _ctx(n_streams=1)
+        sid = ctx.add_filters(synth.make_filters(12))
+        p = synth.make_population(synth.SFH_DPL_QUENCH, 2500, 6).astype(np.float32)
+        t = ctx.submit(p, sid)
+        assert ctx.poll(t) == dsps.DSPS_PENDING
+        assert ctx.poll(t, timeout_us=20_000) == dsps.DSPS_ERR_TIMEOUT
+        assert ctx.poll(t, timeout_us=30_000_000) == dsps.DSPS_OK
+        np.testing.assert_array_equal(t.mags, _direct(ctx, {12: sid}, (p, 12, False, 1, None))[0])
+    finally:
+        del os.environ["DSPS_SERVE_FAULT"]
+
+
+def test_device_buffer_requests_mixed_with_host_requests():
+    """Requests whose buffers are device memory (DSPS_BUF_DEVICE) ride in the
+    same batches as host requests and give the lone call's results bit for bit;
+    a device request holding a host pointer is refused."""
+    from paper_2112_06830_gb300 import dsps
+    ctx = _ctx()
+    sids = {q: ctx.add_filters(synth.make_filters(q)) for q in (4, 8, 12)}
+    reqs = _requests(16, 7)
+    tickets = []
+    for i, (p, q, grad, prec, mbar) in enumerate(reqs):
+        if i % 2:
+            tickets.append(ctx.submit(torch.from_numpy(p).cuda(), sids[q], precision=prec,
+                                      mag_bar=torch.from_numpy(mbar).cuda() if grad else None))
+        else:
+            tickets.append(ctx.submit(p, sids[q], precision=prec, mag_bar=mbar if grad else None))
+    assert all(ctx.poll(t, timeout_us=60_000_000) == dsps.DSPS_OK for t in tickets)
+    for i, (req, t) in enumerate(zip(reqs, tickets)):
+        m, pb = _direct(ctx, sids, req)
+        got = t.mags.cpu().numpy() if i % 2 else t.mags
+        np.testing.assert_array_equal(got, m)
+        if req[2]:
+            gpb = t.param_bar.cpu().numpy() if i % 2 else t.param_bar
+            np.testing.assert_array_equal(gpb, pb)
+    p = np.ascontiguousarray(reqs[0][0])
+    out = torch.empty((p.shape[1], 12), dtype=torch.float32, device="cuda")
+    bad = dsps.dsps_request(p.shape[1], p.ctypes.data, sids[12], 1, 0, None, out.data_ptr(), None,
+                            dsps.DSPS_BUF_DEVICE)
+    with pytest.raises(dsps.DSPSError) as ei:
+        dsps.dsps_submit(ctx.handle, bad)
+    assert ei.value.code == dsps.DSPS_ERR_INVALID_ARG
+    assert ctx.device_error() == 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_photometry_host_buffers_equal_device_call(prec):
+    """dsps_photometry_host (host parameters in, host magnitudes out, one call)
+    equals dsps_photometry on device buffers, with pageable and pinned host
+    memory, and over several chunks of a small work space (ragged last chunk)."""
+    from paper_2112_06830_gb300 import dsps
+    ctx = dsps.Context(_util.ssp("small"), sfh_model=synth.SFH_DELAYED_TAU, max_chunk=256)
+    sid = ctx.add_filters(synth.make_filters(6))
+    p = synth.make_population(synth.SFH_DELAYED_TAU, 1000, 12).astype(np.float32)
+    want = ctx.photometry(torch.from_numpy(p).cuda(), sid, precision=prec)
+    torch.cuda.synchronize()
+    want = want.cpu().numpy()
+    got = ctx.photometry_host(p, sid, precision=prec)
+    np.testing.assert_array_equal(got, want)
+    pinned = torch.from_numpy(p).pin_memory()
+    out = torch.empty((1000, 6), dtype=torch.float32).pin_memory()
+    ctx.photometry_host(pinned, sid, precision=prec, out=out)
+    np.testing.assert_array_equal(out.numpy(), want)
+    assert ctx.device_error() == 0
+    ctx.close()
