@@ -975,6 +975,19 @@ typedef struct {
     double *out;   /* mode 3: [G][n_lam]; mode 4: [G] */
 } orc_job;
 
+/* The forward model's domain (the library's too): redshift z > 0 and finite,
+ * MDF width sigma > 0, log U width > 0 with a nebular axis.  Outside it every
+ * output of the galaxy is NaN; the cosmology integrals are not evaluated
+ * there (at z <= -1 their limits are not numbers). */
+static int orc_in_domain(const orc_grid *g, const double *par)
+{
+    double z = par[11];
+    if (!(z > 0.0) || !isfinite(z)) return 0;
+    if (!(par[6] > 0.0)) return 0;
+    if (orc_nu(g) > 1 && !(par[13] > 0.0)) return 0;
+    return 1;
+}
+
 static void *orc_worker(void *arg)
 {
     orc_job *j = (orc_job *)arg;
@@ -986,6 +999,18 @@ static void *orc_worker(void *arg)
     for (long gi = j->begin; gi < j->end; ++gi) {
         for (int r = 0; r < npar; ++r) par[r] = j->params[(size_t)r * j->n_gal + gi];
         double z = par[11];
+        if (!orc_in_domain(g, par)) {
+            if (j->mode == 0)
+                for (int k = 0; k < K; ++k) j->w_out[(size_t)gi * K + k] = NAN;
+            if (j->mags)
+                for (int q = 0; q < j->f->n_filt; ++q) j->mags[(size_t)gi * j->f->n_filt + q] = NAN;
+            if (j->mode == 3)
+                for (int n = 0; n < g->n_lam; ++n) j->out[(size_t)gi * g->n_lam + n] = NAN;
+            if (j->mode == 4) j->out[gi] = NAN;
+            if (j->pbar)
+                for (int k = 0; k < ngrad; ++k) j->pbar[(size_t)k * j->n_gal + gi] = NAN;
+            continue;
+        }
         double t_obs = orc_age_gyr(g->om0, g->w0, g->h, z);
         if (j->mode == 0) {
             galaxy_weights(g, par, t_obs, omega);

@@ -201,6 +201,7 @@ double terf_host(double z) {
 const char *dsps_last_error_message(void) { return g_last_error.c_str(); }
 
 int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
+    DSPS_TRACE("dsps_create");
     if (!out || !g) return fail(DSPS_ERR_INVALID_ARG, "dsps_create: null argument%s");
     *out = nullptr;
     dsps_opts opts;
@@ -439,6 +440,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
 }
 
 int dsps_destroy(dsps_ctx *ctx) {
+    DSPS_TRACE("dsps_destroy");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return DSPS_OK;
     serve_stop(c);
@@ -450,11 +452,13 @@ int dsps_destroy(dsps_ctx *ctx) {
 
 int dsps_filters_add(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const double *const *lam,
                      const double *const *trans, int32_t *set_id) {
+    DSPS_TRACE("dsps_filters_add");
     return dsps_filters_add_frame(ctx, n_filt, n_pts, lam, trans, DSPS_FRAME_OBSERVER, set_id);
 }
 
 int dsps_filters_add_frame(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, const double *const *lam,
                            const double *const *trans, int32_t frame, int32_t *set_id) {
+    DSPS_TRACE("dsps_filters_add_frame");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !n_pts || !lam || !trans || !set_id) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_add: null argument%s");
     if (frame != DSPS_FRAME_OBSERVER && frame != DSPS_FRAME_REST)
@@ -513,6 +517,7 @@ int dsps_filters_add_frame(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, 
 }
 
 int dsps_filters_count(dsps_ctx *ctx, int32_t set_id, int32_t *n_filt) {
+    DSPS_TRACE("dsps_filters_count");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !n_filt) return fail(DSPS_ERR_INVALID_ARG, "dsps_filters_count: null argument%s");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -522,6 +527,7 @@ int dsps_filters_count(dsps_ctx *ctx, int32_t set_id, int32_t *n_filt) {
 }
 
 int dsps_weights(dsps_ctx *ctx, int64_t n_gal, const float *params, float *w_out, dsps_stream_t stream) {
+    DSPS_TRACE("dsps_weights");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !w_out))) return fail(DSPS_ERR_INVALID_ARG, "dsps_weights: bad argument%s");
     if (n_gal == 0) return DSPS_OK;
@@ -537,6 +543,7 @@ int dsps_weights(dsps_ctx *ctx, int64_t n_gal, const float *params, float *w_out
 
 int dsps_photometry(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
                     float *mags, dsps_stream_t stream) {
+    DSPS_TRACE("dsps_photometry");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry: null context%s");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -545,6 +552,7 @@ int dsps_photometry(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t s
 
 int dsps_photometry_host(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
                          float *mags, dsps_stream_t stream) {
+    DSPS_TRACE("dsps_photometry_host");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry_host: null context%s");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -553,6 +561,7 @@ int dsps_photometry_host(dsps_ctx *ctx, int64_t n_gal, const float *params, int3
 
 int dsps_photometry_histogram(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
                               const dsps_hist_spec *spec, uint64_t *counts, dsps_stream_t stream) {
+    DSPS_TRACE("dsps_photometry_histogram");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || n_gal < 0 || (n_gal > 0 && !params)) return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry_histogram: bad argument%s");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -573,6 +582,7 @@ int dsps_photometry_histogram(dsps_ctx *ctx, int64_t n_gal, const float *params,
 
 int dsps_histogram(dsps_ctx *ctx, int64_t n_gal, const float *mags, int32_t n_filt, const dsps_hist_spec *spec,
                    uint64_t *counts, dsps_stream_t stream) {
+    DSPS_TRACE("dsps_histogram");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || n_gal < 0 || (n_gal > 0 && !mags) || n_filt < 1 || n_filt > DSPS_MAX_FILTERS)
         return fail(DSPS_ERR_INVALID_ARG, "dsps_histogram: bad argument%s");
@@ -588,6 +598,7 @@ int dsps_histogram(dsps_ctx *ctx, int64_t n_gal, const float *mags, int32_t n_fi
 
 int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, int32_t precision,
                         const float *mag_bar, float *mags, float *param_bar, dsps_stream_t stream) {
+    DSPS_TRACE("dsps_photometry_vjp");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_photometry_vjp: null context%s");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -597,6 +608,7 @@ int dsps_photometry_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32
 
 int dsps_spectra(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t n0, int32_t n1, float *out,
                  dsps_stream_t stream) {
+    DSPS_TRACE("dsps_spectra");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !out))) return fail(DSPS_ERR_INVALID_ARG, "dsps_spectra: bad argument%s");
     if (n0 < 0 || n1 <= n0 || n1 > c->n_lam) return fail(DSPS_ERR_INVALID_ARG, "dsps_spectra: need 0 <= n0 < n1 <= n_lam%s");
@@ -607,6 +619,7 @@ int dsps_spectra(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t n0, 
 }
 
 int dsps_line_add(dsps_ctx *ctx, const dsps_line_spec *spec, int32_t *line_id) {
+    DSPS_TRACE("dsps_line_add");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !spec || !line_id) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_add: null argument%s");
     const double lc = spec->lam_line, hw = spec->half_width, cw = spec->cont_width;
@@ -681,6 +694,7 @@ int dsps_line_add(dsps_ctx *ctx, const dsps_line_spec *spec, int32_t *line_id) {
 
 int dsps_line_ew(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line_id, float *ew,
                  dsps_stream_t stream) {
+    DSPS_TRACE("dsps_line_ew");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !ew))) return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew: bad argument%s");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -695,6 +709,7 @@ int dsps_line_ew(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line
 
 int dsps_line_ew_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t line_id, const float *ew_bar,
                      float *ew, float *param_bar, dsps_stream_t stream) {
+    DSPS_TRACE("dsps_line_ew_vjp");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !ew_bar || !param_bar)))
         return fail(DSPS_ERR_INVALID_ARG, "dsps_line_ew_vjp: bad argument%s");
@@ -709,18 +724,21 @@ int dsps_line_ew_vjp(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t 
 }
 
 int dsps_submit(dsps_ctx *ctx, const dsps_request *req, uint64_t *ticket) {
+    DSPS_TRACE("dsps_submit");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !req || !ticket) return fail(DSPS_ERR_INVALID_ARG, "dsps_submit: null argument%s");
     return serve_submit(c, req, ticket);
 }
 
 int dsps_poll(dsps_ctx *ctx, uint64_t ticket, int64_t timeout_us, double *latency_us) {
+    DSPS_TRACE("dsps_poll");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_poll: null context%s");
     return serve_poll(c, ticket, timeout_us, latency_us);
 }
 
 int dsps_device_error(dsps_ctx *ctx, dsps_stream_t stream) {
+    DSPS_TRACE("dsps_device_error");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_device_error: null context%s");
     DSPS_CUDA(cudaSetDevice(c->device));
@@ -735,6 +753,7 @@ int dsps_device_error(dsps_ctx *ctx, dsps_stream_t stream) {
 }
 
 int dsps_profile_enable(dsps_ctx *ctx, int32_t enable) {
+    DSPS_TRACE("dsps_profile_enable");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return fail(DSPS_ERR_INVALID_ARG, "dsps_profile_enable: null context%s");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -743,6 +762,7 @@ int dsps_profile_enable(dsps_ctx *ctx, int32_t enable) {
 }
 
 int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out) {
+    DSPS_TRACE("dsps_profile_read");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !out) return fail(DSPS_ERR_INVALID_ARG, "dsps_profile_read: null argument%s");
     std::lock_guard<std::mutex> lk(c->mu);

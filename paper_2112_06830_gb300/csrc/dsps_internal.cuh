@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdint>
 #include <mutex>
 #include <vector>
@@ -13,6 +15,17 @@
 #include "../../include/dsps.h"
 
 namespace dsps {
+
+// Tracing: an NVTX range named after the ABI function around each call (the
+// header-only NVTX 3; it costs a branch unless a profiler or an NVTX tool is
+// attached, which then sees every library call on the host timeline).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define DSPS_TRACE(name) ::dsps::NvtxRange dsps_trace_range_(name)
 
 constexpr int NPAR = DSPS_NPAR;
 constexpr int NGRAD = DSPS_NGRAD;

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "dsps_internal.cuh"
+#include "serve_host.h"
 
 namespace dsps {
 
@@ -44,56 +45,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int64_t PIECE_MAX = 65536;
 
-// First-fit allocator over one block, 256-byte granules, coalescing frees.
-class Arena {
-public:
-    void reset(unsigned char *base, size_t bytes) {
-        base_ = base;
-        free_.clear();
-        if (bytes) free_[0] = bytes;
-        total_ = bytes;
-    }
-    unsigned char *alloc(size_t bytes) {
-        bytes = (bytes + 255) & ~(size_t)255;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                const size_t off = it->first, sz = it->second;
-                free_.erase(it);
-                if (sz > bytes) free_[off + bytes] = sz - bytes;
-                used_[off] = bytes;
-                return base_ + off;
-            }
-        }
-        return nullptr;
-    }
-    void release(unsigned char *p) {
-        if (!p) return;
-        const size_t off = (size_t)(p - base_);
-        auto u = used_.find(off);
-        if (u == used_.end()) return;
-        size_t sz = u->second;
-        used_.erase(u);
-        auto nx = free_.lower_bound(off);
-        if (nx != free_.end() && off + sz == nx->first) {
-            sz += nx->second;
-            nx = free_.erase(nx);
-        }
-        if (nx != free_.begin()) {
-            auto pv = std::prev(nx);
-            if (pv->first + pv->second == off) {
-                pv->second += sz;
-                return;
-            }
-        }
-        free_[off] = sz;
-    }
-    size_t total() const { return total_; }
-
-private:
-    unsigned char *base_ = nullptr;
-    size_t total_ = 0;
-    std::map<size_t, size_t> free_, used_;
-};
+using serve_host::Arena;
 
 struct Req {
     uint64_t ticket = 0;
@@ -166,11 +118,9 @@ struct Serve {
 namespace {
 
 void parse_faults(Serve *s) {
-    const char *f = std::getenv("DSPS_SERVE_FAULT");
-    if (!f) return;
-    std::string v(f);
-    if (v.rfind("fail_batch:", 0) == 0) s->fault_fail_batch = std::atoll(v.c_str() + 11);
-    if (v.rfind("delay_us:", 0) == 0) s->fault_delay_us = std::atoll(v.c_str() + 9);
+    const serve_host::FaultSpec f = serve_host::parse_faults(std::getenv("DSPS_SERVE_FAULT"));
+    s->fault_fail_batch = f.fail_batch;
+    s->fault_delay_us = f.delay_us;
 }
 
 }  // namespace
@@ -340,18 +290,14 @@ bool Serve::try_launch(std::unique_lock<std::mutex> &lk) {
     b.precision = head.req->r.precision;
     b.grad = head.req->r.want_grad ? 1 : 0;
     b.Q = head.req->Q;
-    std::vector<size_t> take;
-    int64_t G = 0;
+    std::vector<serve_host::PieceKey> keys(pending.size());
     for (size_t i = 0; i < pending.size(); ++i) {
-        const Piece &p = pending[i];
-        if (p.req->r.set_id != b.set_id || p.req->r.precision != b.precision ||
-            (p.req->r.want_grad ? 1 : 0) != b.grad)
-            continue;
-        if (G + p.n > PIECE_MAX) break;
-        take.push_back(i);
-        G += p.n;
-        b.any_host = b.any_host || !p.req->dev;
+        const dsps_request &r = pending[i].req->r;
+        keys[i] = {r.set_id, r.precision, r.want_grad ? 1 : 0, pending[i].n};
     }
+    int64_t G = 0;
+    const std::vector<size_t> take = serve_host::pick_batch(keys, PIECE_MAX, &G);
+    for (size_t i : take) b.any_host = b.any_host || !pending[i].req->dev;
     const int64_t Gpad = (G + 127) / 128 * 128;
     unsigned char *d = dev.alloc(dev_bytes(Gpad, b.Q, b.grad));
     if (!d) return false;    // admission by memory: wait for a batch to finish

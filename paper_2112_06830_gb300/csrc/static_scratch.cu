@@ -70,6 +70,7 @@ int64_t max_rows(int K_pad) {
 
 extern "C" int dsps_photometry_fp32_static(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id,
                                            float *mags, dsps_stream_t stream) {
+    DSPS_TRACE("dsps_photometry_fp32_static");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || n_gal < 0 || (n_gal > 0 && (!params || !mags))) {
         set_last_error("dsps_photometry_fp32_static: bad argument");

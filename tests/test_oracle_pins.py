@@ -604,3 +604,35 @@ def test_salim_curve_at_v_is_av_for_every_delta():
         for l in (1200.0, 3000.0, 9000.0):
             fd = (oracle.dust_curve(g, l, d + 1e-6)[0] - oracle.dust_curve(g, l, d - 1e-6)[0]) / 2e-6
             assert oracle.dust_curve(g, l, d)[1] == pytest.approx(fd, rel=1e-7)
+
+
+# ------------------------------------------------------------ domain of the model
+
+def test_out_of_domain_galaxies_give_nan_and_leave_the_rest_alone():
+    """Outside the forward model's domain (z <= 0 or not finite, MDF width <= 0;
+    the library's own domain) every output of that galaxy is NaN and its
+    neighbours are untouched.  z <= -1 puts the cosmology integrals' limits
+    outside the reals; the oracle must not evaluate them (it returns at once)."""
+    import time
+    g = synth.make_ssp(synth.GridSpec(9, 5, 120, 1e3, 1e5), 0)
+    grid = oracle.Grid(g.log_age_yr, g.lgz, g.lam, g.l_ssp, sfh_model=1)
+    F = oracle.Filters(synth.make_filters(3))
+    p = synth.make_population(1, 9, 2)
+    good = p.copy()
+    bad_z = [0.0, -0.5, -1.0, -2.0, np.nan, np.inf]
+    for k, z in enumerate(bad_z):
+        p[11, k] = z
+    p[6, 6] = 0.0                                      # zero MDF width
+    t0 = time.perf_counter()
+    m = oracle.mags(grid, F, p)
+    w = oracle.weights(grid, p)
+    m2, pb = oracle.mags_vjp(grid, F, p, np.ones((9, 3)))
+    ew = oracle.line_ew(grid, p, 5007.0, 40.0, 300.0)
+    sp = oracle.spectra(grid, p)
+    assert time.perf_counter() - t0 < 30.0
+    bad = list(range(7))
+    assert np.isnan(m[bad]).all() and np.isnan(w[bad]).all() and np.isnan(pb[:, bad]).all()
+    assert np.isnan(ew[bad]).all() and np.isnan(sp[bad]).all() and np.isnan(m2[bad]).all()
+    ok = [7, 8]
+    np.testing.assert_array_equal(m[ok], oracle.mags(grid, F, good)[ok])
+    assert np.isfinite(pb[:, ok]).all()
