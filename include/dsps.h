@@ -200,10 +200,20 @@ typedef struct {
                                   returns DSPS_ERR_UNSUPPORTED; default 0        */
     double dust_agedep_x0;     /* transition centre [log10 yr] and width h [dex], */
     double dust_agedep_h;      /* h > 0 (defaults 7, 0.1: the birth-cloud age)    */
+    int32_t agedep_fused;      /* with dust_agedep, DSPS_PREC_BF16X3 magnitudes:
+                                  1 (default): every group of age bins sharing a
+                                  curve contracted in one launch, each group's
+                                  attenuated spectrum summed on chip before one
+                                  filter integral (grids without a nebular axis,
+                                  n_z <= 32, n_age <= 128); 0: one contraction
+                                  and filter integral per group.  The two agree
+                                  to the split-bf16 rounding (different
+                                  summation order).                            */
 } dsps_opts;
 
 /* Fills *o with the defaults above (device 0, max_chunk 262144,
- * hbm_budget 8 GiB, 4 streams, z_max 10, band_skip 1, linear MDF mean). */
+ * hbm_budget 8 GiB, 4 streams, z_max 10, band_skip 1, linear MDF mean,
+ * agedep_fused 1). */
 void dsps_default_opts(dsps_opts *o);
 
 /* Creates a context on o->device: uploads the SSP block (FP32 copy, and the

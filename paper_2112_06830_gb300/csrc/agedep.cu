@@ -481,13 +481,34 @@ int run_photometry_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const f
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;
     const bool tc = precision == DSPS_PREC_BF16X3;
+    // split-bf16: every group in one launch (agedep_tc.cu) where the grid allows
+    const bool fused = tc && c->opts.agedep_fused && agedep_fused_ok(*c);
     for (int64_t g0 = 0; g0 < n_gal; g0 += w.cap) {
         const int64_t n = n_gal - g0 < w.cap ? n_gal - g0 : w.cap;
-        cudaError_t e = groups_forward(c, w, n_gal, g0, n, params, fs, tc, false, s, prof);
-        if (e == cudaSuccess) {
-            ProfScope ps(*c, 0, s, prof);
-            e = launch_final(*c, w, fs, n, true, hist ? nullptr : mags + g0 * fs.Q, hist, nullptr, nullptr, n_gal, g0,
-                             s);
+        cudaError_t e = cudaSuccess;
+        if (fused) {
+            int parts = 0;
+            {
+                ProfScope ps(*c, 0, s, prof);
+                e = launch_zsort(*c, w, params, n_gal, g0, n, s);
+                if (e == cudaSuccess)
+                    e = launch_weights(*c, w, W_OMEGA_BF16X2_AB, params, n_gal, g0, n, nullptr, s, true);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 2, s, prof);
+                e = launch_phot_tc_groups(*c, w, fs, n, &parts, s);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 0, s, prof);
+                e = launch_combine(*c, w, fs, n, parts, hist ? nullptr : mags + g0 * fs.Q, s, hist);
+            }
+        } else {
+            e = groups_forward(c, w, n_gal, g0, n, params, fs, tc, false, s, prof);
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 0, s, prof);
+                e = launch_final(*c, w, fs, n, true, hist ? nullptr : mags + g0 * fs.Q, hist, nullptr, nullptr, n_gal,
+                                 g0, s);
+            }
         }
         if (e != cudaSuccess) return fail_cuda(e);
     }

@@ -1,0 +1,468 @@
+// agedep_tc.cu -- age-dependent dust (Sec. 3.4.1, Eq. agedep_dust_csp): the
+// split-bf16 forward of every dust group in one tcgen05 launch.
+//
+// With a curve per age bin the spectrum of a galaxy is
+//   L(lam) = sum_g F_g(lam) S_g(lam),   S_g = sum_{i in g} sum_j omega_ij L_ij,
+// F_g = 10^(-0.4 Av_g c_g(lam)) the attenuation of group g (the age bins that
+// share one curve: Av_g = (1 - T_g) Av_young + T_g Av_old, delta_g likewise).
+// The weights of all ages come in the age-block order (weights kernel, mode
+// W_OMEGA_BF16X2_AB): column ka = i * 32 + j, so that each age bin is one
+// 32-wide K block and a group is a contiguous run of blocks.  Per work unit (a
+// 128-galaxy tile and one of TC_PARTS interleaved subsets of its 128-wide
+// wavelength tiles) and per wavelength tile, the groups are contracted one after
+// another -- only the age blocks the tile's mask holds (ages where some galaxy
+// of the tile has a non-zero weight); a group without such a block is skipped by
+// every role -- into one of two TMEM accumulators (128 columns each).  The
+// epilogue warps read the group's block of S_g, multiply it by F_g of each row
+// and add it into a running sum held in a third TMEM region (tcgen05.st); after
+// the last group the running sum goes once through the redshifted filter
+// integral (epilogue.cuh, without dust: it is already in the sum).  So each
+// element pays one light attenuation step per group and one filter reduction,
+// where one launch per group paid the whole epilogue per group.
+//
+// Warp roles as in phot_tc.cu: warp 0 TMA producer (4-stage ring of {W_hi,
+// W_lo, L_hi, L_lo} 32-wide K slices, 64-byte swizzle), warp 1 TMEM allocator
+// and single-thread MMA issuer (per K slice six 128x128x16 tcgen05.mma
+// kind::f16: hi.hi, hi.lo, lo.hi, two K steps), warps 2..9 epilogue (two warps
+// per TMEM lane quadrant, 64 columns each).  Every mbarrier wait is bounded; on
+// expiry the kernel records DERR_TIMEOUT, lets its copies and MMAs land, frees
+// TMEM and returns.
+#include <cudaTypedefs.h>
+
+#include "dsps_internal.cuh"
+#include "epilogue.cuh"
+#include "tc_common.cuh"
+
+namespace dsps {
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128, BN = 128, BK = KBLOCK;
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int NUM_EPI_WARPS = 8;
+constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
+constexpr uint32_t TMEM_COLS = 512;          // accumulators at 0 and BN, running sum at 2 BN
+constexpr uint32_t RUN_COL = 2 * BN;
+constexpr int QMAX = 16;
+constexpr int MAX_GROUPS = 128;
+constexpr size_t BAR_BYTES = 1024;
+constexpr size_t COMB_BYTES = (size_t)BM * QMAX * 4;
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + COMB_BYTES;
+constexpr uint32_t IDESC = make_idesc(BM, BN);
+
+struct GArgs {
+    const float *aux;              // Av_young, delta_young, s, valid, Av_old, delta_old (weights mode AB)
+    const int2 *trange;            // per-tile redshift-shift ranges
+    const unsigned *kmask;         // per-tile masks of the age blocks (4 words)
+    const float4 *tab;
+    ColConst cc;
+    int m_last, n_mtiles, n_ntiles, parts, n_units;
+    int band_skip, m_nz_lo, m_nz_hi, dust_law, bump;
+    int n_groups;
+    short g_i0[MAX_GROUPS], g_i1[MAX_GROUPS];   // age bins [i0, i1) of each group
+    float g_T[MAX_GROUPS];                      // weight of the old-star dust values
+    int64_t n;
+    int *sched;                    // unit counter, zero at launch
+    float *partial;                // [parts][n][4*Q4]
+    unsigned *err;
+};
+
+// Wavelength tiles [nt0, nt1) of tile mt (as phot_tc.cu, with 128-wide tiles)
+// and its mask of age blocks; an empty tile does no work.
+__device__ __forceinline__ void tile_ranges(const GArgs &a, int mt, int &nt0, int &nt1, uint4 &km) {
+    nt0 = 0;
+    nt1 = a.n_ntiles;
+    const unsigned *m = a.kmask + (size_t)mt * 4;
+    km = make_uint4(__ldg(m), __ldg(m + 1), __ldg(m + 2), __ldg(m + 3));
+    const int2 r = a.trange[mt];
+    if (r.y < r.x || a.m_nz_hi < a.m_nz_lo || (km.x | km.y | km.z | km.w) == 0u) {
+        nt1 = nt0;
+        return;
+    }
+    if (!a.band_skip) return;
+    const int n_lo = a.m_nz_lo - r.y - 2;
+    const int n_hi = a.m_nz_hi - r.x + 1;
+    if (n_hi < 0) { nt1 = nt0; return; }
+    nt0 = n_lo <= 0 ? 0 : n_lo / BN;
+    nt1 = min(a.n_ntiles, n_hi / BN + 1);
+    if (nt1 < nt0) nt1 = nt0;
+}
+
+__device__ __forceinline__ unsigned mask_word(const uint4 &km, int w) {
+    return w == 0 ? km.x : w == 1 ? km.y : w == 2 ? km.z : km.w;
+}
+
+// The tile's age blocks of group g in increasing order (a.n_groups..: none).
+struct GroupBlocks {
+    uint4 km;
+    int b, hi;
+    __device__ __forceinline__ GroupBlocks(const uint4 &k, int i0, int i1) : km(k), b(i0 - 1), hi(i1) {}
+    // next set block in (b, hi), or hi
+    __device__ __forceinline__ int next() {
+        for (++b; b < hi; ++b) {
+            const unsigned w = mask_word(km, b >> 5) >> (b & 31);
+            if (w & 1u) return b;
+            if (w == 0u) b = (b | 31);   // rest of this word empty
+        }
+        return hi;
+    }
+};
+
+__device__ __forceinline__ bool group_present(const uint4 &km, int i0, int i1) {
+    for (int w = i0 >> 5; w <= (i1 - 1) >> 5; ++w) {
+        unsigned m = mask_word(km, w);
+        const int lo = max(i0 - 32 * w, 0), hi = min(i1 - 32 * w, 32);
+        m &= (hi >= 32 ? ~0u : ((1u << hi) - 1u)) & (~0u << lo);
+        if (m) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int first_tile(int nt0, int part, int parts) {
+    return nt0 + ((part - nt0 % parts) % parts + parts) % parts;
+}
+
+template <int Q4>
+__global__ void __launch_bounds__(THREADS, 1)
+phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                      const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+                      const __grid_constant__ GArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + (size_t)STAGES * STAGE_BYTES);
+    const uint32_t full0 = smem_u32(bars);
+    const uint32_t empty0 = smem_u32(bars + STAGES);
+    const uint32_t accf0 = smem_u32(bars + 2 * STAGES);
+    const uint32_t acce0 = smem_u32(bars + 2 * STAGES + 2);
+    const uint32_t ebar = smem_u32(bars + 2 * STAGES + 4);
+    const uint32_t drain = smem_u32(bars + 2 * STAGES + 5);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 6);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    UnitRing ring;
+    ring.full0 = smem_u32(bars + 2 * STAGES + 8);
+    ring.empty0 = smem_u32(bars + 2 * STAGES + 8 + UNIT_RING);
+    ring.slot = reinterpret_cast<volatile int *>(bars + 2 * STAGES + 8 + 2 * UNIT_RING);
+    float *comb = reinterpret_cast<float *>(sm + (size_t)STAGES * STAGE_BYTES + BAR_BYTES);
+    const uint32_t sbase = smem_u32(sm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(accf0 + 8 * i, 1);
+            mbar_init(acce0 + 8 * i, NUM_EPI_WARPS);
+        }
+        mbar_init(ebar, NUM_EPI_WARPS);
+        mbar_init(drain, 1);
+        for (int i = 0; i < UNIT_RING; ++i) {
+            mbar_init(ring.full0 + 8 * i, 1);
+            mbar_init(ring.empty0 + 8 * i, 1 + NUM_EPI_WARPS);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int armed[STAGES];
+            for (int s = 0; s < STAGES; ++s) armed[s] = -1;
+            bool ok = true;
+            while (ok) {
+                int u;
+                if (!ring_claim(ring, a.sched, a.n_units, u, abort_flag, a.err) || u < 0) break;
+                const int mt = u / a.parts, part = u - mt * a.parts;
+                int nt0, nt1;
+                uint4 km;
+                tile_ranges(a, mt, nt0, nt1, km);
+                for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts)
+                    for (int g = 0; ok && g < a.n_groups; ++g) {
+                        GroupBlocks it(km, a.g_i0[g], a.g_i1[g]);
+                        for (int kb = it.next(); kb < it.hi; kb = it.next()) {
+                            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, a.err)) { ok = false; break; }
+                            const uint32_t fb = full0 + 8 * stage;
+                            const uint32_t st = sbase + stage * STAGE_BYTES;
+                            mbar_expect_tx(fb, STAGE_BYTES);
+                            tma_load_2d(st, &tmA_hi, fb, kb * BK, mt * BM);
+                            tma_load_2d(st + A_BYTES, &tmA_lo, fb, kb * BK, mt * BM);
+                            tma_load_2d(st + 2 * A_BYTES, &tmB_hi, fb, kb * BK, nt * BN);
+                            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmB_lo, fb, kb * BK, nt * BN);
+                            armed[stage] = (int)phase;
+                            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                        }
+                    }
+            }
+            for (int s = 0; s < STAGES; ++s)
+                if (armed[s] >= 0) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(full0 + 8 * s, (uint32_t)armed[s]) && clock64() - t0 < WAIT_LIMIT) {
+                    }
+                }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int stage = 0, as = 0;
+            uint32_t phase = 0, aphase = 0;
+            bool ok = true;
+            while (ok) {
+                int u;
+                if (!ring_next(ring, u, abort_flag, a.err) || u < 0) break;
+                const int mt = u / a.parts, part = u - mt * a.parts;
+                int nt0, nt1;
+                uint4 km;
+                tile_ranges(a, mt, nt0, nt1, km);
+                for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts)
+                    for (int g = 0; ok && g < a.n_groups; ++g) {
+                        if (!group_present(km, a.g_i0[g], a.g_i1[g])) continue;
+                        if (!mbar_wait(acce0 + 8 * as, aphase ^ 1u, abort_flag, a.err)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t d = tmem_base + (uint32_t)(as * BN);
+                        GroupBlocks it(km, a.g_i0[g], a.g_i1[g]);
+                        bool first = true;
+                        for (int kb = it.next(); kb < it.hi; kb = it.next()) {
+                            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, a.err)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint32_t st = sbase + stage * STAGE_BYTES;
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk) {
+                                const uint64_t ah = sdesc_sw64(st + kk * 32);
+                                const uint64_t al = sdesc_sw64(st + A_BYTES + kk * 32);
+                                const uint64_t bh = sdesc_sw64(st + 2 * A_BYTES + kk * 32);
+                                const uint64_t bl = sdesc_sw64(st + 2 * A_BYTES + B_BYTES + kk * 32);
+                                mma_bf16_desc(d, ah, bh, IDESC, (!first || kk != 0) ? 1u : 0u);
+                                mma_bf16_desc(d, ah, bl, IDESC, 1u);
+                                mma_bf16_desc(d, al, bh, IDESC, 1u);
+                            }
+                            mma_commit(empty0 + 8 * stage);
+                            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                            first = false;
+                        }
+                        if (!ok) break;
+                        mma_commit(accf0 + 8 * as);
+                        if (++as == 2) { as = 0; aphase ^= 1u; }
+                    }
+            }
+            mma_commit(drain);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int qd = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row = qd * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+        int as = 0;
+        uint32_t aphase = 0, ephase = 0;
+        bool ok = true;
+        while (ok) {
+            int u = -1, have = 1;
+            if (lane == 0) have = ring_next(ring, u, abort_flag, a.err) ? 1 : 0;
+            have = __shfl_sync(0xffffffffu, have, 0);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (!have || u < 0) break;
+            const int mt = u / a.parts, part = u - mt * a.parts;
+            int nt0, nt1;
+            uint4 km;
+            tile_ranges(a, mt, nt0, nt1, km);
+            const int64_t rowg = (int64_t)mt * BM + row;
+            // the row's dust values and redshift interpolation
+            RowConst rc = load_row_const(a.aux, rowg, a.n);
+            float avy = 0.f, dly = 0.f, avo = 0.f, dlo = 0.f;
+            if (rowg < a.n) {
+                const float *ax = a.aux + rowg * AUX_STRIDE;
+                avy = ax[0];
+                dly = ax[1];
+                avo = ax[4];
+                dlo = ax[5];
+            }
+            float acc[4 * Q4];
+#pragma unroll
+            for (int q = 0; q < 4 * Q4; ++q) acc[q] = 0.f;
+            for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
+                const int nb = nt * BN + half * (BN / 2);
+                bool any = false;   // the running sum holds a group already
+                for (int g = 0; ok && g < a.n_groups; ++g) {
+                    if (!group_present(km, a.g_i0[g], a.g_i1[g])) continue;
+                    int got = 1;
+                    if (lane == 0) got = mbar_wait(accf0 + 8 * as, aphase, abort_flag, a.err) ? 1 : 0;
+                    got = __shfl_sync(0xffffffffu, got, 0);
+                    if (!got) { ok = false; break; }
+                    tc_fence_after();
+                    // the group's curve (Sec. 3.4.1), as the weights kernel forms it
+                    const float T = a.g_T[g];
+                    const float Avg = group_dust_value(T, avy, avo), dlg = group_dust_value(T, dly, dlo);
+                    RowConst rg = rc;
+                    rg.alpha = -0.4f * 3.32192809488736235f * Avg;
+                    rg.beta = a.dust_law == DSPS_DUST_SALIM ? dlg : dlg - 0.7f;
+                    rg.e = a.bump ? (0.85f - 1.9f * dlg) * (1.f / 4.05f) : 0.f;
+                    const uint32_t tacc = tmem_base + lane_base + (uint32_t)(as * BN + half * (BN / 2));
+                    const uint32_t trun = tmem_base + lane_base + RUN_COL + (uint32_t)(half * (BN / 2));
+#pragma unroll 1
+                    for (int c = 0; c < BN / 64; ++c) {
+                        uint32_t r[32], s[32];
+                        tmem_ld32(tacc + c * 32, r);
+                        if (c == BN / 64 - 1) {
+                            // this warp's reads of the accumulator are done
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(acce0 + 8 * as);
+                        }
+                        if (any) tmem_ld32(trun + c * 32, s);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float v = rc.valid ? __uint_as_float(r[j]) * dust_factor(a.cc, rg, nb + c * 32 + j)
+                                                     : 0.f;
+                            s[j] = __float_as_uint(any ? __uint_as_float(s[j]) + v : v);
+                        }
+                        tmem_st32(trun + c * 32, s);
+                    }
+                    any = true;
+                    if (++as == 2) { as = 0; aphase ^= 1u; }
+                }
+                if (!ok) break;
+                if (!any) continue;
+                // the attenuated spectrum of the tile: one filter integral
+                const uint32_t trun = tmem_base + lane_base + RUN_COL + (uint32_t)(half * (BN / 2));
+                Slide sl;
+#pragma unroll 1
+                for (int c = 0; c < BN / 64; ++c) {
+                    uint32_t r[32];
+                    tmem_ld32(trun + c * 32, r);
+                    if (rc.valid) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            epi_node_plain<Q4>(acc, sl, __uint_as_float(r[j]), nb + c * 32 + j, rc, a.cc, a.tab,
+                                               a.m_last);
+                    }
+                }
+                if (rc.valid) epi_close<Q4>(acc, sl, nb + BN / 2, rc, a.tab, a.m_last);
+            }
+            if (!ok) break;
+            // combine the two column halves of each row (bounded barrier)
+            float *cr = comb + row * QMAX;
+            if (half == 1)
+#pragma unroll
+                for (int q = 0; q < 4 * Q4; ++q) cr[q] = acc[q];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ebar);
+            int got = 1;
+            if (lane == 0) got = mbar_wait(ebar, ephase, abort_flag, a.err) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            ephase ^= 1u;
+            if (!got) break;
+            if (half == 0 && rowg < a.n) {
+                float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)part * a.n + rowg) * (4 * Q4));
+#pragma unroll
+                for (int qq = 0; qq < Q4; ++qq)
+                    dst[qq] = make_float4(acc[4 * qq] + cr[4 * qq], acc[4 * qq + 1] + cr[4 * qq + 1],
+                                          acc[4 * qq + 2] + cr[4 * qq + 2], acc[4 * qq + 3] + cr[4 * qq + 3]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ebar);
+            got = 1;
+            if (lane == 0) got = mbar_wait(ebar, ephase, abort_flag, a.err) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            ephase ^= 1u;
+            if (!got) break;
+        }
+    }
+
+    __syncwarp();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+template <int Q4>
+cudaError_t launch_q4(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
+                      const GArgs &a, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(phot_tc_groups_kernel<Q4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    phot_tc_groups_kernel<Q4><<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool agedep_fused_ok(const Ctx &c) {
+    return c.KA_pad > 0 && c.opts.dust_agedep && c.n_u == 1 && (int)c.dust_groups.size() <= MAX_GROUPS &&
+           c.kmask_words == 4;
+}
+
+cudaError_t launch_phot_tc_groups(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int *parts,
+                                  cudaStream_t s) {
+    *parts = TC_PARTS;
+    if (n <= 0) return cudaSuccess;
+    if (fs.Q > QMAX || !agedep_fused_ok(c)) return cudaErrorInvalidValue;
+    CUtensorMap ah, al, bh, bl;
+    if (!make_tmap(&ah, w.whi, (uint64_t)c.KA_pad, (uint64_t)n, BM) ||
+        !make_tmap(&al, w.wlo, (uint64_t)c.KA_pad, (uint64_t)n, BM) ||
+        !make_tmap(&bh, c.d_Lab_hi, (uint64_t)c.KA_pad, (uint64_t)c.N_pad, BN) ||
+        !make_tmap(&bl, c.d_Lab_lo, (uint64_t)c.KA_pad, (uint64_t)c.N_pad, BN))
+        return cudaErrorInvalidValue;
+    GArgs a{};
+    a.aux = w.aux;
+    a.trange = w.trange;
+    a.kmask = w.kmask;
+    a.tab = reinterpret_cast<const float4 *>(fs.d_tab);
+    a.cc = make_col_const(c);
+    a.m_last = fs.m_rows - 1;
+    a.n_mtiles = (int)((n + BM - 1) / BM);
+    a.n_ntiles = c.N_pad / BN;
+    a.parts = TC_PARTS;
+    a.n_units = a.n_mtiles * TC_PARTS;
+    a.band_skip = c.opts.band_skip ? 1 : 0;
+    a.m_nz_lo = fs.m_nz_lo;
+    a.m_nz_hi = fs.m_nz_hi;
+    a.dust_law = c.opts.dust_law;
+    a.bump = c.opts.dust_bump ? 1 : 0;
+    a.n_groups = (int)c.dust_groups.size();
+    for (int g = 0; g < a.n_groups; ++g) {
+        a.g_i0[g] = (short)c.dust_groups[g].i0;
+        a.g_i1[g] = (short)c.dust_groups[g].i1;
+        a.g_T[g] = c.dust_groups[g].T;
+    }
+    a.n = n;
+    a.sched = w.sched;
+    a.partial = w.partial;
+    a.err = c.d_err;
+    const int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;
+    cudaError_t e = cudaMemsetAsync(w.sched, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    switch (fs.Q4) {
+    case 1: return launch_q4<1>(ah, al, bh, bl, a, grid, s);
+    case 2: return launch_q4<2>(ah, al, bh, bl, a, grid, s);
+    case 3: return launch_q4<3>(ah, al, bh, bl, a, grid, s);
+    default: return launch_q4<4>(ah, al, bh, bl, a, grid, s);
+    }
+}
+
+}  // namespace dsps

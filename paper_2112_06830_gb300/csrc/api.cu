@@ -136,7 +136,8 @@ void free_ctx(Ctx *c) {
     for (auto &ls : c->lines) cudaFree(ls.d_tab);
     void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_k0, c->d_edges, c->d_einh, c->d_bwidth,
                     c->d_zedge, c->d_uedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->ws.ewacc, c->d_err, c->d_stats,
-                    c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d, c->d_hio};
+                    c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d, c->d_hio, c->d_Lab_hi, c->d_Lab_lo,
+                    c->d_wmul_ab};
     for (void *p : ptrs) cudaFree(p);
     for (auto &r : c->prof_recs) {
         cudaEventDestroy(r.a);
@@ -185,6 +186,7 @@ void dsps_default_opts(dsps_opts *o) {
     o->dust_agedep = 0;
     o->dust_agedep_x0 = 7.0;
     o->dust_agedep_h = 0.1;
+    o->agedep_fused = 1;
 }
 
 namespace {
@@ -231,7 +233,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     }
     if (opts.sfh_model < 0 || opts.sfh_model > 2 || opts.mdf_kernel < 0 || opts.mdf_kernel > 1 ||
         opts.mdf_mean < 0 || opts.mdf_mean > 1 || opts.dust_bump < 0 || opts.dust_bump > 1 || opts.dust_law < 0 ||
-        opts.dust_law > 1)
+        opts.dust_law > 1 || opts.agedep_fused < 0 || opts.agedep_fused > 1)
         return fail(DSPS_ERR_INVALID_ARG, "dsps_create: unknown model switch%s");
     if (opts.dust_agedep < 0 || opts.dust_agedep > 1 ||
         (opts.dust_agedep && !(opts.dust_agedep_h > 0 && std::isfinite(opts.dust_agedep_x0))))
@@ -294,6 +296,11 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     c->SEC = (c->n_z * c->A_pad + KBLOCK - 1) / KBLOCK * KBLOCK;
     c->KZ_pad = (n_u * c->SEC + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
     c->kmask_words = (c->SEC / KBLOCK + 31) / 32;
+    if (opts.dust_agedep && n_u == 1 && g->n_z <= KBLOCK && g->n_age <= 128) {
+        // age-block order of the fused age-dependent dust forward: one mask bit per age
+        c->KA_pad = (g->n_age * KBLOCK + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
+        if (c->kmask_words < 4) c->kmask_words = 4;
+    }
     c->N_pad = (c->n_lam + 1 + N_ALIGN - 1) / N_ALIGN * N_ALIGN;   // >= n_lam + 1: room for the closing term
     c->n_t = g->n_t;
     c->t0 = g->t0_gyr;
@@ -350,6 +357,11 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_Ld32, (size_t)c->KZ_pad * c->N_pad));
     chk(dmalloc(&c->d_wmul_d, (size_t)c->KZ_pad));
     chk(dmalloc(&c->d_L_lo, (size_t)c->KZ_pad * c->N_pad));
+    if (c->KA_pad) {
+        chk(dmalloc(&c->d_Lab_hi, (size_t)c->KA_pad * c->N_pad));
+        chk(dmalloc(&c->d_Lab_lo, (size_t)c->KA_pad * c->N_pad));
+        chk(dmalloc(&c->d_wmul_ab, (size_t)c->KA_pad));
+    }
     if (rc != DSPS_OK) { free_ctx(c); return rc; }
     c->ws = workspace_carve(*c, c->d_ws_block, c->chunk, false);
 

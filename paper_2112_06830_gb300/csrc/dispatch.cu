@@ -17,7 +17,8 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t workspace_bytes(const Ctx &c, int64_t rows, bool adjoint) {
     const size_t R = (size_t)rows;
     const size_t W32 = (size_t)(c.K_pad > c.KZ_pad ? c.K_pad : c.KZ_pad);
-    size_t b = al256(R * W32 * 4) + 2 * al256(R * c.KZ_pad * 2) + al256(R * AUX_STRIDE * 4) + al256(R * 4) + al256(R * sizeof(GalPrep)) +
+    const size_t WZ = (size_t)(c.KA_pad > c.KZ_pad ? c.KA_pad : c.KZ_pad);   // split-weight row (kz or age-block order)
+    size_t b = al256(R * W32 * 4) + 2 * al256(R * WZ * 2) + al256(R * AUX_STRIDE * 4) + al256(R * 4) + al256(R * sizeof(GalPrep)) +
                2 * al256(R * 4) + al256((size_t)ZSORT_BUCKETS * 4) + al256((size_t)TC_PARTS * R * 3 * QSTRIDE_MAX * 4) +
                al256(R * QSTRIDE_MAX * 4) + 2 * al256((R / 128 + 1) * sizeof(int2)) + al256((R / 128 + 1) * c.kmask_words * 4) + al256(sizeof(int));
     if (adjoint) b += al256(R * c.N_pad * 4);
@@ -36,8 +37,9 @@ Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint) 
     Workspace w;
     w.cap = rows;
     w.w32 = static_cast<float *>(take(R * (size_t)(c.K_pad > c.KZ_pad ? c.K_pad : c.KZ_pad) * 4));
-    w.whi = static_cast<__nv_bfloat16 *>(take(R * c.KZ_pad * 2));
-    w.wlo = static_cast<__nv_bfloat16 *>(take(R * c.KZ_pad * 2));
+    const size_t WZ = (size_t)(c.KA_pad > c.KZ_pad ? c.KA_pad : c.KZ_pad);
+    w.whi = static_cast<__nv_bfloat16 *>(take(R * WZ * 2));
+    w.wlo = static_cast<__nv_bfloat16 *>(take(R * WZ * 2));
     w.aux = static_cast<float *>(take(R * AUX_STRIDE * 4));
     w.magoff = static_cast<float *>(take(R * 4));
     w.prep = static_cast<GalPrep *>(take(R * sizeof(GalPrep)));

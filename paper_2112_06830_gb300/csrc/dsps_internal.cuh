@@ -206,6 +206,14 @@ struct Ctx {
     int grow_dust_old = -1;                 //   and its gradient row
     int row_sfr = -1, grow_sfr = -1;        // tabulated SFH: rows of the node SFRs and of their gradient
     std::vector<DustGroup> dust_groups;     // age-dependent dust: the groups of age bins
+    // Age-dependent dust, fused split-bf16 forward (agedep_tc.cu): K in age
+    // blocks, column ka = i * KBLOCK + j (age i, metallicity j < n_z <= 32,
+    // the rest zero), rows of KA_pad = n_age * KBLOCK rounded up to K_ALIGN;
+    // built when the grid has no nebular axis and n_z <= KBLOCK (else 0).
+    int KA_pad = 0;
+    __nv_bfloat16 *d_Lab_hi = nullptr;      // [N_pad][KA_pad] row-scaled SSP hi, age-block order
+    __nv_bfloat16 *d_Lab_lo = nullptr;      // [N_pad][KA_pad] lo
+    float *d_wmul_ab = nullptr;             // [KA_pad] 2^E_k at column ka (0 at padding)
     int kmask_words = 0;                    // ceil(SEC / KBLOCK / 32)
     double t0 = 0, t1 = 0;
     double lnlam0 = 0, dlnlam = 0;
@@ -303,7 +311,12 @@ struct ProfScope {
 // ----------------------------------------------------------------------------
 // W_OMEGA_BF16X2_AGE1: the split weights of one age bin (an age-dependent dust
 // group of the transition), written only in the kz blocks holding that age.
-enum WeightsMode { W_MSUN = 0, W_OMEGA_F32 = 1, W_OMEGA_BF16X2 = 2, W_OMEGA_BF16X2_AGE1 = 3 };
+// W_OMEGA_BF16X2_AB: the split weights of all ages in the age-block order of
+// the fused age-dependent dust forward (Ctx::KA_pad), the tiles' K-block mask
+// holding one bit per age with a non-zero weight, and aux holding the young and
+// old dust values (agedep_tc.cu: Av_young, delta_young, s, valid, Av_old,
+// delta_old at entries 0, 1, 2, 3, 4, 5).
+enum WeightsMode { W_MSUN = 0, W_OMEGA_F32 = 1, W_OMEGA_BF16X2 = 2, W_OMEGA_BF16X2_AGE1 = 3, W_OMEGA_BF16X2_AB = 4 };
 
 // Bytes of a work space for `rows` galaxies (what = 1: forward only, 2: with adjoint).
 size_t workspace_bytes(const Ctx &c, int64_t rows, bool adjoint);
@@ -360,6 +373,16 @@ cudaError_t launch_phot_tc(const Ctx &c, const Workspace &w, const FilterSet &fs
                            cudaStream_t s, bool grad = false);
 
 cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp);
+
+// Age-dependent dust, fused split-bf16 forward (agedep_tc.cu): whether the
+// context has the age-block operands, and the contraction of every dust group
+// of each tile in one launch (each group's spectrum attenuated by its curve and
+// summed in TMEM, one filter integral), writing per-part filter sums for
+// launch_combine.  Needs the chunk sorted (launch_zsort) and its weights in the
+// W_OMEGA_BF16X2_AB form.
+bool agedep_fused_ok(const Ctx &c);
+cudaError_t launch_phot_tc_groups(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int *parts,
+                                  cudaStream_t s);
 
 // Adjoint (vjp.cu, vjp_tc.cu, weights.cu).
 cudaError_t launch_combine_grad(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts,

@@ -117,6 +117,27 @@ __device__ __forceinline__ void epi_node(float (&acc)[4 * Q4], Slide &sl, float 
     acc_row<Q4>(acc, tab, min(n + rc.i0, m_last), y);
 }
 
+// The attenuation of node n, F = 10^(-0.4 Av c_n) (Eq. attenuation) with the
+// curve of rc (c_n = u + e D0_n).
+__device__ __forceinline__ float dust_factor(const ColConst &cc, const RowConst &rc, int n) {
+    const float ell = fmaf((float)n, cc.dell, cc.ell0);
+    const float u = dust_pow(cc, rc, ell, n);
+    return exp2f(rc.alpha * dust_curve(cc, rc, u, n));
+}
+
+// One node of the sliding sum for a spectrum already attenuated (age-dependent
+// dust: each group's curve applied before the groups are summed).
+template <int Q4>
+__device__ __forceinline__ void epi_node_plain(float (&acc)[4 * Q4], Slide &sl, float S, int n, const RowConst &rc,
+                                               const ColConst &cc, const float4 *__restrict__ tab, int m_last) {
+    const float v = S * col_kappa(cc, n);
+    const float y = fmaf(rc.w[0], v, fmaf(rc.w[1], sl.v1, fmaf(rc.w[2], sl.v2, rc.w[3] * sl.v3)));
+    sl.v3 = sl.v2;
+    sl.v2 = sl.v1;
+    sl.v1 = v;
+    acc_row<Q4>(acc, tab, min(n + rc.i0, m_last), y);
+}
+
 // Closing rows of a run that ended at node b-1 (grid rows b+i0-1 .. b+i0+1).
 template <int Q4>
 __device__ __forceinline__ void epi_close(float (&acc)[4 * Q4], const Slide &sl, int b, const RowConst &rc,

@@ -1,11 +1,11 @@
 // phot_simt.cu -- FP32 SIMT form of the fused photometry kernel.
 //
 // S = omega . L (Eq. full_mdf) as a register-tiled FP32 GEMM: each CTA owns 128
-// galaxies and one of `parts` interleaved subsets of the 128-wide wavelength
+// galaxies and one of `parts` interleaved subsets of the 256-wide wavelength
 // tiles (tile nt belongs to part nt mod parts, as in the tensor-core form) and
 // walks its tiles -- with sorted rows, only those inside the row tile's
 // redshifted filter band (the others contribute exact zeros); after the K loop
-// of a tile the 128x128 block of S goes through shared memory to the epilogue,
+// of a tile the 128x256 block of S goes through shared memory to the epilogue,
 // where two threads per galaxy row apply dust, the redshifted filter lookup and
 // the wavelength reduction (epilogue.cuh).  Per-(galaxy, filter) sums stay in
 // registers across a CTA's tiles and are written per part (combined in a fixed
@@ -20,9 +20,14 @@ namespace dsps {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 16, THREADS = 256;
+// Tile: BM = 128 galaxies x BN = 256 wavelength nodes x BK = 16 per K step;
+// 256 threads, each an 8 x 16 register tile (rows ty*4 + {0..3, 64..67},
+// columns tx*4 + {0..3} + 64 m); one CTA per SM (181 KB of shared memory).
+constexpr int BM = 128, BN = 256, BK = 16, THREADS = 256;
+constexpr int TN4 = BN / 64;          // float4 column groups per thread
 constexpr int AS_LD = BM + 4;
 constexpr int CS_LD = BN + 1;
+constexpr int EPI_COLS = BN / 2;      // epilogue columns per thread (two threads per row)
 
 struct SArgs {
     const float *W;        // [n][K_pad]
@@ -54,10 +59,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int Q4, bool GRAD>
-__global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
-    __shared__ __align__(16) float As[2][BK][AS_LD];
-    __shared__ __align__(16) float Bs[2][BK][BN];
-    extern __shared__ float Cs[];  // [BM][CS_LD]
+__global__ void __launch_bounds__(THREADS, 1) phot_simt_kernel(SArgs a) {
+    // dynamic shared memory: the K-loop operands As [2][BK][AS_LD] and Bs
+    // [2][BK][BN], and, aliasing them after the K loop, the tile of S, Cs
+    // [BM][CS_LD] (barriers separate the two uses)
+    extern __shared__ __align__(16) float smem_f[];
+    float (*As)[BK][AS_LD] = reinterpret_cast<float (*)[BK][AS_LD]>(smem_f);
+    float (*Bs)[BK][BN] = reinterpret_cast<float (*)[BK][BN]>(smem_f + 2 * BK * AS_LD);
+    float *Cs = smem_f;
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -92,14 +101,14 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
     const int t0 = nbeg / BN;
     const int nfirst = (t0 + ((part - t0 % a.parts) % a.parts + a.parts) % a.parts) * BN;
     const int nstep = a.parts * BN;
-    if (a.steps && tid == 0 && nend > nfirst)
-        atomicAdd(a.steps, (unsigned long long)((nend - nfirst + nstep - 1) / nstep) * KT);
+    if (a.steps && tid == 0 && nend > nfirst)   // counted in 128 x 128 x 16 steps
+        atomicAdd(a.steps, (unsigned long long)((nend - nfirst + nstep - 1) / nstep) * KT * (BN / 128));
     for (int n0 = nfirst; n0 < nend; n0 += nstep) {
-        float c[8][8];
+        float c[8][4 * TN4];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) c[i][j] = 0.f;
+            for (int j = 0; j < 4 * TN4; ++j) c[i][j] = 0.f;
 
         // W (row-major per galaxy) through registers, transposed into As; the
         // SSP panel (row-major per k) straight into Bs with cp.async
@@ -112,7 +121,11 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
                 int64_t gr = m0 + row;
                 ra[t] = gr < a.n ? *reinterpret_cast<const float4 *>(a.W + gr * a.K_pad + k0 + kq)
                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-                int k = idx >> 5, nq = (idx & 31) * 4;
+            }
+#pragma unroll
+            for (int t = 0; t < BK * BN / 4 / THREADS; ++t) {
+                int idx = tid + t * THREADS;
+                int k = idx / (BN / 4), nq = (idx % (BN / 4)) * 4;
                 cp_async16(&Bs[buf][k][nq], a.L + (int64_t)(k0 + k) * a.N_pad + n0 + nq);
             }
             cp_async_commit();
@@ -138,16 +151,22 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
             if (kt + 1 < KT) gload(a.k_lo + (kt + 1) * BK, buf ^ 1);
 #pragma unroll
             for (int k = 0; k < BK; ++k) {
-                float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
-                float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][64 + ty * 4]);
-                float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
-                float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][64 + tx * 4]);
+                const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][64 + ty * 4]);
                 const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                float bv[4 * TN4];
+#pragma unroll
+                for (int m = 0; m < TN4; ++m) {
+                    const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][k][64 * m + tx * 4]);
+                    bv[4 * m] = b.x;
+                    bv[4 * m + 1] = b.y;
+                    bv[4 * m + 2] = b.z;
+                    bv[4 * m + 3] = b.w;
+                }
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) c[i][j] = fmaf(av[i], bv[j], c[i][j]);
+                    for (int j = 0; j < 4 * TN4; ++j) c[i][j] = fmaf(av[i], bv[j], c[i][j]);
             }
             if (kt + 1 < KT) sstore(buf ^ 1);
             cp_async_wait_all();
@@ -158,8 +177,8 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
         for (int i = 0; i < 8; ++i) {
             int r = (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                int col = (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+            for (int j = 0; j < 4 * TN4; ++j) {
+                int col = 64 * (j >> 2) + tx * 4 + (j & 3);
                 Cs[r * CS_LD + col] = c[i][j];
             }
         }
@@ -168,17 +187,19 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
         const RowConst rc = load_row_const(a.aux, m0 + er, a.n);
         if (rc.valid) {
             Slide sl[3];
-            const int nb = n0 + eh * 64;
-            for (int jj = 0; jj < 64; ++jj) {
+            const int nb = n0 + eh * EPI_COLS;
+            for (int jj = 0; jj < EPI_COLS; ++jj) {
                 if constexpr (GRAD)
-                    epi_node_grad<Q4>(acc, sl, Cs[er * CS_LD + eh * 64 + jj], nb + jj, rc, a.cc, a.tab, a.m_last);
+                    epi_node_grad<Q4>(acc, sl, Cs[er * CS_LD + eh * EPI_COLS + jj], nb + jj, rc, a.cc, a.tab,
+                                      a.m_last);
                 else
-                    epi_node<Q4>(acc[0], sl[0], Cs[er * CS_LD + eh * 64 + jj], nb + jj, rc, a.cc, a.tab, a.m_last);
+                    epi_node<Q4>(acc[0], sl[0], Cs[er * CS_LD + eh * EPI_COLS + jj], nb + jj, rc, a.cc, a.tab,
+                                 a.m_last);
             }
             if constexpr (GRAD)
-                epi_close_grad<Q4>(acc, sl, nb + 64, rc, a.tab, a.m_last);
+                epi_close_grad<Q4>(acc, sl, nb + EPI_COLS, rc, a.tab, a.m_last);
             else
-                epi_close<Q4>(acc[0], sl[0], nb + 64, rc, a.tab, a.m_last);
+                epi_close<Q4>(acc[0], sl[0], nb + EPI_COLS, rc, a.tab, a.m_last);
         }
         __syncthreads();
     }
@@ -203,9 +224,11 @@ __global__ void __launch_bounds__(THREADS, 2) phot_simt_kernel(SArgs a) {
     }
 }
 
+constexpr size_t SIMT_SMEM = sizeof(float) * (BM * CS_LD > 2 * BK * (AS_LD + BN) ? BM * CS_LD : 2 * BK * (AS_LD + BN));
+
 template <int Q4, bool GRAD>
 cudaError_t launch_q4(const SArgs &a, int64_t n, cudaStream_t s) {
-    size_t smem = (size_t)BM * CS_LD * sizeof(float);
+    const size_t smem = SIMT_SMEM;
     cudaFuncSetAttribute(phot_simt_kernel<Q4, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((unsigned)((n + BM - 1) / BM * a.parts));
     phot_simt_kernel<Q4, GRAD><<<grid, THREADS, smem, s>>>(a);

@@ -19,6 +19,9 @@
 //   d_wmul  [KZ_pad] 2^E_k, the factor folded into the weights, so that
 //           sum_k (omega_k 2^E_k)(L_kn 2^-E_k) = sum_k omega_k L_kn exactly
 //           (indexed by kz, like d_Lt_*).
+//   d_Lab_*  [N_pad][KA_pad] bf16 hi / lo of L[k][n] 2^-E_k in the age-block
+//           order ka = i * 32 + j (age-dependent dust's fused forward), with
+//           d_wmul_ab = 2^E_k at ka (only when Ctx::KA_pad > 0)
 // E_k is the binary exponent of max_n L[k][n]: every scaled row peaks in
 // [1, 2), far from the bf16 underflow threshold.
 #include "dsps_internal.cuh"
@@ -79,6 +82,37 @@ __global__ void build_lt_kernel(const float *L, const float *rscale, int N, int 
             __nv_bfloat16 h = __float2bfloat16_rn(v);
             hi[(size_t)n * KZ_pad + k] = h;
             lo[(size_t)n * KZ_pad + k] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+// The same split in the age-block order: column ka = i * KBLOCK + j of the
+// output [N_pad][KA_pad] takes SSP row k = i * n_z + j (n_u = 1; zero for
+// j >= n_z and the padding); wmul_ab[ka] = 1 / rscale[k] = 2^E_k.
+__global__ void build_lab_kernel(const float *L, const float *rscale, int N, int n_age, int n_z, int KA_pad,
+                                 int N_pad, __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *wmul_ab) {
+    __shared__ float t[32][33];
+    const int ka0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int i = ka0 / KBLOCK;                    // one age per 32 columns
+    for (int r = ty; r < 32; r += 8) {
+        const int j = r, n = n0 + tx;
+        const bool ok = i < n_age && j < n_z && n < N;
+        const int k = i * n_z + j;
+        t[r][tx] = ok ? L[(size_t)k * N + n] * rscale[k] : 0.f;
+    }
+    if (blockIdx.x == 0 && ty == 0) {
+        const int j = tx;
+        wmul_ab[ka0 + j] = (i < n_age && j < n_z && rscale[i * n_z + j] > 0.f) ? 1.f / rscale[i * n_z + j] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        int n = n0 + r, k = ka0 + tx;
+        if (n < N_pad && k < KA_pad) {
+            float v = t[tx][r];
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            hi[(size_t)n * KA_pad + k] = h;
+            lo[(size_t)n * KA_pad + k] = __float2bfloat16_rn(v - __bfloat162float(h));
         }
     }
 }
@@ -155,6 +189,11 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
         build_l32_kernel<<<(unsigned)((tot + 255) / 256), 256>>>(d_raw, c.K, c.n_lam, c.K_pad, c.N_pad, c.d_L32);
         dim3 g(c.N_pad / 32, c.KZ_pad / 32), b(32, 8);
         build_lt_kernel<<<g, b>>>(d_raw, d_rscale, c.n_lam, c.KZ_pad, c.N_pad, kl, c.d_Lt_hi, c.d_Lt_lo);
+        if (c.KA_pad) {
+            dim3 ga(c.N_pad / 32, c.KA_pad / 32);
+            build_lab_kernel<<<ga, b>>>(d_raw, d_rscale, c.n_lam, c.n_age, c.n_z, c.KA_pad, c.N_pad, c.d_Lab_hi,
+                                        c.d_Lab_lo, c.d_wmul_ab);
+        }
         const size_t totz = (size_t)c.KZ_pad * c.N_pad;
         const unsigned blkz = (unsigned)((totz + 255) / 256);
         build_ldiff_kernel<<<blkz, 256>>>(d_raw, c.n_lam, kl, c.u_ref, c.KZ_pad, c.N_pad, c.d_Ld32);

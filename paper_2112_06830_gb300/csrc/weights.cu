@@ -59,6 +59,8 @@ struct WArgs {
     const double *tlut;    // [n_lut] t_obs(z) [Gyr]
     const float *glut;     // [n_lut] Dmod(z) - 5 log10 z
     const float *wmul;
+    const float *wmul_ab;  // [KA_pad] the age-block order's row multipliers (W_OMEGA_BF16X2_AB)
+    int KA_pad;            // row length of the age-block order
     float *w_msun, *w32;
     __nv_bfloat16 *whi, *wlo;
     float *aux;
@@ -554,6 +556,75 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                 atomicMax(&a.urange[t].y, u_hi);
             }
         }
+    } else if constexpr (MODE == W_OMEGA_BF16X2_AB && !NEB) {
+        // Age-block order ka = i * KBLOCK + j (age-dependent dust's fused
+        // forward): lane takes age i = base + lane, walks the metallicity bins
+        // upwards carrying the lower-edge CDF (one CDF per weight, the
+        // arithmetic of the metallicity-major loop above, so every weight is the
+        // same number), and writes the age's 32 columns (zeros past n_z) as
+        // four 16-byte stores of hi and of lo.  A ballot over the 32 ages of a
+        // pass gives the tile's mask word of those ages (bit i: some weight of
+        // age i non-zero).
+        const float isg = valid ? inv_sig : 0.f;
+        __nv_bfloat16 *rh = a.whi + gi * a.KA_pad, *rl = a.wlo + gi * a.KA_pad;
+        const int nblk = a.KA_pad / KBLOCK;
+        unsigned mw[4] = {0u, 0u, 0u, 0u};
+        for (int base = 0; base < nblk; base += 32) {
+            const int i = base + lane;
+            bool nzr = false;
+            if (i < nblk) {
+                const float fr = valid && i < a.n_age ? frac[i] : 0.f;
+                const float mu = valid ? mdf_mean_at(a, p, min(i, a.n_age - 1)) : 0.f;
+                float ulo = -1e30f, slo = 0.f;
+                uint32_t hw[KBLOCK / 2], lw[KBLOCK / 2];
+#pragma unroll
+                for (int jj = 0; jj < KBLOCK / 2; ++jj) {
+                    float w2[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = 2 * jj + h;
+                        float om = 0.f;
+                        if (j < nz) {
+                            const bool last = j == nz - 1;
+                            const float uh = last ? 1e30f : (__ldg(a.zedge + j + 1) - mu) * isg;
+                            const float s_hi = last ? 0.f : mdf_s<MDF>(uh);
+                            float pj = s_hi - slo;
+                            if (ulo <= 0.f && uh > 0.f) pj += 1.f;
+                            om = fr * pj;
+                            slo = s_hi;
+                            ulo = uh;
+                        }
+                        nzr = nzr || om != 0.f;
+                        w2[h] = om * __ldg(a.wmul_ab + i * KBLOCK + j);
+                    }
+                    const __nv_bfloat162 hv = __floats2bfloat162_rn(w2[0], w2[1]);
+                    const __nv_bfloat162 lv =
+                        __floats2bfloat162_rn(w2[0] - __low2float(hv), w2[1] - __high2float(hv));
+                    hw[jj] = *reinterpret_cast<const uint32_t *>(&hv);
+                    lw[jj] = *reinterpret_cast<const uint32_t *>(&lv);
+                }
+                uint4 *dh = reinterpret_cast<uint4 *>(rh + i * KBLOCK), *dl = reinterpret_cast<uint4 *>(rl + i * KBLOCK);
+#pragma unroll
+                for (int q = 0; q < KBLOCK / 8; ++q) {
+                    dh[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                    dl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                }
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, nzr);
+            if (base / 32 < 4) mw[base / 32] = b;
+        }
+        if (a.trange && valid) {
+            const int64_t t = gi >> 7;
+            if (lane < 4 && lane < a.kmw) {
+                const unsigned v = lane == 0 ? mw[0] : lane == 1 ? mw[1] : lane == 2 ? mw[2] : mw[3];
+                if (v) atomicOr(a.kmask + t * a.kmw + lane, v);
+            }
+            if (lane == 0) {
+                const int i0 = (int)floorf(s_shift);
+                atomicMin(&a.trange[t].x, i0);
+                atomicMax(&a.trange[t].y, i0);
+            }
+        }
     } else if constexpr (NEB) {
         // Age-major k = (i * n_z + j) * n_u + u: each lane takes (i, j) pairs,
         // the metallicity bin probability from its two edges' CDFs, and writes
@@ -647,7 +718,19 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
             dl = group_dust_value(a.dust_T, p[9], dlo);
         }
         if (!valid) atomicOr(a.err, DERR_PARAM);
-        if (MODE != W_MSUN) {
+        if (MODE == W_OMEGA_BF16X2_AB) {
+            // the young and old dust values; each group's curve is formed from
+            // them in the fused contraction (agedep_tc.cu)
+            float *ax = a.aux + gi * AUX_STRIDE;
+            ax[0] = p[8];
+            ax[1] = p[9];
+            ax[2] = s_shift;
+            ax[3] = valid ? 1.f : 0.f;
+            ax[4] = a.dust_row_old >= 0 ? a.params[(int64_t)a.dust_row_old * a.G_stride + g] : p[8];
+            ax[5] = a.dust_row_old >= 0 ? a.params[(int64_t)(a.dust_row_old + 1) * a.G_stride + g] : p[9];
+            ax[6] = ax[7] = 0.f;
+            a.magoff[gi] = valid ? gp.magoff : __int_as_float(0x7fc00000);
+        } else if (MODE != W_MSUN) {
             float *ax = a.aux + gi * AUX_STRIDE;
             store_dust_aux(ax, Av, dl, a.dust_law, a.dust_bump);
             ax[2] = s_shift;
@@ -1079,6 +1162,8 @@ WArgs make_wargs(const Ctx &c, const Workspace &w, const float *params, int64_t 
     a.tlut = c.d_tlut;
     a.glut = c.d_glut;
     a.wmul = c.d_wmul;
+    a.wmul_ab = c.d_wmul_ab;
+    a.KA_pad = c.KA_pad;
     a.w32 = w.w32;
     a.whi = w.whi;
     a.wlo = w.wlo;
@@ -1163,6 +1248,7 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
         a.dust_T = group->T;
         a.dust_row_old = c.row_dust_old;
     }
+    if (mode == W_OMEGA_BF16X2_AB) a.dust_row_old = c.row_dust_old;   // both dust values into aux
     a.w_msun = w_msun;
     a.perm = sorted ? w.perm : nullptr;
     a.gidx = sorted ? w.gidx : nullptr;
@@ -1187,6 +1273,9 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
     case W_MSUN: return launch_models<WeightsLaunch<W_MSUN>::L>(c, a, grid, smem, s);
     case W_OMEGA_F32: return launch_models<WeightsLaunch<W_OMEGA_F32>::L>(c, a, grid, smem, s);
     case W_OMEGA_BF16X2_AGE1: return launch_models<WeightsLaunch<W_OMEGA_BF16X2_AGE1>::L>(c, a, grid, smem, s);
+    case W_OMEGA_BF16X2_AB:
+        if (c.n_u > 1 || !c.KA_pad) return cudaErrorInvalidValue;
+        return launch_models_n<WeightsLaunch<W_OMEGA_BF16X2_AB>::L, false>(c, a, grid, smem, s);
     default: return launch_models<WeightsLaunch<W_OMEGA_BF16X2>::L>(c, a, grid, smem, s);
     }
 }

@@ -66,7 +66,7 @@ class dsps_opts(C.Structure):
                 ("z_max", C.c_double), ("band_skip", C.c_int32), ("mdf_mean", C.c_int32),
                 ("mdf_terf_x0", C.c_double), ("mdf_terf_h", C.c_double), ("dust_bump", C.c_int32),
                 ("dust_law", C.c_int32), ("dust_agedep", C.c_int32), ("dust_agedep_x0", C.c_double),
-                ("dust_agedep_h", C.c_double)]
+                ("dust_agedep_h", C.c_double), ("agedep_fused", C.c_int32)]
 
 
 DSPS_PROF_KINDS = 4
@@ -330,7 +330,7 @@ class Context:
                  max_chunk=None, hbm_budget_bytes=None, n_streams=None, om0=0.3, w0=-1.0, h=0.7, z_max=10.0,
                  band_skip=True, mdf_mean=DSPS_MDF_MEAN_LINEAR, mdf_terf_x0=None, mdf_terf_h=None,
                  dust_bump=False, dust_law=DSPS_DUST_POWERLAW, dust_agedep=False, dust_agedep_x0=None,
-                 dust_agedep_h=None):
+                 dust_agedep_h=None, agedep_fused=True):
         self._keep = [np.ascontiguousarray(ssp.log_age_yr, dtype=np.float64),
                       np.ascontiguousarray(ssp.lgz, dtype=np.float64),
                       np.ascontiguousarray(ssp.lam, dtype=np.float64),
@@ -352,6 +352,7 @@ class Context:
         o.dust_bump = 1 if dust_bump else 0
         o.dust_law = int(dust_law)
         o.dust_agedep = 1 if dust_agedep else 0
+        o.agedep_fused = 1 if agedep_fused else 0
         if dust_agedep_x0 is not None:
             o.dust_agedep_x0 = dust_agedep_x0
         if dust_agedep_h is not None:

@@ -42,6 +42,7 @@ def test_default_opts():
     assert (o.dust_bump, o.dust_law, o.dust_agedep) == (0, dsps.DSPS_DUST_POWERLAW, 0)
     assert (o.dust_agedep_x0, o.dust_agedep_h) == (7.0, 0.1)
     assert (o.mdf_mean, o.mdf_terf_x0, o.mdf_terf_h) == (dsps.DSPS_MDF_MEAN_LINEAR, 9.0, 0.5)
+    assert o.agedep_fused == 1
 
 
 def test_struct_layouts_match_the_header():

@@ -5,7 +5,10 @@ test_oracle_pins.py.  Tolerance per galaxy and parameter:
 relative bound with an absolute floor for components near zero: f = 1e-3 for
 the FP32 form and f = 1e-2 for the split-bf16 form, whose products carry a
 relative error of about 2^-16 = 1.5e-5 (so its floor, 1e-5 of the largest
-component, is one unit roundoff of that arithmetic)."""
+component, is one unit roundoff of that arithmetic).  Each test prints the
+error against both floors, and the split-bf16 tests also assert that at most
+0.5% of the components exceed the bound with the contract's floor f = 1e-3
+(measured: 0 to 0.03%, single components of small SFH rows)."""
 import numpy as np
 import pytest
 
@@ -26,9 +29,18 @@ def _ctx(kind, sfh_model, **kw):
 FLOOR = {0: 1e-3, 1: 1e-2}
 
 
+def _scaled(pb, ref, floor):
+    scale = np.maximum(np.abs(ref), floor * np.abs(ref).max(axis=0, keepdims=True))
+    return np.abs(pb - ref) / scale
+
+
 def _check(pb, ref, prec):
-    scale = np.maximum(np.abs(ref), FLOOR[prec] * np.abs(ref).max(axis=0, keepdims=True))
-    rel = np.abs(pb - ref) / scale
+    rel = _scaled(pb, ref, FLOOR[prec])
+    tight = _scaled(pb, ref, 1e-3)
+    over = float(np.mean(tight > 1e-3))
+    print(f"  scaled gradient error: floor 1e-3 {tight.max():.2e}, floor 1e-2 {_scaled(pb, ref, 1e-2).max():.2e}, "
+          f"components over 1e-3 at floor 1e-3: {over:.4f}")
+    assert over <= 5e-3
     return rel.max(), np.unravel_index(np.argmax(rel), rel.shape)
 
 
@@ -158,9 +170,25 @@ def test_vjp_of_squared_magnitude_loss(full, prec):
     err, where = _check(pb, pb_ref, prec)
     loss = float(np.sum((m_ref - target) ** 2))
     print(f"squared-magnitude loss {loss:.3f}, prec={prec}: max scaled gradient error {err:.2e} at {where}")
-    # the same errors against the contract's floor, 1e-3 of each galaxy's largest component
-    scale3 = np.maximum(np.abs(pb_ref), 1e-3 * np.abs(pb_ref).max(axis=0, keepdims=True))
-    rel3 = np.abs(pb - pb_ref) / scale3
-    print(f"  floor 1e-3: max {rel3.max():.2e}, components over 1e-3: {np.mean(rel3 > 1e-3):.4f}")
     assert err <= 1e-3
     assert np.abs(m - m_ref).max() <= (1e-4 if prec == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_metallicity_gradient_margin(full, prec):
+    """The MDF rows (mean, width, slope) are sums with strong cancellation; this
+    keeps their margin visible: the worst galaxy's error as a fraction of the
+    bound, per row, on 2000 galaxies of the workload (the rest of the rows
+    for comparison)."""
+    ctx, sid, F = full
+    n = 2000
+    p32, p64 = _util.params_f32(synth.make_population(synth.SFH_DPL_QUENCH, n, 1, start=21_000))
+    mbar = np.random.default_rng(21).standard_normal((n, 12))
+    _, pb = _vjp(ctx, sid, p32, mbar, prec)
+    idx = np.arange(0, n, 5)
+    _, ref = oracle.mags_vjp(_util.oracle_grid("full", 1), F, p64[:, idx], mbar[idx])
+    rel = _scaled(pb[:, idx], ref, FLOOR[prec]) / 1e-3          # error / bound
+    worst = rel.max(axis=1)
+    names = ("sfh0", "sfh1", "sfh2", "sfh3", "sfh4", "mdf_mu", "mdf_sigma", "mdf_slope", "Av", "delta", "logM")
+    print(f"prec={prec}: worst error / bound per row: " + ", ".join(f"{k} {v:.2f}" for k, v in zip(names, worst)))
+    assert worst.max() <= 1.0
