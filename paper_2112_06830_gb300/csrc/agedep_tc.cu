@@ -14,7 +14,8 @@
 // of the tile has a non-zero weight); a group without such a block is skipped by
 // every role -- into one of two TMEM accumulators (128 columns each).  The
 // epilogue warps read the group's block of S_g, multiply it by F_g of each row
-// and add it into a running sum held in a third TMEM region (tcgen05.st); after
+// and add it into a running sum held in registers (each thread one row and 64
+// columns); after
 // the last group the running sum goes once through the redshifted filter
 // integral (epilogue.cuh, without dust: it is already in the sum).  So each
 // element pays one light attenuation step per group and one filter reduction,
@@ -24,7 +25,8 @@
 // W_lo, L_hi, L_lo} 32-wide K slices, 64-byte swizzle), warp 1 TMEM allocator
 // and single-thread MMA issuer (per K slice six 128x128x16 tcgen05.mma
 // kind::f16: hi.hi, hi.lo, lo.hi, two K steps), warps 2..9 epilogue (two warps
-// per TMEM lane quadrant, 64 columns each).  Every mbarrier wait is bounded; on
+// per TMEM lane quadrant, 64 columns each, the running sum of those 64 columns
+// in registers).  Every mbarrier wait is bounded; on
 // expiry the kernel records DERR_TIMEOUT, lets its copies and MMAs land, frees
 // TMEM and returns.
 #include <cudaTypedefs.h>
@@ -46,8 +48,8 @@ constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
-constexpr uint32_t TMEM_COLS = 512;          // accumulators at 0 and BN, running sum at 2 BN
-constexpr uint32_t RUN_COL = 2 * BN;
+constexpr uint32_t TMEM_COLS = 2 * BN;       // accumulators at 0 and BN
+constexpr int EPI_COLS = BN / 2;             // columns of a row per epilogue thread
 constexpr int QMAX = 16;
 constexpr int MAX_GROUPS = 128;
 constexpr size_t BAR_BYTES = 1024;
@@ -125,6 +127,36 @@ __device__ __forceinline__ bool group_present(const uint4 &km, int i0, int i1) {
 
 __device__ __forceinline__ int first_tile(int nt0, int part, int parts) {
     return nt0 + ((part - nt0 % parts) % parts + parts) % parts;
+}
+
+// 2^x in one MUFU instruction (PTX ex2.approx, relative error below 2^-22;
+// flushes results below the normal range to 0).
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Adds 16 columns of a group's S_g (nodes n0 ..), times the group's
+// attenuation F_g = 2^(alpha c_g) (Eq. attenuation, alpha = -0.4 log2(10) Av_g;
+// c_g = [k0/4.05] u + e_g D0 with u = (lam/lam_V)^beta_g = 2^(beta_g ell)),
+// into the running sum.  u is exact at the first node and stepped by the
+// factor ustep = 2^(beta_g dell) between nodes (15 products at most: ~2e-6
+// relative); the law and the bump are fixed at compile time so that the loop
+// has no branch; rows out of range add nothing.
+template <bool SALIM, bool BUMP>
+__device__ __forceinline__ void add_group_chunk(float *run, const uint32_t (&r)[16], int n0, float alpha, float beta,
+                                                float ustep, float e, const ColConst &cc, bool valid) {
+    float u = ex2_fast(beta * fmaf((float)n0, cc.dell, cc.ell0));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        float cn = u;
+        if constexpr (SALIM) cn *= __ldg(cc.k0 + n0 + j);
+        if constexpr (BUMP) cn = fmaf(e, __ldg(cc.bump + n0 + j), cn);
+        const float F = ex2_fast(alpha * cn);
+        run[j] = fmaf(__uint_as_float(r[j]), valid ? F : 0.f, run[j]);
+        u *= ustep;
+    }
 }
 
 template <int Q4>
@@ -302,9 +334,15 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
             float acc[4 * Q4];
 #pragma unroll
             for (int q = 0; q < 4 * Q4; ++q) acc[q] = 0.f;
+            const int law = (a.dust_law == DSPS_DUST_SALIM ? 1 : 0) + (a.bump ? 2 : 0);
             for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
-                const int nb = nt * BN + half * (BN / 2);
-                bool any = false;   // the running sum holds a group already
+                const int nb = nt * BN + half * EPI_COLS;
+                float run[EPI_COLS / 32][32];
+#pragma unroll
+                for (int c = 0; c < EPI_COLS / 32; ++c)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) run[c][j] = 0.f;
+                bool any = false;
                 for (int g = 0; ok && g < a.n_groups; ++g) {
                     if (!group_present(km, a.g_i0[g], a.g_i1[g])) continue;
                     int got = 1;
@@ -315,51 +353,43 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                     // the group's curve (Sec. 3.4.1), as the weights kernel forms it
                     const float T = a.g_T[g];
                     const float Avg = group_dust_value(T, avy, avo), dlg = group_dust_value(T, dly, dlo);
-                    RowConst rg = rc;
-                    rg.alpha = -0.4f * 3.32192809488736235f * Avg;
-                    rg.beta = a.dust_law == DSPS_DUST_SALIM ? dlg : dlg - 0.7f;
-                    rg.e = a.bump ? (0.85f - 1.9f * dlg) * (1.f / 4.05f) : 0.f;
-                    const uint32_t tacc = tmem_base + lane_base + (uint32_t)(as * BN + half * (BN / 2));
-                    const uint32_t trun = tmem_base + lane_base + RUN_COL + (uint32_t)(half * (BN / 2));
-#pragma unroll 1
-                    for (int c = 0; c < BN / 64; ++c) {
-                        uint32_t r[32], s[32];
-                        tmem_ld32(tacc + c * 32, r);
-                        if (c == BN / 64 - 1) {
+                    const float alpha = -0.4f * 3.32192809488736235f * Avg;
+                    const float beta = a.dust_law == DSPS_DUST_SALIM ? dlg : dlg - 0.7f;
+                    const float eg = a.bump ? (0.85f - 1.9f * dlg) * (1.f / 4.05f) : 0.f;
+                    const float ustep = ex2_fast(beta * a.cc.dell);
+                    const uint32_t tacc = tmem_base + lane_base + (uint32_t)(as * BN + half * EPI_COLS);
+#pragma unroll
+                    for (int c = 0; c < EPI_COLS / 16; ++c) {
+                        uint32_t r[16];
+                        tmem_ld16(tacc + c * 16, r);
+                        if (c == EPI_COLS / 16 - 1) {
                             // this warp's reads of the accumulator are done
                             tc_fence_before();
                             __syncwarp();
                             if (lane == 0) mbar_arrive(acce0 + 8 * as);
                         }
-                        if (any) tmem_ld32(trun + c * 32, s);
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float v = rc.valid ? __uint_as_float(r[j]) * dust_factor(a.cc, rg, nb + c * 32 + j)
-                                                     : 0.f;
-                            s[j] = __float_as_uint(any ? __uint_as_float(s[j]) + v : v);
+                        const int n0 = nb + c * 16;
+                        float *rr = &run[c >> 1][(c & 1) * 16];
+                        switch (law) {
+                        case 0: add_group_chunk<false, false>(rr, r, n0, alpha, beta, ustep, eg, a.cc, rc.valid); break;
+                        case 1: add_group_chunk<true, false>(rr, r, n0, alpha, beta, ustep, eg, a.cc, rc.valid); break;
+                        case 2: add_group_chunk<false, true>(rr, r, n0, alpha, beta, ustep, eg, a.cc, rc.valid); break;
+                        default: add_group_chunk<true, true>(rr, r, n0, alpha, beta, ustep, eg, a.cc, rc.valid); break;
                         }
-                        tmem_st32(trun + c * 32, s);
                     }
                     any = true;
                     if (++as == 2) { as = 0; aphase ^= 1u; }
                 }
                 if (!ok) break;
-                if (!any) continue;
+                if (!any || !rc.valid) continue;
                 // the attenuated spectrum of the tile: one filter integral
-                const uint32_t trun = tmem_base + lane_base + RUN_COL + (uint32_t)(half * (BN / 2));
                 Slide sl;
-#pragma unroll 1
-                for (int c = 0; c < BN / 64; ++c) {
-                    uint32_t r[32];
-                    tmem_ld32(trun + c * 32, r);
-                    if (rc.valid) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            epi_node_plain<Q4>(acc, sl, __uint_as_float(r[j]), nb + c * 32 + j, rc, a.cc, a.tab,
-                                               a.m_last);
-                    }
-                }
-                if (rc.valid) epi_close<Q4>(acc, sl, nb + BN / 2, rc, a.tab, a.m_last);
+                for (int c = 0; c < EPI_COLS / 32; ++c)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        epi_node_plain<Q4>(acc, sl, run[c][j], nb + c * 32 + j, rc, a.cc, a.tab, a.m_last);
+                epi_close<Q4>(acc, sl, nb + EPI_COLS, rc, a.tab, a.m_last);
             }
             if (!ok) break;
             // combine the two column halves of each row (bounded barrier)

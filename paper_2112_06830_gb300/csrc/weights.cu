@@ -378,10 +378,55 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
     // redshift shift in grid steps (none for rest-frame filters)
     const float s_shift = valid && !a.rest ? log1pf(z) / a.dlnlam_f : 0.f;
     const int nz = a.n_z;
-    if constexpr (MODE == W_OMEGA_BF16X2 || MODE == W_OMEGA_BF16X2_AGE1) {
+    if constexpr (MODE == W_OMEGA_BF16X2 || MODE == W_OMEGA_BF16X2_AGE1 || MODE == W_OMEGA_BF16X2_AB) {
+        // AB: the same weights in the age-block order ka = i * KBLOCK + j (the
+        // fused age-dependent dust forward), the mask holding one bit per age
+        constexpr bool AB = MODE == W_OMEGA_BF16X2_AB;
         uint4 bm = make_uint4(0u, 0u, 0u, 0u);
-        __nv_bfloat16 *rh = a.whi + gi * a.KZ_pad, *rl = a.wlo + gi * a.KZ_pad;
-        if constexpr (MODE == W_OMEGA_BF16X2_AGE1) {
+        const int row_len = AB ? a.KA_pad : a.KZ_pad;
+        __nv_bfloat16 *rh = a.whi + gi * row_len, *rl = a.wlo + gi * row_len;
+        if constexpr (AB) {
+            // Age-block order: lane j takes metallicity bin j (lanes >= n_z write
+            // the zero columns) and the warp walks the ages, four at a time
+            // (independent: both edges' CDFs per weight, the expressions of the
+            // metallicity-major loop below, so every weight is the same number);
+            // age i's 32 columns are one coalesced 64-byte store of hi and of lo,
+            // and a ballot gives the age's mask bit.
+            const int j = lane;
+            const bool jin = j < nz;
+            const bool first = j == 0, last = j == nz - 1;
+            const float ze_lo = jin && !first ? __ldg(a.zedge + j) : 0.f;
+            const float ze_hi = jin && !last ? __ldg(a.zedge + j + 1) : 0.f;
+            const float isg = valid ? inv_sig : 0.f;
+            const int nblk = a.KA_pad / KBLOCK;
+            for (int i0 = 0; i0 < nblk; i0 += 4) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int i = i0 + c;
+                    if (i >= nblk) break;
+                    const float fr = valid && i < a.n_age ? frac[i] : 0.f;
+                    const float mu = valid ? mdf_mean_at(a, p, min(i, a.n_age - 1)) : 0.f;
+                    const float ul = first ? -1e30f : (ze_lo - mu) * isg;
+                    const float uh = last ? 1e30f : (ze_hi - mu) * isg;
+                    const float sl = first ? 0.f : mdf_s<MDF>(ul);
+                    const float sh = last ? 0.f : mdf_s<MDF>(uh);
+                    float pj = sh - sl;
+                    if (ul <= 0.f && uh > 0.f) pj += 1.f;
+                    const float om = jin ? fr * pj : 0.f;
+                    const float w = jin ? om * __ldg(a.wmul_ab + i * KBLOCK + j) : 0.f;
+                    const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                    rh[i * KBLOCK + j] = h;
+                    rl[i * KBLOCK + j] = __float2bfloat16_rn(w - __bfloat162float(h));
+                    const unsigned any = __ballot_sync(0xffffffffu, om != 0.f);
+                    const unsigned bit = any ? 1u << (i & 31) : 0u;
+                    const int wi = i >> 5;
+                    bm.x |= wi == 0 ? bit : 0u;
+                    bm.y |= wi == 1 ? bit : 0u;
+                    bm.z |= wi == 2 ? bit : 0u;
+                    bm.w |= wi == 3 ? bit : 0u;
+                }
+            }
+        } else if constexpr (MODE == W_OMEGA_BF16X2_AGE1) {
             // One age bin i: lane j < n_z takes metallicity bin j (both edges'
             // CDFs, the arithmetic of the loop below), and the warp writes, in
             // every section, the 32-wide kz block holding (j, i) -- the weight
@@ -554,75 +599,6 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                 atomicMax(&a.trange[t].y, i0);
                 atomicMin(&a.urange[t].x, u_lo);
                 atomicMax(&a.urange[t].y, u_hi);
-            }
-        }
-    } else if constexpr (MODE == W_OMEGA_BF16X2_AB && !NEB) {
-        // Age-block order ka = i * KBLOCK + j (age-dependent dust's fused
-        // forward): lane takes age i = base + lane, walks the metallicity bins
-        // upwards carrying the lower-edge CDF (one CDF per weight, the
-        // arithmetic of the metallicity-major loop above, so every weight is the
-        // same number), and writes the age's 32 columns (zeros past n_z) as
-        // four 16-byte stores of hi and of lo.  A ballot over the 32 ages of a
-        // pass gives the tile's mask word of those ages (bit i: some weight of
-        // age i non-zero).
-        const float isg = valid ? inv_sig : 0.f;
-        __nv_bfloat16 *rh = a.whi + gi * a.KA_pad, *rl = a.wlo + gi * a.KA_pad;
-        const int nblk = a.KA_pad / KBLOCK;
-        unsigned mw[4] = {0u, 0u, 0u, 0u};
-        for (int base = 0; base < nblk; base += 32) {
-            const int i = base + lane;
-            bool nzr = false;
-            if (i < nblk) {
-                const float fr = valid && i < a.n_age ? frac[i] : 0.f;
-                const float mu = valid ? mdf_mean_at(a, p, min(i, a.n_age - 1)) : 0.f;
-                float ulo = -1e30f, slo = 0.f;
-                uint32_t hw[KBLOCK / 2], lw[KBLOCK / 2];
-#pragma unroll
-                for (int jj = 0; jj < KBLOCK / 2; ++jj) {
-                    float w2[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int j = 2 * jj + h;
-                        float om = 0.f;
-                        if (j < nz) {
-                            const bool last = j == nz - 1;
-                            const float uh = last ? 1e30f : (__ldg(a.zedge + j + 1) - mu) * isg;
-                            const float s_hi = last ? 0.f : mdf_s<MDF>(uh);
-                            float pj = s_hi - slo;
-                            if (ulo <= 0.f && uh > 0.f) pj += 1.f;
-                            om = fr * pj;
-                            slo = s_hi;
-                            ulo = uh;
-                        }
-                        nzr = nzr || om != 0.f;
-                        w2[h] = om * __ldg(a.wmul_ab + i * KBLOCK + j);
-                    }
-                    const __nv_bfloat162 hv = __floats2bfloat162_rn(w2[0], w2[1]);
-                    const __nv_bfloat162 lv =
-                        __floats2bfloat162_rn(w2[0] - __low2float(hv), w2[1] - __high2float(hv));
-                    hw[jj] = *reinterpret_cast<const uint32_t *>(&hv);
-                    lw[jj] = *reinterpret_cast<const uint32_t *>(&lv);
-                }
-                uint4 *dh = reinterpret_cast<uint4 *>(rh + i * KBLOCK), *dl = reinterpret_cast<uint4 *>(rl + i * KBLOCK);
-#pragma unroll
-                for (int q = 0; q < KBLOCK / 8; ++q) {
-                    dh[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
-                    dl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
-                }
-            }
-            const unsigned b = __ballot_sync(0xffffffffu, nzr);
-            if (base / 32 < 4) mw[base / 32] = b;
-        }
-        if (a.trange && valid) {
-            const int64_t t = gi >> 7;
-            if (lane < 4 && lane < a.kmw) {
-                const unsigned v = lane == 0 ? mw[0] : lane == 1 ? mw[1] : lane == 2 ? mw[2] : mw[3];
-                if (v) atomicOr(a.kmask + t * a.kmw + lane, v);
-            }
-            if (lane == 0) {
-                const int i0 = (int)floorf(s_shift);
-                atomicMin(&a.trange[t].x, i0);
-                atomicMax(&a.trange[t].y, i0);
             }
         }
     } else if constexpr (NEB) {
