@@ -54,7 +54,8 @@ constexpr int QMAX = 16;
 constexpr int MAX_GROUPS = 128;
 constexpr size_t BAR_BYTES = 1024;
 constexpr size_t COMB_BYTES = (size_t)BM * QMAX * 4;
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + COMB_BYTES;
+constexpr size_t ACC_BYTES = (size_t)NUM_EPI_WARPS * 32 * QMAX * 4;   // each epilogue thread's filter sums
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + COMB_BYTES + ACC_BYTES;
 constexpr uint32_t IDESC = make_idesc(BM, BN);
 
 struct GArgs {
@@ -142,8 +143,8 @@ __device__ __forceinline__ float ex2_fast(float x) {
 // c_g = [k0/4.05] u + e_g D0 with u = (lam/lam_V)^beta_g = 2^(beta_g ell)),
 // into the running sum.  u is exact at the first node and stepped by the
 // factor ustep = 2^(beta_g dell) between nodes (15 products at most: ~2e-6
-// relative); the law and the bump are fixed at compile time so that the loop
-// has no branch; rows out of range add nothing.
+// relative), one ex2 per node; the law and the bump are fixed at compile time
+// so that the loop has no branch; rows out of range add nothing.
 template <bool SALIM, bool BUMP>
 __device__ __forceinline__ void add_group_chunk(float *run, const uint32_t (&r)[16], int n0, float alpha, float beta,
                                                 float ustep, float e, const ColConst &cc, bool valid) {
@@ -181,6 +182,9 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
     ring.empty0 = smem_u32(bars + 2 * STAGES + 8 + UNIT_RING);
     ring.slot = reinterpret_cast<volatile int *>(bars + 2 * STAGES + 8 + 2 * UNIT_RING);
     float *comb = reinterpret_cast<float *>(sm + (size_t)STAGES * STAGE_BYTES + BAR_BYTES);
+    // the filter sums of each epilogue thread live in shared memory between
+    // wavelength tiles (the group loop keeps 64 running-sum registers)
+    float *accbuf = comb + BM * QMAX;
     const uint32_t sbase = smem_u32(sm);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -321,8 +325,9 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
             uint4 km;
             tile_ranges(a, mt, nt0, nt1, km);
             const int64_t rowg = (int64_t)mt * BM + row;
-            // the row's dust values and redshift interpolation
-            RowConst rc = load_row_const(a.aux, rowg, a.n);
+            // the row's dust values (the redshift interpolation is read again
+            // for each wavelength tile's filter integral)
+            const bool valid = load_row_const(a.aux, rowg, a.n).valid;
             float avy = 0.f, dly = 0.f, avo = 0.f, dlo = 0.f;
             if (rowg < a.n) {
                 const float *ax = a.aux + rowg * AUX_STRIDE;
@@ -331,9 +336,9 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                 avo = ax[4];
                 dlo = ax[5];
             }
-            float acc[4 * Q4];
+            float *accs = accbuf + (threadIdx.x - 64) * QMAX;
 #pragma unroll
-            for (int q = 0; q < 4 * Q4; ++q) acc[q] = 0.f;
+            for (int q = 0; q < 4 * Q4; ++q) accs[q] = 0.f;
             const int law = (a.dust_law == DSPS_DUST_SALIM ? 1 : 0) + (a.bump ? 2 : 0);
             for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
                 const int nb = nt * BN + half * EPI_COLS;
@@ -371,18 +376,22 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                         const int n0 = nb + c * 16;
                         float *rr = &run[c >> 1][(c & 1) * 16];
                         switch (law) {
-                        case 0: add_group_chunk<false, false>(rr, r, n0, alpha, beta, ustep, eg, a.cc, rc.valid); break;
-                        case 1: add_group_chunk<true, false>(rr, r, n0, alpha, beta, ustep, eg, a.cc, rc.valid); break;
-                        case 2: add_group_chunk<false, true>(rr, r, n0, alpha, beta, ustep, eg, a.cc, rc.valid); break;
-                        default: add_group_chunk<true, true>(rr, r, n0, alpha, beta, ustep, eg, a.cc, rc.valid); break;
+                        case 0: add_group_chunk<false, false>(rr, r, n0, alpha, beta, ustep, eg, a.cc, valid); break;
+                        case 1: add_group_chunk<true, false>(rr, r, n0, alpha, beta, ustep, eg, a.cc, valid); break;
+                        case 2: add_group_chunk<false, true>(rr, r, n0, alpha, beta, ustep, eg, a.cc, valid); break;
+                        default: add_group_chunk<true, true>(rr, r, n0, alpha, beta, ustep, eg, a.cc, valid); break;
                         }
                     }
                     any = true;
                     if (++as == 2) { as = 0; aphase ^= 1u; }
                 }
                 if (!ok) break;
-                if (!any || !rc.valid) continue;
+                if (!any || !valid) continue;
                 // the attenuated spectrum of the tile: one filter integral
+                const RowConst rc = load_row_const(a.aux, rowg, a.n);
+                float acc[4 * Q4];
+#pragma unroll
+                for (int q = 0; q < 4 * Q4; ++q) acc[q] = accs[q];
                 Slide sl;
 #pragma unroll
                 for (int c = 0; c < EPI_COLS / 32; ++c)
@@ -390,8 +399,13 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                     for (int j = 0; j < 32; ++j)
                         epi_node_plain<Q4>(acc, sl, run[c][j], nb + c * 32 + j, rc, a.cc, a.tab, a.m_last);
                 epi_close<Q4>(acc, sl, nb + EPI_COLS, rc, a.tab, a.m_last);
+#pragma unroll
+                for (int q = 0; q < 4 * Q4; ++q) accs[q] = acc[q];
             }
             if (!ok) break;
+            float acc[4 * Q4];
+#pragma unroll
+            for (int q = 0; q < 4 * Q4; ++q) acc[q] = accs[q];
             // combine the two column halves of each row (bounded barrier)
             float *cr = comb + row * QMAX;
             if (half == 1)

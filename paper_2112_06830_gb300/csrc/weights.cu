@@ -388,10 +388,11 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
         if constexpr (AB) {
             // Age-block order: lane j takes metallicity bin j (lanes >= n_z write
             // the zero columns) and the warp walks the ages, four at a time
-            // (independent: both edges' CDFs per weight, the expressions of the
-            // metallicity-major loop below, so every weight is the same number);
-            // age i's 32 columns are one coalesced 64-byte store of hi and of lo,
-            // and a ballot gives the age's mask bit.
+            // (independent).  Lane j evaluates the CDF at its bin's upper edge
+            // and takes the lower edge's from lane j - 1 (one CDF per weight, the
+            // expressions of the metallicity-major loop below, so every weight is
+            // the same number); age i's 32 columns are one coalesced 64-byte
+            // store of hi and of lo, and a ballot gives the age's mask bit.
             const int j = lane;
             const bool jin = j < nz;
             const bool first = j == 0, last = j == nz - 1;
@@ -408,8 +409,9 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                     const float mu = valid ? mdf_mean_at(a, p, min(i, a.n_age - 1)) : 0.f;
                     const float ul = first ? -1e30f : (ze_lo - mu) * isg;
                     const float uh = last ? 1e30f : (ze_hi - mu) * isg;
-                    const float sl = first ? 0.f : mdf_s<MDF>(ul);
                     const float sh = last ? 0.f : mdf_s<MDF>(uh);
+                    const float sl_up = __shfl_up_sync(0xffffffffu, sh, 1);   // lane j - 1's upper edge
+                    const float sl = first ? 0.f : sl_up;
                     float pj = sh - sl;
                     if (ul <= 0.f && uh > 0.f) pj += 1.f;
                     const float om = jin ? fr * pj : 0.f;
