@@ -200,15 +200,16 @@ typedef struct {
                                   returns DSPS_ERR_UNSUPPORTED; default 0        */
     double dust_agedep_x0;     /* transition centre [log10 yr] and width h [dex], */
     double dust_agedep_h;      /* h > 0 (defaults 7, 0.1: the birth-cloud age)    */
-    int32_t agedep_fused;      /* with dust_agedep, DSPS_PREC_BF16X3 magnitudes:
+    int32_t agedep_fused;      /* with dust_agedep, magnitudes (no gradient):
                                   1 (default): every group of age bins sharing a
                                   curve contracted in one launch, each group's
                                   attenuated spectrum summed on chip before one
-                                  filter integral (grids without a nebular axis,
-                                  n_z <= 32, n_age <= 128); 0: one contraction
-                                  and filter integral per group.  The two agree
-                                  to the split-bf16 rounding (different
-                                  summation order).                            */
+                                  filter integral (DSPS_PREC_BF16X3: grids
+                                  without a nebular axis, n_z <= 32, n_age <=
+                                  128; DSPS_PREC_FP32: up to 128 groups); 0: one
+                                  contraction and filter integral per group.
+                                  The two agree to the form's rounding
+                                  (different summation order).                  */
 } dsps_opts;
 
 /* Fills *o with the defaults above (device 0, max_chunk 262144,
@@ -445,6 +446,8 @@ typedef struct {
     int64_t tc_kblocks;        /* 128 x 256 x 32 split-bf16 tensor-core block products executed */
     int64_t simt_steps;        /* 128 x 128 x 16 FP32 multiply-add tile steps of the FP32 form's
                                   photometry contraction executed */
+    int64_t tc_kblocks_n128;   /* 128 x 128 x 32 split-bf16 block products executed by the one-launch
+                                  age-dependent dust contraction */
 } dsps_profile_t;
 int dsps_profile_enable(dsps_ctx *ctx, int32_t enable);
 int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out);

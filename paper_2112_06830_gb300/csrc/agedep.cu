@@ -481,8 +481,10 @@ int run_photometry_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const f
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;
     const bool tc = precision == DSPS_PREC_BF16X3;
-    // split-bf16: every group in one launch (agedep_tc.cu) where the grid allows
-    const bool fused = tc && c->opts.agedep_fused && agedep_fused_ok(*c);
+    // every group in one launch: split-bf16 (agedep_tc.cu) where the grid
+    // allows, FP32 (phot_simt.cu) up to AGEDEP_MAX_GROUPS groups
+    const bool fused = c->opts.agedep_fused &&
+                       (tc ? agedep_fused_ok(*c) : (int)c->dust_groups.size() <= AGEDEP_MAX_GROUPS);
     for (int64_t g0 = 0; g0 < n_gal; g0 += w.cap) {
         const int64_t n = n_gal - g0 < w.cap ? n_gal - g0 : w.cap;
         cudaError_t e = cudaSuccess;
@@ -492,11 +494,12 @@ int run_photometry_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, const f
                 ProfScope ps(*c, 0, s, prof);
                 e = launch_zsort(*c, w, params, n_gal, g0, n, s);
                 if (e == cudaSuccess)
-                    e = launch_weights(*c, w, W_OMEGA_BF16X2_AB, params, n_gal, g0, n, nullptr, s, true);
+                    e = tc ? launch_weights(*c, w, W_OMEGA_BF16X2_AB, params, n_gal, g0, n, nullptr, s, true)
+                           : launch_weights(*c, w, W_OMEGA_F32, params, n_gal, g0, n, nullptr, s, true, nullptr, true);
             }
             if (e == cudaSuccess) {
-                ProfScope ps(*c, 2, s, prof);
-                e = launch_phot_tc_groups(*c, w, fs, n, &parts, s);
+                ProfScope ps(*c, tc ? 2 : 1, s, prof);
+                e = tc ? launch_phot_tc_groups(*c, w, fs, n, &parts, s) : launch_phot_simt_groups(*c, w, fs, n, &parts, s);
             }
             if (e == cudaSuccess) {
                 ProfScope ps(*c, 0, s, prof);

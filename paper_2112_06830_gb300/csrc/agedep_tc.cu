@@ -43,20 +43,26 @@ using namespace tc;
 
 constexpr int BM = 128, BN = 128, BK = KBLOCK;
 constexpr int STAGES = 4;
+constexpr int NACC = 2;                      // TMEM accumulators (MMA runs NACC - 1 groups ahead)
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
-constexpr uint32_t TMEM_COLS = 2 * BN;       // accumulators at 0 and BN
-constexpr int EPI_COLS = BN / 2;             // columns of a row per epilogue thread
+constexpr uint32_t TMEM_COLS = NACC * BN;    // accumulator i at column i * BN
+constexpr int SPLIT = NUM_EPI_WARPS / 4;     // epilogue threads per row (one per column group)
+constexpr int EPI_COLS = BN / SPLIT;         // columns of a row per epilogue thread
 constexpr int QMAX = 16;
-constexpr int MAX_GROUPS = 128;
+constexpr int MAX_GROUPS = AGEDEP_MAX_GROUPS;
 constexpr size_t BAR_BYTES = 1024;
-constexpr size_t COMB_BYTES = (size_t)BM * QMAX * 4;
+constexpr size_t COMB_BYTES = (size_t)(SPLIT > 1 ? SPLIT - 1 : 1) * BM * QMAX * 4;
 constexpr size_t ACC_BYTES = (size_t)NUM_EPI_WARPS * 32 * QMAX * 4;   // each epilogue thread's filter sums
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + COMB_BYTES + ACC_BYTES;
 constexpr uint32_t IDESC = make_idesc(BM, BN);
+static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM allocation: a power of two up to 512");
+static_assert((2 * STAGES + 2 * NACC + 4 + 2 * UNIT_RING) * 8 + UNIT_RING * 4 <= BAR_BYTES, "barrier area");
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
+static_assert(NUM_EPI_WARPS % 4 == 0 && EPI_COLS % 32 == 0, "each epilogue thread: one row, whole 32-column blocks");
 
 struct GArgs {
     const float *aux;              // Av_young, delta_young, s, valid, Av_old, delta_old (weights mode AB)
@@ -71,6 +77,7 @@ struct GArgs {
     float g_T[MAX_GROUPS];                      // weight of the old-star dust values
     int64_t n;
     int *sched;                    // unit counter, zero at launch
+    unsigned long long *kblk;      // 128 x 128 x 32 block products executed (profiling), or nullptr
     float *partial;                // [parts][n][4*Q4]
     unsigned *err;
 };
@@ -144,10 +151,11 @@ __device__ __forceinline__ float ex2_fast(float x) {
 // into the running sum.  u is exact at the first node and stepped by the
 // factor ustep = 2^(beta_g dell) between nodes (15 products at most: ~2e-6
 // relative), one ex2 per node; the law and the bump are fixed at compile time
-// so that the loop has no branch; rows out of range add nothing.
+// so that the loop has no branch.  A row that is out of range or invalid
+// accumulates whatever its accumulator holds: its sum is never integrated.
 template <bool SALIM, bool BUMP>
 __device__ __forceinline__ void add_group_chunk(float *run, const uint32_t (&r)[16], int n0, float alpha, float beta,
-                                                float ustep, float e, const ColConst &cc, bool valid) {
+                                                float ustep, float e, const ColConst &cc) {
     float u = ex2_fast(beta * fmaf((float)n0, cc.dell, cc.ell0));
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -155,12 +163,12 @@ __device__ __forceinline__ void add_group_chunk(float *run, const uint32_t (&r)[
         if constexpr (SALIM) cn *= __ldg(cc.k0 + n0 + j);
         if constexpr (BUMP) cn = fmaf(e, __ldg(cc.bump + n0 + j), cn);
         const float F = ex2_fast(alpha * cn);
-        run[j] = fmaf(__uint_as_float(r[j]), valid ? F : 0.f, run[j]);
+        run[j] = fmaf(__uint_as_float(r[j]), F, run[j]);
         u *= ustep;
     }
 }
 
-template <int Q4>
+template <int Q4, int LAW>
 __global__ void __launch_bounds__(THREADS, 1)
 phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                       const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -172,19 +180,19 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
     const uint32_t full0 = smem_u32(bars);
     const uint32_t empty0 = smem_u32(bars + STAGES);
     const uint32_t accf0 = smem_u32(bars + 2 * STAGES);
-    const uint32_t acce0 = smem_u32(bars + 2 * STAGES + 2);
-    const uint32_t ebar = smem_u32(bars + 2 * STAGES + 4);
-    const uint32_t drain = smem_u32(bars + 2 * STAGES + 5);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 6);
+    const uint32_t acce0 = smem_u32(bars + 2 * STAGES + NACC);
+    const uint32_t ebar = smem_u32(bars + 2 * STAGES + 2 * NACC);
+    const uint32_t drain = smem_u32(bars + 2 * STAGES + 2 * NACC + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 2 * NACC + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     UnitRing ring;
-    ring.full0 = smem_u32(bars + 2 * STAGES + 8);
-    ring.empty0 = smem_u32(bars + 2 * STAGES + 8 + UNIT_RING);
-    ring.slot = reinterpret_cast<volatile int *>(bars + 2 * STAGES + 8 + 2 * UNIT_RING);
+    ring.full0 = smem_u32(bars + 2 * STAGES + 2 * NACC + 4);
+    ring.empty0 = smem_u32(bars + 2 * STAGES + 2 * NACC + 4 + UNIT_RING);
+    ring.slot = reinterpret_cast<volatile int *>(bars + 2 * STAGES + 2 * NACC + 4 + 2 * UNIT_RING);
     float *comb = reinterpret_cast<float *>(sm + (size_t)STAGES * STAGE_BYTES + BAR_BYTES);
     // the filter sums of each epilogue thread live in shared memory between
     // wavelength tiles (the group loop keeps 64 running-sum registers)
-    float *accbuf = comb + BM * QMAX;
+    float *accbuf = comb + COMB_BYTES / 4;
     const uint32_t sbase = smem_u32(sm);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -193,7 +201,7 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NACC; ++i) {
             mbar_init(accf0 + 8 * i, 1);
             mbar_init(acce0 + 8 * i, NUM_EPI_WARPS);
         }
@@ -262,6 +270,7 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
             int stage = 0, as = 0;
             uint32_t phase = 0, aphase = 0;
             bool ok = true;
+            unsigned long long nblk = 0;
             while (ok) {
                 int u;
                 if (!ring_next(ring, u, abort_flag, a.err) || u < 0) break;
@@ -278,6 +287,7 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                         GroupBlocks it(km, a.g_i0[g], a.g_i1[g]);
                         bool first = true;
                         for (int kb = it.next(); kb < it.hi; kb = it.next()) {
+                            ++nblk;
                             if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, a.err)) { ok = false; break; }
                             tc_fence_after();
                             const uint32_t st = sbase + stage * STAGE_BYTES;
@@ -297,9 +307,10 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                         }
                         if (!ok) break;
                         mma_commit(accf0 + 8 * as);
-                        if (++as == 2) { as = 0; aphase ^= 1u; }
+                        if (++as == NACC) { as = 0; aphase ^= 1u; }
                     }
             }
+            if (a.kblk) atomicAdd(a.kblk, nblk);
             mma_commit(drain);
             const long long t0 = clock64();
             while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
@@ -308,7 +319,7 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
     } else {
         // ---------------------------------------------------------------- epilogue
         const int qd = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int cg = (warp - 2) >> 2;   // column group
         const int row = qd * 32 + lane;
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
         int as = 0;
@@ -339,9 +350,11 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
             float *accs = accbuf + (threadIdx.x - 64) * QMAX;
 #pragma unroll
             for (int q = 0; q < 4 * Q4; ++q) accs[q] = 0.f;
-            const int law = (a.dust_law == DSPS_DUST_SALIM ? 1 : 0) + (a.bump ? 2 : 0);
+            // the dust law (LAW bit 0: k0 tilted by delta; bit 1: the bump), fixed at compile time
+            constexpr bool SALIM = (LAW & 1) != 0, BUMP = (LAW & 2) != 0;
+            constexpr int NCHUNK = EPI_COLS / 16;
             for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
-                const int nb = nt * BN + half * EPI_COLS;
+                const int nb = nt * BN + cg * EPI_COLS;
                 float run[EPI_COLS / 32][32];
 #pragma unroll
                 for (int c = 0; c < EPI_COLS / 32; ++c)
@@ -359,31 +372,29 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                     const float T = a.g_T[g];
                     const float Avg = group_dust_value(T, avy, avo), dlg = group_dust_value(T, dly, dlo);
                     const float alpha = -0.4f * 3.32192809488736235f * Avg;
-                    const float beta = a.dust_law == DSPS_DUST_SALIM ? dlg : dlg - 0.7f;
-                    const float eg = a.bump ? (0.85f - 1.9f * dlg) * (1.f / 4.05f) : 0.f;
+                    const float beta = SALIM ? dlg : dlg - 0.7f;
+                    const float eg = BUMP ? (0.85f - 1.9f * dlg) * (1.f / 4.05f) : 0.f;
                     const float ustep = ex2_fast(beta * a.cc.dell);
-                    const uint32_t tacc = tmem_base + lane_base + (uint32_t)(as * BN + half * EPI_COLS);
+                    const uint32_t tacc = tmem_base + lane_base + (uint32_t)(as * BN + cg * EPI_COLS);
+                    // chunk c + 1 is read from TMEM while chunk c is added
+                    uint32_t rb[2][16];
+                    tmem_ld16_async(tacc, rb[0]);
+                    tmem_wait_ld16(rb[0]);
 #pragma unroll
-                    for (int c = 0; c < EPI_COLS / 16; ++c) {
-                        uint32_t r[16];
-                        tmem_ld16(tacc + c * 16, r);
-                        if (c == EPI_COLS / 16 - 1) {
+                    for (int c = 0; c < NCHUNK; ++c) {
+                        if (c == NCHUNK - 1) {
                             // this warp's reads of the accumulator are done
                             tc_fence_before();
                             __syncwarp();
                             if (lane == 0) mbar_arrive(acce0 + 8 * as);
                         }
-                        const int n0 = nb + c * 16;
-                        float *rr = &run[c >> 1][(c & 1) * 16];
-                        switch (law) {
-                        case 0: add_group_chunk<false, false>(rr, r, n0, alpha, beta, ustep, eg, a.cc, valid); break;
-                        case 1: add_group_chunk<true, false>(rr, r, n0, alpha, beta, ustep, eg, a.cc, valid); break;
-                        case 2: add_group_chunk<false, true>(rr, r, n0, alpha, beta, ustep, eg, a.cc, valid); break;
-                        default: add_group_chunk<true, true>(rr, r, n0, alpha, beta, ustep, eg, a.cc, valid); break;
-                        }
+                        if (c + 1 < NCHUNK) tmem_ld16_async(tacc + (c + 1) * 16, rb[(c + 1) & 1]);
+                        add_group_chunk<SALIM, BUMP>(&run[c >> 1][(c & 1) * 16], rb[c & 1], nb + c * 16, alpha, beta,
+                                                     ustep, eg, a.cc);
+                        if (c + 1 < NCHUNK) tmem_wait_ld16(rb[(c + 1) & 1]);
                     }
                     any = true;
-                    if (++as == 2) { as = 0; aphase ^= 1u; }
+                    if (++as == NACC) { as = 0; aphase ^= 1u; }
                 }
                 if (!ok) break;
                 if (!any || !valid) continue;
@@ -406,11 +417,12 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
             float acc[4 * Q4];
 #pragma unroll
             for (int q = 0; q < 4 * Q4; ++q) acc[q] = accs[q];
-            // combine the two column halves of each row (bounded barrier)
-            float *cr = comb + row * QMAX;
-            if (half == 1)
+            // combine the column groups of each row in a fixed order (bounded barrier)
+            if (cg > 0) {
+                float *cr = comb + ((cg - 1) * BM + row) * QMAX;
 #pragma unroll
                 for (int q = 0; q < 4 * Q4; ++q) cr[q] = acc[q];
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(ebar);
             int got = 1;
@@ -418,12 +430,17 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
             got = __shfl_sync(0xffffffffu, got, 0);
             ephase ^= 1u;
             if (!got) break;
-            if (half == 0 && rowg < a.n) {
+            if (cg == 0 && rowg < a.n) {
+#pragma unroll
+                for (int k = 1; k < SPLIT; ++k) {
+                    const float *cr = comb + ((k - 1) * BM + row) * QMAX;
+#pragma unroll
+                    for (int q = 0; q < 4 * Q4; ++q) acc[q] += cr[q];
+                }
                 float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)part * a.n + rowg) * (4 * Q4));
 #pragma unroll
                 for (int qq = 0; qq < Q4; ++qq)
-                    dst[qq] = make_float4(acc[4 * qq] + cr[4 * qq], acc[4 * qq + 1] + cr[4 * qq + 1],
-                                          acc[4 * qq + 2] + cr[4 * qq + 2], acc[4 * qq + 3] + cr[4 * qq + 3]);
+                    dst[qq] = make_float4(acc[4 * qq], acc[4 * qq + 1], acc[4 * qq + 2], acc[4 * qq + 3]);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(ebar);
@@ -444,14 +461,25 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
     }
 }
 
+template <int Q4, int LAW>
+cudaError_t launch_ql(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
+                      const GArgs &a, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(phot_tc_groups_kernel<Q4, LAW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    phot_tc_groups_kernel<Q4, LAW><<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
+    return cudaGetLastError();
+}
+
 template <int Q4>
 cudaError_t launch_q4(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
                       const GArgs &a, int grid, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(phot_tc_groups_kernel<Q4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    phot_tc_groups_kernel<Q4><<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
-    return cudaGetLastError();
+    switch ((a.dust_law == DSPS_DUST_SALIM ? 1 : 0) + (a.bump ? 2 : 0)) {
+    case 0: return launch_ql<Q4, 0>(ah, al, bh, bl, a, grid, s);
+    case 1: return launch_ql<Q4, 1>(ah, al, bh, bl, a, grid, s);
+    case 2: return launch_ql<Q4, 2>(ah, al, bh, bl, a, grid, s);
+    default: return launch_ql<Q4, 3>(ah, al, bh, bl, a, grid, s);
+    }
 }
 
 }  // namespace
@@ -496,6 +524,7 @@ cudaError_t launch_phot_tc_groups(const Ctx &c, const Workspace &w, const Filter
     }
     a.n = n;
     a.sched = w.sched;
+    a.kblk = w.stats ? w.stats + 2 : nullptr;
     a.partial = w.partial;
     a.err = c.d_err;
     const int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;

@@ -352,7 +352,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     chk(dmalloc(&c->d_uedge, (size_t)c->n_u + 1));
     chk(dmalloc(&c->d_ws_block, workspace_bytes(*c, c->chunk, false)));
     chk(dmalloc(&c->d_err, 1));
-    chk(dmalloc(&c->d_stats, 2));
+    chk(dmalloc(&c->d_stats, 3));
     chk(dmalloc(&c->d_L_hi, (size_t)c->KZ_pad * c->N_pad));
     chk(dmalloc(&c->d_Ld32, (size_t)c->KZ_pad * c->N_pad));
     chk(dmalloc(&c->d_wmul_d, (size_t)c->KZ_pad));
@@ -440,7 +440,7 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     std::vector<float> glf(gl.begin(), gl.end());
     up(c->d_glut, glf.data(), glf.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 3 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = prepare_ssp_device(*c, g->l_ssp);
     if (e != cudaSuccess) {
         int r = cuda_fail(e, "dsps_create upload");
@@ -794,10 +794,11 @@ int dsps_profile_read(dsps_ctx *ctx, dsps_profile_t *out) {
         c->ev_pool.push_back(r.b);
     }
     c->prof_recs.clear();
-    unsigned long long counts[2] = {0, 0};
+    unsigned long long counts[3] = {0, 0, 0};
     if (cudaMemcpy(counts, c->d_stats, sizeof counts, cudaMemcpyDeviceToHost) == cudaSuccess) {
         out->tc_kblocks = (int64_t)counts[0];
         out->simt_steps = (int64_t)counts[1];
+        out->tc_kblocks_n128 = (int64_t)counts[2];
         cudaMemset(c->d_stats, 0, sizeof counts);
     }
     return rc;

@@ -248,7 +248,7 @@ struct Ctx {
     int64_t chunk = 0;                      // galaxies per chunk (multiple of 128)
     unsigned char *d_ws_block = nullptr;    // device block holding ws (without Shat)
     Workspace ws;
-    unsigned long long *d_stats = nullptr;  // [2] tensor-core blocks, FP32 tile steps executed (profiling)
+    unsigned long long *d_stats = nullptr;  // [3] tensor-core blocks, FP32 tile steps, 128-wide tensor-core blocks (profiling)
     float *d_Ld32 = nullptr;                // [KZ_pad][N_pad] differenced block (FP32 adjoint; prep.cu)
     float *d_wmul_d = nullptr;              // [KZ_pad] 2^E'_kz of the differenced rows
     __nv_bfloat16 *d_L_hi = nullptr;        // [KZ_pad][N_pad] differenced block, row-scaled hi (tensor adjoint)
@@ -325,9 +325,11 @@ Workspace workspace_carve(const Ctx &c, void *base, int64_t rows, bool adjoint);
 
 // group: with age-dependent dust, the weights of the group's ages only and its
 // dust constants in aux (nullptr: all ages, one curve).
+// aux_yo: aux holds the young and old dust values instead of one curve's
+// constants (a one-launch age-dependent dust contraction).
 cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const float *params, int64_t G_stride,
                            int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted = false,
-                           const DustGroup *group = nullptr);
+                           const DustGroup *group = nullptr, bool aux_yo = false);
 
 // Counting sort of the chunk's galaxies into w.perm by (coarse redshift shift,
 // mean metallicity); also resets w.trange and w.kmask.
@@ -366,6 +368,15 @@ inline void group_k_range(const Ctx &c, const DustGroup *gr, int bk, int &k_lo, 
     const int hi = (gr->i1 * per_age + bk - 1) / bk * bk;
     k_hi = hi < c.K_pad ? hi : c.K_pad;
 }
+
+// Most dust groups a one-launch age-dependent contraction takes.
+constexpr int AGEDEP_MAX_GROUPS = 128;
+
+// Age-dependent dust, FP32 form, every group in one launch (phot_simt.cu):
+// per-part filter sums of the sorted rows from the weights of all ages
+// (launch_weights with aux_yo); *parts gets the number of parts.
+cudaError_t launch_phot_simt_groups(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int *parts,
+                                    cudaStream_t s);
 
 // Writes per-part filter sums to ctx.d_partial (sorted rows); returns the
 // number of parts through *parts.

@@ -48,6 +48,8 @@ struct WArgs {
     int age_lo, age_hi;          // age bins whose weights are written (the others are 0): a dust group
     float dust_T;                // the group's weight of the old-star dust values
     int dust_row_old;            // parameter row of Av_old (delta_old next), or -1: one curve
+    int aux_yo;                  // aux gets the young and old dust values (a one-launch contraction of
+                                 // every dust group forms each group's curve from them)
     double t0, h, inv_h, dz, inv_dz, zmax, dlnlam;
     float zmax_f;          // largest float <= zmax (z <= zmax_f iff (double)z <= zmax)
     float t0_f, h_f, dlnlam_f;   // FP32 copies used by the per-galaxy warps
@@ -696,9 +698,9 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
             dl = group_dust_value(a.dust_T, p[9], dlo);
         }
         if (!valid) atomicOr(a.err, DERR_PARAM);
-        if (MODE == W_OMEGA_BF16X2_AB) {
+        if (MODE == W_OMEGA_BF16X2_AB || a.aux_yo) {
             // the young and old dust values; each group's curve is formed from
-            // them in the fused contraction (agedep_tc.cu)
+            // them in the one-launch contraction (agedep_tc.cu, phot_simt.cu)
             float *ax = a.aux + gi * AUX_STRIDE;
             ax[0] = p[8];
             ax[1] = p[9];
@@ -1217,7 +1219,7 @@ cudaError_t launch_weights_vjp(const Ctx &c, const Workspace &w, const float *pa
 
 cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const float *params, int64_t G_stride,
                            int64_t g_begin, int64_t n, float *w_msun, cudaStream_t s, bool sorted,
-                           const DustGroup *group) {
+                           const DustGroup *group, bool aux_yo) {
     if (n <= 0) return cudaSuccess;
     WArgs a = make_wargs(c, w, params, G_stride, g_begin, n);
     if (group) {
@@ -1226,7 +1228,8 @@ cudaError_t launch_weights(const Ctx &c, const Workspace &w, int mode, const flo
         a.dust_T = group->T;
         a.dust_row_old = c.row_dust_old;
     }
-    if (mode == W_OMEGA_BF16X2_AB) a.dust_row_old = c.row_dust_old;   // both dust values into aux
+    if (mode == W_OMEGA_BF16X2_AB || aux_yo) a.dust_row_old = c.row_dust_old;   // both dust values into aux
+    a.aux_yo = aux_yo ? 1 : 0;
     a.w_msun = w_msun;
     a.perm = sorted ? w.perm : nullptr;
     a.gidx = sorted ? w.gidx : nullptr;

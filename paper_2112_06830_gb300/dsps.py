@@ -74,7 +74,8 @@ DSPS_PROF_KINDS = 4
 
 class dsps_profile_t(C.Structure):
     _fields_ = [("launches", C.c_int64 * DSPS_PROF_KINDS), ("ms", C.c_double * DSPS_PROF_KINDS),
-                ("tc_kblocks", C.c_int64), ("simt_steps", C.c_int64)]
+                ("tc_kblocks", C.c_int64), ("simt_steps", C.c_int64),
+                ("tc_kblocks_n128", C.c_int64)]
 
 
 DSPS_MAX_HIST_BINS = 4096
@@ -300,13 +301,16 @@ def dsps_profile_enable(ctx, enable=True):
 
 def dsps_profile_read(ctx):
     """{kind: (launches, ms)} for kinds 0 weights/sort/combine, 1 fp32, 2 tensor, 3 adjoint, plus
-    "tc_kblocks": 128 x 256 x 32 split-bf16 tensor-core block products executed and
-    "simt_steps": 128 x 128 x 16 FP32 tile steps of the FP32 photometry contraction."""
+    "tc_kblocks": 128 x 256 x 32 split-bf16 tensor-core block products executed,
+    "simt_steps": 128 x 128 x 16 FP32 tile steps of the FP32 photometry contraction and
+    "tc_kblocks_n128": 128 x 128 x 32 split-bf16 block products of the one-launch
+    age-dependent dust contraction."""
     p = dsps_profile_t()
     _check(load().dsps_profile_read(ctx, C.byref(p)), "dsps_profile_read")
     out = {k: (int(p.launches[k]), float(p.ms[k])) for k in range(DSPS_PROF_KINDS)}
     out["tc_kblocks"] = int(p.tc_kblocks)
     out["simt_steps"] = int(p.simt_steps)
+    out["tc_kblocks_n128"] = int(p.tc_kblocks_n128)
     return out
 
 
