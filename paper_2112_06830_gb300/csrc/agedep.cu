@@ -77,6 +77,7 @@ struct FinalArgs {
     const float *mag_bar;     // [G][Q] of the chunk (gradient), or nullptr
     float *cq;                // [n][QS] Nbar (gradient)
     float *param_bar;         // [ngrad][G_stride] (gradient)
+    int dust_rows;            // write the dust rows from gacc's A and D sums (else left to agedep_dust_rows_kernel)
 };
 
 // Magnitudes (or histogram counts) from the summed fluxes; with the gradient,
@@ -112,11 +113,39 @@ __global__ void agedep_final_kernel(FinalArgs a) {
     }
     const float nan = __int_as_float(0x7fc00000);
     const int64_t col = a.g_begin + g;
+    a.param_bar[10 * a.G_stride + col] = valid ? lm : nan;
+    if (!a.dust_rows) return;
     a.param_bar[8 * a.G_stride + col] = valid ? avy : nan;
     a.param_bar[9 * a.G_stride + col] = valid ? dly : nan;
-    a.param_bar[10 * a.G_stride + col] = valid ? lm : nan;
     a.param_bar[(int64_t)a.grow_old * a.G_stride + col] = valid ? avo : nan;
     a.param_bar[(int64_t)(a.grow_old + 1) * a.G_stride + col] = valid ? dlo : nan;
+}
+
+// The dust rows of param_bar from the one-launch gradient pass
+// (launch_phot_tc_groups with G): per sorted row, the parts' sums (fixed
+// order) of sum_g (1 - T_g) s_g, T_g s_g, (1 - T_g) Av_g t_g and T_g Av_g t_g,
+// s_g = sum_n G_n c_g,n F_g,n S_g,n and t_g with dc_g/ddelta, times
+// -0.4 ln 10 (dF/dAv = -0.4 ln10 c F, Eq. attenuation): dLoss/dAv_young,
+// dLoss/dAv_old, dLoss/ddelta_young, dLoss/ddelta_old.
+__global__ void agedep_dust_rows_kernel(const float *dpart, int parts, int64_t n, const float *aux, const int *gidx,
+                                        int64_t G_stride, int64_t g_begin, int grow_old, float *param_bar) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int p = 0; p < parts; ++p) {
+        const float4 v = *reinterpret_cast<const float4 *>(dpart + ((int64_t)p * n + r) * 4);
+        s[0] += v.x;
+        s[1] += v.y;
+        s[2] += v.z;
+        s[3] += v.w;
+    }
+    const bool valid = aux[r * AUX_STRIDE + 3] != 0.f;
+    const float kd = -0.4f * 2.302585092994046f, nan = __int_as_float(0x7fc00000);
+    const int64_t col = g_begin + (gidx ? (int64_t)gidx[r] : r);
+    param_bar[8 * G_stride + col] = valid ? kd * s[0] : nan;
+    param_bar[(int64_t)grow_old * G_stride + col] = valid ? kd * s[1] : nan;
+    param_bar[9 * G_stride + col] = valid ? kd * s[2] : nan;
+    param_bar[(int64_t)(grow_old + 1) * G_stride + col] = valid ? kd * s[3] : nan;
 }
 
 // Keeps, in the merged adjoint rows, the columns of the group's ages
@@ -328,8 +357,9 @@ cudaError_t launch_group_acc(const Workspace &w, const FilterSet &fs, int64_t n,
 
 cudaError_t launch_final(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, bool sorted, float *mags,
                          const HistArgs *hist, const float *mag_bar, float *param_bar, int64_t G_stride,
-                         int64_t g_begin, cudaStream_t s) {
+                         int64_t g_begin, cudaStream_t s, bool dust_rows = true) {
     FinalArgs a{};
+    a.dust_rows = dust_rows ? 1 : 0;
     a.gacc = w.gacc;
     a.n = n;
     a.G_stride = G_stride;
@@ -526,13 +556,35 @@ int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, con
     w.stats = (profile && c->prof) ? c->d_stats : nullptr;
     const bool prof = profile && c->prof;
     const bool tc = precision == DSPS_PREC_BF16X3;
+    // split-bf16 with the one-launch forward: the fluxes from that launch, the
+    // dust rows from its gradient pass over the dust-free adjoint spectrum
+    const bool fused = tc && c->opts.agedep_fused && agedep_fused_ok(*c);
     for (int64_t g0 = 0; g0 < n_gal; g0 += w.cap) {
         const int64_t n = n_gal - g0 < w.cap ? n_gal - g0 : w.cap;
-        cudaError_t e = groups_forward(c, w, n_gal, g0, n, params, fs, tc, true, s, prof);
+        cudaError_t e = cudaSuccess;
+        int parts = 0;
+        if (fused) {
+            {
+                ProfScope ps(*c, 0, s, prof);
+                e = launch_zsort(*c, w, params, n_gal, g0, n, s);
+                if (e == cudaSuccess)
+                    e = launch_weights(*c, w, W_OMEGA_BF16X2_AB, params, n_gal, g0, n, nullptr, s, true);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 2, s, prof);
+                e = launch_phot_tc_groups(*c, w, fs, n, &parts, s);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 0, s, prof);
+                e = launch_group_acc(w, fs, n, parts, 1, 0.f, false, true, s);
+            }
+        } else {
+            e = groups_forward(c, w, n_gal, g0, n, params, fs, tc, true, s, prof);
+        }
         if (e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);
             e = launch_final(*c, w, fs, n, true, mags ? mags + g0 * fs.Q : nullptr, nullptr, mag_bar + g0 * fs.Q,
-                             param_bar, n_gal, g0, s);
+                             param_bar, n_gal, g0, s, !fused);
         }
         // adjoint of the weights, merged over the groups (the group's curve in
         // aux; the tile ranges depend on z alone and stay): padding columns
@@ -544,7 +596,23 @@ int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, con
         if (e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);
             e = launch_merge_rows(*c, w, n, DustGroup{0, 0, 0.f}, true, s);
-            if (any1 && e == cudaSuccess) e = launch_shat(*c, w, fs, n, false, c->opts.band_skip != 0, s, false);
+            if ((any1 || fused) && e == cudaSuccess)
+                e = launch_shat(*c, w, fs, n, false, c->opts.band_skip != 0, s, false);
+        }
+        if (fused && e == cudaSuccess) {
+            // the dust rows: every group in one launch again, its epilogue
+            // folding each group's block with G (aux still holds the young and
+            // old values: the groups below rewrite it)
+            {
+                ProfScope ps(*c, 2, s, prof);
+                e = launch_phot_tc_groups(*c, w, fs, n, &parts, s, reinterpret_cast<const float *>(w.shat));
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(*c, 3, s, prof);
+                agedep_dust_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+                    w.partial, parts, n, w.aux, w.gidx, n_gal, g0, c->grow_dust_old, param_bar);
+                e = cudaGetLastError();
+            }
         }
         if (any1 && e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);

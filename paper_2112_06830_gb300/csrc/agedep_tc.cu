@@ -79,6 +79,11 @@ struct GArgs {
     int *sched;                    // unit counter, zero at launch
     unsigned long long *kblk;      // 128 x 128 x 32 block products executed (profiling), or nullptr
     float *partial;                // [parts][n][4*Q4]
+    // gradient pass (GRAD): the dust-free adjoint spectrum and the dust sums
+    const float *G;                // [n][N_pad] dLoss/dS without dust, each row tile's band columns
+    int N_pad;
+    VjpBand band;                  // the columns of G written
+    float *dpart;                  // out: [parts][n][4] the sums of grad_group_chunk, weighted per group
     unsigned *err;
 };
 
@@ -168,7 +173,32 @@ __device__ __forceinline__ void add_group_chunk(float *run, const uint32_t (&r)[
     }
 }
 
-template <int Q4, int LAW>
+// Gradient pass: with x_n = S_g,n F_g,n G_n (G the dust-free adjoint spectrum,
+// dLoss/dS at node n), adds sum_n x_n c_g,n to sA and sum_n x_n dc_g,n/ddelta
+// to sD over 16 nodes; dF/dAv = -0.4 ln10 c F and dF/ddelta = -0.4 ln10 Av
+// dc/ddelta F (Eq. attenuation), with dc/ddelta = [k0/4.05] u ln(lam/lam_V) +
+// e' D0 (e' = de/ddelta).  lell0 + n ldell = ln(lam_n / lam_V).
+template <bool SALIM, bool BUMP>
+__device__ __forceinline__ void grad_group_chunk(float &sA, float &sD, const float *gk, const uint32_t (&r)[16],
+                                                 int n0, float alpha, float beta, float ustep, float e, float ed,
+                                                 const ColConst &cc, float lell0, float ldell) {
+    float u = ex2_fast(beta * fmaf((float)n0, cc.dell, cc.ell0));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        float cp = u;
+        if constexpr (SALIM) cp *= __ldg(cc.k0 + n0 + j);
+        const float bj = BUMP ? __ldg(cc.bump + n0 + j) : 0.f;
+        const float cn = BUMP ? fmaf(e, bj, cp) : cp;
+        const float x = __uint_as_float(r[j]) * ex2_fast(alpha * cn) * gk[j];
+        sA = fmaf(x, cn, sA);
+        float dc = cp * fmaf((float)(n0 + j), ldell, lell0);
+        if constexpr (BUMP) dc = fmaf(ed, bj, dc);
+        sD = fmaf(x, dc, sD);
+        u *= ustep;
+    }
+}
+
+template <int Q4, int LAW, bool GRAD>
 __global__ void __launch_bounds__(THREADS, 1)
 phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                       const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -353,13 +383,32 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
             // the dust law (LAW bit 0: k0 tilted by delta; bit 1: the bump), fixed at compile time
             constexpr bool SALIM = (LAW & 1) != 0, BUMP = (LAW & 2) != 0;
             constexpr int NCHUNK = EPI_COLS / 16;
+            // gradient pass: sum_g (1 - T_g) s_g, T_g s_g, (1 - T_g) Av_g t_g,
+            // T_g Av_g t_g over this thread's columns, and G's columns
+            float dsum[4] = {0.f, 0.f, 0.f, 0.f};
+            int gc0 = 0, gc1 = 0;
+            if constexpr (GRAD) {
+                int kb0, kb1;
+                vjp_band(a.band, a.trange, mt, a.N_pad, kb0, kb1);
+                gc0 = 32 * kb0;
+                gc1 = 32 * kb1;
+            }
+            const float lell0 = a.cc.ell0 * 0.69314718055994531f, ldell = a.cc.dell * 0.69314718055994531f;
             for (int nt = first_tile(nt0, part, a.parts); ok && nt < nt1; nt += a.parts) {
                 const int nb = nt * BN + cg * EPI_COLS;
+                // forward: the running sum; gradient pass: G at the columns
                 float run[EPI_COLS / 32][32];
 #pragma unroll
                 for (int c = 0; c < EPI_COLS / 32; ++c)
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) run[c][j] = 0.f;
+                    for (int j = 0; j < 32; ++j) {
+                        float v = 0.f;
+                        if constexpr (GRAD) {
+                            const int col = nb + c * 32 + j;
+                            if (valid && rowg < a.n && col >= gc0 && col < gc1) v = a.G[rowg * a.N_pad + col];
+                        }
+                        run[c][j] = v;
+                    }
                 bool any = false;
                 for (int g = 0; ok && g < a.n_groups; ++g) {
                     if (!group_present(km, a.g_i0[g], a.g_i1[g])) continue;
@@ -376,6 +425,7 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                     const float eg = BUMP ? (0.85f - 1.9f * dlg) * (1.f / 4.05f) : 0.f;
                     const float ustep = ex2_fast(beta * a.cc.dell);
                     const uint32_t tacc = tmem_base + lane_base + (uint32_t)(as * BN + cg * EPI_COLS);
+                    float sA = 0.f, sD = 0.f;
                     // chunk c + 1 is read from TMEM while chunk c is added
                     uint32_t rb[2][16];
                     tmem_ld16_async(tacc, rb[0]);
@@ -389,15 +439,26 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                             if (lane == 0) mbar_arrive(acce0 + 8 * as);
                         }
                         if (c + 1 < NCHUNK) tmem_ld16_async(tacc + (c + 1) * 16, rb[(c + 1) & 1]);
-                        add_group_chunk<SALIM, BUMP>(&run[c >> 1][(c & 1) * 16], rb[c & 1], nb + c * 16, alpha, beta,
-                                                     ustep, eg, a.cc);
+                        if constexpr (GRAD)
+                            grad_group_chunk<SALIM, BUMP>(sA, sD, &run[c >> 1][(c & 1) * 16], rb[c & 1], nb + c * 16,
+                                                          alpha, beta, ustep, eg, BUMP ? -1.9f / 4.05f : 0.f, a.cc,
+                                                          lell0, ldell);
+                        else
+                            add_group_chunk<SALIM, BUMP>(&run[c >> 1][(c & 1) * 16], rb[c & 1], nb + c * 16, alpha,
+                                                         beta, ustep, eg, a.cc);
                         if (c + 1 < NCHUNK) tmem_wait_ld16(rb[(c + 1) & 1]);
+                    }
+                    if constexpr (GRAD) {
+                        dsum[0] = fmaf(1.f - T, sA, dsum[0]);
+                        dsum[1] = fmaf(T, sA, dsum[1]);
+                        dsum[2] = fmaf((1.f - T) * Avg, sD, dsum[2]);
+                        dsum[3] = fmaf(T * Avg, sD, dsum[3]);
                     }
                     any = true;
                     if (++as == NACC) { as = 0; aphase ^= 1u; }
                 }
                 if (!ok) break;
-                if (!any || !valid) continue;
+                if (GRAD || !any || !valid) continue;
                 // the attenuated spectrum of the tile: one filter integral
                 const RowConst rc = load_row_const(a.aux, rowg, a.n);
                 float acc[4 * Q4];
@@ -416,7 +477,7 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
             if (!ok) break;
             float acc[4 * Q4];
 #pragma unroll
-            for (int q = 0; q < 4 * Q4; ++q) acc[q] = accs[q];
+            for (int q = 0; q < 4 * Q4; ++q) acc[q] = GRAD ? (q < 4 ? dsum[q] : 0.f) : accs[q];
             // combine the column groups of each row in a fixed order (bounded barrier)
             if (cg > 0) {
                 float *cr = comb + ((cg - 1) * BM + row) * QMAX;
@@ -437,10 +498,15 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
 #pragma unroll
                     for (int q = 0; q < 4 * Q4; ++q) acc[q] += cr[q];
                 }
-                float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)part * a.n + rowg) * (4 * Q4));
+                if constexpr (GRAD) {
+                    *reinterpret_cast<float4 *>(a.dpart + ((int64_t)part * a.n + rowg) * 4) =
+                        make_float4(acc[0], acc[1], acc[2], acc[3]);
+                } else {
+                    float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)part * a.n + rowg) * (4 * Q4));
 #pragma unroll
-                for (int qq = 0; qq < Q4; ++qq)
-                    dst[qq] = make_float4(acc[4 * qq], acc[4 * qq + 1], acc[4 * qq + 2], acc[4 * qq + 3]);
+                    for (int qq = 0; qq < Q4; ++qq)
+                        dst[qq] = make_float4(acc[4 * qq], acc[4 * qq + 1], acc[4 * qq + 2], acc[4 * qq + 3]);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(ebar);
@@ -461,14 +527,21 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
     }
 }
 
+template <int Q4, int LAW, bool GRAD>
+cudaError_t launch_qlg(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
+                       const GArgs &a, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(phot_tc_groups_kernel<Q4, LAW, GRAD>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    phot_tc_groups_kernel<Q4, LAW, GRAD><<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
+    return cudaGetLastError();
+}
+
 template <int Q4, int LAW>
 cudaError_t launch_ql(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
                       const GArgs &a, int grid, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(phot_tc_groups_kernel<Q4, LAW>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    phot_tc_groups_kernel<Q4, LAW><<<grid, THREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, a);
-    return cudaGetLastError();
+    return a.G ? launch_qlg<Q4, LAW, true>(ah, al, bh, bl, a, grid, s)
+               : launch_qlg<Q4, LAW, false>(ah, al, bh, bl, a, grid, s);
 }
 
 template <int Q4>
@@ -490,7 +563,7 @@ bool agedep_fused_ok(const Ctx &c) {
 }
 
 cudaError_t launch_phot_tc_groups(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int *parts,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const float *G) {
     *parts = TC_PARTS;
     if (n <= 0) return cudaSuccess;
     if (fs.Q > QMAX || !agedep_fused_ok(c)) return cudaErrorInvalidValue;
@@ -526,6 +599,10 @@ cudaError_t launch_phot_tc_groups(const Ctx &c, const Workspace &w, const Filter
     a.sched = w.sched;
     a.kblk = w.stats ? w.stats + 2 : nullptr;
     a.partial = w.partial;
+    a.G = G;
+    a.N_pad = c.N_pad;
+    a.band = make_vjp_band(c, fs, c.opts.band_skip != 0);
+    a.dpart = w.partial;
     a.err = c.d_err;
     const int grid = a.n_units < c.num_sms ? a.n_units : c.num_sms;
     cudaError_t e = cudaMemsetAsync(w.sched, 0, sizeof(int), s);

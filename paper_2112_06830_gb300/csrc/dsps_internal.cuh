@@ -392,8 +392,12 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp);
 // launch_combine.  Needs the chunk sorted (launch_zsort) and its weights in the
 // W_OMEGA_BF16X2_AB form.
 bool agedep_fused_ok(const Ctx &c);
+// With G (the dust-free adjoint spectrum of the sorted rows, launch_shat
+// without dust): the gradient pass, writing per part and row the four dust
+// sums (Av and delta, young and old; the -0.4 ln10 factor left out) to
+// w.partial as [parts][n][4].
 cudaError_t launch_phot_tc_groups(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int *parts,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const float *G = nullptr);
 
 // Adjoint (vjp.cu, vjp_tc.cu, weights.cu).
 cudaError_t launch_combine_grad(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int parts,
