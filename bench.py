@@ -658,14 +658,21 @@ def run_ours(a):
     sid_a = ctx_a.add_filters(synth.make_filters(N_FILT))
     d_params_a = torch.from_numpy(synth.with_agedep_dust(params_h, 1, shard_start(rank, G)).astype(np.float32)).cuda()
     d_pbar_a = torch.empty((ctx_a.ngrad, G), dtype=torch.float32, device="cuda")
+    dsps.dsps_profile_enable(ctx_a.handle, True)
     ms_age = timed_fn(lambda: ctx_a.photometry(d_params_a, sid_a, precision=dsps.DSPS_PREC_BF16X3, out=d_mags,
                                                stream=stream))
+    prof_age = dsps.dsps_profile_read(ctx_a.handle)
+    dsps.dsps_profile_enable(ctx_a.handle, False)
     ms_age_fp32 = timed_fn(lambda: ctx_a.photometry(d_params_a, sid_a, precision=dsps.DSPS_PREC_FP32, out=d_mags,
                                                     stream=stream))
     ms_age_grad = timed_fn(lambda: dsps.dsps_photometry_vjp(ctx_a.handle, G, d_params_a.data_ptr(), sid_a,
                                                             dsps.DSPS_PREC_BF16X3, d_mbar.data_ptr(),
                                                             d_mags.data_ptr(), d_pbar_a.data_ptr(),
                                                             stream.cuda_stream))
+    ms_age_grad_fp32 = timed_fn(lambda: dsps.dsps_photometry_vjp(ctx_a.handle, G, d_params_a.data_ptr(), sid_a,
+                                                                 dsps.DSPS_PREC_FP32, d_mbar.data_ptr(),
+                                                                 d_mags.data_ptr(), d_pbar_a.data_ptr(),
+                                                                 stream.cuda_stream))
     assert torch.isfinite(d_pbar_a).all()
     ctx_a.close()
     # the line width under the same dust: a window spectrum per group,
@@ -838,8 +845,22 @@ def run_ours(a):
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 (FFMA) x {mhz:.0f} MHz",
                 "ms_per_launch": per_launch_ms, "steps_per_launch": steps}
 
+    def groups_roofline(prof):
+        launches, kms = prof[2]
+        per_launch_ms = kms / max(launches, 1)
+        kblocks = prof["tc_kblocks_n128"] / max(launches, 1)
+        # three bf16 products per multiply-add in each executed 128 x 128 x 32
+        # block (the age blocks of each dust group that a tile's weights fill)
+        exec_flops = kblocks * 128 * 128 * 32 * 2.0 * 3
+        return {"bound": "tensor", "achieved": exec_flops / (per_launch_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "frac": exec_flops / (per_launch_ms * 1e-3) / 1e12 / peak, "traffic": None,
+                "kernel": "phot_tc_groups_kernel (every dust group in one tcgen05 launch)",
+                "peak_source": f"{peak_src} bf16 burst", "ms_per_launch": per_launch_ms,
+                "kblocks_n128_per_launch": kblocks}
+
     roof = tc_roofline(prof_tc)
     out_neb_roof = tc_roofline(prof_neb)
+    age_roof = groups_roofline(prof_age)
     roof["traffic"] = _traffic("phot_tc_kernel")
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof_dense = tc_roofline(prof_dense)
@@ -900,13 +921,18 @@ def run_ours(a):
                             "split-bf16; gradient with d/du_mean, d/du_sigma"},
         "agedep_dust": {"value": ws * G * N_FILT / (ms_age * 1e-3), "ms_per_step": ms_age,
                         "fwd_grad": {"value": ws * G * N_FILT / (ms_age_grad * 1e-3), "ms_per_step": ms_age_grad},
-                        "fp32": {"value": ws * G * N_FILT / (ms_age_fp32 * 1e-3), "ms_per_step": ms_age_fp32},
+                        "fp32": {"value": ws * G * N_FILT / (ms_age_fp32 * 1e-3), "ms_per_step": ms_age_fp32,
+                                 "fwd_grad": {"value": ws * G * N_FILT / (ms_age_grad_fp32 * 1e-3),
+                                              "ms_per_step": ms_age_grad_fp32}},
+                        "roofline": age_roof,
                         "line_ew": {"value": ws * G / (ms_age_ew * 1e-3), "unit": "galaxy-EWs/s",
                                     "ms_per_step": ms_age_ew,
                                     "fwd_grad": {"value": ws * G / (ms_age_ew_grad * 1e-3),
                                                  "ms_per_step": ms_age_ew_grad}},
-                        "note": "age-dependent dust, T_erf transition at 10 Myr over 0.1 dex: one split-bf16 "
-                                "contraction per group of age bins sharing a curve (young, each transition bin, old); "
+                        "note": "age-dependent dust, T_erf transition at 10 Myr over 0.1 dex, 16 groups of age bins "
+                                "sharing a curve (young, each transition bin, old): forward with every group in one "
+                                "launch (split-bf16 and FP32); gradient: split-bf16 fluxes and dust rows from that "
+                                "launch and a second pass of it, the weights adjoint per group; "
                                 "line width: FP32 window spectrum per group over the group's ages"},
         "sfh_table": {"value": ws * G * N_FILT / (ms_tab * 1e-3), "ms_per_step": ms_tab,
                       "fwd_grad": {"value": ws * G * N_FILT / (ms_tab_grad * 1e-3), "ms_per_step": ms_tab_grad},

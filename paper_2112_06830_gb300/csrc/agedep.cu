@@ -198,17 +198,25 @@ __global__ void merge_rows_kernel(const float *__restrict__ src, float *__restri
 // one-age groups) and F_g the group's attenuation -- FP32 products in place
 // of an adjoint contraction over every K column of which a group keeps n_z.
 // Stored divided by wmul_d (a power of two) when the weights adjoint expects
-// the tensor form's scaled rows.  One block per (128-row tile, group,
+// the tensor form's scaled rows.  One block per (256-row tile, group,
 // section): the group's dust constants of each row come from its parameters
 // (Sec. 3.4.1), the band is walked in 16-column chunks with the next chunk's
-// G and Ld loaded into registers while the current one is contracted, G F_g
-// (each thread staging eight columns of one row, whose group curve it keeps
-// in registers) and the group's n_z rows of Ld staged in shared memory; thread t
-// accumulates rows t / 4 and t / 4 + 64 over the metallicity bins
-// j = (t & 3) + 4 m, m < MAXM / 2, in increasing column order.  The groups
-// (and sections) are the grid's fastest index, so a tile's blocks run
-// together and share its G in L2.
-constexpr int A1_ROWS = 128, A1_CHUNK = 16, A1_THREADS = 256, A1_LD = A1_CHUNK + 4, A1_MAXG = 64;
+// G and Ld loaded into registers while the current one is contracted; thread t
+// stages row t's 16 columns of G F_g (the power law stepped from column to
+// column, one ex2 per column for F_g) and the group's n_z rows of Ld are
+// staged beside them in shared memory; thread t accumulates rows t / 4 + 64 h
+// (h < 4) over the metallicity bins j = (t & 3) + 4 m, m < MAXM / 2, in
+// increasing column order.  The groups (and sections) are the grid's fastest
+// index, so a tile's blocks run together and share its G in L2.
+constexpr int A1_ROWS = 256, A1_CHUNK = 16, A1_THREADS = 256, A1_LD = A1_CHUNK + 4, A1_MAXG = 64;
+constexpr int A1_RPT = A1_ROWS / 64;   // rows per thread in the contraction
+
+// 2^x in one MUFU instruction (PTX ex2.approx, relative error below 2^-22).
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 struct Age1Set {
     int n;                   // one-age groups (<= A1_MAXG per launch)
@@ -233,18 +241,16 @@ __global__ void __launch_bounds__(A1_THREADS, 3) age1_adjoint_kernel(const Age1A
     __shared__ __align__(16) float As[A1_ROWS][A1_LD];    // G F_g, [row][column]
     __shared__ __align__(16) float Bs[2 * MAXM][A1_LD];   // Ld rows of the group's columns, [j][column]
     constexpr int LPT = (2 * MAXM * A1_CHUNK + A1_THREADS - 1) / A1_THREADS;   // Ld values per thread
-    constexpr int SPT = A1_ROWS * A1_CHUNK / A1_THREADS;                       // G values per thread (8)
+    static_assert(A1_ROWS == A1_THREADS && A1_CHUNK == 16, "staging: one row of 16 columns per thread");
     const int tid = threadIdx.x, mt = blockIdx.y;
     const int gi = blockIdx.x / a.n_u, u = blockIdx.x - gi * a.n_u;
     const int i_age = set.age[gi];
     const float T = set.T[gi];
     const int64_t r0 = (int64_t)mt * A1_ROWS;
     for (int e = tid; e < 2 * MAXM * A1_LD; e += A1_THREADS) (&Bs[0][0])[e] = 0.f;   // rows j >= n_z stay 0
-    // staging role: row sq of the tile, columns sk .. sk + 7 of each chunk,
-    // with the row's group curve in registers
-    const int sq = tid >> 1, sk = (tid & 1) * SPT;
-    const int64_t sr = r0 + sq;
-    RowConst rc{0.f, 0.f, {0.f, 1.f, 0.f, 0.f}, 0, true, 0.f, 0.f};
+    // staging role: row tid of the tile, with the row's group curve in registers
+    const int64_t sr = r0 + tid;
+    float alpha = 0.f, beta = 0.f, eb = 0.f;
     if (sr < a.n) {
         float ax[AUX_STRIDE] = {};
         const int64_t g = a.g_begin + (a.gidx ? a.gidx[sr] : sr);
@@ -252,21 +258,40 @@ __global__ void __launch_bounds__(A1_THREADS, 3) age1_adjoint_kernel(const Age1A
         const float avo = a.params[(int64_t)a.row_old * a.G_stride + g];
         const float dlo = a.params[(int64_t)(a.row_old + 1) * a.G_stride + g];
         store_dust_aux(ax, group_dust_value(T, avy, avo), group_dust_value(T, dly, dlo), a.dust_law, a.bump);
-        rc.alpha = ax[0];
-        rc.beta = ax[1];
-        rc.e = ax[6];
+        alpha = ax[0];
+        beta = ax[1];
+        eb = ax[6];
     }
-    int kb0, kb1;
-    vjp_band(a.band, a.trange, mt, a.N_pad, kb0, kb1);
+    const float ustep = exp2f(beta * a.cc.dell);
+    // the bands of the block's two 128-row tiles (G is written over each
+    // tile's band only: a row reads zeros outside its own)
+    static_assert(A1_ROWS == 256, "two 128-row tiles per block");
+    int kb0, kb1, ob0, ob1;
+    vjp_band(a.band, a.trange, 2 * mt, a.N_pad, kb0, kb1);
+    ob0 = kb0;
+    ob1 = kb1;
+    if ((int64_t)(2 * mt + 1) * 128 < a.n) {
+        int kc0, kc1;
+        vjp_band(a.band, a.trange, 2 * mt + 1, a.N_pad, kc0, kc1);
+        if (tid >= 128) {
+            ob0 = kc0;
+            ob1 = kc1;
+        }
+        kb0 = min(kb0, kc0);
+        kb1 = max(kb1, kc1);
+    }
     const int colz = u * a.SEC + i_age;   // column of metallicity bin 0 in this section
     // the band in columns (vjp_band counts 32-column blocks), or the given range
-    const int cbeg = a.col1 > a.col0 ? a.col0 : kb0 * 32, cend = a.col1 > a.col0 ? a.col1 : kb1 * 32;
-    float4 gv[SPT / 4];
+    const bool given = a.col1 > a.col0;
+    const int cbeg = given ? a.col0 : kb0 * 32, cend = given ? a.col1 : kb1 * 32;
+    const int own0 = given ? a.col0 : ob0 * 32, own1 = given ? a.col1 : ob1 * 32;
+    float4 gv[4];
     float lv[LPT];
     auto load = [&](int c0) {
-        const float4 *src = reinterpret_cast<const float4 *>(a.G + sr * a.N_pad + c0 + sk);
+        const bool in = sr < a.n && c0 >= own0 && c0 < own1;   // chunks and bands are 16-aligned
+        const float4 *src = reinterpret_cast<const float4 *>(a.G + sr * a.N_pad + c0);
 #pragma unroll
-        for (int s = 0; s < SPT / 4; ++s) gv[s] = sr < a.n ? src[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int s = 0; s < 4; ++s) gv[s] = in ? src[s] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int t = 0; t < LPT; ++t) {
             const int e = tid + t * A1_THREADS, j = e / A1_CHUNK, k = e % A1_CHUNK;
@@ -274,17 +299,21 @@ __global__ void __launch_bounds__(A1_THREADS, 3) age1_adjoint_kernel(const Age1A
         }
     };
     auto stage = [&](int c0) {
+        // (lam_n / lam_V)^beta at the chunk's first column, then stepped
+        float uc = exp2f(beta * fmaf((float)c0, a.cc.dell, a.cc.ell0));
 #pragma unroll
-        for (int s = 0; s < SPT / 4; ++s) {
+        for (int s = 0; s < 4; ++s) {
             const float g4[4] = {gv[s].x, gv[s].y, gv[s].z, gv[s].w};
             float o4[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const int col = c0 + sk + 4 * s + c;
-                const float ell = fmaf((float)col, a.cc.dell, a.cc.ell0);
-                o4[c] = g4[c] * exp2f(rc.alpha * dust_curve(a.cc, rc, dust_pow(a.cc, rc, ell, col), col));
+                const int col = c0 + 4 * s + c;
+                const float cp = a.cc.k0 ? uc * __ldg(a.cc.k0 + col) : uc;
+                const float cn = a.cc.bump ? fmaf(eb, __ldg(a.cc.bump + col), cp) : cp;
+                o4[c] = g4[c] * fast_exp2(alpha * cn);
+                uc *= ustep;
             }
-            *reinterpret_cast<float4 *>(&As[sq][sk + 4 * s]) = make_float4(o4[0], o4[1], o4[2], o4[3]);
+            *reinterpret_cast<float4 *>(&As[tid][4 * s]) = make_float4(o4[0], o4[1], o4[2], o4[3]);
         }
 #pragma unroll
         for (int t = 0; t < LPT; ++t) {
@@ -293,10 +322,12 @@ __global__ void __launch_bounds__(A1_THREADS, 3) age1_adjoint_kernel(const Age1A
         }
     };
     constexpr int M2 = MAXM / 2;
-    const int row = tid >> 2, qt = tid & 3;   // rows row, row + 64; bins qt + 4 m
-    float acc[2][M2];
+    const int row = tid >> 2, qt = tid & 3;   // rows row + 64 h; bins qt + 4 m
+    float acc[A1_RPT][M2];
 #pragma unroll
-    for (int m = 0; m < M2; ++m) acc[0][m] = acc[1][m] = 0.f;
+    for (int h = 0; h < A1_RPT; ++h)
+#pragma unroll
+        for (int m = 0; m < M2; ++m) acc[h][m] = 0.f;
     if (cbeg < cend) load(cbeg);
     for (int c0 = cbeg; c0 < cend; c0 += A1_CHUNK) {
         __syncthreads();   // the previous chunk's reads are done
@@ -305,18 +336,20 @@ __global__ void __launch_bounds__(A1_THREADS, 3) age1_adjoint_kernel(const Age1A
         if (c0 + A1_CHUNK < cend) load(c0 + A1_CHUNK);
 #pragma unroll
         for (int k = 0; k < A1_CHUNK; k += 4) {
-            const float4 x0 = *reinterpret_cast<const float4 *>(&As[row][k]);
-            const float4 x1 = *reinterpret_cast<const float4 *>(&As[row + 64][k]);
+            float4 x[A1_RPT];
+#pragma unroll
+            for (int h = 0; h < A1_RPT; ++h) x[h] = *reinterpret_cast<const float4 *>(&As[row + 64 * h][k]);
 #pragma unroll
             for (int m = 0; m < M2; ++m) {
                 const float4 y = *reinterpret_cast<const float4 *>(&Bs[qt + 4 * m][k]);
-                acc[0][m] = fmaf(x0.w, y.w, fmaf(x0.z, y.z, fmaf(x0.y, y.y, fmaf(x0.x, y.x, acc[0][m]))));
-                acc[1][m] = fmaf(x1.w, y.w, fmaf(x1.z, y.z, fmaf(x1.y, y.y, fmaf(x1.x, y.x, acc[1][m]))));
+#pragma unroll
+                for (int h = 0; h < A1_RPT; ++h)
+                    acc[h][m] = fmaf(x[h].w, y.w, fmaf(x[h].z, y.z, fmaf(x[h].y, y.y, fmaf(x[h].x, y.x, acc[h][m]))));
             }
         }
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < A1_RPT; ++h) {
         const int64_t r = r0 + row + 64 * h;
         if (r >= a.n) break;
 #pragma unroll

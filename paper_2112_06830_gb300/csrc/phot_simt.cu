@@ -74,12 +74,13 @@ __device__ __forceinline__ void contract_range(const float *__restrict__ W, cons
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int KT = (ke - kb) / BK;
-    float4 ra[2];
+    constexpr int AQ = BK / 4, AL = BM * AQ / THREADS;   // float4 per weights row, per thread
+    float4 ra[AL];
     auto gload = [&](int k0, int buf) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < AL; ++t) {
             int idx = tid + t * THREADS;
-            int row = idx >> 2, kq = (idx & 3) * 4;
+            int row = idx / AQ, kq = (idx % AQ) * 4;
             int64_t gr = m0 + row;
             ra[t] = gr < n ? *reinterpret_cast<const float4 *>(W + gr * K_pad + k0 + kq)
                            : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -103,9 +104,9 @@ __device__ __forceinline__ void contract_range(const float *__restrict__ W, cons
     };
     auto sstore = [&](int buf) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < AL; ++t) {
             int idx = tid + t * THREADS;
-            int row = idx >> 2, kq = (idx & 3) * 4;
+            int row = idx / AQ, kq = (idx % AQ) * 4;
             As[buf][kq + 0][row] = ra[t].x;
             As[buf][kq + 1][row] = ra[t].y;
             As[buf][kq + 2][row] = ra[t].z;
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(THREADS, 1) phot_simt_kernel(SArgs a) {
     const int nfirst = (t0 + ((part - t0 % a.parts) % a.parts + a.parts) % a.parts) * BN;
     const int nstep = a.parts * BN;
     if (a.steps && tid == 0 && nend > nfirst)   // counted in 128 x 128 x 16 steps
-        atomicAdd(a.steps, (unsigned long long)((nend - nfirst + nstep - 1) / nstep) * KT * (BN / 128));
+        atomicAdd(a.steps, (unsigned long long)((nend - nfirst + nstep - 1) / nstep) * KT * (BK / 16) * (BN / 128));
     for (int n0 = nfirst; n0 < nend; n0 += nstep) {
         float c[8][4 * TN4];
 #pragma unroll
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, 1) phot_simt_groups_kernel(SArgs a, c
             const int kx0 = gs.k0[g], kx1 = gs.k1[g];
             const int kb = max(kx0 / BK * BK, a.k_lo), ke = min((kx1 + BK - 1) / BK * BK, a.k_hi);
             if (kb >= ke) continue;
-            steps += (unsigned long long)((ke - kb) / BK);
+            steps += (unsigned long long)((ke - kb) / BK) * (BK / 16);
             float c[8][4 * GTN4];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
