@@ -89,7 +89,17 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 
     };
     auto shat_at = [&](int col, const float (&cm)[4]) {
         const float ell = fmaf((float)col, cc.dell, cc.ell0);
-        const float F = DUST ? exp2f(rc.alpha * dust_curve(cc, rc, dust_pow(cc, rc, ell, col), col)) : 1.f;
+        float F = 1.f;
+        if constexpr (DUST && BF16) {
+            // split to bf16 hi + lo (16 significant bits): ex2.approx (relative
+            // error below 2^-22) for the power law and the attenuation
+            float pw;
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pw) : "f"(rc.beta * ell));
+            const float u = cc.k0 ? __ldg(cc.k0 + col) * pw : pw;
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(F) : "f"(rc.alpha * dust_curve(cc, rc, u, col)));
+        } else if constexpr (DUST) {
+            F = exp2f(rc.alpha * dust_curve(cc, rc, dust_pow(cc, rc, ell, col), col));
+        }
         return col_kappa(cc, col) * F * fmaf(rc.w[0], cm[0], fmaf(rc.w[1], cm[1], fmaf(rc.w[2], cm[2], rc.w[3] * cm[3])));
     };
     auto store = [&](int col, float sh) {
