@@ -353,3 +353,32 @@ def test_fused_groups_extreme_transitions_and_invalid_rows(prec):
         assert err <= tol
         assert ctx.device_error() == dsps.DSPS_ERR_INVALID_ARG
         ctx.close()
+
+
+@pytest.mark.parametrize("x0,h", [(7.0, 0.1), (8.0, 0.3), (4.0, 0.1), (12.0, 0.1), (8.5, 1.5)])
+def test_fused_gradient_matches_per_group_gradient(x0, h):
+    """The split-bf16 gradient whose fluxes and dust rows come from the
+    one-launch contraction (a forward and a gradient pass) against the one
+    that runs a gradient-mode contraction per dust group: the same terms in
+    another summation order.  Transitions inside the grid and beyond both ends
+    (one group of every age, T = 0 or 1) and a wide one."""
+    from paper_2112_06830_gb300 import dsps
+    f = synth.make_filters(8)
+    g = _util.ssp("full")
+    kw = dict(sfh_model=synth.SFH_DPL_QUENCH, dust_agedep=True, dust_agedep_x0=x0, dust_agedep_h=h)
+    a = dsps.Context(g, **kw)
+    b = dsps.Context(g, agedep_fused=False, **kw)
+    sa, sb = a.add_filters(f), b.add_filters(f)
+    p32, _ = _pop(700, 66, 1000)
+    p = torch.from_numpy(p32).cuda()
+    mb = torch.from_numpy(np.random.default_rng(13).standard_normal((700, 8)).astype(np.float32)).cuda()
+    ma, ga = a.photometry_vjp(p, sa, mb, precision=dsps.DSPS_PREC_BF16X3)
+    mbb, gb = b.photometry_vjp(p, sb, mb, precision=dsps.DSPS_PREC_BF16X3)
+    dm = (ma - mbb).abs().max().item()
+    scale = torch.clamp(gb.abs(), min=1e-3 * gb.abs().amax(dim=0, keepdim=True))
+    rel = ((ga - gb).abs() / scale).max().item()
+    print(f"x0={x0} h={h}: fused vs per-group |dm| {dm:.2e}, scaled gradient difference {rel:.2e}")
+    assert torch.isfinite(ga).all() and dm <= 1e-4 and rel <= 2e-3
+    assert a.device_error() == 0 and b.device_error() == 0
+    a.close()
+    b.close()
