@@ -647,11 +647,18 @@ int run_photometry_vjp_agedep_ws(Ctx *c, const Workspace &w0, int64_t n_gal, con
                 e = cudaGetLastError();
             }
         }
-        if (any1 && e == cudaSuccess) {
+        // with the one-launch forward, the adjoint rows of every group from one
+        // tensor-core launch over the dust-free adjoint spectrum
+        const bool vjp1 = fused && agedep_vjp_tc_ok(*c);
+        if (vjp1 && e == cudaSuccess) {
+            ProfScope ps(*c, 3, s, prof);
+            e = launch_vjp_groups_tc(*c, w, fs, params, n_gal, g0, n, s);
+        }
+        if (!vjp1 && any1 && e == cudaSuccess) {
             ProfScope ps(*c, 3, s, prof);
             e = launch_age1_adjoint(*c, w, &fs, params, n_gal, g0, n, tc, s);
         }
-        for (size_t k = 0; k < c->dust_groups.size() && e == cudaSuccess; ++k) {
+        for (size_t k = 0; !vjp1 && k < c->dust_groups.size() && e == cudaSuccess; ++k) {
             const DustGroup &gr = c->dust_groups[k];
             if (age1_direct(*c, gr)) continue;
             ProfScope ps(*c, 3, s, prof);

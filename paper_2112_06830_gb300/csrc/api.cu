@@ -137,7 +137,7 @@ void free_ctx(Ctx *c) {
     void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_k0, c->d_edges, c->d_einh, c->d_bwidth,
                     c->d_zedge, c->d_uedge, c->d_tlut, c->d_glut, c->d_ws_block, c->ws.shat, c->ws.ewacc, c->d_err, c->d_stats,
                     c->d_L_hi, c->d_L_lo, c->d_Ld32, c->d_wmul_d, c->d_hio, c->d_Lab_hi, c->d_Lab_lo,
-                    c->d_wmul_ab};
+                    c->d_wmul_ab, c->d_Ldab_hi, c->d_Ldab_lo};
     for (void *p : ptrs) cudaFree(p);
     for (auto &r : c->prof_recs) {
         cudaEventDestroy(r.a);
@@ -360,6 +360,8 @@ int dsps_create(dsps_ctx **out, const dsps_grid *g, const dsps_opts *o) {
     if (c->KA_pad) {
         chk(dmalloc(&c->d_Lab_hi, (size_t)c->KA_pad * c->N_pad));
         chk(dmalloc(&c->d_Lab_lo, (size_t)c->KA_pad * c->N_pad));
+        chk(dmalloc(&c->d_Ldab_hi, (size_t)c->KA_pad * c->N_pad));
+        chk(dmalloc(&c->d_Ldab_lo, (size_t)c->KA_pad * c->N_pad));
         chk(dmalloc(&c->d_wmul_ab, (size_t)c->KA_pad));
     }
     if (rc != DSPS_OK) { free_ctx(c); return rc; }

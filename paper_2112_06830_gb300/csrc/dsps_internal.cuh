@@ -213,6 +213,8 @@ struct Ctx {
     int KA_pad = 0;
     __nv_bfloat16 *d_Lab_hi = nullptr;      // [N_pad][KA_pad] row-scaled SSP hi, age-block order
     __nv_bfloat16 *d_Lab_lo = nullptr;      // [N_pad][KA_pad] lo
+    __nv_bfloat16 *d_Ldab_hi = nullptr;     // [KA_pad][N_pad] the differenced split rows, age-block order
+    __nv_bfloat16 *d_Ldab_lo = nullptr;
     float *d_wmul_ab = nullptr;             // [KA_pad] 2^E_k at column ka (0 at padding)
     int kmask_words = 0;                    // ceil(SEC / KBLOCK / 32)
     double t0 = 0, t1 = 0;
@@ -372,7 +374,14 @@ inline void group_k_range(const Ctx &c, const DustGroup *gr, int bk, int &k_lo, 
 // Most dust groups a one-launch age-dependent contraction takes.
 constexpr int AGEDEP_MAX_GROUPS = 128;
 
-// Age-dependent dust, FP32 form, every group in one launch (phot_simt.cu):
+// Age-dependent dust, split-bf16: the merged adjoint rows of the weights (w.what2,
+// in the tensor adjoint's row scale) for every dust group in one launch, from
+// the dust-free adjoint spectrum in w.shat (agedep_vjp_tc.cu).
+bool agedep_vjp_tc_ok(const Ctx &c);
+cudaError_t launch_vjp_groups_tc(const Ctx &c, const Workspace &w, const FilterSet &fs, const float *params,
+                                 int64_t G_stride, int64_t g_begin, int64_t n, cudaStream_t s);
+
+// Age-dependent dust, FP32 form, every group in one launch (agedep_simt.cu):
 // per-part filter sums of the sorted rows from the weights of all ages
 // (launch_weights with aux_yo); *parts gets the number of parts.
 cudaError_t launch_phot_simt_groups(const Ctx &c, const Workspace &w, const FilterSet &fs, int64_t n, int *parts,

@@ -22,6 +22,10 @@
 //   d_Lab_*  [N_pad][KA_pad] bf16 hi / lo of L[k][n] 2^-E_k in the age-block
 //           order ka = i * 32 + j (age-dependent dust's fused forward), with
 //           d_wmul_ab = 2^E_k at ka (only when Ctx::KA_pad > 0)
+//   d_Ldab_* [KA_pad][N_pad] the rows of d_L_* in the age-block order (row ka =
+//           32 i + j holds row kz = j A_pad + i; zero for j >= n_z or i >= n_age):
+//           the age-dependent adjoint's operand, whose products then carry the
+//           same 2^-E'_kz as the tensor adjoint's (only when KA_pad > 0, n_u = 1)
 // E_k is the binary exponent of max_n L[k][n]: every scaled row peaks in
 // [1, 2), far from the bf16 underflow threshold.
 #include "dsps_internal.cuh"
@@ -172,6 +176,21 @@ __global__ void build_split_kernel(const float *A, const float *rscale, int K_pa
     lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// Row ka of the age-block differenced copy from row kz of d_L_* (bf16 pairs
+// moved as 32-bit words; N_pad is even).
+__global__ void build_ldab_kernel(const __nv_bfloat16 *hi, const __nv_bfloat16 *lo, int n_age, int n_z, int A_pad,
+                                  int N_pad, __nv_bfloat16 *ohi, __nv_bfloat16 *olo) {
+    const int ka = blockIdx.y, i = ka / KBLOCK, j = ka % KBLOCK;
+    const bool ok = i < n_age && j < n_z;
+    const size_t src = (size_t)(j * A_pad + i) * N_pad, dst = (size_t)ka * N_pad;
+    for (int n2 = blockIdx.x * blockDim.x + threadIdx.x; 2 * n2 < N_pad; n2 += gridDim.x * blockDim.x) {
+        const unsigned vh = ok ? reinterpret_cast<const unsigned *>(hi + src)[n2] : 0u;
+        const unsigned vl = ok ? reinterpret_cast<const unsigned *>(lo + src)[n2] : 0u;
+        reinterpret_cast<unsigned *>(ohi + dst)[n2] = vh;
+        reinterpret_cast<unsigned *>(olo + dst)[n2] = vl;
+    }
+}
+
 }  // namespace
 
 cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
@@ -199,6 +218,9 @@ cudaError_t prepare_ssp_device(Ctx &c, const float *h_lssp) {
         build_ldiff_kernel<<<blkz, 256>>>(d_raw, c.n_lam, kl, c.u_ref, c.KZ_pad, c.N_pad, c.d_Ld32);
         row_exponent_abs_kernel<<<c.KZ_pad, 256>>>(c.d_Ld32, c.KZ_pad, c.N_pad, c.d_wmul_d, d_rscale);
         build_split_kernel<<<blkz, 256>>>(c.d_Ld32, d_rscale, c.KZ_pad, c.N_pad, c.d_L_hi, c.d_L_lo);
+        if (c.d_Ldab_hi)
+            build_ldab_kernel<<<dim3(4, c.KA_pad), 256>>>(c.d_L_hi, c.d_L_lo, c.n_age, c.n_z, c.A_pad, c.N_pad,
+                                                         c.d_Ldab_hi, c.d_Ldab_lo);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
