@@ -402,6 +402,14 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
             const float ze_hi = jin && !last ? __ldg(a.zedge + j + 1) : 0.f;
             const float isg = valid ? inv_sig : 0.f;
             const int nblk = a.KA_pad / KBLOCK;
+            unsigned wbits = 0u;   // mask bits of the current 32 ages (flushed into bm at word ends)
+            auto flush = [&](int wi) {
+                if (wi == 0) bm.x = wbits;
+                else if (wi == 1) bm.y = wbits;
+                else if (wi == 2) bm.z = wbits;
+                else bm.w = wbits;
+                wbits = 0u;
+            };
             for (int i0 = 0; i0 < nblk; i0 += 4) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -417,19 +425,17 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                     float pj = sh - sl;
                     if (ul <= 0.f && uh > 0.f) pj += 1.f;
                     const float om = jin ? fr * pj : 0.f;
-                    const float w = jin ? om * __ldg(a.wmul_ab + i * KBLOCK + j) : 0.f;
+                    // (the multiplier is 0 at the columns j >= n_z, and om finite)
+                    const float w = om * __ldg(a.wmul_ab + i * KBLOCK + j);
                     const __nv_bfloat16 h = __float2bfloat16_rn(w);
                     rh[i * KBLOCK + j] = h;
                     rl[i * KBLOCK + j] = __float2bfloat16_rn(w - __bfloat162float(h));
                     const unsigned any = __ballot_sync(0xffffffffu, om != 0.f);
-                    const unsigned bit = any ? 1u << (i & 31) : 0u;
-                    const int wi = i >> 5;
-                    bm.x |= wi == 0 ? bit : 0u;
-                    bm.y |= wi == 1 ? bit : 0u;
-                    bm.z |= wi == 2 ? bit : 0u;
-                    bm.w |= wi == 3 ? bit : 0u;
+                    wbits |= (any != 0u ? 1u : 0u) << (i & 31);
+                    if ((i & 31) == 31) flush(i >> 5);
                 }
             }
+            if (nblk & 31) flush((nblk - 1) >> 5);
         } else if constexpr (MODE == W_OMEGA_BF16X2_AGE1) {
             // One age bin i: lane j < n_z takes metallicity bin j (both edges'
             // CDFs, the arithmetic of the loop below), and the warp writes, in
