@@ -20,8 +20,9 @@
 // (power law stepped from node to node, one ex2 per node).  Products
 // hi.hi + hi.lo + lo.hi accumulate in TMEM (two 256-column accumulators); the
 // epilogue writes each age's n_z columns to the merged adjoint rows in the
-// metallicity-major order (kz = j A_pad + i), which carry the row scale of the
-// tensor adjoint (the B rows are those of d_L_* permuted).
+// metallicity-major order (kz = j A_pad + i; two neighbouring ages of a bin as
+// one 8-byte store), which carry the row scale of the tensor adjoint (the B
+// rows are those of d_L_* permuted).
 //
 // Warp roles: 0 TMA producer (4-stage ring), 1 TMEM allocator and
 // single-thread MMA issuer, 2..17 A writers, 18..21 epilogue (one TMEM lane
@@ -363,10 +364,16 @@ vjp_groups_tc_kernel(const __grid_constant__ CUtensorMap tmB_hi0, const __grid_c
             if (!got) break;
             tc_fence_after();
             const int64_t rowg = (int64_t)mt * BM + row;
-            for (int c = 0; c < na; ++c) {
-                uint32_t v[32];
+            // two neighbouring ages of one metallicity bin are adjacent in the
+            // merged rows (kz = j A_pad + i): stored as one 8-byte pair where
+            // the first age is even (A_pad is a multiple of 4)
+            for (int c = 0; c < na;) {
+                const bool pair = c + 1 < na && ((i0 + c) & 1) == 0;
+                uint32_t v[32], w[32];
                 tmem_ld32(tmem_base + lane_base + (uint32_t)(as * BNMAX + c * BK), v);
-                if (c == na - 1) {
+                if (pair) tmem_ld32(tmem_base + lane_base + (uint32_t)(as * BNMAX + (c + 1) * BK), w);
+                const int cn = c + (pair ? 2 : 1);
+                if (cn == na) {
                     // this warp's reads of the accumulator are done
                     tc_fence_before();
                     __syncwarp();
@@ -374,10 +381,19 @@ vjp_groups_tc_kernel(const __grid_constant__ CUtensorMap tmB_hi0, const __grid_c
                 }
                 if (rowg < a.n) {
                     float *dst = a.what + rowg * a.KZ_pad + (i0 + c);
+                    if (pair) {
 #pragma unroll
-                    for (int j = 0; j < BK; ++j)
-                        if (j < a.n_z) dst[(int64_t)j * a.A_pad] = __uint_as_float(v[j]);
+                        for (int j = 0; j < BK; ++j)
+                            if (j < a.n_z)
+                                *reinterpret_cast<float2 *>(dst + (int64_t)j * a.A_pad) =
+                                    make_float2(__uint_as_float(v[j]), __uint_as_float(w[j]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < BK; ++j)
+                            if (j < a.n_z) dst[(int64_t)j * a.A_pad] = __uint_as_float(v[j]);
+                    }
                 }
+                c = cn;
             }
             if (++as == 2) { as = 0; aphase ^= 1u; }
         }
