@@ -183,6 +183,7 @@ __device__ __forceinline__ void grad_group_chunk(float &sA, float &sD, const flo
                                                  int n0, float alpha, float beta, float ustep, float e, float ed,
                                                  const ColConst &cc, float lell0, float ldell) {
     float u = ex2_fast(beta * fmaf((float)n0, cc.dell, cc.ell0));
+    float lj = fmaf((float)n0, ldell, lell0);   // ln(lam_n / lam_V), stepped
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         float cp = u;
@@ -191,7 +192,8 @@ __device__ __forceinline__ void grad_group_chunk(float &sA, float &sD, const flo
         const float cn = BUMP ? fmaf(e, bj, cp) : cp;
         const float x = __uint_as_float(r[j]) * ex2_fast(alpha * cn) * gk[j];
         sA = fmaf(x, cn, sA);
-        float dc = cp * fmaf((float)(n0 + j), ldell, lell0);
+        float dc = cp * lj;
+        lj += ldell;
         if constexpr (BUMP) dc = fmaf(ed, bj, dc);
         sD = fmaf(x, dc, sD);
         u *= ustep;
@@ -399,16 +401,20 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
                 // forward: the running sum; gradient pass: G at the columns
                 float run[EPI_COLS / 32][32];
 #pragma unroll
-                for (int c = 0; c < EPI_COLS / 32; ++c)
+                for (int c = 0; c < EPI_COLS / 32; ++c) {
+                    // (nb and the band edges are multiples of 32: a 32-column block is in or out)
+                    const int col0 = nb + c * 32;
+                    const bool in = GRAD && valid && rowg < a.n && col0 >= gc0 && col0 < gc1;
+                    const float4 *src = reinterpret_cast<const float4 *>(a.G + (in ? rowg * a.N_pad + col0 : 0));
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        float v = 0.f;
-                        if constexpr (GRAD) {
-                            const int col = nb + c * 32 + j;
-                            if (valid && rowg < a.n && col >= gc0 && col < gc1) v = a.G[rowg * a.N_pad + col];
-                        }
-                        run[c][j] = v;
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const float4 v = in ? src[j4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        run[c][4 * j4] = v.x;
+                        run[c][4 * j4 + 1] = v.y;
+                        run[c][4 * j4 + 2] = v.z;
+                        run[c][4 * j4 + 3] = v.w;
                     }
+                }
                 bool any = false;
                 for (int g = 0; ok && g < a.n_groups; ++g) {
                     if (!group_present(km, a.g_i0[g], a.g_i1[g])) continue;
