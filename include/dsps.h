@@ -251,6 +251,28 @@ int dsps_filters_add_frame(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts,
                            int32_t *set_id);
 int dsps_filters_count(dsps_ctx *ctx, int32_t set_id, int32_t *n_filt);
 
+/* Band coverage: for each galaxy g and filter q of the set, the fraction of
+ * the filter's response D_q = int T_q(lam) dlam / lam (the denominator of Eq.
+ * restmag, over the whole filter) that falls on the SSP grid as the galaxy is
+ * seen: lam in [(1+z) lam_0, (1+z) lam_{N-1}] for an observer-frame set,
+ * [lam_0, lam_{N-1}] for a rest-frame one (Sec. 2.2; the SED is zero outside
+ * the grid).  coverage[g][q] = 1 for a band that the redshifted grid covers,
+ * 0 for one wholly outside it.  A band with coverage below about 1e-8 sees
+ * the grid only through the last points of the filter's far tail, where the
+ * library's filter table (resampled on the grid's ln-lambda spacing and
+ * interpolated with 4-point Lagrange weights) and a linear interpolation of
+ * the filter's own table differ: such magnitudes can be off by up to ~0.2
+ * mag, and one with coverage 0 can still be finite (~70 mag, the stencil
+ * reaching a grid step past the filter's end).  At or above 1e-8 the
+ * magnitudes keep the precision form's tolerance.  Evaluated from the
+ * filter's own table (trapezoids of T / lam, partial intervals linear in lam)
+ * with FP64 cumulative sums from both ends.  params: device
+ * [npar][n_gal] FP32 (row 11, z, is read); coverage: device [n_gal][Q] FP32;
+ * NaN where z is not finite or z <= 0 (observer frame).  Asynchronous on
+ * stream.  INVALID_ARG for a null pointer, n_gal < 0 or an unknown set. */
+int dsps_band_coverage(dsps_ctx *ctx, int64_t n_gal, const float *params, int32_t set_id, float *coverage,
+                       dsps_stream_t stream);
+
 /* SSP weights in Msun, w_out[g][i][j] = 10^logM * P_SFH(age_i) * P_met(Z_j | age_i)
  * (Sec. 3.1 Eq. cspsum with P_SFH, Sec. 3.2 Eq. agedep_mdf), times P_neb(u_k)
  * with a nebular axis (Eq. nebsed).

@@ -132,6 +132,7 @@ void free_ctx(Ctx *c) {
     for (auto &fs : c->sets) {
         cudaFree(fs.d_tab);
         cudaFree(fs.d_offq);
+        cudaFree(fs.d_cov);
     }
     for (auto &ls : c->lines) cudaFree(ls.d_tab);
     void *ptrs[] = {c->d_L32, c->d_Lt_hi, c->d_Lt_lo, c->d_wmul, c->d_logage, c->d_mua, c->d_mub, c->d_bump, c->d_k0, c->d_edges, c->d_einh, c->d_bwidth,
@@ -518,13 +519,47 @@ int dsps_filters_add_frame(dsps_ctx *ctx, int32_t n_filt, const int32_t *n_pts, 
             }
         }
     }
+    // band coverage: the filter's own table, with the response accumulated from
+    // both ends (trapezoids of T / lam) so that small fractions at either end
+    // keep their relative precision
+    std::vector<double> cov;
+    for (int q = 0; q < n_filt; ++q) {
+        const int np = n_pts[q];
+        std::vector<double> A(np, 0.0), B(np, 0.0);
+        for (int m = 1; m < np; ++m)
+            A[m] = A[m - 1] + 0.5 * (lam[q][m] - lam[q][m - 1]) * (trans[q][m] / lam[q][m] + trans[q][m - 1] / lam[q][m - 1]);
+        for (int m = np - 2; m >= 0; --m)
+            B[m] = B[m + 1] + 0.5 * (lam[q][m + 1] - lam[q][m]) * (trans[q][m + 1] / lam[q][m + 1] + trans[q][m] / lam[q][m]);
+        const double D = A[np - 1];
+        fs.cov_off[q] = (int)(cov.size() / 3);
+        int mid = np - 1;
+        for (int m = 0; m < np; ++m) {
+            cov.push_back(std::log(lam[q][m]));
+            cov.push_back(A[m] / D);
+            cov.push_back(B[m] / D);
+            if (mid == np - 1 && A[m] >= 0.5 * D) mid = m;
+        }
+        fs.cov_mid[q] = fs.cov_off[q] + mid;
+    }
+    fs.cov_off[n_filt] = (int)(cov.size() / 3);
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     if (dmalloc(&fs.d_tab, tab.size()) != DSPS_OK) return DSPS_ERR_CUDA;
     if (dmalloc(&fs.d_offq, (size_t)n_filt) != DSPS_OK) { cudaFree(fs.d_tab); return DSPS_ERR_CUDA; }
+    if (cudaMalloc(&fs.d_cov, cov.size() * sizeof(double)) != cudaSuccess) {
+        cudaFree(fs.d_tab);
+        cudaFree(fs.d_offq);
+        return fail(DSPS_ERR_CUDA, "dsps_filters_add: out of device memory%s");
+    }
     cudaError_t e = cudaMemcpy(fs.d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(fs.d_offq, offq.data(), offq.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { cudaFree(fs.d_tab); cudaFree(fs.d_offq); return cuda_fail(e, "dsps_filters_add upload"); }
+    if (e == cudaSuccess) e = cudaMemcpy(fs.d_cov, cov.data(), cov.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(fs.d_tab);
+        cudaFree(fs.d_offq);
+        cudaFree(fs.d_cov);
+        return cuda_fail(e, "dsps_filters_add upload");
+    }
     c->sets.push_back(fs);
     *set_id = (int32_t)c->sets.size() - 1;
     return DSPS_OK;

@@ -120,6 +120,12 @@ struct FilterSet {
     float *d_tab = nullptr;    // [m_rows][4*Q4] T_q(lam0 exp(m dlnlam))
     float *d_offq = nullptr;   // [Q] 2.5 log10(AB0 D_q)
     int rest = 0;              // 1: rest-frame absolute magnitudes (Eq. restmag: no shift, no distance terms)
+    // band coverage (coverage.cu): per filter q, points cov_off[q] .. cov_off[q+1] - 1
+    // of the filter's own table as (ln lam, A, B), A / B the response int T dlam / lam
+    // left / right of the point over D_q (FP64), and the point where A reaches 1/2
+    double *d_cov = nullptr;
+    int cov_off[DSPS_MAX_FILTERS + 1] = {};
+    int cov_mid[DSPS_MAX_FILTERS] = {};
 };
 
 // A registered emission line (spectrum.cu): the window of grid columns

@@ -114,6 +114,7 @@ _SIGS = [
                                          C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.POINTER(C.c_double)),
                                          C.c_int32, C.POINTER(C.c_int32)]),
     ("dsps_filters_count", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    ("dsps_band_coverage", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("dsps_weights", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("dsps_photometry", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                   C.c_void_p]),
@@ -217,6 +218,10 @@ def dsps_filters_count(ctx, set_id):
     q = C.c_int32()
     _check(load().dsps_filters_count(ctx, set_id, C.byref(q)), "dsps_filters_count")
     return q.value
+
+
+def dsps_band_coverage(ctx, n_gal, params_ptr, set_id, coverage_ptr, stream=0):
+    _check(load().dsps_band_coverage(ctx, n_gal, params_ptr, set_id, coverage_ptr, stream), "dsps_band_coverage")
 
 
 def dsps_weights(ctx, n_gal, params_ptr, w_out_ptr, stream=0):
@@ -410,6 +415,16 @@ class Context:
         shape = (G, self.n_age, self.n_z) + ((self.n_u,) if self.n_u > 1 else ())
         out = torch.empty(shape, dtype=torch.float32, device=params.device)
         dsps_weights(self.handle, G, params.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def band_coverage(self, params, set_id, stream=None):
+        """[G, Q] fraction of each band's filter response on the redshifted SSP grid."""
+        import torch
+        assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == self.npar
+        params = params.contiguous()
+        G = params.shape[1]
+        out = torch.empty((G, self.n_filt[set_id]), dtype=torch.float32, device=params.device)
+        dsps_band_coverage(self.handle, G, params.data_ptr(), set_id, out.data_ptr(), _stream_handle(stream))
         return out
 
     def photometry(self, params, set_id, precision=DSPS_PREC_BF16X3, out=None, stream=None):
