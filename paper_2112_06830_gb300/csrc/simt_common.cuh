@@ -47,6 +47,16 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Two FP32 FMAs in one instruction (PTX fma.rn.f32x2, sm_100 family): c0 +=
+// a b0, c1 += a b1, each rounded once like fmaf, so the sums are bit-identical
+// to the scalar form; half the issue slots, which the operand loads then use.
+__device__ __forceinline__ void fma2(float &c0, float &c1, float a, float b0, float b1) {
+    asm("{\n.reg .b64 d, x, y;\nmov.b64 x, {%2, %2};\nmov.b64 y, {%3, %4};\nmov.b64 d, {%0, %1};\n"
+        "fma.rn.f32x2 d, x, y, d;\nmov.b64 {%0, %1}, d;\n}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a), "f"(b0), "f"(b1));
+}
+
 // One K range of a tile: c += W[m0 + row, k] L[k, n0 + col] over k in [kb, ke)
 // (multiples of BK), for the thread's 8 rows (ty*4 + {0..3}, 64 + ty*4 +
 // {0..3}) and 4*TN4_ columns (tx*4 + {0..3} + 64 m).  W (row-major per galaxy)
@@ -127,7 +137,7 @@ __device__ __forceinline__ void contract_range(const float *__restrict__ W, cons
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 4 * TN4_; ++j) c[i][j] = fmaf(av[i], bv[j], c[i][j]);
+                for (int j = 0; j < 4 * TN4_; j += 2) fma2(c[i][j], c[i][j + 1], av[i], bv[j], bv[j + 1]);
         }
         if (kt + 1 < KT) sstore(buf ^ 1);
         cp_async_wait_all();

@@ -30,6 +30,7 @@
 
 #include "dsps_internal.cuh"
 #include "epilogue.cuh"
+#include "simt_common.cuh"
 
 namespace dsps {
 
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(THREADS, 2) spec_window_kernel(SwArgs a) {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) c[i][j] = fmaf(av[i], bv[j], c[i][j]);
+                for (int j = 0; j < 4; j += 2) simt::fma2(c[i][j], c[i][j + 1], av[i], bv[j], bv[j + 1]);
         }
         if (kt + 1 < KT) sstore(buf ^ 1);
         __syncthreads();
