@@ -30,6 +30,7 @@
 #include <type_traits>
 
 #include "dsps_internal.cuh"
+#include "f32x2.cuh"
 
 namespace dsps {
 
@@ -102,6 +103,25 @@ __device__ __forceinline__ float mdf_s(float u) {
     if constexpr (MDF == DSPS_MDF_TRIWEIGHT) c = terf_lower_f(a);
     else c = gauss_cdf_f(a);
     return u > 0.f ? -c : c;
+}
+
+// mdf_s of two edges at once: the triweight's polynomial in paired FP32 ops
+// (the same operations in the same order as terf_lower_f, so the same
+// numbers), the Gaussian's pair by pair.
+template <int MDF>
+__device__ __forceinline__ float2 mdf_s2(float2 u) {
+    if constexpr (MDF != DSPS_MDF_TRIWEIGHT) {
+        return make_float2(mdf_s<MDF>(u.x), mdf_s<MDF>(u.y));
+    } else {
+        const float2 x = make_float2(-fabsf(u.x) + 3.f, -fabsf(u.y) + 3.f);
+        const float2 x2 = mul2(x, x);
+        float2 poly = fma2v(x, splat2(-1.f / 7.f), splat2(3.f));
+        poly = fma2v(x, poly, splat2(-21.6f));
+        poly = fma2v(x, poly, splat2(54.f));
+        const float2 c = mul2(mul2(mul2(splat2(35.f / 69984.f), x2), x2), poly);
+        const float cx = x.x <= 0.f ? 0.f : c.x, cy = x.y <= 0.f ? 0.f : c.y;
+        return make_float2(u.x > 0.f ? -cx : cx, u.y > 0.f ? -cy : cy);
+    }
 }
 
 __host__ __device__ inline size_t weights_smem_per_warp(int n_t, int n_age) {
@@ -410,29 +430,50 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                 else bm.w = wbits;
                 wbits = 0u;
             };
+            // two ages at a time in paired FP32 ops (the scalar operations, so the
+            // same numbers); nblk is even (KA_pad is a multiple of 64)
             for (int i0 = 0; i0 < nblk; i0 += 4) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < 4; c += 2) {
                     const int i = i0 + c;
                     if (i >= nblk) break;
-                    const float fr = valid && i < a.n_age ? frac[i] : 0.f;
-                    const float mu = valid ? mdf_mean_at(a, p, min(i, a.n_age - 1)) : 0.f;
-                    const float ul = first ? -1e30f : (ze_lo - mu) * isg;
-                    const float uh = last ? 1e30f : (ze_hi - mu) * isg;
-                    const float sh = last ? 0.f : mdf_s<MDF>(uh);
-                    const float sl_up = __shfl_up_sync(0xffffffffu, sh, 1);   // lane j - 1's upper edge
-                    const float sl = first ? 0.f : sl_up;
-                    float pj = sh - sl;
-                    if (ul <= 0.f && uh > 0.f) pj += 1.f;
-                    const float om = jin ? fr * pj : 0.f;
+                    const float2 fr = make_float2(valid && i < a.n_age ? frac[i] : 0.f,
+                                                  valid && i + 1 < a.n_age ? frac[i + 1] : 0.f);
+                    float2 mu = splat2(0.f);
+                    if (valid) {
+                        const int ia = min(i, a.n_age - 1), ib = min(i + 1, a.n_age - 1);
+                        mu = fma2v(splat2(p[7]), make_float2(__ldg(a.mub + ia), __ldg(a.mub + ib)),
+                                   mul2(make_float2(__ldg(a.mua + ia), __ldg(a.mua + ib)), splat2(p[5])));
+                    }
+                    const float2 ulv = mul2(sub2(splat2(ze_lo), mu), splat2(isg));
+                    const float2 uhv = mul2(sub2(splat2(ze_hi), mu), splat2(isg));
+                    const float ul[2] = {first ? -1e30f : ulv.x, first ? -1e30f : ulv.y};
+                    const float uh[2] = {last ? 1e30f : uhv.x, last ? 1e30f : uhv.y};
+                    float2 sh = mdf_s2<MDF>(make_float2(uh[0], uh[1]));
+                    if (last) sh = splat2(0.f);
+                    const float2 sl_up = make_float2(__shfl_up_sync(0xffffffffu, sh.x, 1),   // lane j - 1's upper edge
+                                                     __shfl_up_sync(0xffffffffu, sh.y, 1));
+                    const float2 d = sub2(sh, first ? splat2(0.f) : sl_up);
+                    float pj[2] = {d.x, d.y};
+#pragma unroll
+                    for (int t = 0; t < 2; ++t)
+                        if (ul[t] <= 0.f && uh[t] > 0.f) pj[t] += 1.f;
+                    const float2 omv = mul2(fr, make_float2(pj[0], pj[1]));
+                    const float2 om = jin ? omv : splat2(0.f);
                     // (the multiplier is 0 at the columns j >= n_z, and om finite)
-                    const float w = om * __ldg(a.wmul_ab + i * KBLOCK + j);
-                    const __nv_bfloat16 h = __float2bfloat16_rn(w);
-                    rh[i * KBLOCK + j] = h;
-                    rl[i * KBLOCK + j] = __float2bfloat16_rn(w - __bfloat162float(h));
-                    const unsigned any = __ballot_sync(0xffffffffu, om != 0.f);
-                    wbits |= (any != 0u ? 1u : 0u) << (i & 31);
-                    if ((i & 31) == 31) flush(i >> 5);
+                    const float2 w = mul2(om, make_float2(__ldg(a.wmul_ab + i * KBLOCK + j),
+                                                          __ldg(a.wmul_ab + (i + 1) * KBLOCK + j)));
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(w.x, w.y);
+                    const float2 r = sub2(w, __bfloat1622float2(h));
+                    const __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
+                    rh[i * KBLOCK + j] = __low2bfloat16(h);
+                    rh[(i + 1) * KBLOCK + j] = __high2bfloat16(h);
+                    rl[i * KBLOCK + j] = __low2bfloat16(l);
+                    rl[(i + 1) * KBLOCK + j] = __high2bfloat16(l);
+                    const unsigned any0 = __ballot_sync(0xffffffffu, om.x != 0.f);
+                    const unsigned any1 = __ballot_sync(0xffffffffu, om.y != 0.f);
+                    wbits |= ((any0 != 0u ? 1u : 0u) | (any1 != 0u ? 2u : 0u)) << (i & 31);
+                    if ((i & 31) == 30) flush(i >> 5);
                 }
             }
             if (nblk & 31) flush((nblk - 1) >> 5);
@@ -515,9 +556,13 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                 auto bin = [&](int j, auto last_c) {
                     constexpr bool last = decltype(last_c)::value;
                     const float ze = last ? 0.f : __ldg(a.zedge + j + 1);
-                    float uh[4];
-    #pragma unroll
-                    for (int c = 0; c < 4; ++c) uh[c] = last ? 1e30f : (ze - mu4[c]) * isg;
+                    // the four ages in two pairs (paired FP32, the scalar results)
+                    float2 uh01 = splat2(1e30f), uh23 = splat2(1e30f);
+                    if constexpr (!last) {
+                        uh01 = mul2(sub2(splat2(ze), make_float2(mu4[0], mu4[1])), splat2(isg));
+                        uh23 = mul2(sub2(splat2(ze), make_float2(mu4[2], mu4[3])), splat2(isg));
+                    }
+                    const float uh[4] = {uh01.x, uh01.y, uh23.x, uh23.y};
                     const float uh_max = fmaxf(fmaxf(uh[0], uh[1]), fmaxf(uh[2], uh[3]));
                     const float ul_min = fminf(fminf(ulo[0], ulo[1]), fminf(ulo[2], ulo[3]));
                     float om[4] = {0.f, 0.f, 0.f, 0.f};
@@ -529,15 +574,29 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                             ulo[c] = uh[c];
                         }
                     } else {
-    #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const float s_hi = last ? 0.f : mdf_s<MDF>(uh[c]);
-                            float pj = s_hi - slo[c];
-                            if (ulo[c] <= 0.f && uh[c] > 0.f) pj += 1.f;
-                            om[c] = fr4[c] * pj;
-                            slo[c] = s_hi;
-                            ulo[c] = uh[c];
+                        float2 sh01 = splat2(0.f), sh23 = splat2(0.f);
+                        if constexpr (!last) {
+                            sh01 = mdf_s2<MDF>(uh01);
+                            sh23 = mdf_s2<MDF>(uh23);
                         }
+                        const float2 d01 = sub2(sh01, make_float2(slo[0], slo[1]));
+                        const float2 d23 = sub2(sh23, make_float2(slo[2], slo[3]));
+                        float pj[4] = {d01.x, d01.y, d23.x, d23.y};
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (ulo[c] <= 0.f && uh[c] > 0.f) pj[c] += 1.f;
+                        const float2 om01 = mul2(make_float2(fr4[0], fr4[1]), make_float2(pj[0], pj[1]));
+                        const float2 om23 = mul2(make_float2(fr4[2], fr4[3]), make_float2(pj[2], pj[3]));
+                        om[0] = om01.x;
+                        om[1] = om01.y;
+                        om[2] = om23.x;
+                        om[3] = om23.y;
+                        slo[0] = sh01.x;
+                        slo[1] = sh01.y;
+                        slo[2] = sh23.x;
+                        slo[3] = sh23.y;
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c) ulo[c] = uh[c];
                         nzg = (om[0] != 0.f) | (om[1] != 0.f) | (om[2] != 0.f) | (om[3] != 0.f);
                     }
                     const int kz = j * a.A_pad + 4 * gq;
@@ -564,10 +623,13 @@ __global__ void __launch_bounds__(256, NEB ? 3 : 4) weights_kernel(WArgs a) {
                         float o[4];
     #pragma unroll
                         for (int c = 0; c < 4; ++c) o[c] = NEB ? om[c] * pu[u] : om[c];
-                        const float w0 = o[0] * wm.x, w1 = o[1] * wm.y, w2 = o[2] * wm.z, w3 = o[3] * wm.w;
-                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(w0, w1), h23 = __floats2bfloat162_rn(w2, w3);
-                        const __nv_bfloat162 l01 = __floats2bfloat162_rn(w0 - __low2float(h01), w1 - __high2float(h01));
-                        const __nv_bfloat162 l23 = __floats2bfloat162_rn(w2 - __low2float(h23), w3 - __high2float(h23));
+                        const float2 w01 = mul2(make_float2(o[0], o[1]), make_float2(wm.x, wm.y));
+                        const float2 w23 = mul2(make_float2(o[2], o[3]), make_float2(wm.z, wm.w));
+                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(w01.x, w01.y);
+                        const __nv_bfloat162 h23 = __floats2bfloat162_rn(w23.x, w23.y);
+                        const float2 r01 = sub2(w01, __bfloat1622float2(h01)), r23 = sub2(w23, __bfloat1622float2(h23));
+                        const __nv_bfloat162 l01 = __floats2bfloat162_rn(r01.x, r01.y);
+                        const __nv_bfloat162 l23 = __floats2bfloat162_rn(r23.x, r23.y);
                         uint2 hv, lv;
                         hv.x = *reinterpret_cast<const unsigned *>(&h01);
                         hv.y = *reinterpret_cast<const unsigned *>(&h23);
