@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(THREADS, 1) phot_simt_kernel(SArgs a) {
 #pragma unroll
             for (int j = 0; j < 4 * TN4; ++j) c[i][j] = 0.f;
 
-        contract_range<TN4, false>(a.W, a.L, a.K_pad, a.N_pad, a.n, m0, n0, a.k_lo, a.k_hi, 0, 0, As, Bs, c);
+        // the gradient mode's three sums per filter leave no registers for paired operands
+        contract_range<TN4, false, !GRAD>(a.W, a.L, a.K_pad, a.N_pad, a.n, m0, n0, a.k_lo, a.k_hi, 0, 0, As, Bs, c);
 
 #pragma unroll
         for (int i = 0; i < 8; ++i) {

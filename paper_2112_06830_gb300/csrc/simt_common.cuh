@@ -64,7 +64,9 @@ __device__ __forceinline__ void fma2(float &c0, float &c1, float a, float b0, fl
 // straight into Bs with cp.async; two buffers.  With MASK the weights of k
 // outside [kx0, kx1) are read as zero (a dust group's ages in a K step shared
 // with the neighbouring group).  Starts and ends with the block synchronised.
-template <int TN4_, bool MASK>
+// PAIRED: the products as paired FMAs (fma2), else scalar (the same sums; for
+// kernels whose other live registers leave no room for the operand pairs).
+template <int TN4_, bool MASK, bool PAIRED = true>
 __device__ __forceinline__ void contract_range(const float *__restrict__ W, const float *__restrict__ L, int K_pad,
                                                int N_pad, int64_t n, int64_t m0, int n0, int kb, int ke, int kx0,
                                                int kx1, float (*As)[BK][AS_LD], float (*Bs)[BK][64 * TN4_],
@@ -135,9 +137,15 @@ __device__ __forceinline__ void contract_range(const float *__restrict__ W, cons
                 bv[4 * m + 3] = b.w;
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                if constexpr (PAIRED) {
 #pragma unroll
-                for (int j = 0; j < 4 * TN4_; j += 2) fma2(c[i][j], c[i][j + 1], av[i], bv[j], bv[j + 1]);
+                    for (int j = 0; j < 4 * TN4_; j += 2) fma2(c[i][j], c[i][j + 1], av[i], bv[j], bv[j + 1]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4 * TN4_; ++j) c[i][j] = fmaf(av[i], bv[j], c[i][j]);
+                }
+            }
         }
         if (kt + 1 < KT) sstore(buf ^ 1);
         cp_async_wait_all();
