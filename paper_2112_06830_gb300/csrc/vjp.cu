@@ -17,6 +17,7 @@
 #include "dsps_internal.cuh"
 #include "epilogue.cuh"
 #include "simt_common.cuh"
+#include "f32x2.cuh"
 
 namespace dsps {
 
@@ -74,10 +75,16 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 
 #pragma unroll
     for (int q = 0; q < 4 * Q4; ++q) nb[q] = q < band.Q ? cq[r * QSTRIDE_MAX + q] : 0.f;
     // Grid indices col + i0 - 1 .. col + i0 + 2 are table rows col + i0 .. col +
-    // i0 + 3.  One pass covers 64 columns (two per lane, 32 apart), for which
-    // the warp needs 67 consecutive rows: each lane reduces its two rows (and
-    // lanes 0..2 the last three), the neighbours' come by shuffles.  The two
-    // halves' loads are independent, which hides the table latency.
+    // i0 + 3.  One pass covers 64 columns, for which the warp needs 67
+    // consecutive rows: lane l reduces rows col0 + l and col0 + 32 + l (its two
+    // chains as paired FP32 operations; consecutive lanes read consecutive
+    // rows) and lanes 0..2 rows col0 + 64 .. 66; the 67 sums go through a
+    // per-warp shared buffer, from which lane l takes the stencils of columns
+    // col0 + 2l and col0 + 2l + 1.  The two columns' attenuation and stencil are
+    // paired FP32 operations (f32x2.cuh: each column gets the numbers of the
+    // scalar operations), and their bf16 halves one 4-byte store each.
+    __shared__ __align__(16) float srow_all[8][68];
+    float *srow = srow_all[(threadIdx.x >> 5) & 7];
     auto reduce_row = [&](int row) {
         const float4 *tr = tab + (size_t)min(row, m_last) * Q4;
         float v = 0.f;
@@ -88,54 +95,77 @@ __global__ void __launch_bounds__(256) shat_kernel(const float *aux, const int2 
         }
         return v;
     };
-    auto shat_at = [&](int col, const float (&cm)[4]) {
-        const float ell = fmaf((float)col, cc.dell, cc.ell0);
-        float F = 1.f;
+    auto reduce_row2 = [&](int row_a, int row_b) {
+        const float4 *ta = tab + (size_t)min(row_a, m_last) * Q4;
+        const float4 *tb = tab + (size_t)min(row_b, m_last) * Q4;
+        float2 v = splat2(0.f);
+#pragma unroll
+        for (int qq = 0; qq < Q4; ++qq) {
+            const float4 a4 = __ldg(ta + qq), b4 = __ldg(tb + qq);
+            v = fma2v(splat2(nb[4 * qq + 3]), make_float2(a4.w, b4.w), v);
+            v = fma2v(splat2(nb[4 * qq + 2]), make_float2(a4.z, b4.z), v);
+            v = fma2v(splat2(nb[4 * qq + 1]), make_float2(a4.y, b4.y), v);
+            v = fma2v(splat2(nb[4 * qq + 0]), make_float2(a4.x, b4.x), v);
+        }
+        return v;
+    };
+    // Shat at columns c0, c0 + 1 from their stencil rows (cmd: row + d of each)
+    auto shat2 = [&](int c0, float2 cm0, float2 cm1, float2 cm2, float2 cm3) {
+        const float2 ell = fma2v(make_float2((float)c0, (float)(c0 + 1)), splat2(cc.dell), splat2(cc.ell0));
+        float2 F = splat2(1.f);
         if constexpr (DUST && BF16) {
             // split to bf16 hi + lo (16 significant bits): ex2.approx (relative
             // error below 2^-22) for the power law and the attenuation
-            float pw;
-            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pw) : "f"(rc.beta * ell));
-            const float u = cc.k0 ? __ldg(cc.k0 + col) * pw : pw;
-            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(F) : "f"(rc.alpha * dust_curve(cc, rc, u, col)));
+            const float2 bl = mul2(splat2(rc.beta), ell);
+            float2 pw;
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pw.x) : "f"(bl.x));
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pw.y) : "f"(bl.y));
+            float2 u = cc.k0 ? mul2(make_float2(__ldg(cc.k0 + c0), __ldg(cc.k0 + c0 + 1)), pw) : pw;
+            if (cc.bump) u = fma2v(splat2(rc.e), make_float2(__ldg(cc.bump + c0), __ldg(cc.bump + c0 + 1)), u);
+            const float2 ar = mul2(splat2(rc.alpha), u);
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(F.x) : "f"(ar.x));
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(F.y) : "f"(ar.y));
         } else if constexpr (DUST) {
-            F = exp2f(rc.alpha * dust_curve(cc, rc, dust_pow(cc, rc, ell, col), col));
+            F.x = exp2f(rc.alpha * dust_curve(cc, rc, dust_pow(cc, rc, ell.x, c0), c0));
+            F.y = exp2f(rc.alpha * dust_curve(cc, rc, dust_pow(cc, rc, ell.y, c0 + 1), c0 + 1));
         }
-        return col_kappa(cc, col) * F * fmaf(rc.w[0], cm[0], fmaf(rc.w[1], cm[1], fmaf(rc.w[2], cm[2], rc.w[3] * cm[3])));
+        float2 t = mul2(splat2(rc.w[3]), cm3);
+        t = fma2v(splat2(rc.w[2]), cm2, t);
+        t = fma2v(splat2(rc.w[1]), cm1, t);
+        t = fma2v(splat2(rc.w[0]), cm0, t);
+        return mul2(mul2(make_float2(col_kappa(cc, c0), col_kappa(cc, c0 + 1)), F), t);
     };
-    auto store = [&](int col, float sh) {
+    auto store2 = [&](int c0, float2 sh) {
         if (BF16) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(sh);
-            out_hi[r * N_pad + col] = h;
-            out_lo[r * N_pad + col] = __float2bfloat16_rn(sh - __bfloat162float(h));
+            const __nv_bfloat162 h = __floats2bfloat162_rn(sh.x, sh.y);
+            const float2 rr = sub2(sh, __bfloat1622float2(h));
+            *reinterpret_cast<__nv_bfloat162 *>(out_hi + r * N_pad + c0) = h;
+            *reinterpret_cast<__nv_bfloat162 *>(out_lo + r * N_pad + c0) = __floats2bfloat162_rn(rr.x, rr.y);
         } else {
-            out32[r * N_pad + col] = sh;
+            *reinterpret_cast<float2 *>(out32 + r * N_pad + c0) = sh;
         }
     };
     const int cend = kb1 * 32;
     for (int col0 = kb0 * 32; col0 < cend; col0 += 64) {
         const bool two = col0 + 32 < cend;
-        const int ca = col0 + lane, cb = ca + 32;
-        float va = 0.f, vb = 0.f, ve = 0.f;
+        const int c0 = col0 + 2 * lane;
+        float2 R = splat2(0.f);
+        float ve = 0.f;
         if (rc.valid) {
-            va = reduce_row(ca + rc.i0);
-            vb = reduce_row(cb + rc.i0);
-            if (two && lane < 3) ve = reduce_row(cb + 32 + rc.i0);
+            R = reduce_row2(col0 + lane + rc.i0, col0 + 32 + lane + rc.i0);
+            if (two && lane < 3) ve = reduce_row(col0 + 64 + lane + rc.i0);
         }
-        float cma[4], cmb[4];
-        cma[0] = va;
-        cmb[0] = vb;
-#pragma unroll
-        for (int d = 1; d < 4; ++d) {
-            const int src = (lane + d) & 31;
-            const float a1 = __shfl_sync(0xffffffffu, va, src);
-            const float b1 = __shfl_sync(0xffffffffu, vb, src);
-            const float e1 = __shfl_sync(0xffffffffu, ve, src);
-            cma[d] = lane + d < 32 ? a1 : b1;
-            cmb[d] = lane + d < 32 ? b1 : e1;
-        }
-        store(ca, rc.valid ? shat_at(ca, cma) : 0.f);
-        if (two) store(cb, rc.valid ? shat_at(cb, cmb) : 0.f);
+        __syncwarp();   // the previous pass's reads are done
+        srow[lane] = R.x;
+        srow[32 + lane] = R.y;
+        if (lane < 3) srow[64 + lane] = ve;
+        __syncwarp();
+        const float2 p01 = *reinterpret_cast<const float2 *>(srow + 2 * lane);
+        const float2 p23 = *reinterpret_cast<const float2 *>(srow + 2 * lane + 2);
+        const float p4 = srow[2 * lane + 4];
+        if (c0 < cend)
+            store2(c0, rc.valid ? shat2(c0, p01, make_float2(p01.y, p23.x), p23, make_float2(p23.y, p4))
+                                : splat2(0.f));
     }
 }
 
