@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(THREADS, 1) phot_simt_groups_kernel(SArgs a, c
         if (rc.valid) {
             Slide sl;
             const int nb = n0 + eh * EPI_COLS;
-            for (int jj = 0; jj < EPI_COLS; ++jj)
-                epi_node_plain<Q4>(acc, sl, Cs[er * CS_LD + eh * EPI_COLS + jj], nb + jj, rc, a.cc, a.tab, a.m_last);
+            const float *crow = Cs + er * CS_LD + eh * EPI_COLS;
+            for (int jj = 0; jj < EPI_COLS; jj += 2)
+                epi_node_plain2<Q4>(acc, sl, crow[jj], crow[jj + 1], nb + jj, rc, a.cc, a.tab, a.m_last);
             epi_close<Q4>(acc, sl, nb + EPI_COLS, rc, a.tab, a.m_last);
         }
         __syncthreads();

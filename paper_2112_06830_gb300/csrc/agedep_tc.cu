@@ -474,8 +474,9 @@ phot_tc_groups_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_c
 #pragma unroll
                 for (int c = 0; c < EPI_COLS / 32; ++c)
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        epi_node_plain<Q4>(acc, sl, run[c][j], nb + c * 32 + j, rc, a.cc, a.tab, a.m_last);
+                    for (int j = 0; j < 32; j += 2)
+                        epi_node_plain2<Q4>(acc, sl, run[c][j], run[c][j + 1], nb + c * 32 + j, rc, a.cc, a.tab,
+                                            a.m_last);
                 epi_close<Q4>(acc, sl, nb + EPI_COLS, rc, a.tab, a.m_last);
 #pragma unroll
                 for (int q = 0; q < 4 * Q4; ++q) accs[q] = acc[q];

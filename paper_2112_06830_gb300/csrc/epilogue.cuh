@@ -123,6 +123,33 @@ __device__ __forceinline__ void epi_node(float (&acc)[4 * Q4], Slide &sl, float 
     acc_row<Q4>(acc, tab, min(n + rc.i0, m_last), y);
 }
 
+// Nodes n and n + 1 (n even within a run of columns): the operations of two
+// epi_node calls, paired where they do not depend on each other (f32x2.cuh:
+// the same numbers); the two filter rows are then added in node order.
+template <int Q4>
+__device__ __forceinline__ void epi_node2(float (&acc)[4 * Q4], Slide &sl, float S0, float S1, int n,
+                                          const RowConst &rc, const ColConst &cc, const float4 *__restrict__ tab,
+                                          int m_last) {
+    const float2 ell = fma2v(make_float2((float)n, (float)(n + 1)), splat2(cc.dell), splat2(cc.ell0));
+    const float2 be = mul2(splat2(rc.beta), ell);
+    float2 u = make_float2(exp2f(be.x), exp2f(be.y));
+    if (cc.k0) u = mul2(make_float2(__ldg(cc.k0 + n), __ldg(cc.k0 + n + 1)), u);
+    if (cc.bump) u = fma2v(splat2(rc.e), make_float2(__ldg(cc.bump + n), __ldg(cc.bump + n + 1)), u);
+    const float2 ac = mul2(splat2(rc.alpha), u);
+    const float2 F = make_float2(exp2f(ac.x), exp2f(ac.y));
+    const float2 v = mul2(mul2(make_float2(S0, S1), F), make_float2(col_kappa(cc, n), col_kappa(cc, n + 1)));
+    // y_n = w0 v_n + w1 v_n-1 + w2 v_n-2 + w3 v_n-3 and y_n+1 likewise, innermost term first
+    float2 y = mul2(splat2(rc.w[3]), make_float2(sl.v3, sl.v2));
+    y = fma2v(splat2(rc.w[2]), make_float2(sl.v2, sl.v1), y);
+    y = fma2v(splat2(rc.w[1]), make_float2(sl.v1, v.x), y);
+    y = fma2v(splat2(rc.w[0]), v, y);
+    sl.v3 = sl.v1;
+    sl.v2 = v.x;
+    sl.v1 = v.y;
+    acc_row<Q4>(acc, tab, min(n + rc.i0, m_last), y.x);
+    acc_row<Q4>(acc, tab, min(n + 1 + rc.i0, m_last), y.y);
+}
+
 // The attenuation of node n, F = 10^(-0.4 Av c_n) (Eq. attenuation) with the
 // curve of rc (c_n = u + e D0_n).
 __device__ __forceinline__ float dust_factor(const ColConst &cc, const RowConst &rc, int n) {
@@ -142,6 +169,23 @@ __device__ __forceinline__ void epi_node_plain(float (&acc)[4 * Q4], Slide &sl, 
     sl.v2 = sl.v1;
     sl.v1 = v;
     acc_row<Q4>(acc, tab, min(n + rc.i0, m_last), y);
+}
+
+// epi_node_plain for nodes n and n + 1, paired like epi_node2.
+template <int Q4>
+__device__ __forceinline__ void epi_node_plain2(float (&acc)[4 * Q4], Slide &sl, float S0, float S1, int n,
+                                                const RowConst &rc, const ColConst &cc,
+                                                const float4 *__restrict__ tab, int m_last) {
+    const float2 v = mul2(make_float2(S0, S1), make_float2(col_kappa(cc, n), col_kappa(cc, n + 1)));
+    float2 y = mul2(splat2(rc.w[3]), make_float2(sl.v3, sl.v2));
+    y = fma2v(splat2(rc.w[2]), make_float2(sl.v2, sl.v1), y);
+    y = fma2v(splat2(rc.w[1]), make_float2(sl.v1, v.x), y);
+    y = fma2v(splat2(rc.w[0]), v, y);
+    sl.v3 = sl.v1;
+    sl.v2 = v.x;
+    sl.v1 = v.y;
+    acc_row<Q4>(acc, tab, min(n + rc.i0, m_last), y.x);
+    acc_row<Q4>(acc, tab, min(n + 1 + rc.i0, m_last), y.y);
 }
 
 // Closing rows of a run that ended at node b-1 (grid rows b+i0-1 .. b+i0+1).

@@ -345,14 +345,16 @@ phot_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant
                         if (lane == 0) mbar_arrive(acce0 + 8 * as);
                     }
                     if (rc.valid) {
+                        if constexpr (GRAD) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            if constexpr (GRAD)
+                            for (int j = 0; j < 32; ++j)
                                 epi_node_grad<Q4>(acc, sl, __uint_as_float(r[j]), nb + c * 32 + j, rc, a.cc, a.tab,
                                                   a.m_last);
-                            else
-                                epi_node<Q4>(acc[0], sl[0], __uint_as_float(r[j]), nb + c * 32 + j, rc, a.cc,
-                                             a.tab, a.m_last);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 2)
+                                epi_node2<Q4>(acc[0], sl[0], __uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                              nb + c * 32 + j, rc, a.cc, a.tab, a.m_last);
                         }
                     }
                 }
