@@ -34,6 +34,7 @@
 #include "dsps_internal.cuh"
 #include "epilogue.cuh"
 #include "tc_common.cuh"
+#include "f32x2.cuh"
 
 namespace dsps {
 
@@ -162,14 +163,21 @@ template <bool SALIM, bool BUMP>
 __device__ __forceinline__ void add_group_chunk(float *run, const uint32_t (&r)[16], int n0, float alpha, float beta,
                                                 float ustep, float e, const ColConst &cc) {
     float u = ex2_fast(beta * fmaf((float)n0, cc.dell, cc.ell0));
+    // two nodes per paired FP32 operation (u itself is a running product)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        float cn = u;
-        if constexpr (SALIM) cn *= __ldg(cc.k0 + n0 + j);
-        if constexpr (BUMP) cn = fmaf(e, __ldg(cc.bump + n0 + j), cn);
-        const float F = ex2_fast(alpha * cn);
-        run[j] = fmaf(__uint_as_float(r[j]), F, run[j]);
+    for (int j = 0; j < 16; j += 2) {
+        float2 cn;
+        cn.x = u;
         u *= ustep;
+        cn.y = u;
+        u *= ustep;
+        if constexpr (SALIM) cn = mul2(cn, make_float2(__ldg(cc.k0 + n0 + j), __ldg(cc.k0 + n0 + j + 1)));
+        if constexpr (BUMP) cn = fma2v(splat2(e), make_float2(__ldg(cc.bump + n0 + j), __ldg(cc.bump + n0 + j + 1)), cn);
+        const float2 ac = mul2(splat2(alpha), cn);
+        const float2 rr = fma2v(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
+                                make_float2(ex2_fast(ac.x), ex2_fast(ac.y)), make_float2(run[j], run[j + 1]));
+        run[j] = rr.x;
+        run[j + 1] = rr.y;
     }
 }
 
@@ -184,19 +192,31 @@ __device__ __forceinline__ void grad_group_chunk(float &sA, float &sD, const flo
                                                  const ColConst &cc, float lell0, float ldell) {
     float u = ex2_fast(beta * fmaf((float)n0, cc.dell, cc.ell0));
     float lj = fmaf((float)n0, ldell, lell0);   // ln(lam_n / lam_V), stepped
+    // two nodes per paired FP32 operation; u, lj and the two sums run node by node
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        float cp = u;
-        if constexpr (SALIM) cp *= __ldg(cc.k0 + n0 + j);
-        const float bj = BUMP ? __ldg(cc.bump + n0 + j) : 0.f;
-        const float cn = BUMP ? fmaf(e, bj, cp) : cp;
-        const float x = __uint_as_float(r[j]) * ex2_fast(alpha * cn) * gk[j];
-        sA = fmaf(x, cn, sA);
-        float dc = cp * lj;
-        lj += ldell;
-        if constexpr (BUMP) dc = fmaf(ed, bj, dc);
-        sD = fmaf(x, dc, sD);
+    for (int j = 0; j < 16; j += 2) {
+        float2 cp, l2;
+        cp.x = u;
         u *= ustep;
+        cp.y = u;
+        u *= ustep;
+        l2.x = lj;
+        lj += ldell;
+        l2.y = lj;
+        lj += ldell;
+        if constexpr (SALIM) cp = mul2(cp, make_float2(__ldg(cc.k0 + n0 + j), __ldg(cc.k0 + n0 + j + 1)));
+        const float2 bj = BUMP ? make_float2(__ldg(cc.bump + n0 + j), __ldg(cc.bump + n0 + j + 1)) : splat2(0.f);
+        const float2 cn = BUMP ? fma2v(splat2(e), bj, cp) : cp;
+        const float2 ac = mul2(splat2(alpha), cn);
+        const float2 x = mul2(mul2(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
+                                   make_float2(ex2_fast(ac.x), ex2_fast(ac.y))),
+                              make_float2(gk[j], gk[j + 1]));
+        float2 dc = mul2(cp, l2);
+        if constexpr (BUMP) dc = fma2v(splat2(ed), bj, dc);
+        sA = fmaf(x.x, cn.x, sA);
+        sD = fmaf(x.x, dc.x, sD);
+        sA = fmaf(x.y, cn.y, sA);
+        sD = fmaf(x.y, dc.y, sD);
     }
 }
 

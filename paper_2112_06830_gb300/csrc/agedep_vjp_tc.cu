@@ -33,6 +33,7 @@
 #include "dsps_internal.cuh"
 #include "epilogue.cuh"
 #include "tc_common.cuh"
+#include "f32x2.cuh"
 
 namespace dsps {
 
@@ -88,8 +89,8 @@ __device__ __forceinline__ void write_a_row_part(unsigned char *a_hi, unsigned c
 #pragma unroll
     for (int q = 0; q < NPT / 2; ++q) {
         const __nv_bfloat162 hv = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
-        const __nv_bfloat162 lv =
-            __floats2bfloat162_rn(x[2 * q] - __low2float(hv), x[2 * q + 1] - __high2float(hv));
+        const float2 rv = sub2(make_float2(x[2 * q], x[2 * q + 1]), __bfloat1622float2(hv));
+        const __nv_bfloat162 lv = __floats2bfloat162_rn(rv.x, rv.y);
         hw[q] = *reinterpret_cast<const uint32_t *>(&hv);
         lw[q] = *reinterpret_cast<const uint32_t *>(&lv);
     }
@@ -317,17 +318,26 @@ vjp_groups_tc_kernel(const __grid_constant__ CUtensorMap tmB_hi0, const __grid_c
                 const int n0 = kb * BK + NPT * h;
                 float x[NPT];
                 float uc = ex2_approx(beta * fmaf((float)n0, a.cc.dell, a.cc.ell0));
+                // two nodes per paired FP32 operation (the power law itself is a
+                // running product, node by node)
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
-                    const float g4[4] = {gv[q].x, gv[q].y, gv[q].z, gv[q].w};
+                    const float2 g2[2] = {make_float2(gv[q].x, gv[q].y), make_float2(gv[q].z, gv[q].w)};
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
+                    for (int e = 0; e < 4; e += 2) {
                         const int nn = n0 + 4 * q + e;
-                        float cn = uc;
-                        if constexpr ((LAW & 1) != 0) cn *= __ldg(a.cc.k0 + nn);
-                        if constexpr ((LAW & 2) != 0) cn = fmaf(eb, __ldg(a.cc.bump + nn), cn);
-                        x[4 * q + e] = g4[e] * ex2_approx(alpha * cn);
+                        float2 cn;
+                        cn.x = uc;
                         uc *= ustep;
+                        cn.y = uc;
+                        uc *= ustep;
+                        if constexpr ((LAW & 1) != 0) cn = mul2(cn, make_float2(__ldg(a.cc.k0 + nn), __ldg(a.cc.k0 + nn + 1)));
+                        if constexpr ((LAW & 2) != 0)
+                            cn = fma2v(splat2(eb), make_float2(__ldg(a.cc.bump + nn), __ldg(a.cc.bump + nn + 1)), cn);
+                        const float2 ac = mul2(splat2(alpha), cn);
+                        const float2 xv = mul2(g2[e >> 1], make_float2(ex2_approx(ac.x), ex2_approx(ac.y)));
+                        x[4 * q + e] = xv.x;
+                        x[4 * q + e + 1] = xv.y;
                     }
                 }
 #pragma unroll
