@@ -1047,8 +1047,18 @@ __global__ void __launch_bounds__(256, NEB ? 2 : 4) weights_vjp_kernel(WArgs a, 
             fr4[c] = i < a.n_age ? frac[i] : 0.f;
             fb4[c] = 0.f;
         }
+        // the next edge's adjoint row entries (and multipliers) are loaded one
+        // edge ahead, so that the loads overlap the current edge's arithmetic
+        float4 wv_next = *reinterpret_cast<const float4 *>(wrow + 4 * gq);
+        float4 m_next = scaled ? __ldg(reinterpret_cast<const float4 *>(a.wmul + 4 * gq)) : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int e = 0; e < nz; ++e) {
             const int kz = e * a.A_pad + 4 * gq;
+            float4 wv = wv_next;
+            const float4 m = m_next;
+            if (e + 1 < nz) {
+                wv_next = *reinterpret_cast<const float4 *>(wrow + kz + a.A_pad);
+                if (scaled) m_next = __ldg(reinterpret_cast<const float4 *>(a.wmul + kz + a.A_pad));
+            }
             float2 u01 = splat2(0.f), u23 = splat2(0.f);   // the four ages in two pairs
             if (e > 0) {
                 const float ze = __ldg(a.zedge + e);
@@ -1057,9 +1067,7 @@ __global__ void __launch_bounds__(256, NEB ? 2 : 4) weights_vjp_kernel(WArgs a, 
                 if (tri && fminf(fminf(u01.x, u01.y), fminf(u23.x, u23.y)) >= 3.f) break;
             }
             const float u[4] = {u01.x, u01.y, u23.x, u23.y};
-            float4 wv = *reinterpret_cast<const float4 *>(wrow + kz);
             if (scaled) {
-                const float4 m = __ldg(reinterpret_cast<const float4 *>(a.wmul + kz));
                 wv.x *= m.x;
                 wv.y *= m.y;
                 wv.z *= m.z;
