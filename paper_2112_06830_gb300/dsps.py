@@ -418,7 +418,11 @@ class Context:
         return out
 
     def band_coverage(self, params, set_id, stream=None):
-        """[G, Q] fraction of each band's filter response on the redshifted SSP grid."""
+        """[G, Q] fraction of each band's filter response on the redshifted SSP grid
+        (include/dsps.h: dsps_band_coverage).  A magnitude whose band has coverage
+        below about 1e-8 is set by the last points of the filter's far tail and can
+        be off by up to ~0.2 mag; at or above it the precision form's tolerance
+        holds.  NaN where z is not finite or z <= 0 (observer-frame sets)."""
         import torch
         assert params.is_cuda and params.dtype == torch.float32 and params.shape[0] == self.npar
         params = params.contiguous()
