@@ -51,6 +51,8 @@ def test_coverage_matches_the_filter_tables(rest):
     assert ((ref <= 1e-30) <= (cov <= 1e-30)).all()
     assert (err[ref > 1e-30] <= 1e-5).all()
     assert ((cov >= 0) & (cov <= 1)).all()
+    empty = ctx.band_coverage(torch.from_numpy(np.ascontiguousarray(p32[:, :0])).cuda(), sid)
+    assert tuple(empty.shape) == (0, 16)
     p32[11, :3] = [0.0, -1.0, np.nan]
     cov2 = ctx.band_coverage(torch.from_numpy(p32).cuda(), sid).cpu().numpy()
     if rest:
